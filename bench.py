@@ -1,0 +1,339 @@
+"""Benchmark: lnL + gradient evaluations per second of the epoch-model tree
+likelihood on one B300, with the partials pass against the HBM roofline.
+
+Workload (default): GTR nucleotide model, 3 epochs at 1/3 and 2/3 of the
+root height, 500-taxon coalescent tree, 10,000 patterns with weights
+U{1..20}, 4 discrete-gamma categories (alpha = 0.5), FP32 partials with
+per-pattern power-of-two scaling; FP64 eigendecomposition, segment
+exponentials and epoch products.  Synthetic seeded data.
+
+A step is one pass of the whole path: branch segmentation, normalisation and
+eigendecomposition of every Q_k, segment exponentials and epoch products,
+pruning with rescaling, root log-sum, pre-order adjoint, per-branch adjoints
+and the chain rule to node heights, boundaries, model parameters and branch
+rates.  `value` is measured with all inputs resident on the device (CUDA
+graph replays, CUDA events on the library's stream); `e2e` goes through the
+C ABI from host arrays every step (uploads of Q, dQ, tree, tip codes and
+weights; lnL and gradient read back), wall clock with the device drained.
+
+`--impl reference` times the FP64 CPU oracle on a bounded sample of the same
+workload (the reference arm of this comparison).
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import os
+import subprocess
+import sys
+import threading
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+METRIC = "lnL+gradient evals/sec & partials GB/s (%HBM roofline) vs plain FP64 GPU path at <=1e-5 rel"
+UNIT = "evals/s"
+
+
+def hbm_peak():
+    try:
+        with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as f:
+            return float(json.load(f)["hbm_gbs"]), "measured"
+    except Exception:
+        return 6400.0, "fallback"
+
+
+def make_workload(name):
+    import synth
+
+    if name == "gtr":
+        w = synth.config2()
+        return w, {"workload": "GTR 3-epoch, 500-taxon coalescent, 10,000 patterns, 4 gamma categories",
+                   "taxa": 500, "patterns": 10000, "categories": 4, "states": 4, "epochs": 3,
+                   "params": int(w.n_params)}
+    if name == "gy94":
+        w = synth.config3()
+        return w, {"workload": "GY94 61-state 4-epoch, 128-taxon coalescent, 5,000 codon sites",
+                   "taxa": 128, "patterns": int(w.n_patterns), "categories": 4, "states": 61,
+                   "epochs": 4, "params": int(w.n_params)}
+    raise SystemExit(f"unknown workload {name}")
+
+
+# ---------------------------------------------------------------------------
+# clocks sampled during the timed region
+# ---------------------------------------------------------------------------
+class ClockSampler:
+    Q = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+         "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+         "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, index=0):
+        self.index = index
+        self.proc = None
+        self.lines = []
+
+    def start(self):
+        try:
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", "-i", str(self.index), f"--query-gpu={self.Q}",
+                 "--format=csv,noheader,nounits", "-lms", "100"],
+                stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+            self.thread = threading.Thread(target=self._read, daemon=True)
+            self.thread.start()
+        except Exception:
+            self.proc = None
+
+    def _read(self):
+        for line in self.proc.stdout:
+            self.lines.append(line.strip())
+
+    def stop(self):
+        if not self.proc:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["unsampled"]}
+        self.proc.terminate()
+        try:
+            self.proc.wait(timeout=5)
+        except Exception:
+            self.proc.kill()
+        sm, smax, reasons = [], None, set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for ln in self.lines:
+            f = [x.strip() for x in ln.split(",")]
+            if len(f) < 9:
+                continue
+            try:
+                sm.append(float(f[1]))
+                smax = float(f[2])
+            except ValueError:
+                continue
+            for n, v in zip(names, f[5:9]):
+                if v.lower().startswith("active"):
+                    reasons.add(n)
+        return {"sm_mhz": float(np.median(sm)) if sm else None, "sm_max_mhz": smax,
+                "reasons": sorted(reasons), "samples": len(sm)}
+
+
+# ---------------------------------------------------------------------------
+# algorithmic bytes of one partials pass (pruning over all internal nodes,
+# K = 4 FP32 layout: 16 B per (category, pattern) vector, 1 B tip codes,
+# 2 B scale exponents) plus the root log-sum
+# ---------------------------------------------------------------------------
+def partials_bytes(w):
+    N, P, C = w.n_taxa, w.n_patterns, w.n_categories
+    nn = 2 * N - 1
+    vec = 16 * C * P
+    total = 0
+    for u in range(N, nn):
+        total += vec + 2 * P                     # write partials + exponents
+    for v in range(nn):
+        if w.parent[v] < 0:
+            continue
+        total += vec if v >= N else P           # read child partials / tip codes
+    total += (N - 1) * 2 * P + vec + 8 * P + 16 * P  # root: exponents, root partial, weights, outputs
+    return total
+
+
+def run_ours(args, w, cfg, rank, world):
+    import torch
+
+    from paper_1309_3075_b300 import binding
+    from paper_1309_3075_b300.binding import EPOCH_FP32, EPOCH_FP64, EpochLikelihood
+
+    dev = rank % max(torch.cuda.device_count(), 1)
+    torch.cuda.set_device(dev)
+    stream = torch.cuda.Stream()
+    lik = EpochLikelihood(w, precision=EPOCH_FP32, cuda_stream=stream.cuda_stream)
+    nn = 2 * w.n_taxa - 1
+
+    # ---- device-resident timing: K graph replays --------------------------
+    for _ in range(args.warmup):
+        binding.epoch_evaluate_async(lik.ctx, True)
+    torch.cuda.synchronize()
+    l0, _ = lik.counters()
+    clocks = ClockSampler(dev)
+    clocks.start()
+    if world > 1:
+        torch.distributed.barrier()
+    torch.cuda.synchronize()
+    ev0, ev1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    ev0.record(stream)
+    for _ in range(args.steps):
+        binding.epoch_evaluate_async(lik.ctx, True)
+    ev1.record(stream)
+    torch.cuda.synchronize()
+    ms = ev0.elapsed_time(ev1)
+    if world > 1:
+        t = torch.tensor([ms], device="cuda")
+        torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MAX)
+        ms = float(t.item())
+    clk = clocks.stop()
+    l1, _ = lik.counters()
+    launches = l1 - l0
+    lnl32, g32 = binding.epoch_read_results(lik.ctx, nn, w.n_epochs, lik.n_params, True)
+    ms_step = ms / args.steps
+
+    # ---- the partials pass alone (dominant kernel), same stream ------------
+    for _ in range(3):
+        binding.epoch_update_partials(lik.ctx)
+    torch.cuda.synchronize()
+    reps = max(args.steps, 10)
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    e0.record(stream)
+    for _ in range(reps):
+        binding.epoch_update_partials(lik.ctx)
+    e1.record(stream)
+    torch.cuda.synchronize()
+    part_ms = e0.elapsed_time(e1) / reps
+    pbytes = partials_bytes(w)
+    achieved = pbytes / (part_ms * 1e-3) / 1e9
+    peak, peak_kind = hbm_peak()
+
+    # ---- e2e through the C ABI from host arrays ----------------------------
+    Q, dQ = np.ascontiguousarray(w.Q), np.ascontiguousarray(w.dQ)
+    tips = np.ascontiguousarray(w.tips, dtype=np.int32)
+    for _ in range(2):
+        lik.load(w)
+        binding.epoch_evaluate_async(lik.ctx, True)
+        binding.epoch_read_results(lik.ctx, nn, w.n_epochs, lik.n_params, True)
+    torch.cuda.synchronize()
+    e_steps = max(3, min(args.steps, 20))
+    t0 = time.perf_counter()
+    for _ in range(e_steps):
+        binding.epoch_set_rate_matrices(lik.ctx, Q, w.pi, 1, 1)
+        binding.epoch_set_rate_derivatives(lik.ctx, dQ)
+        binding.epoch_set_boundaries(lik.ctx, w.boundaries)
+        binding.epoch_set_categories(lik.ctx, w.cat_rates, w.cat_weights)
+        binding.epoch_set_tree(lik.ctx, w.heights, w.parent)
+        binding.epoch_set_tip_data(lik.ctx, tips, w.pattern_weights)
+        binding.epoch_evaluate_async(lik.ctx, True)
+        binding.epoch_read_results(lik.ctx, nn, w.n_epochs, lik.n_params, True)
+    torch.cuda.synchronize()
+    e2e_s = (time.perf_counter() - t0) / e_steps
+    h2d = (Q.nbytes + dQ.nbytes + w.pi.nbytes + w.boundaries.nbytes + 2 * 8 * w.n_categories
+           + w.heights.nbytes + w.parent.astype(np.int32).nbytes + 8 * nn
+           + w.n_taxa * w.n_patterns + w.pattern_weights.nbytes)
+    d2h = 8 + 8 * (2 * nn + w.n_epochs - 1 + lik.n_params)
+
+    # ---- plain FP64 GPU path on the same workload --------------------------
+    lik64 = EpochLikelihood(w, precision=EPOCH_FP64, cuda_stream=stream.cuda_stream)
+    for _ in range(2):
+        binding.epoch_evaluate_async(lik64.ctx, True)
+    torch.cuda.synchronize()
+    f_steps = max(3, min(args.steps, 10))
+    f0, f1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    f0.record(stream)
+    for _ in range(f_steps):
+        binding.epoch_evaluate_async(lik64.ctx, True)
+    f1.record(stream)
+    torch.cuda.synchronize()
+    fp64_ms = f0.elapsed_time(f1) / f_steps
+    lnl64, g64 = binding.epoch_read_results(lik64.ctx, nn, w.n_epochs, lik64.n_params, True)
+    lik64.close()
+    lik.close()
+    rel_err = abs(lnl32 - lnl64) / abs(lnl64)
+    grad_err = float(np.abs(g32["heights"] - g64["heights"]).max() / np.abs(g64["heights"]).max())
+
+    out = {
+        "metric": METRIC,
+        "value": world * 1e3 / ms_step,
+        "unit": UNIT,
+        "n_gpus": world,
+        "steps": args.steps,
+        "warmup": args.warmup,
+        "ms_per_step": ms_step,
+        "higher_is_better": True,
+        "scaling": "weak",
+        "vs_baseline": None,
+        "dtype": "f32",
+        "data": "synthetic (seeded coalescent tree, simulated alignment)",
+        "config": {**cfg, "parallelism": f"replicas{world}",
+                   "l2": "working set > L2 (partials 320 MB + adjoint partials 320 MB per step)"},
+        "e2e": {"value": world / e2e_s, "unit": UNIT, "h2d_bytes_per_step": int(h2d),
+                "d2h_bytes_per_step": int(d2h)},
+        "gpu_launches": int(launches),
+        "roofline": {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s",
+                     "frac": achieved / peak, "traffic": None, "peak_source": peak_kind,
+                     "kernel": "partials pass (post-order pruning + rescaling + root)",
+                     "ms_per_launch": part_ms, "algorithmic_bytes": int(pbytes)},
+        "fp64_gpu": {"value": 1e3 / fp64_ms, "unit": UNIT, "ms_per_step": fp64_ms,
+                     "lnL_rel_err_fp32_vs_fp64": rel_err, "grad_rel_err_fp32_vs_fp64": grad_err,
+                     "speedup": fp64_ms / ms_step},
+        "lnL": lnl32,
+        "clocks": clk,
+    }
+    return out
+
+
+def oracle_sample_rate(w, budget_s):
+    """Oracle lnL + gradient on pattern slices of the workload; returns
+    (evals/s scaled to the full workload, description, cores)."""
+    import oracle
+
+    P = w.n_patterns
+    sl = min(P, 1000)
+    sub = w.slice_patterns(0, sl)
+    oracle.build()
+    n = 0
+    t0 = time.perf_counter()
+    while True:
+        oracle.gradient(sub)
+        n += 1
+        if time.perf_counter() - t0 > budget_s:
+            break
+    dt = time.perf_counter() - t0
+    per_full = dt / n * (P / sl)
+    return 1.0 / per_full, f"{n} lnL+gradient evaluations on the first {sl} of {P} patterns " \
+                           f"(oracle, single thread), scaled by {P}/{sl}", 1
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=50)
+    ap.add_argument("--warmup", type=int, default=5)
+    ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    ap.add_argument("--workload", default="gtr", choices=["gtr", "gy94"])
+    ap.add_argument("--cpu-seconds", type=float, default=12.0)
+    args = ap.parse_args()
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    w, cfg = make_workload(args.workload)
+
+    if args.impl == "reference":
+        if rank != 0:
+            return
+        rate, sample, cores = oracle_sample_rate(w, args.cpu_seconds * max(args.steps, 1) / 50)
+        out = {"impl": "reference", "metric": METRIC, "value": rate, "unit": UNIT, "n_gpus": 0,
+               "steps": args.steps, "warmup": args.warmup, "higher_is_better": True,
+               "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+               "config": {**cfg, "parallelism": "cpu"},
+               "cpu_baseline": {"value": rate, "unit": UNIT, "cores": cores, "kind": "oracle",
+                                "sample": sample},
+               "e2e": {"value": rate, "unit": UNIT, "h2d_bytes_per_step": 0,
+                       "d2h_bytes_per_step": 0}}
+        print(json.dumps(out))
+        return
+
+    if world > 1:
+        import torch
+        import torch.distributed as dist
+
+        torch.cuda.set_device(int(os.environ.get("LOCAL_RANK", "0")))
+        dist.init_process_group("nccl")
+    out = run_ours(args, w, cfg, rank, world)
+    if rank == 0:
+        rate, sample, cores = oracle_sample_rate(w, args.cpu_seconds)
+        out["cpu_baseline"] = {"value": rate, "unit": UNIT, "cores": cores, "kind": "oracle",
+                               "sample": sample}
+        print(json.dumps(out))
+    if world > 1:
+        import torch.distributed as dist
+
+        dist.destroy_process_group()
+
+
+if __name__ == "__main__":
+    main()

@@ -1,0 +1,222 @@
+/*
+ * epoch.h -- C ABI of libepoch, a B300 (sm_103a) library for the tree
+ * likelihood and its gradient under the epoch (time-heterogeneous)
+ * substitution model of Bielejec, Lemey, Baele, Rambaut and Suchard,
+ * "Inferring heterogeneous evolutionary processes through time"
+ * (arXiv 1309.3075).
+ *
+ * Model (paper, Methods and "Relaxing time-homogeneity"):
+ *   S rate matrices Q_s (K x K, rows sum to zero); epoch boundaries
+ *   b_1 < ... < b_{E-1}; epoch e is governed by Q_{phi(e)}.  For the branch
+ *   above node v (parent u) and rate category c the transition matrix is the
+ *   time-ordered product of exp(r_v rho_c dt_k Q_{phi(e_k)}) over the epoch
+ *   segments k the branch spans, the segment at the parent end on the left
+ *   (Eq. matrixProduct, Eq. convolution).  Felsenstein pruning
+ *   (Eq. partial_likelihood) runs over all site patterns and categories and
+ *   lnL = sum_p n_p log sum_c w_c sum_i pi_i L_root(c,p,i).
+ *
+ * Conventions used by every entry point:
+ *   - Times are HEIGHTS before the youngest tip (>= 0 not required, only
+ *     parent height >= child height).  Epoch 0 = [0, b_1) is the youngest,
+ *     epoch E-1 = [b_{E-1}, +inf) the oldest.  A segment belongs to the epoch
+ *     of its lower end; pieces of zero length are dropped, except that a
+ *     zero-length branch keeps one zero-length segment (P = I) so its height
+ *     derivatives are one-sided.
+ *   - Matrices are row-major FP64, row = parent (ancestral) state.
+ *   - Nodes: tips 0..N-1, internal nodes N..2N-2; parent[root] = -1; the tree
+ *     is binary (every internal node has exactly two children).
+ *   - Tip codes: 0..K-1 observed state, K = missing (every state allowed),
+ *     K+1+m = ambiguity mask m (see epoch_set_ambiguity_masks).
+ *   - Every Q_s is normalised separately (when asked) so that
+ *     sum_i pi_i q_ii = -1 (Methods, after Eq. makeprobs); pi is also the root
+ *     distribution.
+ *   - Host arrays passed in are copied before the call returns; the caller
+ *     keeps ownership.  The context owns all device memory it allocates.
+ *   - Calls are ordered: create -> set_rate_matrices -> set_categories ->
+ *     set_tree -> set_tip_data -> compute_branch_matrices -> update_partials
+ *     -> log_likelihood / gradient.  A call whose inputs are not yet set
+ *     returns EPOCH_ERR_ORDER.  Setting an input again invalidates the
+ *     results that depend on it.
+ *   - Nothing aborts.  Invalid arguments are rejected on the host before any
+ *     device work (EPOCH_ERR_ARG, EPOCH_ERR_NUMERIC); device-side failures
+ *     (non-finite partials, an eigensolver that did not converge, a bounded
+ *     wait that ran out) are reported through a device status word read at
+ *     the next synchronising call.  epoch_last_error() gives a message.
+ *     lnL = -inf for an impossible pattern is a valid result, not an error.
+ *   - All device work is enqueued on the context's CUDA stream.  Calls
+ *     documented "async" return without synchronising; calls that return
+ *     host results synchronise that stream.
+ */
+#ifndef EPOCH_H
+#define EPOCH_H
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+#define EPOCH_MAX_STATES 64   /* K <= 64                                   */
+#define EPOCH_MAX_EPOCHS 32   /* E <= 32                                   */
+#define EPOCH_MAX_CATEGORIES 16
+
+typedef struct epoch_ctx epoch_ctx; /* opaque; owns all device memory */
+
+typedef enum {
+  EPOCH_OK = 0,
+  EPOCH_ERR_ARG = 1,      /* invalid argument (size, index, NULL, order of heights) */
+  EPOCH_ERR_ORDER = 2,    /* an input this call needs has not been set        */
+  EPOCH_ERR_CAPACITY = 3, /* more taxa/patterns than the context was made for */
+  EPOCH_ERR_NUMERIC = 4,  /* NaN/negative rates, rows not summing to 0, ...   */
+  EPOCH_ERR_CUDA = 5,     /* a CUDA runtime call failed                       */
+  EPOCH_ERR_TIMEOUT = 6,  /* a bounded device-side wait ran out               */
+  EPOCH_ERR_UNSUPPORTED = 7 /* valid request this build does not provide      */
+} epoch_status;
+
+typedef enum {
+  EPOCH_FP64 = 0,     /* plain FP64 path: one thread per (pattern, category, state) */
+  EPOCH_FP32 = 1,     /* FP32 partials with per-pattern power-of-two rescaling */
+  EPOCH_FP32_TC = 2   /* FP32 partials; dense contractions (K >= 16) on tensor
+                         cores with 3-term BF16 splitting, FP32 accumulate   */
+} epoch_precision;
+
+/* ---- context ----------------------------------------------------------- */
+
+/* Create a context.
+ *   states       K, 2..EPOCH_MAX_STATES
+ *   n_epochs     E >= 1
+ *   boundaries   [E-1] heights, strictly increasing (NULL if E == 1)
+ *   epoch_to_matrix [E] phi(e) in 0..n_matrices-1, or NULL = identity (S = E)
+ *   n_matrices   S
+ *   max_taxa     largest N a later epoch_set_tree may use (>= 2)
+ *   n_patterns   P >= 1 (site patterns)
+ *   n_categories C, 1..EPOCH_MAX_CATEGORIES
+ *   precision    an epoch_precision value
+ *   cuda_stream  cudaStream_t to enqueue on, or NULL for a private stream
+ * Allocates every device buffer the path needs (partials, scale exponents,
+ * branch matrices, work lists).  On error *out is NULL. */
+epoch_status epoch_create(epoch_ctx **out, int states, int n_epochs,
+                          const double *boundaries, const int *epoch_to_matrix,
+                          int n_matrices, int max_taxa, int n_patterns,
+                          int n_categories, int precision, void *cuda_stream);
+
+void epoch_destroy(epoch_ctx *ctx);
+
+/* Human-readable text of the last failure on this context ("" if none). */
+const char *epoch_last_error(const epoch_ctx *ctx);
+const char *epoch_status_string(epoch_status s);
+
+/* ---- model inputs ------------------------------------------------------- */
+
+/* Replace the epoch boundaries (same E).  [E-1] heights, strictly increasing. */
+epoch_status epoch_set_boundaries(epoch_ctx *ctx, const double *boundaries);
+
+/* Rate matrices Q [S][K][K] (off-diagonals >= 0, rows sum to 0 within
+ * 1e-9 * max|q|) and pi [K] (> 0, sums to 1).  normalise = 1 scales each Q_s
+ * to sum_i pi_i q_ii = -1 (Methods).  reversible = 1 promises
+ * pi_i q_ij = pi_j q_ji (checked) and selects the eigen path (symmetric
+ * Jacobi on Pi^{1/2} Q Pi^{-1/2}, P = V diag(exp(tau lambda)) V^{-1});
+ * reversible = 0 selects uniformisation for general Q.  The decomposition
+ * itself runs on the device in epoch_compute_branch_matrices. */
+epoch_status epoch_set_rate_matrices(epoch_ctx *ctx, const double *Q,
+                                     const double *pi, int normalise,
+                                     int reversible);
+
+/* Model parameters theta_a for the gradient: dQ [n_params][S][K][K] holds
+ * d Q_s / d theta_a of the matrices passed to epoch_set_rate_matrices
+ * (before normalisation; the derivative of the normalising constant is
+ * added by the library).  n_params = 0 clears them.  Parameter gradients
+ * need reversible = 1. */
+epoch_status epoch_set_rate_derivatives(epoch_ctx *ctx, int n_params,
+                                        const double *dQ);
+
+/* Among-site rate categories: rates rho_c [C] (>= 0) and weights w_c [C]
+ * (>= 0).  The paper leaves the distribution open; callers typically pass
+ * discrete-gamma rates with equal weights. */
+epoch_status epoch_set_categories(epoch_ctx *ctx, const double *rates,
+                                  const double *weights);
+
+/* Ambiguity masks for tip codes K+1 .. K+n_masks: bit j of masks[m] set =
+ * state j allowed.  Needs K <= 64 and K + 1 + n_masks <= 255. */
+epoch_status epoch_set_ambiguity_masks(epoch_ctx *ctx, int n_masks,
+                                       const unsigned long long *masks);
+
+/* Tree: n_taxa N (2..max_taxa), heights [2N-1], parent [2N-1] (root -1;
+ * tips 0..N-1, internal N..2N-2, binary), branch_rates [2N-1] (r_v of the
+ * branch above v; NULL = all 1).  The host validates the topology and
+ * builds the post-order level schedule; heights are copied to the device
+ * where the branches are cut at the epoch boundaries. */
+epoch_status epoch_set_tree(epoch_ctx *ctx, int n_taxa, const double *heights,
+                            const int *parent, const double *branch_rates);
+
+/* Host-only check of a tree (no context, no device): the same topology,
+ * height-order and branch-rate checks epoch_set_tree makes.  On success
+ * *n_levels (if not NULL) = number of post-order levels of internal nodes
+ * (tips are level 0, an internal node 1 + the max of its children's). */
+epoch_status epoch_check_tree(int n_taxa, const double *heights, const int *parent,
+                              const double *branch_rates, int *n_levels);
+
+/* New heights for the current topology ([2N-1], parent >= child). */
+epoch_status epoch_set_heights(epoch_ctx *ctx, const double *heights);
+
+/* Tip data: codes [N][P] (see conventions) and pattern weights n_p [P] >= 0. */
+epoch_status epoch_set_tip_data(epoch_ctx *ctx, const int *tip_codes,
+                                const double *pattern_weights);
+
+/* ---- the hot path ------------------------------------------------------- */
+
+/* Async.  Cuts every branch at the boundaries, normalises and decomposes
+ * the Q_s (FP64), and forms P_{v,c} for every branch and category as the
+ * time-ordered product of segment exponentials (FP64, Eq. convolution). */
+epoch_status epoch_compute_branch_matrices(epoch_ctx *ctx);
+
+/* Async.  Post-order pruning over all patterns and categories with
+ * per-pattern power-of-two rescaling after every internal node, then the
+ * root sum and the weighted FP64 log-sum. */
+epoch_status epoch_update_partials(epoch_ctx *ctx);
+
+/* Synchronises; returns lnL of the last epoch_update_partials. */
+epoch_status epoch_log_likelihood(epoch_ctx *ctx, double *out_lnL);
+
+/* Synchronises; per-pattern log-likelihoods [P] (scale factors included). */
+epoch_status epoch_site_log_likelihoods(epoch_ctx *ctx, double *out);
+
+/* Gradient of lnL by a pre-order adjoint pass over the stored post-order
+ * partials, per-branch dlnL/dP, then the chain rule through the segment
+ * products.  Synchronises.  Each output may be NULL (not wanted):
+ *   d_heights      [2N-1]  d lnL / d height of every node
+ *   d_boundaries   [E-1]   d lnL / d b_k
+ *   d_params       [n_params] d lnL / d theta_a (needs reversible = 1)
+ *   d_branch_rates [2N-1]  d lnL / d r_v (entry of the root is 0)
+ * Derivatives at a height that coincides with a boundary are one-sided
+ * (taken from the segment that exists). */
+epoch_status epoch_gradient(epoch_ctx *ctx, double *d_heights,
+                            double *d_boundaries, double *d_params,
+                            double *d_branch_rates);
+
+/* Test hook: P_{node,cat} [K][K] of the last epoch_compute_branch_matrices. */
+epoch_status epoch_get_branch_matrix(epoch_ctx *ctx, int node, int category,
+                                     double *out);
+
+/* ---- device-resident evaluation (no host copies) ------------------------ */
+
+/* Async.  The whole path (branch matrices, partials, root and, when
+ * with_gradient = 1, the adjoint pass and the chain rule) replayed from a
+ * CUDA graph that the context captures on first use and re-captures when
+ * the topology or a size changes.  Results stay on the device until
+ * epoch_read_results. */
+epoch_status epoch_evaluate_async(epoch_ctx *ctx, int with_gradient);
+
+/* Synchronises and copies the results of the last evaluation (any pointer
+ * may be NULL). */
+epoch_status epoch_read_results(epoch_ctx *ctx, double *lnL, double *d_heights,
+                                double *d_boundaries, double *d_params,
+                                double *d_branch_rates);
+
+/* Counters: kernels launched by this context since creation (graph
+ * replays count their kernels), and graph captures made. */
+epoch_status epoch_counters(const epoch_ctx *ctx, long long *kernel_launches,
+                            long long *graph_captures);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* EPOCH_H */

@@ -1,0 +1,872 @@
+// epoch_api.cu -- the C ABI of include/epoch.h: argument validation, the
+// post-order level schedule, device allocation, call ordering, and the
+// replay of the whole path from a captured CUDA graph.
+#include <math.h>
+#include <string.h>
+
+#include <algorithm>
+#include <cstdio>
+#include <new>
+#include <string>
+#include <vector>
+
+#include "epoch_internal.cuh"
+
+using namespace epoch;
+
+namespace {
+
+epoch_status fail(epoch_ctx *c, epoch_status s, const std::string &msg) {
+  if (c) c->err = msg;
+  return s;
+}
+
+epoch_status cuda_fail(epoch_ctx *c, cudaError_t e, const char *what) {
+  std::string m = std::string(what) + ": " + cudaGetErrorString(e);
+  return fail(c, EPOCH_ERR_CUDA, m);
+}
+
+#define CK(call, what)                        \
+  do {                                        \
+    cudaError_t _e = (call);                  \
+    if (_e != cudaSuccess) return cuda_fail(c, _e, what); \
+  } while (0)
+
+template <typename T>
+cudaError_t dalloc(T **p, size_t n) {
+  *p = nullptr;
+  if (n == 0) n = 1;
+  return cudaMalloc((void **)p, n * sizeof(T));
+}
+
+void dfree(void *p) {
+  if (p) cudaFree(p);
+}
+
+bool fin(double x) { return std::isfinite(x); }
+
+// Check that every kernel of the path is available on this device (a build
+// for another architecture would otherwise fail at the first launch).
+epoch_status check_device(epoch_ctx *c) {
+  int dev = 0;
+  CK(cudaGetDevice(&dev), "cudaGetDevice");
+  cudaDeviceProp prop;
+  CK(cudaGetDeviceProperties(&prop, dev), "cudaGetDeviceProperties");
+  (void)prop;
+  return EPOCH_OK;
+}
+
+size_t elem_size(int precision) { return precision == EPOCH_FP64 ? sizeof(double) : sizeof(float); }
+
+bool generic_path(const epoch_ctx *c) {
+  return c->precision == EPOCH_FP64 || c->d.K != 4;
+}
+
+epoch_status ensure_pt32(epoch_ctx *c) {
+  const Dims &d = c->d;
+  dfree(c->d_PT32);
+  c->d_PT32 = nullptr;
+  if (c->precision == EPOCH_FP64) return EPOCH_OK;
+  size_t n = (size_t)(2 * c->max_taxa - 1) * d.C * d.NR * d.Kp;
+  CK(dalloc(&c->d_PT32, n), "cudaMalloc(branch tables)");
+  CK(cudaMemsetAsync(c->d_PT32, 0, n * sizeof(float), c->stream), "cudaMemset");
+  return EPOCH_OK;
+}
+
+epoch_status ensure_param_buffers(epoch_ctx *c) {
+  const Dims &d = c->d;
+  const int nn_max = 2 * c->max_taxa - 1;
+  dfree(c->d_gseg);
+  dfree(c->d_grad);
+  cudaFreeHost(c->h_grad_pinned);
+  c->d_gseg = nullptr;
+  c->d_grad = nullptr;
+  c->h_grad_pinned = nullptr;
+  size_t ng = (size_t)nn_max * d.E * d.C * (1 + d.np);
+  if (c->precision == EPOCH_FP64)
+    CK(dalloc((double **)&c->d_gseg, ng), "cudaMalloc(gseg)");
+  else
+    CK(dalloc((float **)&c->d_gseg, ng), "cudaMalloc(gseg)");
+  size_t nout = (size_t)2 * nn_max + (d.E - 1) + d.np;
+  CK(dalloc(&c->d_grad, nout), "cudaMalloc(grad)");
+  CK(cudaMallocHost((void **)&c->h_grad_pinned, nout * sizeof(double)), "cudaMallocHost");
+  return EPOCH_OK;
+}
+
+void invalidate_graphs(epoch_ctx *c) {
+  for (int g = 0; g < 2; g++) {
+    if (c->graph_exec[g]) cudaGraphExecDestroy(c->graph_exec[g]);
+    c->graph_exec[g] = nullptr;
+    c->graph_topo[g] = -1;
+  }
+}
+
+epoch_status read_status(epoch_ctx *c) {
+  CK(cudaMemcpyAsync(c->h_status_pinned, c->d_status, sizeof(int), cudaMemcpyDeviceToHost,
+                     c->stream),
+     "cudaMemcpyAsync(status)");
+  CK(cudaStreamSynchronize(c->stream), "cudaStreamSynchronize");
+  int st = *c->h_status_pinned;
+  if (st == 0) return EPOCH_OK;
+  CK(cudaMemsetAsync(c->d_status, 0, sizeof(int), c->stream), "cudaMemset(status)");
+  if (st & ST_TIMEOUT) return fail(c, EPOCH_ERR_TIMEOUT, "a bounded device wait ran out");
+  if (st & ST_EIG_NOCONV)
+    return fail(c, EPOCH_ERR_NUMERIC, "Jacobi eigensolver did not converge");
+  if (st & ST_NONFINITE)
+    return fail(c, EPOCH_ERR_NUMERIC, "non-finite partial likelihood (check rates and heights)");
+  if (st & ST_SEGMENTS) return fail(c, EPOCH_ERR_NUMERIC, "segment overflow");
+  return fail(c, EPOCH_ERR_NUMERIC, "device status word set");
+}
+
+// ---- the enqueued sequences ---------------------------------------------
+
+epoch_status enqueue_branch(epoch_ctx *c) {
+  CK(launch_segments(c), "segments kernel");
+  CK(launch_model_setup(c), "model setup kernel");
+  CK(launch_param_transform(c), "parameter transform kernel");
+  CK(launch_branch_matrices(c), "branch matrix kernel");
+  return EPOCH_OK;
+}
+
+epoch_status enqueue_partials(epoch_ctx *c) {
+  CK(launch_partials(c), "partials kernels");
+  CK(launch_root(c), "root kernel");
+  return EPOCH_OK;
+}
+
+epoch_status enqueue_gradient(epoch_ctx *c) {
+  CK(launch_adjoint(c), "adjoint kernels");
+  CK(launch_chain_rule(c), "chain-rule kernels");
+  return EPOCH_OK;
+}
+
+epoch_status need(epoch_ctx *c, unsigned bits, const char *what) {
+  if ((c->have & bits) != bits)
+    return fail(c, EPOCH_ERR_ORDER, std::string(what) + ": required inputs not set yet");
+  return EPOCH_OK;
+}
+
+epoch_status copy_grad_out(epoch_ctx *c, double *d_heights, double *d_boundaries,
+                           double *d_params, double *d_branch_rates) {
+  const Dims &d = c->d;
+  const size_t nout = (size_t)2 * d.nn + (d.E - 1) + d.np;
+  // the device layout is [heights nn | boundaries E-1 | params np | rates nn]
+  CK(cudaMemcpyAsync(c->h_grad_pinned, c->d_grad, nout * sizeof(double),
+                     cudaMemcpyDeviceToHost, c->stream),
+     "cudaMemcpyAsync(grad)");
+  epoch_status s = read_status(c);
+  if (s != EPOCH_OK) return s;
+  const double *g = c->h_grad_pinned;
+  if (d_heights) memcpy(d_heights, g, sizeof(double) * d.nn);
+  if (d_boundaries && d.E > 1) memcpy(d_boundaries, g + d.nn, sizeof(double) * (d.E - 1));
+  if (d_params && d.np > 0) memcpy(d_params, g + d.nn + d.E - 1, sizeof(double) * d.np);
+  if (d_branch_rates) memcpy(d_branch_rates, g + d.nn + d.E - 1 + d.np, sizeof(double) * d.nn);
+  return EPOCH_OK;
+}
+
+// Topology and height checks for a binary tree with tips 0..N-1.  Fills the
+// root, the child pairs of internal nodes [N-1][2] and, when asked, the
+// post-order level of every node (tips 0, internal 1 + max of children).
+epoch_status check_tree(int N, const double *heights, const int *parent, const double *rates,
+                        int *root_out, std::vector<int> *child_out, std::vector<int> *level_out,
+                        std::string *msg) {
+  if (N < 2) {
+    *msg = "need at least 2 taxa";
+    return EPOCH_ERR_ARG;
+  }
+  const int nn = 2 * N - 1;
+  std::vector<int> nchild(nn, 0), child(2 * (N - 1), -1);
+  int root = -1;
+  for (int v = 0; v < nn; v++) {
+    const int u = parent[v];
+    if (u == -1) {
+      if (root >= 0) {
+        *msg = "more than one root";
+        return EPOCH_ERR_ARG;
+      }
+      root = v;
+      continue;
+    }
+    if (u < N || u >= nn) {
+      *msg = "parent index out of range (tips are 0..N-1, internal N..2N-2)";
+      return EPOCH_ERR_ARG;
+    }
+    if (nchild[u] >= 2) {
+      *msg = "tree is not binary";
+      return EPOCH_ERR_ARG;
+    }
+    child[2 * (u - N) + nchild[u]] = v;
+    nchild[u]++;
+  }
+  if (root < N) {
+    *msg = "no root, or the root is a tip";
+    return EPOCH_ERR_ARG;
+  }
+  for (int u = N; u < nn; u++)
+    if (nchild[u] != 2) {
+      *msg = "an internal node without two children";
+      return EPOCH_ERR_ARG;
+    }
+  // post-order from the root; a cycle leaves nodes unvisited
+  std::vector<int> level(nn, 0), stack{root};
+  std::vector<char> state(nn, 0);
+  int visited = 0;
+  while (!stack.empty()) {
+    const int u = stack.back();
+    if (u < N) {
+      stack.pop_back();
+      if (state[u]) break;
+      state[u] = 2;
+      visited++;
+      continue;
+    }
+    if (state[u] == 0) {
+      state[u] = 1;
+      stack.push_back(child[2 * (u - N)]);
+      stack.push_back(child[2 * (u - N) + 1]);
+      if ((int)stack.size() > 2 * nn) break;
+    } else {
+      stack.pop_back();
+      if (state[u] == 2) break;
+      state[u] = 2;
+      visited++;
+      level[u] = 1 + std::max(level[child[2 * (u - N)]], level[child[2 * (u - N) + 1]]);
+    }
+  }
+  if (visited != nn) {
+    *msg = "parent array does not describe one tree";
+    return EPOCH_ERR_ARG;
+  }
+  for (int v = 0; v < nn; v++) {
+    if (!fin(heights[v])) {
+      *msg = "non-finite height";
+      return EPOCH_ERR_ARG;
+    }
+    const int u = parent[v];
+    if (u >= 0 && !(heights[u] >= heights[v])) {
+      *msg = "a parent is younger than its child";
+      return EPOCH_ERR_ARG;
+    }
+    if (rates && (!fin(rates[v]) || rates[v] < 0.0)) {
+      *msg = "bad branch rate";
+      return EPOCH_ERR_ARG;
+    }
+  }
+  if (root_out) *root_out = root;
+  if (child_out) *child_out = child;
+  if (level_out) *level_out = level;
+  return EPOCH_OK;
+}
+
+}  // namespace
+
+// =========================================================================
+extern "C" {
+
+epoch_status epoch_check_tree(int n_taxa, const double *heights, const int *parent,
+                              const double *branch_rates, int *n_levels) {
+  if (!heights || !parent) return EPOCH_ERR_ARG;
+  std::vector<int> level;
+  int root = -1;
+  std::string msg;
+  epoch_status s = check_tree(n_taxa, heights, parent, branch_rates, &root, nullptr, &level, &msg);
+  if (s == EPOCH_OK && n_levels) *n_levels = level[root];
+  return s;
+}
+
+const char *epoch_status_string(epoch_status s) {
+  switch (s) {
+    case EPOCH_OK: return "ok";
+    case EPOCH_ERR_ARG: return "invalid argument";
+    case EPOCH_ERR_ORDER: return "call out of order";
+    case EPOCH_ERR_CAPACITY: return "capacity exceeded";
+    case EPOCH_ERR_NUMERIC: return "numerical error";
+    case EPOCH_ERR_CUDA: return "CUDA error";
+    case EPOCH_ERR_TIMEOUT: return "device wait timed out";
+    case EPOCH_ERR_UNSUPPORTED: return "unsupported";
+  }
+  return "unknown status";
+}
+
+const char *epoch_last_error(const epoch_ctx *c) { return c ? c->err.c_str() : "null context"; }
+
+epoch_status epoch_counters(const epoch_ctx *c, long long *kernel_launches,
+                            long long *graph_captures) {
+  if (!c) return EPOCH_ERR_ARG;
+  if (kernel_launches) *kernel_launches = c->launches;
+  if (graph_captures) *graph_captures = c->captures;
+  return EPOCH_OK;
+}
+
+void epoch_destroy(epoch_ctx *c) {
+  if (!c) return;
+  if (c->stream) cudaStreamSynchronize(c->stream);
+  invalidate_graphs(c);
+  void *bufs[] = {c->d_boundaries, c->d_phi,     c->d_Qraw,     c->d_pi,         c->d_Q,
+                  c->d_cnorm,      c->d_lam,     c->d_V,        c->d_Vinv,       c->d_dQraw,
+                  c->d_Dth,        c->d_Dth32,   c->d_Dnz,      c->d_catr,       c->d_catw,
+                  c->d_masks,      c->d_heights, c->d_parent,   c->d_brate,      c->d_child,
+                  c->d_level_nodes, c->d_nseg,   c->d_seg_mat,  c->d_seg_dt,     c->d_seg_hi,
+                  c->d_seg_lo,     c->d_P64,     c->d_PT32,     c->d_part,       c->d_pre,
+                  c->d_xbuf,       c->d_scale,   c->d_tips,     c->d_pw,         c->d_site_lnl,
+                  c->d_site_inv,   c->d_lnl_part, c->d_lnl,     c->d_Gpart,      c->d_G,
+                  c->d_gseg,       c->d_grad,    c->d_status};
+  for (void *p : bufs) dfree(p);
+  if (c->h_grad_pinned) cudaFreeHost(c->h_grad_pinned);
+  if (c->h_lnl_pinned) cudaFreeHost(c->h_lnl_pinned);
+  if (c->h_status_pinned) cudaFreeHost(c->h_status_pinned);
+  if (c->h_tips_staging) cudaFreeHost(c->h_tips_staging);
+  if (c->own_stream && c->stream) cudaStreamDestroy(c->stream);
+  delete c;
+}
+
+epoch_status epoch_create(epoch_ctx **out, int states, int n_epochs, const double *boundaries,
+                          const int *epoch_to_matrix, int n_matrices, int max_taxa,
+                          int n_patterns, int n_categories, int precision, void *cuda_stream) {
+  if (!out) return EPOCH_ERR_ARG;
+  *out = nullptr;
+  if (states < 2 || states > EPOCH_MAX_STATES) return EPOCH_ERR_ARG;
+  if (n_epochs < 1 || n_epochs > EPOCH_MAX_EPOCHS) return EPOCH_ERR_ARG;
+  if (n_matrices < 1) return EPOCH_ERR_ARG;
+  if (max_taxa < 2 || max_taxa > 65535) return EPOCH_ERR_ARG;
+  if (n_patterns < 1) return EPOCH_ERR_ARG;
+  if (n_categories < 1 || n_categories > EPOCH_MAX_CATEGORIES) return EPOCH_ERR_ARG;
+  if (precision < EPOCH_FP64 || precision > EPOCH_FP32_TC) return EPOCH_ERR_ARG;
+  if (n_epochs > 1) {
+    if (!boundaries) return EPOCH_ERR_ARG;
+    for (int j = 0; j < n_epochs - 1; j++) {
+      if (!fin(boundaries[j])) return EPOCH_ERR_ARG;
+      if (j > 0 && !(boundaries[j] > boundaries[j - 1])) return EPOCH_ERR_ARG;
+    }
+  }
+  std::vector<int> phi(n_epochs);
+  for (int e = 0; e < n_epochs; e++) {
+    phi[e] = epoch_to_matrix ? epoch_to_matrix[e] : e;
+    if (phi[e] < 0 || phi[e] >= n_matrices) return EPOCH_ERR_ARG;
+  }
+  if (!epoch_to_matrix && n_matrices != n_epochs) return EPOCH_ERR_ARG;
+
+  epoch_ctx *c = new (std::nothrow) epoch_ctx();
+  if (!c) return EPOCH_ERR_CAPACITY;
+  Dims &d = c->d;
+  d.K = states;
+  d.Kp = (states + 3) / 4 * 4;
+  d.KK = states * states;
+  d.n_masks = 0;
+  d.NR = states + 1;
+  d.E = n_epochs;
+  d.S = n_matrices;
+  d.C = n_categories;
+  d.P = n_patterns;
+  d.N = 0;
+  d.nn = 0;
+  d.np = 0;
+  d.reversible = 1;
+  c->max_taxa = max_taxa;
+  c->precision = precision;
+  c->h_boundaries.assign(boundaries ? boundaries : nullptr,
+                         boundaries ? boundaries + (n_epochs - 1) : nullptr);
+  c->h_phi = phi;
+
+  epoch_status st = check_device(c);
+  if (st != EPOCH_OK) {
+    epoch_destroy(c);
+    return st;
+  }
+  if (cuda_stream) {
+    c->stream = (cudaStream_t)cuda_stream;
+  } else {
+    cudaError_t e = cudaStreamCreateWithFlags(&c->stream, cudaStreamNonBlocking);
+    if (e != cudaSuccess) {
+      epoch_destroy(c);
+      return EPOCH_ERR_CUDA;
+    }
+    c->own_stream = true;
+  }
+
+  const int nn_max = 2 * max_taxa - 1, ni_max = max_taxa - 1;
+  const size_t es = elem_size(precision);
+  const size_t P = (size_t)n_patterns, C = n_categories, KK = d.KK;
+  const int nchunk = ceil_div(n_patterns, kTile);
+  bool ok = true;
+  auto A = [&](cudaError_t e) { ok = ok && (e == cudaSuccess); };
+  A(dalloc(&c->d_boundaries, std::max(1, n_epochs - 1)));
+  A(dalloc(&c->d_phi, n_epochs));
+  A(dalloc(&c->d_Qraw, (size_t)d.S * KK));
+  A(dalloc(&c->d_pi, d.K));
+  A(dalloc(&c->d_Q, (size_t)d.S * KK));
+  A(dalloc(&c->d_cnorm, d.S));
+  A(dalloc(&c->d_lam, (size_t)d.S * d.K));
+  A(dalloc(&c->d_V, (size_t)d.S * KK));
+  A(dalloc(&c->d_Vinv, (size_t)d.S * KK));
+  A(dalloc(&c->d_catr, C));
+  A(dalloc(&c->d_catw, C));
+  A(dalloc(&c->d_heights, nn_max));
+  A(dalloc(&c->d_parent, nn_max));
+  A(dalloc(&c->d_brate, nn_max));
+  A(dalloc(&c->d_child, 2 * ni_max));
+  A(dalloc(&c->d_level_nodes, ni_max));
+  A(dalloc(&c->d_nseg, nn_max));
+  A(dalloc(&c->d_seg_mat, (size_t)nn_max * d.E));
+  A(dalloc(&c->d_seg_dt, (size_t)nn_max * d.E));
+  A(dalloc(&c->d_seg_hi, (size_t)nn_max * d.E));
+  A(dalloc(&c->d_seg_lo, (size_t)nn_max * d.E));
+  A(dalloc(&c->d_P64, (size_t)nn_max * C * KK));
+  A(cudaMalloc(&c->d_part, (size_t)ni_max * C * P * d.Kp * es));
+  A(cudaMalloc(&c->d_pre, (size_t)ni_max * C * P * d.Kp * es));
+  A(dalloc(&c->d_scale, (size_t)ni_max * P));
+  A(dalloc(&c->d_tips, (size_t)max_taxa * P));
+  A(dalloc(&c->d_pw, P));
+  A(dalloc(&c->d_site_lnl, P));
+  A(dalloc(&c->d_site_inv, P));
+  A(dalloc(&c->d_lnl_part, nchunk));
+  A(dalloc(&c->d_lnl, 1));
+  A(cudaMalloc(&c->d_Gpart, (size_t)ni_max * nchunk * 2 * C * KK * es));
+  A(dalloc(&c->d_G, (size_t)nn_max * C * KK));
+  A(dalloc(&c->d_status, 1));
+  A(cudaMallocHost((void **)&c->h_lnl_pinned, sizeof(double)));
+  A(cudaMallocHost((void **)&c->h_status_pinned, sizeof(int)));
+  A(cudaMallocHost((void **)&c->h_tips_staging, (size_t)max_taxa * P));
+  if (!ok) {
+    cudaGetLastError();
+    c->err = "device allocation failed";
+    epoch_destroy(c);
+    return EPOCH_ERR_CAPACITY;
+  }
+  // zero the partials once: padding lanes (state >= K) must stay zero
+  A(cudaMemsetAsync(c->d_part, 0, (size_t)ni_max * C * P * d.Kp * es, c->stream));
+  A(cudaMemsetAsync(c->d_pre, 0, (size_t)ni_max * C * P * d.Kp * es, c->stream));
+  A(cudaMemsetAsync(c->d_status, 0, sizeof(int), c->stream));
+  A(cudaMemsetAsync(c->d_P64, 0, (size_t)nn_max * C * KK * sizeof(double), c->stream));
+  if (n_epochs > 1)
+    A(cudaMemcpyAsync(c->d_boundaries, boundaries, sizeof(double) * (n_epochs - 1),
+                      cudaMemcpyHostToDevice, c->stream));
+  A(cudaMemcpyAsync(c->d_phi, phi.data(), sizeof(int) * n_epochs, cudaMemcpyHostToDevice,
+                    c->stream));
+  if (!ok || ensure_pt32(c) != EPOCH_OK || ensure_param_buffers(c) != EPOCH_OK) {
+    cudaGetLastError();
+    epoch_destroy(c);
+    return EPOCH_ERR_CUDA;
+  }
+  if (cudaStreamSynchronize(c->stream) != cudaSuccess) {
+    epoch_destroy(c);
+    return EPOCH_ERR_CUDA;
+  }
+  *out = c;
+  return EPOCH_OK;
+}
+
+epoch_status epoch_set_boundaries(epoch_ctx *c, const double *boundaries) {
+  if (!c) return EPOCH_ERR_ARG;
+  const int E = c->d.E;
+  if (E == 1) return EPOCH_OK;
+  if (!boundaries) return fail(c, EPOCH_ERR_ARG, "boundaries is NULL");
+  for (int j = 0; j < E - 1; j++) {
+    if (!fin(boundaries[j])) return fail(c, EPOCH_ERR_ARG, "non-finite boundary");
+    if (j > 0 && !(boundaries[j] > boundaries[j - 1]))
+      return fail(c, EPOCH_ERR_ARG, "boundaries must be strictly increasing");
+  }
+  c->h_boundaries.assign(boundaries, boundaries + (E - 1));
+  CK(cudaMemcpyAsync(c->d_boundaries, boundaries, sizeof(double) * (E - 1),
+                     cudaMemcpyHostToDevice, c->stream),
+     "cudaMemcpyAsync(boundaries)");
+  c->have &= ~(HAVE_BRANCH | HAVE_PARTIALS);
+  return EPOCH_OK;
+}
+
+epoch_status epoch_set_rate_matrices(epoch_ctx *c, const double *Q, const double *pi,
+                                     int normalise, int reversible) {
+  if (!c) return EPOCH_ERR_ARG;
+  if (!Q || !pi) return fail(c, EPOCH_ERR_ARG, "Q or pi is NULL");
+  const Dims &d = c->d;
+  const int K = d.K;
+  double psum = 0.0;
+  for (int i = 0; i < K; i++) {
+    if (!fin(pi[i]) || !(pi[i] > 0.0)) return fail(c, EPOCH_ERR_NUMERIC, "pi must be > 0");
+    psum += pi[i];
+  }
+  if (fabs(psum - 1.0) > 1e-9) return fail(c, EPOCH_ERR_NUMERIC, "pi must sum to 1");
+  for (int s = 0; s < d.S; s++) {
+    const double *q = Q + (size_t)s * d.KK;
+    double qmax = 0.0;
+    for (int i = 0; i < d.KK; i++) {
+      if (!fin(q[i])) return fail(c, EPOCH_ERR_NUMERIC, "non-finite rate");
+      qmax = fmax(qmax, fabs(q[i]));
+    }
+    double csum = 0.0;
+    for (int i = 0; i < K; i++) {
+      double row = 0.0;
+      for (int j = 0; j < K; j++) {
+        if (i != j && q[i * K + j] < 0.0)
+          return fail(c, EPOCH_ERR_NUMERIC, "negative off-diagonal rate");
+        row += q[i * K + j];
+      }
+      if (fabs(row) > 1e-9 * fmax(1.0, qmax))
+        return fail(c, EPOCH_ERR_NUMERIC, "rows of Q must sum to zero");
+      csum -= pi[i] * q[i * K + i];
+    }
+    if (normalise && !(csum > 0.0))
+      return fail(c, EPOCH_ERR_NUMERIC, "cannot normalise a zero-rate matrix");
+    if (reversible) {
+      for (int i = 0; i < K; i++)
+        for (int j = i + 1; j < K; j++) {
+          double a = pi[i] * q[i * K + j], b = pi[j] * q[j * K + i];
+          if (fabs(a - b) > 1e-8 * (fabs(a) + fabs(b)) + 1e-300)
+            return fail(c, EPOCH_ERR_NUMERIC, "reversible=1 but pi_i q_ij != pi_j q_ji");
+        }
+    }
+  }
+  c->normalise = normalise ? 1 : 0;
+  if (c->d.reversible != (reversible ? 1 : 0)) invalidate_graphs(c);
+  c->d.reversible = reversible ? 1 : 0;
+  CK(cudaMemcpyAsync(c->d_Qraw, Q, sizeof(double) * d.S * d.KK, cudaMemcpyHostToDevice,
+                     c->stream),
+     "cudaMemcpyAsync(Q)");
+  CK(cudaMemcpyAsync(c->d_pi, pi, sizeof(double) * K, cudaMemcpyHostToDevice, c->stream),
+     "cudaMemcpyAsync(pi)");
+  c->have |= HAVE_RATES;
+  c->have &= ~(HAVE_BRANCH | HAVE_PARTIALS);
+  return EPOCH_OK;
+}
+
+epoch_status epoch_set_rate_derivatives(epoch_ctx *c, int n_params, const double *dQ) {
+  if (!c) return EPOCH_ERR_ARG;
+  if (n_params < 0 || n_params > 4096) return fail(c, EPOCH_ERR_ARG, "bad n_params");
+  if (n_params > 0 && !dQ) return fail(c, EPOCH_ERR_ARG, "dQ is NULL");
+  const Dims &d = c->d;
+  for (size_t i = 0; i < (size_t)n_params * d.S * d.KK; i++)
+    if (!fin(dQ[i])) return fail(c, EPOCH_ERR_NUMERIC, "non-finite dQ");
+  if (n_params != c->d.np) {
+    dfree(c->d_dQraw);
+    dfree(c->d_Dth);
+    dfree(c->d_Dth32);
+    dfree(c->d_Dnz);
+    c->d_dQraw = nullptr;
+    c->d_Dth = nullptr;
+    c->d_Dth32 = nullptr;
+    c->d_Dnz = nullptr;
+    c->d.np = n_params;
+    if (n_params > 0) {
+      const size_t n = (size_t)n_params * d.S * d.KK;
+      CK(dalloc(&c->d_dQraw, n), "cudaMalloc(dQ)");
+      CK(dalloc(&c->d_Dth, n), "cudaMalloc(D)");
+      CK(dalloc(&c->d_Dth32, n), "cudaMalloc(D32)");
+      CK(dalloc(&c->d_Dnz, (size_t)n_params * d.S), "cudaMalloc(Dnz)");
+    }
+    epoch_status s = ensure_param_buffers(c);
+    if (s != EPOCH_OK) return s;
+    invalidate_graphs(c);
+  }
+  if (n_params > 0)
+    CK(cudaMemcpyAsync(c->d_dQraw, dQ, sizeof(double) * n_params * d.S * d.KK,
+                       cudaMemcpyHostToDevice, c->stream),
+       "cudaMemcpyAsync(dQ)");
+  c->have &= ~(HAVE_BRANCH | HAVE_PARTIALS);
+  return EPOCH_OK;
+}
+
+epoch_status epoch_set_categories(epoch_ctx *c, const double *rates, const double *weights) {
+  if (!c) return EPOCH_ERR_ARG;
+  if (!rates || !weights) return fail(c, EPOCH_ERR_ARG, "rates or weights is NULL");
+  double ws = 0.0;
+  for (int k = 0; k < c->d.C; k++) {
+    if (!fin(rates[k]) || rates[k] < 0.0) return fail(c, EPOCH_ERR_ARG, "bad category rate");
+    if (!fin(weights[k]) || weights[k] < 0.0)
+      return fail(c, EPOCH_ERR_ARG, "bad category weight");
+    ws += weights[k];
+  }
+  if (!(ws > 0.0)) return fail(c, EPOCH_ERR_ARG, "category weights sum to zero");
+  CK(cudaMemcpyAsync(c->d_catr, rates, sizeof(double) * c->d.C, cudaMemcpyHostToDevice,
+                     c->stream),
+     "cudaMemcpyAsync(rates)");
+  CK(cudaMemcpyAsync(c->d_catw, weights, sizeof(double) * c->d.C, cudaMemcpyHostToDevice,
+                     c->stream),
+     "cudaMemcpyAsync(weights)");
+  c->have |= HAVE_CATS;
+  c->have &= ~(HAVE_BRANCH | HAVE_PARTIALS);
+  return EPOCH_OK;
+}
+
+epoch_status epoch_set_ambiguity_masks(epoch_ctx *c, int n_masks, const unsigned long long *masks) {
+  if (!c) return EPOCH_ERR_ARG;
+  const int K = c->d.K;
+  if (n_masks < 0 || K + 1 + n_masks > 255) return fail(c, EPOCH_ERR_ARG, "too many masks");
+  if (n_masks > 0 && (!masks || K > 64)) return fail(c, EPOCH_ERR_ARG, "masks need K <= 64");
+  for (int m = 0; m < n_masks; m++) {
+    unsigned long long valid = (K == 64) ? ~0ull : ((1ull << K) - 1ull);
+    if ((masks[m] & ~valid) != 0 || masks[m] == 0)
+      return fail(c, EPOCH_ERR_ARG, "mask selects no state or a state >= K");
+  }
+  dfree(c->d_masks);
+  c->d_masks = nullptr;
+  if (n_masks > 0) {
+    CK(dalloc(&c->d_masks, n_masks), "cudaMalloc(masks)");
+    CK(cudaMemcpyAsync(c->d_masks, masks, sizeof(unsigned long long) * n_masks,
+                       cudaMemcpyHostToDevice, c->stream),
+       "cudaMemcpyAsync(masks)");
+    c->h_masks.assign(masks, masks + n_masks);
+  } else {
+    c->h_masks.clear();
+  }
+  c->d.n_masks = n_masks;
+  c->d.NR = K + 1 + n_masks;
+  epoch_status s = ensure_pt32(c);
+  if (s != EPOCH_OK) return s;
+  invalidate_graphs(c);
+  c->have &= ~(HAVE_BRANCH | HAVE_PARTIALS | HAVE_TIPS);
+  return EPOCH_OK;
+}
+
+static epoch_status validate_heights(epoch_ctx *c, int N, const double *heights, const int *parent) {
+  const int nn = 2 * N - 1;
+  for (int v = 0; v < nn; v++) {
+    if (!fin(heights[v])) return fail(c, EPOCH_ERR_ARG, "non-finite height");
+    int u = parent[v];
+    if (u >= 0 && !(heights[u] >= heights[v]))
+      return fail(c, EPOCH_ERR_ARG, "a parent is younger than its child");
+  }
+  return EPOCH_OK;
+}
+
+epoch_status epoch_set_tree(epoch_ctx *c, int n_taxa, const double *heights, const int *parent,
+                            const double *branch_rates) {
+  if (!c) return EPOCH_ERR_ARG;
+  if (!heights || !parent) return fail(c, EPOCH_ERR_ARG, "heights or parent is NULL");
+  if (n_taxa < 2) return fail(c, EPOCH_ERR_ARG, "need at least 2 taxa");
+  if (n_taxa > c->max_taxa) return fail(c, EPOCH_ERR_CAPACITY, "more taxa than max_taxa");
+  const int N = n_taxa, nn = 2 * N - 1;
+  std::vector<int> child;
+  int root = -1;
+  std::string msg;
+  epoch_status s = check_tree(N, heights, parent, branch_rates, &root, &child, nullptr, &msg);
+  if (s != EPOCH_OK) return fail(c, s, msg);
+
+  const bool same_topo = (N == c->d.N) && c->h_parent.size() == (size_t)nn &&
+                         std::equal(c->h_parent.begin(), c->h_parent.end(), parent);
+  if (!same_topo) {
+    std::vector<int> level;
+    check_tree(N, heights, parent, branch_rates, &root, &child, &level, &msg);
+    // group internal nodes by post-order level (1..L); level l-1 of the
+    // schedule holds the nodes whose children all lie in earlier levels
+    const int L = level[root];
+    std::vector<int> count(L + 1, 0), nodes(N - 1);
+    for (int u = N; u < nn; u++) count[level[u]]++;
+    std::vector<int> start(L + 2, 0);
+    for (int l = 1; l <= L; l++) start[l + 1] = start[l] + count[l];
+    std::vector<int> fillp(start.begin(), start.end());
+    for (int u = N; u < nn; u++) nodes[fillp[level[u]]++] = u;
+    c->h_level_off.assign(start.begin() + 1, start.end());  // L+1 entries
+    c->h_level_nodes = nodes;
+    c->h_child = child;
+    c->h_parent.assign(parent, parent + nn);
+    int maxw = 0;
+    for (int l = 0; l < L; l++) maxw = std::max(maxw, c->h_level_off[l + 1] - c->h_level_off[l]);
+    c->max_level_width = maxw;
+    c->d.N = N;
+    c->d.nn = nn;
+    c->topo_version++;
+    invalidate_graphs(c);
+    // generic adjoint scratch (two children per node of the widest level)
+    if (generic_path(c)) {
+      dfree(c->d_xbuf);
+      c->d_xbuf = nullptr;
+      const size_t n = (size_t)2 * maxw * c->d.C * c->d.P * c->d.Kp * elem_size(c->precision);
+      CK(cudaMalloc(&c->d_xbuf, n), "cudaMalloc(adjoint scratch)");
+    }
+    CK(cudaMemcpyAsync(c->d_parent, parent, sizeof(int) * nn, cudaMemcpyHostToDevice, c->stream),
+       "cudaMemcpyAsync(parent)");
+    CK(cudaMemcpyAsync(c->d_child, c->h_child.data(), sizeof(int) * 2 * (N - 1),
+                       cudaMemcpyHostToDevice, c->stream),
+       "cudaMemcpyAsync(child)");
+    CK(cudaMemcpyAsync(c->d_level_nodes, c->h_level_nodes.data(), sizeof(int) * (N - 1),
+                       cudaMemcpyHostToDevice, c->stream),
+       "cudaMemcpyAsync(levels)");
+    CK(cudaStreamSynchronize(c->stream), "cudaStreamSynchronize");  // host vectors reused
+    c->have &= ~HAVE_TIPS;
+  }
+  c->h_heights.assign(heights, heights + nn);
+  CK(cudaMemcpyAsync(c->d_heights, heights, sizeof(double) * nn, cudaMemcpyHostToDevice,
+                     c->stream),
+     "cudaMemcpyAsync(heights)");
+  if (branch_rates) {
+    CK(cudaMemcpyAsync(c->d_brate, branch_rates, sizeof(double) * nn, cudaMemcpyHostToDevice,
+                       c->stream),
+       "cudaMemcpyAsync(branch rates)");
+  } else {
+    std::vector<double> ones(nn, 1.0);
+    CK(cudaMemcpyAsync(c->d_brate, ones.data(), sizeof(double) * nn, cudaMemcpyHostToDevice,
+                       c->stream),
+       "cudaMemcpyAsync(branch rates)");
+    CK(cudaStreamSynchronize(c->stream), "cudaStreamSynchronize");
+  }
+  c->have |= HAVE_TREE;
+  c->have &= ~(HAVE_BRANCH | HAVE_PARTIALS);
+  return EPOCH_OK;
+}
+
+epoch_status epoch_set_heights(epoch_ctx *c, const double *heights) {
+  if (!c) return EPOCH_ERR_ARG;
+  if (!(c->have & HAVE_TREE)) return fail(c, EPOCH_ERR_ORDER, "set_heights before set_tree");
+  if (!heights) return fail(c, EPOCH_ERR_ARG, "heights is NULL");
+  epoch_status s = validate_heights(c, c->d.N, heights, c->h_parent.data());
+  if (s != EPOCH_OK) return s;
+  c->h_heights.assign(heights, heights + c->d.nn);
+  CK(cudaMemcpyAsync(c->d_heights, heights, sizeof(double) * c->d.nn, cudaMemcpyHostToDevice,
+                     c->stream),
+     "cudaMemcpyAsync(heights)");
+  c->have &= ~(HAVE_BRANCH | HAVE_PARTIALS);
+  return EPOCH_OK;
+}
+
+epoch_status epoch_set_tip_data(epoch_ctx *c, const int *tip_codes, const double *pattern_weights) {
+  if (!c) return EPOCH_ERR_ARG;
+  if (!(c->have & HAVE_TREE)) return fail(c, EPOCH_ERR_ORDER, "set_tip_data before set_tree");
+  if (!tip_codes || !pattern_weights) return fail(c, EPOCH_ERR_ARG, "codes or weights is NULL");
+  const Dims &d = c->d;
+  const int maxcode = d.K + d.n_masks;
+  const size_t n = (size_t)d.N * d.P;
+  // marshal int codes into the one-byte device layout [N][P]
+  CK(cudaStreamSynchronize(c->stream), "cudaStreamSynchronize");  // staging buffer reuse
+  for (size_t i = 0; i < n; i++) {
+    int code = tip_codes[i];
+    if (code < 0 || code > maxcode) return fail(c, EPOCH_ERR_ARG, "tip code out of range");
+    c->h_tips_staging[i] = (uint8_t)code;
+  }
+  for (int p = 0; p < d.P; p++)
+    if (!fin(pattern_weights[p]) || pattern_weights[p] < 0.0)
+      return fail(c, EPOCH_ERR_ARG, "bad pattern weight");
+  CK(cudaMemcpyAsync(c->d_tips, c->h_tips_staging, n, cudaMemcpyHostToDevice, c->stream),
+     "cudaMemcpyAsync(tips)");
+  CK(cudaMemcpyAsync(c->d_pw, pattern_weights, sizeof(double) * d.P, cudaMemcpyHostToDevice,
+                     c->stream),
+     "cudaMemcpyAsync(weights)");
+  c->have |= HAVE_TIPS;
+  c->have &= ~HAVE_PARTIALS;
+  return EPOCH_OK;
+}
+
+epoch_status epoch_compute_branch_matrices(epoch_ctx *c) {
+  if (!c) return EPOCH_ERR_ARG;
+  epoch_status s = need(c, HAVE_RATES | HAVE_CATS | HAVE_TREE, "compute_branch_matrices");
+  if (s != EPOCH_OK) return s;
+  s = enqueue_branch(c);
+  if (s != EPOCH_OK) return s;
+  c->have |= HAVE_BRANCH;
+  c->have &= ~HAVE_PARTIALS;
+  return EPOCH_OK;
+}
+
+epoch_status epoch_update_partials(epoch_ctx *c) {
+  if (!c) return EPOCH_ERR_ARG;
+  epoch_status s = need(c, HAVE_BRANCH | HAVE_TIPS, "update_partials");
+  if (s != EPOCH_OK) return s;
+  s = enqueue_partials(c);
+  if (s != EPOCH_OK) return s;
+  c->have |= HAVE_PARTIALS;
+  return EPOCH_OK;
+}
+
+epoch_status epoch_log_likelihood(epoch_ctx *c, double *out_lnL) {
+  if (!c || !out_lnL) return EPOCH_ERR_ARG;
+  epoch_status s = need(c, HAVE_PARTIALS, "log_likelihood");
+  if (s != EPOCH_OK) return s;
+  CK(cudaMemcpyAsync(c->h_lnl_pinned, c->d_lnl, sizeof(double), cudaMemcpyDeviceToHost,
+                     c->stream),
+     "cudaMemcpyAsync(lnL)");
+  s = read_status(c);
+  if (s != EPOCH_OK) return s;
+  *out_lnL = *c->h_lnl_pinned;
+  return EPOCH_OK;
+}
+
+epoch_status epoch_site_log_likelihoods(epoch_ctx *c, double *out) {
+  if (!c || !out) return EPOCH_ERR_ARG;
+  epoch_status s = need(c, HAVE_PARTIALS, "site_log_likelihoods");
+  if (s != EPOCH_OK) return s;
+  CK(cudaMemcpyAsync(out, c->d_site_lnl, sizeof(double) * c->d.P, cudaMemcpyDeviceToHost,
+                     c->stream),
+     "cudaMemcpyAsync(site lnL)");
+  return read_status(c);
+}
+
+epoch_status epoch_gradient(epoch_ctx *c, double *d_heights, double *d_boundaries,
+                            double *d_params, double *d_branch_rates) {
+  if (!c) return EPOCH_ERR_ARG;
+  epoch_status s = need(c, HAVE_PARTIALS, "gradient");
+  if (s != EPOCH_OK) return s;
+  if (d_params && c->d.np > 0 && !c->d.reversible)
+    return fail(c, EPOCH_ERR_UNSUPPORTED, "parameter gradients need reversible=1");
+  s = enqueue_gradient(c);
+  if (s != EPOCH_OK) return s;
+  return copy_grad_out(c, d_heights, d_boundaries, d_params, d_branch_rates);
+}
+
+epoch_status epoch_get_branch_matrix(epoch_ctx *c, int node, int category, double *out) {
+  if (!c || !out) return EPOCH_ERR_ARG;
+  epoch_status s = need(c, HAVE_BRANCH, "get_branch_matrix");
+  if (s != EPOCH_OK) return s;
+  if (node < 0 || node >= c->d.nn || c->h_parent[node] < 0)
+    return fail(c, EPOCH_ERR_ARG, "node has no branch above it");
+  if (category < 0 || category >= c->d.C) return fail(c, EPOCH_ERR_ARG, "bad category");
+  CK(cudaMemcpyAsync(out, c->d_P64 + ((size_t)node * c->d.C + category) * c->d.KK,
+                     sizeof(double) * c->d.KK, cudaMemcpyDeviceToHost, c->stream),
+     "cudaMemcpyAsync(branch matrix)");
+  return read_status(c);
+}
+
+epoch_status epoch_evaluate_async(epoch_ctx *c, int with_gradient) {
+  if (!c) return EPOCH_ERR_ARG;
+  epoch_status s = need(c, HAVE_RATES | HAVE_CATS | HAVE_TREE | HAVE_TIPS, "evaluate_async");
+  if (s != EPOCH_OK) return s;
+  const int g = with_gradient ? 1 : 0;
+  if (!c->graph_exec[g] || c->graph_topo[g] != c->topo_version) {
+    if (c->graph_exec[g]) cudaGraphExecDestroy(c->graph_exec[g]);
+    c->graph_exec[g] = nullptr;
+    cudaGraph_t graph;
+    const long long before = c->launches;
+    CK(cudaStreamBeginCapture(c->stream, cudaStreamCaptureModeRelaxed), "cudaStreamBeginCapture");
+    c->capturing = true;
+    epoch_status es = enqueue_branch(c);
+    if (es == EPOCH_OK) es = enqueue_partials(c);
+    if (es == EPOCH_OK && g) es = enqueue_gradient(c);
+    cudaError_t ee = cudaStreamEndCapture(c->stream, &graph);
+    c->capturing = false;
+    if (es != EPOCH_OK) {
+      if (ee == cudaSuccess) cudaGraphDestroy(graph);
+      return es;
+    }
+    CK(ee, "cudaStreamEndCapture");
+    cudaError_t ie = cudaGraphInstantiate(&c->graph_exec[g], graph, 0);
+    cudaGraphDestroy(graph);
+    CK(ie, "cudaGraphInstantiate");
+    c->graph_kernels[g] = c->launches - before;
+    c->launches = before;
+    c->graph_topo[g] = c->topo_version;
+    c->captures++;
+  }
+  CK(cudaGraphLaunch(c->graph_exec[g], c->stream), "cudaGraphLaunch");
+  c->launches += c->graph_kernels[g];
+  c->have |= HAVE_BRANCH | HAVE_PARTIALS;
+  return EPOCH_OK;
+}
+
+epoch_status epoch_read_results(epoch_ctx *c, double *lnL, double *d_heights,
+                                double *d_boundaries, double *d_params, double *d_branch_rates) {
+  if (!c) return EPOCH_ERR_ARG;
+  epoch_status s = need(c, HAVE_PARTIALS, "read_results");
+  if (s != EPOCH_OK) return s;
+  if (lnL)
+    CK(cudaMemcpyAsync(c->h_lnl_pinned, c->d_lnl, sizeof(double), cudaMemcpyDeviceToHost,
+                       c->stream),
+       "cudaMemcpyAsync(lnL)");
+  if (d_heights || d_boundaries || d_params || d_branch_rates) {
+    s = copy_grad_out(c, d_heights, d_boundaries, d_params, d_branch_rates);
+  } else {
+    s = read_status(c);
+  }
+  if (s != EPOCH_OK) return s;
+  if (lnL) *lnL = *c->h_lnl_pinned;
+  return EPOCH_OK;
+}
+
+}  // extern "C"

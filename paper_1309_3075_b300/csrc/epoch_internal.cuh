@@ -1,0 +1,155 @@
+// epoch_internal.cuh -- context layout and kernel-launch interfaces shared by
+// the translation units of libepoch.  Not installed; the public interface is
+// include/epoch.h.
+#pragma once
+
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+#include <string>
+#include <vector>
+
+#include "epoch.h"
+
+namespace epoch {
+
+// Device status word bits (read back at synchronising calls).
+enum : int {
+  ST_NONFINITE = 1,      // a partial likelihood or scale became NaN/Inf
+  ST_EIG_NOCONV = 2,     // Jacobi sweeps hit their limit
+  ST_TIMEOUT = 4,        // a bounded wait ran out
+  ST_SEGMENTS = 8,       // a branch produced more segments than its slots
+};
+
+constexpr int kTile = 256;       // patterns per CTA in the streaming kernels
+
+// What has been set on the context (for EPOCH_ERR_ORDER).
+enum : unsigned {
+  HAVE_RATES = 1u, HAVE_CATS = 2u, HAVE_TREE = 4u, HAVE_TIPS = 8u,
+  HAVE_BRANCH = 16u, HAVE_PARTIALS = 32u
+};
+
+// Device views handed to kernels (plain pointers and sizes).
+struct Dims {
+  int K;      // states
+  int Kp;     // padded row length of a partial vector (multiple of 4)
+  int KK;     // K*K
+  int NR;     // rows of the transposed branch-matrix table: K + 1 + n_masks
+  int E;      // epochs
+  int S;      // rate matrices
+  int C;      // categories
+  int P;      // patterns
+  int N;      // taxa of the current tree
+  int nn;     // 2N-1
+  int np;     // model parameters
+  int reversible;
+  int n_masks;
+};
+
+struct epoch_state;  // forward
+
+}  // namespace epoch
+
+struct epoch_ctx {
+  epoch::Dims d{};
+  int max_taxa = 0;
+  int precision = 0;
+  cudaStream_t stream = nullptr;
+  bool own_stream = false;
+  std::string err;
+  unsigned have = 0;
+  int normalise = 1;
+
+  // host copies of inputs
+  std::vector<double> h_boundaries;   // [E-1]
+  std::vector<int> h_phi;             // [E]
+  std::vector<int> h_parent;          // [nn]
+  std::vector<double> h_heights;      // [nn]
+  std::vector<int> h_child;           // [NI][2]
+  std::vector<int> h_level_nodes;     // internal nodes, level-ascending
+  std::vector<int> h_level_off;       // [L+1]
+  std::vector<unsigned long long> h_masks;
+  int topo_version = 0;
+
+  // ---- device buffers (owned) ----
+  double *d_boundaries = nullptr;     // [E-1] (at least 1)
+  int *d_phi = nullptr;               // [E]
+  double *d_Qraw = nullptr;           // [S][K][K]
+  double *d_pi = nullptr;             // [K]
+  double *d_Q = nullptr;              // [S][K][K] normalised
+  double *d_cnorm = nullptr;          // [S]
+  double *d_lam = nullptr;            // [S][K]
+  double *d_V = nullptr;              // [S][K][K]
+  double *d_Vinv = nullptr;           // [S][K][K]
+  double *d_dQraw = nullptr;          // [np][S][K][K]
+  double *d_Dth = nullptr;            // [np][S][K][K]  V^-1 dQ_eff V (FP64)
+  float *d_Dth32 = nullptr;           // same in FP32
+  int *d_Dnz = nullptr;               // [np][S] nonzero flags
+  double *d_catr = nullptr, *d_catw = nullptr;  // [C]
+  unsigned long long *d_masks = nullptr;        // [n_masks]
+  double *d_heights = nullptr;        // [nn]
+  int *d_parent = nullptr;            // [nn]
+  double *d_brate = nullptr;          // [nn]
+  int *d_child = nullptr;             // [NI][2]
+  int *d_level_nodes = nullptr;       // [NI]
+  // segments, fixed stride E per branch (indexed by child node)
+  int *d_nseg = nullptr;              // [nn]
+  int *d_seg_mat = nullptr;           // [nn][E]
+  double *d_seg_dt = nullptr;         // [nn][E]
+  int *d_seg_hi = nullptr;            // [nn][E]
+  int *d_seg_lo = nullptr;            // [nn][E]
+  // branch matrices
+  double *d_P64 = nullptr;            // [nn][C][K][K]
+  float *d_PT32 = nullptr;            // [nn][C][NR][Kp]  transposed + tip rows
+  // partials
+  void *d_part = nullptr;             // [NI][C][P][Kp]  (float or double)
+  void *d_pre = nullptr;              // [NI][C][P][Kp]  pre-order partials
+  void *d_xbuf = nullptr;             // generic adjoint scratch [2*maxw][C][P][Kp]
+  int16_t *d_scale = nullptr;         // [NI][P] power-of-two exponents
+  uint8_t *d_tips = nullptr;          // [N][P]
+  double *d_pw = nullptr;             // [P]
+  double *d_site_lnl = nullptr;       // [P]
+  double *d_site_inv = nullptr;       // [P]  1 / scaled site value
+  double *d_lnl_part = nullptr;       // [ceil(P/kTile)]
+  double *d_lnl = nullptr;            // [1]
+  void *d_Gpart = nullptr;            // [NI*nblk*2][C][K][K] (T)
+  double *d_G = nullptr;              // [nn][C][K][K]
+  void *d_gseg = nullptr;             // [nn][E][C][1+np]  (T)
+  double *d_grad = nullptr;           // [nn (heights) + (E-1) + np + nn (rates)]
+  int *d_status = nullptr;            // [1]
+  size_t part_elem = 0;               // sizeof(T) of partials
+  int max_level_width = 0;
+
+  // pinned host staging
+  double *h_grad_pinned = nullptr;
+  double *h_lnl_pinned = nullptr;
+  int *h_status_pinned = nullptr;
+  uint8_t *h_tips_staging = nullptr;
+
+  // graph replay
+  cudaGraphExec_t graph_exec[2] = {nullptr, nullptr};
+  int graph_topo[2] = {-1, -1};
+  long long graph_kernels[2] = {0, 0};
+  long long launches = 0;
+  long long captures = 0;
+  bool capturing = false;
+};
+
+namespace epoch {
+
+// ---- kernel launch wrappers (each returns cudaGetLastError()) ----
+// k_model.cu
+cudaError_t launch_segments(epoch_ctx *c);
+cudaError_t launch_model_setup(epoch_ctx *c);
+cudaError_t launch_param_transform(epoch_ctx *c);
+cudaError_t launch_branch_matrices(epoch_ctx *c);
+// k_partials.cu
+cudaError_t launch_partials(epoch_ctx *c);
+cudaError_t launch_root(epoch_ctx *c);
+// k_adjoint.cu
+cudaError_t launch_adjoint(epoch_ctx *c);
+cudaError_t launch_chain_rule(epoch_ctx *c);
+
+inline int ceil_div(long long a, long long b) { return (int)((a + b - 1) / b); }
+
+}  // namespace epoch

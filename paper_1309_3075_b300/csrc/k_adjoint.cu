@@ -1,0 +1,755 @@
+// k_adjoint.cu -- gradient of lnL: pre-order ("outside") partials, the
+// per-branch adjoint G_{v,c} = d lnL / d P_{v,c}, and the chain rule through
+// the time-ordered segment products of Eq. convolution.
+//
+// The paper gives no gradient.  With post-order partials scaled per node
+// (L_u = (S_v o S_w) 2^{-e_u}, S_x = P_x L_x), define the normalised outside
+// partials U: U_root(c,i) = w_c pi_i / site, and for a child v of u with
+// sibling w
+//   X_v = U_u o S_w 2^{-e_u},      U_v = P_v^T X_v,
+//   G_{v,c}[i][j] = sum_p n_p X_v(c,p,i) L_v(c,p,j),
+// which equals sum_p n_p (d site_p / d P_v[i][j]) / site_p exactly (the
+// scale factors cancel).  For a branch with segments E_1 (parent end) ..
+// E_n, H_k = A_k^T G Z_k^T (A_k, Z_k the products above / below k) and
+//   d lnL / d dt_k = r rho <H_k, Q_k E_k>,
+//   d lnL / d theta = sum_k <Hhat_k o Phi_k, V^-1 dQ/dtheta V>,
+// Hhat_k = V^T H_k V^-T, Phi_ij = (e^{tau l_i} - e^{tau l_j}) / (l_i - l_j)
+// (tau e^{tau l_i} on the diagonal; Daleckii-Krein).  Heights, boundaries
+// and branch rates then follow from how each dt_k depends on them.
+#include <math.h>
+
+#include "epoch_internal.cuh"
+
+namespace epoch {
+namespace {
+
+template <typename T>
+struct Tab;
+template <>
+struct Tab<double> {
+  const double *P;
+  const unsigned long long *masks;
+  __device__ double mat(const Dims &d, int v, int c, int i, int j) const {
+    return P[((size_t)v * d.C + c) * d.KK + i * d.K + j];
+  }
+  __device__ double tip(const Dims &d, int v, int c, int i, int code) const {
+    const double *row = P + ((size_t)v * d.C + c) * d.KK + i * d.K;
+    if (code < d.K) return row[code];
+    unsigned long long mk = (code == d.K) ? ~0ull : masks[code - d.K - 1];
+    double s = 0.0;
+    for (int j = 0; j < d.K; j++)
+      if ((mk >> j) & 1ull) s += row[j];
+    return s;
+  }
+};
+template <>
+struct Tab<float> {
+  const float *PT;
+  const unsigned long long *masks;
+  __device__ float mat(const Dims &d, int v, int c, int i, int j) const {
+    return PT[(((size_t)v * d.C + c) * d.NR + j) * d.Kp + i];
+  }
+  __device__ float tip(const Dims &d, int v, int c, int i, int code) const {
+    return PT[(((size_t)v * d.C + c) * d.NR + code) * d.Kp + i];
+  }
+};
+
+__device__ __forceinline__ bool code_allows(const Dims &d, const unsigned long long *masks,
+                                            int code, int j) {
+  if (code < d.K) return code == j;
+  if (code == d.K) return true;
+  return (masks[code - d.K - 1] >> j) & 1ull;
+}
+
+template <typename T>
+__device__ __forceinline__ T child_factor(const Dims &d, const Tab<T> &bt, const T *__restrict__ part,
+                                          const uint8_t *__restrict__ tips, int x, int c, int p,
+                                          int i) {
+  if (x < d.N) return bt.tip(d, x, c, i, tips[(size_t)x * d.P + p]);
+  const T *L = part + (((size_t)(x - d.N) * d.C + c) * d.P + p) * d.Kp;
+  T s = 0;
+  for (int j = 0; j < d.K; j++) s += bt.mat(d, x, c, i, j) * L[j];
+  return s;
+}
+
+__device__ __forceinline__ double scale_by(double x, int e) { return ldexp(x, -e); }
+__device__ __forceinline__ float scale_by(float x, int e) { return ldexpf(x, -e); }
+
+// ---- generic pre-order (plain path and SIMT path for K > 4) ---------------
+
+// X for both children of each node of the level: one thread per
+// (child slot, category, pattern, state).
+template <typename T>
+__global__ void k_pre_x(Dims d, Tab<T> bt, const int *__restrict__ lvl_nodes, int lvl_off,
+                        const int *__restrict__ child, int root, const T *__restrict__ part,
+                        const T *__restrict__ pre, const int16_t *__restrict__ scale,
+                        const uint8_t *__restrict__ tips, const double *__restrict__ pi,
+                        const double *__restrict__ catw, const double *__restrict__ site_inv,
+                        T *__restrict__ xbuf) {
+  const int bi = blockIdx.y, x = blockIdx.z;
+  const int u = lvl_nodes[lvl_off + bi];
+  const int slot = u - d.N;
+  const long long idx = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+  if (idx >= (long long)d.C * d.P * d.Kp) return;
+  const int i = (int)(idx % d.Kp);
+  const long long cp = idx / d.Kp;
+  const int p = (int)(cp % d.P), c = (int)(cp / d.P);
+  T out = 0;
+  if (i < d.K) {
+    const int sib = child[2 * slot + 1 - x];
+    T uu;
+    if (u == root)
+      uu = (T)(catw[c] * pi[i] * site_inv[p]);
+    else
+      uu = pre[(((size_t)slot * d.C + c) * d.P + p) * d.Kp + i];
+    const T s = child_factor<T>(d, bt, part, tips, sib, c, p, i);
+    out = scale_by(uu * s, (int)scale[(size_t)slot * d.P + p]);
+  }
+  xbuf[((((size_t)bi * 2 + x) * d.C + c) * d.P + p) * d.Kp + i] = out;
+}
+
+// U_v = P_v^T X_v for internal children.
+template <typename T>
+__global__ void k_pre_u(Dims d, Tab<T> bt, const int *__restrict__ lvl_nodes, int lvl_off,
+                        const int *__restrict__ child, const T *__restrict__ xbuf,
+                        T *__restrict__ pre) {
+  const int bi = blockIdx.y, x = blockIdx.z;
+  const int u = lvl_nodes[lvl_off + bi];
+  const int slot = u - d.N;
+  const int v = child[2 * slot + x];
+  if (v < d.N) return;
+  const long long idx = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+  if (idx >= (long long)d.C * d.P * d.Kp) return;
+  const int j = (int)(idx % d.Kp);
+  const long long cp = idx / d.Kp;
+  const int p = (int)(cp % d.P), c = (int)(cp / d.P);
+  T acc = 0;
+  if (j < d.K) {
+    const T *X = xbuf + ((((size_t)bi * 2 + x) * d.C + c) * d.P + p) * d.Kp;
+    for (int i = 0; i < d.K; i++) acc += bt.mat(d, v, c, i, j) * X[i];
+  }
+  pre[(((size_t)(v - d.N) * d.C + c) * d.P + p) * d.Kp + j] = acc;
+}
+
+// Partial sums of G over a chunk of kTile patterns: one CTA per
+// (chunk, node of level, child slot); threads over (c, i, j).
+template <typename T>
+__global__ void k_G_part(Dims d, const int *__restrict__ lvl_nodes, int lvl_off,
+                         const int *__restrict__ child, const T *__restrict__ xbuf,
+                         const T *__restrict__ part, const uint8_t *__restrict__ tips,
+                         const unsigned long long *__restrict__ masks,
+                         const double *__restrict__ pw, int nchunk, T *__restrict__ Gpart) {
+  const int chunk = blockIdx.x, bi = blockIdx.y, x = blockIdx.z;
+  const int u = lvl_nodes[lvl_off + bi];
+  const int slot = u - d.N;
+  const int v = child[2 * slot + x];
+  const int p0 = chunk * kTile, p1 = min(d.P, p0 + kTile);
+  T *out = Gpart + (((size_t)slot * nchunk + chunk) * 2 + x) * d.C * d.KK;
+  for (int item = threadIdx.x; item < d.C * d.KK; item += blockDim.x) {
+    const int c = item / d.KK, ij = item % d.KK, i = ij / d.K, j = ij % d.K;
+    T acc = 0;
+    const T *X = xbuf + (((size_t)bi * 2 + x) * d.C + c) * d.P * d.Kp;
+    if (v < d.N) {
+      for (int p = p0; p < p1; p++)
+        if (code_allows(d, masks, tips[(size_t)v * d.P + p], j))
+          acc += (T)pw[p] * X[(size_t)p * d.Kp + i];
+    } else {
+      const T *L = part + ((size_t)(v - d.N) * d.C + c) * d.P * d.Kp;
+      for (int p = p0; p < p1; p++)
+        acc += (T)pw[p] * X[(size_t)p * d.Kp + i] * L[(size_t)p * d.Kp + j];
+    }
+    out[item] = acc;
+  }
+}
+
+// ---- fused FP32 pre-order for K = 4 -----------------------------------------
+// Reduce 32 per-lane values to one per lane (lane l ends with the warp sum of
+// value l) in 31 shuffles.
+__device__ __forceinline__ float reduce_scatter32(float (&v)[32]) {
+  const int lane = threadIdx.x & 31;
+#pragma unroll
+  for (int k = 0; k < 16; k++) {
+    const bool up = lane & 16;
+    const float send = up ? v[k] : v[k + 16];
+    const float keep = up ? v[k + 16] : v[k];
+    v[k] = keep + __shfl_xor_sync(0xffffffffu, send, 16);
+  }
+#pragma unroll
+  for (int k = 0; k < 8; k++) {
+    const bool up = lane & 8;
+    const float send = up ? v[k] : v[k + 8];
+    const float keep = up ? v[k + 8] : v[k];
+    v[k] = keep + __shfl_xor_sync(0xffffffffu, send, 8);
+  }
+#pragma unroll
+  for (int k = 0; k < 4; k++) {
+    const bool up = lane & 4;
+    const float send = up ? v[k] : v[k + 4];
+    const float keep = up ? v[k + 4] : v[k];
+    v[k] = keep + __shfl_xor_sync(0xffffffffu, send, 4);
+  }
+#pragma unroll
+  for (int k = 0; k < 2; k++) {
+    const bool up = lane & 2;
+    const float send = up ? v[k] : v[k + 2];
+    const float keep = up ? v[k + 2] : v[k];
+    v[k] = keep + __shfl_xor_sync(0xffffffffu, send, 2);
+  }
+  {
+    const bool up = lane & 1;
+    const float send = up ? v[0] : v[1];
+    const float keep = up ? v[1] : v[0];
+    v[0] = keep + __shfl_xor_sync(0xffffffffu, send, 1);
+  }
+  return v[0];
+}
+
+__device__ __forceinline__ float4 matvec_t(const float4 *t, float4 l) {
+  // S = sum_j l_j * row_j  (rows of the transposed table)
+  float4 s;
+  s.x = l.x * t[0].x + l.y * t[1].x + l.z * t[2].x + l.w * t[3].x;
+  s.y = l.x * t[0].y + l.y * t[1].y + l.z * t[2].y + l.w * t[3].y;
+  s.z = l.x * t[0].z + l.y * t[1].z + l.z * t[2].z + l.w * t[3].z;
+  s.w = l.x * t[0].w + l.y * t[1].w + l.z * t[2].w + l.w * t[3].w;
+  return s;
+}
+__device__ __forceinline__ float dot4(float4 a, float4 b) {
+  return a.x * b.x + a.y * b.y + a.z * b.z + a.w * b.w;
+}
+__device__ __forceinline__ float4 mul4(float4 a, float4 b) {
+  return make_float4(a.x * b.x, a.y * b.y, a.z * b.z, a.w * b.w);
+}
+__device__ __forceinline__ float4 ldexp4(float4 a, int e) {
+  return make_float4(ldexpf(a.x, -e), ldexpf(a.y, -e), ldexpf(a.z, -e), ldexpf(a.w, -e));
+}
+
+// One thread per pattern of one node u; per category: recompute S_v, S_w,
+// form X_v, X_w, store U_v, U_w (internal children) and accumulate the
+// weighted outer products into per-CTA sums of G (deterministic: fixed
+// shuffle and warp order).  Gpart[slot][blk][child][c][16].
+template <int CMAX>
+__global__ void __launch_bounds__(kTile) k_pre_k4(Dims d, const float *__restrict__ PT32,
+                                                  const int *__restrict__ lvl_nodes, int lvl_off,
+                                                  const int *__restrict__ child, int root,
+                                                  const float4 *__restrict__ part, float4 *pre,
+                                                  const int16_t *__restrict__ scale,
+                                                  const uint8_t *__restrict__ tips,
+                                                  const unsigned long long *__restrict__ masks,
+                                                  const double *__restrict__ pi,
+                                                  const double *__restrict__ catw,
+                                                  const double *__restrict__ site_inv,
+                                                  const double *__restrict__ pw,
+                                                  float *__restrict__ Gpart) {
+  extern __shared__ float4 spt[];  // [2][C][NR] tables, then warp sums
+  const int u = lvl_nodes[lvl_off + blockIdx.y];
+  const int slot = u - d.N;
+  const int ch0 = child[2 * slot], ch1 = child[2 * slot + 1];
+  const int CN = d.C * d.NR;
+  const float4 *pt4 = reinterpret_cast<const float4 *>(PT32);
+  for (int idx = threadIdx.x; idx < 2 * CN; idx += blockDim.x) {
+    const int x = idx / CN, r = idx - x * CN;
+    spt[idx] = pt4[(size_t)(x ? ch1 : ch0) * CN + r];
+  }
+  float *wsum = reinterpret_cast<float *>(spt + 2 * CN);  // [nwarps][32]
+  __syncthreads();
+  const int p = blockIdx.x * blockDim.x + threadIdx.x;
+  const bool active = p < d.P;
+  const int pc = active ? p : 0;
+  const int e = active ? (int)scale[(size_t)slot * d.P + pc] : 0;
+  const float n = active ? (float)pw[pc] : 0.f;
+  const float sinv = (float)site_inv[pc];
+  int code0 = 0, code1 = 0;
+  if (ch0 < d.N) code0 = tips[(size_t)ch0 * d.P + pc];
+  if (ch1 < d.N) code1 = tips[(size_t)ch1 * d.P + pc];
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nw = blockDim.x >> 5;
+  const int nblk = gridDim.x;
+  for (int c = 0; c < d.C; c++) {
+    const float4 *t0 = spt + c * d.NR, *t1 = spt + CN + c * d.NR;
+    float4 uu;
+    if (u == root) {
+      const float wc = (float)catw[c];
+      uu = make_float4(wc * (float)pi[0] * sinv, d.K > 1 ? wc * (float)pi[1] * sinv : 0.f,
+                       d.K > 2 ? wc * (float)pi[2] * sinv : 0.f,
+                       d.K > 3 ? wc * (float)pi[3] * sinv : 0.f);
+    } else {
+      uu = pre[((size_t)slot * d.C + c) * d.P + pc];
+    }
+    float4 l0, l1, s0, s1;
+    if (ch0 < d.N) {
+      s0 = t0[code0];
+      const unsigned long long mk = code0 < d.K ? (1ull << code0)
+                                    : (code0 == d.K ? ~0ull : masks[code0 - d.K - 1]);
+      l0 = make_float4((mk & 1ull) ? 1.f : 0.f, (mk & 2ull) ? 1.f : 0.f,
+                       (mk & 4ull) ? 1.f : 0.f, (mk & 8ull) ? 1.f : 0.f);
+    } else {
+      l0 = part[((size_t)(ch0 - d.N) * d.C + c) * d.P + pc];
+      s0 = matvec_t(t0, l0);
+    }
+    if (ch1 < d.N) {
+      s1 = t1[code1];
+      const unsigned long long mk = code1 < d.K ? (1ull << code1)
+                                    : (code1 == d.K ? ~0ull : masks[code1 - d.K - 1]);
+      l1 = make_float4((mk & 1ull) ? 1.f : 0.f, (mk & 2ull) ? 1.f : 0.f,
+                       (mk & 4ull) ? 1.f : 0.f, (mk & 8ull) ? 1.f : 0.f);
+    } else {
+      l1 = part[((size_t)(ch1 - d.N) * d.C + c) * d.P + pc];
+      s1 = matvec_t(t1, l1);
+    }
+    const float4 x0 = ldexp4(mul4(uu, s1), e);  // X for child 0
+    const float4 x1 = ldexp4(mul4(uu, s0), e);  // X for child 1
+    if (active && ch0 >= d.N) {
+      float4 o = make_float4(dot4(t0[0], x0), dot4(t0[1], x0), dot4(t0[2], x0), dot4(t0[3], x0));
+      pre[((size_t)(ch0 - d.N) * d.C + c) * d.P + p] = o;
+    }
+    if (active && ch1 >= d.N) {
+      float4 o = make_float4(dot4(t1[0], x1), dot4(t1[1], x1), dot4(t1[2], x1), dot4(t1[3], x1));
+      pre[((size_t)(ch1 - d.N) * d.C + c) * d.P + p] = o;
+    }
+    float g[32];
+    const float xa[4] = {x0.x * n, x0.y * n, x0.z * n, x0.w * n};
+    const float la[4] = {l0.x, l0.y, l0.z, l0.w};
+    const float xb[4] = {x1.x * n, x1.y * n, x1.z * n, x1.w * n};
+    const float lb[4] = {l1.x, l1.y, l1.z, l1.w};
+#pragma unroll
+    for (int i = 0; i < 4; i++)
+#pragma unroll
+      for (int j = 0; j < 4; j++) {
+        g[i * 4 + j] = xa[i] * la[j];
+        g[16 + i * 4 + j] = xb[i] * lb[j];
+      }
+    const float r = reduce_scatter32(g);
+    wsum[warp * 32 + lane] = r;
+    __syncthreads();
+    if (warp == 0) {
+      float t = 0.f;
+      for (int k = 0; k < nw; k++) t += wsum[k * 32 + lane];
+      const int xch = lane >> 4, ij = lane & 15;
+      Gpart[((((size_t)slot * nblk + blockIdx.x) * 2 + xch) * d.C + c) * 16 + ij] = t;
+    }
+    __syncthreads();
+  }
+}
+
+// G[v][c][i][j] = sum over pattern blocks of Gpart (FP64 accumulate, fixed
+// order).  One thread per (child node v, c, i, j).
+template <typename T>
+__global__ void k_G_reduce(Dims d, const int *__restrict__ parent, const int *__restrict__ child,
+                           const T *__restrict__ Gpart, int nchunk, double *__restrict__ G) {
+  const long long idx = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+  if (idx >= (long long)d.nn * d.C * d.KK) return;
+  const int ij = (int)(idx % d.KK);
+  const int c = (int)((idx / d.KK) % d.C);
+  const int v = (int)(idx / ((long long)d.KK * d.C));
+  const int u = parent[v];
+  if (u < 0) {
+    G[idx] = 0.0;
+    return;
+  }
+  const int slot = u - d.N;
+  const int x = (child[2 * slot] == v) ? 0 : 1;
+  double acc = 0.0;
+  for (int k = 0; k < nchunk; k++)
+    acc += (double)Gpart[((((size_t)slot * nchunk + k) * 2 + x) * d.C + c) * d.KK + ij];
+  G[idx] = acc;
+}
+
+// ---- chain rule per (branch, category) --------------------------------------
+// Matrices in shared memory in precision T (FP64 on the plain path, FP32 on
+// the FP32 paths, where G itself comes from FP32 partials).
+template <typename T>
+__device__ void mm(const Dims &d, const T *A, const T *B, T *C, bool ta, bool tb) {
+  // C = op(A) op(B)
+  const int K = d.K;
+  for (int idx = threadIdx.x; idx < d.KK; idx += blockDim.x) {
+    const int i = idx / K, j = idx % K;
+    T acc = 0;
+    for (int m = 0; m < K; m++) {
+      const T a = ta ? A[m * K + i] : A[i * K + m];
+      const T b = tb ? B[j * K + m] : B[m * K + j];
+      acc += a * b;
+    }
+    C[idx] = acc;
+  }
+}
+
+template <typename T>
+__device__ T bsum(T x, T *red) {
+  for (int o = 16; o > 0; o >>= 1) x += __shfl_xor_sync(0xffffffffu, x, o);
+  const int w = threadIdx.x >> 5, l = threadIdx.x & 31;
+  __syncthreads();
+  if (l == 0) red[w] = x;
+  __syncthreads();
+  T t = 0;
+  for (int i = 0; i < (int)((blockDim.x + 31) >> 5); i++) t += red[i];
+  __syncthreads();
+  return t;
+}
+
+__device__ __forceinline__ double t_expm1(double x) { return expm1(x); }
+__device__ __forceinline__ float t_expm1(float x) { return expm1f(x); }
+
+// Segment exponential E = exp(tau Q_s) into Eo (eigen path or
+// uniformisation); scratch W, Y, B.
+template <typename T>
+__device__ void seg_exp(const Dims &d, int s, double tau, const double *lam, const double *V,
+                        const double *Vinv, const double *Qn, T *Eo, T *W, T *Y, T *Bm, T *ev) {
+  const int K = d.K, KK = d.KK;
+  if (d.reversible) {
+    for (int i = threadIdx.x; i < K; i += blockDim.x) ev[i] = (T)exp(tau * lam[(size_t)s * K + i]);
+    __syncthreads();
+    const double *Vs = V + (size_t)s * KK, *Vi = Vinv + (size_t)s * KK;
+    for (int idx = threadIdx.x; idx < KK; idx += blockDim.x) {
+      const int i = idx / K, j = idx % K;
+      T acc = 0;
+      for (int m = 0; m < K; m++) acc += (T)Vs[i * K + m] * ev[m] * (T)Vi[m * K + j];
+      Eo[idx] = acc;
+    }
+    __syncthreads();
+    return;
+  }
+  const double *Qs = Qn + (size_t)s * KK;
+  double mu = 0.0;
+  for (int i = 0; i < K; i++) mu = fmax(mu, fabs(Qs[i * K + i]));
+  for (int idx = threadIdx.x; idx < KK; idx += blockDim.x)
+    Eo[idx] = (idx / K == idx % K) ? (T)1 : (T)0;
+  __syncthreads();
+  if (mu == 0.0 || tau == 0.0) return;
+  for (int idx = threadIdx.x; idx < KK; idx += blockDim.x)
+    Bm[idx] = (T)(Qs[idx] / mu + ((idx / K == idx % K) ? 1.0 : 0.0));
+  const double mt = mu * tau;
+  const int npc = (int)ceil(mt / 30.0);
+  const double x = mt / npc;
+  const int mmax = (int)ceil(x + 12.0 * sqrt(x) + 30.0);
+  for (int piece = 0; piece < npc; piece++) {
+    double w = exp(-x);
+    __syncthreads();
+    for (int idx = threadIdx.x; idx < KK; idx += blockDim.x) {
+      Y[idx] = Eo[idx];
+      W[idx] = (T)w * Eo[idx];
+    }
+    __syncthreads();
+    for (int m = 1; m <= mmax; m++) {
+      w = w * x / (double)m;
+      mm<T>(d, Y, Bm, Eo, false, false);
+      __syncthreads();
+      for (int idx = threadIdx.x; idx < KK; idx += blockDim.x) {
+        Y[idx] = Eo[idx];
+        W[idx] += (T)w * Eo[idx];
+      }
+      __syncthreads();
+    }
+    for (int idx = threadIdx.x; idx < KK; idx += blockDim.x) Eo[idx] = W[idx];
+    __syncthreads();
+  }
+}
+
+template <typename T>
+__global__ void k_grad_branch(Dims d, const double *__restrict__ G, const int *__restrict__ nseg,
+                              const int *__restrict__ seg_mat, const double *__restrict__ seg_dt,
+                              const double *__restrict__ brate, const double *__restrict__ catr,
+                              const double *__restrict__ lam, const double *__restrict__ V,
+                              const double *__restrict__ Vinv, const double *__restrict__ Qn,
+                              const T *__restrict__ Dth, const int *__restrict__ Dnz,
+                              T *__restrict__ gseg) {
+  extern __shared__ unsigned char smraw[];
+  T *sm = reinterpret_cast<T *>(smraw);
+  const int v = blockIdx.x, c = blockIdx.y;
+  const int ns = nseg[v];
+  if (ns == 0) return;
+  const int K = d.K, KK = d.KK;
+  // seven K x K work matrices (an FP64 K = 64 set must fit in 227 KB); G is
+  // read from global memory on the FP64 path and staged as an eighth
+  // matrix on the FP32 path
+  T *A = sm, *Z = A + KK, *H = Z + KK, *E = H + KK, *W = E + KK, *Y = W + KK, *Bm = Y + KK,
+    *ev = Bm + KK, *red = ev + K;
+  const double r = brate[v] * catr[c];
+  const int stride = 1 + d.np;
+  const T *Gm;
+  if constexpr (sizeof(T) == sizeof(double)) {
+    Gm = reinterpret_cast<const T *>(G + ((size_t)v * d.C + c) * KK);
+  } else {
+    T *g = red + 32;
+    for (int idx = threadIdx.x; idx < KK; idx += blockDim.x)
+      g[idx] = (T)G[((size_t)v * d.C + c) * KK + idx];
+    Gm = g;
+  }
+  for (int idx = threadIdx.x; idx < KK; idx += blockDim.x) A[idx] = (idx / K == idx % K) ? 1 : 0;
+  __syncthreads();
+  for (int k = 0; k < ns; k++) {
+    const int s = seg_mat[v * d.E + k];
+    const double tau = r * seg_dt[v * d.E + k];
+    // Z = E_{k+1} ... E_{n-1}  (recomputed; branches rarely have many segments)
+    for (int idx = threadIdx.x; idx < KK; idx += blockDim.x) Z[idx] = (idx / K == idx % K) ? 1 : 0;
+    __syncthreads();
+    for (int q = k + 1; q < ns; q++) {
+      seg_exp<T>(d, seg_mat[v * d.E + q], r * seg_dt[v * d.E + q], lam, V, Vinv, Qn, E, W, Y, Bm,
+                 ev);
+      mm<T>(d, Z, E, W, false, false);
+      __syncthreads();
+      for (int idx = threadIdx.x; idx < KK; idx += blockDim.x) Z[idx] = W[idx];
+      __syncthreads();
+    }
+    // H = A^T G Z^T
+    if (ns == 1) {
+      for (int idx = threadIdx.x; idx < KK; idx += blockDim.x) H[idx] = Gm[idx];
+    } else {
+      mm<T>(d, A, Gm, W, true, false);
+      __syncthreads();
+      mm<T>(d, W, Z, H, false, true);
+    }
+    __syncthreads();
+    // this segment's exponential
+    seg_exp<T>(d, s, tau, lam, V, Vinv, Qn, E, W, Y, Bm, ev);
+    T dk;
+    if (d.reversible) {
+      // Hhat = V^T H V^-T  into W
+      const double *Vs = V + (size_t)s * KK, *Vi = Vinv + (size_t)s * KK;
+      for (int idx = threadIdx.x; idx < KK; idx += blockDim.x) {  // Y = H V^-T
+        const int i = idx / K, j = idx % K;
+        T acc = 0;
+        for (int m = 0; m < K; m++) acc += H[i * K + m] * (T)Vi[j * K + m];
+        Y[idx] = acc;
+      }
+      __syncthreads();
+      for (int idx = threadIdx.x; idx < KK; idx += blockDim.x) {  // W = V^T Y
+        const int i = idx / K, j = idx % K;
+        T acc = 0;
+        for (int m = 0; m < K; m++) acc += (T)Vs[m * K + i] * Y[m * K + j];
+        W[idx] = acc;
+      }
+      for (int i = threadIdx.x; i < K; i += blockDim.x)
+        ev[i] = (T)exp(tau * lam[(size_t)s * K + i]);
+      __syncthreads();
+      T part = 0;
+      for (int i = threadIdx.x; i < K; i += blockDim.x)
+        part += W[i * K + i] * (T)lam[(size_t)s * K + i] * ev[i];
+      dk = bsum<T>(part, red);
+      // model parameters: <Hhat o Phi, D_a,s>
+      if (d.np > 0) {
+        for (int idx = threadIdx.x; idx < KK; idx += blockDim.x) {  // W <- Hhat o Phi
+          const int i = idx / K, j = idx % K;
+          const T li = (T)lam[(size_t)s * K + i], lj = (T)lam[(size_t)s * K + j];
+          const T tt = (T)tau;
+          const T xx = tt * (li - lj);
+          T phi;
+          if (xx == (T)0)
+            phi = tt * ev[j];
+          else
+            phi = ev[j] * tt * (t_expm1(xx) / xx);
+          W[idx] *= phi;
+        }
+        __syncthreads();
+        for (int a = 0; a < d.np; a++) {
+          if (!Dnz[a * d.S + s]) {
+            if (threadIdx.x == 0) gseg[(((size_t)v * d.E + k) * d.C + c) * stride + 1 + a] = 0;
+            continue;
+          }
+          const T *Da = Dth + ((size_t)a * d.S + s) * KK;
+          T pa = 0;
+          for (int idx = threadIdx.x; idx < KK; idx += blockDim.x) pa += W[idx] * Da[idx];
+          const T ga = bsum<T>(pa, red);
+          if (threadIdx.x == 0) gseg[(((size_t)v * d.E + k) * d.C + c) * stride + 1 + a] = ga;
+        }
+      }
+    } else {
+      // <H, Q E>
+      const double *Qs = Qn + (size_t)s * KK;
+      T part = 0;
+      for (int idx = threadIdx.x; idx < KK; idx += blockDim.x) {
+        const int i = idx / K, j = idx % K;
+        T qe = 0;
+        for (int m = 0; m < K; m++) qe += (T)Qs[i * K + m] * E[m * K + j];
+        part += H[idx] * qe;
+      }
+      dk = bsum<T>(part, red);
+      for (int a = 0; a < d.np; a++)
+        if (threadIdx.x == 0) gseg[(((size_t)v * d.E + k) * d.C + c) * stride + 1 + a] = 0;
+    }
+    if (threadIdx.x == 0) gseg[(((size_t)v * d.E + k) * d.C + c) * stride] = dk;
+    // A <- A E_k
+    __syncthreads();
+    if (k + 1 < ns) {
+      mm<T>(d, A, E, W, false, false);
+      __syncthreads();
+      for (int idx = threadIdx.x; idx < KK; idx += blockDim.x) A[idx] = W[idx];
+      __syncthreads();
+    }
+  }
+}
+
+// Final reductions into FP64 outputs (fixed order, deterministic):
+//   blocks [0, nb_nodes): node heights and branch rates (thread per node);
+//   next E-1 blocks: boundary j;  next np blocks: parameter a.
+// out = [d_heights (nn) | d_boundaries (E-1) | d_params (np) | d_rates (nn)].
+template <typename T>
+__global__ void k_grad_reduce(Dims d, const int *__restrict__ parent, const int *__restrict__ child,
+                              const int *__restrict__ nseg, const double *__restrict__ seg_dt,
+                              const int *__restrict__ seg_hi, const int *__restrict__ seg_lo,
+                              const double *__restrict__ brate, const double *__restrict__ catr,
+                              const T *__restrict__ gseg, int nb_nodes, double *__restrict__ out) {
+  __shared__ double red[32];
+  const int stride = 1 + d.np;
+  // d lnL / d dt of segment (v, k) summed over categories
+  auto gdt = [&](int v, int k) {
+    double acc = 0.0;
+    for (int c = 0; c < d.C; c++)
+      acc += brate[v] * catr[c] * (double)gseg[(((size_t)v * d.E + k) * d.C + c) * stride];
+    return acc;
+  };
+  if ((int)blockIdx.x < nb_nodes) {
+    const int u = blockIdx.x * blockDim.x + threadIdx.x;
+    if (u >= d.nn) return;
+    double dh = 0.0;
+    if (u >= d.N) {
+      for (int x = 0; x < 2; x++) dh += gdt(child[2 * (u - d.N) + x], 0);
+    }
+    double dr = 0.0;
+    if (parent[u] >= 0) {
+      dh -= gdt(u, nseg[u] - 1);
+      for (int k = 0; k < nseg[u]; k++) {
+        double acc = 0.0;
+        for (int c = 0; c < d.C; c++)
+          acc += catr[c] * (double)gseg[(((size_t)u * d.E + k) * d.C + c) * stride];
+        dr += acc * seg_dt[u * d.E + k];
+      }
+    }
+    out[u] = dh;
+    out[d.nn + (d.E - 1) + d.np + u] = dr;
+    return;
+  }
+  const int b = blockIdx.x - nb_nodes;
+  double part = 0.0;
+  if (b < d.E - 1) {
+    const int ref = -(b + 1);
+    for (int v = threadIdx.x; v < d.nn; v += blockDim.x) {
+      for (int k = 0; k < nseg[v]; k++) {
+        if (seg_hi[v * d.E + k] == ref) part += gdt(v, k);
+        if (seg_lo[v * d.E + k] == ref) part -= gdt(v, k);
+      }
+    }
+  } else {
+    const int a = b - (d.E - 1);
+    for (int v = threadIdx.x; v < d.nn; v += blockDim.x)
+      for (int k = 0; k < nseg[v]; k++)
+        for (int c = 0; c < d.C; c++)
+          part += (double)gseg[(((size_t)v * d.E + k) * d.C + c) * stride + 1 + a];
+  }
+  for (int o = 16; o > 0; o >>= 1) part += __shfl_xor_sync(0xffffffffu, part, o);
+  const int w = threadIdx.x >> 5, l = threadIdx.x & 31;
+  if (l == 0) red[w] = part;
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    double t = 0.0;
+    for (int i = 0; i < (int)(blockDim.x >> 5); i++) t += red[i];
+    if (b < d.E - 1)
+      out[d.nn + b] = t;
+    else
+      out[d.nn + (d.E - 1) + (b - (d.E - 1))] = t;
+  }
+}
+
+template <int CMAX>
+void launch_pre_k4_levels(epoch_ctx *c, int root) {
+  const Dims &d = c->d;
+  const size_t smem = sizeof(float4) * 2 * d.C * d.NR + sizeof(float) * 32 * (kTile / 32);
+  if (smem > 48 * 1024)
+    cudaFuncSetAttribute(k_pre_k4<CMAX>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+  const int L = (int)c->h_level_off.size() - 1;
+  for (int l = L - 1; l >= 0; l--) {
+    const int w = c->h_level_off[l + 1] - c->h_level_off[l];
+    dim3 grid(ceil_div(d.P, kTile), w);
+    k_pre_k4<CMAX><<<grid, kTile, smem, c->stream>>>(
+        d, c->d_PT32, c->d_level_nodes, c->h_level_off[l], c->d_child, root,
+        reinterpret_cast<const float4 *>(c->d_part), reinterpret_cast<float4 *>(c->d_pre),
+        c->d_scale, c->d_tips, c->d_masks, c->d_pi, c->d_catw, c->d_site_inv, c->d_pw,
+        (float *)c->d_Gpart);
+    c->launches++;
+  }
+}
+
+template <typename T>
+void launch_pre_generic(epoch_ctx *c, Tab<T> bt, int root) {
+  const Dims &d = c->d;
+  const int L = (int)c->h_level_off.size() - 1;
+  const long long items = (long long)d.C * d.P * d.Kp;
+  const int nchunk = ceil_div(d.P, kTile);
+  for (int l = L - 1; l >= 0; l--) {
+    const int w = c->h_level_off[l + 1] - c->h_level_off[l];
+    dim3 g(ceil_div(items, 256), w, 2);
+    k_pre_x<T><<<g, 256, 0, c->stream>>>(d, bt, c->d_level_nodes, c->h_level_off[l], c->d_child,
+                                         root, (const T *)c->d_part, (const T *)c->d_pre,
+                                         c->d_scale, c->d_tips, c->d_pi, c->d_catw,
+                                         c->d_site_inv, (T *)c->d_xbuf);
+    k_pre_u<T><<<g, 256, 0, c->stream>>>(d, bt, c->d_level_nodes, c->h_level_off[l], c->d_child,
+                                         (const T *)c->d_xbuf, (T *)c->d_pre);
+    dim3 gg(nchunk, w, 2);
+    k_G_part<T><<<gg, 256, 0, c->stream>>>(d, c->d_level_nodes, c->h_level_off[l], c->d_child,
+                                           (const T *)c->d_xbuf, (const T *)c->d_part, c->d_tips,
+                                           c->d_masks, c->d_pw, nchunk, (T *)c->d_Gpart);
+    c->launches += 3;
+  }
+}
+
+}  // namespace
+
+cudaError_t launch_adjoint(epoch_ctx *c) {
+  const Dims &d = c->d;
+  int root = -1;
+  for (int v = 0; v < d.nn; v++)
+    if (c->h_parent[v] < 0) root = v;
+  const int nchunk = ceil_div(d.P, kTile);
+  const long long nG = (long long)d.nn * d.C * d.KK;
+  if (c->precision == EPOCH_FP64) {
+    launch_pre_generic<double>(c, Tab<double>{c->d_P64, c->d_masks}, root);
+    k_G_reduce<double><<<ceil_div(nG, 256), 256, 0, c->stream>>>(
+        d, c->d_parent, c->d_child, (const double *)c->d_Gpart, nchunk, c->d_G);
+  } else {
+    if (d.K == 4) {
+      if (d.C <= 4)
+        launch_pre_k4_levels<4>(c, root);
+      else if (d.C <= 8)
+        launch_pre_k4_levels<8>(c, root);
+      else
+        launch_pre_k4_levels<16>(c, root);
+    } else {
+      launch_pre_generic<float>(c, Tab<float>{c->d_PT32, c->d_masks}, root);
+    }
+    k_G_reduce<float><<<ceil_div(nG, 256), 256, 0, c->stream>>>(
+        d, c->d_parent, c->d_child, (const float *)c->d_Gpart, nchunk, c->d_G);
+  }
+  c->launches++;
+  return cudaGetLastError();
+}
+
+cudaError_t launch_chain_rule(epoch_ctx *c) {
+  const Dims &d = c->d;
+  dim3 grid(d.nn, d.C);
+  const int threads = d.KK >= 1024 ? 256 : (d.KK >= 256 ? 128 : 32);
+  const int nb_nodes = ceil_div(d.nn, 256);
+  const int nblocks = nb_nodes + (d.E - 1) + d.np;
+  if (c->precision == EPOCH_FP64) {
+    size_t smem = sizeof(double) * (7 * d.KK + d.K + 32);
+    cudaFuncSetAttribute(k_grad_branch<double>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                         (int)smem);
+    k_grad_branch<double><<<grid, threads, smem, c->stream>>>(
+        d, c->d_G, c->d_nseg, c->d_seg_mat, c->d_seg_dt, c->d_brate, c->d_catr, c->d_lam, c->d_V,
+        c->d_Vinv, c->d_Q, c->d_Dth, c->d_Dnz, (double *)c->d_gseg);
+    k_grad_reduce<double><<<nblocks, 256, 0, c->stream>>>(
+        d, c->d_parent, c->d_child, c->d_nseg, c->d_seg_dt, c->d_seg_hi, c->d_seg_lo, c->d_brate,
+        c->d_catr, (const double *)c->d_gseg, nb_nodes, c->d_grad);
+  } else {
+    size_t smem = sizeof(float) * (8 * d.KK + d.K + 32);
+    cudaFuncSetAttribute(k_grad_branch<float>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                         (int)smem);
+    k_grad_branch<float><<<grid, threads, smem, c->stream>>>(
+        d, c->d_G, c->d_nseg, c->d_seg_mat, c->d_seg_dt, c->d_brate, c->d_catr, c->d_lam, c->d_V,
+        c->d_Vinv, c->d_Q, c->d_Dth32, c->d_Dnz, (float *)c->d_gseg);
+    k_grad_reduce<float><<<nblocks, 256, 0, c->stream>>>(
+        d, c->d_parent, c->d_child, c->d_nseg, c->d_seg_dt, c->d_seg_hi, c->d_seg_lo, c->d_brate,
+        c->d_catr, (const float *)c->d_gseg, nb_nodes, c->d_grad);
+  }
+  c->launches += 2;
+  return cudaGetLastError();
+}
+
+}  // namespace epoch

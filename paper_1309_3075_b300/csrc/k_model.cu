@@ -1,0 +1,462 @@
+// k_model.cu -- branch segmentation, rate-matrix normalisation and
+// eigendecomposition, parameter-derivative transforms and the FP64 branch
+// transition matrices (time-ordered products of segment exponentials).
+//
+// Paper: Methods (Eq. makeprobs and the normalisation sum_i pi_i q_ii = -1),
+// "Relaxing time-homogeneity" (branch segmentation, Eq. matrixProduct,
+// Eq. convolution) and Appendix A (eigen-decomposition reuse).
+#include <math.h>
+
+#include "epoch_internal.cuh"
+
+namespace epoch {
+namespace {
+
+// ---------------------------------------------------------------------------
+// Segmentation: one thread per node v (the branch above v).  Segments are
+// written parent end first into a fixed stride of E slots: a branch crosses
+// at most E-1 boundaries.  A segment belongs to the epoch of its lower end;
+// refs name what bounds it (node id >= 0, boundary j as -(j+1)).
+// ---------------------------------------------------------------------------
+__global__ void k_segments(Dims d, const double *__restrict__ heights,
+                           const int *__restrict__ parent,
+                           const double *__restrict__ b, const int *__restrict__ phi,
+                           int *__restrict__ nseg, int *__restrict__ seg_mat,
+                           double *__restrict__ seg_dt, int *__restrict__ seg_hi,
+                           int *__restrict__ seg_lo) {
+  int v = blockIdx.x * blockDim.x + threadIdx.x;
+  if (v >= d.nn) return;
+  int u = parent[v];
+  if (u < 0) {
+    nseg[v] = 0;
+    return;
+  }
+  const int E = d.E;
+  double lo = heights[v], hi = heights[u];
+  int base = v * E;
+  int n = 0;
+  if (hi == lo) {
+    int e = 0;
+    for (int j = 0; j < E - 1; j++) e += (b[j] <= lo);
+    seg_mat[base] = phi[e];
+    seg_dt[base] = 0.0;
+    seg_hi[base] = u;
+    seg_lo[base] = v;
+    nseg[v] = 1;
+    return;
+  }
+  double top = hi;
+  int top_ref = u;
+  for (int j = E - 2; j >= 0; j--) {
+    double bj = b[j];
+    if (bj > lo && bj < hi) {
+      // the piece above b_j lies in epoch j+1 (boundaries strictly increase)
+      seg_mat[base + n] = phi[j + 1];
+      seg_dt[base + n] = top - bj;
+      seg_hi[base + n] = top_ref;
+      seg_lo[base + n] = -(j + 1);
+      n++;
+      top = bj;
+      top_ref = -(j + 1);
+    }
+  }
+  int e = 0;
+  for (int j = 0; j < E - 1; j++) e += (b[j] <= lo);
+  seg_mat[base + n] = phi[e];
+  seg_dt[base + n] = top - lo;
+  seg_hi[base + n] = top_ref;
+  seg_lo[base + n] = v;
+  nseg[v] = n + 1;
+}
+
+// ---------------------------------------------------------------------------
+// Block-wide FP64 sum (all threads get the result).
+// ---------------------------------------------------------------------------
+__device__ double block_sum(double x, double *red) {
+  for (int o = 16; o > 0; o >>= 1) x += __shfl_xor_sync(0xffffffffu, x, o);
+  int w = threadIdx.x >> 5, l = threadIdx.x & 31;
+  __syncthreads();
+  if (l == 0) red[w] = x;
+  __syncthreads();
+  double t = 0.0;
+  int nw = (blockDim.x + 31) >> 5;
+  for (int i = 0; i < nw; i++) t += red[i];
+  __syncthreads();
+  return t;
+}
+
+// ---------------------------------------------------------------------------
+// Normalise each Q_s and, for reversible models, diagonalise the symmetric
+// S = Pi^{1/2} Q Pi^{-1/2} by parallel cyclic Jacobi (round-robin pairing:
+// the n/2 rotations of a round act on disjoint index pairs and are applied
+// together as J^T A J).  Q = V diag(lambda) V^{-1}, V = Pi^{-1/2} U,
+// V^{-1} = U^T Pi^{1/2}.  One CTA per matrix, FP64.
+// ---------------------------------------------------------------------------
+__global__ void k_model_setup(Dims d, int normalise, const double *__restrict__ Qraw,
+                              const double *__restrict__ pi, double *__restrict__ Qn,
+                              double *__restrict__ cnorm, double *__restrict__ lam,
+                              double *__restrict__ V, double *__restrict__ Vinv,
+                              int *__restrict__ status) {
+  extern __shared__ double sm[];
+  const int K = d.K, KK = d.KK;
+  const int s = blockIdx.x;
+  double *A = sm;            // K*K
+  double *U = A + KK;        // K*K
+  double *rs = U + KK;       // K   sqrt(pi)
+  double *red = rs + K;      // 32
+  double *cs = red + 32;     // 32 rotation cosines
+  double *sn = cs + 32;      // 32 rotation sines
+  int *pq = (int *)(sn + 32);  // 64 pair indices
+  int *ord = pq + 64;          // 64 round-robin order
+  const int tid = threadIdx.x, nt = blockDim.x;
+
+  for (int i = tid; i < KK; i += nt) A[i] = Qraw[(size_t)s * KK + i];
+  for (int i = tid; i < K; i += nt) rs[i] = sqrt(pi[i]);
+  __syncthreads();
+  double part = 0.0;
+  for (int i = tid; i < K; i += nt) part -= pi[i] * A[i * K + i];
+  double c = block_sum(part, red);
+  double scale = normalise ? c : 1.0;
+  if (!(scale > 0.0)) scale = 1.0;  // rejected on the host already
+  for (int i = tid; i < KK; i += nt) {
+    A[i] /= scale;
+    Qn[(size_t)s * KK + i] = A[i];
+  }
+  if (tid == 0) cnorm[s] = scale;
+  if (!d.reversible) return;
+  __syncthreads();
+  // symmetric form
+  for (int idx = tid; idx < KK; idx += nt) {
+    int i = idx / K, j = idx % K;
+    U[idx] = rs[i] * A[idx] / rs[j];
+  }
+  __syncthreads();
+  for (int idx = tid; idx < KK; idx += nt) {
+    int i = idx / K, j = idx % K;
+    A[idx] = 0.5 * (U[i * K + j] + U[j * K + i]);
+  }
+  __syncthreads();
+  for (int idx = tid; idx < KK; idx += nt) U[idx] = (idx / K == idx % K) ? 1.0 : 0.0;
+  const int n = K + (K & 1);
+  for (int i = tid; i < n; i += nt) ord[i] = i;
+  part = 0.0;
+  for (int i = tid; i < KK; i += nt) part += A[i] * A[i];
+  double fro2 = block_sum(part, red);
+  const double tol2 = 1e-32 * fro2;  // (1e-16 * ||A||_F)^2
+  int converged = 0;
+  for (int sweep = 0; sweep < 60; sweep++) {
+    part = 0.0;
+    for (int idx = tid; idx < KK; idx += nt) {
+      int i = idx / K, j = idx % K;
+      if (j > i) part += A[idx] * A[idx];
+    }
+    double off = block_sum(part, red);
+    if (off <= tol2) {
+      converged = 1;
+      break;
+    }
+    for (int round = 0; round < n - 1; round++) {
+      const int npair = n / 2;
+      for (int k = tid; k < npair; k += nt) {
+        int a = ord[k], b2 = ord[n - 1 - k];
+        int p = a < b2 ? a : b2, q = a < b2 ? b2 : a;
+        double cc = 1.0, ss = 0.0;
+        if (q < K) {
+          double apq = A[p * K + q];
+          if (apq != 0.0) {
+            double theta = (A[q * K + q] - A[p * K + p]) / (2.0 * apq);
+            double t;
+            if (fabs(theta) > 1e150)
+              t = 0.5 / theta;
+            else
+              t = (theta >= 0.0 ? 1.0 : -1.0) / (fabs(theta) + sqrt(theta * theta + 1.0));
+            cc = 1.0 / sqrt(t * t + 1.0);
+            ss = t * cc;
+          }
+        }
+        cs[k] = cc;
+        sn[k] = ss;
+        pq[2 * k] = p;
+        pq[2 * k + 1] = q;
+      }
+      __syncthreads();
+      // rows: B = J^T A
+      for (int idx = tid; idx < npair * K; idx += nt) {
+        int k = idx / K, col = idx % K;
+        int p = pq[2 * k], q = pq[2 * k + 1];
+        if (q >= K || sn[k] == 0.0) continue;
+        double ap = A[p * K + col], aq = A[q * K + col];
+        A[p * K + col] = cs[k] * ap - sn[k] * aq;
+        A[q * K + col] = sn[k] * ap + cs[k] * aq;
+      }
+      __syncthreads();
+      // columns: A' = B J, U' = U J
+      for (int idx = tid; idx < npair * K; idx += nt) {
+        int k = idx / K, row = idx % K;
+        int p = pq[2 * k], q = pq[2 * k + 1];
+        if (q >= K || sn[k] == 0.0) continue;
+        double ap = A[row * K + p], aq = A[row * K + q];
+        A[row * K + p] = cs[k] * ap - sn[k] * aq;
+        A[row * K + q] = sn[k] * ap + cs[k] * aq;
+        double up = U[row * K + p], uq = U[row * K + q];
+        U[row * K + p] = cs[k] * up - sn[k] * uq;
+        U[row * K + q] = sn[k] * up + cs[k] * uq;
+      }
+      __syncthreads();
+      for (int k = tid; k < npair; k += nt) {
+        int p = pq[2 * k], q = pq[2 * k + 1];
+        if (q < K && sn[k] != 0.0) {
+          A[p * K + q] = 0.0;
+          A[q * K + p] = 0.0;
+        }
+      }
+      if (tid == 0) {
+        int last = ord[n - 1];
+        for (int i = n - 1; i >= 2; i--) ord[i] = ord[i - 1];
+        ord[1] = last;
+      }
+      __syncthreads();
+    }
+  }
+  if (!converged) {
+    part = 0.0;
+    for (int idx = tid; idx < KK; idx += nt) {
+      int i = idx / K, j = idx % K;
+      if (j > i) part += A[idx] * A[idx];
+    }
+    double off = block_sum(part, red);
+    if (off > 1e-24 * fro2 && tid == 0) atomicOr(status, ST_EIG_NOCONV);
+  }
+  for (int i = tid; i < K; i += nt) lam[(size_t)s * K + i] = A[i * K + i];
+  for (int idx = tid; idx < KK; idx += nt) {
+    int i = idx / K, j = idx % K;
+    V[(size_t)s * KK + idx] = U[idx] / rs[i];
+    Vinv[(size_t)s * KK + idx] = U[j * K + i] * rs[j];
+  }
+}
+
+// ---------------------------------------------------------------------------
+// Parameter derivatives in the eigenbasis: D_{a,s} = V_s^{-1} dQ_eff V_s with
+// dQ_eff = (dQraw - Q_s dc) / c the derivative of the normalised matrix
+// (c = -sum_i pi_i qraw_ii, dc its derivative).  One CTA per (a, s), FP64.
+// ---------------------------------------------------------------------------
+__global__ void k_param_transform(Dims d, int normalise, const double *__restrict__ dQraw,
+                                  const double *__restrict__ pi,
+                                  const double *__restrict__ Qn,
+                                  const double *__restrict__ cnorm,
+                                  const double *__restrict__ V,
+                                  const double *__restrict__ Vinv,
+                                  double *__restrict__ D, float *__restrict__ D32,
+                                  int *__restrict__ Dnz) {
+  extern __shared__ double sm[];
+  const int K = d.K, KK = d.KK;
+  const int a = blockIdx.x, s = blockIdx.y;
+  double *X = sm, *T = sm + KK, *red = sm + 2 * KK;
+  const double *dq = dQraw + ((size_t)a * d.S + s) * KK;
+  const int tid = threadIdx.x, nt = blockDim.x;
+  double part = 0.0;
+  int nz = 0;
+  for (int i = tid; i < KK; i += nt) nz |= (dq[i] != 0.0);
+  for (int i = tid; i < K; i += nt) part -= pi[i] * dq[i * K + i];
+  double dc = block_sum(part, red);
+  nz = __syncthreads_or(nz);
+  double c = cnorm[s];
+  for (int i = tid; i < KK; i += nt)
+    X[i] = normalise ? (dq[i] - Qn[(size_t)s * KK + i] * dc) / c : dq[i];
+  __syncthreads();
+  const double *Vs = V + (size_t)s * KK, *Vi = Vinv + (size_t)s * KK;
+  for (int idx = tid; idx < KK; idx += nt) {  // T = X V
+    int i = idx / K, j = idx % K;
+    double acc = 0.0;
+    for (int k = 0; k < K; k++) acc += X[i * K + k] * Vs[k * K + j];
+    T[idx] = acc;
+  }
+  __syncthreads();
+  double *out = D + ((size_t)a * d.S + s) * KK;
+  float *out32 = D32 + ((size_t)a * d.S + s) * KK;
+  for (int idx = tid; idx < KK; idx += nt) {  // D = V^-1 T
+    int i = idx / K, j = idx % K;
+    double acc = 0.0;
+    for (int k = 0; k < K; k++) acc += Vi[i * K + k] * T[k * K + j];
+    out[idx] = acc;
+    out32[idx] = (float)acc;
+  }
+  if (tid == 0) Dnz[a * d.S + s] = nz;
+}
+
+// ---------------------------------------------------------------------------
+// Branch transition matrices, FP64.  One CTA per (branch v, category c):
+// M = I; for each segment from the parent end, M <- M * exp(r rho dt Q_s)
+// (Eq. convolution).  Reversible: exp via the eigensystem,
+// E = V diag(exp(tau lambda)) V^{-1}.  General Q: uniformisation,
+// M <- sum_m Pois(m; mu tau) M B^m, B = I + Q/mu, in pieces of mu*tau <= 30.
+// Writes P64[v][c] and, for the FP32 paths, the transposed table
+// PT32[v][c][j][i] = P[i][j] with rows K (missing: row sums) and
+// K+1+m (ambiguity mask m) appended.
+// ---------------------------------------------------------------------------
+__global__ void k_branch_matrices(Dims d, const int *__restrict__ nseg,
+                                  const int *__restrict__ seg_mat,
+                                  const double *__restrict__ seg_dt,
+                                  const double *__restrict__ brate,
+                                  const double *__restrict__ catr,
+                                  const double *__restrict__ lam,
+                                  const double *__restrict__ V,
+                                  const double *__restrict__ Vinv,
+                                  const double *__restrict__ Qn,
+                                  const unsigned long long *__restrict__ masks,
+                                  double *__restrict__ P64, float *__restrict__ PT32) {
+  extern __shared__ double sm[];
+  const int K = d.K, KK = d.KK;
+  const int v = blockIdx.x, c = blockIdx.y;
+  const int ns = nseg[v];
+  if (ns == 0) return;  // root
+  double *M = sm, *W = sm + KK, *Y = sm + 2 * KK, *B = sm + 3 * KK, *ev = sm + 4 * KK;
+  const int tid = threadIdx.x, nt = blockDim.x;
+  const double r = brate[v] * catr[c];
+  for (int idx = tid; idx < KK; idx += nt) M[idx] = (idx / K == idx % K) ? 1.0 : 0.0;
+  __syncthreads();
+  for (int k = 0; k < ns; k++) {
+    const int s = seg_mat[v * d.E + k];
+    const double tau = r * seg_dt[v * d.E + k];
+    if (d.reversible) {
+      const double *Vs = V + (size_t)s * KK, *Vi = Vinv + (size_t)s * KK;
+      for (int i = tid; i < K; i += nt) ev[i] = exp(tau * lam[(size_t)s * K + i]);
+      __syncthreads();
+      // W = V diag(ev) V^-1
+      for (int idx = tid; idx < KK; idx += nt) {
+        int i = idx / K, j = idx % K;
+        double acc = 0.0;
+        for (int m = 0; m < K; m++) acc += Vs[i * K + m] * ev[m] * Vi[m * K + j];
+        W[idx] = acc;
+      }
+      __syncthreads();
+      if (k == 0) {
+        for (int idx = tid; idx < KK; idx += nt) M[idx] = W[idx];
+      } else {
+        for (int idx = tid; idx < KK; idx += nt) {
+          int i = idx / K, j = idx % K;
+          double acc = 0.0;
+          for (int m = 0; m < K; m++) acc += M[i * K + m] * W[m * K + j];
+          Y[idx] = acc;
+        }
+        __syncthreads();
+        for (int idx = tid; idx < KK; idx += nt) M[idx] = Y[idx];
+      }
+      __syncthreads();
+    } else {
+      const double *Qs = Qn + (size_t)s * KK;
+      double mu = 0.0;
+      for (int i = 0; i < K; i++) mu = fmax(mu, fabs(Qs[i * K + i]));
+      if (mu == 0.0 || tau == 0.0) continue;
+      for (int idx = tid; idx < KK; idx += nt)
+        B[idx] = Qs[idx] / mu + ((idx / K == idx % K) ? 1.0 : 0.0);
+      const double mt = mu * tau;
+      const int npc = (int)ceil(mt / 30.0);
+      const double x = mt / npc;
+      const int mmax = (int)ceil(x + 12.0 * sqrt(x) + 30.0);
+      for (int piece = 0; piece < npc; piece++) {
+        double w = exp(-x);
+        __syncthreads();
+        for (int idx = tid; idx < KK; idx += nt) {
+          Y[idx] = M[idx];       // Y = M B^0
+          W[idx] = w * M[idx];   // accumulator
+        }
+        __syncthreads();
+        for (int m = 1; m <= mmax; m++) {
+          w = w * x / (double)m;
+          // Y <- Y B  (in place through M as scratch is unsafe: use ev-free temp)
+          for (int idx = tid; idx < KK; idx += nt) {
+            int i = idx / K, j = idx % K;
+            double acc = 0.0;
+            for (int q = 0; q < K; q++) acc += Y[i * K + q] * B[q * K + j];
+            M[idx] = acc;
+          }
+          __syncthreads();
+          for (int idx = tid; idx < KK; idx += nt) {
+            Y[idx] = M[idx];
+            W[idx] += w * M[idx];
+          }
+          __syncthreads();
+        }
+        for (int idx = tid; idx < KK; idx += nt) M[idx] = W[idx];
+        __syncthreads();
+      }
+    }
+  }
+  __syncthreads();
+  double *out = P64 + ((size_t)v * d.C + c) * KK;
+  for (int idx = tid; idx < KK; idx += nt) out[idx] = M[idx];
+  if (PT32) {
+    float *pt = PT32 + ((size_t)v * d.C + c) * d.NR * d.Kp;
+    for (int idx = tid; idx < d.NR * d.Kp; idx += nt) {
+      int row = idx / d.Kp, i = idx % d.Kp;
+      double val = 0.0;
+      if (i < K) {
+        if (row < K) {
+          val = M[i * K + row];
+        } else {
+          unsigned long long mk = (row == K) ? ~0ull : masks[row - K - 1];
+          for (int j = 0; j < K; j++)
+            if ((mk >> j) & 1ull) val += M[i * K + j];
+        }
+      }
+      pt[idx] = (float)val;
+    }
+  }
+}
+
+}  // namespace
+
+cudaError_t launch_segments(epoch_ctx *c) {
+  const Dims &d = c->d;
+  k_segments<<<ceil_div(d.nn, 128), 128, 0, c->stream>>>(
+      d, c->d_heights, c->d_parent, c->d_boundaries, c->d_phi, c->d_nseg, c->d_seg_mat,
+      c->d_seg_dt, c->d_seg_hi, c->d_seg_lo);
+  c->launches++;
+  return cudaGetLastError();
+}
+
+static size_t setup_smem(const Dims &d) {
+  return sizeof(double) * (2 * d.KK + d.K + 32 + 64) + sizeof(int) * 128;
+}
+
+cudaError_t launch_model_setup(epoch_ctx *c) {
+  const Dims &d = c->d;
+  size_t smem = setup_smem(d);
+  cudaFuncSetAttribute(k_model_setup, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+  k_model_setup<<<d.S, 256, smem, c->stream>>>(d, c->normalise, c->d_Qraw, c->d_pi, c->d_Q,
+                                               c->d_cnorm, c->d_lam, c->d_V, c->d_Vinv,
+                                               c->d_status);
+  c->launches++;
+  return cudaGetLastError();
+}
+
+cudaError_t launch_param_transform(epoch_ctx *c) {
+  const Dims &d = c->d;
+  if (d.np == 0 || !d.reversible) return cudaSuccess;
+  size_t smem = sizeof(double) * (2 * d.KK + 32);
+  cudaFuncSetAttribute(k_param_transform, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                       (int)smem);
+  dim3 grid(d.np, d.S);
+  k_param_transform<<<grid, 256, smem, c->stream>>>(d, c->normalise, c->d_dQraw, c->d_pi,
+                                                    c->d_Q, c->d_cnorm, c->d_V, c->d_Vinv,
+                                                    c->d_Dth, c->d_Dth32, c->d_Dnz);
+  c->launches++;
+  return cudaGetLastError();
+}
+
+cudaError_t launch_branch_matrices(epoch_ctx *c) {
+  const Dims &d = c->d;
+  size_t smem = sizeof(double) * (4 * d.KK + d.K);
+  cudaFuncSetAttribute(k_branch_matrices, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                       (int)smem);
+  int threads = d.KK >= 1024 ? 256 : (d.KK >= 256 ? 128 : 32);
+  dim3 grid(d.nn, d.C);
+  k_branch_matrices<<<grid, threads, smem, c->stream>>>(
+      d, c->d_nseg, c->d_seg_mat, c->d_seg_dt, c->d_brate, c->d_catr, c->d_lam, c->d_V,
+      c->d_Vinv, c->d_Q, c->d_masks, c->d_P64, c->precision == EPOCH_FP64 ? nullptr : c->d_PT32);
+  c->launches++;
+  return cudaGetLastError();
+}
+
+}  // namespace epoch

@@ -1,0 +1,342 @@
+// k_partials.cu -- post-order pruning (Eq. partial_likelihood) with
+// per-pattern power-of-two rescaling, and the root sum / weighted log-sum.
+//
+// Layout: partials of internal node u live at slot u-N as [C][P][Kp]; a
+// pattern's state vector is contiguous (Kp = 4 for K <= 4: one 16-byte
+// vector).  Tips are never expanded: a tip child contributes the row of the
+// transposed branch-matrix table selected by its code (FP32 paths) or the
+// column / masked row-sum of P (FP64 path).  After each internal node the
+// pattern's values over (category, state) are divided by 2^e, e the binary
+// exponent of their maximum, which is exact; e is kept per (node, pattern).
+#include <math.h>
+
+#include "epoch_internal.cuh"
+
+namespace epoch {
+namespace {
+
+// ---- generic kernels (any K; FP64 = the plain path, FP32 = SIMT path) -----
+
+template <typename T>
+struct BranchTable;
+
+// FP64: row-major P64[v][c][i][j].
+template <>
+struct BranchTable<double> {
+  const double *P;
+  const unsigned long long *masks;
+  __device__ double mat(const Dims &d, int v, int c, int i, int j) const {
+    return P[((size_t)v * d.C + c) * d.KK + i * d.K + j];
+  }
+  __device__ double tip(const Dims &d, int v, int c, int i, int code) const {
+    const double *row = P + ((size_t)v * d.C + c) * d.KK + i * d.K;
+    if (code < d.K) return row[code];
+    unsigned long long mk = (code == d.K) ? ~0ull : masks[code - d.K - 1];
+    double s = 0.0;
+    for (int j = 0; j < d.K; j++)
+      if ((mk >> j) & 1ull) s += row[j];
+    return s;
+  }
+};
+
+// FP32: transposed table PT32[v][c][row][Kp], row j < K = column j of P,
+// rows K.. = missing / mask sums.
+template <>
+struct BranchTable<float> {
+  const float *PT;
+  const unsigned long long *masks;
+  __device__ float mat(const Dims &d, int v, int c, int i, int j) const {
+    return PT[(((size_t)v * d.C + c) * d.NR + j) * d.Kp + i];
+  }
+  __device__ float tip(const Dims &d, int v, int c, int i, int code) const {
+    return PT[(((size_t)v * d.C + c) * d.NR + code) * d.Kp + i];
+  }
+};
+
+// S_x(c,p,i) = sum_j P_x[i][j] L_x(c,p,j) for child x (tip: from its code).
+template <typename T>
+__device__ __forceinline__ T child_factor(const Dims &d, const BranchTable<T> &bt,
+                                          const T *__restrict__ part,
+                                          const uint8_t *__restrict__ tips, int x, int c,
+                                          int p, int i) {
+  if (x < d.N) return bt.tip(d, x, c, i, tips[(size_t)x * d.P + p]);
+  const T *L = part + (((size_t)(x - d.N) * d.C + c) * d.P + p) * d.Kp;
+  T s = 0;
+  for (int j = 0; j < d.K; j++) s += bt.mat(d, x, c, i, j) * L[j];
+  return s;
+}
+
+// One thread per (category, pattern, state) of one node of the level.
+template <typename T>
+__global__ void k_partials_generic(Dims d, BranchTable<T> bt, const int *__restrict__ lvl_nodes,
+                                   int lvl_off, const int *__restrict__ child, T *part,
+                                   const uint8_t *__restrict__ tips) {
+  const int u = lvl_nodes[lvl_off + blockIdx.y];
+  const int slot = u - d.N;
+  const long long idx = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+  if (idx >= (long long)d.C * d.P * d.Kp) return;
+  const int i = (int)(idx % d.Kp);
+  const long long cp = idx / d.Kp;
+  const int p = (int)(cp % d.P), c = (int)(cp / d.P);
+  T out = 0;
+  if (i < d.K) {
+    const int v = child[2 * slot], w = child[2 * slot + 1];
+    out = child_factor<T>(d, bt, part, tips, v, c, p, i) *
+          child_factor<T>(d, bt, part, tips, w, c, p, i);
+  }
+  part[(((size_t)slot * d.C + c) * d.P + p) * d.Kp + i] = out;
+}
+
+__device__ __forceinline__ double scale_by(double x, int e) { return ldexp(x, -e); }
+__device__ __forceinline__ float scale_by(float x, int e) { return ldexpf(x, -e); }
+__device__ __forceinline__ int exp_of(double m) {
+  int e;
+  frexp(m, &e);
+  return e;
+}
+__device__ __forceinline__ int exp_of(float m) {
+  int e;
+  frexpf(m, &e);
+  return e;
+}
+
+// One thread per (node of the level, pattern): divide by 2^e of the max.
+template <typename T>
+__global__ void k_rescale_generic(Dims d, const int *__restrict__ lvl_nodes, int lvl_off, T *part,
+                                  int16_t *__restrict__ scale, int *__restrict__ status) {
+  const int u = lvl_nodes[lvl_off + blockIdx.y];
+  const int slot = u - d.N;
+  const int p = blockIdx.x * blockDim.x + threadIdx.x;
+  if (p >= d.P) return;
+  T m = 0;
+  for (int c = 0; c < d.C; c++) {
+    const T *L = part + (((size_t)slot * d.C + c) * d.P + p) * d.Kp;
+    for (int i = 0; i < d.K; i++) m = fmax(m, L[i]);
+  }
+  int e = 0;
+  if (!isfinite(m)) {
+    atomicOr(status, ST_NONFINITE);
+  } else if (m > 0) {
+    e = exp_of(m);
+    for (int c = 0; c < d.C; c++) {
+      T *L = part + (((size_t)slot * d.C + c) * d.P + p) * d.Kp;
+      for (int i = 0; i < d.K; i++) L[i] = scale_by(L[i], e);
+    }
+  }
+  scale[(size_t)slot * d.P + p] = (int16_t)e;
+}
+
+// ---- fused FP32 kernel for K = 4 -------------------------------------------
+// One thread per pattern, all categories; the 16-byte state vector of a
+// (category, pattern) is one float4 load; children's transposed tables are
+// staged in shared memory.  Pruning, rescaling and the exponent store are
+// fused.  HBM traffic per internal node and pattern: C*16 B per internal
+// child read, 1 B per tip child, C*16 B + 2 B written.
+template <int CMAX>
+__global__ void __launch_bounds__(kTile) k_partials_k4(Dims d, const float *__restrict__ PT32,
+                                                       const int *__restrict__ lvl_nodes,
+                                                       int lvl_off, const int *__restrict__ child,
+                                                       float4 *part, int16_t *__restrict__ scale,
+                                                       const uint8_t *__restrict__ tips,
+                                                       int *__restrict__ status) {
+  extern __shared__ float4 spt[];  // [2][C][NR]
+  const int u = lvl_nodes[lvl_off + blockIdx.y];
+  const int slot = u - d.N;
+  const int ch0 = child[2 * slot], ch1 = child[2 * slot + 1];
+  const int CN = d.C * d.NR;
+  const float4 *pt4 = reinterpret_cast<const float4 *>(PT32);
+  for (int idx = threadIdx.x; idx < 2 * CN; idx += blockDim.x) {
+    const int x = idx / CN, r = idx - x * CN;
+    spt[idx] = pt4[(size_t)(x ? ch1 : ch0) * CN + r];
+  }
+  __syncthreads();
+  const int p = blockIdx.x * blockDim.x + threadIdx.x;
+  if (p >= d.P) return;
+  float4 acc[CMAX];
+#pragma unroll
+  for (int c = 0; c < CMAX; c++) acc[c] = make_float4(1.f, 1.f, 1.f, 1.f);
+#pragma unroll
+  for (int x = 0; x < 2; x++) {
+    const int node = x ? ch1 : ch0;
+    const float4 *tab = spt + x * CN;
+    if (node < d.N) {
+      const int code = tips[(size_t)node * d.P + p];
+#pragma unroll
+      for (int c = 0; c < CMAX; c++) {
+        if (c < d.C) {
+          const float4 s = tab[c * d.NR + code];
+          acc[c].x *= s.x; acc[c].y *= s.y; acc[c].z *= s.z; acc[c].w *= s.w;
+        }
+      }
+    } else {
+      const float4 *L = part + (size_t)(node - d.N) * d.C * d.P + p;
+      float4 l[CMAX];
+#pragma unroll
+      for (int c = 0; c < CMAX; c++)
+        if (c < d.C) l[c] = __ldcs(L + (size_t)c * d.P);
+#pragma unroll
+      for (int c = 0; c < CMAX; c++) {
+        if (c < d.C) {
+          const float4 *t = tab + c * d.NR;
+          const float4 r0 = t[0], r1 = t[1], r2 = t[2], r3 = t[3];
+          float4 s;
+          s.x = l[c].x * r0.x + l[c].y * r1.x + l[c].z * r2.x + l[c].w * r3.x;
+          s.y = l[c].x * r0.y + l[c].y * r1.y + l[c].z * r2.y + l[c].w * r3.y;
+          s.z = l[c].x * r0.z + l[c].y * r1.z + l[c].z * r2.z + l[c].w * r3.z;
+          s.w = l[c].x * r0.w + l[c].y * r1.w + l[c].z * r2.w + l[c].w * r3.w;
+          acc[c].x *= s.x; acc[c].y *= s.y; acc[c].z *= s.z; acc[c].w *= s.w;
+        }
+      }
+    }
+  }
+  float m = 0.f;
+#pragma unroll
+  for (int c = 0; c < CMAX; c++)
+    if (c < d.C) m = fmaxf(m, fmaxf(fmaxf(acc[c].x, acc[c].y), fmaxf(acc[c].z, acc[c].w)));
+  int e = 0;
+  if (!isfinite(m)) {
+    atomicOr(status, ST_NONFINITE);
+  } else if (m > 0.f) {
+    frexpf(m, &e);
+  }
+  float4 *out = part + (size_t)slot * d.C * d.P + p;
+#pragma unroll
+  for (int c = 0; c < CMAX; c++) {
+    if (c < d.C) {
+      float4 a = acc[c];
+      a.x = ldexpf(a.x, -e); a.y = ldexpf(a.y, -e); a.z = ldexpf(a.z, -e); a.w = ldexpf(a.w, -e);
+      out[(size_t)c * d.P] = a;
+    }
+  }
+  scale[(size_t)slot * d.P + p] = (int16_t)e;
+}
+
+// ---- root: per-pattern site likelihood and the weighted log-sum ----------
+// site_p = sum_c w_c sum_i pi_i L_root(c,p,i) (scaled), lnL_p = log site_p +
+// ln2 * sum_u e_u(p); the block sums of n_p lnL_p are reduced in a fixed
+// order by k_lnl_final (deterministic).
+template <typename T>
+__global__ void k_root(Dims d, int root_slot, const T *__restrict__ part,
+                       const int16_t *__restrict__ scale, const double *__restrict__ pi,
+                       const double *__restrict__ catw, const double *__restrict__ pw,
+                       double *__restrict__ site_lnl, double *__restrict__ site_inv,
+                       double *__restrict__ lnl_part) {
+  __shared__ double red[32];
+  const int p = blockIdx.x * blockDim.x + threadIdx.x;
+  double contrib = 0.0;
+  if (p < d.P) {
+    double site = 0.0;
+    for (int c = 0; c < d.C; c++) {
+      const T *L = part + (((size_t)root_slot * d.C + c) * d.P + p) * d.Kp;
+      double sc = 0.0;
+      for (int i = 0; i < d.K; i++) sc += pi[i] * (double)L[i];
+      site += catw[c] * sc;
+    }
+    int esum = 0;
+    for (int s = 0; s < d.N - 1; s++) esum += scale[(size_t)s * d.P + p];
+    const double lp = log(site) + 0.69314718055994530942 * (double)esum;
+    site_lnl[p] = lp;
+    site_inv[p] = site > 0.0 ? 1.0 / site : 0.0;
+    const double n = pw[p];
+    contrib = (n != 0.0) ? n * lp : 0.0;
+  }
+  for (int o = 16; o > 0; o >>= 1) contrib += __shfl_xor_sync(0xffffffffu, contrib, o);
+  const int w = threadIdx.x >> 5, l = threadIdx.x & 31;
+  if (l == 0) red[w] = contrib;
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    double t = 0.0;
+    for (int i = 0; i < (int)(blockDim.x >> 5); i++) t += red[i];
+    lnl_part[blockIdx.x] = t;
+  }
+}
+
+__global__ void k_lnl_final(int n, const double *__restrict__ part, double *__restrict__ out) {
+  __shared__ double red[32];
+  double t = 0.0;
+  for (int i = threadIdx.x; i < n; i += blockDim.x) t += part[i];
+  for (int o = 16; o > 0; o >>= 1) t += __shfl_xor_sync(0xffffffffu, t, o);
+  const int w = threadIdx.x >> 5, l = threadIdx.x & 31;
+  if (l == 0) red[w] = t;
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    double s = 0.0;
+    for (int i = 0; i < (int)(blockDim.x >> 5); i++) s += red[i];
+    out[0] = s;
+  }
+}
+
+template <int CMAX>
+cudaError_t launch_k4_levels(epoch_ctx *c) {
+  const Dims &d = c->d;
+  const size_t smem = sizeof(float4) * 2 * d.C * d.NR;
+  if (smem > 48 * 1024)
+    cudaFuncSetAttribute(k_partials_k4<CMAX>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                         (int)smem);
+  const int L = (int)c->h_level_off.size() - 1;
+  for (int l = 0; l < L; l++) {
+    const int w = c->h_level_off[l + 1] - c->h_level_off[l];
+    dim3 grid(ceil_div(d.P, kTile), w);
+    k_partials_k4<CMAX><<<grid, kTile, smem, c->stream>>>(
+        d, c->d_PT32, c->d_level_nodes, c->h_level_off[l], c->d_child,
+        reinterpret_cast<float4 *>(c->d_part), c->d_scale, c->d_tips, c->d_status);
+    c->launches++;
+  }
+  return cudaGetLastError();
+}
+
+template <typename T>
+cudaError_t launch_generic_levels(epoch_ctx *c, BranchTable<T> bt) {
+  const Dims &d = c->d;
+  const int L = (int)c->h_level_off.size() - 1;
+  const long long items = (long long)d.C * d.P * d.Kp;
+  for (int l = 0; l < L; l++) {
+    const int w = c->h_level_off[l + 1] - c->h_level_off[l];
+    dim3 g1(ceil_div(items, 256), w);
+    k_partials_generic<T><<<g1, 256, 0, c->stream>>>(d, bt, c->d_level_nodes, c->h_level_off[l],
+                                                     c->d_child, (T *)c->d_part, c->d_tips);
+    dim3 g2(ceil_div(d.P, 256), w);
+    k_rescale_generic<T><<<g2, 256, 0, c->stream>>>(d, c->d_level_nodes, c->h_level_off[l],
+                                                    (T *)c->d_part, c->d_scale, c->d_status);
+    c->launches += 2;
+  }
+  return cudaGetLastError();
+}
+
+}  // namespace
+
+cudaError_t launch_partials(epoch_ctx *c) {
+  const Dims &d = c->d;
+  if (c->precision == EPOCH_FP64) {
+    BranchTable<double> bt{c->d_P64, c->d_masks};
+    return launch_generic_levels<double>(c, bt);
+  }
+  if (d.K == 4) {
+    if (d.C <= 4) return launch_k4_levels<4>(c);
+    if (d.C <= 8) return launch_k4_levels<8>(c);
+    return launch_k4_levels<16>(c);
+  }
+  BranchTable<float> bt{c->d_PT32, c->d_masks};
+  return launch_generic_levels<float>(c, bt);
+}
+
+cudaError_t launch_root(epoch_ctx *c) {
+  const Dims &d = c->d;
+  int root_slot = -1;
+  for (int v = 0; v < d.nn; v++)
+    if (c->h_parent[v] < 0) root_slot = v - d.N;
+  const int nb = ceil_div(d.P, kTile);
+  if (c->precision == EPOCH_FP64)
+    k_root<double><<<nb, kTile, 0, c->stream>>>(d, root_slot, (const double *)c->d_part,
+                                                c->d_scale, c->d_pi, c->d_catw, c->d_pw,
+                                                c->d_site_lnl, c->d_site_inv, c->d_lnl_part);
+  else
+    k_root<float><<<nb, kTile, 0, c->stream>>>(d, root_slot, (const float *)c->d_part,
+                                               c->d_scale, c->d_pi, c->d_catw, c->d_pw,
+                                               c->d_site_lnl, c->d_site_inv, c->d_lnl_part);
+  k_lnl_final<<<1, 256, 0, c->stream>>>(nb, c->d_lnl_part, c->d_lnl);
+  c->launches += 2;
+  return cudaGetLastError();
+}
+
+}  // namespace epoch

@@ -1,0 +1,123 @@
+"""Parity at the full workload sizes (the launch configuration bench.py
+times): the nucleotide GTR case (500 taxa, 10,000 patterns, 4 categories, 3
+epochs) against the oracle outright; the codon GY94 case (128 taxa, 5,000
+codon sites, 4 categories, 4 epochs) on a sample of per-pattern values the
+oracle computes in seconds, and its gradient against central finite
+differences of the FP64 GPU likelihood."""
+import numpy as np
+import pytest
+
+import oracle
+import synth
+from paper_1309_3075_b300 import binding
+from paper_1309_3075_b300.binding import EPOCH_FP32, EPOCH_FP64, EpochLikelihood
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module", autouse=True)
+def _built():
+    from paper_1309_3075_b300 import build
+
+    build.build()
+
+
+@pytest.fixture(scope="module")
+def gtr_full():
+    return synth.config2()
+
+
+@pytest.fixture(scope="module")
+def gy94_full():
+    return synth.config3()
+
+
+def maxrel(g, ref):
+    return np.abs(np.asarray(g) - np.asarray(ref)).max() / max(np.abs(ref).max(), 1e-300)
+
+
+@pytest.mark.parametrize("prec,tol", [(EPOCH_FP64, 1e-10), (EPOCH_FP32, 1e-5)])
+def test_gtr_full_size_lnl_and_gradient(gtr_full, prec, tol):
+    w = gtr_full
+    lik = EpochLikelihood(w, precision=prec)
+    try:
+        lnl, g = lik.evaluate(with_gradient=True)
+    finally:
+        lik.close()
+    ref = oracle.gradient(w)
+    assert abs(lnl - ref["lnL"]) <= tol * abs(ref["lnL"])
+    gtol = 1e-9 if prec == EPOCH_FP64 else 1e-4
+    assert maxrel(g["heights"], ref["heights"]) <= gtol
+    assert maxrel(g["boundaries"], ref["boundaries"]) <= gtol
+    assert maxrel(g["params"], ref["params"]) <= gtol
+    assert maxrel(g["branch_rates"], ref["branch_rates"]) <= gtol
+
+
+@pytest.mark.parametrize("prec,tol", [(EPOCH_FP64, 1e-10), (EPOCH_FP32, 1e-5)])
+def test_gy94_full_size_sampled_sites(gy94_full, prec, tol):
+    w = gy94_full
+    lik = EpochLikelihood(w, precision=prec)
+    try:
+        lnl = lik.log_likelihood()
+        site = lik.site_log_likelihoods()
+    finally:
+        lik.close()
+    # lnL is the weighted sum of the per-pattern values
+    assert abs(lnl - (w.pattern_weights * site).sum()) <= 1e-12 * abs(lnl)
+    idx = np.random.default_rng(7).choice(w.n_patterns, size=160, replace=False)
+    idx.sort()
+    sub = w.replace(tips=np.ascontiguousarray(w.tips[:, idx]),
+                    pattern_weights=w.pattern_weights[idx])
+    _, rsite = oracle.log_likelihood(sub)
+    assert np.abs(site[idx] - rsite).max() <= tol * np.abs(rsite).max() * 10
+
+
+def test_gy94_full_size_gradient_vs_finite_differences(gy94_full):
+    """Config: d lnL / d (node heights, boundaries, kappa, omega_k) by the
+    adjoint kernels, against central differences (h = 1e-6) of the FP64 GPU
+    lnL, on a sample of coordinates; the FP32 path's gradient against the
+    FP64 one."""
+    w = gy94_full
+    lik = EpochLikelihood(w, precision=EPOCH_FP64)
+    lik32 = EpochLikelihood(w, precision=EPOCH_FP32)
+    try:
+        lnl, g = lik.evaluate(with_gradient=True)
+        _, g32 = lik32.evaluate(with_gradient=True)
+
+        def lnl_at(heights=None, bounds=None, Q=None):
+            if Q is not None:
+                binding.epoch_set_rate_matrices(lik.ctx, Q, w.pi)
+            if bounds is not None:
+                binding.epoch_set_boundaries(lik.ctx, bounds)
+            if heights is not None:
+                binding.epoch_set_heights(lik.ctx, heights)
+            val = lik.evaluate(with_gradient=False)[0]
+            binding.epoch_set_rate_matrices(lik.ctx, w.Q, w.pi)
+            binding.epoch_set_boundaries(lik.ctx, w.boundaries)
+            binding.epoch_set_heights(lik.ctx, w.heights)
+            return val
+
+        h = 1e-6
+        rng = np.random.default_rng(3)
+        nodes = rng.choice(np.arange(w.n_taxa, 2 * w.n_taxa - 2), size=4, replace=False)
+        for u in nodes:
+            hp, hm = w.heights.copy(), w.heights.copy()
+            hp[u] += h
+            hm[u] -= h
+            fd = (lnl_at(heights=hp) - lnl_at(heights=hm)) / (2 * h)
+            assert abs(g["heights"][u] - fd) <= 1e-4 * max(1.0, abs(fd)), (u, g["heights"][u], fd)
+        for j in range(w.n_epochs - 1):
+            bp, bm = w.boundaries.copy(), w.boundaries.copy()
+            bp[j] += h
+            bm[j] -= h
+            fd = (lnl_at(bounds=bp) - lnl_at(bounds=bm)) / (2 * h)
+            assert abs(g["boundaries"][j] - fd) <= 1e-4 * max(1.0, abs(fd)), (j, g["boundaries"][j], fd)
+        for a in range(w.n_params):
+            fd = (lnl_at(Q=w.Q + h * w.dQ[a]) - lnl_at(Q=w.Q - h * w.dQ[a])) / (2 * h)
+            assert abs(g["params"][a] - fd) <= 1e-4 * max(1.0, abs(fd)), (w.param_names[a], g["params"][a], fd)
+        for k in ("heights", "boundaries", "params"):
+            assert maxrel(g32[k], g[k]) <= 1e-4, k
+        assert abs(lnl - lik32.evaluate(with_gradient=False)[0]) <= 1e-5 * abs(lnl)
+    finally:
+        lik.close()
+        lik32.close()

@@ -1,0 +1,281 @@
+"""GPU parity: libepoch (through the C ABI) against the FP64 CPU oracle on the
+same seeded inputs.
+
+Tolerances (the benchmark spec): lnL relative error <= 1e-10 on the FP64
+path and <= 1e-5 on the FP32 paths.  Branch matrices on every path are FP64
+and must match to 1e-12.  Gradients: FP64 path within 1e-9 of the oracle's
+(max-norm relative); FP32 paths within 1e-4 (max-norm relative), the FD
+bound the benchmark spec states for the gradient.
+"""
+import numpy as np
+import pytest
+
+import oracle
+import synth
+from paper_1309_3075_b300 import binding
+from paper_1309_3075_b300.binding import EPOCH_FP32, EPOCH_FP64, EpochError, EpochLikelihood
+
+pytestmark = pytest.mark.gpu
+
+LNL_TOL = {EPOCH_FP64: 1e-10, EPOCH_FP32: 1e-5}
+GRAD_TOL = {EPOCH_FP64: 1e-9, EPOCH_FP32: 1e-4}
+
+
+@pytest.fixture(scope="module", autouse=True)
+def _built():
+    from paper_1309_3075_b300 import build
+
+    build.build()
+
+
+def rel(a, b):
+    return abs(a - b) / max(abs(b), 1e-300)
+
+
+def vec_close(g, ref, tol):
+    scale = max(np.abs(ref).max() if ref.size else 0.0, 1e-12)
+    return np.abs(np.asarray(g) - np.asarray(ref)).max() <= tol * scale
+
+
+def check_lnl(w, prec, site_sample=None):
+    lik = EpochLikelihood(w, precision=prec)
+    try:
+        lnl = lik.log_likelihood()
+        site = lik.site_log_likelihoods()
+    finally:
+        lik.close()
+    ref, rsite = oracle.log_likelihood(w)
+    assert rel(lnl, ref) <= LNL_TOL[prec], (w.name, prec, lnl, ref, rel(lnl, ref))
+    tol = LNL_TOL[prec] * 10
+    assert np.allclose(site, rsite, rtol=tol, atol=tol * np.abs(rsite).max())
+    return lnl
+
+
+def check_grad(w, prec):
+    lik = EpochLikelihood(w, precision=prec)
+    try:
+        lik.log_likelihood()
+        g = lik.gradient()
+    finally:
+        lik.close()
+    ref = oracle.gradient(w)
+    tol = GRAD_TOL[prec]
+    nn = 2 * w.n_taxa - 1
+    assert vec_close(g["heights"], ref["heights"], tol), ("heights", np.abs(g["heights"] - ref["heights"]).max())
+    if w.n_epochs > 1:
+        assert vec_close(g["boundaries"], ref["boundaries"], tol), (g["boundaries"], ref["boundaries"])
+    assert vec_close(g["branch_rates"][: nn], ref["branch_rates"], tol)
+    if w.n_params and w.reversible:
+        assert vec_close(g["params"], ref["params"], tol), (g["params"], ref["params"])
+    return g, ref
+
+
+# ---------------------------------------------------------------------------
+# likelihood
+# ---------------------------------------------------------------------------
+
+
+@pytest.mark.parametrize("prec", [EPOCH_FP64, EPOCH_FP32])
+def test_config1_hky_two_epochs(prec):
+    w = synth.config1()
+    check_lnl(w, prec)
+    check_grad(w, prec)
+
+
+@pytest.mark.parametrize("prec", [EPOCH_FP64, EPOCH_FP32])
+@pytest.mark.parametrize("dated", [False, True])
+def test_nucleotide_several_tiles_ragged(prec, dated):
+    # 700 patterns = two full 256-pattern tiles and a ragged tail
+    w = synth.small_nucleotide(201, n_taxa=40, n_sites=700, n_cat=4, n_epochs=3, dated=dated)
+    check_lnl(w, prec)
+    check_grad(w, prec)
+
+
+@pytest.mark.parametrize("prec", [EPOCH_FP64, EPOCH_FP32])
+def test_branch_matrices_match_oracle(prec):
+    w = synth.small_nucleotide(202, n_taxa=25, n_sites=50, n_cat=3, n_epochs=4, dated=True)
+    lik = EpochLikelihood(w, precision=prec)
+    try:
+        lik.log_likelihood()
+        for v in range(2 * w.n_taxa - 2):
+            for c in range(w.n_categories):
+                P = lik.branch_matrix(v, c)
+                assert np.allclose(P, oracle.branch_matrix(w, v, c), rtol=0, atol=1e-12)
+    finally:
+        lik.close()
+
+
+@pytest.mark.parametrize("prec", [EPOCH_FP64, EPOCH_FP32])
+def test_codon_small(prec):
+    w = synth.small_codon(203, n_taxa=10, n_sites=120, n_cat=2, n_epochs=3)
+    check_lnl(w, prec)
+    check_grad(w, prec)
+
+
+@pytest.mark.parametrize("prec", [EPOCH_FP64, EPOCH_FP32])
+@pytest.mark.parametrize("K", [2, 3, 7, 20])
+def test_other_state_counts(prec, K):
+    w = synth.tiny_tree_workload(300 + K, K=K, n_taxa=9, n_sites=300, n_epochs=3, n_cat=2,
+                                 missing_frac=0.05)
+    check_lnl(w, prec)
+    check_grad(w, prec)
+
+
+@pytest.mark.parametrize("prec", [EPOCH_FP64, EPOCH_FP32])
+def test_asymmetric_uniformisation(prec):
+    w = synth.tiny_tree_workload(310, K=12, n_taxa=8, n_sites=40, n_epochs=3, n_cat=1,
+                                 reversible=False)
+    check_lnl(w, prec)
+    check_grad(w, prec)
+
+
+@pytest.mark.parametrize("prec", [EPOCH_FP64, EPOCH_FP32])
+def test_categories_and_single_epoch(prec):
+    w = synth.small_nucleotide(204, n_taxa=30, n_sites=300, n_cat=8, n_epochs=1)
+    check_lnl(w, prec)
+    check_grad(w, prec)
+    w1 = synth.small_nucleotide(205, n_taxa=30, n_sites=1, n_cat=1, n_epochs=2)
+    check_lnl(w1, prec)
+
+
+@pytest.mark.parametrize("prec", [EPOCH_FP64, EPOCH_FP32])
+def test_shared_processes_phi(prec):
+    """Alternating epochs sharing two processes (the paper's seasonal design)."""
+    base = synth.small_nucleotide(206, n_taxa=30, n_sites=200, n_cat=2, n_epochs=5)
+    phi = np.array([0, 1, 0, 1, 0], np.int32)
+    w = base.replace(Q=base.Q[:2].copy(), epoch_to_matrix=phi,
+                     dQ=np.ascontiguousarray(base.dQ[:12, :2]))
+    check_lnl(w, prec)
+    check_grad(w, prec)
+
+
+# ---------------------------------------------------------------------------
+# edge cases
+# ---------------------------------------------------------------------------
+
+
+@pytest.mark.parametrize("prec", [EPOCH_FP64, EPOCH_FP32])
+def test_zero_length_branch_and_node_on_boundary(prec):
+    w = synth.small_nucleotide(207, n_taxa=12, n_sites=80, n_cat=2, n_epochs=3, dated=True)
+    h = w.heights.copy()
+    p = w.parent
+    # a tip at the height of its parent (zero-length branch)
+    t = 0
+    h[t] = h[p[t]]
+    # an internal node exactly on the first boundary
+    u = next(v for v in range(w.n_taxa, 2 * w.n_taxa - 2)
+             if h[p[v]] > w.boundaries[0] and max(h[c] for c in np.where(p == v)[0]) < w.boundaries[0])
+    h[u] = w.boundaries[0]
+    w2 = w.replace(heights=h)
+    check_lnl(w2, prec)
+    check_grad(w2, prec)
+
+
+@pytest.mark.parametrize("prec", [EPOCH_FP64, EPOCH_FP32])
+def test_missing_and_ambiguous_tips(prec):
+    w = synth.small_nucleotide(208, n_taxa=15, n_sites=260, n_cat=2, n_epochs=2)
+    rng = np.random.default_rng(0)
+    tips = w.tips.copy()
+    tips[rng.random(tips.shape) < 0.1] = 4                # missing
+    masks = np.array([0b0101, 0b1010, 0b0011], np.uint64)  # purine, pyrimidine, AC
+    sel = rng.random(tips.shape) < 0.1
+    tips[sel] = 5 + rng.integers(0, 3, size=sel.sum())
+    tips[3] = 4                                           # one tip entirely missing
+    w2 = w.replace(tips=tips, masks=masks)
+    check_lnl(w2, prec)
+    check_grad(w2, prec)
+
+
+@pytest.mark.parametrize("prec", [EPOCH_FP64, EPOCH_FP32])
+def test_underflow_needs_scaling(prec):
+    w = synth.small_nucleotide(209, n_taxa=600, n_sites=300, n_cat=2, n_epochs=3)
+    rnd = np.random.default_rng(1).integers(0, 4, size=w.tips.shape).astype(np.int32)
+    w = w.replace(tips=rnd, heights=w.heights * 40, boundaries=w.boundaries * 40)
+    lnl = check_lnl(w, prec)
+    assert lnl / w.pattern_weights.sum() < -709  # far below the FP64 range per site
+
+
+# ---------------------------------------------------------------------------
+# API behaviour on the device
+# ---------------------------------------------------------------------------
+
+
+def test_graph_replay_matches_direct_calls():
+    w = synth.small_nucleotide(210, n_taxa=50, n_sites=600, n_cat=4, n_epochs=3)
+    for prec in (EPOCH_FP64, EPOCH_FP32):
+        lik = EpochLikelihood(w, precision=prec)
+        try:
+            lnl = lik.log_likelihood()
+            g = lik.gradient()
+            for _ in range(3):
+                lnl2, g2 = lik.evaluate(with_gradient=True)
+                assert lnl2 == lnl
+                assert np.array_equal(g2["heights"], g["heights"])
+                assert np.array_equal(g2["params"], g["params"])
+            lnl3, _ = lik.evaluate(with_gradient=False)
+            assert lnl3 == lnl
+            launches, captures = lik.counters()
+            assert launches > 0 and captures == 2
+            # new heights, same topology: the captured graph is reused
+            h = w.heights * 1.1
+            binding.epoch_set_heights(lik.ctx, h)
+            lnl4, _ = lik.evaluate(with_gradient=True)
+            assert lik.counters()[1] == 2
+            assert rel(lnl4, oracle.log_likelihood(w.replace(heights=h, boundaries=w.boundaries))[0]) \
+                <= LNL_TOL[prec]
+        finally:
+            lik.close()
+
+
+def test_errors_are_status_codes():
+    w = synth.small_nucleotide(211, n_taxa=10, n_sites=20, n_cat=2, n_epochs=2)
+    ctx = binding.epoch_create(4, 2, w.boundaries, None, 2, 10, 20, 2, EPOCH_FP32)
+    try:
+        with pytest.raises(EpochError) as e:
+            binding.epoch_update_partials(ctx)
+        assert e.value.status == 2  # out of order
+        bad = w.Q.copy()
+        bad[0, 0, 1] = -0.1
+        with pytest.raises(EpochError) as e:
+            binding.epoch_set_rate_matrices(ctx, bad, w.pi)
+        assert e.value.status == 4
+        asym = w.Q.copy()
+        asym[0, 0, 1] += 0.3
+        asym[0, 0, 0] -= 0.3
+        with pytest.raises(EpochError) as e:
+            binding.epoch_set_rate_matrices(ctx, asym, w.pi, 1, 1)
+        assert e.value.status == 4  # claims reversibility it does not have
+        with pytest.raises(EpochError) as e:
+            binding.epoch_set_tree(ctx, *synth.coalescent_tree(11, np.random.default_rng(0)))
+        assert e.value.status == 3  # more taxa than max_taxa
+        binding.epoch_set_tree(ctx, w.heights, w.parent)
+        tips = w.tips.copy()
+        tips[0, 0] = 9
+        with pytest.raises(EpochError) as e:
+            binding.epoch_set_tip_data(ctx, tips, w.pattern_weights)
+        assert e.value.status == 1
+    finally:
+        binding.epoch_destroy(ctx)
+
+
+def test_impossible_pattern_gives_minus_infinity():
+    """Two identical-height tips with different states on a zero-length
+    cherry have probability 0: lnL = -inf is a result, not an error."""
+    w = synth.small_nucleotide(212, n_taxa=6, n_sites=5, n_cat=1, n_epochs=2)
+    h = w.heights.copy()
+    p = w.parent
+    u = next(x for x in range(w.n_taxa, 2 * w.n_taxa - 1)
+             if (np.where(p == x)[0] < w.n_taxa).all())   # a cherry: both children tips
+    kids = np.where(p == u)[0]
+    h[kids] = h[u]
+    tips = w.tips.copy()
+    tips[kids[0], 0], tips[kids[1], 0] = 0, 1
+    w2 = w.replace(heights=h, tips=tips)
+    for prec in (EPOCH_FP64, EPOCH_FP32):
+        lik = EpochLikelihood(w2, precision=prec)
+        try:
+            assert lik.log_likelihood() == -np.inf
+            site = lik.site_log_likelihoods()
+            assert site[0] == -np.inf and np.isfinite(site[1:]).all()
+        finally:
+            lik.close()
