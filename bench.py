@@ -79,10 +79,14 @@ class ClockSampler:
         try:
             self.proc = subprocess.Popen(
                 ["nvidia-smi", "-i", str(self.index), f"--query-gpu={self.Q}",
-                 "--format=csv,noheader,nounits", "-lms", "100"],
+                 "--format=csv,noheader,nounits", "-lms", "50"],
                 stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
             self.thread = threading.Thread(target=self._read, daemon=True)
             self.thread.start()
+            t0 = time.time()
+            while not self.lines and time.time() - t0 < 3.0:  # sampler running before timing
+                time.sleep(0.02)
+            self.lines.clear()
         except Exception:
             self.proc = None
 
@@ -149,12 +153,12 @@ def run_ours(args, w, cfg, rank, world):
     nn = 2 * w.n_taxa - 1
 
     # ---- device-resident timing: K graph replays --------------------------
+    clocks = ClockSampler(dev)
+    clocks.start()
     for _ in range(args.warmup):
         binding.epoch_evaluate_async(lik.ctx, True)
     torch.cuda.synchronize()
     l0, _ = lik.counters()
-    clocks = ClockSampler(dev)
-    clocks.start()
     if world > 1:
         torch.distributed.barrier()
     torch.cuda.synchronize()
@@ -292,7 +296,7 @@ def oracle_sample_rate(w, budget_s):
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
-    ap.add_argument("--steps", type=int, default=50)
+    ap.add_argument("--steps", type=int, default=500)
     ap.add_argument("--warmup", type=int, default=5)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--workload", default="gtr", choices=["gtr", "gy94"])

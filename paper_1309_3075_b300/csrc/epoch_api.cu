@@ -310,7 +310,8 @@ void epoch_destroy(epoch_ctx *c) {
                   c->d_seg_lo,     c->d_P64,     c->d_PT32,     c->d_part,       c->d_pre,
                   c->d_xbuf,       c->d_scale,   c->d_tips,     c->d_pw,         c->d_site_lnl,
                   c->d_site_inv,   c->d_lnl_part, c->d_lnl,     c->d_Gpart,      c->d_G,
-                  c->d_gseg,       c->d_grad,    c->d_status};
+                  c->d_gseg,       c->d_grad,    c->d_status,   c->d_flags,      c->d_ctl,
+                  c->d_site_log};
   for (void *p : bufs) dfree(p);
   if (c->h_grad_pinned) cudaFreeHost(c->h_grad_pinned);
   if (c->h_lnl_pinned) cudaFreeHost(c->h_lnl_pinned);
@@ -424,6 +425,9 @@ epoch_status epoch_create(epoch_ctx **out, int states, int n_epochs, const doubl
   A(cudaMalloc(&c->d_Gpart, (size_t)ni_max * nchunk * 2 * C * KK * es));
   A(dalloc(&c->d_G, (size_t)nn_max * C * KK));
   A(dalloc(&c->d_status, 1));
+  A(dalloc(&c->d_flags, (size_t)ni_max * nchunk));
+  A(dalloc(&c->d_ctl, 8));
+  A(dalloc(&c->d_site_log, P));
   A(cudaMallocHost((void **)&c->h_lnl_pinned, sizeof(double)));
   A(cudaMallocHost((void **)&c->h_status_pinned, sizeof(int)));
   A(cudaMallocHost((void **)&c->h_tips_staging, (size_t)max_taxa * P));

@@ -162,174 +162,6 @@ __global__ void k_G_part(Dims d, const int *__restrict__ lvl_nodes, int lvl_off,
   }
 }
 
-// ---- fused FP32 pre-order for K = 4 -----------------------------------------
-// Reduce 32 per-lane values to one per lane (lane l ends with the warp sum of
-// value l) in 31 shuffles.
-__device__ __forceinline__ float reduce_scatter32(float (&v)[32]) {
-  const int lane = threadIdx.x & 31;
-#pragma unroll
-  for (int k = 0; k < 16; k++) {
-    const bool up = lane & 16;
-    const float send = up ? v[k] : v[k + 16];
-    const float keep = up ? v[k + 16] : v[k];
-    v[k] = keep + __shfl_xor_sync(0xffffffffu, send, 16);
-  }
-#pragma unroll
-  for (int k = 0; k < 8; k++) {
-    const bool up = lane & 8;
-    const float send = up ? v[k] : v[k + 8];
-    const float keep = up ? v[k + 8] : v[k];
-    v[k] = keep + __shfl_xor_sync(0xffffffffu, send, 8);
-  }
-#pragma unroll
-  for (int k = 0; k < 4; k++) {
-    const bool up = lane & 4;
-    const float send = up ? v[k] : v[k + 4];
-    const float keep = up ? v[k + 4] : v[k];
-    v[k] = keep + __shfl_xor_sync(0xffffffffu, send, 4);
-  }
-#pragma unroll
-  for (int k = 0; k < 2; k++) {
-    const bool up = lane & 2;
-    const float send = up ? v[k] : v[k + 2];
-    const float keep = up ? v[k + 2] : v[k];
-    v[k] = keep + __shfl_xor_sync(0xffffffffu, send, 2);
-  }
-  {
-    const bool up = lane & 1;
-    const float send = up ? v[0] : v[1];
-    const float keep = up ? v[1] : v[0];
-    v[0] = keep + __shfl_xor_sync(0xffffffffu, send, 1);
-  }
-  return v[0];
-}
-
-__device__ __forceinline__ float4 matvec_t(const float4 *t, float4 l) {
-  // S = sum_j l_j * row_j  (rows of the transposed table)
-  float4 s;
-  s.x = l.x * t[0].x + l.y * t[1].x + l.z * t[2].x + l.w * t[3].x;
-  s.y = l.x * t[0].y + l.y * t[1].y + l.z * t[2].y + l.w * t[3].y;
-  s.z = l.x * t[0].z + l.y * t[1].z + l.z * t[2].z + l.w * t[3].z;
-  s.w = l.x * t[0].w + l.y * t[1].w + l.z * t[2].w + l.w * t[3].w;
-  return s;
-}
-__device__ __forceinline__ float dot4(float4 a, float4 b) {
-  return a.x * b.x + a.y * b.y + a.z * b.z + a.w * b.w;
-}
-__device__ __forceinline__ float4 mul4(float4 a, float4 b) {
-  return make_float4(a.x * b.x, a.y * b.y, a.z * b.z, a.w * b.w);
-}
-__device__ __forceinline__ float4 ldexp4(float4 a, int e) {
-  return make_float4(ldexpf(a.x, -e), ldexpf(a.y, -e), ldexpf(a.z, -e), ldexpf(a.w, -e));
-}
-
-// One thread per pattern of one node u; per category: recompute S_v, S_w,
-// form X_v, X_w, store U_v, U_w (internal children) and accumulate the
-// weighted outer products into per-CTA sums of G (deterministic: fixed
-// shuffle and warp order).  Gpart[slot][blk][child][c][16].
-template <int CMAX>
-__global__ void __launch_bounds__(kTile) k_pre_k4(Dims d, const float *__restrict__ PT32,
-                                                  const int *__restrict__ lvl_nodes, int lvl_off,
-                                                  const int *__restrict__ child, int root,
-                                                  const float4 *__restrict__ part, float4 *pre,
-                                                  const int16_t *__restrict__ scale,
-                                                  const uint8_t *__restrict__ tips,
-                                                  const unsigned long long *__restrict__ masks,
-                                                  const double *__restrict__ pi,
-                                                  const double *__restrict__ catw,
-                                                  const double *__restrict__ site_inv,
-                                                  const double *__restrict__ pw,
-                                                  float *__restrict__ Gpart) {
-  extern __shared__ float4 spt[];  // [2][C][NR] tables, then warp sums
-  const int u = lvl_nodes[lvl_off + blockIdx.y];
-  const int slot = u - d.N;
-  const int ch0 = child[2 * slot], ch1 = child[2 * slot + 1];
-  const int CN = d.C * d.NR;
-  const float4 *pt4 = reinterpret_cast<const float4 *>(PT32);
-  for (int idx = threadIdx.x; idx < 2 * CN; idx += blockDim.x) {
-    const int x = idx / CN, r = idx - x * CN;
-    spt[idx] = pt4[(size_t)(x ? ch1 : ch0) * CN + r];
-  }
-  float *wsum = reinterpret_cast<float *>(spt + 2 * CN);  // [nwarps][32]
-  __syncthreads();
-  const int p = blockIdx.x * blockDim.x + threadIdx.x;
-  const bool active = p < d.P;
-  const int pc = active ? p : 0;
-  const int e = active ? (int)scale[(size_t)slot * d.P + pc] : 0;
-  const float n = active ? (float)pw[pc] : 0.f;
-  const float sinv = (float)site_inv[pc];
-  int code0 = 0, code1 = 0;
-  if (ch0 < d.N) code0 = tips[(size_t)ch0 * d.P + pc];
-  if (ch1 < d.N) code1 = tips[(size_t)ch1 * d.P + pc];
-  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nw = blockDim.x >> 5;
-  const int nblk = gridDim.x;
-  for (int c = 0; c < d.C; c++) {
-    const float4 *t0 = spt + c * d.NR, *t1 = spt + CN + c * d.NR;
-    float4 uu;
-    if (u == root) {
-      const float wc = (float)catw[c];
-      uu = make_float4(wc * (float)pi[0] * sinv, d.K > 1 ? wc * (float)pi[1] * sinv : 0.f,
-                       d.K > 2 ? wc * (float)pi[2] * sinv : 0.f,
-                       d.K > 3 ? wc * (float)pi[3] * sinv : 0.f);
-    } else {
-      uu = pre[((size_t)slot * d.C + c) * d.P + pc];
-    }
-    float4 l0, l1, s0, s1;
-    if (ch0 < d.N) {
-      s0 = t0[code0];
-      const unsigned long long mk = code0 < d.K ? (1ull << code0)
-                                    : (code0 == d.K ? ~0ull : masks[code0 - d.K - 1]);
-      l0 = make_float4((mk & 1ull) ? 1.f : 0.f, (mk & 2ull) ? 1.f : 0.f,
-                       (mk & 4ull) ? 1.f : 0.f, (mk & 8ull) ? 1.f : 0.f);
-    } else {
-      l0 = part[((size_t)(ch0 - d.N) * d.C + c) * d.P + pc];
-      s0 = matvec_t(t0, l0);
-    }
-    if (ch1 < d.N) {
-      s1 = t1[code1];
-      const unsigned long long mk = code1 < d.K ? (1ull << code1)
-                                    : (code1 == d.K ? ~0ull : masks[code1 - d.K - 1]);
-      l1 = make_float4((mk & 1ull) ? 1.f : 0.f, (mk & 2ull) ? 1.f : 0.f,
-                       (mk & 4ull) ? 1.f : 0.f, (mk & 8ull) ? 1.f : 0.f);
-    } else {
-      l1 = part[((size_t)(ch1 - d.N) * d.C + c) * d.P + pc];
-      s1 = matvec_t(t1, l1);
-    }
-    const float4 x0 = ldexp4(mul4(uu, s1), e);  // X for child 0
-    const float4 x1 = ldexp4(mul4(uu, s0), e);  // X for child 1
-    if (active && ch0 >= d.N) {
-      float4 o = make_float4(dot4(t0[0], x0), dot4(t0[1], x0), dot4(t0[2], x0), dot4(t0[3], x0));
-      pre[((size_t)(ch0 - d.N) * d.C + c) * d.P + p] = o;
-    }
-    if (active && ch1 >= d.N) {
-      float4 o = make_float4(dot4(t1[0], x1), dot4(t1[1], x1), dot4(t1[2], x1), dot4(t1[3], x1));
-      pre[((size_t)(ch1 - d.N) * d.C + c) * d.P + p] = o;
-    }
-    float g[32];
-    const float xa[4] = {x0.x * n, x0.y * n, x0.z * n, x0.w * n};
-    const float la[4] = {l0.x, l0.y, l0.z, l0.w};
-    const float xb[4] = {x1.x * n, x1.y * n, x1.z * n, x1.w * n};
-    const float lb[4] = {l1.x, l1.y, l1.z, l1.w};
-#pragma unroll
-    for (int i = 0; i < 4; i++)
-#pragma unroll
-      for (int j = 0; j < 4; j++) {
-        g[i * 4 + j] = xa[i] * la[j];
-        g[16 + i * 4 + j] = xb[i] * lb[j];
-      }
-    const float r = reduce_scatter32(g);
-    wsum[warp * 32 + lane] = r;
-    __syncthreads();
-    if (warp == 0) {
-      float t = 0.f;
-      for (int k = 0; k < nw; k++) t += wsum[k * 32 + lane];
-      const int xch = lane >> 4, ij = lane & 15;
-      Gpart[((((size_t)slot * nblk + blockIdx.x) * 2 + xch) * d.C + c) * 16 + ij] = t;
-    }
-    __syncthreads();
-  }
-}
-
 // G[v][c][i][j] = sum over pattern blocks of Gpart (FP64 accumulate, fixed
 // order).  One thread per (child node v, c, i, j).
 template <typename T>
@@ -648,25 +480,6 @@ __global__ void k_grad_reduce(Dims d, const int *__restrict__ parent, const int 
   }
 }
 
-template <int CMAX>
-void launch_pre_k4_levels(epoch_ctx *c, int root) {
-  const Dims &d = c->d;
-  const size_t smem = sizeof(float4) * 2 * d.C * d.NR + sizeof(float) * 32 * (kTile / 32);
-  if (smem > 48 * 1024)
-    cudaFuncSetAttribute(k_pre_k4<CMAX>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
-  const int L = (int)c->h_level_off.size() - 1;
-  for (int l = L - 1; l >= 0; l--) {
-    const int w = c->h_level_off[l + 1] - c->h_level_off[l];
-    dim3 grid(ceil_div(d.P, kTile), w);
-    k_pre_k4<CMAX><<<grid, kTile, smem, c->stream>>>(
-        d, c->d_PT32, c->d_level_nodes, c->h_level_off[l], c->d_child, root,
-        reinterpret_cast<const float4 *>(c->d_part), reinterpret_cast<float4 *>(c->d_pre),
-        c->d_scale, c->d_tips, c->d_masks, c->d_pi, c->d_catw, c->d_site_inv, c->d_pw,
-        (float *)c->d_Gpart);
-    c->launches++;
-  }
-}
-
 template <typename T>
 void launch_pre_generic(epoch_ctx *c, Tab<T> bt, int root) {
   const Dims &d = c->d;
@@ -704,18 +517,16 @@ cudaError_t launch_adjoint(epoch_ctx *c) {
     k_G_reduce<double><<<ceil_div(nG, 256), 256, 0, c->stream>>>(
         d, c->d_parent, c->d_child, (const double *)c->d_Gpart, nchunk, c->d_G);
   } else {
-    if (d.K == 4) {
-      if (d.C <= 4)
-        launch_pre_k4_levels<4>(c, root);
-      else if (d.C <= 8)
-        launch_pre_k4_levels<8>(c, root);
-      else
-        launch_pre_k4_levels<16>(c, root);
+    int nc = nchunk;
+    if (fast_k4(c)) {
+      cudaError_t e = launch_preorder_k4(c);
+      if (e != cudaSuccess) return e;
+      nc = ceil_div(d.P, persist_tile());
     } else {
       launch_pre_generic<float>(c, Tab<float>{c->d_PT32, c->d_masks}, root);
     }
     k_G_reduce<float><<<ceil_div(nG, 256), 256, 0, c->stream>>>(
-        d, c->d_parent, c->d_child, (const float *)c->d_Gpart, nchunk, c->d_G);
+        d, c->d_parent, c->d_child, (const float *)c->d_Gpart, nc, c->d_G);
   }
   c->launches++;
   return cudaGetLastError();

@@ -315,22 +315,26 @@ __global__ void k_branch_matrices(Dims d, const int *__restrict__ nseg,
   const double r = brate[v] * catr[c];
   for (int idx = tid; idx < KK; idx += nt) M[idx] = (idx / K == idx % K) ? 1.0 : 0.0;
   __syncthreads();
+  bool M_is_identity = true;
   for (int k = 0; k < ns; k++) {
     const int s = seg_mat[v * d.E + k];
     const double tau = r * seg_dt[v * d.E + k];
+    if (tau == 0.0) continue;  // exp(0) = I exactly (zero-length branch)
     if (d.reversible) {
       const double *Vs = V + (size_t)s * KK, *Vi = Vinv + (size_t)s * KK;
       for (int i = tid; i < K; i += nt) ev[i] = exp(tau * lam[(size_t)s * K + i]);
       __syncthreads();
-      // W = V diag(ev) V^-1
+      // W = V diag(ev) V^-1; transition probabilities are >= 0, so the
+      // rounding-level negatives of the eigen form are cut at 0 (keeps
+      // every partial likelihood >= 0)
       for (int idx = tid; idx < KK; idx += nt) {
         int i = idx / K, j = idx % K;
         double acc = 0.0;
         for (int m = 0; m < K; m++) acc += Vs[i * K + m] * ev[m] * Vi[m * K + j];
-        W[idx] = acc;
+        W[idx] = fmax(acc, 0.0);
       }
       __syncthreads();
-      if (k == 0) {
+      if (k == 0 || M_is_identity) {
         for (int idx = tid; idx < KK; idx += nt) M[idx] = W[idx];
       } else {
         for (int idx = tid; idx < KK; idx += nt) {
@@ -342,6 +346,7 @@ __global__ void k_branch_matrices(Dims d, const int *__restrict__ nseg,
         __syncthreads();
         for (int idx = tid; idx < KK; idx += nt) M[idx] = Y[idx];
       }
+      M_is_identity = false;
       __syncthreads();
     } else {
       const double *Qs = Qn + (size_t)s * KK;
@@ -381,6 +386,7 @@ __global__ void k_branch_matrices(Dims d, const int *__restrict__ nseg,
         for (int idx = tid; idx < KK; idx += nt) M[idx] = W[idx];
         __syncthreads();
       }
+      M_is_identity = false;
     }
   }
   __syncthreads();

@@ -126,91 +126,6 @@ __global__ void k_rescale_generic(Dims d, const int *__restrict__ lvl_nodes, int
   scale[(size_t)slot * d.P + p] = (int16_t)e;
 }
 
-// ---- fused FP32 kernel for K = 4 -------------------------------------------
-// One thread per pattern, all categories; the 16-byte state vector of a
-// (category, pattern) is one float4 load; children's transposed tables are
-// staged in shared memory.  Pruning, rescaling and the exponent store are
-// fused.  HBM traffic per internal node and pattern: C*16 B per internal
-// child read, 1 B per tip child, C*16 B + 2 B written.
-template <int CMAX>
-__global__ void __launch_bounds__(kTile) k_partials_k4(Dims d, const float *__restrict__ PT32,
-                                                       const int *__restrict__ lvl_nodes,
-                                                       int lvl_off, const int *__restrict__ child,
-                                                       float4 *part, int16_t *__restrict__ scale,
-                                                       const uint8_t *__restrict__ tips,
-                                                       int *__restrict__ status) {
-  extern __shared__ float4 spt[];  // [2][C][NR]
-  const int u = lvl_nodes[lvl_off + blockIdx.y];
-  const int slot = u - d.N;
-  const int ch0 = child[2 * slot], ch1 = child[2 * slot + 1];
-  const int CN = d.C * d.NR;
-  const float4 *pt4 = reinterpret_cast<const float4 *>(PT32);
-  for (int idx = threadIdx.x; idx < 2 * CN; idx += blockDim.x) {
-    const int x = idx / CN, r = idx - x * CN;
-    spt[idx] = pt4[(size_t)(x ? ch1 : ch0) * CN + r];
-  }
-  __syncthreads();
-  const int p = blockIdx.x * blockDim.x + threadIdx.x;
-  if (p >= d.P) return;
-  float4 acc[CMAX];
-#pragma unroll
-  for (int c = 0; c < CMAX; c++) acc[c] = make_float4(1.f, 1.f, 1.f, 1.f);
-#pragma unroll
-  for (int x = 0; x < 2; x++) {
-    const int node = x ? ch1 : ch0;
-    const float4 *tab = spt + x * CN;
-    if (node < d.N) {
-      const int code = tips[(size_t)node * d.P + p];
-#pragma unroll
-      for (int c = 0; c < CMAX; c++) {
-        if (c < d.C) {
-          const float4 s = tab[c * d.NR + code];
-          acc[c].x *= s.x; acc[c].y *= s.y; acc[c].z *= s.z; acc[c].w *= s.w;
-        }
-      }
-    } else {
-      const float4 *L = part + (size_t)(node - d.N) * d.C * d.P + p;
-      float4 l[CMAX];
-#pragma unroll
-      for (int c = 0; c < CMAX; c++)
-        if (c < d.C) l[c] = __ldcs(L + (size_t)c * d.P);
-#pragma unroll
-      for (int c = 0; c < CMAX; c++) {
-        if (c < d.C) {
-          const float4 *t = tab + c * d.NR;
-          const float4 r0 = t[0], r1 = t[1], r2 = t[2], r3 = t[3];
-          float4 s;
-          s.x = l[c].x * r0.x + l[c].y * r1.x + l[c].z * r2.x + l[c].w * r3.x;
-          s.y = l[c].x * r0.y + l[c].y * r1.y + l[c].z * r2.y + l[c].w * r3.y;
-          s.z = l[c].x * r0.z + l[c].y * r1.z + l[c].z * r2.z + l[c].w * r3.z;
-          s.w = l[c].x * r0.w + l[c].y * r1.w + l[c].z * r2.w + l[c].w * r3.w;
-          acc[c].x *= s.x; acc[c].y *= s.y; acc[c].z *= s.z; acc[c].w *= s.w;
-        }
-      }
-    }
-  }
-  float m = 0.f;
-#pragma unroll
-  for (int c = 0; c < CMAX; c++)
-    if (c < d.C) m = fmaxf(m, fmaxf(fmaxf(acc[c].x, acc[c].y), fmaxf(acc[c].z, acc[c].w)));
-  int e = 0;
-  if (!isfinite(m)) {
-    atomicOr(status, ST_NONFINITE);
-  } else if (m > 0.f) {
-    frexpf(m, &e);
-  }
-  float4 *out = part + (size_t)slot * d.C * d.P + p;
-#pragma unroll
-  for (int c = 0; c < CMAX; c++) {
-    if (c < d.C) {
-      float4 a = acc[c];
-      a.x = ldexpf(a.x, -e); a.y = ldexpf(a.y, -e); a.z = ldexpf(a.z, -e); a.w = ldexpf(a.w, -e);
-      out[(size_t)c * d.P] = a;
-    }
-  }
-  scale[(size_t)slot * d.P + p] = (int16_t)e;
-}
-
 // ---- root: per-pattern site likelihood and the weighted log-sum ----------
 // site_p = sum_c w_c sum_i pi_i L_root(c,p,i) (scaled), lnL_p = log site_p +
 // ln2 * sum_u e_u(p); the block sums of n_p lnL_p are reduced in a fixed
@@ -266,25 +181,6 @@ __global__ void k_lnl_final(int n, const double *__restrict__ part, double *__re
   }
 }
 
-template <int CMAX>
-cudaError_t launch_k4_levels(epoch_ctx *c) {
-  const Dims &d = c->d;
-  const size_t smem = sizeof(float4) * 2 * d.C * d.NR;
-  if (smem > 48 * 1024)
-    cudaFuncSetAttribute(k_partials_k4<CMAX>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                         (int)smem);
-  const int L = (int)c->h_level_off.size() - 1;
-  for (int l = 0; l < L; l++) {
-    const int w = c->h_level_off[l + 1] - c->h_level_off[l];
-    dim3 grid(ceil_div(d.P, kTile), w);
-    k_partials_k4<CMAX><<<grid, kTile, smem, c->stream>>>(
-        d, c->d_PT32, c->d_level_nodes, c->h_level_off[l], c->d_child,
-        reinterpret_cast<float4 *>(c->d_part), c->d_scale, c->d_tips, c->d_status);
-    c->launches++;
-  }
-  return cudaGetLastError();
-}
-
 template <typename T>
 cudaError_t launch_generic_levels(epoch_ctx *c, BranchTable<T> bt) {
   const Dims &d = c->d;
@@ -311,17 +207,14 @@ cudaError_t launch_partials(epoch_ctx *c) {
     BranchTable<double> bt{c->d_P64, c->d_masks};
     return launch_generic_levels<double>(c, bt);
   }
-  if (d.K == 4) {
-    if (d.C <= 4) return launch_k4_levels<4>(c);
-    if (d.C <= 8) return launch_k4_levels<8>(c);
-    return launch_k4_levels<16>(c);
-  }
+  if (fast_k4(c)) return launch_partials_k4(c);  // includes the root log-sum
   BranchTable<float> bt{c->d_PT32, c->d_masks};
   return launch_generic_levels<float>(c, bt);
 }
 
 cudaError_t launch_root(epoch_ctx *c) {
   const Dims &d = c->d;
+  if (fast_k4(c)) return cudaSuccess;  // done by the persistent pass
   int root_slot = -1;
   for (int v = 0; v < d.nn; v++)
     if (c->h_parent[v] < 0) root_slot = v - d.N;
