@@ -258,6 +258,28 @@ epoch_status check_tree(int N, const double *heights, const int *parent, const d
   return EPOCH_OK;
 }
 
+// FP32 K = 4 schedule (see k_k4.cu): level 0 holds the cherries (both
+// children tips); they are recomputed, not stored, by the post-order pass
+// unless level 0 is the root's own level (two taxa).  G tile sums are
+// [nn][tiles][C][16].
+epoch_status plan_k4(epoch_ctx *c) {
+  const Dims &d = c->d;
+  const int L = (int)c->h_level_off.size() - 1;
+  c->k4_first_level = (L == 1) ? 0 : 1;
+  const size_t tiles = (size_t)ceil_div(d.P, k4_tile());
+  const size_t need = (size_t)(2 * c->max_taxa - 1) * tiles * d.C * 16 * sizeof(float);
+  if (c->gpart_bytes < need) {
+    dfree(c->d_Gpart);
+    c->d_Gpart = nullptr;
+    c->gpart_bytes = need;
+    CK(cudaMalloc(&c->d_Gpart, c->gpart_bytes), "cudaMalloc(G tile sums)");
+  }
+  // exponents of cherries are never written: they stay zero
+  CK(cudaMemsetAsync(c->d_scale, 0, (size_t)(d.N - 1) * d.P * sizeof(int16_t), c->stream),
+     "cudaMemset(scale)");
+  return EPOCH_OK;
+}
+
 }  // namespace
 
 // =========================================================================
@@ -310,8 +332,8 @@ void epoch_destroy(epoch_ctx *c) {
                   c->d_seg_lo,     c->d_P64,     c->d_PT32,     c->d_part,       c->d_pre,
                   c->d_xbuf,       c->d_scale,   c->d_tips,     c->d_pw,         c->d_site_lnl,
                   c->d_site_inv,   c->d_lnl_part, c->d_lnl,     c->d_Gpart,      c->d_G,
-                  c->d_gseg,       c->d_grad,    c->d_status,   c->d_flags,      c->d_ctl,
-                  c->d_site_log};
+                  c->d_gseg,       c->d_grad,    c->d_status,   c->d_ctl,        c->d_site_log,
+                  c->d_level_off};
   for (void *p : bufs) dfree(p);
   if (c->h_grad_pinned) cudaFreeHost(c->h_grad_pinned);
   if (c->h_lnl_pinned) cudaFreeHost(c->h_lnl_pinned);
@@ -420,13 +442,16 @@ epoch_status epoch_create(epoch_ctx **out, int states, int n_epochs, const doubl
   A(dalloc(&c->d_pw, P));
   A(dalloc(&c->d_site_lnl, P));
   A(dalloc(&c->d_site_inv, P));
-  A(dalloc(&c->d_lnl_part, nchunk));
+  A(dalloc(&c->d_lnl_part, ceil_div(n_patterns, 32)));
   A(dalloc(&c->d_lnl, 1));
-  A(cudaMalloc(&c->d_Gpart, (size_t)ni_max * nchunk * 2 * C * KK * es));
+  if (precision == EPOCH_FP64 || states != 4) {  // the K = 4 FP32 layout is sized per tree
+    c->gpart_bytes = (size_t)ni_max * nchunk * 2 * C * KK * es;
+    A(cudaMalloc(&c->d_Gpart, c->gpart_bytes));
+  }
   A(dalloc(&c->d_G, (size_t)nn_max * C * KK));
   A(dalloc(&c->d_status, 1));
-  A(dalloc(&c->d_flags, (size_t)ni_max * nchunk));
   A(dalloc(&c->d_ctl, 8));
+  A(dalloc(&c->d_level_off, max_taxa + 1));
   A(dalloc(&c->d_site_log, P));
   A(cudaMallocHost((void **)&c->h_lnl_pinned, sizeof(double)));
   A(cudaMallocHost((void **)&c->h_status_pinned, sizeof(int)));
@@ -685,6 +710,14 @@ epoch_status epoch_set_tree(epoch_ctx *c, int n_taxa, const double *heights, con
     CK(cudaMemcpyAsync(c->d_level_nodes, c->h_level_nodes.data(), sizeof(int) * (N - 1),
                        cudaMemcpyHostToDevice, c->stream),
        "cudaMemcpyAsync(levels)");
+    CK(cudaMemcpyAsync(c->d_level_off, c->h_level_off.data(), sizeof(int) * (L + 1),
+                       cudaMemcpyHostToDevice, c->stream),
+       "cudaMemcpyAsync(level offsets)");
+    c->root = root;
+    if (fast_k4(c)) {
+      s = plan_k4(c);
+      if (s != EPOCH_OK) return s;
+    }
     CK(cudaStreamSynchronize(c->stream), "cudaStreamSynchronize");  // host vectors reused
     c->have &= ~HAVE_TIPS;
   }

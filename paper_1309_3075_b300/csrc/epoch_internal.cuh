@@ -117,9 +117,15 @@ struct epoch_ctx {
   void *d_gseg = nullptr;             // [nn][E][C][1+np]  (T)
   double *d_grad = nullptr;           // [nn (heights) + (E-1) + np + nn (rates)]
   int *d_status = nullptr;            // [1]
-  int *d_flags = nullptr;             // [NI][tiles] readiness flags (persistent passes)
-  int *d_ctl = nullptr;               // [8] work counters / abort word
+  int *d_ctl = nullptr;               // [8] block counters of last-block reductions
   double *d_site_log = nullptr;       // [P] log of the scaled root sum
+  int *d_level_off = nullptr;         // [L+1] level offsets into d_level_nodes
+  // FP32 K = 4 schedule (k_k4.cu): level 0 holds the cherries, which the
+  // post-order pass recomputes instead of storing (unless level 0 is the
+  // root's level); k4_first_level is the first stored post-order level
+  int root = -1;
+  int k4_first_level = 1;
+  size_t gpart_bytes = 0;
   size_t part_elem = 0;               // sizeof(T) of partials
   int max_level_width = 0;
 
@@ -152,12 +158,11 @@ cudaError_t launch_root(epoch_ctx *c);
 // k_adjoint.cu
 cudaError_t launch_adjoint(epoch_ctx *c);
 cudaError_t launch_chain_rule(epoch_ctx *c);
-// k_persist.cu (FP32, K = 4: single-launch dependency-driven passes)
-int persist_tile();
-cudaError_t launch_partials_k4(epoch_ctx *c);
-cudaError_t launch_preorder_k4(epoch_ctx *c);
+// k_k4.cu (FP32, K = 4)
+int k4_tile();                                  // patterns per CTA of the K = 4 kernels
+cudaError_t launch_partials_k4(epoch_ctx *c);   // pruning, rescaling, root log-sum
+cudaError_t launch_preorder_k4(epoch_ctx *c);   // adjoint pass and G
 
-// The FP32 K = 4 path runs the persistent passes.
 inline bool fast_k4(const epoch_ctx *c) { return c->precision != EPOCH_FP64 && c->d.K == 4; }
 
 inline int ceil_div(long long a, long long b) { return (int)((a + b - 1) / b); }

@@ -517,16 +517,10 @@ cudaError_t launch_adjoint(epoch_ctx *c) {
     k_G_reduce<double><<<ceil_div(nG, 256), 256, 0, c->stream>>>(
         d, c->d_parent, c->d_child, (const double *)c->d_Gpart, nchunk, c->d_G);
   } else {
-    int nc = nchunk;
-    if (fast_k4(c)) {
-      cudaError_t e = launch_preorder_k4(c);
-      if (e != cudaSuccess) return e;
-      nc = ceil_div(d.P, persist_tile());
-    } else {
-      launch_pre_generic<float>(c, Tab<float>{c->d_PT32, c->d_masks}, root);
-    }
+    if (fast_k4(c)) return launch_preorder_k4(c);  // adjoint pass and G reduction
+    launch_pre_generic<float>(c, Tab<float>{c->d_PT32, c->d_masks}, root);
     k_G_reduce<float><<<ceil_div(nG, 256), 256, 0, c->stream>>>(
-        d, c->d_parent, c->d_child, (const float *)c->d_Gpart, nc, c->d_G);
+        d, c->d_parent, c->d_child, (const float *)c->d_Gpart, nchunk, c->d_G);
   }
   c->launches++;
   return cudaGetLastError();
