@@ -58,9 +58,7 @@ epoch_status check_device(epoch_ctx *c) {
 
 size_t elem_size(int precision) { return precision == EPOCH_FP64 ? sizeof(double) : sizeof(float); }
 
-bool generic_path(const epoch_ctx *c) {
-  return c->precision == EPOCH_FP64 || c->d.K != 4;
-}
+bool generic_path(const epoch_ctx *c) { return !fast_k4(c); }
 
 epoch_status ensure_pt32(epoch_ctx *c) {
   const Dims &d = c->d;
@@ -70,6 +68,14 @@ epoch_status ensure_pt32(epoch_ctx *c) {
   size_t n = (size_t)(2 * c->max_taxa - 1) * d.C * d.NR * d.Kp;
   CK(dalloc(&c->d_PT32, n), "cudaMalloc(branch tables)");
   CK(cudaMemsetAsync(c->d_PT32, 0, n * sizeof(float), c->stream), "cudaMemset");
+  dfree(c->d_pairS);
+  dfree(c->d_pairL);
+  c->d_pairS = c->d_pairL = nullptr;
+  if (fast_k4(c)) {  // code-pair tables of the cherries
+    const size_t np = (size_t)(2 * c->max_taxa - 1) * d.C * d.NR * d.NR * 4;
+    CK(dalloc(&c->d_pairS, np), "cudaMalloc(pair tables)");
+    CK(dalloc(&c->d_pairL, np), "cudaMalloc(pair tables)");
+  }
   return EPOCH_OK;
 }
 
@@ -125,6 +131,7 @@ epoch_status enqueue_branch(epoch_ctx *c) {
   CK(launch_model_setup(c), "model setup kernel");
   CK(launch_param_transform(c), "parameter transform kernel");
   CK(launch_branch_matrices(c), "branch matrix kernel");
+  if (fast_k4(c)) CK(launch_pair_tables_k4(c), "pair table kernel");
   return EPOCH_OK;
 }
 
@@ -259,15 +266,16 @@ epoch_status check_tree(int N, const double *heights, const int *parent, const d
 }
 
 // FP32 K = 4 schedule (see k_k4.cu): level 0 holds the cherries (both
-// children tips); they are recomputed, not stored, by the post-order pass
-// unless level 0 is the root's own level (two taxa).  G tile sums are
-// [nn][tiles][C][16].
+// children tips); the post-order pass recomputes them from code-pair tables
+// instead of storing them, unless level 0 is the root's own level (two
+// taxa).  G tile sums are [nn][tiles][C][16]; code-pair tables are
+// [nn][C][NR^2] float4 each.
 epoch_status plan_k4(epoch_ctx *c) {
   const Dims &d = c->d;
   const int L = (int)c->h_level_off.size() - 1;
   c->k4_first_level = (L == 1) ? 0 : 1;
-  const size_t tiles = (size_t)ceil_div(d.P, k4_tile());
-  const size_t need = (size_t)(2 * c->max_taxa - 1) * tiles * d.C * 16 * sizeof(float);
+  const size_t nn_max = (size_t)(2 * c->max_taxa - 1);
+  const size_t need = nn_max * k4_tiles(d.P) * d.C * 16 * sizeof(float);
   if (c->gpart_bytes < need) {
     dfree(c->d_Gpart);
     c->d_Gpart = nullptr;
@@ -275,7 +283,7 @@ epoch_status plan_k4(epoch_ctx *c) {
     CK(cudaMalloc(&c->d_Gpart, c->gpart_bytes), "cudaMalloc(G tile sums)");
   }
   // exponents of cherries are never written: they stay zero
-  CK(cudaMemsetAsync(c->d_scale, 0, (size_t)(d.N - 1) * d.P * sizeof(int16_t), c->stream),
+  CK(cudaMemsetAsync(c->d_scale, 0, (size_t)(d.N - 1) * d.Pp * sizeof(int16_t), c->stream),
      "cudaMemset(scale)");
   return EPOCH_OK;
 }
@@ -330,10 +338,11 @@ void epoch_destroy(epoch_ctx *c) {
                   c->d_masks,      c->d_heights, c->d_parent,   c->d_brate,      c->d_child,
                   c->d_level_nodes, c->d_nseg,   c->d_seg_mat,  c->d_seg_dt,     c->d_seg_hi,
                   c->d_seg_lo,     c->d_P64,     c->d_PT32,     c->d_part,       c->d_pre,
-                  c->d_xbuf,       c->d_scale,   c->d_tips,     c->d_pw,         c->d_site_lnl,
+                  c->d_xbuf,       c->d_scale,   c->d_tips,     c->d_pw,         c->d_pwf,
+                  c->d_site_lnl,
                   c->d_site_inv,   c->d_lnl_part, c->d_lnl,     c->d_Gpart,      c->d_G,
                   c->d_gseg,       c->d_grad,    c->d_status,   c->d_ctl,        c->d_site_log,
-                  c->d_level_off};
+                  c->d_level_off,  c->d_pairS,   c->d_pairL};
   for (void *p : bufs) dfree(p);
   if (c->h_grad_pinned) cudaFreeHost(c->h_grad_pinned);
   if (c->h_lnl_pinned) cudaFreeHost(c->h_lnl_pinned);
@@ -381,6 +390,7 @@ epoch_status epoch_create(epoch_ctx **out, int states, int n_epochs, const doubl
   d.S = n_matrices;
   d.C = n_categories;
   d.P = n_patterns;
+  d.Pp = (n_patterns + 15) / 16 * 16;
   d.N = 0;
   d.nn = 0;
   d.np = 0;
@@ -437,14 +447,15 @@ epoch_status epoch_create(epoch_ctx **out, int states, int n_epochs, const doubl
   A(dalloc(&c->d_P64, (size_t)nn_max * C * KK));
   A(cudaMalloc(&c->d_part, (size_t)ni_max * C * P * d.Kp * es));
   A(cudaMalloc(&c->d_pre, (size_t)ni_max * C * P * d.Kp * es));
-  A(dalloc(&c->d_scale, (size_t)ni_max * P));
-  A(dalloc(&c->d_tips, (size_t)max_taxa * P));
+  A(dalloc(&c->d_scale, (size_t)ni_max * d.Pp));
+  A(dalloc(&c->d_tips, (size_t)max_taxa * d.Pp));
   A(dalloc(&c->d_pw, P));
+  A(dalloc(&c->d_pwf, d.Pp));
   A(dalloc(&c->d_site_lnl, P));
   A(dalloc(&c->d_site_inv, P));
   A(dalloc(&c->d_lnl_part, ceil_div(n_patterns, 32)));
   A(dalloc(&c->d_lnl, 1));
-  if (precision == EPOCH_FP64 || states != 4) {  // the K = 4 FP32 layout is sized per tree
+  if (precision == EPOCH_FP64 || states != 4 || n_categories > 8) {  // K = 4 FP32: per tree
     c->gpart_bytes = (size_t)ni_max * nchunk * 2 * C * KK * es;
     A(cudaMalloc(&c->d_Gpart, c->gpart_bytes));
   }
@@ -455,7 +466,7 @@ epoch_status epoch_create(epoch_ctx **out, int states, int n_epochs, const doubl
   A(dalloc(&c->d_site_log, P));
   A(cudaMallocHost((void **)&c->h_lnl_pinned, sizeof(double)));
   A(cudaMallocHost((void **)&c->h_status_pinned, sizeof(int)));
-  A(cudaMallocHost((void **)&c->h_tips_staging, (size_t)max_taxa * P));
+  A(cudaMallocHost((void **)&c->h_tips_staging, (size_t)max_taxa * d.Pp + sizeof(float) * d.Pp));
   if (!ok) {
     cudaGetLastError();
     c->err = "device allocation failed";
@@ -642,7 +653,11 @@ epoch_status epoch_set_ambiguity_masks(epoch_ctx *c, int n_masks, const unsigned
   epoch_status s = ensure_pt32(c);
   if (s != EPOCH_OK) return s;
   invalidate_graphs(c);
-  c->have &= ~(HAVE_BRANCH | HAVE_PARTIALS | HAVE_TIPS);
+  // the kernel path can depend on the number of masks: the tree must be set
+  // again (re-planned), then the tip data
+  c->have &= ~(HAVE_BRANCH | HAVE_PARTIALS | HAVE_TIPS | HAVE_TREE);
+  c->h_parent.clear();
+  c->d.N = 0;
   return EPOCH_OK;
 }
 
@@ -761,19 +776,30 @@ epoch_status epoch_set_tip_data(epoch_ctx *c, const int *tip_codes, const double
   if (!tip_codes || !pattern_weights) return fail(c, EPOCH_ERR_ARG, "codes or weights is NULL");
   const Dims &d = c->d;
   const int maxcode = d.K + d.n_masks;
-  const size_t n = (size_t)d.N * d.P;
-  // marshal int codes into the one-byte device layout [N][P]
+  // marshal int codes into the one-byte device layout [N][Pp] (row stride
+  // padded to 16 bytes; padding holds code 0 and is never used as a pattern)
   CK(cudaStreamSynchronize(c->stream), "cudaStreamSynchronize");  // staging buffer reuse
-  for (size_t i = 0; i < n; i++) {
-    int code = tip_codes[i];
-    if (code < 0 || code > maxcode) return fail(c, EPOCH_ERR_ARG, "tip code out of range");
-    c->h_tips_staging[i] = (uint8_t)code;
+  for (int x = 0; x < d.N; x++) {
+    uint8_t *row = c->h_tips_staging + (size_t)x * d.Pp;
+    for (int p = 0; p < d.P; p++) {
+      const int code = tip_codes[(size_t)x * d.P + p];
+      if (code < 0 || code > maxcode) return fail(c, EPOCH_ERR_ARG, "tip code out of range");
+      row[p] = (uint8_t)code;
+    }
+    for (int p = d.P; p < d.Pp; p++) row[p] = 0;
   }
-  for (int p = 0; p < d.P; p++)
+  float *wf = reinterpret_cast<float *>(c->h_tips_staging + (size_t)c->max_taxa * d.Pp);
+  for (int p = 0; p < d.P; p++) {
     if (!fin(pattern_weights[p]) || pattern_weights[p] < 0.0)
       return fail(c, EPOCH_ERR_ARG, "bad pattern weight");
-  CK(cudaMemcpyAsync(c->d_tips, c->h_tips_staging, n, cudaMemcpyHostToDevice, c->stream),
+    wf[p] = (float)pattern_weights[p];
+  }
+  for (int p = d.P; p < d.Pp; p++) wf[p] = 0.f;
+  CK(cudaMemcpyAsync(c->d_tips, c->h_tips_staging, (size_t)d.N * d.Pp, cudaMemcpyHostToDevice,
+                     c->stream),
      "cudaMemcpyAsync(tips)");
+  CK(cudaMemcpyAsync(c->d_pwf, wf, sizeof(float) * d.Pp, cudaMemcpyHostToDevice, c->stream),
+     "cudaMemcpyAsync(weights)");
   CK(cudaMemcpyAsync(c->d_pw, pattern_weights, sizeof(double) * d.P, cudaMemcpyHostToDevice,
                      c->stream),
      "cudaMemcpyAsync(weights)");

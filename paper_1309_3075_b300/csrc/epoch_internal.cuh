@@ -39,6 +39,8 @@ struct Dims {
   int S;      // rate matrices
   int C;      // categories
   int P;      // patterns
+  int Pp;     // row stride of the per-pattern byte/short/float arrays (P rounded
+              // up to 16: every row starts on a 16-byte boundary for bulk copies)
   int N;      // taxa of the current tree
   int nn;     // 2N-1
   int np;     // model parameters
@@ -108,6 +110,7 @@ struct epoch_ctx {
   int16_t *d_scale = nullptr;         // [NI][P] power-of-two exponents
   uint8_t *d_tips = nullptr;          // [N][P]
   double *d_pw = nullptr;             // [P]
+  float *d_pwf = nullptr;             // [Pp] pattern weights as FP32 (0 in the padding)
   double *d_site_lnl = nullptr;       // [P]
   double *d_site_inv = nullptr;       // [P]  1 / scaled site value
   double *d_lnl_part = nullptr;       // [ceil(P/kTile)]
@@ -125,6 +128,8 @@ struct epoch_ctx {
   // root's level); k4_first_level is the first stored post-order level
   int root = -1;
   int k4_first_level = 1;
+  float *d_pairS = nullptr;           // [nn][C][NR*NR][4] S of each cherry per code pair
+  float *d_pairL = nullptr;           // [nn][C][NR*NR][4] L of each cherry per code pair
   size_t gpart_bytes = 0;
   size_t part_elem = 0;               // sizeof(T) of partials
   int max_level_width = 0;
@@ -159,11 +164,15 @@ cudaError_t launch_root(epoch_ctx *c);
 cudaError_t launch_adjoint(epoch_ctx *c);
 cudaError_t launch_chain_rule(epoch_ctx *c);
 // k_k4.cu (FP32, K = 4)
-int k4_tile();                                  // patterns per CTA of the K = 4 kernels
+int k4_tiles(int P);                            // pattern tiles of the K = 4 kernels
+cudaError_t launch_pair_tables_k4(epoch_ctx *c); // cherries' code-pair tables
 cudaError_t launch_partials_k4(epoch_ctx *c);   // pruning, rescaling, root log-sum
 cudaError_t launch_preorder_k4(epoch_ctx *c);   // adjoint pass and G
 
-inline bool fast_k4(const epoch_ctx *c) { return c->precision != EPOCH_FP64 && c->d.K == 4; }
+// FP32, K = 4, at most 8 categories and 3 ambiguity masks (NR <= 8)
+inline bool fast_k4(const epoch_ctx *c) {
+  return c->precision != EPOCH_FP64 && c->d.K == 4 && c->d.C <= 8 && c->d.NR <= 8;
+}
 
 inline int ceil_div(long long a, long long b) { return (int)((a + b - 1) / b); }
 

@@ -65,7 +65,7 @@ template <typename T>
 __device__ __forceinline__ T child_factor(const Dims &d, const Tab<T> &bt, const T *__restrict__ part,
                                           const uint8_t *__restrict__ tips, int x, int c, int p,
                                           int i) {
-  if (x < d.N) return bt.tip(d, x, c, i, tips[(size_t)x * d.P + p]);
+  if (x < d.N) return bt.tip(d, x, c, i, tips[(size_t)x * d.Pp + p]);
   const T *L = part + (((size_t)(x - d.N) * d.C + c) * d.P + p) * d.Kp;
   T s = 0;
   for (int j = 0; j < d.K; j++) s += bt.mat(d, x, c, i, j) * L[j];
@@ -103,7 +103,7 @@ __global__ void k_pre_x(Dims d, Tab<T> bt, const int *__restrict__ lvl_nodes, in
     else
       uu = pre[(((size_t)slot * d.C + c) * d.P + p) * d.Kp + i];
     const T s = child_factor<T>(d, bt, part, tips, sib, c, p, i);
-    out = scale_by(uu * s, (int)scale[(size_t)slot * d.P + p]);
+    out = scale_by(uu * s, (int)scale[(size_t)slot * d.Pp + p]);
   }
   xbuf[((((size_t)bi * 2 + x) * d.C + c) * d.P + p) * d.Kp + i] = out;
 }
@@ -151,7 +151,7 @@ __global__ void k_G_part(Dims d, const int *__restrict__ lvl_nodes, int lvl_off,
     const T *X = xbuf + (((size_t)bi * 2 + x) * d.C + c) * d.P * d.Kp;
     if (v < d.N) {
       for (int p = p0; p < p1; p++)
-        if (code_allows(d, masks, tips[(size_t)v * d.P + p], j))
+        if (code_allows(d, masks, tips[(size_t)v * d.Pp + p], j))
           acc += (T)pw[p] * X[(size_t)p * d.Kp + i];
     } else {
       const T *L = part + ((size_t)(v - d.N) * d.C + c) * d.P * d.Kp;

@@ -59,7 +59,7 @@ __device__ __forceinline__ T child_factor(const Dims &d, const BranchTable<T> &b
                                           const T *__restrict__ part,
                                           const uint8_t *__restrict__ tips, int x, int c,
                                           int p, int i) {
-  if (x < d.N) return bt.tip(d, x, c, i, tips[(size_t)x * d.P + p]);
+  if (x < d.N) return bt.tip(d, x, c, i, tips[(size_t)x * d.Pp + p]);
   const T *L = part + (((size_t)(x - d.N) * d.C + c) * d.P + p) * d.Kp;
   T s = 0;
   for (int j = 0; j < d.K; j++) s += bt.mat(d, x, c, i, j) * L[j];
@@ -123,7 +123,7 @@ __global__ void k_rescale_generic(Dims d, const int *__restrict__ lvl_nodes, int
       for (int i = 0; i < d.K; i++) L[i] = scale_by(L[i], e);
     }
   }
-  scale[(size_t)slot * d.P + p] = (int16_t)e;
+  scale[(size_t)slot * d.Pp + p] = (int16_t)e;
 }
 
 // ---- root: per-pattern site likelihood and the weighted log-sum ----------
@@ -148,7 +148,7 @@ __global__ void k_root(Dims d, int root_slot, const T *__restrict__ part,
       site += catw[c] * sc;
     }
     int esum = 0;
-    for (int s = 0; s < d.N - 1; s++) esum += scale[(size_t)s * d.P + p];
+    for (int s = 0; s < d.N - 1; s++) esum += scale[(size_t)s * d.Pp + p];
     const double lp = log(site) + 0.69314718055994530942 * (double)esum;
     site_lnl[p] = lp;
     site_inv[p] = site > 0.0 ? 1.0 / site : 0.0;
