@@ -127,10 +127,16 @@ epoch_status read_status(epoch_ctx *c) {
 // ---- the enqueued sequences ---------------------------------------------
 
 epoch_status enqueue_branch(epoch_ctx *c) {
-  CK(launch_segments(c), "segments kernel");
-  CK(launch_model_setup(c), "model setup kernel");
-  CK(launch_param_transform(c), "parameter transform kernel");
-  CK(launch_branch_matrices(c), "branch matrix kernel");
+  if (fast_k4(c) && c->d.reversible) {
+    CK(launch_model_setup(c), "model setup kernel");
+    CK(launch_param_transform(c), "parameter transform kernel");
+    CK(launch_branch_k4(c), "branch matrix kernel");
+  } else {
+    CK(launch_segments(c), "segments kernel");
+    CK(launch_model_setup(c), "model setup kernel");
+    CK(launch_param_transform(c), "parameter transform kernel");
+    CK(launch_branch_matrices(c), "branch matrix kernel");
+  }
   if (fast_k4(c)) CK(launch_pair_tables_k4(c), "pair table kernel");
   return EPOCH_OK;
 }

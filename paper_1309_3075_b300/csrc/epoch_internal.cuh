@@ -168,6 +168,9 @@ int k4_tiles(int P);                            // pattern tiles of the K = 4 ke
 cudaError_t launch_pair_tables_k4(epoch_ctx *c); // cherries' code-pair tables
 cudaError_t launch_partials_k4(epoch_ctx *c);   // pruning, rescaling, root log-sum
 cudaError_t launch_preorder_k4(epoch_ctx *c);   // adjoint pass and G
+// k_k4small.cu (FP32, K = 4, reversible): per-(branch, category) threads
+cudaError_t launch_branch_k4(epoch_ctx *c);     // segments + branch matrices + tables
+cudaError_t launch_chain_k4(epoch_ctx *c);      // chain rule through the products
 
 // FP32, K = 4, at most 8 categories and 3 ambiguity masks (NR <= 8)
 inline bool fast_k4(const epoch_ctx *c) {

@@ -543,12 +543,18 @@ cudaError_t launch_chain_rule(epoch_ctx *c) {
         d, c->d_parent, c->d_child, c->d_nseg, c->d_seg_dt, c->d_seg_hi, c->d_seg_lo, c->d_brate,
         c->d_catr, (const double *)c->d_gseg, nb_nodes, c->d_grad);
   } else {
-    size_t smem = sizeof(float) * (8 * d.KK + d.K + 32);
-    cudaFuncSetAttribute(k_grad_branch<float>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                         (int)smem);
-    k_grad_branch<float><<<grid, threads, smem, c->stream>>>(
-        d, c->d_G, c->d_nseg, c->d_seg_mat, c->d_seg_dt, c->d_brate, c->d_catr, c->d_lam, c->d_V,
-        c->d_Vinv, c->d_Q, c->d_Dth32, c->d_Dnz, (float *)c->d_gseg);
+    if (fast_k4(c) && d.reversible) {
+      cudaError_t e = launch_chain_k4(c);
+      if (e != cudaSuccess) return e;
+      c->launches--;  // counted below with the reduction
+    } else {
+      size_t smem = sizeof(float) * (8 * d.KK + d.K + 32);
+      cudaFuncSetAttribute(k_grad_branch<float>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                           (int)smem);
+      k_grad_branch<float><<<grid, threads, smem, c->stream>>>(
+          d, c->d_G, c->d_nseg, c->d_seg_mat, c->d_seg_dt, c->d_brate, c->d_catr, c->d_lam,
+          c->d_V, c->d_Vinv, c->d_Q, c->d_Dth32, c->d_Dnz, (float *)c->d_gseg);
+    }
     k_grad_reduce<float><<<nblocks, 256, 0, c->stream>>>(
         d, c->d_parent, c->d_child, c->d_nseg, c->d_seg_dt, c->d_seg_hi, c->d_seg_lo, c->d_brate,
         c->d_catr, (const float *)c->d_gseg, nb_nodes, c->d_grad);

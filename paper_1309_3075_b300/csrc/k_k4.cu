@@ -349,6 +349,7 @@ __global__ void k4_G_reduce(Dims d, int ntile, const int *__restrict__ parent,
   const int v = (int)(idx / (16LL * d.C));
   double acc = 0.0;
   if (parent[v] >= 0)
+#pragma unroll 8
     for (int t = 0; t < ntile; t++)
       acc += (double)Gpart[(((size_t)v * ntile + t) * d.C + c) * 16 + ij];
   G[idx] = acc;
@@ -369,6 +370,7 @@ __global__ void __launch_bounds__(256) k4_site_lnl(Dims d, const int16_t *__rest
   const int p = blockIdx.x * 32 + pl;
   int acc = 0;
   if (p < d.P)
+#pragma unroll 8
     for (int s = gi; s < d.N - 1; s += 8) acc += scale[(size_t)s * d.Pp + p];
   es[gi][pl] = acc;
   __syncthreads();

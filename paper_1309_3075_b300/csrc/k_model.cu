@@ -430,7 +430,9 @@ cudaError_t launch_model_setup(epoch_ctx *c) {
   const Dims &d = c->d;
   size_t smem = setup_smem(d);
   cudaFuncSetAttribute(k_model_setup, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
-  k_model_setup<<<d.S, 256, smem, c->stream>>>(d, c->normalise, c->d_Qraw, c->d_pi, c->d_Q,
+  // small K: one warp per matrix (its barriers are cheap); large K: 8 warps
+  const int threads = d.K <= 8 ? 32 : 256;
+  k_model_setup<<<d.S, threads, smem, c->stream>>>(d, c->normalise, c->d_Qraw, c->d_pi, c->d_Q,
                                                c->d_cnorm, c->d_lam, c->d_V, c->d_Vinv,
                                                c->d_status);
   c->launches++;
