@@ -50,6 +50,8 @@
 #ifndef EPOCH_H
 #define EPOCH_H
 
+#include <stdint.h>
+
 #ifdef __cplusplus
 extern "C" {
 #endif
@@ -57,6 +59,7 @@ extern "C" {
 #define EPOCH_MAX_STATES 64   /* K <= 64                                   */
 #define EPOCH_MAX_EPOCHS 32   /* E <= 32                                   */
 #define EPOCH_MAX_CATEGORIES 16
+#define EPOCH_NOALLOC_MAX_PATTERNS 262144 /* epoch_site_log_sum_noalloc */
 
 typedef struct epoch_ctx epoch_ctx; /* opaque; owns all device memory */
 
@@ -215,6 +218,40 @@ epoch_status epoch_read_results(epoch_ctx *ctx, double *lnL, double *d_heights,
  * replays count their kernels), and graph captures made. */
 epoch_status epoch_counters(const epoch_ctx *ctx, long long *kernel_launches,
                             long long *graph_captures);
+
+/* ---- allocation-free root log-sum (no counterpart in the paper) ---------- */
+
+/* The weighted log-sum that ends the root step, for callers that must not
+ * have a library allocate device memory (a fixed-footprint sampler loop, a
+ * program whose own pool already holds the HBM).  The call allocates
+ * nothing: its block sums and counter live in one static device array sized
+ * for EPOCH_NOALLOC_MAX_PATTERNS patterns.  Async on cuda_stream (NULL =
+ * legacy default stream); no context needed.
+ *
+ * All pointers are DEVICE pointers owned by the caller:
+ *   site_log   [n_patterns]  log of the scaled root sum of each pattern
+ *   exponents  [n_rows][row_stride] int16 power-of-two scale exponents of
+ *              each pattern (row_stride >= n_patterns); may be NULL when
+ *              n_rows = 0
+ *   weights    [n_patterns]  pattern weights n_p
+ *   site_out   [n_patterns]  out: site_log[p] + ln2 * sum_u exponents[u][p]
+ *              (may be NULL)
+ *   lnL_out    [1]           out: sum_p n_p site_out[p] (terms with n_p = 0
+ *              skipped), summed in a fixed order
+ * Returns EPOCH_ERR_ARG for a negative size, a NULL input that is needed or
+ * row_stride < n_patterns; EPOCH_ERR_CAPACITY when n_patterns exceeds
+ * EPOCH_NOALLOC_MAX_PATTERNS (nothing is launched); EPOCH_ERR_CUDA when the
+ * launch fails.
+ * The first call on a device looks up the scratch array's address and
+ * zeroes its counter (on cuda_stream); make that first call before any
+ * stream capture begins.  Calls on the same device that can overlap in time
+ * share the scratch and race: order them (one stream, or events). */
+epoch_status epoch_site_log_sum_noalloc(const double *site_log,
+                                        const int16_t *exponents, int n_rows,
+                                        long long row_stride,
+                                        const double *weights, int n_patterns,
+                                        double *site_out, double *lnL_out,
+                                        void *cuda_stream);
 
 #ifdef __cplusplus
 }

@@ -58,6 +58,8 @@ _SIGS = {
     "epoch_evaluate_async": [_vp, C.c_int],
     "epoch_read_results": [_vp, _dp, _dp, _dp, _dp, _dp],
     "epoch_counters": [_vp, C.POINTER(C.c_longlong), C.POINTER(C.c_longlong)],
+    "epoch_site_log_sum_noalloc": [_vp, _vp, C.c_int, C.c_longlong, _vp, C.c_int, _vp, _vp,
+                                   _vp],
 }
 _RESTYPE = {"epoch_destroy": None, "epoch_last_error": C.c_char_p,
             "epoch_status_string": C.c_char_p}
@@ -323,3 +325,15 @@ class EpochLikelihood:
             self.close()
         except Exception:
             pass
+
+
+def epoch_site_log_sum_noalloc(site_log, exponents, n_rows, row_stride, weights, n_patterns,
+                               site_out, lnl_out, cuda_stream=None):
+    """Device-pointer call (integers, e.g. ``tensor.data_ptr()``; 0 or None for
+    NULL).  Returns the status code instead of raising, so callers can see
+    EPOCH_ERR_CAPACITY; the call allocates no device memory."""
+    def p(x):
+        return _vp(int(x)) if x else None
+    return int(lib().epoch_site_log_sum_noalloc(p(site_log), p(exponents), int(n_rows),
+                                                int(row_stride), p(weights), int(n_patterns),
+                                                p(site_out), p(lnl_out), p(cuda_stream)))
