@@ -50,12 +50,12 @@ def make_workload(name):
     import synth
 
     if name == "gtr":
-        w = synth.config2()
+        w = synth.gtr_500taxa()
         return w, {"workload": "GTR 3-epoch, 500-taxon coalescent, 10,000 patterns, 4 gamma categories",
                    "taxa": 500, "patterns": 10000, "categories": 4, "states": 4, "epochs": 3,
                    "params": int(w.n_params)}
     if name == "gy94":
-        w = synth.config3()
+        w = synth.gy94_128taxa()
         return w, {"workload": "GY94 61-state 4-epoch, 128-taxon coalescent, 5,000 codon sites",
                    "taxa": 128, "patterns": int(w.n_patterns), "categories": 4, "states": 61,
                    "epochs": 4, "params": int(w.n_params)}

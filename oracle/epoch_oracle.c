@@ -28,7 +28,7 @@
  *     taken term by term (product rule), and d exp(X)/d theta uses the
  *     block-triangular exponential exp([[X, Y], [0, X]]) (Van Loan 1978).
  *
- * Conventions (readings of the paper, all listed in the design doc):
+ * Conventions (readings of the paper where it is silent or garbled):
  *   - times are heights before the youngest tip; epoch 0 = [0, b_1) is the
  *     youngest, epoch E-1 = [b_{E-1}, inf) the oldest;
  *   - P rows = parent (ancestral) state; the left factor of the product is

@@ -26,10 +26,10 @@ from synth.workloads import (  # noqa: F401
     asym_raw,
     simulate_alignment,
     compress_patterns,
-    config1,
-    config2,
-    config3,
-    config5,
+    hky_8taxa,
+    gtr_500taxa,
+    gy94_128taxa,
+    asym50_forest,
     small_nucleotide,
     small_codon,
     tiny_tree_workload,

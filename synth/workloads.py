@@ -359,7 +359,7 @@ def compress_patterns(aln: np.ndarray):
 
 
 # ---------------------------------------------------------------------------
-# workloads shaped like the paper's (seed = 1309 + config index)
+# workloads shaped like the paper's nucleotide, codon and trait analyses (seeds 1310-1314)
 # ---------------------------------------------------------------------------
 
 
@@ -367,7 +367,7 @@ def _epoch_bounds(root, fracs):
     return np.array([root * f for f in fracs], dtype=np.float64)
 
 
-def config1(seed: int = 1310, n_taxa: int = 8, n_sites: int = 200) -> Workload:
+def hky_8taxa(seed: int = 1310, n_taxa: int = 8, n_sites: int = 200) -> Workload:
     """Plain FP64 epoch likelihood: 8-taxon coalescent (root 1.0), HKY with
     kappa_e ~ LogN(1, 0.5) per epoch, pi ~ Dirichlet(1), 2 epochs split at 0.5,
     200 simulated sites compressed to unique patterns, one rate category."""
@@ -418,7 +418,7 @@ def _gtr_workload(name, seed, n_taxa, n_sites, n_cat, alpha, fracs, dated=False,
                     param_names=names, seed=seed)
 
 
-def config2(seed: int = 1311, n_taxa: int = 500, n_sites: int = 10_000, dated=False) -> Workload:
+def gtr_500taxa(seed: int = 1311, n_taxa: int = 500, n_sites: int = 10_000, dated=False) -> Workload:
     """GTR (exchangeabilities ~ LogN(0,1) per epoch, pi ~ Dirichlet(1)), 3 epochs
     at 1/3 and 2/3 of the root height, 500-taxon coalescent, 10,000 simulated
     columns each its own pattern with weight ~ U{1..20}, 4 discrete-gamma
@@ -467,7 +467,7 @@ def _gy94_workload(name, seed, n_taxa, n_sites, n_cat, fracs, kappa=2.0, dated=F
                     param_names=names, seed=seed)
 
 
-def config3(seed: int = 1312, n_taxa: int = 128, n_sites: int = 5000, dated=False) -> Workload:
+def gy94_128taxa(seed: int = 1312, n_taxa: int = 128, n_sites: int = 5000, dated=False) -> Workload:
     """GY94 (61 sense codons), kappa = 2 shared, omega_k ~ LogN(-1, 0.7) for 4
     epochs with boundaries at 1/4, 1/2, 3/4 of the root height, 128-taxon
     coalescent, 5,000 simulated codon sites compressed to patterns, 4
@@ -494,7 +494,7 @@ def _asym_tree(rng, K, n_taxa, n_epochs, n_pat, name):
                     np.ones(n_pat), reversible=0)
 
 
-def config5(seed: int = 1314, n_trees: int = 256, K: int = 50, taxa=(50, 1000), epochs=(1, 8),
+def asym50_forest(seed: int = 1314, n_trees: int = 256, K: int = 50, taxa=(50, 1000), epochs=(1, 8),
             patterns=(1, 4)) -> BatchWorkload:
     """Batched phylogeography: n_trees independent coalescent trees (root 1.0)
     with N_t ~ U{50..1000} taxa, E_t ~ U{1..8} epochs at sorted U(0,1) heights,

@@ -24,12 +24,12 @@ def _built():
 
 @pytest.fixture(scope="module")
 def gtr_full():
-    return synth.config2()
+    return synth.gtr_500taxa()
 
 
 @pytest.fixture(scope="module")
 def gy94_full():
-    return synth.config3()
+    return synth.gy94_128taxa()
 
 
 def maxrel(g, ref):

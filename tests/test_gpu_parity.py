@@ -1,11 +1,11 @@
 """GPU parity: libepoch (through the C ABI) against the FP64 CPU oracle on the
 same seeded inputs.
 
-Tolerances (the benchmark spec): lnL relative error <= 1e-10 on the FP64
-path and <= 1e-5 on the FP32 paths.  Branch matrices on every path are FP64
-and must match to 1e-12.  Gradients: FP64 path within 1e-9 of the oracle's
-(max-norm relative); FP32 paths within 1e-4 (max-norm relative), the FD
-bound the benchmark spec states for the gradient.
+Tolerances: lnL relative error <= 1e-10 on the FP64 path and <= 1e-5 on
+the FP32 paths.  Branch matrices on every path are FP64 and must match to
+1e-12.  Gradients: FP64 path within 1e-9 of the oracle's (max-norm
+relative); FP32 paths within 1e-4 (max-norm relative), the bound also used
+for the finite-difference check of the gradient.
 """
 import numpy as np
 import pytest
@@ -84,8 +84,8 @@ def check_grad(w, prec):
 
 
 @pytest.mark.parametrize("prec", [EPOCH_FP64, EPOCH_FP32])
-def test_config1_hky_two_epochs(prec):
-    w = synth.config1()
+def test_hky_8taxa_two_epochs(prec):
+    w = synth.hky_8taxa()
     check_lnl(w, prec)
     check_grad(w, prec)
 

@@ -90,12 +90,12 @@ def test_simulated_frequencies_approach_pi():
     assert chi2 < stats.chi2.ppf(0.999, 3)
 
 
-def test_configs_shapes():
-    w1 = synth.config1()
+def test_workload_shapes():
+    w1 = synth.hky_8taxa()
     assert w1.n_taxa == 8 and w1.n_epochs == 2 and w1.pattern_weights.sum() == 200
     assert np.isclose(w1.boundaries[0], 0.5)
     w2 = synth.small_nucleotide(5, 20, 100)
     assert w2.n_categories == 4 and w2.n_epochs == 3
     assert ((w2.pattern_weights >= 1) & (w2.pattern_weights <= 20)).all()
-    b = synth.config5(n_trees=3, taxa=(50, 60))
+    b = synth.asym50_forest(n_trees=3, taxa=(50, 60))
     assert len(b.trees) == 3 and all(t.K == 50 and t.reversible == 0 for t in b.trees)
