@@ -291,6 +291,21 @@ epoch_status plan_k4(epoch_ctx *c) {
   // exponents of cherries are never written: they stay zero
   CK(cudaMemsetAsync(c->d_scale, 0, (size_t)(d.N - 1) * d.Pp * sizeof(int16_t), c->stream),
      "cudaMemset(scale)");
+  k4_schedule(c);
+  if (c->k4_walk_cap < c->h_k4_walk.size()) {
+    dfree(c->d_k4_walk);
+    c->d_k4_walk = nullptr;
+    c->k4_walk_cap = c->h_k4_walk.size();
+    CK(cudaMalloc(&c->d_k4_walk, sizeof(int4) * c->k4_walk_cap), "cudaMalloc(walk steps)");
+  }
+  if (!c->d_k4_nt) CK(dalloc(&c->d_k4_nt, nn_max), "cudaMalloc(G tile counts)");
+  if (!c->h_k4_walk.empty())
+    CK(cudaMemcpyAsync(c->d_k4_walk, c->h_k4_walk.data(), sizeof(int4) * c->h_k4_walk.size(),
+                       cudaMemcpyHostToDevice, c->stream),
+       "cudaMemcpyAsync(walk steps)");
+  CK(cudaMemcpyAsync(c->d_k4_nt, c->h_k4_nt.data(), sizeof(int) * d.nn, cudaMemcpyHostToDevice,
+                     c->stream),
+     "cudaMemcpyAsync(G tile counts)");
   return EPOCH_OK;
 }
 
@@ -348,7 +363,7 @@ void epoch_destroy(epoch_ctx *c) {
                   c->d_site_lnl,
                   c->d_site_inv,   c->d_lnl_part, c->d_lnl,     c->d_Gpart,      c->d_G,
                   c->d_gseg,       c->d_grad,    c->d_status,   c->d_ctl,        c->d_site_log,
-                  c->d_level_off,  c->d_pairS,   c->d_pairL};
+                  c->d_level_off,  c->d_pairS,   c->d_pairL,    c->d_k4_walk,    c->d_k4_nt};
   for (void *p : bufs) dfree(p);
   if (c->h_grad_pinned) cudaFreeHost(c->h_grad_pinned);
   if (c->h_lnl_pinned) cudaFreeHost(c->h_lnl_pinned);

@@ -128,6 +128,18 @@ struct epoch_ctx {
   // root's level); k4_first_level is the first stored post-order level
   int root = -1;
   int k4_first_level = 1;
+  // walks over the narrow top levels [k4_top, L) and the adjoint launches
+  // below them (k4_schedule in k_k4.cu)
+  int k4_top = 0;
+  int k4_top_begin = 0;               // level-order index of the first walk node
+  int k4_walk_post = 0, k4_walk_pre = 0;    // steps of each walk
+  int k4_slots_post = 0, k4_slots_pre = 0;  // value slots per walk thread
+  std::vector<int4> h_k4_walk;        // post-order steps, then pre-order steps (4 int4 each)
+  std::vector<int> h_k4_launch;       // adjoint launches: (first node, nodes, tiles per CTA)
+  std::vector<int> h_k4_nt;           // [nn] G tiles of each branch
+  int4 *d_k4_walk = nullptr;
+  size_t k4_walk_cap = 0;             // int4 capacity of d_k4_walk
+  int *d_k4_nt = nullptr;             // [nn]
   float *d_pairS = nullptr;           // [nn][C][NR*NR][4] S of each cherry per code pair
   float *d_pairL = nullptr;           // [nn][C][NR*NR][4] L of each cherry per code pair
   size_t gpart_bytes = 0;
@@ -168,6 +180,7 @@ int k4_tiles(int P);                            // pattern tiles of the K = 4 ke
 cudaError_t launch_pair_tables_k4(epoch_ctx *c); // cherries' code-pair tables
 cudaError_t launch_partials_k4(epoch_ctx *c);   // pruning, rescaling, root log-sum
 cudaError_t launch_preorder_k4(epoch_ctx *c);   // adjoint pass and G
+void k4_schedule(epoch_ctx *c);                 // host: walks, launches, tile counts
 // k_k4small.cu (FP32, K = 4, reversible): per-(branch, category) threads
 cudaError_t launch_branch_k4(epoch_ctx *c);     // segments + branch matrices + tables
 cudaError_t launch_chain_k4(epoch_ctx *c);      // chain rule through the products

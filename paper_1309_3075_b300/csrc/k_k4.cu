@@ -1,38 +1,50 @@
 // k_k4.cu -- the FP32 path for K = 4 (nucleotides): post-order pruning with
 // rescaling, and the pre-order adjoint pass with the per-branch adjoint G.
 //
-//  * One launch per post-order level; grid = (tiles of 256 patterns, nodes
-//    of the level).  The 16-byte state vector of a (category, pattern) is one
-//    load; every branch table a CTA needs sits in shared memory.
+//  * Wide levels of the tree: one launch per post-order level; grid =
+//    (pattern tiles, nodes of the level).  The 16-byte state vector of a
+//    (category, pattern) is one load; every branch table a CTA needs sits in
+//    shared memory.  A CTA branches once on the kinds of its node's two
+//    children (tip, cherry, stored) into code specialised for that pair.
+//  * The narrow top of the tree (levels of at most kWalkWidth nodes, up to
+//    the root) is done by one "walk" launch per pass: every thread owns one
+//    (pattern, category) and steps through the top nodes in order, keeping
+//    the values its later steps need in its own shared-memory slots.  No
+//    thread reads another's values, so the walk has no barriers; patterns
+//    are independent (Eq. partial_likelihood), which is what makes this
+//    legal.  The host assigns the slots (k4_schedule).
 //  * Cherries (internal nodes whose two children are tips) are not stored by
 //    the post-order pass.  Their partial L = T_a[code_a] o T_b[code_b] and
-//    S = P L depend only on the pair of one-byte tip codes, so k4_pair_tables
-//    tabulates both for every code pair (NR^2 entries per category, NR = K +
-//    1 + masks) right after the branch matrices; a parent then reads a
-//    cherry child's S (and, in the adjoint, its L) with one lookup.  A
-//    cherry's values are products of probabilities: no rescaling (e = 0).
-//    The pre-order pass stores every internal node's outside partial U,
-//    cherries included, and visits the cherries' level too, so each node's
-//    step touches exactly its two child branches.
+//    S = P L depend only on the pair of one-byte tip codes, so
+//    k4_pair_tables tabulates both for every code pair (NR^2 entries per
+//    category, NR = K + 1 + masks); a parent reads a cherry child's S (and,
+//    in the adjoint, its L) with one lookup.  A cherry's values are products
+//    of probabilities: no rescaling (e = 0).
 //  * Power-of-two rescaling by exponent arithmetic (exact).
 //  * Adjoint threads are laid out as (category, pattern lane); a thread owns
-//    kPPT patterns of one category, keeps the 32 G accumulators of its two
+//    Cp * m patterns of one category, keeps the 32 G accumulators of its two
 //    branches in registers, and the CTA reduces them once, through shared
-//    memory in a fixed order (deterministic), into a per-(branch, tile)
-//    sum; k4_G_reduce adds the tiles in FP64.
+//    memory in a fixed order (deterministic), into a per-(branch, tile) sum;
+//    k4_G_reduce adds the tiles in FP64.  The G of the walk's branches comes
+//    from the same kernel with the U stores switched off.
 #include <math.h>
 #include <stdint.h>
 
 #include <algorithm>
+#include <vector>
 
 #include "epoch_internal.cuh"
 
 namespace epoch {
 namespace {
 
-constexpr int kThr = 256;  // threads per CTA
-constexpr int kTP = 256;   // patterns per CTA tile
-constexpr int kBatch = 2;  // adjoint patterns whose loads are issued together
+constexpr int kThr = 256;       // threads per CTA of the level kernels
+constexpr int kTP = 256;        // patterns of one fine tile
+constexpr int kWalkThr = 128;   // threads per CTA of the walks
+constexpr int kWalkWidth = 4;   // widest level the walks take
+constexpr int kWalkSlots = 32;  // value slots per walk thread (16 B each)
+constexpr size_t kWalkSmem = 160 * 1024;  // shared memory of a walk CTA at most
+enum : int { kTip = 0, kCherry = 1, kStored = 2 };
 
 __device__ __forceinline__ float4 mul4(float4 a, float4 b) {
   return make_float4(a.x * b.x, a.y * b.y, a.z * b.z, a.w * b.w);
@@ -43,11 +55,23 @@ __device__ __forceinline__ float4 scl4(float4 a, float s) {
 __device__ __forceinline__ float dot4(float4 a, float4 b) {
   return a.x * b.x + a.y * b.y + a.z * b.z + a.w * b.w;
 }
+__device__ __forceinline__ float max4(float4 a) {
+  return fmaxf(fmaxf(a.x, a.y), fmaxf(a.z, a.w));
+}
 // a * 2^-e, exact; e is the binary exponent of a value in (0, 2] so -e is in
 // [-1, 149]: one multiply by 2^-e when -e <= 126, else by 2^126 then 2^(-e-126).
 __device__ __forceinline__ float4 pow2_scale(float4 a, int e) {
   if (e >= -126) return scl4(a, __int_as_float((127 - e) << 23));
   return scl4(scl4(a, __int_as_float(253 << 23)), __int_as_float((1 - e) << 23));
+}
+// m = f 2^e with f in [0.5, 1); 0 for m = 0
+__device__ __forceinline__ int binary_exponent(float m) {
+  int e = 0;
+  if (m > 0.f) {
+    e = ((__float_as_int(m) >> 23) & 255) - 126;
+    if (e == -126) frexpf(m, &e);  // denormal maximum
+  }
+  return e;
 }
 // S = P L with rows t[j] = column j of P: S = sum_j L_j t[j]
 __device__ __forceinline__ float4 matvec_t(const float4 *t, float4 l) {
@@ -85,25 +109,26 @@ struct K4Args {
   const float *pwf;        // [Pp]
   int root;
   double *site_log, *site_inv;
-  float *Gpart;            // [nn][tiles][C][16]
-  int ntile;
+  float *Gpart;            // [nn][gstride][C][16]
+  int gstride;             // fine tiles of 256 patterns
+  int top_begin;           // level-order index from which the adjoint stores no U
   int *status;
 };
 
-// A child: kind 0 tip, 1 cherry (tips a, b), 2 stored.
+// A child: kind tip, cherry (tips a, b) or stored.
 struct Kid {
   int node, kind, a, b;
 };
 __device__ __forceinline__ Kid classify(const K4Args &g, int x) {
-  Kid k{x, 0, -1, -1};
+  Kid k{x, kTip, -1, -1};
   if (x >= g.d.N) {
     const int a = g.child[2 * (x - g.d.N)], b = g.child[2 * (x - g.d.N) + 1];
     if (a < g.d.N && b < g.d.N && x != g.root) {
-      k.kind = 1;
+      k.kind = kCherry;
       k.a = a;
       k.b = b;
     } else {
-      k.kind = 2;
+      k.kind = kStored;
     }
   }
   return k;
@@ -133,15 +158,15 @@ __global__ void k4_pair_tables(Dims d, const float4 *__restrict__ PT, const int 
 //   stored: first 4 rows [C][4]
 __device__ __forceinline__ int table_size(const K4Args &g, const Kid &k, bool pre) {
   const int C = g.d.C, NR = g.d.NR;
-  if (k.kind == 0) return C * NR;
-  if (k.kind == 1) return pre ? C * (2 * NR * NR + 4) : C * NR * NR;
+  if (k.kind == kTip) return C * NR;
+  if (k.kind == kCherry) return pre ? C * (2 * NR * NR + 4) : C * NR * NR;
   return C * 4;
 }
 __device__ void load_table(const K4Args &g, const Kid &k, bool pre, float4 *dst) {
   const int C = g.d.C, NR = g.d.NR, NR2 = NR * NR;
-  if (k.kind == 0) {
+  if (k.kind == kTip) {
     for (int i = threadIdx.x; i < C * NR; i += blockDim.x) dst[i] = g.PT[(size_t)k.node * C * NR + i];
-  } else if (k.kind == 1) {
+  } else if (k.kind == kCherry) {
     for (int i = threadIdx.x; i < C * NR2; i += blockDim.x) dst[i] = g.pairS[(size_t)k.node * C * NR2 + i];
     if (pre) {
       for (int i = threadIdx.x; i < C * NR2; i += blockDim.x)
@@ -155,37 +180,34 @@ __device__ void load_table(const K4Args &g, const Kid &k, bool pre, float4 *dst)
   }
 }
 
-// ---- post-order ------------------------------------------------------------
-template <int CMAX>
-__global__ void __launch_bounds__(kThr) k4_post(K4Args g, int off) {
-  extern __shared__ float4 tabs[];
+// ---- post-order level kernel ---------------------------------------------------
+// Thread = pattern (all categories).  Loads first, then the tables barrier.
+template <int CMAX, int K0, int K1>
+__device__ __forceinline__ void post_node(const K4Args &g, int u, const Kid &k0, const Kid &k1,
+                                          const float4 *t0, const float4 *t1) {
   const Dims &d = g.d;
   const int C = d.C, NR = d.NR, NR2 = NR * NR;
-  const int u = g.nodes[off + blockIdx.y];
   const int slot = u - d.N;
-  const Kid k0 = classify(g, g.child[2 * slot]), k1 = classify(g, g.child[2 * slot + 1]);
-  float4 *t0 = tabs, *t1 = tabs + table_size(g, k0, false);
-  load_table(g, k0, false, t0);
-  load_table(g, k1, false, t1);
   const int p = blockIdx.x * kTP + threadIdx.x;
-  // loads first (stored children's vectors, codes), then the tables barrier
   float4 l0[CMAX], l1[CMAX];
   int i0 = 0, i1 = 0;
   if (p < d.P) {
-    if (k0.kind == 2) {
+    if constexpr (K0 == kStored) {
+      const float4 *src = g.part + (size_t)(k0.node - d.N) * C * d.P + p;
 #pragma unroll
       for (int c = 0; c < CMAX; c++)
-        if (c < C) l0[c] = __ldcs(g.part + ((size_t)(k0.node - d.N) * C + c) * d.P + p);
-    } else if (k0.kind == 1) {
+        if (c < C) l0[c] = __ldcs(src + (size_t)c * d.P);
+    } else if constexpr (K0 == kCherry) {
       i0 = g.tips[(size_t)k0.a * d.Pp + p] * NR + g.tips[(size_t)k0.b * d.Pp + p];
     } else {
       i0 = g.tips[(size_t)k0.node * d.Pp + p];
     }
-    if (k1.kind == 2) {
+    if constexpr (K1 == kStored) {
+      const float4 *src = g.part + (size_t)(k1.node - d.N) * C * d.P + p;
 #pragma unroll
       for (int c = 0; c < CMAX; c++)
-        if (c < C) l1[c] = __ldcs(g.part + ((size_t)(k1.node - d.N) * C + c) * d.P + p);
-    } else if (k1.kind == 1) {
+        if (c < C) l1[c] = __ldcs(src + (size_t)c * d.P);
+    } else if constexpr (K1 == kCherry) {
       i1 = g.tips[(size_t)k1.a * d.Pp + p] * NR + g.tips[(size_t)k1.b * d.Pp + p];
     } else {
       i1 = g.tips[(size_t)k1.node * d.Pp + p];
@@ -198,126 +220,235 @@ __global__ void __launch_bounds__(kThr) k4_post(K4Args g, int off) {
 #pragma unroll
   for (int c = 0; c < CMAX; c++)
     if (c < C) {
-      const float4 s0 = k0.kind == 2 ? matvec_t(t0 + 4 * c, l0[c])
-                                     : t0[k0.kind == 1 ? c * NR2 + i0 : c * NR + i0];
-      const float4 s1 = k1.kind == 2 ? matvec_t(t1 + 4 * c, l1[c])
-                                     : t1[k1.kind == 1 ? c * NR2 + i1 : c * NR + i1];
+      float4 s0, s1;
+      if constexpr (K0 == kStored) s0 = matvec_t(t0 + 4 * c, l0[c]);
+      else if constexpr (K0 == kCherry) s0 = t0[c * NR2 + i0];
+      else s0 = t0[c * NR + i0];
+      if constexpr (K1 == kStored) s1 = matvec_t(t1 + 4 * c, l1[c]);
+      else if constexpr (K1 == kCherry) s1 = t1[c * NR2 + i1];
+      else s1 = t1[c * NR + i1];
       acc[c] = mul4(s0, s1);
-      m = fmaxf(m, fmaxf(fmaxf(acc[c].x, acc[c].y), fmaxf(acc[c].z, acc[c].w)));
+      m = fmaxf(m, max4(acc[c]));
     }
   int e = 0;
-  if (!(m <= 3.0e38f)) {  // NaN or Inf
-    atomicOr(g.status, ST_NONFINITE);
-  } else if (m > 0.f) {
-    e = ((__float_as_int(m) >> 23) & 255) - 126;  // m = f 2^e, f in [0.5, 1)
-    if (e == -126) frexpf(m, &e);                 // denormal maximum
-  }
+  if (!(m <= 3.0e38f)) atomicOr(g.status, ST_NONFINITE);  // NaN or Inf
+  else e = binary_exponent(m);
   double site = 0.0;
+  const bool is_root = (u == g.root);
+  float4 *dst = g.part + (size_t)slot * C * d.P + p;
 #pragma unroll
   for (int c = 0; c < CMAX; c++)
     if (c < C) {
       const float4 v = pow2_scale(acc[c], e);
-      g.part[((size_t)slot * C + c) * d.P + p] = v;
-      if (u == g.root)
+      dst[(size_t)c * d.P] = v;
+      if (is_root)
         site += g.catw[c] * ((double)v.x * g.pi[0] + (double)v.y * g.pi[1] +
                              (double)v.z * g.pi[2] + (double)v.w * g.pi[3]);
     }
   g.scale[(size_t)slot * d.Pp + p] = (int16_t)e;
-  if (u == g.root) {
+  if (is_root) {
     g.site_log[p] = log(site);
     g.site_inv[p] = site > 0.0 ? 1.0 / site : 0.0;
   }
 }
 
-// ---- pre-order -------------------------------------------------------------
-// Thread = (category c, lane): c = tid / GS, GS = kThr / Cp; the thread owns
-// patterns lane + GS k of the tile (Cp of them), processed kBatch at a
-// time with their loads issued together.
 template <int CMAX>
-__global__ void __launch_bounds__(kThr, 2) k4_pre(K4Args g, int off, int Cp) {
+__global__ void __launch_bounds__(kThr) k4_post(K4Args g, int off) {
+  extern __shared__ float4 tabs[];
+  const int u = g.nodes[off + blockIdx.y];
+  const int slot = u - g.d.N;
+  Kid k0 = classify(g, g.child[2 * slot]), k1 = classify(g, g.child[2 * slot + 1]);
+  if (k0.kind > k1.kind) {
+    const Kid t = k0;
+    k0 = k1;
+    k1 = t;
+  }
+  float4 *t0 = tabs, *t1 = tabs + table_size(g, k0, false);
+  load_table(g, k0, false, t0);
+  load_table(g, k1, false, t1);
+  switch (k0.kind * 3 + k1.kind) {
+    case 0: post_node<CMAX, kTip, kTip>(g, u, k0, k1, t0, t1); break;
+    case 1: post_node<CMAX, kTip, kCherry>(g, u, k0, k1, t0, t1); break;
+    case 2: post_node<CMAX, kTip, kStored>(g, u, k0, k1, t0, t1); break;
+    case 4: post_node<CMAX, kCherry, kCherry>(g, u, k0, k1, t0, t1); break;
+    case 5: post_node<CMAX, kCherry, kStored>(g, u, k0, k1, t0, t1); break;
+    default: post_node<CMAX, kStored, kStored>(g, u, k0, k1, t0, t1); break;
+  }
+}
+
+// ---- pre-order level kernel ------------------------------------------------------
+// Thread = (category c, lane): c = tid / GS, GS = kThr / Cp; the CTA covers m
+// fine tiles and the thread owns patterns lane + GS k of them (Cp m in all),
+// kPreB at a time.  The float4 operands of the next kPreB patterns (U of the
+// node, partials of stored children) are copied into the thread's own
+// shared-memory stage with cp.async while it computes the current ones
+// (double buffer; a thread reads only what it copied, so no barrier).
+constexpr int kPreB = 2;
+constexpr int kStageF4 = 2 * kPreB * 3 * kThr;  // float4 of the stage
+
+__device__ __forceinline__ void cp_async16(void *smem, const void *gmem, bool full) {
+  const unsigned s = (unsigned)__cvta_generic_to_shared(smem);
+  const int n = full ? 16 : 0;  // 0: fill the 16 bytes with zeros, read nothing
+  asm volatile("cp.async.cg.shared.global [%0], [%1], 16, %2;\n" ::"r"(s), "l"(gmem), "r"(n)
+               : "memory");
+}
+__device__ __forceinline__ void cp_async_commit() {
+  asm volatile("cp.async.commit_group;\n" ::: "memory");
+}
+__device__ __forceinline__ void cp_async_wait_prev() {
+  asm volatile("cp.async.wait_group 1;\n" ::: "memory");
+}
+
+struct PreSmall {
+  int e, i0, i1;
+  float n;
+};
+
+template <int K0, int K1>
+__device__ __forceinline__ void pre_node(const K4Args &g, int slot, bool is_root, bool store,
+                                         const Kid &k0, const Kid &k1, const float4 *t0,
+                                         const float4 *t1, const float4 *Ltip, float4 *stage,
+                                         int Cp, int m, float (&acc)[32]) {
+  const Dims &d = g.d;
+  const int C = d.C, NR = d.NR, NR2 = NR * NR;
+  const int GS = kThr / Cp;
+  const int c = threadIdx.x / GS, lp = threadIdx.x % GS;
+  if (c >= C) return;  // idle lanes when C is not a power of two
+  const double wcd = g.catw[c];
+  const float4 pi4 = make_float4((float)g.pi[0], (float)g.pi[1], (float)g.pi[2], (float)g.pi[3]);
+  // this category's table views
+  const float4 *S0t = K0 == kTip ? t0 + c * NR : t0 + c * NR2;
+  const float4 *S1t = K1 == kTip ? t1 + c * NR : t1 + c * NR2;
+  const float4 *L0t = t0 + C * NR2 + c * NR2;
+  const float4 *L1t = t1 + C * NR2 + c * NR2;
+  const float4 *P0 = K0 == kCherry ? t0 + 2 * C * NR2 + 4 * c : t0 + 4 * c;
+  const float4 *P1 = K1 == kCherry ? t1 + 2 * C * NR2 + 4 * c : t1 + 4 * c;
+  const float4 *up = g.pre + ((size_t)slot * C + c) * d.P;
+  const int16_t *ep = g.scale + (size_t)slot * d.Pp;
+  const float4 *l0p = K0 == kStored ? g.part + ((size_t)(k0.node - d.N) * C + c) * d.P : nullptr;
+  const float4 *l1p = K1 == kStored ? g.part + ((size_t)(k1.node - d.N) * C + c) * d.P : nullptr;
+  float4 *w0p = K0 != kTip ? g.pre + ((size_t)(k0.node - d.N) * C + c) * d.P : nullptr;
+  float4 *w1p = K1 != kTip ? g.pre + ((size_t)(k1.node - d.N) * C + c) * d.P : nullptr;
+  const uint8_t *c0a = g.tips + (size_t)(K0 == kCherry ? k0.a : k0.node) * d.Pp;
+  const uint8_t *c0b = g.tips + (size_t)(K0 == kCherry ? k0.b : 0) * d.Pp;
+  const uint8_t *c1a = g.tips + (size_t)(K1 == kCherry ? k1.a : k1.node) * d.Pp;
+  const uint8_t *c1b = g.tips + (size_t)(K1 == kCherry ? k1.b : 0) * d.Pp;
+  const int npat = Cp * m;
+  const int pbase = blockIdx.x * kTP * m + lp;
+  // stage[buf][k][operand][thread]
+  auto sp = [&](int buf, int k, int o) { return stage + ((buf * kPreB + k) * 3 + o) * kThr + threadIdx.x; };
+  PreSmall nxt[kPreB];
+  auto issue = [&](int j0, int buf) {
+#pragma unroll
+    for (int k = 0; k < kPreB; k++) {
+      const int p = pbase + GS * (j0 + k);
+      const bool act = (j0 + k < npat) && p < d.P;
+      const int pc = act ? p : 0;
+      if (!is_root) cp_async16(sp(buf, k, 0), up + pc, act);
+      if constexpr (K0 == kStored) cp_async16(sp(buf, k, 1), l0p + pc, act);
+      if constexpr (K1 == kStored) cp_async16(sp(buf, k, 2), l1p + pc, act);
+      nxt[k].e = act ? ep[pc] : 0;
+      nxt[k].n = act ? g.pwf[pc] : 0.f;
+      if constexpr (K0 == kCherry) nxt[k].i0 = act ? c0a[pc] * NR + c0b[pc] : 0;
+      else if constexpr (K0 == kTip) nxt[k].i0 = act ? c0a[pc] : 0;
+      if constexpr (K1 == kCherry) nxt[k].i1 = act ? c1a[pc] * NR + c1b[pc] : 0;
+      else if constexpr (K1 == kTip) nxt[k].i1 = act ? c1a[pc] : 0;
+    }
+    cp_async_commit();
+  };
+  issue(0, 0);
+  int buf = 0;
+  for (int j0 = 0; j0 < npat; j0 += kPreB, buf ^= 1) {
+    PreSmall cur[kPreB];
+#pragma unroll
+    for (int k = 0; k < kPreB; k++) cur[k] = nxt[k];
+    if (j0 + kPreB < npat) issue(j0 + kPreB, buf ^ 1);
+    else cp_async_commit();  // empty group keeps the count
+    cp_async_wait_prev();    // this buffer's copies have landed
+#pragma unroll
+    for (int k = 0; k < kPreB; k++) {
+      const int p = pbase + GS * (j0 + k);
+      const bool act = (j0 + k < npat) && p < d.P;
+      // the root's U is the root distribution over the site likelihood
+      const float4 uu = is_root ? (act ? scl4(pi4, (float)(wcd * g.site_inv[p])) : pi4)
+                                : *sp(buf, k, 0);
+      float4 L0, L1, S0, S1;
+      if constexpr (K0 == kTip) {
+        L0 = Ltip[cur[k].i0];
+        S0 = S0t[cur[k].i0];
+      } else if constexpr (K0 == kCherry) {
+        L0 = L0t[cur[k].i0];
+        S0 = S0t[cur[k].i0];
+      } else {
+        L0 = *sp(buf, k, 1);
+        S0 = matvec_t(P0, L0);
+      }
+      if constexpr (K1 == kTip) {
+        L1 = Ltip[cur[k].i1];
+        S1 = S1t[cur[k].i1];
+      } else if constexpr (K1 == kCherry) {
+        L1 = L1t[cur[k].i1];
+        S1 = S1t[cur[k].i1];
+      } else {
+        L1 = *sp(buf, k, 2);
+        S1 = matvec_t(P1, L1);
+      }
+      const float4 X0 = pow2_scale(mul4(uu, S1), cur[k].e);
+      const float4 X1 = pow2_scale(mul4(uu, S0), cur[k].e);
+      if constexpr (K0 != kTip)
+        if (store && act) w0p[p] = matvec(P0, X0);
+      if constexpr (K1 != kTip)
+        if (store && act) w1p[p] = matvec(P1, X1);
+      const float n = cur[k].n;
+      const float xa[4] = {X0.x * n, X0.y * n, X0.z * n, X0.w * n};
+      const float xb[4] = {X1.x * n, X1.y * n, X1.z * n, X1.w * n};
+      const float la[4] = {L0.x, L0.y, L0.z, L0.w};
+      const float lb[4] = {L1.x, L1.y, L1.z, L1.w};
+#pragma unroll
+      for (int i = 0; i < 4; i++)
+#pragma unroll
+        for (int j = 0; j < 4; j++) {
+          acc[i * 4 + j] += xa[i] * la[j];
+          acc[16 + i * 4 + j] += xb[i] * lb[j];
+        }
+    }
+  }
+  asm volatile("cp.async.wait_all;\n" ::: "memory");
+}
+
+__global__ void __launch_bounds__(kThr, 2) k4_pre(K4Args g, int off, int Cp, int m) {
   extern __shared__ float4 tabs[];
   __shared__ float red[kThr / 32][32][33];
   __shared__ float wsum[kThr / 32][32];
   const Dims &d = g.d;
-  const int C = d.C, NR = d.NR, NR2 = NR * NR;
-  const int u = g.nodes[off + blockIdx.y];
+  const int C = d.C;
+  const int idx = off + blockIdx.y;
+  const int u = g.nodes[idx];
   const int slot = u - d.N;
-  const bool is_root = (u == g.root);
-  const int x0 = g.child[2 * slot], x1 = g.child[2 * slot + 1];
-  const Kid k0 = classify(g, x0), k1 = classify(g, x1);
+  const bool is_root = (u == g.root), store = idx < g.top_begin;
+  Kid k0 = classify(g, g.child[2 * slot]), k1 = classify(g, g.child[2 * slot + 1]);
+  if (k0.kind > k1.kind) {
+    const Kid t = k0;
+    k0 = k1;
+    k1 = t;
+  }
   float4 *t0 = tabs, *t1 = tabs + table_size(g, k0, true);
+  float4 *Ltip = t1 + table_size(g, k1, true);
+  float4 *stage = tabs + 2 * C * (2 * d.NR * d.NR + 4) + d.NR;  // after the largest table set
   load_table(g, k0, true, t0);
   load_table(g, k1, true, t1);
-  const int GS = kThr / Cp;
-  const int c = threadIdx.x / GS, lp = threadIdx.x % GS;
-  const bool cact = c < C;
-  const int cc = cact ? c : 0;
-  const float wc = (float)g.catw[cc];
-  const float4 pi4 = make_float4((float)g.pi[0], (float)g.pi[1], (float)g.pi[2], (float)g.pi[3]);
+  for (int i = threadIdx.x; i < d.NR; i += blockDim.x) Ltip[i] = onehot(i, g.masks);
   __syncthreads();
-  // this category's table views
-  const float4 *S0t = k0.kind == 0 ? t0 + cc * NR : (k0.kind == 1 ? t0 + cc * NR2 : nullptr);
-  const float4 *S1t = k1.kind == 0 ? t1 + cc * NR : (k1.kind == 1 ? t1 + cc * NR2 : nullptr);
-  const float4 *L0t = k0.kind == 1 ? t0 + C * NR2 + cc * NR2 : nullptr;
-  const float4 *L1t = k1.kind == 1 ? t1 + C * NR2 + cc * NR2 : nullptr;
-  const float4 *P0 = k0.kind == 0 ? t0 + cc * NR : (k0.kind == 1 ? t0 + 2 * C * NR2 + 4 * cc : t0 + 4 * cc);
-  const float4 *P1 = k1.kind == 0 ? t1 + cc * NR : (k1.kind == 1 ? t1 + 2 * C * NR2 + 4 * cc : t1 + 4 * cc);
   float acc[32];
 #pragma unroll
   for (int q = 0; q < 32; q++) acc[q] = 0.f;
-  const int p0 = blockIdx.x * kTP;
-  if (cact) {
-    for (int kb = 0; kb < Cp; kb += kBatch) {
-      float4 uu[kBatch], L0[kBatch], L1[kBatch];
-      int e[kBatch], i0[kBatch], i1[kBatch];
-      float n[kBatch];
-      bool act[kBatch];
-#pragma unroll
-      for (int k = 0; k < kBatch; k++) {
-        const int p = p0 + lp + GS * (kb + k);
-        act[k] = (kb + k < Cp) && p < d.P;
-        const int pc = act[k] ? p : 0;
-        e[k] = g.scale[(size_t)slot * d.Pp + pc];
-        n[k] = act[k] ? g.pwf[pc] : 0.f;
-        if (is_root) {
-          const float w = wc * (float)g.site_inv[pc];
-          uu[k] = make_float4(w * pi4.x, w * pi4.y, w * pi4.z, w * pi4.w);
-        } else {
-          uu[k] = __ldg(g.pre + ((size_t)slot * C + cc) * d.P + pc);
-        }
-        if (k0.kind == 2) L0[k] = __ldg(g.part + ((size_t)(x0 - d.N) * C + cc) * d.P + pc);
-        else if (k0.kind == 1) i0[k] = g.tips[(size_t)k0.a * d.Pp + pc] * NR + g.tips[(size_t)k0.b * d.Pp + pc];
-        else i0[k] = g.tips[(size_t)x0 * d.Pp + pc];
-        if (k1.kind == 2) L1[k] = __ldg(g.part + ((size_t)(x1 - d.N) * C + cc) * d.P + pc);
-        else if (k1.kind == 1) i1[k] = g.tips[(size_t)k1.a * d.Pp + pc] * NR + g.tips[(size_t)k1.b * d.Pp + pc];
-        else i1[k] = g.tips[(size_t)x1 * d.Pp + pc];
-      }
-#pragma unroll
-      for (int k = 0; k < kBatch; k++) {
-        if (k0.kind == 1) L0[k] = L0t[i0[k]];
-        else if (k0.kind == 0) L0[k] = onehot(i0[k], g.masks);
-        if (k1.kind == 1) L1[k] = L1t[i1[k]];
-        else if (k1.kind == 0) L1[k] = onehot(i1[k], g.masks);
-        const float4 S0 = k0.kind == 2 ? matvec_t(P0, L0[k]) : S0t[i0[k]];
-        const float4 S1 = k1.kind == 2 ? matvec_t(P1, L1[k]) : S1t[i1[k]];
-        const float4 X0 = pow2_scale(mul4(uu[k], S1), e[k]);
-        const float4 X1 = pow2_scale(mul4(uu[k], S0), e[k]);
-        const int p = p0 + lp + GS * (kb + k);
-        if (act[k] && k0.kind != 0) g.pre[((size_t)(x0 - d.N) * C + cc) * d.P + p] = matvec(P0, X0);
-        if (act[k] && k1.kind != 0) g.pre[((size_t)(x1 - d.N) * C + cc) * d.P + p] = matvec(P1, X1);
-        const float xa[4] = {X0.x * n[k], X0.y * n[k], X0.z * n[k], X0.w * n[k]};
-        const float xb[4] = {X1.x * n[k], X1.y * n[k], X1.z * n[k], X1.w * n[k]};
-        const float la[4] = {L0[k].x, L0[k].y, L0[k].z, L0[k].w};
-        const float lb[4] = {L1[k].x, L1[k].y, L1[k].z, L1[k].w};
-#pragma unroll
-        for (int i = 0; i < 4; i++)
-#pragma unroll
-          for (int j = 0; j < 4; j++) {
-            acc[i * 4 + j] += xa[i] * la[j];
-            acc[16 + i * 4 + j] += xb[i] * lb[j];
-          }
-      }
-    }
+  switch (k0.kind * 3 + k1.kind) {
+    case 0: pre_node<kTip, kTip>(g, slot, is_root, store, k0, k1, t0, t1, Ltip, stage, Cp, m, acc); break;
+    case 1: pre_node<kTip, kCherry>(g, slot, is_root, store, k0, k1, t0, t1, Ltip, stage, Cp, m, acc); break;
+    case 2: pre_node<kTip, kStored>(g, slot, is_root, store, k0, k1, t0, t1, Ltip, stage, Cp, m, acc); break;
+    case 4: pre_node<kCherry, kCherry>(g, slot, is_root, store, k0, k1, t0, t1, Ltip, stage, Cp, m, acc); break;
+    case 5: pre_node<kCherry, kStored>(g, slot, is_root, store, k0, k1, t0, t1, Ltip, stage, Cp, m, acc); break;
+    default: pre_node<kStored, kStored>(g, slot, is_root, store, k0, k1, t0, t1, Ltip, stage, Cp, m, acc); break;
   }
   // per-warp transpose: lane l sums value l; then the warps of a category
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
@@ -329,29 +460,207 @@ __global__ void __launch_bounds__(kThr, 2) k4_pre(K4Args g, int off, int Cp) {
   for (int k = 0; k < 32; k++) s += red[warp][lane][k];
   wsum[warp][lane] = s;
   __syncthreads();
+  const int GS = kThr / Cp;
   const int wpc = (GS + 31) / 32;
-  for (int idx = threadIdx.x; idx < C * 32; idx += blockDim.x) {
-    const int cq = idx >> 5, l = idx & 31;
+  for (int i = threadIdx.x; i < C * 32; i += blockDim.x) {
+    const int cq = i >> 5, l = i & 31;
     float tot = 0.f;
     for (int k = 0; k < wpc; k++) tot += wsum[cq * wpc + k][l];
-    const int br = (l < 16) ? x0 : x1;
-    g.Gpart[(((size_t)br * g.ntile + blockIdx.x) * C + cq) * 16 + (l & 15)] = tot;
+    const int br = (l < 16) ? k0.node : k1.node;
+    g.Gpart[(((size_t)br * g.gstride + blockIdx.x) * C + cq) * 16 + (l & 15)] = tot;
+  }
+}
+
+// ---- walks over the narrow top of the tree ---------------------------------------
+// Step descriptor, four int4 (built by k4_schedule):
+//   w[0] = {u, value slot (post: out, pre: in; -1 none), u is the root, 0}
+//   w[1], w[2] = the children {kind, node, tip a, tip b}
+//   w[3] = {child 0 slot, child 1 slot, 0, 0}  (post: where a stored child's
+//          value is; pre: where the child's U goes; -1 = not in the walk)
+// Shared memory of a walk CTA: the descriptors [steps][4] int4, the first
+// four table rows of every non-tip child [steps][2][C][4] float4, then the
+// value slots [slots][kWalkThr] float4.
+// Thread = (pattern pl, category c), lane = pl * CP + c.  A thread loads the
+// global operands of step i + kWalkDepth while it computes step i (a register
+// ring; the step loop is unrolled by kWalkDepth so the ring is indexed
+// statically), so the walk waits on memory only at its start.
+constexpr int kWalkDepth = 4;
+
+struct WalkOp {
+  float4 l0, l1;  // stored child: its partial; tip / cherry: table index in .x
+  int e;          // pre-order: scale exponent of u
+};
+
+__device__ __forceinline__ float4 walk_load(const K4Args &g, int4 k, bool in_slot, int c, int p) {
+  const Dims &d = g.d;
+  if (k.x == kTip) return make_float4(__int_as_float(g.tips[(size_t)k.y * d.Pp + p]), 0.f, 0.f, 0.f);
+  if (k.x == kCherry)
+    return make_float4(
+        __int_as_float(g.tips[(size_t)k.z * d.Pp + p] * d.NR + g.tips[(size_t)k.w * d.Pp + p]), 0.f,
+        0.f, 0.f);
+  if (in_slot) return make_float4(0.f, 0.f, 0.f, 0.f);
+  return g.part[((size_t)(k.y - d.N) * d.C + c) * d.P + p];
+}
+
+template <bool POST>
+__device__ __forceinline__ void walk_fetch(const K4Args &g, const int4 *sd, int s, int nsteps, int c,
+                                           int p, WalkOp &f) {
+  if (s >= nsteps) return;
+  const int4 h = sd[4 * s], q0 = sd[4 * s + 1], q1 = sd[4 * s + 2], sl = sd[4 * s + 3];
+  f.l0 = walk_load(g, q0, POST && sl.x >= 0, c, p);
+  f.l1 = walk_load(g, q1, POST && sl.y >= 0, c, p);
+  if (!POST) f.e = g.scale[(size_t)(h.x - g.d.N) * g.d.Pp + p];
+}
+
+// S = P_x L_x of child q for category c; rows = its staged first four rows
+__device__ __forceinline__ float4 walk_S(const K4Args &g, int4 q, float4 op, const float4 *rows,
+                                         const float4 *slotv, int c) {
+  const Dims &d = g.d;
+  if (q.x == kTip) return __ldg(g.PT + ((size_t)q.y * d.C + c) * d.NR + __float_as_int(op.x));
+  if (q.x == kCherry)
+    return __ldg(g.pairS + ((size_t)q.y * d.C + c) * d.NR * d.NR + __float_as_int(op.x));
+  return matvec_t(rows, slotv ? *slotv : op);
+}
+
+// Stages the descriptors and the table rows; returns the value slots.
+__device__ float4 *walk_stage(const K4Args &g, const int4 *__restrict__ W, int nsteps, float4 *sm) {
+  const Dims &d = g.d;
+  const int C = d.C;
+  int4 *sd = reinterpret_cast<int4 *>(sm);
+  float4 *rows = sm + 4 * nsteps;
+  for (int i = threadIdx.x; i < 4 * nsteps; i += blockDim.x) sd[i] = W[i];
+  for (int i = threadIdx.x; i < nsteps * 8 * C; i += blockDim.x) {
+    const int s = i / (8 * C), r = i % (8 * C), side = r / (4 * C), cr = r % (4 * C);
+    const int4 q = W[4 * s + 1 + side];
+    if (q.x != kTip) rows[i] = g.PT[((size_t)q.y * C + cr / 4) * d.NR + (cr & 3)];
+  }
+  __syncthreads();
+  return rows + (size_t)nsteps * 8 * C;
+}
+
+template <int CP>
+__global__ void __launch_bounds__(kWalkThr) k4_walk_post(K4Args g, const int4 *__restrict__ W,
+                                                         int nsteps) {
+  extern __shared__ float4 sm[];
+  const Dims &d = g.d;
+  const int C = d.C;
+  float4 *vals = walk_stage(g, W, nsteps, sm);
+  const int4 *sd = reinterpret_cast<const int4 *>(sm);
+  const float4 *rows = sm + 4 * nsteps;
+  const int c = threadIdx.x % CP, pl = threadIdx.x / CP;
+  const int p = blockIdx.x * (kWalkThr / CP) + pl;
+  const bool act = c < C && p < d.P;
+  const int cc = c < C ? c : 0, pc = p < d.P ? p : 0;
+  WalkOp ring[kWalkDepth];
+#pragma unroll
+  for (int k = 0; k < kWalkDepth; k++) walk_fetch<true>(g, sd, k, nsteps, cc, pc, ring[k]);
+  for (int i0 = 0; i0 < nsteps; i0 += kWalkDepth) {
+#pragma unroll
+    for (int k = 0; k < kWalkDepth; k++) {
+      const int i = i0 + k;
+      if (i < nsteps) {
+        const WalkOp f = ring[k];
+        walk_fetch<true>(g, sd, i + kWalkDepth, nsteps, cc, pc, ring[k]);
+        const int4 h = sd[4 * i], q0 = sd[4 * i + 1], q1 = sd[4 * i + 2], sl = sd[4 * i + 3];
+        const float4 *r0 = rows + (size_t)i * 8 * C + 4 * cc;
+        const float4 *r1 = r0 + 4 * C;
+        const float4 s0 = walk_S(g, q0, f.l0, r0, sl.x >= 0 ? vals + sl.x * kWalkThr + threadIdx.x : nullptr, cc);
+        const float4 s1 = walk_S(g, q1, f.l1, r1, sl.y >= 0 ? vals + sl.y * kWalkThr + threadIdx.x : nullptr, cc);
+        const float4 acc = act ? mul4(s0, s1) : make_float4(0.f, 0.f, 0.f, 0.f);
+        float mx = max4(acc);
+#pragma unroll
+        for (int o = 1; o < CP; o <<= 1) mx = fmaxf(mx, __shfl_xor_sync(0xffffffffu, mx, o));
+        int e = 0;
+        if (!(mx <= 3.0e38f)) {
+          if (c == 0) atomicOr(g.status, ST_NONFINITE);
+        } else {
+          e = binary_exponent(mx);
+        }
+        const float4 v = pow2_scale(acc, e);
+        const int slot = h.x - d.N;
+        if (act) g.part[((size_t)slot * C + c) * d.P + p] = v;
+        if (c == 0 && p < d.P) g.scale[(size_t)slot * d.Pp + p] = (int16_t)e;
+        if (h.z) {
+          double site = act ? g.catw[c] * ((double)v.x * g.pi[0] + (double)v.y * g.pi[1] +
+                                           (double)v.z * g.pi[2] + (double)v.w * g.pi[3])
+                            : 0.0;
+#pragma unroll
+          for (int o = 1; o < CP; o <<= 1) site += __shfl_xor_sync(0xffffffffu, site, o);
+          if (c == 0 && p < d.P) {
+            g.site_log[p] = log(site);
+            g.site_inv[p] = site > 0.0 ? 1.0 / site : 0.0;
+          }
+        } else if (h.y >= 0) {
+          vals[h.y * kWalkThr + threadIdx.x] = v;
+        }
+      }
+    }
+  }
+}
+
+template <int CP>
+__global__ void __launch_bounds__(kWalkThr) k4_walk_pre(K4Args g, const int4 *__restrict__ W,
+                                                        int nsteps) {
+  extern __shared__ float4 sm[];
+  const Dims &d = g.d;
+  const int C = d.C;
+  float4 *vals = walk_stage(g, W, nsteps, sm);
+  const int4 *sd = reinterpret_cast<const int4 *>(sm);
+  const float4 *rows = sm + 4 * nsteps;
+  const int c = threadIdx.x % CP, pl = threadIdx.x / CP;
+  const int p = blockIdx.x * (kWalkThr / CP) + pl;
+  const bool act = c < C && p < d.P;
+  const int cc = c < C ? c : 0, pc = p < d.P ? p : 0;
+  const double wcd = g.catw[cc];
+  const float4 pi4 = make_float4((float)g.pi[0], (float)g.pi[1], (float)g.pi[2], (float)g.pi[3]);
+  WalkOp ring[kWalkDepth];
+#pragma unroll
+  for (int k = 0; k < kWalkDepth; k++) walk_fetch<false>(g, sd, k, nsteps, cc, pc, ring[k]);
+  for (int i0 = 0; i0 < nsteps; i0 += kWalkDepth) {
+#pragma unroll
+    for (int k = 0; k < kWalkDepth; k++) {
+      const int i = i0 + k;
+      if (i < nsteps) {
+        const WalkOp f = ring[k];
+        walk_fetch<false>(g, sd, i + kWalkDepth, nsteps, cc, pc, ring[k]);
+        const int4 h = sd[4 * i], q0 = sd[4 * i + 1], q1 = sd[4 * i + 2], sl = sd[4 * i + 3];
+        const float4 *r0 = rows + (size_t)i * 8 * C + 4 * cc;
+        const float4 *r1 = r0 + 4 * C;
+        const float4 uu = h.z ? scl4(pi4, (float)(wcd * g.site_inv[pc]))
+                              : vals[h.y * kWalkThr + threadIdx.x];
+        const float4 s0 = walk_S(g, q0, f.l0, r0, nullptr, cc);
+        const float4 s1 = walk_S(g, q1, f.l1, r1, nullptr, cc);
+        if (q0.x != kTip) {
+          const float4 U = matvec(r0, pow2_scale(mul4(uu, s1), f.e));
+          if (act) g.pre[((size_t)(q0.y - d.N) * C + c) * d.P + p] = U;
+          if (sl.x >= 0) vals[sl.x * kWalkThr + threadIdx.x] = U;
+        }
+        if (q1.x != kTip) {
+          const float4 U = matvec(r1, pow2_scale(mul4(uu, s0), f.e));
+          if (act) g.pre[((size_t)(q1.y - d.N) * C + c) * d.P + p] = U;
+          if (sl.y >= 0) vals[sl.y * kWalkThr + threadIdx.x] = U;
+        }
+      }
+    }
   }
 }
 
 // G[v][c][ij] = sum over the tiles of branch v, FP64, fixed order.
-__global__ void k4_G_reduce(Dims d, int ntile, const int *__restrict__ parent,
-                            const float *__restrict__ Gpart, double *__restrict__ G) {
+__global__ void k4_G_reduce(Dims d, int gstride, const int *__restrict__ parent,
+                            const int *__restrict__ nt, const float *__restrict__ Gpart,
+                            double *__restrict__ G) {
   const long long idx = (long long)blockIdx.x * blockDim.x + threadIdx.x;
   if (idx >= (long long)d.nn * d.C * 16) return;
   const int ij = (int)(idx & 15);
   const int c = (int)((idx >> 4) % d.C);
   const int v = (int)(idx / (16LL * d.C));
   double acc = 0.0;
-  if (parent[v] >= 0)
+  if (parent[v] >= 0) {
+    const int n = nt[v];
+    const float *src = Gpart + ((size_t)v * gstride * d.C + c) * 16 + ij;
 #pragma unroll 8
-    for (int t = 0; t < ntile; t++)
-      acc += (double)Gpart[(((size_t)v * ntile + t) * d.C + c) * 16 + ij];
+    for (int t = 0; t < n; t++) acc += (double)src[(size_t)t * d.C * 16];
+  }
   G[idx] = acc;
 }
 
@@ -426,14 +735,21 @@ K4Args make_args(epoch_ctx *c) {
   a.site_log = c->d_site_log;
   a.site_inv = c->d_site_inv;
   a.Gpart = (float *)c->d_Gpart;
-  a.ntile = ceil_div(c->d.P, kTP);
+  a.gstride = k4_tiles(c->d.P);
+  a.top_begin = c->k4_top_begin;
   a.status = c->d_status;
   return a;
 }
 
-// largest table set of a node: two cherry children in the pre-order pass
+// largest table set of a node: two cherry children in the pre-order pass,
+// plus the one-hot rows of the tip codes
 size_t table_smem(const Dims &d) {
-  return sizeof(float4) * 2 * d.C * (2 * d.NR * d.NR + 4);
+  return sizeof(float4) * (2 * d.C * (2 * d.NR * d.NR + 4) + d.NR);
+}
+size_t pre_smem(const Dims &d) { return table_smem(d) + sizeof(float4) * kStageF4; }
+
+size_t walk_smem(int C, int nsteps, int slots) {
+  return sizeof(float4) * ((size_t)nsteps * (4 + 8 * C) + (size_t)kWalkThr * slots);
 }
 
 int pow2_at_least(int x) {
@@ -442,17 +758,48 @@ int pow2_at_least(int x) {
   return p;
 }
 
+template <int CP>
+cudaError_t walk(epoch_ctx *c, bool post) {
+  K4Args a = make_args(c);
+  const int n = post ? c->k4_walk_post : c->k4_walk_pre;
+  if (n == 0) return cudaSuccess;
+  const int4 *W = c->d_k4_walk + (post ? 0 : 4 * c->k4_walk_post);
+  const int slots = post ? c->k4_slots_post : c->k4_slots_pre;
+  const size_t smem = walk_smem(c->d.C, n, slots);
+  const int grid = ceil_div(c->d.P, kWalkThr / CP);
+  if (post) {
+    cudaFuncSetAttribute(k4_walk_post<CP>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    k4_walk_post<CP><<<grid, kWalkThr, smem, c->stream>>>(a, W, n);
+  } else {
+    cudaFuncSetAttribute(k4_walk_pre<CP>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    k4_walk_pre<CP><<<grid, kWalkThr, smem, c->stream>>>(a, W, n);
+  }
+  c->launches++;
+  return cudaGetLastError();
+}
+
+cudaError_t walk_dispatch(epoch_ctx *c, bool post) {
+  switch (pow2_at_least(c->d.C)) {
+    case 1: return walk<1>(c, post);
+    case 2: return walk<2>(c, post);
+    case 4: return walk<4>(c, post);
+    default: return walk<8>(c, post);
+  }
+}
+
 template <int CMAX>
 cudaError_t post(epoch_ctx *c) {
   K4Args a = make_args(c);
-  const int L = (int)c->h_level_off.size() - 1;
   const size_t smem = table_smem(c->d);
   cudaFuncSetAttribute(k4_post<CMAX>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
-  for (int l = c->k4_first_level; l < L; l++) {
+  const int last = std::max(c->k4_top, c->k4_first_level);
+  for (int l = c->k4_first_level; l < last; l++) {
     const int w = c->h_level_off[l + 1] - c->h_level_off[l];
-    k4_post<CMAX><<<dim3(a.ntile, w), kThr, smem, c->stream>>>(a, c->h_level_off[l]);
+    k4_post<CMAX><<<dim3(k4_tiles(c->d.P), w), kThr, smem, c->stream>>>(a, c->h_level_off[l]);
     c->launches++;
   }
+  cudaError_t err = walk_dispatch(c, true);
+  if (err != cudaSuccess) return err;
   cudaMemsetAsync(c->d_ctl, 0, sizeof(int), c->stream);
   k4_site_lnl<<<ceil_div(c->d.P, 32), 256, 0, c->stream>>>(c->d, c->d_scale, c->d_site_log,
                                                            c->d_pw, c->d_site_lnl,
@@ -461,20 +808,20 @@ cudaError_t post(epoch_ctx *c) {
   return cudaGetLastError();
 }
 
-template <int CMAX>
 cudaError_t pre(epoch_ctx *c) {
   K4Args a = make_args(c);
-  const int L = (int)c->h_level_off.size() - 1;
-  const size_t smem = table_smem(c->d);
-  cudaFuncSetAttribute(k4_pre<CMAX>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+  const size_t smem = pre_smem(c->d);
+  cudaFuncSetAttribute(k4_pre, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
   const int Cp = pow2_at_least(c->d.C);
-  for (int l = L - 1; l >= 0; l--) {
-    const int w = c->h_level_off[l + 1] - c->h_level_off[l];
-    k4_pre<CMAX><<<dim3(a.ntile, w), kThr, smem, c->stream>>>(a, c->h_level_off[l], Cp);
+  cudaError_t err = walk_dispatch(c, false);
+  if (err != cudaSuccess) return err;
+  for (size_t i = 0; i + 2 < c->h_k4_launch.size(); i += 3) {
+    const int off = c->h_k4_launch[i], w = c->h_k4_launch[i + 1], m = c->h_k4_launch[i + 2];
+    k4_pre<<<dim3(ceil_div(c->d.P, kTP * m), w), kThr, smem, c->stream>>>(a, off, Cp, m);
     c->launches++;
   }
   const long long nG = (long long)c->d.nn * c->d.C * 16;
-  k4_G_reduce<<<ceil_div(nG, 256), 256, 0, c->stream>>>(c->d, a.ntile, c->d_parent,
+  k4_G_reduce<<<ceil_div(nG, 256), 256, 0, c->stream>>>(c->d, a.gstride, c->d_parent, c->d_k4_nt,
                                                         (const float *)c->d_Gpart, c->d_G);
   c->launches++;
   return cudaGetLastError();
@@ -483,6 +830,144 @@ cudaError_t pre(epoch_ctx *c) {
 }  // namespace
 
 int k4_tiles(int P) { return (P + kTP - 1) / kTP; }
+
+// Host schedule of the K = 4 passes for the current topology.
+//   * walks: the top levels [k4_top, L) whose widths are all <= kWalkWidth
+//     (the root's level always), as long as both walks fit kWalkSlots value
+//     slots per thread; the post-order walk starts at max(k4_top,
+//     k4_first_level) because unstored cherries are read from their tables.
+//   * adjoint launches, top down: levels k4_top-1 .. 0, the first of them
+//     extended over the walk's nodes, whose U the walk already stored (their
+//     level-order index is >= k4_top_begin, so the kernel skips the stores)
+//     and for which it only forms G.  m = fine tiles per CTA, the largest of
+//     4, 2, 1 that still gives >= 4 CTAs per SM.
+//   * nt[v]: tiles of the launch that handled v's parent (G tile count).
+void k4_schedule(epoch_ctx *c) {
+  const Dims &d = c->d;
+  const int N = d.N, nn = d.nn;
+  const int L = (int)c->h_level_off.size() - 1;
+  const std::vector<int> &off = c->h_level_off, &nodes = c->h_level_nodes, &child = c->h_child;
+  std::vector<int> lvl(nn, -1);
+  for (int l = 0; l < L; l++)
+    for (int i = off[l]; i < off[l + 1]; i++) lvl[nodes[i]] = l;
+  auto kind_of = [&](int x) {
+    if (x < N) return (int)kTip;
+    const int a = child[2 * (x - N)], b = child[2 * (x - N) + 1];
+    return (a < N && b < N && x != c->root) ? (int)kCherry : (int)kStored;
+  };
+  auto kid_desc = [&](int x) {
+    int4 q{kind_of(x), x, -1, -1};
+    if (q.x == kCherry) {
+      q.z = child[2 * (x - N)];
+      q.w = child[2 * (x - N) + 1];
+    }
+    return q;
+  };
+  int top = L - 1;
+  while (top > 0 && off[top] - off[top - 1] <= kWalkWidth) top--;
+  std::vector<int4> post_steps, pre_steps;
+  int slots_post = 0, slots_pre = 0;
+  for (;; top++) {
+    post_steps.clear();
+    pre_steps.clear();
+    const int pfirst = std::max(top, c->k4_first_level);
+    // post-order walk: level-ascending; a value lives until its parent's step
+    std::vector<int> slot_of(nn, -1), free_slots;
+    int nslot = 0;
+    for (int i = off[pfirst]; i < off[L]; i++) {
+      const int u = nodes[i];
+      const int x0 = child[2 * (u - N)], x1 = child[2 * (u - N) + 1];
+      int4 sl{-1, -1, 0, 0};
+      if (x0 >= N && lvl[x0] >= pfirst && kind_of(x0) == kStored) sl.x = slot_of[x0];
+      if (x1 >= N && lvl[x1] >= pfirst && kind_of(x1) == kStored) sl.y = slot_of[x1];
+      if (sl.x >= 0) free_slots.push_back(sl.x);
+      if (sl.y >= 0) free_slots.push_back(sl.y);
+      int out = -1;
+      if (u != c->root) {
+        if (!free_slots.empty()) {
+          out = free_slots.back();
+          free_slots.pop_back();
+        } else {
+          out = nslot++;
+        }
+        slot_of[u] = out;
+      }
+      post_steps.push_back(int4{u, out, u == c->root ? 1 : 0, 0});
+      post_steps.push_back(kid_desc(x0));
+      post_steps.push_back(kid_desc(x1));
+      post_steps.push_back(sl);
+    }
+    slots_post = nslot;
+    // pre-order walk: level-descending; a U lives from its parent's step to
+    // its own
+    std::fill(slot_of.begin(), slot_of.end(), -1);
+    free_slots.clear();
+    nslot = 0;
+    for (int l = L - 1; l >= top; l--)
+      for (int i = off[l]; i < off[l + 1]; i++) {
+        const int u = nodes[i];
+        const int x0 = child[2 * (u - N)], x1 = child[2 * (u - N) + 1];
+        if (x0 < N && x1 < N) continue;  // no U to form below u
+        const int in = slot_of[u];
+        if (in >= 0) free_slots.push_back(in);
+        int4 sl{-1, -1, 0, 0};
+        auto take = [&]() {
+          if (!free_slots.empty()) {
+            const int s = free_slots.back();
+            free_slots.pop_back();
+            return s;
+          }
+          return nslot++;
+        };
+        // a child that is itself a later step keeps its U in a slot
+        if (x0 >= N && lvl[x0] >= top && kind_of(x0) == kStored) slot_of[x0] = sl.x = take();
+        if (x1 >= N && lvl[x1] >= top && kind_of(x1) == kStored) slot_of[x1] = sl.y = take();
+        pre_steps.push_back(int4{u, in, u == c->root ? 1 : 0, 0});
+        pre_steps.push_back(kid_desc(x0));
+        pre_steps.push_back(kid_desc(x1));
+        pre_steps.push_back(sl);
+      }
+    slots_pre = nslot;
+    const bool fits = slots_post <= kWalkSlots && slots_pre <= kWalkSlots &&
+                      walk_smem(d.C, (int)post_steps.size() / 4, slots_post) <= kWalkSmem &&
+                      walk_smem(d.C, (int)pre_steps.size() / 4, slots_pre) <= kWalkSmem;
+    if (fits || top >= L - 1) break;
+  }
+  c->k4_top = top;
+  c->k4_top_begin = off[top];
+  c->k4_walk_post = (int)post_steps.size() / 4;
+  c->k4_walk_pre = (int)pre_steps.size() / 4;
+  c->k4_slots_post = slots_post;
+  c->k4_slots_pre = slots_pre;
+  c->h_k4_walk = post_steps;
+  c->h_k4_walk.insert(c->h_k4_walk.end(), pre_steps.begin(), pre_steps.end());
+  // adjoint launches
+  const int T0 = k4_tiles(d.P);
+  const long long want = 4LL * 148;  // CTAs: >= 2 per SM at 2 resident per SM
+  auto pick_m = [&](int w) {
+    for (int m = 4; m > 1; m >>= 1)
+      if ((long long)w * ((T0 + m - 1) / m) >= want) return m;
+    return 1;
+  };
+  c->h_k4_launch.clear();
+  c->h_k4_nt.assign(nn, 0);
+  auto add_launch = [&](int first, int count) {
+    const int m = pick_m(count);
+    c->h_k4_launch.insert(c->h_k4_launch.end(), {first, count, m});
+    const int nt = (T0 + m - 1) / m;
+    for (int i = first; i < first + count; i++) {
+      const int u = nodes[i];
+      c->h_k4_nt[child[2 * (u - N)]] = nt;
+      c->h_k4_nt[child[2 * (u - N) + 1]] = nt;
+    }
+  };
+  if (top == 0) {
+    add_launch(0, off[L]);
+  } else {
+    add_launch(off[top - 1], off[L] - off[top - 1]);
+    for (int l = top - 2; l >= 0; l--) add_launch(off[l], off[l + 1] - off[l]);
+  }
+}
 
 cudaError_t launch_pair_tables_k4(epoch_ctx *c) {
   if (c->d.N < 2) return cudaSuccess;
@@ -499,9 +984,6 @@ cudaError_t launch_partials_k4(epoch_ctx *c) {
   return post<8>(c);
 }
 
-cudaError_t launch_preorder_k4(epoch_ctx *c) {
-  if (c->d.C <= 4) return pre<4>(c);
-  return pre<8>(c);
-}
+cudaError_t launch_preorder_k4(epoch_ctx *c) { return pre(c); }
 
 }  // namespace epoch
