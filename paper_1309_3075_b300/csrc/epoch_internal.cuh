@@ -184,6 +184,7 @@ void k4_schedule(epoch_ctx *c);                 // host: walks, launches, tile c
 // k_k4small.cu (FP32, K = 4, reversible): per-(branch, category) threads
 cudaError_t launch_branch_k4(epoch_ctx *c);     // segments + branch matrices + tables
 cudaError_t launch_chain_k4(epoch_ctx *c);      // chain rule through the products
+size_t k4_chain_smem(const Dims &d);            // its shared memory (model tables)
 
 // FP32, K = 4, at most 8 categories and 3 ambiguity masks (NR <= 8)
 inline bool fast_k4(const epoch_ctx *c) {

@@ -543,7 +543,7 @@ cudaError_t launch_chain_rule(epoch_ctx *c) {
         d, c->d_parent, c->d_child, c->d_nseg, c->d_seg_dt, c->d_seg_hi, c->d_seg_lo, c->d_brate,
         c->d_catr, (const double *)c->d_gseg, nb_nodes, c->d_grad);
   } else {
-    if (fast_k4(c) && d.reversible) {
+    if (fast_k4(c) && d.reversible && k4_chain_smem(d) <= 160 * 1024) {
       cudaError_t e = launch_chain_k4(c);
       if (e != cudaSuccess) return e;
       c->launches--;  // counted below with the reduction

@@ -645,48 +645,57 @@ __global__ void __launch_bounds__(kWalkThr) k4_walk_pre(K4Args g, const int4 *__
   }
 }
 
-// G[v][c][ij] = sum over the tiles of branch v, FP64, fixed order.
+// G[v][c][ij] = sum over the tiles of branch v, FP64, fixed order: the four
+// threads of a quad take every fourth tile and combine by shuffles.
 __global__ void k4_G_reduce(Dims d, int gstride, const int *__restrict__ parent,
                             const int *__restrict__ nt, const float *__restrict__ Gpart,
                             double *__restrict__ G) {
-  const long long idx = (long long)blockIdx.x * blockDim.x + threadIdx.x;
-  if (idx >= (long long)d.nn * d.C * 16) return;
-  const int ij = (int)(idx & 15);
-  const int c = (int)((idx >> 4) % d.C);
-  const int v = (int)(idx / (16LL * d.C));
+  const long long t4 = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+  const long long idx = t4 >> 2;
+  const int part = (int)(t4 & 3);
+  const bool live = idx < (long long)d.nn * d.C * 16;
   double acc = 0.0;
-  if (parent[v] >= 0) {
-    const int n = nt[v];
-    const float *src = Gpart + ((size_t)v * gstride * d.C + c) * 16 + ij;
-#pragma unroll 8
-    for (int t = 0; t < n; t++) acc += (double)src[(size_t)t * d.C * 16];
+  if (live) {
+    const int ij = (int)(idx & 15);
+    const int c = (int)((idx >> 4) % d.C);
+    const int v = (int)(idx / (16LL * d.C));
+    if (parent[v] >= 0) {
+      const int n = nt[v];
+      const float *src = Gpart + ((size_t)v * gstride * d.C + c) * 16 + ij;
+#pragma unroll 4
+      for (int t = part; t < n; t += 4) acc += (double)src[(size_t)t * d.C * 16];
+    }
   }
-  G[idx] = acc;
+  acc += __shfl_xor_sync(0xffffffffu, acc, 1);
+  acc += __shfl_xor_sync(0xffffffffu, acc, 2);
+  if (live && part == 0) G[idx] = acc;
 }
 
 // lnL_p = log(scaled root sum) + ln2 * sum_u e_u(p); block sums of n_p lnL_p
-// reduced in a fixed order by the last block to finish.
-__global__ void __launch_bounds__(256) k4_site_lnl(Dims d, const int16_t *__restrict__ scale,
-                                                   const double *__restrict__ site_log,
-                                                   const double *__restrict__ pw,
-                                                   double *__restrict__ site_lnl,
-                                                   double *__restrict__ part, int *ctl,
-                                                   double *__restrict__ lnl) {
-  __shared__ int es[8][32];
-  __shared__ double redd[8];
+// reduced in a fixed order by the last block to finish.  Block = 32 patterns
+// x 32 warps; warp w adds the exponents of nodes w, w + 32, ...
+constexpr int kLnlWarps = 32;
+__global__ void __launch_bounds__(32 * kLnlWarps) k4_site_lnl(Dims d, const int16_t *__restrict__ scale,
+                                                              const double *__restrict__ site_log,
+                                                              const double *__restrict__ pw,
+                                                              double *__restrict__ site_lnl,
+                                                              double *__restrict__ part, int *ctl,
+                                                              double *__restrict__ lnl) {
+  __shared__ int es[kLnlWarps][33];
+  __shared__ double redd[kLnlWarps];
   __shared__ int s_last;
   const int pl = threadIdx.x & 31, gi = threadIdx.x >> 5;
   const int p = blockIdx.x * 32 + pl;
   int acc = 0;
   if (p < d.P)
-#pragma unroll 8
-    for (int s = gi; s < d.N - 1; s += 8) acc += scale[(size_t)s * d.Pp + p];
+#pragma unroll 4
+    for (int s = gi; s < d.N - 1; s += kLnlWarps) acc += scale[(size_t)s * d.Pp + p];
   es[gi][pl] = acc;
   __syncthreads();
   double contrib = 0.0;
   if (gi == 0 && p < d.P) {
     int tot = 0;
-    for (int k = 0; k < 8; k++) tot += es[k][pl];
+    for (int k = 0; k < kLnlWarps; k++) tot += es[k][pl];
     const double lp = site_log[p] + 0.69314718055994530942 * (double)tot;
     site_lnl[p] = lp;
     const double nw = pw[p];
@@ -710,7 +719,7 @@ __global__ void __launch_bounds__(256) k4_site_lnl(Dims d, const int16_t *__rest
   __syncthreads();
   if (threadIdx.x == 0) {
     double s = 0.0;
-    for (int k = 0; k < 8; k++) s += redd[k];
+    for (int k = 0; k < kLnlWarps; k++) s += redd[k];
     lnl[0] = s;
   }
 }
@@ -801,7 +810,7 @@ cudaError_t post(epoch_ctx *c) {
   cudaError_t err = walk_dispatch(c, true);
   if (err != cudaSuccess) return err;
   cudaMemsetAsync(c->d_ctl, 0, sizeof(int), c->stream);
-  k4_site_lnl<<<ceil_div(c->d.P, 32), 256, 0, c->stream>>>(c->d, c->d_scale, c->d_site_log,
+  k4_site_lnl<<<ceil_div(c->d.P, 32), 32 * kLnlWarps, 0, c->stream>>>(c->d, c->d_scale, c->d_site_log,
                                                            c->d_pw, c->d_site_lnl,
                                                            c->d_lnl_part, c->d_ctl, c->d_lnl);
   c->launches++;
@@ -820,7 +829,7 @@ cudaError_t pre(epoch_ctx *c) {
     k4_pre<<<dim3(ceil_div(c->d.P, kTP * m), w), kThr, smem, c->stream>>>(a, off, Cp, m);
     c->launches++;
   }
-  const long long nG = (long long)c->d.nn * c->d.C * 16;
+  const long long nG = 4LL * c->d.nn * c->d.C * 16;
   k4_G_reduce<<<ceil_div(nG, 256), 256, 0, c->stream>>>(c->d, a.gstride, c->d_parent, c->d_k4_nt,
                                                         (const float *)c->d_Gpart, c->d_G);
   c->launches++;

@@ -133,6 +133,10 @@ __device__ __forceinline__ void mm4(const float *A, const float *B, float *C) {
     }
 }
 
+// Thread = (branch v, category c, quarter q): the four threads of a quad
+// form the same 4 x 4 products (registers) and split the model parameters
+// (q, q + 4, ...).  The eigensystems and V^-1 dQ V of every matrix sit in
+// shared memory as FP32.
 __global__ void __launch_bounds__(128) k4_chain(Dims d, const double *__restrict__ G,
                                                 const int *__restrict__ nseg,
                                                 const int *__restrict__ seg_mat,
@@ -145,8 +149,20 @@ __global__ void __launch_bounds__(128) k4_chain(Dims d, const double *__restrict
                                                 const float *__restrict__ Dth,
                                                 const int *__restrict__ Dnz,
                                                 float *__restrict__ gseg) {
+  extern __shared__ float sm[];
+  float *sV = sm, *sVi = sV + d.S * 16, *slam = sVi + d.S * 16, *sD = slam + d.S * 4;
+  int *sNz = reinterpret_cast<int *>(sD + (size_t)d.np * d.S * 16);
+  for (int i = threadIdx.x; i < d.S * 16; i += blockDim.x) {
+    sV[i] = (float)V[i];
+    sVi[i] = (float)Vinv[i];
+  }
+  for (int i = threadIdx.x; i < d.S * 4; i += blockDim.x) slam[i] = (float)lam[i];
+  for (int i = threadIdx.x; i < d.np * d.S * 16; i += blockDim.x) sD[i] = Dth[i];
+  for (int i = threadIdx.x; i < d.np * d.S; i += blockDim.x) sNz[i] = Dnz[i];
+  __syncthreads();
   const int idx = blockIdx.x * blockDim.x + threadIdx.x;
-  const int v = idx / d.C, c = idx % d.C;
+  const int qq = idx & 3, vc = idx >> 2;
+  const int v = vc / d.C, c = vc % d.C;
   if (v >= d.nn) return;
   const int ns = nseg[v];
   if (ns == 0) return;
@@ -161,16 +177,12 @@ __global__ void __launch_bounds__(128) k4_chain(Dims d, const double *__restrict
   for (int k = 0; k < ns; k++) {
     const int s = seg_mat[v * E + k];
     const float tau = (float)(r * seg_dt[v * E + k]);
-    float li[4], ev[4], Vs[16], Vi[16];
+    const float *Vs = sV + s * 16, *Vi = sVi + s * 16;
+    float li[4], ev[4];
 #pragma unroll
     for (int i = 0; i < 4; i++) {
-      li[i] = (float)lam[s * 4 + i];
+      li[i] = slam[s * 4 + i];
       ev[i] = expf(tau * li[i]);
-    }
-#pragma unroll
-    for (int q = 0; q < 16; q++) {
-      Vs[q] = (float)V[s * 16 + q];
-      Vi[q] = (float)Vinv[s * 16 + q];
     }
     // Z = E_{k+1} ... E_{n-1}
     float Z[16];
@@ -179,17 +191,17 @@ __global__ void __launch_bounds__(128) k4_chain(Dims d, const double *__restrict
     for (int qn = k + 1; qn < ns; qn++) {
       const int s2 = seg_mat[v * E + qn];
       const float t2 = (float)(r * seg_dt[v * E + qn]);
+      const float *V2 = sV + s2 * 16, *Vi2 = sVi + s2 * 16;
       float e2[4], Ek[16], T[16];
 #pragma unroll
-      for (int i = 0; i < 4; i++) e2[i] = expf(t2 * (float)lam[s2 * 4 + i]);
+      for (int i = 0; i < 4; i++) e2[i] = expf(t2 * slam[s2 * 4 + i]);
 #pragma unroll
       for (int i = 0; i < 4; i++)
 #pragma unroll
         for (int j = 0; j < 4; j++) {
           float acc = 0.f;
 #pragma unroll
-          for (int m = 0; m < 4; m++)
-            acc += (float)V[s2 * 16 + i * 4 + m] * e2[m] * (float)Vinv[s2 * 16 + m * 4 + j];
+          for (int m = 0; m < 4; m++) acc += V2[i * 4 + m] * e2[m] * Vi2[m * 4 + j];
           Ek[i * 4 + j] = acc;
         }
       mm4(Z, Ek, T);
@@ -242,12 +254,14 @@ __global__ void __launch_bounds__(128) k4_chain(Dims d, const double *__restrict
         for (int m = 0; m < 4; m++) acc += Vs[m * 4 + i] * Y[m * 4 + j];
         Hh[i * 4 + j] = acc;
       }
-    float dk = 0.f;
-#pragma unroll
-    for (int i = 0; i < 4; i++) dk += Hh[i * 5] * li[i] * ev[i];
     float *out = gseg + (((size_t)v * E + k) * d.C + c) * stride;
-    out[0] = dk;
-    if (d.np > 0) {
+    if (qq == 0) {
+      float dk = 0.f;
+#pragma unroll
+      for (int i = 0; i < 4; i++) dk += Hh[i * 5] * li[i] * ev[i];
+      out[0] = dk;
+    }
+    if (d.np > qq) {
       float W[16];
 #pragma unroll
       for (int i = 0; i < 4; i++)
@@ -257,10 +271,10 @@ __global__ void __launch_bounds__(128) k4_chain(Dims d, const double *__restrict
           const float ph = (x == 0.f) ? tau * ev[j] : ev[j] * tau * (expm1f(x) / x);
           W[i * 4 + j] = Hh[i * 4 + j] * ph;
         }
-      for (int a = 0; a < d.np; a++) {
+      for (int a = qq; a < d.np; a += 4) {
         float ga = 0.f;
-        if (Dnz[a * d.S + s]) {
-          const float *Da = Dth + ((size_t)a * d.S + s) * 16;
+        if (sNz[a * d.S + s]) {
+          const float *Da = sD + ((size_t)a * d.S + s) * 16;
 #pragma unroll
           for (int q = 0; q < 16; q++) ga += W[q] * Da[q];
         }
@@ -288,6 +302,11 @@ __global__ void __launch_bounds__(128) k4_chain(Dims d, const double *__restrict
 
 }  // namespace
 
+size_t k4_chain_smem(const Dims &d) {
+  return sizeof(float) * ((size_t)d.S * 36 + (size_t)d.np * d.S * 16) +
+         sizeof(int) * (size_t)d.np * d.S;
+}
+
 cudaError_t launch_branch_k4(epoch_ctx *c) {
   const Dims &d = c->d;
   const int n = d.nn * d.C * 4;
@@ -301,9 +320,10 @@ cudaError_t launch_branch_k4(epoch_ctx *c) {
 
 cudaError_t launch_chain_k4(epoch_ctx *c) {
   const Dims &d = c->d;
-  const int n = d.nn * d.C;
-  // one warp per CTA spreads the latency-bound chains over the SMs
-  k4_chain<<<ceil_div(n, 32), 32, 0, c->stream>>>(d, c->d_G, c->d_nseg, c->d_seg_mat,
+  const int n = d.nn * d.C * 4;
+  const size_t smem = k4_chain_smem(d);
+  cudaFuncSetAttribute(k4_chain, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+  k4_chain<<<ceil_div(n, 128), 128, smem, c->stream>>>(d, c->d_G, c->d_nseg, c->d_seg_mat,
                                                     c->d_seg_dt, c->d_brate, c->d_catr, c->d_lam,
                                                     c->d_V, c->d_Vinv, c->d_Dth32, c->d_Dnz,
                                                     (float *)c->d_gseg);

@@ -87,27 +87,153 @@ __device__ double block_sum(double x, double *red) {
 
 // ---------------------------------------------------------------------------
 // Normalise each Q_s and, for reversible models, diagonalise the symmetric
-// S = Pi^{1/2} Q Pi^{-1/2} by parallel cyclic Jacobi (round-robin pairing:
-// the n/2 rotations of a round act on disjoint index pairs and are applied
-// together as J^T A J).  Q = V diag(lambda) V^{-1}, V = Pi^{-1/2} U,
-// V^{-1} = U^T Pi^{1/2}.  One CTA per matrix, FP64.
+// S = Pi^{1/2} Q Pi^{-1/2}: Q = V diag(lambda) V^{-1}, V = Pi^{-1/2} U,
+// V^{-1} = U^T Pi^{1/2}.  One CTA per matrix.
+//
+// Each FP64 instruction of a warp costs tens of cycles on this part whatever
+// its active lanes, so the rotations are found in FP32 and only polished in
+// FP64:
+//   1. parallel cyclic Jacobi in FP32 (round-robin pairing: the n/2 rotations
+//      of a round act on disjoint index pairs and are applied together as
+//      J^T A J) until the off-diagonal part is below 1e-6 of the matrix;
+//   2. U = the FP32 rotations in FP64, made orthogonal to FP64 rounding by
+//      two Newton-Schulz steps U <- U (3 I - U^T U) / 2;
+//   3. A' = U^T S U in FP64 (off-diagonal ~1e-7), then exact FP64 Jacobi
+//      sweeps on A' (quadratic convergence: two sweeps to 1e-16), U <- U J.
 // ---------------------------------------------------------------------------
+// FP64: the exact angle (the annihilated entry is then set to zero).
+__device__ __forceinline__ void jacobi_rotation(double app, double aqq, double apq, double &c,
+                                                double &s) {
+  const double theta = (aqq - app) / (2.0 * apq);
+  double t;
+  if (fabs(theta) > 1e18)
+    t = 0.5 / theta;
+  else
+    t = (theta >= 0.0 ? 1.0 : -1.0) / (fabs(theta) + sqrt(theta * theta + 1.0));
+  c = 1.0 / sqrt(t * t + 1.0);
+  s = t * c;
+}
+// FP32: an angle to ~1e-6 is enough (the FP64 stage finishes the job), so
+// the fast reciprocal and square-root instructions do.
+__device__ __forceinline__ void jacobi_rotation(float app, float aqq, float apq, float &c,
+                                                float &s) {
+  const float theta = __fdividef(aqq - app, 2.f * apq);
+  float t;
+  if (fabsf(theta) > 1e18f) {
+    t = __fdividef(0.5f, theta);
+  } else {
+    const float h = theta * theta + 1.f;
+    t = copysignf(__fdividef(1.f, fabsf(theta) + h * rsqrtf(h)), theta);
+  }
+  c = rsqrtf(t * t + 1.f);
+  s = t * c;
+}
+
+// Cyclic Jacobi sweeps on the K x K symmetric A (row-major, shared memory),
+// rotations accumulated into U (U <- U J).  Stops when the squared
+// off-diagonal norm is <= tol2 (absolute); returns the last measured value.
+template <typename T, int KT>
+__device__ __forceinline__ double jacobi_sweeps(T *A, T *U, int Kr, double tol2, int max_sweeps,
+                                                double *red, T *cs, T *sn, int *pq) {
+  const int K = KT ? KT : Kr;
+  const int KK = K * K, tid = threadIdx.x, nt = blockDim.x;
+  const int n = K + (K & 1), npair = n / 2;
+  double off = 0.0;
+  for (int sweep = 0;; sweep++) {
+    double part = 0.0;
+    for (int idx = tid; idx < KK; idx += nt) {
+      const int i = idx / K, j = idx % K;
+      if (j > i) part += (double)A[idx] * (double)A[idx];
+    }
+    off = block_sum(part, red);
+    if (off <= tol2 || sweep == max_sweeps) break;
+    for (int round = 0; round < n - 1; round++) {
+      for (int k = tid; k < npair; k += nt) {
+        // round-robin position after `round` shifts: element 0 stays, the
+        // others move one place per round
+        auto pos = [&](int i) {
+          const int m = i - 1 - round;  // in (-(n - 1), n - 1)
+          return i == 0 ? 0 : 1 + (m < 0 ? m + n - 1 : m);
+        };
+        const int a = pos(k), b = pos(n - 1 - k);
+        const int p = a < b ? a : b, q = a < b ? b : a;
+        T c = T(1), s = T(0);
+        if (q < K && A[p * K + q] != T(0))
+          jacobi_rotation(A[p * K + p], A[q * K + q], A[p * K + q], c, s);
+        cs[k] = c;
+        sn[k] = s;
+        pq[2 * k] = p;
+        pq[2 * k + 1] = q;
+      }
+      __syncthreads();
+      for (int idx = tid; idx < npair * K; idx += nt) {  // rows: B = J^T A
+        const int k = idx / K, col = idx % K, p = pq[2 * k], q = pq[2 * k + 1];
+        if (q >= K || sn[k] == T(0)) continue;
+        const T ap = A[p * K + col], aq = A[q * K + col];
+        A[p * K + col] = cs[k] * ap - sn[k] * aq;
+        A[q * K + col] = sn[k] * ap + cs[k] * aq;
+      }
+      __syncthreads();
+      for (int idx = tid; idx < npair * K; idx += nt) {  // columns: A' = B J, U' = U J
+        const int k = idx / K, row = idx % K, p = pq[2 * k], q = pq[2 * k + 1];
+        if (q >= K || sn[k] == T(0)) continue;
+        const T ap = A[row * K + p], aq = A[row * K + q];
+        A[row * K + p] = cs[k] * ap - sn[k] * aq;
+        A[row * K + q] = sn[k] * ap + cs[k] * aq;
+        const T up = U[row * K + p], uq = U[row * K + q];
+        U[row * K + p] = cs[k] * up - sn[k] * uq;
+        U[row * K + q] = sn[k] * up + cs[k] * uq;
+      }
+      __syncthreads();
+      for (int k = tid; k < npair; k += nt) {  // the annihilated pair
+        const int p = pq[2 * k], q = pq[2 * k + 1];
+        if (q < K && sn[k] != T(0)) {
+          A[p * K + q] = T(0);
+          A[q * K + p] = T(0);
+        }
+      }
+      __syncthreads();
+    }
+  }
+  return off;
+}
+
+// C = op(X) Y for K x K row-major FP64 matrices in shared memory (op = X^T
+// when tx); every thread forms whole entries of C.
+template <int KT>
+__device__ __forceinline__ void mm_shared(const double *X, const double *Y, double *C, int Kr,
+                                          bool tx) {
+  const int K = KT ? KT : Kr;
+  for (int idx = threadIdx.x; idx < K * K; idx += blockDim.x) {
+    const int i = idx / K, j = idx % K;
+    double acc = 0.0;
+    for (int m = 0; m < K; m++) acc += (tx ? X[m * K + i] : X[i * K + m]) * Y[m * K + j];
+    C[idx] = acc;
+  }
+  __syncthreads();
+}
+
+template <int KT>  // KT: K known at compile time (0 = take d.K)
 __global__ void k_model_setup(Dims d, int normalise, const double *__restrict__ Qraw,
                               const double *__restrict__ pi, double *__restrict__ Qn,
                               double *__restrict__ cnorm, double *__restrict__ lam,
                               double *__restrict__ V, double *__restrict__ Vinv,
                               int *__restrict__ status) {
   extern __shared__ double sm[];
-  const int K = d.K, KK = d.KK;
+  const int K = KT ? KT : d.K, KK = K * K;
   const int s = blockIdx.x;
-  double *A = sm;            // K*K
-  double *U = A + KK;        // K*K
-  double *rs = U + KK;       // K   sqrt(pi)
+  double *A = sm;            // K*K  S, then U^T S U
+  double *U = A + KK;        // K*K  eigenvectors
+  double *T1 = U + KK;       // K*K  work
+  double *T2 = T1 + KK;      // K*K  work
+  double *rs = T2 + KK;      // K    sqrt(pi)
   double *red = rs + K;      // 32
   double *cs = red + 32;     // 32 rotation cosines
   double *sn = cs + 32;      // 32 rotation sines
-  int *pq = (int *)(sn + 32);  // 64 pair indices
-  int *ord = pq + 64;          // 64 round-robin order
+  int *pq = (int *)(sn + 32);                // 64 pair indices
+  float *A32 = (float *)(pq + 64);           // K*K
+  float *U32 = A32 + KK;                     // K*K
+  float *cs32 = U32 + KK, *sn32 = cs32 + 32;  // 32 + 32
   const int tid = threadIdx.x, nt = blockDim.x;
 
   for (int i = tid; i < KK; i += nt) A[i] = Qraw[(size_t)s * KK + i];
@@ -118,118 +244,58 @@ __global__ void k_model_setup(Dims d, int normalise, const double *__restrict__ 
   double c = block_sum(part, red);
   double scale = normalise ? c : 1.0;
   if (!(scale > 0.0)) scale = 1.0;  // rejected on the host already
+  const double inv_scale = 1.0 / scale;
   for (int i = tid; i < KK; i += nt) {
-    A[i] /= scale;
+    A[i] *= inv_scale;
     Qn[(size_t)s * KK + i] = A[i];
   }
   if (tid == 0) cnorm[s] = scale;
   if (!d.reversible) return;
   __syncthreads();
-  // symmetric form
+  // symmetric form S = (Pi^1/2 Q Pi^-1/2 + its transpose) / 2
   for (int idx = tid; idx < KK; idx += nt) {
-    int i = idx / K, j = idx % K;
-    U[idx] = rs[i] * A[idx] / rs[j];
+    const int i = idx / K, j = idx % K;
+    T1[idx] = rs[i] * A[idx] / rs[j];
   }
   __syncthreads();
-  for (int idx = tid; idx < KK; idx += nt) {
-    int i = idx / K, j = idx % K;
-    A[idx] = 0.5 * (U[i * K + j] + U[j * K + i]);
-  }
-  __syncthreads();
-  for (int idx = tid; idx < KK; idx += nt) U[idx] = (idx / K == idx % K) ? 1.0 : 0.0;
-  const int n = K + (K & 1);
-  for (int i = tid; i < n; i += nt) ord[i] = i;
   part = 0.0;
-  for (int i = tid; i < KK; i += nt) part += A[i] * A[i];
-  double fro2 = block_sum(part, red);
-  const double tol2 = 1e-32 * fro2;  // (1e-16 * ||A||_F)^2
-  int converged = 0;
-  for (int sweep = 0; sweep < 60; sweep++) {
-    part = 0.0;
-    for (int idx = tid; idx < KK; idx += nt) {
-      int i = idx / K, j = idx % K;
-      if (j > i) part += A[idx] * A[idx];
-    }
-    double off = block_sum(part, red);
-    if (off <= tol2) {
-      converged = 1;
-      break;
-    }
-    for (int round = 0; round < n - 1; round++) {
-      const int npair = n / 2;
-      for (int k = tid; k < npair; k += nt) {
-        int a = ord[k], b2 = ord[n - 1 - k];
-        int p = a < b2 ? a : b2, q = a < b2 ? b2 : a;
-        double cc = 1.0, ss = 0.0;
-        if (q < K) {
-          double apq = A[p * K + q];
-          if (apq != 0.0) {
-            double theta = (A[q * K + q] - A[p * K + p]) / (2.0 * apq);
-            double t;
-            if (fabs(theta) > 1e150)
-              t = 0.5 / theta;
-            else
-              t = (theta >= 0.0 ? 1.0 : -1.0) / (fabs(theta) + sqrt(theta * theta + 1.0));
-            cc = 1.0 / sqrt(t * t + 1.0);
-            ss = t * cc;
-          }
-        }
-        cs[k] = cc;
-        sn[k] = ss;
-        pq[2 * k] = p;
-        pq[2 * k + 1] = q;
-      }
-      __syncthreads();
-      // rows: B = J^T A
-      for (int idx = tid; idx < npair * K; idx += nt) {
-        int k = idx / K, col = idx % K;
-        int p = pq[2 * k], q = pq[2 * k + 1];
-        if (q >= K || sn[k] == 0.0) continue;
-        double ap = A[p * K + col], aq = A[q * K + col];
-        A[p * K + col] = cs[k] * ap - sn[k] * aq;
-        A[q * K + col] = sn[k] * ap + cs[k] * aq;
-      }
-      __syncthreads();
-      // columns: A' = B J, U' = U J
-      for (int idx = tid; idx < npair * K; idx += nt) {
-        int k = idx / K, row = idx % K;
-        int p = pq[2 * k], q = pq[2 * k + 1];
-        if (q >= K || sn[k] == 0.0) continue;
-        double ap = A[row * K + p], aq = A[row * K + q];
-        A[row * K + p] = cs[k] * ap - sn[k] * aq;
-        A[row * K + q] = sn[k] * ap + cs[k] * aq;
-        double up = U[row * K + p], uq = U[row * K + q];
-        U[row * K + p] = cs[k] * up - sn[k] * uq;
-        U[row * K + q] = sn[k] * up + cs[k] * uq;
-      }
-      __syncthreads();
-      for (int k = tid; k < npair; k += nt) {
-        int p = pq[2 * k], q = pq[2 * k + 1];
-        if (q < K && sn[k] != 0.0) {
-          A[p * K + q] = 0.0;
-          A[q * K + p] = 0.0;
-        }
-      }
-      if (tid == 0) {
-        int last = ord[n - 1];
-        for (int i = n - 1; i >= 2; i--) ord[i] = ord[i - 1];
-        ord[1] = last;
-      }
-      __syncthreads();
-    }
+  for (int idx = tid; idx < KK; idx += nt) {
+    const int i = idx / K, j = idx % K;
+    A[idx] = 0.5 * (T1[i * K + j] + T1[j * K + i]);
+    A32[idx] = (float)A[idx];
+    U32[idx] = (i == j) ? 1.f : 0.f;
+    part += A[idx] * A[idx];
   }
-  if (!converged) {
-    part = 0.0;
+  const double fro2 = block_sum(part, red);
+  // 1. FP32 rotations
+  jacobi_sweeps<float, KT>(A32, U32, K, 1e-12 * fro2, 40, red, cs32, sn32, pq);
+  // 2. orthogonal U in FP64
+  for (int idx = tid; idx < KK; idx += nt) U[idx] = (double)U32[idx];
+  __syncthreads();
+  for (int it = 0; it < 2; it++) {
+    mm_shared<KT>(U, U, T1, K, true);  // T1 = U^T U
     for (int idx = tid; idx < KK; idx += nt) {
-      int i = idx / K, j = idx % K;
-      if (j > i) part += A[idx] * A[idx];
+      const int i = idx / K, j = idx % K;
+      T1[idx] = ((i == j) ? 1.5 : 0.0) - 0.5 * T1[idx];
     }
-    double off = block_sum(part, red);
-    if (off > 1e-24 * fro2 && tid == 0) atomicOr(status, ST_EIG_NOCONV);
+    __syncthreads();
+    mm_shared<KT>(U, T1, T2, K, false);  // T2 = U (3 I - U^T U) / 2
+    for (int idx = tid; idx < KK; idx += nt) U[idx] = T2[idx];
+    __syncthreads();
   }
+  // 3. A' = U^T S U, symmetrised, then exact FP64 sweeps
+  mm_shared<KT>(A, U, T1, K, false);   // T1 = S U
+  mm_shared<KT>(U, T1, T2, K, true);   // T2 = U^T S U
+  for (int idx = tid; idx < KK; idx += nt) {
+    const int i = idx / K, j = idx % K;
+    A[idx] = 0.5 * (T2[i * K + j] + T2[j * K + i]);
+  }
+  __syncthreads();
+  const double off = jacobi_sweeps<double, KT>(A, U, K, 1e-32 * fro2, 30, red, cs, sn, pq);
+  if (off > 1e-24 * fro2 && tid == 0) atomicOr(status, ST_EIG_NOCONV);
   for (int i = tid; i < K; i += nt) lam[(size_t)s * K + i] = A[i * K + i];
   for (int idx = tid; idx < KK; idx += nt) {
-    int i = idx / K, j = idx % K;
+    const int i = idx / K, j = idx % K;
     V[(size_t)s * KK + idx] = U[idx] / rs[i];
     Vinv[(size_t)s * KK + idx] = U[j * K + i] * rs[j];
   }
@@ -423,18 +489,19 @@ cudaError_t launch_segments(epoch_ctx *c) {
 }
 
 static size_t setup_smem(const Dims &d) {
-  return sizeof(double) * (2 * d.KK + d.K + 32 + 64) + sizeof(int) * 128;
+  return sizeof(double) * (4 * d.KK + d.K + 32 + 64) + sizeof(int) * 64 +
+         sizeof(float) * (2 * d.KK + 64);
 }
 
 cudaError_t launch_model_setup(epoch_ctx *c) {
   const Dims &d = c->d;
   size_t smem = setup_smem(d);
-  cudaFuncSetAttribute(k_model_setup, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
   // small K: one warp per matrix (its barriers are cheap); large K: 8 warps
   const int threads = d.K <= 8 ? 32 : 256;
-  k_model_setup<<<d.S, threads, smem, c->stream>>>(d, c->normalise, c->d_Qraw, c->d_pi, c->d_Q,
-                                               c->d_cnorm, c->d_lam, c->d_V, c->d_Vinv,
-                                               c->d_status);
+  auto kern = d.K == 4 ? k_model_setup<4> : k_model_setup<0>;
+  cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+  kern<<<d.S, threads, smem, c->stream>>>(d, c->normalise, c->d_Qraw, c->d_pi, c->d_Q, c->d_cnorm,
+                                          c->d_lam, c->d_V, c->d_Vinv, c->d_status);
   c->launches++;
   return cudaGetLastError();
 }
