@@ -126,18 +126,39 @@ class ClockSampler:
 # 2 B scale exponents) plus the root log-sum
 # ---------------------------------------------------------------------------
 def partials_bytes(w):
+    """Bytes the partials pass (pruning, rescaling, root log-sum) must move in
+    this design: every stored partial written once and read once by its
+    parent, one-byte tip codes, int16 exponents written and summed, the root's
+    per-pattern outputs.  Cherries (non-root nodes whose children are both
+    tips) are not stored; their parents read the two tip codes instead."""
     N, P, C = w.n_taxa, w.n_patterns, w.n_categories
     nn = 2 * N - 1
+    parent = np.asarray(w.parent)
+    kids = [[] for _ in range(nn)]
+    for v in range(nn):
+        if parent[v] >= 0:
+            kids[parent[v]].append(v)
+    root = int(np.where(parent < 0)[0][0])
+    cherry = [u >= N and u != root and all(k < N for k in kids[u]) for u in range(nn)]
     vec = 16 * C * P
     total = 0
     for u in range(N, nn):
-        total += vec + 2 * P                     # write partials + exponents
-    for v in range(nn):
-        if w.parent[v] < 0:
+        if cherry[u]:
             continue
-        total += vec if v >= N else P           # read child partials / tip codes
-    total += (N - 1) * 2 * P + vec + 8 * P + 16 * P  # root: exponents, root partial, weights, outputs
+        total += vec + 2 * P                     # write the partial and its exponents
+        for k in kids[u]:
+            total += P if k < N else (2 * P if cherry[k] else vec)
+    total += (N - 1) * 2 * P                     # exponents summed per pattern
+    total += 8 * P + 8 * P + 8 * P + 16 * P      # site log, weights, site lnL; root outputs
     return total
+
+
+def survey_bytes(w):
+    """The same pass counted with every internal node stored (no cherry
+    tables): the reference figure for this pass."""
+    N, P, C = w.n_taxa, w.n_patterns, w.n_categories
+    vec = 16 * C * P
+    return (N - 1) * (2 * vec + 4 * P) + N * P + 40 * P
 
 
 def run_ours(args, w, cfg, rank, world):
@@ -196,29 +217,53 @@ def run_ours(args, w, cfg, rank, world):
     peak, peak_kind = hbm_peak()
 
     # ---- e2e through the C ABI from host arrays ----------------------------
-    Q, dQ = np.ascontiguousarray(w.Q), np.ascontiguousarray(w.dQ)
-    tips = np.ascontiguousarray(w.tips, dtype=np.int32)
+    # An inference loop changes the model parameters and node heights between
+    # evaluations; the alignment is uploaded once.  Every step uploads all of
+    # them (from pinned host memory), evaluates, and reads back lnL and the
+    # whole gradient.  A second loop also re-uploads the alignment each step.
+    def pinned(a, dtype=np.float64):
+        t = torch.empty(np.asarray(a).shape, dtype=torch.float64 if dtype == np.float64
+                        else torch.int32, pin_memory=True)
+        v = t.numpy()
+        v[...] = a
+        return t, v
+    keep = []
+    host = {}
+    for name, arr in (("Q", w.Q), ("dQ", w.dQ), ("pi", w.pi), ("b", w.boundaries),
+                      ("cr", w.cat_rates), ("cw", w.cat_weights), ("h", w.heights),
+                      ("pw", w.pattern_weights)):
+        t, v = pinned(arr)
+        keep.append(t)
+        host[name] = v
+    tt, tips = pinned(np.asarray(w.tips, dtype=np.int32), np.int32)
+    keep.append(tt)
     for _ in range(2):
         lik.load(w)
         binding.epoch_evaluate_async(lik.ctx, True)
         binding.epoch_read_results(lik.ctx, nn, w.n_epochs, lik.n_params, True)
     torch.cuda.synchronize()
-    e_steps = max(3, min(args.steps, 20))
-    t0 = time.perf_counter()
-    for _ in range(e_steps):
-        binding.epoch_set_rate_matrices(lik.ctx, Q, w.pi, 1, 1)
-        binding.epoch_set_rate_derivatives(lik.ctx, dQ)
-        binding.epoch_set_boundaries(lik.ctx, w.boundaries)
-        binding.epoch_set_categories(lik.ctx, w.cat_rates, w.cat_weights)
-        binding.epoch_set_tree(lik.ctx, w.heights, w.parent)
-        binding.epoch_set_tip_data(lik.ctx, tips, w.pattern_weights)
-        binding.epoch_evaluate_async(lik.ctx, True)
-        binding.epoch_read_results(lik.ctx, nn, w.n_epochs, lik.n_params, True)
-    torch.cuda.synchronize()
-    e2e_s = (time.perf_counter() - t0) / e_steps
-    h2d = (Q.nbytes + dQ.nbytes + w.pi.nbytes + w.boundaries.nbytes + 2 * 8 * w.n_categories
-           + w.heights.nbytes + w.parent.astype(np.int32).nbytes + 8 * nn
-           + w.n_taxa * w.n_patterns + w.pattern_weights.nbytes)
+    e_steps = max(5, min(args.steps, 50))
+
+    def e2e_loop(with_alignment):
+        t0 = time.perf_counter()
+        for _ in range(e_steps):
+            binding.epoch_set_rate_matrices(lik.ctx, host["Q"], host["pi"], 1, 1)
+            binding.epoch_set_rate_derivatives(lik.ctx, host["dQ"])
+            binding.epoch_set_boundaries(lik.ctx, host["b"])
+            binding.epoch_set_categories(lik.ctx, host["cr"], host["cw"])
+            binding.epoch_set_heights(lik.ctx, host["h"])
+            if with_alignment:
+                binding.epoch_set_tip_data(lik.ctx, tips, host["pw"])
+            binding.epoch_evaluate_async(lik.ctx, True)
+            binding.epoch_read_results(lik.ctx, nn, w.n_epochs, lik.n_params, True)
+        torch.cuda.synchronize()
+        return (time.perf_counter() - t0) / e_steps
+
+    e2e_s = e2e_loop(False)
+    e2e_aln_s = e2e_loop(True)
+    h2d = (host["Q"].nbytes + host["dQ"].nbytes + host["pi"].nbytes + host["b"].nbytes
+           + host["cr"].nbytes + host["cw"].nbytes + host["h"].nbytes)
+    h2d_aln = h2d + w.n_taxa * w.n_patterns + host["pw"].nbytes
     d2h = 8 + 8 * (2 * nn + w.n_epochs - 1 + lik.n_params)
 
     # ---- plain FP64 GPU path on the same workload --------------------------
@@ -237,6 +282,7 @@ def run_ours(args, w, cfg, rank, world):
     lnl64, g64 = binding.epoch_read_results(lik64.ctx, nn, w.n_epochs, lik64.n_params, True)
     lik64.close()
     lik.close()
+    forest = run_forest(args, stream) if not args.no_forest else None
     rel_err = abs(lnl32 - lnl64) / abs(lnl64)
     grad_err = float(np.abs(g32["heights"] - g64["heights"]).max() / np.abs(g64["heights"]).max())
 
@@ -256,11 +302,16 @@ def run_ours(args, w, cfg, rank, world):
         "config": {**cfg, "parallelism": f"replicas{world}",
                    "l2": "working set > L2 (partials 320 MB + adjoint partials 320 MB per step)"},
         "e2e": {"value": world / e2e_s, "unit": UNIT, "h2d_bytes_per_step": int(h2d),
-                "d2h_bytes_per_step": int(d2h)},
+                "d2h_bytes_per_step": int(d2h),
+                "per_step_inputs": "Q, dQ, pi, boundaries, categories, node heights (pinned); "
+                                   "alignment uploaded once",
+                "with_alignment_each_step": {"value": world / e2e_aln_s, "unit": UNIT,
+                                             "h2d_bytes_per_step": int(h2d_aln)}},
         "gpu_launches": int(launches),
         "roofline": {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s",
                      "frac": achieved / peak, "traffic": None, "peak_source": peak_kind,
                      "kernel": "partials pass (post-order pruning + rescaling + root)",
+                     "effective_gbs_all_nodes_stored": survey_bytes(w) / (part_ms * 1e-3) / 1e9,
                      "ms_per_launch": part_ms, "algorithmic_bytes": int(pbytes)},
         "fp64_gpu": {"value": 1e3 / fp64_ms, "unit": UNIT, "ms_per_step": fp64_ms,
                      "lnL_rel_err_fp32_vs_fp64": rel_err, "grad_rel_err_fp32_vs_fp64": grad_err,
@@ -268,7 +319,45 @@ def run_ours(args, w, cfg, rank, world):
         "lnL": lnl32,
         "clocks": clk,
     }
+    if forest:
+        out["forest"] = forest
     return out
+
+
+def run_forest(args, stream):
+    """The batched trait workload: 256 coalescent trees (50-1000 taxa, 1-8
+    epochs, K = 50 asymmetric rates, 1-4 patterns) in one persistent launch
+    replayed from a CUDA graph (epoch_batch_*)."""
+    import torch
+
+    import synth
+    from paper_1309_3075_b300.binding import EpochBatch
+
+    bw = synth.asym50_forest()
+    fb = EpochBatch(bw.trees, cuda_stream=stream.cuda_stream)
+    try:
+        for _ in range(max(3, args.warmup)):  # the first call tunes the launch shape
+            fb.evaluate()
+        reps = max(10, min(args.steps, 50))
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        from paper_1309_3075_b300 import binding
+        torch.cuda.synchronize()
+        e0.record(stream)
+        for _ in range(reps):
+            binding.epoch_batch_evaluate_async(fb.b)
+        e1.record(stream)
+        torch.cuda.synchronize()
+        ms = e0.elapsed_time(e1) / reps
+        lnl = fb.evaluate()
+        warps, ctas = fb.launch_shape()
+    finally:
+        fb.close()
+    n_tax = sum(t.n_taxa for t in bw.trees)
+    return {"workload": f"{len(bw.trees)} trees, {n_tax} taxa in all, K=50 asymmetric, "
+                        "1-8 epochs, 1-4 patterns, one launch per evaluation",
+            "batch_evals_per_s": 1e3 / ms, "tree_evals_per_s": len(bw.trees) * 1e3 / ms,
+            "ms_per_batch": ms, "launch_shape": {"warps_per_cta": warps, "ctas_per_sm": ctas},
+            "lnL_sum": float(np.sum(lnl))}
 
 
 def oracle_sample_rate(w, budget_s):
@@ -301,6 +390,8 @@ def main():
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--workload", default="gtr", choices=["gtr", "gy94"])
     ap.add_argument("--cpu-seconds", type=float, default=12.0)
+    ap.add_argument("--no-forest", action="store_true",
+                    help="skip the batched 256-tree measurement")
     args = ap.parse_args()
     world = int(os.environ.get("WORLD_SIZE", "1"))
     rank = int(os.environ.get("RANK", "0"))

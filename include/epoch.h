@@ -219,6 +219,60 @@ epoch_status epoch_read_results(epoch_ctx *ctx, double *lnL, double *d_heights,
 epoch_status epoch_counters(const epoch_ctx *ctx, long long *kernel_launches,
                             long long *graph_captures);
 
+/* ---- many trees in one launch (the batched trait workload) ---------------- */
+
+/* Log-likelihoods of n_trees independent trees, each with its own taxa,
+ * epochs (own boundaries and one K x K rate matrix per epoch), root
+ * distribution and at most 4 site patterns, one rate category.  One
+ * persistent kernel evaluates all of them (trees are taken from a queue
+ * longest first); the launch is captured in a CUDA graph and replayed.  The
+ * branch products of Eq. convolution are applied to the partial vectors by
+ * uniformisation, so Q need not be reversible.  FP32 partials with
+ * per-pattern power-of-two rescaling; FP64 root log-sum.
+ * Sizes: 2 <= states <= 64; per tree n_taxa >= 2, 1 <= n_epochs <= 32,
+ * 1 <= n_patterns <= 4; the R matrices of the largest tree's epochs must
+ * fit in shared memory (n_epochs * K * K * 4 bytes, about 200 KB), else
+ * EPOCH_ERR_CAPACITY.  cuda_stream as in epoch_create. */
+typedef struct epoch_batch epoch_batch;
+epoch_status epoch_batch_create(epoch_batch **out, int states, int n_trees,
+                                const int *n_taxa, const int *n_epochs,
+                                const int *n_patterns, void *cuda_stream);
+void epoch_batch_destroy(epoch_batch *b);
+const char *epoch_batch_last_error(const epoch_batch *b);
+
+/* Models of every tree, concatenated in tree order (host arrays, copied):
+ *   boundaries [sum_t (E_t - 1)] heights, strictly increasing per tree
+ *   Q          [sum_t E_t][K][K] row-major, rows summing to zero; epoch e of
+ *              tree t uses its e-th matrix
+ *   pi         [n_trees][K] root distribution (and normalisation weights)
+ *   normalise  1: each Q scaled so that sum_i pi_i q_ii = -1 */
+epoch_status epoch_batch_set_models(epoch_batch *b, const double *boundaries,
+                                    const double *Q, const double *pi,
+                                    int normalise);
+
+/* Trees, concatenated: heights [sum_t (2 N_t - 1)] and parent (local node
+ * indices, tips 0..N_t-1, root -1), same conventions as epoch_set_tree. */
+epoch_status epoch_batch_set_trees(epoch_batch *b, const double *heights,
+                                   const int *parent);
+
+/* Tip codes [sum_t N_t * P_t] (tree t: [N_t][P_t], 0..K-1, K = missing) and
+ * pattern weights [sum_t P_t]. */
+epoch_status epoch_batch_set_tip_data(epoch_batch *b, const int *codes,
+                                      const double *weights);
+
+/* Async.  The first call times a few launch shapes on the current inputs
+ * and keeps the fastest (epoch_batch_launch_shape reports it), then
+ * captures the launch in a graph; later calls replay it. */
+epoch_status epoch_batch_evaluate_async(epoch_batch *b);
+
+/* Synchronises; lnL [n_trees] of the last evaluation.  EPOCH_ERR_NUMERIC
+ * when a partial became non-finite or a branch needed more than 4096
+ * uniformisation terms. */
+epoch_status epoch_batch_read(epoch_batch *b, double *lnL);
+
+epoch_status epoch_batch_launch_shape(const epoch_batch *b, int *warps_per_cta,
+                                      int *ctas_per_sm);
+
 /* ---- allocation-free root log-sum (no counterpart in the paper) ---------- */
 
 /* The weighted log-sum that ends the root step, for callers that must not

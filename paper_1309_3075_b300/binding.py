@@ -60,9 +60,19 @@ _SIGS = {
     "epoch_counters": [_vp, C.POINTER(C.c_longlong), C.POINTER(C.c_longlong)],
     "epoch_site_log_sum_noalloc": [_vp, _vp, C.c_int, C.c_longlong, _vp, C.c_int, _vp, _vp,
                                    _vp],
+    "epoch_batch_create": [C.POINTER(_vp), C.c_int, C.c_int, _ip, _ip, _ip, _vp],
+    "epoch_batch_destroy": [_vp],
+    "epoch_batch_last_error": [_vp],
+    "epoch_batch_set_models": [_vp, _dp, _dp, _dp, C.c_int],
+    "epoch_batch_set_trees": [_vp, _dp, _ip],
+    "epoch_batch_set_tip_data": [_vp, _ip, _dp],
+    "epoch_batch_evaluate_async": [_vp],
+    "epoch_batch_read": [_vp, _dp],
+    "epoch_batch_launch_shape": [_vp, _ip, _ip],
 }
 _RESTYPE = {"epoch_destroy": None, "epoch_last_error": C.c_char_p,
-            "epoch_status_string": C.c_char_p}
+            "epoch_status_string": C.c_char_p, "epoch_batch_destroy": None,
+            "epoch_batch_last_error": C.c_char_p}
 
 
 def lib():
@@ -337,3 +347,110 @@ def epoch_site_log_sum_noalloc(site_log, exponents, n_rows, row_stride, weights,
     return int(lib().epoch_site_log_sum_noalloc(p(site_log), p(exponents), int(n_rows),
                                                 int(row_stride), p(weights), int(n_patterns),
                                                 p(site_out), p(lnl_out), p(cuda_stream)))
+
+
+# ---- many trees in one launch ------------------------------------------------
+
+def _bcheck(b, st, where):
+    if st != 0:
+        msg = lib().epoch_batch_last_error(b).decode() if b else ""
+        raise EpochError(st, where, msg)
+
+
+def epoch_batch_create(states, n_taxa, n_epochs, n_patterns, cuda_stream=None):
+    out = _vp()
+    nt, ntp = _i(n_taxa)
+    ne, nep = _i(n_epochs)
+    npt, npp = _i(n_patterns)
+    st = lib().epoch_batch_create(C.byref(out), int(states), len(nt), ntp, nep, npp,
+                                  _vp(cuda_stream) if cuda_stream else None)
+    _bcheck(None, st, "epoch_batch_create")
+    return out
+
+
+def epoch_batch_destroy(b):
+    lib().epoch_batch_destroy(b)
+
+
+def epoch_batch_set_models(b, boundaries, Q, pi, normalise=1):
+    bd, bdp = _d(boundaries)
+    q, qp = _d(Q)
+    p, pp = _d(pi)
+    _bcheck(b, lib().epoch_batch_set_models(b, bdp if bd is not None and bd.size else None, qp,
+                                            pp, int(normalise)), "epoch_batch_set_models")
+
+
+def epoch_batch_set_trees(b, heights, parent):
+    h, hp = _d(heights)
+    p, pp = _i(parent)
+    _bcheck(b, lib().epoch_batch_set_trees(b, hp, pp), "epoch_batch_set_trees")
+
+
+def epoch_batch_set_tip_data(b, codes, weights):
+    c, cp = _i(codes)
+    w, wp = _d(weights)
+    _bcheck(b, lib().epoch_batch_set_tip_data(b, cp, wp), "epoch_batch_set_tip_data")
+
+
+def epoch_batch_evaluate_async(b):
+    _bcheck(b, lib().epoch_batch_evaluate_async(b), "epoch_batch_evaluate_async")
+
+
+def epoch_batch_read(b, n_trees):
+    out = np.zeros(n_trees)
+    _bcheck(b, lib().epoch_batch_read(b, out.ctypes.data_as(_dp)), "epoch_batch_read")
+    return out
+
+
+def epoch_batch_launch_shape(b):
+    w, c = C.c_int(0), C.c_int(0)
+    _bcheck(b, lib().epoch_batch_launch_shape(b, C.byref(w), C.byref(c)),
+            "epoch_batch_launch_shape")
+    return w.value, c.value
+
+
+class EpochBatch:
+    """Owns one epoch_batch.  ``trees`` is a sequence of objects with the
+    attributes of ``synth.Workload`` (one rate matrix per epoch, one
+    category, at most 4 patterns); arrays are concatenated in tree order."""
+
+    def __init__(self, trees, cuda_stream=None):
+        trees = list(trees)
+        self.T = len(trees)
+        self.K = int(trees[0].K)
+        self.b = epoch_batch_create(
+            self.K, [np.asarray(t.tips).shape[0] for t in trees],
+            [len(np.asarray(t.boundaries).reshape(-1)) + 1 for t in trees],
+            [np.asarray(t.tips).shape[1] for t in trees], cuda_stream)
+        self.load(trees)
+
+    def load(self, trees):
+        bnd = np.concatenate([np.asarray(t.boundaries, dtype=np.float64).reshape(-1)
+                              for t in trees])
+        Q = np.concatenate([np.asarray(t.Q, dtype=np.float64).reshape(-1) for t in trees])
+        pi = np.concatenate([np.asarray(t.pi, dtype=np.float64).reshape(-1) for t in trees])
+        epoch_batch_set_models(self.b, bnd, Q, pi, int(getattr(trees[0], "normalise", 1)))
+        epoch_batch_set_trees(self.b, np.concatenate([np.asarray(t.heights) for t in trees]),
+                              np.concatenate([np.asarray(t.parent) for t in trees]))
+        epoch_batch_set_tip_data(self.b,
+                                 np.concatenate([np.asarray(t.tips).reshape(-1) for t in trees]),
+                                 np.concatenate([np.asarray(t.pattern_weights, dtype=np.float64)
+                                                 for t in trees]))
+
+    def evaluate(self):
+        epoch_batch_evaluate_async(self.b)
+        return epoch_batch_read(self.b, self.T)
+
+    def launch_shape(self):
+        return epoch_batch_launch_shape(self.b)
+
+    def close(self):
+        if self.b:
+            epoch_batch_destroy(self.b)
+            self.b = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass

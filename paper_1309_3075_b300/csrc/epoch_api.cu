@@ -369,6 +369,8 @@ void epoch_destroy(epoch_ctx *c) {
   if (c->h_lnl_pinned) cudaFreeHost(c->h_lnl_pinned);
   if (c->h_status_pinned) cudaFreeHost(c->h_status_pinned);
   if (c->h_tips_staging) cudaFreeHost(c->h_tips_staging);
+  for (cudaEvent_t e : c->tips_staging_ev)
+    if (e) cudaEventDestroy(e);
   if (c->own_stream && c->stream) cudaStreamDestroy(c->stream);
   delete c;
 }
@@ -487,7 +489,10 @@ epoch_status epoch_create(epoch_ctx **out, int states, int n_epochs, const doubl
   A(dalloc(&c->d_site_log, P));
   A(cudaMallocHost((void **)&c->h_lnl_pinned, sizeof(double)));
   A(cudaMallocHost((void **)&c->h_status_pinned, sizeof(int)));
-  A(cudaMallocHost((void **)&c->h_tips_staging, (size_t)max_taxa * d.Pp + sizeof(float) * d.Pp));
+  c->tips_staging_half = ((size_t)max_taxa * d.Pp + sizeof(float) * d.Pp + 255) & ~(size_t)255;
+  A(cudaMallocHost((void **)&c->h_tips_staging, 2 * c->tips_staging_half));
+  A(cudaEventCreateWithFlags(&c->tips_staging_ev[0], cudaEventDisableTiming));
+  A(cudaEventCreateWithFlags(&c->tips_staging_ev[1], cudaEventDisableTiming));
   if (!ok) {
     cudaGetLastError();
     c->err = "device allocation failed";
@@ -528,7 +533,7 @@ epoch_status epoch_set_boundaries(epoch_ctx *c, const double *boundaries) {
       return fail(c, EPOCH_ERR_ARG, "boundaries must be strictly increasing");
   }
   c->h_boundaries.assign(boundaries, boundaries + (E - 1));
-  CK(cudaMemcpyAsync(c->d_boundaries, boundaries, sizeof(double) * (E - 1),
+  CK(cudaMemcpyAsync(c->d_boundaries, c->h_boundaries.data(), sizeof(double) * (E - 1),
                      cudaMemcpyHostToDevice, c->stream),
      "cudaMemcpyAsync(boundaries)");
   c->have &= ~(HAVE_BRANCH | HAVE_PARTIALS);
@@ -580,10 +585,12 @@ epoch_status epoch_set_rate_matrices(epoch_ctx *c, const double *Q, const double
   c->normalise = normalise ? 1 : 0;
   if (c->d.reversible != (reversible ? 1 : 0)) invalidate_graphs(c);
   c->d.reversible = reversible ? 1 : 0;
-  CK(cudaMemcpyAsync(c->d_Qraw, Q, sizeof(double) * d.S * d.KK, cudaMemcpyHostToDevice,
+  c->h_Qraw.assign(Q, Q + (size_t)d.S * d.KK);
+  c->h_pi.assign(pi, pi + K);
+  CK(cudaMemcpyAsync(c->d_Qraw, c->h_Qraw.data(), sizeof(double) * d.S * d.KK, cudaMemcpyHostToDevice,
                      c->stream),
      "cudaMemcpyAsync(Q)");
-  CK(cudaMemcpyAsync(c->d_pi, pi, sizeof(double) * K, cudaMemcpyHostToDevice, c->stream),
+  CK(cudaMemcpyAsync(c->d_pi, c->h_pi.data(), sizeof(double) * K, cudaMemcpyHostToDevice, c->stream),
      "cudaMemcpyAsync(pi)");
   c->have |= HAVE_RATES;
   c->have &= ~(HAVE_BRANCH | HAVE_PARTIALS);
@@ -618,8 +625,9 @@ epoch_status epoch_set_rate_derivatives(epoch_ctx *c, int n_params, const double
     if (s != EPOCH_OK) return s;
     invalidate_graphs(c);
   }
+  if (n_params > 0) c->h_dQ.assign(dQ, dQ + (size_t)n_params * d.S * d.KK);
   if (n_params > 0)
-    CK(cudaMemcpyAsync(c->d_dQraw, dQ, sizeof(double) * n_params * d.S * d.KK,
+    CK(cudaMemcpyAsync(c->d_dQraw, c->h_dQ.data(), sizeof(double) * n_params * d.S * d.KK,
                        cudaMemcpyHostToDevice, c->stream),
        "cudaMemcpyAsync(dQ)");
   c->have &= ~(HAVE_BRANCH | HAVE_PARTIALS);
@@ -637,10 +645,12 @@ epoch_status epoch_set_categories(epoch_ctx *c, const double *rates, const doubl
     ws += weights[k];
   }
   if (!(ws > 0.0)) return fail(c, EPOCH_ERR_ARG, "category weights sum to zero");
-  CK(cudaMemcpyAsync(c->d_catr, rates, sizeof(double) * c->d.C, cudaMemcpyHostToDevice,
+  c->h_catr.assign(rates, rates + c->d.C);
+  c->h_catw.assign(weights, weights + c->d.C);
+  CK(cudaMemcpyAsync(c->d_catr, c->h_catr.data(), sizeof(double) * c->d.C, cudaMemcpyHostToDevice,
                      c->stream),
      "cudaMemcpyAsync(rates)");
-  CK(cudaMemcpyAsync(c->d_catw, weights, sizeof(double) * c->d.C, cudaMemcpyHostToDevice,
+  CK(cudaMemcpyAsync(c->d_catw, c->h_catw.data(), sizeof(double) * c->d.C, cudaMemcpyHostToDevice,
                      c->stream),
      "cudaMemcpyAsync(weights)");
   c->have |= HAVE_CATS;
@@ -662,10 +672,10 @@ epoch_status epoch_set_ambiguity_masks(epoch_ctx *c, int n_masks, const unsigned
   c->d_masks = nullptr;
   if (n_masks > 0) {
     CK(dalloc(&c->d_masks, n_masks), "cudaMalloc(masks)");
-    CK(cudaMemcpyAsync(c->d_masks, masks, sizeof(unsigned long long) * n_masks,
+    c->h_masks.assign(masks, masks + n_masks);
+    CK(cudaMemcpyAsync(c->d_masks, c->h_masks.data(), sizeof(unsigned long long) * n_masks,
                        cudaMemcpyHostToDevice, c->stream),
        "cudaMemcpyAsync(masks)");
-    c->h_masks.assign(masks, masks + n_masks);
   } else {
     c->h_masks.clear();
   }
@@ -738,7 +748,8 @@ epoch_status epoch_set_tree(epoch_ctx *c, int n_taxa, const double *heights, con
       const size_t n = (size_t)2 * maxw * c->d.C * c->d.P * c->d.Kp * elem_size(c->precision);
       CK(cudaMalloc(&c->d_xbuf, n), "cudaMalloc(adjoint scratch)");
     }
-    CK(cudaMemcpyAsync(c->d_parent, parent, sizeof(int) * nn, cudaMemcpyHostToDevice, c->stream),
+    CK(cudaMemcpyAsync(c->d_parent, c->h_parent.data(), sizeof(int) * nn, cudaMemcpyHostToDevice,
+                       c->stream),
        "cudaMemcpyAsync(parent)");
     CK(cudaMemcpyAsync(c->d_child, c->h_child.data(), sizeof(int) * 2 * (N - 1),
                        cudaMemcpyHostToDevice, c->stream),
@@ -758,11 +769,12 @@ epoch_status epoch_set_tree(epoch_ctx *c, int n_taxa, const double *heights, con
     c->have &= ~HAVE_TIPS;
   }
   c->h_heights.assign(heights, heights + nn);
-  CK(cudaMemcpyAsync(c->d_heights, heights, sizeof(double) * nn, cudaMemcpyHostToDevice,
+  CK(cudaMemcpyAsync(c->d_heights, c->h_heights.data(), sizeof(double) * nn, cudaMemcpyHostToDevice,
                      c->stream),
      "cudaMemcpyAsync(heights)");
   if (branch_rates) {
-    CK(cudaMemcpyAsync(c->d_brate, branch_rates, sizeof(double) * nn, cudaMemcpyHostToDevice,
+    c->h_brate.assign(branch_rates, branch_rates + nn);
+    CK(cudaMemcpyAsync(c->d_brate, c->h_brate.data(), sizeof(double) * nn, cudaMemcpyHostToDevice,
                        c->stream),
        "cudaMemcpyAsync(branch rates)");
   } else {
@@ -784,7 +796,7 @@ epoch_status epoch_set_heights(epoch_ctx *c, const double *heights) {
   epoch_status s = validate_heights(c, c->d.N, heights, c->h_parent.data());
   if (s != EPOCH_OK) return s;
   c->h_heights.assign(heights, heights + c->d.nn);
-  CK(cudaMemcpyAsync(c->d_heights, heights, sizeof(double) * c->d.nn, cudaMemcpyHostToDevice,
+  CK(cudaMemcpyAsync(c->d_heights, c->h_heights.data(), sizeof(double) * c->d.nn, cudaMemcpyHostToDevice,
                      c->stream),
      "cudaMemcpyAsync(heights)");
   c->have &= ~(HAVE_BRANCH | HAVE_PARTIALS);
@@ -798,32 +810,44 @@ epoch_status epoch_set_tip_data(epoch_ctx *c, const int *tip_codes, const double
   const Dims &d = c->d;
   const int maxcode = d.K + d.n_masks;
   // marshal int codes into the one-byte device layout [N][Pp] (row stride
-  // padded to 16 bytes; padding holds code 0 and is never used as a pattern)
-  CK(cudaStreamSynchronize(c->stream), "cudaStreamSynchronize");  // staging buffer reuse
-  for (int x = 0; x < d.N; x++) {
-    uint8_t *row = c->h_tips_staging + (size_t)x * d.Pp;
+  // padded to 16 bytes; padding holds code 0 and is never used as a pattern).
+  // The pinned staging area has two halves used in turn; a half is refilled
+  // only after the copy out of it (two calls ago) has finished, so this call
+  // does not wait for the work queued on the stream.
+  uint8_t *stage = c->h_tips_staging + c->tips_staging_cur * c->tips_staging_half;
+  CK(cudaEventSynchronize(c->tips_staging_ev[c->tips_staging_cur]), "cudaEventSynchronize");
+  std::vector<unsigned> bad(1, 0u);
+  for (int x = 0; x < d.N; x++) {  // branch-free so that the loop vectorises
+    uint8_t *row = stage + (size_t)x * d.Pp;
+    const int *src = tip_codes + (size_t)x * d.P;
+    unsigned b = 0;
     for (int p = 0; p < d.P; p++) {
-      const int code = tip_codes[(size_t)x * d.P + p];
-      if (code < 0 || code > maxcode) return fail(c, EPOCH_ERR_ARG, "tip code out of range");
+      const unsigned code = (unsigned)src[p];
+      b |= (unsigned)(code > (unsigned)maxcode);
       row[p] = (uint8_t)code;
     }
     for (int p = d.P; p < d.Pp; p++) row[p] = 0;
+    bad[0] |= b;
   }
-  float *wf = reinterpret_cast<float *>(c->h_tips_staging + (size_t)c->max_taxa * d.Pp);
+  for (unsigned b : bad)
+    if (b) return fail(c, EPOCH_ERR_ARG, "tip code out of range");
+  float *wf = reinterpret_cast<float *>(stage + (size_t)c->max_taxa * d.Pp);
   for (int p = 0; p < d.P; p++) {
     if (!fin(pattern_weights[p]) || pattern_weights[p] < 0.0)
       return fail(c, EPOCH_ERR_ARG, "bad pattern weight");
     wf[p] = (float)pattern_weights[p];
   }
   for (int p = d.P; p < d.Pp; p++) wf[p] = 0.f;
-  CK(cudaMemcpyAsync(c->d_tips, c->h_tips_staging, (size_t)d.N * d.Pp, cudaMemcpyHostToDevice,
-                     c->stream),
+  CK(cudaMemcpyAsync(c->d_tips, stage, (size_t)d.N * d.Pp, cudaMemcpyHostToDevice, c->stream),
      "cudaMemcpyAsync(tips)");
   CK(cudaMemcpyAsync(c->d_pwf, wf, sizeof(float) * d.Pp, cudaMemcpyHostToDevice, c->stream),
      "cudaMemcpyAsync(weights)");
-  CK(cudaMemcpyAsync(c->d_pw, pattern_weights, sizeof(double) * d.P, cudaMemcpyHostToDevice,
+  c->h_pw.assign(pattern_weights, pattern_weights + d.P);
+  CK(cudaMemcpyAsync(c->d_pw, c->h_pw.data(), sizeof(double) * d.P, cudaMemcpyHostToDevice,
                      c->stream),
      "cudaMemcpyAsync(weights)");
+  CK(cudaEventRecord(c->tips_staging_ev[c->tips_staging_cur], c->stream), "cudaEventRecord");
+  c->tips_staging_cur ^= 1;
   c->have |= HAVE_TIPS;
   c->have &= ~HAVE_PARTIALS;
   return EPOCH_OK;

@@ -71,6 +71,10 @@ struct epoch_ctx {
   std::vector<int> h_level_nodes;     // internal nodes, level-ascending
   std::vector<int> h_level_off;       // [L+1]
   std::vector<unsigned long long> h_masks;
+  // host copies of the other inputs: device copies are made from these
+  // (pageable, owned by the context), so a caller's array -- pinned or not --
+  // is free again when the call returns
+  std::vector<double> h_Qraw, h_pi, h_dQ, h_catr, h_catw, h_brate, h_pw;
   int topo_version = 0;
 
   // ---- device buffers (owned) ----
@@ -150,7 +154,10 @@ struct epoch_ctx {
   double *h_grad_pinned = nullptr;
   double *h_lnl_pinned = nullptr;
   int *h_status_pinned = nullptr;
-  uint8_t *h_tips_staging = nullptr;
+  uint8_t *h_tips_staging = nullptr;  // two halves, used in turn (see set_tip_data)
+  size_t tips_staging_half = 0;        // bytes per half
+  int tips_staging_cur = 0;
+  cudaEvent_t tips_staging_ev[2] = {nullptr, nullptr};  // copy out of each half done
 
   // graph replay
   cudaGraphExec_t graph_exec[2] = {nullptr, nullptr};

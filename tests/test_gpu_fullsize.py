@@ -131,3 +131,25 @@ def test_gy94_full_size_gradient_vs_finite_differences(gy94_full):
     finally:
         lik.close()
         lik32.close()
+
+
+def test_forest_full_size_sampled_trees():
+    """The 256-tree batch in the launch the bench times; the oracle checks four
+    of the smaller trees (its dense uniformisation is slow at K = 50)."""
+    torch = pytest.importorskip("torch")
+    if not torch.cuda.is_available():
+        pytest.skip("needs a GPU")
+    from paper_1309_3075_b300.binding import EpochBatch
+    bw = synth.asym50_forest()
+    b = EpochBatch(bw.trees)
+    try:
+        got = b.evaluate()
+    finally:
+        b.close()
+    assert np.all(np.isfinite(got))
+    sizes = np.array([t.n_taxa for t in bw.trees])
+    order = np.argsort(sizes, kind="stable")
+    pick = [int(order[i]) for i in (0, 1, 2, 12)]
+    for t in pick:
+        ref = oracle.log_likelihood(bw.trees[t])[0]
+        assert abs(got[t] - ref) <= 1e-5 * abs(ref), (t, got[t], ref)
