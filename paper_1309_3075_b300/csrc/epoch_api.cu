@@ -71,6 +71,9 @@ epoch_status ensure_pt32(epoch_ctx *c) {
   dfree(c->d_pairS);
   dfree(c->d_pairL);
   c->d_pairS = c->d_pairL = nullptr;
+  dfree(c->d_tcB);
+  c->d_tcB = nullptr;
+  if (tc_path(c)) CK(dalloc(&c->d_tcB, tc_operand_floats(c)), "cudaMalloc(tensor-core operands)");
   if (fast_k4(c)) {  // code-pair tables of the cherries
     const size_t np = (size_t)(2 * c->max_taxa - 1) * d.C * d.NR * d.NR * 4;
     CK(dalloc(&c->d_pairS, np), "cudaMalloc(pair tables)");
@@ -138,6 +141,7 @@ epoch_status enqueue_branch(epoch_ctx *c) {
     CK(launch_branch_matrices(c), "branch matrix kernel");
   }
   if (fast_k4(c)) CK(launch_pair_tables_k4(c), "pair table kernel");
+  if (tc_path(c)) CK(launch_tc_prep(c), "tensor-core operand kernel");
   return EPOCH_OK;
 }
 
@@ -363,7 +367,8 @@ void epoch_destroy(epoch_ctx *c) {
                   c->d_site_lnl,
                   c->d_site_inv,   c->d_lnl_part, c->d_lnl,     c->d_Gpart,      c->d_G,
                   c->d_gseg,       c->d_grad,    c->d_status,   c->d_ctl,        c->d_site_log,
-                  c->d_level_off,  c->d_pairS,   c->d_pairL,    c->d_k4_walk,    c->d_k4_nt};
+                  c->d_level_off,  c->d_pairS,   c->d_pairL,    c->d_k4_walk,    c->d_k4_nt,
+                  c->d_tcB};
   for (void *p : bufs) dfree(p);
   if (c->h_grad_pinned) cudaFreeHost(c->h_grad_pinned);
   if (c->h_lnl_pinned) cudaFreeHost(c->h_lnl_pinned);
@@ -406,6 +411,8 @@ epoch_status epoch_create(epoch_ctx **out, int states, int n_epochs, const doubl
   Dims &d = c->d;
   d.K = states;
   d.Kp = (states + 3) / 4 * 4;
+  // the tensor-core tiles are 64 states wide: pad large state spaces to 64
+  if (precision == EPOCH_FP32_TC && states > 32) d.Kp = 64;
   d.KK = states * states;
   d.n_masks = 0;
   d.NR = states + 1;

@@ -144,6 +144,7 @@ struct epoch_ctx {
   int4 *d_k4_walk = nullptr;
   size_t k4_walk_cap = 0;             // int4 capacity of d_k4_walk
   int *d_k4_nt = nullptr;             // [nn]
+  float *d_tcB = nullptr;             // [nn][C][4][64*64] tensor-core operands (k_tc.cu)
   float *d_pairS = nullptr;           // [nn][C][NR*NR][4] S of each cherry per code pair
   float *d_pairL = nullptr;           // [nn][C][NR*NR][4] L of each cherry per code pair
   size_t gpart_bytes = 0;
@@ -192,6 +193,14 @@ void k4_schedule(epoch_ctx *c);                 // host: walks, launches, tile c
 cudaError_t launch_branch_k4(epoch_ctx *c);     // segments + branch matrices + tables
 cudaError_t launch_chain_k4(epoch_ctx *c);      // chain rule through the products
 size_t k4_chain_smem(const Dims &d);            // its shared memory (model tables)
+
+// k_tc.cu (FP32_TC, 4 < K <= 64): tcgen05 tile products
+bool tc_path(const epoch_ctx *c);
+cudaError_t launch_tc_prep(epoch_ctx *c);          // P and P^T as TF32 hi/lo operands
+cudaError_t launch_tc_pre_u(epoch_ctx *c, int level);  // U = P^T X of one level
+cudaError_t launch_tc_post(epoch_ctx *c, int level);   // pruning + rescaling of one level
+cudaError_t launch_tc_pre_x(epoch_ctx *c, int level, int root);  // X of one level
+size_t tc_operand_floats(const epoch_ctx *c);
 
 // FP32, K = 4, at most 8 categories and 3 ambiguity masks (NR <= 8)
 inline bool fast_k4(const epoch_ctx *c) {

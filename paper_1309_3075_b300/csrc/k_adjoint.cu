@@ -480,6 +480,67 @@ __global__ void k_grad_reduce(Dims d, const int *__restrict__ parent, const int 
   }
 }
 
+// G over one chunk of kTile patterns for (level node, child x, category c),
+// register-tiled for large K: the 64 x 64 block of (i, j) is split over a
+// 16 x 16 thread grid, each thread owning a 4 x 4 tile; patterns go through
+// shared memory 32 at a time (X rows, and n_p L_v rows or the tip code's
+// indicator).  Same output layout as k_G_part.
+constexpr int kGSub = 32;
+__global__ void __launch_bounds__(256) k_G_tiled(Dims d, const int *__restrict__ lvl_nodes,
+                                                 int lvl_off, const int *__restrict__ child,
+                                                 const float *__restrict__ xbuf,
+                                                 const float *__restrict__ part,
+                                                 const uint8_t *__restrict__ tips,
+                                                 const unsigned long long *__restrict__ masks,
+                                                 const double *__restrict__ pw, int nchunk,
+                                                 float *__restrict__ Gpart) {
+  __shared__ __align__(16) float Xs[kGSub][64];
+  __shared__ __align__(16) float Ls[kGSub][64];
+  const int chunk = blockIdx.x, bi = blockIdx.y, x = blockIdx.z / d.C, c = blockIdx.z % d.C;
+  const int u = lvl_nodes[lvl_off + bi];
+  const int slot = u - d.N;
+  const int v = child[2 * slot + x];
+  const int p0 = chunk * kTile, p1 = min(d.P, p0 + kTile);
+  const float *X = xbuf + (((size_t)bi * 2 + x) * d.C + c) * d.P * d.Kp;
+  const float *L = v >= d.N ? part + ((size_t)(v - d.N) * d.C + c) * d.P * d.Kp : nullptr;
+  const int ti = threadIdx.x >> 4, tj = threadIdx.x & 15;
+  float acc[4][4] = {};
+  for (int q0 = p0; q0 < p1; q0 += kGSub) {
+    for (int e = threadIdx.x; e < kGSub * 64; e += blockDim.x) {
+      const int pr = e >> 6, k = e & 63, p = q0 + pr;
+      float xv = 0.f, lv = 0.f;
+      if (p < p1 && k < d.K) {
+        xv = X[(size_t)p * d.Kp + k];
+        const float n = (float)pw[p];
+        if (L) lv = n * L[(size_t)p * d.Kp + k];
+        else lv = code_allows(d, masks, tips[(size_t)v * d.Pp + p], k) ? n : 0.f;
+      }
+      Xs[pr][k] = xv;
+      Ls[pr][k] = lv;
+    }
+    __syncthreads();
+#pragma unroll 4
+    for (int pr = 0; pr < kGSub; pr++) {
+      const float4 a = *reinterpret_cast<const float4 *>(&Xs[pr][4 * ti]);
+      const float4 b = *reinterpret_cast<const float4 *>(&Ls[pr][4 * tj]);
+      const float av[4] = {a.x, a.y, a.z, a.w}, bv[4] = {b.x, b.y, b.z, b.w};
+#pragma unroll
+      for (int r = 0; r < 4; r++)
+#pragma unroll
+        for (int q = 0; q < 4; q++) acc[r][q] += av[r] * bv[q];
+    }
+    __syncthreads();
+  }
+  float *out = Gpart + (((size_t)slot * nchunk + chunk) * 2 + x) * d.C * d.KK + (size_t)c * d.KK;
+#pragma unroll
+  for (int r = 0; r < 4; r++)
+#pragma unroll
+    for (int q = 0; q < 4; q++) {
+      const int i = 4 * ti + r, j = 4 * tj + q;
+      if (i < d.K && j < d.K) out[i * d.K + j] = acc[r][q];
+    }
+}
+
 template <typename T>
 void launch_pre_generic(epoch_ctx *c, Tab<T> bt, int root) {
   const Dims &d = c->d;
@@ -489,16 +550,35 @@ void launch_pre_generic(epoch_ctx *c, Tab<T> bt, int root) {
   for (int l = L - 1; l >= 0; l--) {
     const int w = c->h_level_off[l + 1] - c->h_level_off[l];
     dim3 g(ceil_div(items, 256), w, 2);
-    k_pre_x<T><<<g, 256, 0, c->stream>>>(d, bt, c->d_level_nodes, c->h_level_off[l], c->d_child,
-                                         root, (const T *)c->d_part, (const T *)c->d_pre,
-                                         c->d_scale, c->d_tips, c->d_pi, c->d_catw,
-                                         c->d_site_inv, (T *)c->d_xbuf);
-    k_pre_u<T><<<g, 256, 0, c->stream>>>(d, bt, c->d_level_nodes, c->h_level_off[l], c->d_child,
-                                         (const T *)c->d_xbuf, (T *)c->d_pre);
-    dim3 gg(nchunk, w, 2);
-    k_G_part<T><<<gg, 256, 0, c->stream>>>(d, c->d_level_nodes, c->h_level_off[l], c->d_child,
-                                           (const T *)c->d_xbuf, (const T *)c->d_part, c->d_tips,
-                                           c->d_masks, c->d_pw, nchunk, (T *)c->d_Gpart);
+    if (sizeof(T) == sizeof(float) && tc_path(c)) {
+      launch_tc_pre_x(c, l, root);  // S by tile products, then X
+      c->launches--;                // counted below
+    } else {
+      k_pre_x<T><<<g, 256, 0, c->stream>>>(d, bt, c->d_level_nodes, c->h_level_off[l],
+                                           c->d_child, root, (const T *)c->d_part,
+                                           (const T *)c->d_pre, c->d_scale, c->d_tips, c->d_pi,
+                                           c->d_catw, c->d_site_inv, (T *)c->d_xbuf);
+    }
+    if (sizeof(T) == sizeof(float) && tc_path(c)) {
+      launch_tc_pre_u(c, l);  // U = P^T X on the tensor cores
+      c->launches--;          // counted below
+    } else {
+      k_pre_u<T><<<g, 256, 0, c->stream>>>(d, bt, c->d_level_nodes, c->h_level_off[l],
+                                           c->d_child, (const T *)c->d_xbuf, (T *)c->d_pre);
+    }
+    if (sizeof(T) == sizeof(float) && d.Kp == 64) {
+      dim3 gg(nchunk, w, 2 * d.C);
+      k_G_tiled<<<gg, 256, 0, c->stream>>>(d, c->d_level_nodes, c->h_level_off[l], c->d_child,
+                                           (const float *)c->d_xbuf, (const float *)c->d_part,
+                                           c->d_tips, c->d_masks, c->d_pw, nchunk,
+                                           (float *)c->d_Gpart);
+    } else {
+      dim3 gg(nchunk, w, 2);
+      k_G_part<T><<<gg, 256, 0, c->stream>>>(d, c->d_level_nodes, c->h_level_off[l], c->d_child,
+                                             (const T *)c->d_xbuf, (const T *)c->d_part,
+                                             c->d_tips, c->d_masks, c->d_pw, nchunk,
+                                             (T *)c->d_Gpart);
+    }
     c->launches += 3;
   }
 }

@@ -188,6 +188,11 @@ cudaError_t launch_generic_levels(epoch_ctx *c, BranchTable<T> bt) {
   const long long items = (long long)d.C * d.P * d.Kp;
   for (int l = 0; l < L; l++) {
     const int w = c->h_level_off[l + 1] - c->h_level_off[l];
+    if (sizeof(T) == sizeof(float) && tc_path(c)) {  // tile products on the tensor cores
+      cudaError_t e = launch_tc_post(c, l);
+      if (e != cudaSuccess) return e;
+      continue;
+    }
     dim3 g1(ceil_div(items, 256), w);
     k_partials_generic<T><<<g1, 256, 0, c->stream>>>(d, bt, c->d_level_nodes, c->h_level_off[l],
                                                      c->d_child, (T *)c->d_part, c->d_tips);

@@ -1,0 +1,462 @@
+// k_tc.cu -- tensor-core contractions of the large-K path (codon K = 61,
+// traits; K <= 64): tcgen05.mma with the accumulator in tensor memory.
+//
+// A partial vector of one (category, pattern) is a 64-float row (K padded
+// with zeros), so a branch applied to 128 patterns is one tile product
+//     D[128 x 64] = A[128 x 64] * B^T,   B[n][k] = P[n][k] (S = P L)
+//                                        or  B[n][k] = P[k][n] (U = P^T X),
+// run as tcgen05.mma kind::tf32 (M = 128, N = 64, K = 8 per instruction).
+// FP32 accuracy comes from the three-term split x = hi + lo (hi = x rounded
+// to TF32, lo = the rest rounded to TF32): A B ~ Ahi Bhi + Ahi Blo + Alo Bhi;
+// the dropped Alo Blo is below 2^-22 of the product.
+//
+// Operands sit in shared memory in the no-swizzle K-major canonical layout:
+// 8-row x 16-byte core matrices, element (r, k) at byte
+//     (r / 8) * 2048 + (k / 4) * 128 + (r % 8) * 16 + (k % 4) * 4,
+// i.e. leading-dimension (K) byte offset 128 between core matrices and
+// stride-dimension byte offset 2048 between 8-row groups.  The B operands of
+// every (branch, category) are laid out once per evaluation (k_tc_prep).
+#include <stdint.h>
+
+#include "epoch_internal.cuh"
+
+namespace epoch {
+namespace {
+
+constexpr int kRows = 128;            // tile rows (patterns)
+constexpr int kTcThr = 128;           // one thread per row; warp w owns TMEM lanes 32w..
+constexpr int kTile4 = 64 * 64;       // floats of one 64 x 64 operand
+constexpr int kATile = kRows * 64;    // floats of one 128 x 64 operand
+
+__device__ __forceinline__ int core_off(int r, int k) {  // in floats
+  return (r >> 3) * 512 + (k >> 2) * 32 + (r & 7) * 4 + (k & 3);
+}
+__device__ __forceinline__ float to_tf32(float x) {
+  uint32_t r;
+  asm("cvt.rna.tf32.f32 %0, %1;" : "=r"(r) : "f"(x));
+  return __uint_as_float(r);
+}
+__device__ __forceinline__ uint32_t su32(const void *p) {
+  return (uint32_t)__cvta_generic_to_shared(p);
+}
+__device__ __forceinline__ uint64_t smem_desc(uint32_t addr) {
+  uint64_t d = (uint64_t)((addr >> 4) & 0x3FFF);
+  d |= (uint64_t)(128 >> 4) << 16;   // leading (K) byte offset
+  d |= (uint64_t)(2048 >> 4) << 32;  // stride (8-row group) byte offset
+  d |= (uint64_t)1 << 46;            // descriptor version; no swizzle, base offset 0
+  return d;
+}
+// kind::tf32, D = F32, A = B = TF32, both K-major, N = 64, M = 128
+constexpr uint32_t kIdesc = (1u << 4) | (2u << 7) | (2u << 10) | ((64u >> 3) << 17) |
+                            ((128u >> 4) << 24);
+
+__device__ __forceinline__ void mma_tf32(uint32_t dtmem, uint64_t a, uint64_t b, uint32_t acc) {
+  asm volatile(
+      "{\n.reg .pred p;\nsetp.ne.b32 p, %4, 0;\n"
+      "tcgen05.mma.cta_group::1.kind::tf32 [%0], %1, %2, %3, p;\n}\n" ::"r"(dtmem),
+      "l"(a), "l"(b), "r"(kIdesc), "r"(acc));
+}
+
+// B operands: for every (v, c): [post hi | post lo | pre hi | pre lo], each
+// 64 x 64 in core order; post = P_v (rows = parent state), pre = P_v^T.
+__global__ void k_tc_prep(Dims d, const double *__restrict__ P64, const int *__restrict__ parent,
+                          float *__restrict__ tcB) {
+  const int v = blockIdx.x / d.C, c = blockIdx.x % d.C;
+  if (parent[v] < 0) return;
+  const double *P = P64 + ((size_t)v * d.C + c) * d.KK;
+  float *out = tcB + ((size_t)v * d.C + c) * 4 * kTile4;
+  for (int idx = threadIdx.x; idx < kTile4; idx += blockDim.x) {
+    const int r = idx >> 6, k = idx & 63;
+    const bool in = r < d.K && k < d.K;
+    const float vp = in ? (float)P[r * d.K + k] : 0.f;   // post: B[r][k] = P[r][k]
+    const float vq = in ? (float)P[k * d.K + r] : 0.f;   // pre:  B[r][k] = P[k][r]
+    const float hp = to_tf32(vp), hq = to_tf32(vq);
+    const int o = core_off(r, k);
+    out[o] = hp;
+    out[kTile4 + o] = to_tf32(vp - hp);
+    out[2 * kTile4 + o] = hq;
+    out[3 * kTile4 + o] = to_tf32(vq - hq);
+  }
+}
+
+// Shared memory of one tile: A hi, A lo (32 KB each), B hi, B lo (16 KB each).
+constexpr size_t kTcSmem = sizeof(float) * (2 * kATile + 2 * kTile4) + 1024;
+
+// A: the thread's own row (rows >= rows read as zero) -> hi / lo in core order.
+__device__ __forceinline__ void tc_stage_A(const float *A, int lda, int rows, float *sm) {
+  float *sAh = sm, *sAl = sAh + kATile;
+  const int r = threadIdx.x;
+  const float4 *src = reinterpret_cast<const float4 *>(A + (size_t)r * lda);
+#pragma unroll 4
+  for (int q = 0; q < 16; q++) {
+    const float4 x = r < rows ? src[q] : make_float4(0.f, 0.f, 0.f, 0.f);
+    const float4 h = make_float4(to_tf32(x.x), to_tf32(x.y), to_tf32(x.z), to_tf32(x.w));
+    const float4 l = make_float4(to_tf32(x.x - h.x), to_tf32(x.y - h.y), to_tf32(x.z - h.z),
+                                 to_tf32(x.w - h.w));
+    const int o = core_off(r, 4 * q);
+    *reinterpret_cast<float4 *>(sAh + o) = h;
+    *reinterpret_cast<float4 *>(sAl + o) = l;
+  }
+}
+// B: hi | lo (2 x 16 KB) copied as laid out by k_tc_prep.
+__device__ __forceinline__ void tc_stage_B(const float *Bq, float *sm) {
+  const float4 *src = reinterpret_cast<const float4 *>(Bq);
+  float4 *dst = reinterpret_cast<float4 *>(sm + 2 * kATile);
+  for (int i = threadIdx.x; i < 2 * kTile4 / 4; i += kTcThr) dst[i] = src[i];
+}
+// Issue (thread 0) D[col..col+63] = A B^T with the three split products, then
+// signal mbar when they have completed.  Staged operands must be fenced and
+// the CTA synchronised before the call.
+__device__ __forceinline__ void tc_mma(uint32_t dtmem, float *sm, uint64_t *mbar) {
+  if (threadIdx.x != 0) return;
+  asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+  const uint32_t ah = su32(sm), al = ah + kATile * 4, bh = ah + 2 * kATile * 4,
+                 bl = bh + kTile4 * 4;
+  for (int ks = 0; ks < 8; ks++) {  // 8 TF32 of K per instruction = 256 bytes
+    const uint32_t o = ks * 256;
+    mma_tf32(dtmem, smem_desc(ah + o), smem_desc(bh + o), ks > 0);
+    mma_tf32(dtmem, smem_desc(ah + o), smem_desc(bl + o), 1);
+    mma_tf32(dtmem, smem_desc(al + o), smem_desc(bh + o), 1);
+  }
+  asm volatile(
+      "tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(
+          su32(mbar)));
+}
+__device__ __forceinline__ void tc_sync_staged() {
+  asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+  asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
+  __syncthreads();
+}
+// Bounded wait for the MMAs signalled on mbar; flips the phase.
+__device__ __forceinline__ bool tc_wait(uint64_t *mbar, uint32_t &phase) {
+  uint32_t done = 0;
+  for (int it = 0; it < (1 << 24) && !done; it++)
+    asm volatile(
+        "{\n.reg .pred p;\nmbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n"
+        "selp.u32 %0, 1, 0, p;\n}\n"
+        : "=r"(done)
+        : "r"(su32(mbar)), "r"(phase));
+  phase ^= 1u;
+  asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+  return done != 0;
+}
+// 16 columns of the thread's TMEM lane (warp w reads lanes 32w..32w+31).
+__device__ __forceinline__ void tc_ld16(uint32_t taddr, int col, float *out) {
+  uint32_t v[16];
+  const uint32_t a = taddr + ((uint32_t)(32 * (threadIdx.x >> 5)) << 16) + col;
+  asm volatile(
+      "tcgen05.ld.sync.aligned.32x32b.x16.b32 {%0,%1,%2,%3,%4,%5,%6,%7,%8,%9,%10,%11,%12,%13,%14,%"
+      "15}, [%16];"
+      : "=r"(v[0]), "=r"(v[1]), "=r"(v[2]), "=r"(v[3]), "=r"(v[4]), "=r"(v[5]), "=r"(v[6]),
+        "=r"(v[7]), "=r"(v[8]), "=r"(v[9]), "=r"(v[10]), "=r"(v[11]), "=r"(v[12]), "=r"(v[13]),
+        "=r"(v[14]), "=r"(v[15])
+      : "r"(a));
+  asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
+#pragma unroll
+  for (int j = 0; j < 16; j++) out[j] = __uint_as_float(v[j]);
+}
+
+// One 128-row tile: D[r][0..63] = sum_k A[r][k] B[n][k] for the rows r < rows
+// (A rows lda floats apart; rows >= rows read as zero and are not stored).
+// Returns false when the MMAs did not complete within the wait bound.
+__device__ bool tc_tile(const float *A, int lda, int rows, const float *Bq, float *D, int ldd,
+                        float *sm, uint32_t taddr, uint64_t *mbar, uint32_t &phase) {
+  tc_stage_A(A, lda, rows, sm);
+  tc_stage_B(Bq, sm);
+  tc_sync_staged();
+  tc_mma(taddr, sm, mbar);
+  if (!tc_wait(mbar, phase)) return false;
+  const int r = threadIdx.x;
+  float *drow = D + (size_t)r * ldd;
+#pragma unroll
+  for (int cb = 0; cb < 4; cb++) {
+    float v[16];
+    tc_ld16(taddr, cb * 16, v);
+    if (r < rows) {
+#pragma unroll
+      for (int q = 0; q < 4; q++)
+        *reinterpret_cast<float4 *>(drow + cb * 16 + 4 * q) =
+            make_float4(v[4 * q], v[4 * q + 1], v[4 * q + 2], v[4 * q + 3]);
+    }
+  }
+  asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
+  __syncthreads();  // shared memory and TMEM free for the next tile
+  return true;
+}
+
+// CTA prologue / epilogue: TMEM columns and the MMA-completion barrier.
+__device__ uint32_t tc_begin(uint32_t *s_tmem, uint64_t *mbar, uint32_t ncols) {
+  if ((threadIdx.x >> 5) == 0) {
+    asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(
+                     su32(s_tmem)),
+                 "r"(ncols));
+    asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;");
+  }
+  if (threadIdx.x == 0) asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(su32(mbar)), "r"(1));
+  asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+  asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
+  __syncthreads();
+  asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+  return *s_tmem;
+}
+__device__ void tc_end(uint32_t taddr, uint32_t ncols) {
+  asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
+  __syncthreads();
+  if ((threadIdx.x >> 5) == 0)
+    asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(taddr), "r"(ncols));
+}
+
+// Pre-order: U_v = P_v^T X_v for the non-tip children of one level's nodes.
+// grid = (tiles of 128 patterns, level nodes * 2 children, categories).
+__global__ void __launch_bounds__(kTcThr) k_tc_pre_u(Dims d, const int *__restrict__ lvl_nodes,
+                                                    int lvl_off, const int *__restrict__ child,
+                                                    const float *__restrict__ xbuf,
+                                                    const float *__restrict__ tcB,
+                                                    float *__restrict__ pre, int *status) {
+  extern __shared__ __align__(1024) float tsm[];
+  __shared__ uint32_t s_tmem;
+  __shared__ __align__(8) uint64_t mbar;
+  const int bi = blockIdx.y >> 1, x = blockIdx.y & 1, c = blockIdx.z;
+  const int u = lvl_nodes[lvl_off + bi];
+  const int v = child[2 * (u - d.N) + x];
+  if (v < d.N) return;  // tips carry no outside partial (uniform over the CTA)
+  float *sm = reinterpret_cast<float *>((reinterpret_cast<uintptr_t>(tsm) + 1023) & ~(uintptr_t)1023);
+  const uint32_t taddr = tc_begin(&s_tmem, &mbar, 64);
+  uint32_t phase = 0;
+  const int p0 = blockIdx.x * kRows;
+  const int rows = min(kRows, d.P - p0);
+  const float *A = xbuf + ((((size_t)bi * 2 + x) * d.C + c) * d.P + p0) * d.Kp;
+  const float *B = tcB + ((size_t)v * d.C + c) * 4 * kTile4 + 2 * kTile4;  // pre hi | lo
+  float *D = pre + ((((size_t)(v - d.N) * d.C + c) * d.P) + p0) * d.Kp;
+  if (!tc_tile(A, d.Kp, rows, B, D, d.Kp, sm, taddr, &mbar, phase) && threadIdx.x == 0)
+    atomicOr(status, ST_TIMEOUT);
+  tc_end(taddr, 64);
+}
+
+
+// Post-order level: for every node u of the level and category c, S of each
+// stored child by a tile product (tips: the table row of their code), then
+// L_u = S_0 o S_1 rescaled per pattern by 2^-e, e the binary exponent of the
+// max over (c, i) (frexp convention).  TMEM holds S for both children and all
+// categories: 2 C blocks of 64 columns.  grid = (tiles of 128 patterns, nodes).
+__global__ void __launch_bounds__(kTcThr) k_tc_post(Dims d, const int *__restrict__ lvl_nodes,
+                                                   int lvl_off, const int *__restrict__ child,
+                                                   const float *__restrict__ PT,
+                                                   const uint8_t *__restrict__ tips,
+                                                   const float *__restrict__ tcB, float *part,
+                                                   int16_t *__restrict__ scale, uint32_t ncols,
+                                                   int *status) {
+  extern __shared__ __align__(1024) float tsm[];
+  __shared__ uint32_t s_tmem;
+  __shared__ __align__(8) uint64_t mbar;
+  float *sm = reinterpret_cast<float *>((reinterpret_cast<uintptr_t>(tsm) + 1023) & ~(uintptr_t)1023);
+  const int u = lvl_nodes[lvl_off + blockIdx.y];
+  const int slot = u - d.N;
+  const int kid[2] = {child[2 * slot], child[2 * slot + 1]};
+  const uint32_t taddr = tc_begin(&s_tmem, &mbar, ncols);
+  uint32_t phase = 0;
+  const int p0 = blockIdx.x * kRows, rows = min(kRows, d.P - p0);
+  bool ok = true;
+  for (int c = 0; c < d.C && ok; c++)
+    for (int sd = 0; sd < 2 && ok; sd++) {
+      const int v = kid[sd];
+      if (v < d.N) continue;
+      tc_stage_A(part + ((((size_t)(v - d.N) * d.C + c) * d.P) + p0) * d.Kp, d.Kp, rows, sm);
+      tc_stage_B(tcB + ((size_t)v * d.C + c) * 4 * kTile4, sm);
+      tc_sync_staged();
+      tc_mma(taddr + (c * 2 + sd) * 64, sm, &mbar);
+      ok = tc_wait(&mbar, phase);
+    }
+  if (!ok) {
+    if (threadIdx.x == 0) atomicOr(status, ST_TIMEOUT);
+    tc_end(taddr, ncols);
+    return;
+  }
+  const int r = threadIdx.x, p = p0 + r;
+  const bool live = r < rows;
+  int code[2] = {0, 0};
+  for (int sd = 0; sd < 2; sd++)
+    if (kid[sd] < d.N && live) code[sd] = tips[(size_t)kid[sd] * d.Pp + p];
+  // S values of child sd, category c, columns cb*16.. (TMEM or the tip row)
+  auto load_s = [&](int sd, int c, int cb, float *s) {
+    if (kid[sd] >= d.N) {
+      tc_ld16(taddr, (c * 2 + sd) * 64 + cb * 16, s);
+    } else {
+      const float4 *row = reinterpret_cast<const float4 *>(
+          PT + (((size_t)kid[sd] * d.C + c) * d.NR + code[sd]) * d.Kp + cb * 16);
+#pragma unroll
+      for (int q = 0; q < 4; q++) {
+        const float4 t = row[q];
+        s[4 * q] = t.x;
+        s[4 * q + 1] = t.y;
+        s[4 * q + 2] = t.z;
+        s[4 * q + 3] = t.w;
+      }
+    }
+  };
+  float m = 0.f;
+  for (int c = 0; c < d.C; c++)
+    for (int cb = 0; cb < 4; cb++) {
+      float s0[16], s1[16];
+      load_s(0, c, cb, s0);
+      load_s(1, c, cb, s1);
+#pragma unroll
+      for (int j = 0; j < 16; j++)
+        if (cb * 16 + j < d.K) m = fmaxf(m, s0[j] * s1[j]);
+    }
+  int e = 0;
+  if (!(m <= 3.0e38f)) {
+    if (live) atomicOr(status, ST_NONFINITE);
+  } else if (m > 0.f) {
+    frexpf(m, &e);
+  }
+  for (int c = 0; c < d.C; c++) {
+    float *dst = part + ((((size_t)slot * d.C + c) * d.P) + p) * d.Kp;
+    for (int cb = 0; cb < 4; cb++) {
+      float s0[16], s1[16];
+      load_s(0, c, cb, s0);
+      load_s(1, c, cb, s1);
+      if (live) {
+#pragma unroll
+        for (int q = 0; q < 4; q++) {
+          float4 o;
+          o.x = cb * 16 + 4 * q + 0 < d.K ? ldexpf(s0[4 * q + 0] * s1[4 * q + 0], -e) : 0.f;
+          o.y = cb * 16 + 4 * q + 1 < d.K ? ldexpf(s0[4 * q + 1] * s1[4 * q + 1], -e) : 0.f;
+          o.z = cb * 16 + 4 * q + 2 < d.K ? ldexpf(s0[4 * q + 2] * s1[4 * q + 2], -e) : 0.f;
+          o.w = cb * 16 + 4 * q + 3 < d.K ? ldexpf(s0[4 * q + 3] * s1[4 * q + 3], -e) : 0.f;
+          *reinterpret_cast<float4 *>(dst + cb * 16 + 4 * q) = o;
+        }
+      }
+    }
+  }
+  if (live) scale[(size_t)slot * d.Pp + p] = (int16_t)e;
+  tc_end(taddr, ncols);
+}
+
+// Pre-order level, one category: X of both children of u,
+//   X_0 = U_u o S_1 2^-e_u,  X_1 = U_u o S_0 2^-e_u,
+// with S of stored children by tile products, into the adjoint scratch.
+// grid = (tiles of 128 patterns, nodes, categories).
+__global__ void __launch_bounds__(kTcThr) k_tc_pre_x(
+    Dims d, const int *__restrict__ lvl_nodes, int lvl_off, const int *__restrict__ child, int root,
+    const float *__restrict__ PT, const uint8_t *__restrict__ tips, const float *__restrict__ tcB,
+    const float *__restrict__ part, const float *__restrict__ pre, const int16_t *__restrict__ scale,
+    const double *__restrict__ pi, const double *__restrict__ catw,
+    const double *__restrict__ site_inv, float *__restrict__ xbuf, int *status) {
+  extern __shared__ __align__(1024) float tsm[];
+  __shared__ uint32_t s_tmem;
+  __shared__ __align__(8) uint64_t mbar;
+  float *sm = reinterpret_cast<float *>((reinterpret_cast<uintptr_t>(tsm) + 1023) & ~(uintptr_t)1023);
+  const int bi = blockIdx.y, c = blockIdx.z;
+  const int u = lvl_nodes[lvl_off + bi];
+  const int slot = u - d.N;
+  const int kid[2] = {child[2 * slot], child[2 * slot + 1]};
+  const uint32_t taddr = tc_begin(&s_tmem, &mbar, 128);
+  uint32_t phase = 0;
+  const int p0 = blockIdx.x * kRows, rows = min(kRows, d.P - p0);
+  bool ok = true;
+  for (int sd = 0; sd < 2 && ok; sd++) {
+    const int v = kid[sd];
+    if (v < d.N) continue;
+    tc_stage_A(part + ((((size_t)(v - d.N) * d.C + c) * d.P) + p0) * d.Kp, d.Kp, rows, sm);
+    tc_stage_B(tcB + ((size_t)v * d.C + c) * 4 * kTile4, sm);
+    tc_sync_staged();
+    tc_mma(taddr + sd * 64, sm, &mbar);
+    ok = tc_wait(&mbar, phase);
+  }
+  if (!ok) {
+    if (threadIdx.x == 0) atomicOr(status, ST_TIMEOUT);
+    tc_end(taddr, 128);
+    return;
+  }
+  const int r = threadIdx.x, p = p0 + r;
+  const bool live = r < rows;
+  const int pc = live ? p : p0;
+  int code[2] = {0, 0};
+  for (int sd = 0; sd < 2; sd++)
+    if (kid[sd] < d.N) code[sd] = tips[(size_t)kid[sd] * d.Pp + pc];
+  const int e = scale[(size_t)slot * d.Pp + pc];
+  const double rootw = (u == root) ? catw[c] * site_inv[pc] : 0.0;
+  const float *urow = pre + ((((size_t)slot * d.C + c) * d.P) + pc) * d.Kp;
+  float *x0 = xbuf + ((((size_t)bi * 2 + 0) * d.C + c) * d.P + pc) * d.Kp;
+  float *x1 = xbuf + ((((size_t)bi * 2 + 1) * d.C + c) * d.P + pc) * d.Kp;
+  for (int cb = 0; cb < 4; cb++) {
+    float s[2][16];
+    for (int sd = 0; sd < 2; sd++) {
+      if (kid[sd] >= d.N) {
+        tc_ld16(taddr, sd * 64 + cb * 16, s[sd]);
+      } else {
+        const float *row = PT + (((size_t)kid[sd] * d.C + c) * d.NR + code[sd]) * d.Kp + cb * 16;
+#pragma unroll
+        for (int j = 0; j < 16; j++) s[sd][j] = row[j];
+      }
+    }
+    if (live) {
+#pragma unroll
+      for (int j = 0; j < 16; j++) {
+        const int i = cb * 16 + j;
+        float uu = 0.f;
+        if (i < d.K) uu = (u == root) ? (float)(rootw * pi[i]) : urow[i];
+        x0[i] = i < d.K ? ldexpf(uu * s[1][j], -e) : 0.f;
+        x1[i] = i < d.K ? ldexpf(uu * s[0][j], -e) : 0.f;
+      }
+    }
+  }
+  tc_end(taddr, 128);
+}
+
+}  // namespace
+
+bool tc_path(const epoch_ctx *c) {
+  return c->precision == EPOCH_FP32_TC && !fast_k4(c) && c->d.Kp == 64 && c->d.C <= 4;
+}
+
+cudaError_t launch_tc_post(epoch_ctx *c, int level) {
+  const Dims &d = c->d;
+  const int w = c->h_level_off[level + 1] - c->h_level_off[level];
+  uint32_t ncols = 128;
+  while (ncols < (uint32_t)(2 * d.C * 64)) ncols <<= 1;
+  cudaFuncSetAttribute(k_tc_post, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kTcSmem);
+  k_tc_post<<<dim3(ceil_div(d.P, kRows), w), kTcThr, kTcSmem, c->stream>>>(
+      d, c->d_level_nodes, c->h_level_off[level], c->d_child, c->d_PT32, c->d_tips, c->d_tcB,
+      (float *)c->d_part, c->d_scale, ncols, c->d_status);
+  c->launches++;
+  return cudaGetLastError();
+}
+
+cudaError_t launch_tc_pre_x(epoch_ctx *c, int level, int root) {
+  const Dims &d = c->d;
+  const int w = c->h_level_off[level + 1] - c->h_level_off[level];
+  cudaFuncSetAttribute(k_tc_pre_x, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kTcSmem);
+  k_tc_pre_x<<<dim3(ceil_div(d.P, kRows), w, d.C), kTcThr, kTcSmem, c->stream>>>(
+      d, c->d_level_nodes, c->h_level_off[level], c->d_child, root, c->d_PT32, c->d_tips,
+      c->d_tcB, (const float *)c->d_part, (const float *)c->d_pre, c->d_scale, c->d_pi,
+      c->d_catw, c->d_site_inv, (float *)c->d_xbuf, c->d_status);
+  c->launches++;
+  return cudaGetLastError();
+}
+
+cudaError_t launch_tc_prep(epoch_ctx *c) {
+  const Dims &d = c->d;
+  k_tc_prep<<<d.nn * d.C, 256, 0, c->stream>>>(d, c->d_P64, c->d_parent, c->d_tcB);
+  c->launches++;
+  return cudaGetLastError();
+}
+
+cudaError_t launch_tc_pre_u(epoch_ctx *c, int level) {
+  const Dims &d = c->d;
+  const int w = c->h_level_off[level + 1] - c->h_level_off[level];
+  cudaFuncSetAttribute(k_tc_pre_u, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kTcSmem);
+  dim3 g(ceil_div(d.P, kRows), 2 * w, d.C);
+  k_tc_pre_u<<<g, kTcThr, kTcSmem, c->stream>>>(d, c->d_level_nodes, c->h_level_off[level],
+                                                 c->d_child, (const float *)c->d_xbuf, c->d_tcB,
+                                                 (float *)c->d_pre, c->d_status);
+  c->launches++;
+  return cudaGetLastError();
+}
+
+size_t tc_operand_floats(const epoch_ctx *c) {
+  return (size_t)(2 * c->max_taxa - 1) * c->d.C * 4 * kTile4;
+}
+
+}  // namespace epoch

@@ -10,7 +10,7 @@ import pytest
 import oracle
 import synth
 from paper_1309_3075_b300 import binding
-from paper_1309_3075_b300.binding import EPOCH_FP32, EPOCH_FP64, EpochLikelihood
+from paper_1309_3075_b300.binding import EPOCH_FP32, EPOCH_FP32_TC, EPOCH_FP64, EpochLikelihood
 
 pytestmark = pytest.mark.gpu
 
@@ -53,7 +53,8 @@ def test_gtr_full_size_lnl_and_gradient(gtr_full, prec, tol):
     assert maxrel(g["branch_rates"], ref["branch_rates"]) <= gtol
 
 
-@pytest.mark.parametrize("prec,tol", [(EPOCH_FP64, 1e-10), (EPOCH_FP32, 1e-5)])
+@pytest.mark.parametrize("prec,tol", [(EPOCH_FP64, 1e-10), (EPOCH_FP32, 1e-5),
+                                      (EPOCH_FP32_TC, 1e-5)])
 def test_gy94_full_size_sampled_sites(gy94_full, prec, tol):
     w = gy94_full
     lik = EpochLikelihood(w, precision=prec)
@@ -80,9 +81,11 @@ def test_gy94_full_size_gradient_vs_finite_differences(gy94_full):
     w = gy94_full
     lik = EpochLikelihood(w, precision=EPOCH_FP64)
     lik32 = EpochLikelihood(w, precision=EPOCH_FP32)
+    liktc = EpochLikelihood(w, precision=EPOCH_FP32_TC)
     try:
         lnl, g = lik.evaluate(with_gradient=True)
         _, g32 = lik32.evaluate(with_gradient=True)
+        lnltc, gtc = liktc.evaluate(with_gradient=True)
 
         def lnl_at(heights=None, bounds=None, Q=None):
             if Q is not None:
@@ -127,10 +130,13 @@ def test_gy94_full_size_gradient_vs_finite_differences(gy94_full):
             assert abs(g["params"][a] - fd4) <= 1e-4 * max(1.0, abs(fd4)), (w.param_names[a], g["params"][a], fd4)
         for k in ("heights", "boundaries", "params"):
             assert maxrel(g32[k], g[k]) <= 1e-4, k
+            assert maxrel(gtc[k], g[k]) <= 1e-4, ("tensor cores", k)
         assert abs(lnl - lik32.evaluate(with_gradient=False)[0]) <= 1e-5 * abs(lnl)
+        assert abs(lnl - lnltc) <= 1e-5 * abs(lnl)
     finally:
         lik.close()
         lik32.close()
+        liktc.close()
 
 
 def test_forest_full_size_sampled_trees():

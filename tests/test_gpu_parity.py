@@ -13,12 +13,13 @@ import pytest
 import oracle
 import synth
 from paper_1309_3075_b300 import binding
-from paper_1309_3075_b300.binding import EPOCH_FP32, EPOCH_FP64, EpochError, EpochLikelihood
+from paper_1309_3075_b300.binding import (EPOCH_FP32, EPOCH_FP32_TC, EPOCH_FP64, EpochError,
+                                          EpochLikelihood)
 
 pytestmark = pytest.mark.gpu
 
-LNL_TOL = {EPOCH_FP64: 1e-10, EPOCH_FP32: 1e-5}
-GRAD_TOL = {EPOCH_FP64: 1e-9, EPOCH_FP32: 1e-4}
+LNL_TOL = {EPOCH_FP64: 1e-10, EPOCH_FP32: 1e-5, EPOCH_FP32_TC: 1e-5}
+GRAD_TOL = {EPOCH_FP64: 1e-9, EPOCH_FP32: 1e-4, EPOCH_FP32_TC: 1e-4}
 
 
 @pytest.fixture(scope="module", autouse=True)
@@ -113,7 +114,7 @@ def test_branch_matrices_match_oracle(prec):
         lik.close()
 
 
-@pytest.mark.parametrize("prec", [EPOCH_FP64, EPOCH_FP32])
+@pytest.mark.parametrize("prec", [EPOCH_FP64, EPOCH_FP32, EPOCH_FP32_TC])
 def test_codon_small(prec):
     w = synth.small_codon(203, n_taxa=10, n_sites=120, n_cat=2, n_epochs=3)
     check_lnl(w, prec)
@@ -125,6 +126,17 @@ def test_codon_small(prec):
 def test_other_state_counts(prec, K):
     w = synth.tiny_tree_workload(300 + K, K=K, n_taxa=9, n_sites=300, n_epochs=3, n_cat=2,
                                  missing_frac=0.05)
+    check_lnl(w, prec)
+    check_grad(w, prec)
+
+
+@pytest.mark.parametrize("prec", [EPOCH_FP32_TC])
+@pytest.mark.parametrize("K,P", [(50, 300), (64, 129)])
+def test_tensor_core_large_state_spaces(prec, K, P):
+    """Tensor-core tiles: K = 50 asymmetric traits and K = 64 (no padding),
+    pattern counts that leave a ragged last tile of 128."""
+    w = synth.tiny_tree_workload(320 + K, K=K, n_taxa=12, n_sites=P, n_epochs=3, n_cat=2,
+                                 reversible=(K == 64), missing_frac=0.05)
     check_lnl(w, prec)
     check_grad(w, prec)
 
