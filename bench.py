@@ -125,6 +125,27 @@ class ClockSampler:
 # K = 4 FP32 layout: 16 B per (category, pattern) vector, 1 B tip codes,
 # 2 B scale exponents) plus the root log-sum
 # ---------------------------------------------------------------------------
+# DRAM bytes of one partials pass (the k4_post levels, k4_walk_post and
+# k4_site_lnl of one evaluation) on the GTR 500-taxon workload, from one ncu
+# capture with warm L2 (profiles/k4_passes_gtr500.md).  Reported only while
+# the kernel source is the one that was measured.
+PARTIALS_TRAFFIC = {"source": "paper_1309_3075_b300/csrc/k_k4.cu",
+                    "sha1": "1ec3d28838190857c8485d0e3a3d1d9b645be822", "bytes": 180061440}
+
+
+def measured_traffic(workload):
+    import hashlib
+    if workload != "gtr":
+        return None
+    path = os.path.join(os.path.dirname(os.path.abspath(__file__)), PARTIALS_TRAFFIC["source"])
+    try:
+        with open(path, "rb") as f:
+            digest = hashlib.sha1(f.read()).hexdigest()
+    except OSError:
+        return None
+    return PARTIALS_TRAFFIC["bytes"] if digest == PARTIALS_TRAFFIC["sha1"] else None
+
+
 def partials_bytes(w):
     """Bytes the partials pass (pruning, rescaling, root log-sum) must move in
     this design: every stored partial written once and read once by its
@@ -311,7 +332,8 @@ def run_ours(args, w, cfg, rank, world):
                                              "h2d_bytes_per_step": int(h2d_aln)}},
         "gpu_launches": int(launches),
         "roofline": {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s",
-                     "frac": achieved / peak, "traffic": None, "peak_source": peak_kind,
+                     "frac": achieved / peak, "traffic": measured_traffic(args.workload),
+                     "peak_source": peak_kind,
                      "kernel": "partials pass (post-order pruning + rescaling + root)",
                      "effective_gbs_all_nodes_stored": survey_bytes(w) / (part_ms * 1e-3) / 1e9,
                      "ms_per_launch": part_ms, "algorithmic_bytes": int(pbytes)},
