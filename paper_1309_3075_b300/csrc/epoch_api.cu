@@ -132,12 +132,12 @@ epoch_status read_status(epoch_ctx *c) {
 epoch_status enqueue_branch(epoch_ctx *c) {
   if (fast_k4(c) && c->d.reversible) {
     CK(launch_model_setup(c), "model setup kernel");
-    CK(launch_param_transform(c), "parameter transform kernel");
+    CK(fork_side(c, 0, [&] { return launch_param_transform(c); }), "parameter transform kernel");
     CK(launch_branch_k4(c), "branch matrix kernel");
   } else {
     CK(launch_segments(c), "segments kernel");
     CK(launch_model_setup(c), "model setup kernel");
-    CK(launch_param_transform(c), "parameter transform kernel");
+    CK(fork_side(c, 0, [&] { return launch_param_transform(c); }), "parameter transform kernel");
     CK(launch_branch_matrices(c), "branch matrix kernel");
   }
   if (fast_k4(c)) CK(launch_pair_tables_k4(c), "pair table kernel");
@@ -376,6 +376,12 @@ void epoch_destroy(epoch_ctx *c) {
   if (c->h_tips_staging) cudaFreeHost(c->h_tips_staging);
   for (cudaEvent_t e : c->tips_staging_ev)
     if (e) cudaEventDestroy(e);
+  for (int k = 0; k < 2; k++) {
+    if (c->side[k]) cudaStreamSynchronize(c->side[k]);
+    if (c->side[k]) cudaStreamDestroy(c->side[k]);
+    if (c->fork_ev[k]) cudaEventDestroy(c->fork_ev[k]);
+    if (c->join_ev[k]) cudaEventDestroy(c->join_ev[k]);
+  }
   if (c->own_stream && c->stream) cudaStreamDestroy(c->stream);
   delete c;
 }
@@ -445,6 +451,14 @@ epoch_status epoch_create(epoch_ctx **out, int states, int n_epochs, const doubl
       return EPOCH_ERR_CUDA;
     }
     c->own_stream = true;
+  }
+  for (int k = 0; k < 2; k++) {
+    if (cudaStreamCreateWithFlags(&c->side[k], cudaStreamNonBlocking) != cudaSuccess ||
+        cudaEventCreateWithFlags(&c->fork_ev[k], cudaEventDisableTiming) != cudaSuccess ||
+        cudaEventCreateWithFlags(&c->join_ev[k], cudaEventDisableTiming) != cudaSuccess) {
+      epoch_destroy(c);
+      return EPOCH_ERR_CUDA;
+    }
   }
 
   const int nn_max = 2 * max_taxa - 1, ni_max = max_taxa - 1;
@@ -866,6 +880,7 @@ epoch_status epoch_compute_branch_matrices(epoch_ctx *c) {
   if (s != EPOCH_OK) return s;
   s = enqueue_branch(c);
   if (s != EPOCH_OK) return s;
+  CK(join_sides(c), "join");
   c->have |= HAVE_BRANCH;
   c->have &= ~HAVE_PARTIALS;
   return EPOCH_OK;
@@ -877,6 +892,7 @@ epoch_status epoch_update_partials(epoch_ctx *c) {
   if (s != EPOCH_OK) return s;
   s = enqueue_partials(c);
   if (s != EPOCH_OK) return s;
+  CK(join_sides(c), "join");
   c->have |= HAVE_PARTIALS;
   return EPOCH_OK;
 }
@@ -913,6 +929,7 @@ epoch_status epoch_gradient(epoch_ctx *c, double *d_heights, double *d_boundarie
     return fail(c, EPOCH_ERR_UNSUPPORTED, "parameter gradients need reversible=1");
   s = enqueue_gradient(c);
   if (s != EPOCH_OK) return s;
+  CK(join_sides(c), "join");
   return copy_grad_out(c, d_heights, d_boundaries, d_params, d_branch_rates);
 }
 
@@ -944,6 +961,8 @@ epoch_status epoch_evaluate_async(epoch_ctx *c, int with_gradient) {
     epoch_status es = enqueue_branch(c);
     if (es == EPOCH_OK) es = enqueue_partials(c);
     if (es == EPOCH_OK && g) es = enqueue_gradient(c);
+    cudaError_t je = join_sides(c);  // every side branch rejoins before the capture ends
+    if (es == EPOCH_OK && je != cudaSuccess) es = cuda_fail(c, je, "join");
     cudaError_t ee = cudaStreamEndCapture(c->stream, &graph);
     c->capturing = false;
     if (es != EPOCH_OK) {

@@ -58,6 +58,12 @@ struct epoch_ctx {
   int precision = 0;
   cudaStream_t stream = nullptr;
   bool own_stream = false;
+  // side branches: work no later kernel of the pass needs runs off the main
+  // stream (captured as parallel graph branches); 0: parameter transform,
+  // 1: per-pattern log-sum
+  cudaStream_t side[2] = {nullptr, nullptr};
+  cudaEvent_t fork_ev[2] = {nullptr, nullptr}, join_ev[2] = {nullptr, nullptr};
+  bool side_pending[2] = {false, false};
   std::string err;
   unsigned have = 0;
   int normalise = 1;
@@ -208,5 +214,34 @@ inline bool fast_k4(const epoch_ctx *c) {
 }
 
 inline int ceil_div(long long a, long long b) { return (int)((a + b - 1) / b); }
+
+// Enqueue `launch` (which launches on c->stream) on side stream s after all
+// work queued so far on the main stream; join_side makes the main stream wait
+// for it.  Every fork is joined before a capture ends or a call returns.
+template <class F>
+cudaError_t fork_side(epoch_ctx *c, int s, F launch) {
+  if (!c->side[s]) return launch();
+  cudaError_t e = cudaEventRecord(c->fork_ev[s], c->stream);
+  if (e == cudaSuccess) e = cudaStreamWaitEvent(c->side[s], c->fork_ev[s], 0);
+  if (e != cudaSuccess) return e;
+  cudaStream_t keep = c->stream;
+  c->stream = c->side[s];
+  e = launch();
+  c->stream = keep;
+  if (e != cudaSuccess) return e;
+  e = cudaEventRecord(c->join_ev[s], c->side[s]);
+  c->side_pending[s] = (e == cudaSuccess);
+  return e;
+}
+inline cudaError_t join_side(epoch_ctx *c, int s) {
+  if (!c->side_pending[s]) return cudaSuccess;
+  c->side_pending[s] = false;
+  return cudaStreamWaitEvent(c->stream, c->join_ev[s], 0);
+}
+inline cudaError_t join_sides(epoch_ctx *c) {
+  cudaError_t e = join_side(c, 0);
+  cudaError_t e2 = join_side(c, 1);
+  return e != cudaSuccess ? e : e2;
+}
 
 }  // namespace epoch

@@ -607,6 +607,10 @@ cudaError_t launch_adjoint(epoch_ctx *c) {
 }
 
 cudaError_t launch_chain_rule(epoch_ctx *c) {
+  {
+    cudaError_t je = join_side(c, 0);  // the parameter transform
+    if (je != cudaSuccess) return je;
+  }
   const Dims &d = c->d;
   dim3 grid(d.nn, d.C);
   const int threads = d.KK >= 1024 ? 256 : (d.KK >= 256 ? 128 : 32);

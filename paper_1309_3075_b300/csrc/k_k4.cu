@@ -673,8 +673,8 @@ __global__ void k4_G_reduce(Dims d, int gstride, const int *__restrict__ parent,
 
 // lnL_p = log(scaled root sum) + ln2 * sum_u e_u(p); block sums of n_p lnL_p
 // reduced in a fixed order by the last block to finish.  Block = 32 patterns
-// x 32 warps; warp w adds the exponents of nodes w, w + 32, ...
-constexpr int kLnlWarps = 32;
+// x 8 warps; warp w adds the exponents of nodes w, w + 8, ...
+constexpr int kLnlWarps = 8;
 __global__ void __launch_bounds__(32 * kLnlWarps) k4_site_lnl(Dims d, const int16_t *__restrict__ scale,
                                                               const double *__restrict__ site_log,
                                                               const double *__restrict__ pw,
@@ -809,12 +809,16 @@ cudaError_t post(epoch_ctx *c) {
   }
   cudaError_t err = walk_dispatch(c, true);
   if (err != cudaSuccess) return err;
-  cudaMemsetAsync(c->d_ctl, 0, sizeof(int), c->stream);
-  k4_site_lnl<<<ceil_div(c->d.P, 32), 32 * kLnlWarps, 0, c->stream>>>(c->d, c->d_scale, c->d_site_log,
-                                                           c->d_pw, c->d_site_lnl,
-                                                           c->d_lnl_part, c->d_ctl, c->d_lnl);
-  c->launches++;
-  return cudaGetLastError();
+  // the log-sum feeds no later kernel of the evaluation: it runs beside the
+  // adjoint pass (joined before the results are read)
+  return fork_side(c, 1, [&] {
+    cudaMemsetAsync(c->d_ctl, 0, sizeof(int), c->stream);
+    k4_site_lnl<<<ceil_div(c->d.P, 32), 32 * kLnlWarps, 0, c->stream>>>(
+        c->d, c->d_scale, c->d_site_log, c->d_pw, c->d_site_lnl, c->d_lnl_part, c->d_ctl,
+        c->d_lnl);
+    c->launches++;
+    return cudaGetLastError();
+  });
 }
 
 cudaError_t pre(epoch_ctx *c) {
