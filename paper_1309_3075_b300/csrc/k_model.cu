@@ -101,10 +101,23 @@ __device__ double block_sum(double x, double *red) {
 //   3. A' = U^T S U in FP64 (off-diagonal ~1e-7), then exact FP64 Jacobi
 //      sweeps on A' (quadratic convergence: two sweeps to 1e-16), U <- U J.
 // ---------------------------------------------------------------------------
-// FP64: the exact angle (the annihilated entry is then set to zero).
+// FP64: the exact angle (the annihilated entry is then set to zero).  In
+// the polishing sweeps the pivot is tiny against the diagonal gap, so
+// t = tan(angle) = r (1 - r^2 + 2 r^4) with r = a_pq / (a_qq - a_pp) and
+// c = 1 - t^2 / 2 + 3 t^4 / 8 hold to rounding for |r| < 1e-5 and need no
+// square root (each FP64 instruction is expensive here).
 __device__ __forceinline__ void jacobi_rotation(double app, double aqq, double apq, double &c,
                                                 double &s) {
-  const double theta = (aqq - app) / (2.0 * apq);
+  const double gap = aqq - app;
+  if (fabs(apq) < 1e-5 * fabs(gap)) {
+    const double r = apq / gap, r2 = r * r;
+    const double t = r * (1.0 - r2 * (1.0 - 2.0 * r2));
+    const double t2 = t * t;
+    c = 1.0 - t2 * (0.5 - 0.375 * t2);
+    s = t * c;
+    return;
+  }
+  const double theta = gap / (2.0 * apq);
   double t;
   if (fabs(theta) > 1e18)
     t = 0.5 / theta;
