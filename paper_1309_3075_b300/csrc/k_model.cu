@@ -211,6 +211,63 @@ __device__ __forceinline__ double jacobi_sweeps(T *A, T *U, int Kr, double tol2,
   return off;
 }
 
+// Cyclic Jacobi on a symmetric 4 x 4 FP32 matrix held in registers by one
+// thread (every index is a compile-time constant): sweeps over the pairs
+// (0,1) (0,2) (0,3) (1,2) (1,3) (2,3) until the squared off-diagonal norm is
+// <= tol2 (at most 12 sweeps).  A and U: row-major in shared memory, U = I on
+// entry; A is overwritten by the rotated matrix, U by the rotations.
+__device__ __forceinline__ void rot4(float (&a)[4][4], float (&u)[4][4], int p, int q) {
+  const float apq = a[p][q];
+  if (apq == 0.f) return;
+  float c, s;
+  jacobi_rotation(a[p][p], a[q][q], apq, c, s);
+#pragma unroll
+  for (int k = 0; k < 4; k++) {  // rows p, q
+    const float x = a[p][k], y = a[q][k];
+    a[p][k] = c * x - s * y;
+    a[q][k] = s * x + c * y;
+  }
+#pragma unroll
+  for (int k = 0; k < 4; k++) {  // columns p, q
+    const float x = a[k][p], y = a[k][q];
+    a[k][p] = c * x - s * y;
+    a[k][q] = s * x + c * y;
+    const float ux = u[k][p], uy = u[k][q];
+    u[k][p] = c * ux - s * uy;
+    u[k][q] = s * ux + c * uy;
+  }
+  a[p][q] = 0.f;
+  a[q][p] = 0.f;
+}
+__device__ void jacobi4_registers(float *A, float *U, float tol2) {
+  float a[4][4], u[4][4];
+#pragma unroll
+  for (int i = 0; i < 4; i++)
+#pragma unroll
+    for (int j = 0; j < 4; j++) {
+      a[i][j] = A[i * 4 + j];
+      u[i][j] = (i == j) ? 1.f : 0.f;
+    }
+  for (int sweep = 0; sweep < 12; sweep++) {
+    const float off = a[0][1] * a[0][1] + a[0][2] * a[0][2] + a[0][3] * a[0][3] +
+                      a[1][2] * a[1][2] + a[1][3] * a[1][3] + a[2][3] * a[2][3];
+    if (off <= tol2) break;
+    rot4(a, u, 0, 1);
+    rot4(a, u, 0, 2);
+    rot4(a, u, 0, 3);
+    rot4(a, u, 1, 2);
+    rot4(a, u, 1, 3);
+    rot4(a, u, 2, 3);
+  }
+#pragma unroll
+  for (int i = 0; i < 4; i++)
+#pragma unroll
+    for (int j = 0; j < 4; j++) {
+      A[i * 4 + j] = a[i][j];
+      U[i * 4 + j] = u[i][j];
+    }
+}
+
 // C = op(X) Y for K x K row-major FP64 matrices in shared memory (op = X^T
 // when tx); every thread forms whole entries of C.
 template <int KT>
@@ -280,8 +337,14 @@ __global__ void k_model_setup(Dims d, int normalise, const double *__restrict__ 
     part += A[idx] * A[idx];
   }
   const double fro2 = block_sum(part, red);
-  // 1. FP32 rotations
-  jacobi_sweeps<float, KT>(A32, U32, K, 1e-12 * fro2, 40, red, cs32, sn32, pq);
+  // 1. FP32 rotations (K = 4: one thread, the matrix in registers)
+  if constexpr (KT == 4) {
+    __syncthreads();
+    if (tid == 0) jacobi4_registers(A32, U32, (float)(1e-12 * fro2));
+    __syncthreads();
+  } else {
+    jacobi_sweeps<float, KT>(A32, U32, K, 1e-12 * fro2, 40, red, cs32, sn32, pq);
+  }
   // 2. orthogonal U in FP64
   for (int idx = tid; idx < KK; idx += nt) U[idx] = (double)U32[idx];
   __syncthreads();
