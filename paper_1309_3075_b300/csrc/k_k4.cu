@@ -337,8 +337,9 @@ __device__ __forceinline__ void pre_node(const K4Args &g, int slot, bool is_root
   const int pbase = blockIdx.x * kTP * m + lp;
   // stage[buf][k][operand][thread]
   auto sp = [&](int buf, int k, int o) { return stage + ((buf * kPreB + k) * 3 + o) * kThr + threadIdx.x; };
-  PreSmall nxt[kPreB];
-  auto issue = [&](int j0, int buf) {
+  // two register sets for the small per-pattern values, used in turn so a
+  // set's loads have a whole compute phase to land before they are read
+  auto issue = [&](int j0, int buf, PreSmall (&nxt)[kPreB]) {
 #pragma unroll
     for (int k = 0; k < kPreB; k++) {
       const int p = pbase + GS * (j0 + k);
@@ -356,15 +357,7 @@ __device__ __forceinline__ void pre_node(const K4Args &g, int slot, bool is_root
     }
     cp_async_commit();
   };
-  issue(0, 0);
-  int buf = 0;
-  for (int j0 = 0; j0 < npat; j0 += kPreB, buf ^= 1) {
-    PreSmall cur[kPreB];
-#pragma unroll
-    for (int k = 0; k < kPreB; k++) cur[k] = nxt[k];
-    if (j0 + kPreB < npat) issue(j0 + kPreB, buf ^ 1);
-    else cp_async_commit();  // empty group keeps the count
-    cp_async_wait_prev();    // this buffer's copies have landed
+  auto compute = [&](int j0, int buf, const PreSmall (&cur)[kPreB]) {
 #pragma unroll
     for (int k = 0; k < kPreB; k++) {
       const int p = pbase + GS * (j0 + k);
@@ -412,6 +405,19 @@ __device__ __forceinline__ void pre_node(const K4Args &g, int slot, bool is_root
           acc[16 + i * 4 + j] += xb[i] * lb[j];
         }
     }
+  };
+  PreSmall sa[kPreB], sb[kPreB];
+  issue(0, 0, sa);
+  for (int j0 = 0; j0 < npat; j0 += 2 * kPreB) {
+    if (j0 + kPreB < npat) issue(j0 + kPreB, 1, sb);
+    else cp_async_commit();  // empty group keeps the count
+    cp_async_wait_prev();    // buffer 0's copies have landed
+    compute(j0, 0, sa);
+    if (j0 + kPreB >= npat) break;
+    if (j0 + 2 * kPreB < npat) issue(j0 + 2 * kPreB, 0, sa);
+    else cp_async_commit();
+    cp_async_wait_prev();    // buffer 1's copies have landed
+    compute(j0 + kPreB, 1, sb);
   }
   asm volatile("cp.async.wait_all;\n" ::: "memory");
 }
