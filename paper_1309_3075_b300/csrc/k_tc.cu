@@ -36,6 +36,16 @@ __device__ __forceinline__ float to_tf32(float x) {
   asm("cvt.rna.tf32.f32 %0, %1;" : "=r"(r) : "f"(x));
   return __uint_as_float(r);
 }
+// x * 2^-e for the binary exponent e of a value in (0, 2] (e in [-148, 1]),
+// exactly: one multiply by 2^-e when -e <= 126, else 2^126 then 2^(-e-126).
+struct Pow2 {
+  float a, b;
+};
+__device__ __forceinline__ Pow2 pow2_neg(int e) {
+  if (e >= -126) return {__int_as_float((127 - e) << 23), 1.f};
+  return {__int_as_float(253 << 23), __int_as_float((1 - e) << 23)};
+}
+__device__ __forceinline__ float sc(float x, Pow2 f) { return (x * f.a) * f.b; }
 __device__ __forceinline__ uint32_t su32(const void *p) {
   return (uint32_t)__cvta_generic_to_shared(p);
 }
@@ -310,6 +320,7 @@ __global__ void __launch_bounds__(kTcThr) k_tc_post(Dims d, const int *__restric
   } else if (m > 0.f) {
     frexpf(m, &e);
   }
+  const Pow2 f = pow2_neg(e);
   for (int c = 0; c < d.C; c++) {
     float *dst = part + ((((size_t)slot * d.C + c) * d.P) + p) * d.Kp;
     for (int cb = 0; cb < 4; cb++) {
@@ -319,12 +330,13 @@ __global__ void __launch_bounds__(kTcThr) k_tc_post(Dims d, const int *__restric
       if (live) {
 #pragma unroll
         for (int q = 0; q < 4; q++) {
+          const int i = cb * 16 + 4 * q;
           float4 o;
-          o.x = cb * 16 + 4 * q + 0 < d.K ? ldexpf(s0[4 * q + 0] * s1[4 * q + 0], -e) : 0.f;
-          o.y = cb * 16 + 4 * q + 1 < d.K ? ldexpf(s0[4 * q + 1] * s1[4 * q + 1], -e) : 0.f;
-          o.z = cb * 16 + 4 * q + 2 < d.K ? ldexpf(s0[4 * q + 2] * s1[4 * q + 2], -e) : 0.f;
-          o.w = cb * 16 + 4 * q + 3 < d.K ? ldexpf(s0[4 * q + 3] * s1[4 * q + 3], -e) : 0.f;
-          *reinterpret_cast<float4 *>(dst + cb * 16 + 4 * q) = o;
+          o.x = i + 0 < d.K ? sc(s0[4 * q + 0] * s1[4 * q + 0], f) : 0.f;
+          o.y = i + 1 < d.K ? sc(s0[4 * q + 1] * s1[4 * q + 1], f) : 0.f;
+          o.z = i + 2 < d.K ? sc(s0[4 * q + 2] * s1[4 * q + 2], f) : 0.f;
+          o.w = i + 3 < d.K ? sc(s0[4 * q + 3] * s1[4 * q + 3], f) : 0.f;
+          *reinterpret_cast<float4 *>(dst + i) = o;
         }
       }
     }
@@ -375,7 +387,7 @@ __global__ void __launch_bounds__(kTcThr) k_tc_pre_x(
   int code[2] = {0, 0};
   for (int sd = 0; sd < 2; sd++)
     if (kid[sd] < d.N) code[sd] = tips[(size_t)kid[sd] * d.Pp + pc];
-  const int e = scale[(size_t)slot * d.Pp + pc];
+  const Pow2 f = pow2_neg(scale[(size_t)slot * d.Pp + pc]);
   const double rootw = (u == root) ? catw[c] * site_inv[pc] : 0.0;
   const float *urow = pre + ((((size_t)slot * d.C + c) * d.P) + pc) * d.Kp;
   float *x0 = xbuf + ((((size_t)bi * 2 + 0) * d.C + c) * d.P + pc) * d.Kp;
@@ -393,12 +405,24 @@ __global__ void __launch_bounds__(kTcThr) k_tc_pre_x(
     }
     if (live) {
 #pragma unroll
-      for (int j = 0; j < 16; j++) {
-        const int i = cb * 16 + j;
-        float uu = 0.f;
-        if (i < d.K) uu = (u == root) ? (float)(rootw * pi[i]) : urow[i];
-        x0[i] = i < d.K ? ldexpf(uu * s[1][j], -e) : 0.f;
-        x1[i] = i < d.K ? ldexpf(uu * s[0][j], -e) : 0.f;
+      for (int q = 0; q < 4; q++) {
+        const int i = cb * 16 + 4 * q;
+        float4 uu;
+        if (u == root) {
+          uu = make_float4(i < d.K ? (float)(rootw * pi[i]) : 0.f,
+                           i + 1 < d.K ? (float)(rootw * pi[i + 1]) : 0.f,
+                           i + 2 < d.K ? (float)(rootw * pi[i + 2]) : 0.f,
+                           i + 3 < d.K ? (float)(rootw * pi[i + 3]) : 0.f);
+        } else {
+          uu = *reinterpret_cast<const float4 *>(urow + i);  // zero beyond K
+        }
+        const float *a = s[1] + 4 * q, *b = s[0] + 4 * q;
+        *reinterpret_cast<float4 *>(x0 + i) =
+            make_float4(sc(uu.x * a[0], f), sc(uu.y * a[1], f), sc(uu.z * a[2], f),
+                        sc(uu.w * a[3], f));
+        *reinterpret_cast<float4 *>(x1 + i) =
+            make_float4(sc(uu.x * b[0], f), sc(uu.y * b[1], f), sc(uu.z * b[2], f),
+                        sc(uu.w * b[3], f));
       }
     }
   }
