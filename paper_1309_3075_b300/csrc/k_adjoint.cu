@@ -192,6 +192,30 @@ template <typename T>
 __device__ void mm(const Dims &d, const T *A, const T *B, T *C, bool ta, bool tb) {
   // C = op(A) op(B)
   const int K = d.K;
+  if (sizeof(T) == sizeof(float) && blockDim.x == 256 && K > 16 && K <= 64) {
+    // 16 x 16 threads, a 4 x 4 block of C each (rows bi.., columns bj..)
+    const int bi = (threadIdx.x >> 4) * 4, bj = (threadIdx.x & 15) * 4;
+    T acc[4][4] = {};
+    for (int m = 0; m < K; m++) {
+      T a[4], b[4];
+#pragma unroll
+      for (int r = 0; r < 4; r++) {
+        const int i = bi + r, j = bj + r;
+        a[r] = i < K ? (ta ? A[m * K + i] : A[i * K + m]) : (T)0;
+        b[r] = j < K ? (tb ? B[j * K + m] : B[m * K + j]) : (T)0;
+      }
+#pragma unroll
+      for (int r = 0; r < 4; r++)
+#pragma unroll
+        for (int q = 0; q < 4; q++) acc[r][q] += a[r] * b[q];
+    }
+#pragma unroll
+    for (int r = 0; r < 4; r++)
+#pragma unroll
+      for (int q = 0; q < 4; q++)
+        if (bi + r < K && bj + q < K) C[(bi + r) * K + bj + q] = acc[r][q];
+    return;
+  }
   for (int idx = threadIdx.x; idx < d.KK; idx += blockDim.x) {
     const int i = idx / K, j = idx % K;
     T acc = 0;
@@ -230,6 +254,17 @@ __device__ void seg_exp(const Dims &d, int s, double tau, const double *lam, con
     for (int i = threadIdx.x; i < K; i += blockDim.x) ev[i] = (T)exp(tau * lam[(size_t)s * K + i]);
     __syncthreads();
     const double *Vs = V + (size_t)s * KK, *Vi = Vinv + (size_t)s * KK;
+    if (sizeof(T) == sizeof(float) && blockDim.x == 256 && K > 16) {
+      // E = (V diag(ev)) V^-1 through shared memory and the tiled product
+      for (int idx = threadIdx.x; idx < KK; idx += blockDim.x) {
+        W[idx] = (T)Vs[idx] * ev[idx % K];
+        Y[idx] = (T)Vi[idx];
+      }
+      __syncthreads();
+      mm<T>(d, W, Y, Eo, false, false);
+      __syncthreads();
+      return;
+    }
     for (int idx = threadIdx.x; idx < KK; idx += blockDim.x) {
       const int i = idx / K, j = idx % K;
       T acc = 0;
