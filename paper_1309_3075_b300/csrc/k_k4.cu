@@ -46,6 +46,14 @@ constexpr int kWalkSlots = 32;  // value slots per walk thread (16 B each)
 constexpr size_t kWalkSmem = 160 * 1024;  // shared memory of a walk CTA at most
 enum : int { kTip = 0, kCherry = 1, kStored = 2 };
 
+// Programmatic dependent launch: a level kernel is launched while its
+// predecessor finishes; it reads only data of launches before the predecessor
+// (tables, topology) until pdl_wait() returns, which is when the predecessor
+// has completed and its writes are visible.  pdl_trigger() lets the next
+// level be scheduled as soon as every CTA of this one has passed its wait.
+__device__ __forceinline__ void pdl_wait() { asm volatile("griddepcontrol.wait;" ::: "memory"); }
+__device__ __forceinline__ void pdl_trigger() { asm volatile("griddepcontrol.launch_dependents;"); }
+
 __device__ __forceinline__ float4 mul4(float4 a, float4 b) {
   return make_float4(a.x * b.x, a.y * b.y, a.z * b.z, a.w * b.w);
 }
@@ -252,9 +260,11 @@ __device__ __forceinline__ void post_node(const K4Args &g, int u, const Kid &k0,
   }
 }
 
+// early = 1: the predecessor wrote none of the tables (see pdl_wait)
 template <int CMAX>
-__global__ void __launch_bounds__(kThr) k4_post(K4Args g, int off) {
+__global__ void __launch_bounds__(kThr) k4_post(K4Args g, int off, int early) {
   extern __shared__ float4 tabs[];
+  if (!early) pdl_wait();
   const int u = g.nodes[off + blockIdx.y];
   const int slot = u - g.d.N;
   Kid k0 = classify(g, g.child[2 * slot]), k1 = classify(g, g.child[2 * slot + 1]);
@@ -266,6 +276,8 @@ __global__ void __launch_bounds__(kThr) k4_post(K4Args g, int off) {
   float4 *t0 = tabs, *t1 = tabs + table_size(g, k0, false);
   load_table(g, k0, false, t0);
   load_table(g, k1, false, t1);
+  if (early) pdl_wait();
+  pdl_trigger();
   switch (k0.kind * 3 + k1.kind) {
     case 0: post_node<CMAX, kTip, kTip>(g, u, k0, k1, t0, t1); break;
     case 1: post_node<CMAX, kTip, kCherry>(g, u, k0, k1, t0, t1); break;
@@ -444,6 +456,8 @@ __global__ void __launch_bounds__(kThr, 2) k4_pre(K4Args g, int off, int Cp, int
   load_table(g, k0, true, t0);
   load_table(g, k1, true, t1);
   for (int i = threadIdx.x; i < d.NR; i += blockDim.x) Ltip[i] = onehot(i, g.masks);
+  pdl_wait();  // the level above (or the walk) has stored this level's U
+  pdl_trigger();
   __syncthreads();
   float acc[32];
 #pragma unroll
@@ -551,6 +565,8 @@ __global__ void __launch_bounds__(kWalkThr) k4_walk_post(K4Args g, const int4 *_
   const Dims &d = g.d;
   const int C = d.C;
   float4 *vals = walk_stage(g, W, nsteps, sm);
+  pdl_wait();
+  pdl_trigger();
   const int4 *sd = reinterpret_cast<const int4 *>(sm);
   const float4 *rows = sm + 4 * nsteps;
   const int c = threadIdx.x % CP, pl = threadIdx.x / CP;
@@ -611,6 +627,8 @@ __global__ void __launch_bounds__(kWalkThr) k4_walk_pre(K4Args g, const int4 *__
   const Dims &d = g.d;
   const int C = d.C;
   float4 *vals = walk_stage(g, W, nsteps, sm);
+  pdl_wait();
+  pdl_trigger();
   const int4 *sd = reinterpret_cast<const int4 *>(sm);
   const float4 *rows = sm + 4 * nsteps;
   const int c = threadIdx.x % CP, pl = threadIdx.x / CP;
@@ -730,6 +748,23 @@ __global__ void __launch_bounds__(32 * kLnlWarps) k4_site_lnl(Dims d, const int1
   }
 }
 
+// Launch with programmatic stream serialisation (see pdl_wait).
+template <typename Kern, typename... Args>
+cudaError_t launch_pdl(Kern kern, dim3 grid, dim3 block, size_t smem, cudaStream_t s,
+                       Args... args) {
+  cudaLaunchConfig_t cfg = {};
+  cfg.gridDim = grid;
+  cfg.blockDim = block;
+  cfg.dynamicSmemBytes = smem;
+  cfg.stream = s;
+  cudaLaunchAttribute at[1];
+  at[0].id = cudaLaunchAttributeProgrammaticStreamSerialization;
+  at[0].val.programmaticStreamSerializationAllowed = 1;
+  cfg.attrs = at;
+  cfg.numAttrs = 1;
+  return cudaLaunchKernelEx(&cfg, kern, args...);
+}
+
 K4Args make_args(epoch_ctx *c) {
   K4Args a{};
   a.d = c->d;
@@ -784,10 +819,12 @@ cudaError_t walk(epoch_ctx *c, bool post) {
   const int grid = ceil_div(c->d.P, kWalkThr / CP);
   if (post) {
     cudaFuncSetAttribute(k4_walk_post<CP>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
-    k4_walk_post<CP><<<grid, kWalkThr, smem, c->stream>>>(a, W, n);
+    cudaError_t e = launch_pdl(k4_walk_post<CP>, dim3(grid), dim3(kWalkThr), smem, c->stream, a, W, n);
+    if (e != cudaSuccess) return e;
   } else {
     cudaFuncSetAttribute(k4_walk_pre<CP>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
-    k4_walk_pre<CP><<<grid, kWalkThr, smem, c->stream>>>(a, W, n);
+    cudaError_t e = launch_pdl(k4_walk_pre<CP>, dim3(grid), dim3(kWalkThr), smem, c->stream, a, W, n);
+    if (e != cudaSuccess) return e;
   }
   c->launches++;
   return cudaGetLastError();
@@ -810,7 +847,11 @@ cudaError_t post(epoch_ctx *c) {
   const int last = std::max(c->k4_top, c->k4_first_level);
   for (int l = c->k4_first_level; l < last; l++) {
     const int w = c->h_level_off[l + 1] - c->h_level_off[l];
-    k4_post<CMAX><<<dim3(k4_tiles(c->d.P), w), kThr, smem, c->stream>>>(a, c->h_level_off[l]);
+    // the first level's predecessor wrote the cherry tables it loads
+    const int early = l > c->k4_first_level ? 1 : 0;
+    cudaError_t e = launch_pdl(k4_post<CMAX>, dim3(k4_tiles(c->d.P), w), dim3(kThr), smem,
+                               c->stream, a, c->h_level_off[l], early);
+    if (e != cudaSuccess) return e;
     c->launches++;
   }
   cudaError_t err = walk_dispatch(c, true);
@@ -836,7 +877,9 @@ cudaError_t pre(epoch_ctx *c) {
   if (err != cudaSuccess) return err;
   for (size_t i = 0; i + 2 < c->h_k4_launch.size(); i += 3) {
     const int off = c->h_k4_launch[i], w = c->h_k4_launch[i + 1], m = c->h_k4_launch[i + 2];
-    k4_pre<<<dim3(ceil_div(c->d.P, kTP * m), w), kThr, smem, c->stream>>>(a, off, Cp, m);
+    cudaError_t e = launch_pdl(k4_pre, dim3(ceil_div(c->d.P, kTP * m), w), dim3(kThr), smem,
+                               c->stream, a, off, Cp, m);
+    if (e != cudaSuccess) return e;
     c->launches++;
   }
   const long long nG = 4LL * c->d.nn * c->d.C * 16;
