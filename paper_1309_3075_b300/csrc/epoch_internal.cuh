@@ -215,6 +215,31 @@ inline bool fast_k4(const epoch_ctx *c) {
 
 inline int ceil_div(long long a, long long b) { return (int)((a + b - 1) / b); }
 
+// Programmatic dependent launch: a level kernel is launched while its
+// predecessor finishes; it reads only data of launches before the predecessor
+// (tables, topology) until pdl_wait() returns, which is when the predecessor
+// has completed and its writes are visible.  pdl_trigger() lets the next
+// level be scheduled as soon as every CTA of this one has passed its wait.
+__device__ __forceinline__ void pdl_wait() { asm volatile("griddepcontrol.wait;" ::: "memory"); }
+__device__ __forceinline__ void pdl_trigger() { asm volatile("griddepcontrol.launch_dependents;"); }
+
+// Launch with programmatic stream serialisation (see pdl_wait).
+template <typename Kern, typename... Args>
+cudaError_t launch_pdl(Kern kern, dim3 grid, dim3 block, size_t smem, cudaStream_t s,
+                       Args... args) {
+  cudaLaunchConfig_t cfg = {};
+  cfg.gridDim = grid;
+  cfg.blockDim = block;
+  cfg.dynamicSmemBytes = smem;
+  cfg.stream = s;
+  cudaLaunchAttribute at[1];
+  at[0].id = cudaLaunchAttributeProgrammaticStreamSerialization;
+  at[0].val.programmaticStreamSerializationAllowed = 1;
+  cfg.attrs = at;
+  cfg.numAttrs = 1;
+  return cudaLaunchKernelEx(&cfg, kern, args...);
+}
+
 // Enqueue `launch` (which launches on c->stream) on side stream s after all
 // work queued so far on the main stream; join_side makes the main stream wait
 // for it.  Every fork is joined before a capture ends or a call returns.

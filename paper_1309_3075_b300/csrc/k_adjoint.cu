@@ -454,6 +454,8 @@ __global__ void k_grad_reduce(Dims d, const int *__restrict__ parent, const int 
                               const int *__restrict__ seg_hi, const int *__restrict__ seg_lo,
                               const double *__restrict__ brate, const double *__restrict__ catr,
                               const T *__restrict__ gseg, int nb_nodes, double *__restrict__ out) {
+  pdl_wait();  // the segment terms
+  pdl_trigger();
   __shared__ double red[32];
   const int stride = 1 + d.np;
   // d lnL / d dt of segment (v, k) summed over categories
@@ -674,9 +676,11 @@ cudaError_t launch_chain_rule(epoch_ctx *c) {
           d, c->d_G, c->d_nseg, c->d_seg_mat, c->d_seg_dt, c->d_brate, c->d_catr, c->d_lam,
           c->d_V, c->d_Vinv, c->d_Q, c->d_Dth32, c->d_Dnz, (float *)c->d_gseg);
     }
-    k_grad_reduce<float><<<nblocks, 256, 0, c->stream>>>(
-        d, c->d_parent, c->d_child, c->d_nseg, c->d_seg_dt, c->d_seg_hi, c->d_seg_lo, c->d_brate,
-        c->d_catr, (const float *)c->d_gseg, nb_nodes, c->d_grad);
+    launch_pdl(k_grad_reduce<float>, dim3(nblocks), dim3(256), 0, c->stream, d,
+               (const int *)c->d_parent, (const int *)c->d_child, (const int *)c->d_nseg,
+               (const double *)c->d_seg_dt, (const int *)c->d_seg_hi, (const int *)c->d_seg_lo,
+               (const double *)c->d_brate, (const double *)c->d_catr, (const float *)c->d_gseg,
+               nb_nodes, c->d_grad);
   }
   c->launches += 2;
   return cudaGetLastError();

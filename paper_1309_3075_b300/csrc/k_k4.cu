@@ -46,14 +46,6 @@ constexpr int kWalkSlots = 32;  // value slots per walk thread (16 B each)
 constexpr size_t kWalkSmem = 160 * 1024;  // shared memory of a walk CTA at most
 enum : int { kTip = 0, kCherry = 1, kStored = 2 };
 
-// Programmatic dependent launch: a level kernel is launched while its
-// predecessor finishes; it reads only data of launches before the predecessor
-// (tables, topology) until pdl_wait() returns, which is when the predecessor
-// has completed and its writes are visible.  pdl_trigger() lets the next
-// level be scheduled as soon as every CTA of this one has passed its wait.
-__device__ __forceinline__ void pdl_wait() { asm volatile("griddepcontrol.wait;" ::: "memory"); }
-__device__ __forceinline__ void pdl_trigger() { asm volatile("griddepcontrol.launch_dependents;"); }
-
 __device__ __forceinline__ float4 mul4(float4 a, float4 b) {
   return make_float4(a.x * b.x, a.y * b.y, a.z * b.z, a.w * b.w);
 }
@@ -146,6 +138,8 @@ __device__ __forceinline__ Kid classify(const K4Args &g, int x) {
 // One CTA per internal node (non-cherries return); threads over (c, pair).
 __global__ void k4_pair_tables(Dims d, const float4 *__restrict__ PT, const int *__restrict__ child,
                                int root, float4 *__restrict__ pairS, float4 *__restrict__ pairL) {
+  pdl_wait();  // the branch tables
+  pdl_trigger();
   const int u = d.N + blockIdx.x;
   const int a = child[2 * blockIdx.x], b = child[2 * blockIdx.x + 1];
   if (a >= d.N || b >= d.N || u == root) return;
@@ -674,6 +668,8 @@ __global__ void __launch_bounds__(kWalkThr) k4_walk_pre(K4Args g, const int4 *__
 __global__ void k4_G_reduce(Dims d, int gstride, const int *__restrict__ parent,
                             const int *__restrict__ nt, const float *__restrict__ Gpart,
                             double *__restrict__ G) {
+  pdl_wait();  // the last adjoint level's tile sums
+  pdl_trigger();
   const long long t4 = (long long)blockIdx.x * blockDim.x + threadIdx.x;
   const long long idx = t4 >> 2;
   const int part = (int)(t4 & 3);
@@ -746,23 +742,6 @@ __global__ void __launch_bounds__(32 * kLnlWarps) k4_site_lnl(Dims d, const int1
     for (int k = 0; k < kLnlWarps; k++) s += redd[k];
     lnl[0] = s;
   }
-}
-
-// Launch with programmatic stream serialisation (see pdl_wait).
-template <typename Kern, typename... Args>
-cudaError_t launch_pdl(Kern kern, dim3 grid, dim3 block, size_t smem, cudaStream_t s,
-                       Args... args) {
-  cudaLaunchConfig_t cfg = {};
-  cfg.gridDim = grid;
-  cfg.blockDim = block;
-  cfg.dynamicSmemBytes = smem;
-  cfg.stream = s;
-  cudaLaunchAttribute at[1];
-  at[0].id = cudaLaunchAttributeProgrammaticStreamSerialization;
-  at[0].val.programmaticStreamSerializationAllowed = 1;
-  cfg.attrs = at;
-  cfg.numAttrs = 1;
-  return cudaLaunchKernelEx(&cfg, kern, args...);
 }
 
 K4Args make_args(epoch_ctx *c) {
@@ -883,10 +862,11 @@ cudaError_t pre(epoch_ctx *c) {
     c->launches++;
   }
   const long long nG = 4LL * c->d.nn * c->d.C * 16;
-  k4_G_reduce<<<ceil_div(nG, 256), 256, 0, c->stream>>>(c->d, a.gstride, c->d_parent, c->d_k4_nt,
-                                                        (const float *)c->d_Gpart, c->d_G);
+  cudaError_t e = launch_pdl(k4_G_reduce, dim3(ceil_div(nG, 256)), dim3(256), 0, c->stream,
+                             c->d, a.gstride, (const int *)c->d_parent, (const int *)c->d_k4_nt,
+                             (const float *)c->d_Gpart, c->d_G);
   c->launches++;
-  return cudaGetLastError();
+  return e;
 }
 
 }  // namespace
@@ -1033,12 +1013,13 @@ void k4_schedule(epoch_ctx *c) {
 
 cudaError_t launch_pair_tables_k4(epoch_ctx *c) {
   if (c->d.N < 2) return cudaSuccess;
-  k4_pair_tables<<<c->d.N - 1, 128, 0, c->stream>>>(c->d, reinterpret_cast<const float4 *>(c->d_PT32),
-                                                    c->d_child, c->root,
-                                                    reinterpret_cast<float4 *>(c->d_pairS),
-                                                    reinterpret_cast<float4 *>(c->d_pairL));
+  cudaError_t e = launch_pdl(k4_pair_tables, dim3(c->d.N - 1), dim3(128), 0, c->stream, c->d,
+                             reinterpret_cast<const float4 *>(c->d_PT32),
+                             (const int *)c->d_child, c->root,
+                             reinterpret_cast<float4 *>(c->d_pairS),
+                             reinterpret_cast<float4 *>(c->d_pairL));
   c->launches++;
-  return cudaGetLastError();
+  return e;
 }
 
 cudaError_t launch_partials_k4(epoch_ctx *c) {

@@ -35,6 +35,8 @@ __global__ void __launch_bounds__(128) k4_branch(Dims d, const double *__restric
                                                  double *__restrict__ seg_dt, int *__restrict__ seg_hi,
                                                  int *__restrict__ seg_lo, double *__restrict__ P64,
                                                  float *__restrict__ PT32) {
+  pdl_wait();  // the eigensystems
+  pdl_trigger();
   const int idx = blockIdx.x * blockDim.x + threadIdx.x;
   const int i = idx & 3, vc = idx >> 2;
   const int v = vc / d.C, c = vc % d.C;
@@ -159,6 +161,8 @@ __global__ void __launch_bounds__(128) k4_chain(Dims d, const double *__restrict
   for (int i = threadIdx.x; i < d.S * 4; i += blockDim.x) slam[i] = (float)lam[i];
   for (int i = threadIdx.x; i < d.np * d.S * 16; i += blockDim.x) sD[i] = Dth[i];
   for (int i = threadIdx.x; i < d.np * d.S; i += blockDim.x) sNz[i] = Dnz[i];
+  pdl_wait();  // G
+  pdl_trigger();
   __syncthreads();
   const int idx = blockIdx.x * blockDim.x + threadIdx.x;
   const int qq = idx & 3, vc = idx >> 2;
@@ -310,12 +314,16 @@ size_t k4_chain_smem(const Dims &d) {
 cudaError_t launch_branch_k4(epoch_ctx *c) {
   const Dims &d = c->d;
   const int n = d.nn * d.C * 4;
-  k4_branch<<<ceil_div(n, 64), 64, 0, c->stream>>>(
-      d, c->d_heights, c->d_parent, c->d_boundaries, c->d_phi, c->d_brate, c->d_catr, c->d_lam,
-      c->d_V, c->d_Vinv, c->d_masks, c->d_nseg, c->d_seg_mat, c->d_seg_dt, c->d_seg_hi,
-      c->d_seg_lo, c->d_P64, c->d_PT32);
+  cudaError_t e = launch_pdl(k4_branch, dim3(ceil_div(n, 64)), dim3(64), 0, c->stream, d,
+                             (const double *)c->d_heights, (const int *)c->d_parent,
+                             (const double *)c->d_boundaries, (const int *)c->d_phi,
+                             (const double *)c->d_brate, (const double *)c->d_catr,
+                             (const double *)c->d_lam, (const double *)c->d_V,
+                             (const double *)c->d_Vinv, (const unsigned long long *)c->d_masks,
+                             c->d_nseg, c->d_seg_mat, c->d_seg_dt, c->d_seg_hi, c->d_seg_lo,
+                             c->d_P64, c->d_PT32);
   c->launches++;
-  return cudaGetLastError();
+  return e;
 }
 
 cudaError_t launch_chain_k4(epoch_ctx *c) {
@@ -323,12 +331,15 @@ cudaError_t launch_chain_k4(epoch_ctx *c) {
   const int n = d.nn * d.C * 4;
   const size_t smem = k4_chain_smem(d);
   cudaFuncSetAttribute(k4_chain, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
-  k4_chain<<<ceil_div(n, 128), 128, smem, c->stream>>>(d, c->d_G, c->d_nseg, c->d_seg_mat,
-                                                    c->d_seg_dt, c->d_brate, c->d_catr, c->d_lam,
-                                                    c->d_V, c->d_Vinv, c->d_Dth32, c->d_Dnz,
-                                                    (float *)c->d_gseg);
+  cudaError_t e = launch_pdl(k4_chain, dim3(ceil_div(n, 128)), dim3(128), smem, c->stream, d,
+                             (const double *)c->d_G, (const int *)c->d_nseg,
+                             (const int *)c->d_seg_mat, (const double *)c->d_seg_dt,
+                             (const double *)c->d_brate, (const double *)c->d_catr,
+                             (const double *)c->d_lam, (const double *)c->d_V,
+                             (const double *)c->d_Vinv, (const float *)c->d_Dth32,
+                             (const int *)c->d_Dnz, (float *)c->d_gseg);
   c->launches++;
-  return cudaGetLastError();
+  return e;
 }
 
 }  // namespace epoch
