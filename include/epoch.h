@@ -214,6 +214,26 @@ epoch_status epoch_read_results(epoch_ctx *ctx, double *lnL, double *d_heights,
                                 double *d_boundaries, double *d_params,
                                 double *d_branch_rates);
 
+/* Zero-copy variants for callers whose arrays live on the device (a torch
+ * tensor's data pointer, on this context's device).  Both are async on the
+ * context's stream; order other streams after it with an event.
+ *
+ * epoch_set_heights_device: d_heights [2N-1] DEVICE pointer, copied on the
+ * device.  The tree check runs on the device too: a non-finite height or a
+ * parent below its child makes the next synchronising call (read_results,
+ * log_likelihood, gradient) return EPOCH_ERR_ARG.
+ *
+ * epoch_read_results_device: copies the results of the last
+ * epoch_evaluate_async into caller DEVICE memory, either pointer may be NULL:
+ *   d_lnL  [1]
+ *   d_grad [2(2N-1) + (E-1) + n_params]: d/d heights [2N-1], d/d boundaries
+ *          [E-1], d/d parameters [n_params], d/d branch rates [2N-1]
+ *          (the gradient part holds values only for with_gradient = 1).
+ * No status check: call epoch_read_results (or any synchronising call) to
+ * see device errors. */
+epoch_status epoch_set_heights_device(epoch_ctx *ctx, const double *d_heights);
+epoch_status epoch_read_results_device(epoch_ctx *ctx, double *d_lnL, double *d_grad);
+
 /* Counters: kernels launched by this context since creation (graph
  * replays count their kernels), and graph captures made. */
 epoch_status epoch_counters(const epoch_ctx *ctx, long long *kernel_launches,

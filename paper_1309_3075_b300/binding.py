@@ -58,6 +58,8 @@ _SIGS = {
     "epoch_evaluate_async": [_vp, C.c_int],
     "epoch_read_results": [_vp, _dp, _dp, _dp, _dp, _dp],
     "epoch_counters": [_vp, C.POINTER(C.c_longlong), C.POINTER(C.c_longlong)],
+    "epoch_set_heights_device": [_vp, _vp],
+    "epoch_read_results_device": [_vp, _vp, _vp],
     "epoch_site_log_sum_noalloc": [_vp, _vp, C.c_int, C.c_longlong, _vp, C.c_int, _vp, _vp,
                                    _vp],
     "epoch_batch_create": [C.POINTER(_vp), C.c_int, C.c_int, _ip, _ip, _ip, _vp],
@@ -255,6 +257,19 @@ def epoch_read_results(ctx, n_nodes=0, n_epochs=1, n_params=0, with_gradient=Tru
                        "branch_rates": dr}
 
 
+def epoch_set_heights_device(ctx, heights_ptr):
+    """heights_ptr: device address (int) of 2N-1 float64 values."""
+    _check(ctx, lib().epoch_set_heights_device(ctx, _vp(int(heights_ptr))),
+           "epoch_set_heights_device")
+
+
+def epoch_read_results_device(ctx, lnl_ptr=0, grad_ptr=0):
+    """Device addresses (int, 0 = not wanted); async on the context's stream."""
+    _check(ctx, lib().epoch_read_results_device(ctx, _vp(int(lnl_ptr)) if lnl_ptr else None,
+                                                _vp(int(grad_ptr)) if grad_ptr else None),
+           "epoch_read_results_device")
+
+
 def epoch_counters(ctx):
     a, b = C.c_longlong(0), C.c_longlong(0)
     _check(ctx, lib().epoch_counters(ctx, C.byref(a), C.byref(b)), "epoch_counters")
@@ -277,6 +292,7 @@ class EpochLikelihood:
         self.P = int(np.asarray(w.tips).shape[1])
         self.C = int(len(w.cat_rates))
         self.precision = precision
+        self.cuda_stream = cuda_stream
         phi = getattr(w, "epoch_to_matrix", None)
         self.ctx = epoch_create(self.K, self.E, w.boundaries, phi, self.S,
                                 max_taxa or self.N, self.P, self.C, precision, cuda_stream)

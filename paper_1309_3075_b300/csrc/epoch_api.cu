@@ -119,6 +119,9 @@ epoch_status read_status(epoch_ctx *c) {
   if (st == 0) return EPOCH_OK;
   CK(cudaMemsetAsync(c->d_status, 0, sizeof(int), c->stream), "cudaMemset(status)");
   if (st & ST_TIMEOUT) return fail(c, EPOCH_ERR_TIMEOUT, "a bounded device wait ran out");
+  if (st & ST_HEIGHTS)  // first: bad heights also make everything after them non-finite
+    return fail(c, EPOCH_ERR_ARG, "heights set from device memory: non-finite or a parent "
+                                  "below its child");
   if (st & ST_EIG_NOCONV)
     return fail(c, EPOCH_ERR_NUMERIC, "Jacobi eigensolver did not converge");
   if (st & ST_NONFINITE)
@@ -931,6 +934,32 @@ epoch_status epoch_gradient(epoch_ctx *c, double *d_heights, double *d_boundarie
   if (s != EPOCH_OK) return s;
   CK(join_sides(c), "join");
   return copy_grad_out(c, d_heights, d_boundaries, d_params, d_branch_rates);
+}
+
+epoch_status epoch_set_heights_device(epoch_ctx *c, const double *d_heights) {
+  if (!c) return EPOCH_ERR_ARG;
+  if (!(c->have & HAVE_TREE)) return fail(c, EPOCH_ERR_ORDER, "set_heights_device before set_tree");
+  if (!d_heights) return fail(c, EPOCH_ERR_ARG, "heights is NULL");
+  CK(cudaMemcpyAsync(c->d_heights, d_heights, sizeof(double) * c->d.nn, cudaMemcpyDeviceToDevice,
+                     c->stream),
+     "cudaMemcpyAsync(heights)");
+  CK(launch_check_heights(c), "height check kernel");
+  c->have &= ~(HAVE_BRANCH | HAVE_PARTIALS);
+  return EPOCH_OK;
+}
+
+epoch_status epoch_read_results_device(epoch_ctx *c, double *d_lnL, double *d_grad) {
+  if (!c) return EPOCH_ERR_ARG;
+  if (d_lnL)
+    CK(cudaMemcpyAsync(d_lnL, c->d_lnl, sizeof(double), cudaMemcpyDeviceToDevice, c->stream),
+       "cudaMemcpyAsync(lnL)");
+  if (d_grad) {
+    const size_t n = (size_t)2 * c->d.nn + (c->d.E - 1) + c->d.np;
+    CK(cudaMemcpyAsync(d_grad, c->d_grad, sizeof(double) * n, cudaMemcpyDeviceToDevice,
+                       c->stream),
+       "cudaMemcpyAsync(gradient)");
+  }
+  return EPOCH_OK;
 }
 
 epoch_status epoch_get_branch_matrix(epoch_ctx *c, int node, int category, double *out) {

@@ -19,6 +19,7 @@ enum : int {
   ST_EIG_NOCONV = 2,     // Jacobi sweeps hit their limit
   ST_TIMEOUT = 4,        // a bounded wait ran out
   ST_SEGMENTS = 8,       // a branch produced more segments than its slots
+  ST_HEIGHTS = 16,       // heights set from device memory failed the tree check
 };
 
 constexpr int kTile = 256;       // patterns per CTA in the streaming kernels
@@ -183,6 +184,7 @@ cudaError_t launch_segments(epoch_ctx *c);
 cudaError_t launch_model_setup(epoch_ctx *c);
 cudaError_t launch_param_transform(epoch_ctx *c);
 cudaError_t launch_branch_matrices(epoch_ctx *c);
+cudaError_t launch_check_heights(epoch_ctx *c);  // device-side check of d_heights
 // k_partials.cu
 cudaError_t launch_partials(epoch_ctx *c);
 cudaError_t launch_root(epoch_ctx *c);

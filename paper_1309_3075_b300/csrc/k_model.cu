@@ -569,6 +569,24 @@ static size_t setup_smem(const Dims &d) {
          sizeof(float) * (2 * d.KK + 64);
 }
 
+// Heights that arrived from device memory: every height finite and no parent
+// below its child, else ST_HEIGHTS (reported by the next synchronising call).
+__global__ void k_check_heights(Dims d, const double *__restrict__ h, const int *__restrict__ parent,
+                                int *status) {
+  const int v = blockIdx.x * blockDim.x + threadIdx.x;
+  if (v >= d.nn) return;
+  const int u = parent[v];
+  const bool ok = isfinite(h[v]) && (u < 0 || h[u] >= h[v]);
+  if (!ok) atomicOr(status, ST_HEIGHTS);
+}
+
+cudaError_t launch_check_heights(epoch_ctx *c) {
+  k_check_heights<<<ceil_div(c->d.nn, 256), 256, 0, c->stream>>>(c->d, c->d_heights, c->d_parent,
+                                                                 c->d_status);
+  c->launches++;
+  return cudaGetLastError();
+}
+
 cudaError_t launch_model_setup(epoch_ctx *c) {
   const Dims &d = c->d;
   size_t smem = setup_smem(d);
