@@ -33,6 +33,9 @@ from synth.workloads import (  # noqa: F401
     small_nucleotide,
     small_codon,
     tiny_tree_workload,
+    exchange_raw,
+    flu_seasonal,
+    amino_acid,
     GENETIC_CODE,
     SENSE_CODONS,
 )

@@ -551,3 +551,89 @@ def tiny_tree_workload(seed: int, K: int = 4, n_taxa: int = 4, n_sites: int = 6,
     w = rng.integers(1, 4, size=n_sites).astype(np.float64)
     return Workload(f"tiny-K{K}-{n_taxa}taxa", K, b, phi, Q, pi, rates, cw, heights, parent,
                     aln, w, reversible=int(reversible), dQ=dQ, param_names=names, seed=seed)
+
+
+def exchange_raw(s: np.ndarray, pi: np.ndarray):
+    """General time-reversible K-state CTMC from K(K-1)/2 exchangeabilities
+    (pairs (i, j), i < j, in row order): q_ij = s_ij pi_j.  Returns (Q, dQ)
+    with dQ[k] = dQ/ds_k."""
+    pi = np.asarray(pi, dtype=np.float64)
+    K = len(pi)
+    pairs = [(i, j) for i in range(K) for j in range(i + 1, K)]
+    Q = np.zeros((K, K))
+    dQ = np.zeros((len(pairs), K, K))
+    for k, (i, j) in enumerate(pairs):
+        Q[i, j] = s[k] * pi[j]
+        Q[j, i] = s[k] * pi[i]
+        dQ[k, i, j] = pi[j]
+        dQ[k, j, i] = pi[i]
+    return _fill_diag(Q), np.stack([_fill_diag(d) for d in dQ])
+
+
+def flu_seasonal(seed: int = 1315, n_taxa: int = 522, K: int = 7, n_epochs: int = 13,
+                 n_processes: int = 2, n_traits: int = 1, reversible: bool = True,
+                 sampling_span: float = 0.4) -> Workload:
+    """Seasonal phylogeography shaped like the paper's influenza analysis
+    (Results, seasonal H3N2): n_taxa dated tips (heights ~ U(0, span) of a
+    coalescent tree rescaled to root 1.0), K discrete locations, n_epochs
+    epochs of equal length (boundaries k / n_epochs of the root height) that
+    alternate between n_processes rate matrices (phi_e = e mod n_processes,
+    the seasonal design), one simulated location trait per taxon (n_traits
+    replicate traits, each its own pattern, weight 1), one rate category.
+
+    reversible: exchange rates s_ij ~ LogN(0, 1) per process with pi uniform
+    (the symmetric location-exchange model; the parameters are the K(K-1)/2
+    exchangeabilities of each process); else asymmetric q_ij ~ LogN(0, 1),
+    pi uniform, no model parameters."""
+    rng = np.random.default_rng(seed)
+    th = rng.uniform(0.0, sampling_span, size=n_taxa)
+    heights, parent = coalescent_tree(n_taxa, rng, tip_heights=th)
+    pi = np.full(K, 1.0 / K)
+    npair = K * (K - 1) // 2
+    if reversible:
+        Qs, dQs = zip(*[exchange_raw(rng.lognormal(0.0, 1.0, size=npair), pi)
+                        for _ in range(n_processes)])
+        Q = np.stack(Qs)
+        dQ = np.zeros((npair * n_processes, n_processes, K, K))
+        names = []
+        for s in range(n_processes):
+            dQ[npair * s:npair * (s + 1), s] = dQs[s]
+            names += [f"s{i}{j}_{s}" for i in range(K) for j in range(i + 1, K)]
+    else:
+        Q = np.stack([asym_raw(rng.lognormal(0.0, 1.0, size=(K, K))) for _ in range(n_processes)])
+        dQ, names = None, []
+    b = np.arange(1, n_epochs, dtype=np.float64) / n_epochs
+    phi = (np.arange(n_epochs) % n_processes).astype(np.int32)
+    aln = simulate_alignment(heights, parent, b, phi, Q, pi, np.ones(1), n_traits, rng)
+    return Workload(f"seasonal-K{K}-{n_epochs}epoch-{n_taxa}taxa", K, b, phi, Q, pi, np.ones(1),
+                    np.ones(1), heights, parent, aln, np.ones(n_traits), reversible=int(reversible),
+                    dQ=dQ, param_names=names, seed=seed)
+
+
+def amino_acid(seed: int = 1316, n_taxa: int = 200, n_sites: int = 2000, n_epochs: int = 3,
+               n_cat: int = 4, K: int = 20, dated: bool = False) -> Workload:
+    """Protein-shaped data: K = 20 states, a general time-reversible matrix
+    per epoch (190 exchangeabilities ~ LogN(0, 1), pi ~ Dirichlet(10 * 1)
+    shared), epochs at equal fractions of the root height, coalescent tree
+    with root 1.0, simulated sites compressed to patterns, discrete-gamma
+    categories (alpha = 0.5).  Parameters: the first three exchangeabilities
+    (pairs 01, 02, 03) of each epoch."""
+    rng = np.random.default_rng(seed)
+    th = rng.uniform(0.0, 0.2, size=n_taxa) if dated else None
+    heights, parent = coalescent_tree(n_taxa, rng, tip_heights=th)
+    pi = rng.dirichlet(np.full(K, 10.0))
+    npair = K * (K - 1) // 2
+    Qs, dQs = zip(*[exchange_raw(rng.lognormal(0.0, 1.0, size=npair), pi) for _ in range(n_epochs)])
+    Q = np.stack(Qs)
+    dQ = np.zeros((3 * n_epochs, n_epochs, K, K))
+    names = []
+    for e in range(n_epochs):
+        dQ[3 * e:3 * e + 3, e] = dQs[e][:3]
+        names += [f"s01_{e}", f"s02_{e}", f"s03_{e}"]
+    b = _epoch_bounds(1.0, [k / n_epochs for k in range(1, n_epochs)])
+    phi = np.arange(n_epochs, dtype=np.int32)
+    rates, cw = discrete_gamma(0.5, n_cat) if n_cat > 1 else (np.ones(1), np.ones(1))
+    aln = simulate_alignment(heights, parent, b, phi, Q, pi, rates, n_sites, rng)
+    tips, w = compress_patterns(aln)
+    return Workload(f"aa-K{K}-{n_epochs}epoch-{n_taxa}taxa-{n_sites}s", K, b, phi, Q, pi, rates, cw,
+                    heights, parent, tips, w, dQ=dQ, param_names=names, seed=seed)

@@ -460,3 +460,19 @@ def test_time_rescaling_identity(oracle_lib):
         lhs = (w.heights * g["heights"]).sum() + (w.boundaries * g["boundaries"]).sum()
         rhs = (w.branch_rates * g["branch_rates"]).sum()
         assert np.isclose(lhs, rhs, rtol=1e-11, atol=1e-11)
+
+
+def test_many_epochs_one_process_is_homogeneous(oracle_lib):
+    """The seasonal shape with 13 epochs that all use one process: by
+    Chapman-Kolmogorov the twelve boundaries change nothing (Eq.
+    matrixProduct), so lnL equals the single-epoch lnL and every boundary
+    derivative vanishes; with two alternating processes it differs."""
+    w = synth.flu_seasonal(seed=21, n_taxa=40, n_processes=1, n_traits=5)
+    one = w.replace(boundaries=np.zeros(0), epoch_to_matrix=np.zeros(1, np.int32))
+    assert np.isclose(oracle_lib.log_likelihood(w)[0], oracle_lib.log_likelihood(one)[0],
+                      rtol=1e-13)
+    g = oracle_lib.gradient(w.replace(dQ=None))
+    assert np.abs(g["boundaries"]).max() <= 1e-10 * np.abs(g["heights"]).max()
+    w2 = synth.flu_seasonal(seed=21, n_taxa=40, n_processes=2, n_traits=5)
+    g2 = oracle_lib.gradient(w2.replace(dQ=None))
+    assert np.abs(g2["boundaries"]).max() > 1e-3

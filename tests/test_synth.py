@@ -99,3 +99,22 @@ def test_workload_shapes():
     assert ((w2.pattern_weights >= 1) & (w2.pattern_weights <= 20)).all()
     b = synth.asym50_forest(n_trees=3, taxa=(50, 60))
     assert len(b.trees) == 3 and all(t.K == 50 and t.reversible == 0 for t in b.trees)
+
+
+def test_exchange_builder_and_new_shapes():
+    rng = np.random.default_rng(4)
+    pi = rng.dirichlet(np.ones(7))
+    s = rng.lognormal(size=21)
+    Q, dQ = synth.exchange_raw(s, pi)
+    assert np.allclose(Q.sum(1), 0) and np.allclose(pi[:, None] * Q, (pi[:, None] * Q).T)
+    for k in (0, 5, 20):
+        s2 = s.copy()
+        s2[k] += 1.0
+        assert np.allclose(synth.exchange_raw(s2, pi)[0] - Q, dQ[k])
+    f = synth.flu_seasonal()
+    assert f.K == 7 and f.n_epochs == 13 and f.n_taxa == 522 and f.n_patterns == 1
+    assert list(f.epoch_to_matrix) == [e % 2 for e in range(13)] and f.n_matrices == 2
+    assert np.allclose(f.boundaries, np.arange(1, 13) / 13) and np.isclose(f.heights[-1], 1.0)
+    assert f.n_params == 42 and f.heights[:522].min() == 0.0 and f.heights[:522].max() > 0.1
+    a = synth.amino_acid(n_taxa=20, n_sites=50)
+    assert a.K == 20 and a.n_epochs == 3 and a.pattern_weights.sum() == 50 and a.n_params == 9
