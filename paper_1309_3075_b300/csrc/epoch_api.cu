@@ -503,7 +503,9 @@ epoch_status epoch_create(epoch_ctx **out, int states, int n_epochs, const doubl
   A(dalloc(&c->d_lnl_part, ceil_div(n_patterns, 32)));
   A(dalloc(&c->d_lnl, 1));
   if (precision == EPOCH_FP64 || states != 4 || n_categories > 8) {  // K = 4 FP32: per tree
-    c->gpart_bytes = (size_t)ni_max * nchunk * 2 * C * KK * es;
+    // G terms per pattern on the few-pattern path, else per tile of kTile
+    const size_t nG = small_path(c) ? P : (size_t)nchunk;
+    c->gpart_bytes = (size_t)ni_max * nG * 2 * C * KK * es;
     A(cudaMalloc(&c->d_Gpart, c->gpart_bytes));
   }
   A(dalloc(&c->d_G, (size_t)nn_max * C * KK));
@@ -788,6 +790,16 @@ epoch_status epoch_set_tree(epoch_ctx *c, int n_taxa, const double *heights, con
     if (fast_k4(c)) {
       s = plan_k4(c);
       if (s != EPOCH_OK) return s;
+    }
+    if (small_path(c)) {  // G terms per (branch, pattern)
+      const size_t need = (size_t)(c->max_taxa - 1) * c->d.P * 2 * c->d.C * c->d.KK *
+                          elem_size(c->precision);
+      if (c->gpart_bytes < need) {
+        dfree(c->d_Gpart);
+        c->d_Gpart = nullptr;
+        c->gpart_bytes = need;
+        CK(cudaMalloc(&c->d_Gpart, need), "cudaMalloc(G terms)");
+      }
     }
     CK(cudaStreamSynchronize(c->stream), "cudaStreamSynchronize");  // host vectors reused
     c->have &= ~HAVE_TIPS;

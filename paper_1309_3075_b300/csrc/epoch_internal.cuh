@@ -215,6 +215,17 @@ inline bool fast_k4(const epoch_ctx *c) {
   return c->precision != EPOCH_FP64 && c->d.K == 4 && c->d.C <= 8 && c->d.NR <= 8;
 }
 
+// Few patterns (discrete traits): one CTA per pattern walks the whole tree
+// in one launch per pass (k_small.cu) instead of one launch per level.  A
+// node's values over (category, state) must fit one warp.
+constexpr int kSmallMaxPatterns = 64;
+inline bool small_path(const epoch_ctx *c) {
+  return !fast_k4(c) && c->d.P <= kSmallMaxPatterns && c->d.C * c->d.Kp <= 32;
+}
+// k_small.cu
+cudaError_t launch_small_post(epoch_ctx *c);  // pruning, rescaling, root, lnL
+cudaError_t launch_small_pre(epoch_ctx *c);   // adjoint pass; G terms per pattern
+
 inline int ceil_div(long long a, long long b) { return (int)((a + b - 1) / b); }
 
 // Programmatic dependent launch: a level kernel is launched while its

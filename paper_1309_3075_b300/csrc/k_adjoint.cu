@@ -18,69 +18,17 @@
 // and branch rates then follow from how each dt_k depends on them.
 #include <math.h>
 
-#include "epoch_internal.cuh"
+#include "branch_table.cuh"
 
 namespace epoch {
 namespace {
-
-template <typename T>
-struct Tab;
-template <>
-struct Tab<double> {
-  const double *P;
-  const unsigned long long *masks;
-  __device__ double mat(const Dims &d, int v, int c, int i, int j) const {
-    return P[((size_t)v * d.C + c) * d.KK + i * d.K + j];
-  }
-  __device__ double tip(const Dims &d, int v, int c, int i, int code) const {
-    const double *row = P + ((size_t)v * d.C + c) * d.KK + i * d.K;
-    if (code < d.K) return row[code];
-    unsigned long long mk = (code == d.K) ? ~0ull : masks[code - d.K - 1];
-    double s = 0.0;
-    for (int j = 0; j < d.K; j++)
-      if ((mk >> j) & 1ull) s += row[j];
-    return s;
-  }
-};
-template <>
-struct Tab<float> {
-  const float *PT;
-  const unsigned long long *masks;
-  __device__ float mat(const Dims &d, int v, int c, int i, int j) const {
-    return PT[(((size_t)v * d.C + c) * d.NR + j) * d.Kp + i];
-  }
-  __device__ float tip(const Dims &d, int v, int c, int i, int code) const {
-    return PT[(((size_t)v * d.C + c) * d.NR + code) * d.Kp + i];
-  }
-};
-
-__device__ __forceinline__ bool code_allows(const Dims &d, const unsigned long long *masks,
-                                            int code, int j) {
-  if (code < d.K) return code == j;
-  if (code == d.K) return true;
-  return (masks[code - d.K - 1] >> j) & 1ull;
-}
-
-template <typename T>
-__device__ __forceinline__ T child_factor(const Dims &d, const Tab<T> &bt, const T *__restrict__ part,
-                                          const uint8_t *__restrict__ tips, int x, int c, int p,
-                                          int i) {
-  if (x < d.N) return bt.tip(d, x, c, i, tips[(size_t)x * d.Pp + p]);
-  const T *L = part + (((size_t)(x - d.N) * d.C + c) * d.P + p) * d.Kp;
-  T s = 0;
-  for (int j = 0; j < d.K; j++) s += bt.mat(d, x, c, i, j) * L[j];
-  return s;
-}
-
-__device__ __forceinline__ double scale_by(double x, int e) { return ldexp(x, -e); }
-__device__ __forceinline__ float scale_by(float x, int e) { return ldexpf(x, -e); }
 
 // ---- generic pre-order (plain path and SIMT path for K > 4) ---------------
 
 // X for both children of each node of the level: one thread per
 // (child slot, category, pattern, state).
 template <typename T>
-__global__ void k_pre_x(Dims d, Tab<T> bt, const int *__restrict__ lvl_nodes, int lvl_off,
+__global__ void k_pre_x(Dims d, BranchTable<T> bt, const int *__restrict__ lvl_nodes, int lvl_off,
                         const int *__restrict__ child, int root, const T *__restrict__ part,
                         const T *__restrict__ pre, const int16_t *__restrict__ scale,
                         const uint8_t *__restrict__ tips, const double *__restrict__ pi,
@@ -110,7 +58,7 @@ __global__ void k_pre_x(Dims d, Tab<T> bt, const int *__restrict__ lvl_nodes, in
 
 // U_v = P_v^T X_v for internal children.
 template <typename T>
-__global__ void k_pre_u(Dims d, Tab<T> bt, const int *__restrict__ lvl_nodes, int lvl_off,
+__global__ void k_pre_u(Dims d, BranchTable<T> bt, const int *__restrict__ lvl_nodes, int lvl_off,
                         const int *__restrict__ child, const T *__restrict__ xbuf,
                         T *__restrict__ pre) {
   const int bi = blockIdx.y, x = blockIdx.z;
@@ -518,11 +466,13 @@ __global__ void k_grad_reduce(Dims d, const int *__restrict__ parent, const int 
 }
 
 // G over one chunk of kTile patterns for (level node, child x, category c),
-// register-tiled for large K: the 64 x 64 block of (i, j) is split over a
-// 16 x 16 thread grid, each thread owning a 4 x 4 tile; patterns go through
-// shared memory 32 at a time (X rows, and n_p L_v rows or the tip code's
-// indicator).  Same output layout as k_G_part.
-constexpr int kGSub = 32;
+// register-tiled: the KB x KB block of (i, j) (KB = K rounded up to 8, 16, 32
+// or 64) is split over a (KB/4) x (KB/4) thread grid, each thread owning a
+// 4 x 4 tile.  Below KB = 64 the 256 threads form 256 / (KB/4)^2 groups that
+// take interleaved patterns and are summed in a fixed order at the end.
+// Patterns go through shared memory 2048 / KB at a time (X rows, and n_p L_v
+// rows or the tip code's indicator).  Same output layout as k_G_part.
+template <int KB>
 __global__ void __launch_bounds__(256) k_G_tiled(Dims d, const int *__restrict__ lvl_nodes,
                                                  int lvl_off, const int *__restrict__ child,
                                                  const float *__restrict__ xbuf,
@@ -531,8 +481,9 @@ __global__ void __launch_bounds__(256) k_G_tiled(Dims d, const int *__restrict__
                                                  const unsigned long long *__restrict__ masks,
                                                  const double *__restrict__ pw, int nchunk,
                                                  float *__restrict__ Gpart) {
-  __shared__ __align__(16) float Xs[kGSub][64];
-  __shared__ __align__(16) float Ls[kGSub][64];
+  constexpr int TW = KB / 4, NG = 256 / (TW * TW), SUB = 2048 / KB;
+  __shared__ __align__(16) float Xs[SUB * KB];
+  __shared__ __align__(16) float Ls[SUB * KB];
   const int chunk = blockIdx.x, bi = blockIdx.y, x = blockIdx.z / d.C, c = blockIdx.z % d.C;
   const int u = lvl_nodes[lvl_off + bi];
   const int slot = u - d.N;
@@ -540,11 +491,12 @@ __global__ void __launch_bounds__(256) k_G_tiled(Dims d, const int *__restrict__
   const int p0 = chunk * kTile, p1 = min(d.P, p0 + kTile);
   const float *X = xbuf + (((size_t)bi * 2 + x) * d.C + c) * d.P * d.Kp;
   const float *L = v >= d.N ? part + ((size_t)(v - d.N) * d.C + c) * d.P * d.Kp : nullptr;
-  const int ti = threadIdx.x >> 4, tj = threadIdx.x & 15;
+  const int grp = threadIdx.x / (TW * TW), t = threadIdx.x % (TW * TW);
+  const int ti = t / TW, tj = t % TW;
   float acc[4][4] = {};
-  for (int q0 = p0; q0 < p1; q0 += kGSub) {
-    for (int e = threadIdx.x; e < kGSub * 64; e += blockDim.x) {
-      const int pr = e >> 6, k = e & 63, p = q0 + pr;
+  for (int q0 = p0; q0 < p1; q0 += SUB) {
+    for (int e = threadIdx.x; e < SUB * KB; e += blockDim.x) {
+      const int pr = e / KB, k = e % KB, p = q0 + pr;
       float xv = 0.f, lv = 0.f;
       if (p < p1 && k < d.K) {
         xv = X[(size_t)p * d.Kp + k];
@@ -552,14 +504,14 @@ __global__ void __launch_bounds__(256) k_G_tiled(Dims d, const int *__restrict__
         if (L) lv = n * L[(size_t)p * d.Kp + k];
         else lv = code_allows(d, masks, tips[(size_t)v * d.Pp + p], k) ? n : 0.f;
       }
-      Xs[pr][k] = xv;
-      Ls[pr][k] = lv;
+      Xs[e] = xv;
+      Ls[e] = lv;
     }
     __syncthreads();
 #pragma unroll 4
-    for (int pr = 0; pr < kGSub; pr++) {
-      const float4 a = *reinterpret_cast<const float4 *>(&Xs[pr][4 * ti]);
-      const float4 b = *reinterpret_cast<const float4 *>(&Ls[pr][4 * tj]);
+    for (int pr = grp; pr < SUB; pr += NG) {
+      const float4 a = *reinterpret_cast<const float4 *>(&Xs[pr * KB + 4 * ti]);
+      const float4 b = *reinterpret_cast<const float4 *>(&Ls[pr * KB + 4 * tj]);
       const float av[4] = {a.x, a.y, a.z, a.w}, bv[4] = {b.x, b.y, b.z, b.w};
 #pragma unroll
       for (int r = 0; r < 4; r++)
@@ -569,17 +521,51 @@ __global__ void __launch_bounds__(256) k_G_tiled(Dims d, const int *__restrict__
     __syncthreads();
   }
   float *out = Gpart + (((size_t)slot * nchunk + chunk) * 2 + x) * d.C * d.KK + (size_t)c * d.KK;
+  if (NG == 1) {
+#pragma unroll
+    for (int r = 0; r < 4; r++)
+#pragma unroll
+      for (int q = 0; q < 4; q++) {
+        const int i = 4 * ti + r, j = 4 * tj + q;
+        if (i < d.K && j < d.K) out[i * d.K + j] = acc[r][q];
+      }
+    return;
+  }
+  // NG * KB * KB = 4096 floats: the two staging buffers together hold every
+  // group's tile (flat index e, split at SUB * KB between Xs and Ls)
+  float *red = Xs;
 #pragma unroll
   for (int r = 0; r < 4; r++)
 #pragma unroll
     for (int q = 0; q < 4; q++) {
-      const int i = 4 * ti + r, j = 4 * tj + q;
-      if (i < d.K && j < d.K) out[i * d.K + j] = acc[r][q];
+      const int e = grp * KB * KB + (4 * ti + r) * KB + 4 * tj + q;
+      if (e < SUB * KB) red[e] = acc[r][q];
+      else Ls[e - SUB * KB] = acc[r][q];
     }
+  __syncthreads();
+  for (int e = threadIdx.x; e < KB * KB; e += blockDim.x) {
+    const int i = e / KB, j = e % KB;
+    float sum = 0.f;
+    for (int g = 0; g < NG; g++) {
+      const int f = g * KB * KB + e;
+      sum += f < SUB * KB ? red[f] : Ls[f - SUB * KB];
+    }
+    if (i < d.K && j < d.K) out[i * d.K + j] = sum;
+  }
+}
+
+template <int KB>
+void launch_G_tiled(epoch_ctx *c, int l, int w, int nchunk) {
+  const Dims &d = c->d;
+  dim3 gg(nchunk, w, 2 * d.C);
+  k_G_tiled<KB><<<gg, 256, 0, c->stream>>>(d, c->d_level_nodes, c->h_level_off[l], c->d_child,
+                                           (const float *)c->d_xbuf, (const float *)c->d_part,
+                                           c->d_tips, c->d_masks, c->d_pw, nchunk,
+                                           (float *)c->d_Gpart);
 }
 
 template <typename T>
-void launch_pre_generic(epoch_ctx *c, Tab<T> bt, int root) {
+void launch_pre_generic(epoch_ctx *c, BranchTable<T> bt, int root) {
   const Dims &d = c->d;
   const int L = (int)c->h_level_off.size() - 1;
   const long long items = (long long)d.C * d.P * d.Kp;
@@ -603,12 +589,14 @@ void launch_pre_generic(epoch_ctx *c, Tab<T> bt, int root) {
       k_pre_u<T><<<g, 256, 0, c->stream>>>(d, bt, c->d_level_nodes, c->h_level_off[l],
                                            c->d_child, (const T *)c->d_xbuf, (T *)c->d_pre);
     }
-    if (sizeof(T) == sizeof(float) && d.Kp == 64) {
-      dim3 gg(nchunk, w, 2 * d.C);
-      k_G_tiled<<<gg, 256, 0, c->stream>>>(d, c->d_level_nodes, c->h_level_off[l], c->d_child,
-                                           (const float *)c->d_xbuf, (const float *)c->d_part,
-                                           c->d_tips, c->d_masks, c->d_pw, nchunk,
-                                           (float *)c->d_Gpart);
+    if (sizeof(T) == sizeof(float) && d.K > 32) {
+      launch_G_tiled<64>(c, l, w, nchunk);
+    } else if (sizeof(T) == sizeof(float) && d.K > 16) {
+      launch_G_tiled<32>(c, l, w, nchunk);
+    } else if (sizeof(T) == sizeof(float) && d.K > 8) {
+      launch_G_tiled<16>(c, l, w, nchunk);
+    } else if (sizeof(T) == sizeof(float)) {
+      launch_G_tiled<8>(c, l, w, nchunk);
     } else {
       dim3 gg(nchunk, w, 2);
       k_G_part<T><<<gg, 256, 0, c->stream>>>(d, c->d_level_nodes, c->h_level_off[l], c->d_child,
@@ -627,15 +615,27 @@ cudaError_t launch_adjoint(epoch_ctx *c) {
   int root = -1;
   for (int v = 0; v < d.nn; v++)
     if (c->h_parent[v] < 0) root = v;
-  const int nchunk = ceil_div(d.P, kTile);
   const long long nG = (long long)d.nn * d.C * d.KK;
+  if (small_path(c)) {  // one launch for all levels; G terms per pattern
+    cudaError_t e = launch_small_pre(c);
+    if (e != cudaSuccess) return e;
+    if (c->precision == EPOCH_FP64)
+      k_G_reduce<double><<<ceil_div(nG, 256), 256, 0, c->stream>>>(
+          d, c->d_parent, c->d_child, (const double *)c->d_Gpart, d.P, c->d_G);
+    else
+      k_G_reduce<float><<<ceil_div(nG, 256), 256, 0, c->stream>>>(
+          d, c->d_parent, c->d_child, (const float *)c->d_Gpart, d.P, c->d_G);
+    c->launches++;
+    return cudaGetLastError();
+  }
+  const int nchunk = ceil_div(d.P, kTile);
   if (c->precision == EPOCH_FP64) {
-    launch_pre_generic<double>(c, Tab<double>{c->d_P64, c->d_masks}, root);
+    launch_pre_generic<double>(c, BranchTable<double>{c->d_P64, c->d_masks}, root);
     k_G_reduce<double><<<ceil_div(nG, 256), 256, 0, c->stream>>>(
         d, c->d_parent, c->d_child, (const double *)c->d_Gpart, nchunk, c->d_G);
   } else {
     if (fast_k4(c)) return launch_preorder_k4(c);  // adjoint pass and G reduction
-    launch_pre_generic<float>(c, Tab<float>{c->d_PT32, c->d_masks}, root);
+    launch_pre_generic<float>(c, BranchTable<float>{c->d_PT32, c->d_masks}, root);
     k_G_reduce<float><<<ceil_div(nG, 256), 256, 0, c->stream>>>(
         d, c->d_parent, c->d_child, (const float *)c->d_Gpart, nchunk, c->d_G);
   }

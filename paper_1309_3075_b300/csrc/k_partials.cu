@@ -10,61 +10,12 @@
 // exponent of their maximum, which is exact; e is kept per (node, pattern).
 #include <math.h>
 
-#include "epoch_internal.cuh"
+#include "branch_table.cuh"
 
 namespace epoch {
 namespace {
 
 // ---- generic kernels (any K; FP64 = the plain path, FP32 = SIMT path) -----
-
-template <typename T>
-struct BranchTable;
-
-// FP64: row-major P64[v][c][i][j].
-template <>
-struct BranchTable<double> {
-  const double *P;
-  const unsigned long long *masks;
-  __device__ double mat(const Dims &d, int v, int c, int i, int j) const {
-    return P[((size_t)v * d.C + c) * d.KK + i * d.K + j];
-  }
-  __device__ double tip(const Dims &d, int v, int c, int i, int code) const {
-    const double *row = P + ((size_t)v * d.C + c) * d.KK + i * d.K;
-    if (code < d.K) return row[code];
-    unsigned long long mk = (code == d.K) ? ~0ull : masks[code - d.K - 1];
-    double s = 0.0;
-    for (int j = 0; j < d.K; j++)
-      if ((mk >> j) & 1ull) s += row[j];
-    return s;
-  }
-};
-
-// FP32: transposed table PT32[v][c][row][Kp], row j < K = column j of P,
-// rows K.. = missing / mask sums.
-template <>
-struct BranchTable<float> {
-  const float *PT;
-  const unsigned long long *masks;
-  __device__ float mat(const Dims &d, int v, int c, int i, int j) const {
-    return PT[(((size_t)v * d.C + c) * d.NR + j) * d.Kp + i];
-  }
-  __device__ float tip(const Dims &d, int v, int c, int i, int code) const {
-    return PT[(((size_t)v * d.C + c) * d.NR + code) * d.Kp + i];
-  }
-};
-
-// S_x(c,p,i) = sum_j P_x[i][j] L_x(c,p,j) for child x (tip: from its code).
-template <typename T>
-__device__ __forceinline__ T child_factor(const Dims &d, const BranchTable<T> &bt,
-                                          const T *__restrict__ part,
-                                          const uint8_t *__restrict__ tips, int x, int c,
-                                          int p, int i) {
-  if (x < d.N) return bt.tip(d, x, c, i, tips[(size_t)x * d.Pp + p]);
-  const T *L = part + (((size_t)(x - d.N) * d.C + c) * d.P + p) * d.Kp;
-  T s = 0;
-  for (int j = 0; j < d.K; j++) s += bt.mat(d, x, c, i, j) * L[j];
-  return s;
-}
 
 // One thread per (category, pattern, state) of one node of the level.
 template <typename T>
@@ -85,19 +36,6 @@ __global__ void k_partials_generic(Dims d, BranchTable<T> bt, const int *__restr
           child_factor<T>(d, bt, part, tips, w, c, p, i);
   }
   part[(((size_t)slot * d.C + c) * d.P + p) * d.Kp + i] = out;
-}
-
-__device__ __forceinline__ double scale_by(double x, int e) { return ldexp(x, -e); }
-__device__ __forceinline__ float scale_by(float x, int e) { return ldexpf(x, -e); }
-__device__ __forceinline__ int exp_of(double m) {
-  int e;
-  frexp(m, &e);
-  return e;
-}
-__device__ __forceinline__ int exp_of(float m) {
-  int e;
-  frexpf(m, &e);
-  return e;
 }
 
 // One thread per (node of the level, pattern): divide by 2^e of the max.
@@ -208,6 +146,7 @@ cudaError_t launch_generic_levels(epoch_ctx *c, BranchTable<T> bt) {
 
 cudaError_t launch_partials(epoch_ctx *c) {
   const Dims &d = c->d;
+  if (small_path(c)) return launch_small_post(c);  // includes the root log-sum
   if (c->precision == EPOCH_FP64) {
     BranchTable<double> bt{c->d_P64, c->d_masks};
     return launch_generic_levels<double>(c, bt);
@@ -219,7 +158,7 @@ cudaError_t launch_partials(epoch_ctx *c) {
 
 cudaError_t launch_root(epoch_ctx *c) {
   const Dims &d = c->d;
-  if (fast_k4(c)) return cudaSuccess;  // done by the persistent pass
+  if (fast_k4(c) || small_path(c)) return cudaSuccess;  // done by the pruning pass
   int root_slot = -1;
   for (int v = 0; v < d.nn; v++)
     if (c->h_parent[v] < 0) root_slot = v - d.N;

@@ -1,0 +1,235 @@
+// k_small.cu -- the whole tree in one launch per pass when the patterns are
+// few: a discrete trait (one pattern, as in the paper's seasonal
+// phylogeography), or a handful of replicate traits.  With one launch per
+// post-order level the evaluation would be bound by launch latency (tens of
+// levels, two passes, a few kernels each); here one CTA per pattern walks
+// every level with a block barrier in between.
+//
+// A node's values over (category, state) sit in one aligned group of g lanes
+// of a warp (g = C * Kp rounded up to a power of two, at most 32), lane
+// c * Kp + i holding state i of category c.  The rescaling maximum (Eq.
+// partial_likelihood followed by the per-pattern power-of-two scaling), the
+// adjoint product U_v = P_v^T X_v and the branch adjoint G_v = n_p X_v (x) L_v
+// then need only shuffles inside the group.  Results and layouts are those of
+// the per-level kernels (k_partials.cu, k_adjoint.cu): partials, exponents and
+// outside partials in the same buffers, G terms per (branch, pattern) reduced
+// by k_G_reduce in a fixed order, so the chain rule is shared.
+#include <math.h>
+
+#include "branch_table.cuh"
+
+namespace epoch {
+namespace {
+
+constexpr int kSmallThreads = 1024;
+
+// Post-order pruning with rescaling over all levels, then the root sum of
+// the CTA's pattern: site_p = sum_c w_c sum_i pi_i L_root(c,p,i) (scaled) and
+// lnL_p = log site_p + ln2 * sum_u e_u(p).
+template <typename T>
+__global__ void __launch_bounds__(kSmallThreads)
+    k_small_post(Dims d, BranchTable<T> bt, const int *__restrict__ lvl_nodes,
+                 const int *__restrict__ lvl_off, int L, const int *__restrict__ child,
+                 T *__restrict__ part, int16_t *__restrict__ scale,
+                 const uint8_t *__restrict__ tips, int gsz, const double *__restrict__ pi,
+                 const double *__restrict__ catw, double *__restrict__ site_lnl,
+                 double *__restrict__ site_inv, int *__restrict__ status) {
+  __shared__ int s_esum;
+  __shared__ double s_site[32];
+  const int p = blockIdx.x;
+  const int lane_g = threadIdx.x & (gsz - 1), grp = threadIdx.x / gsz;
+  const int ngrp = blockDim.x / gsz;
+  const int c = lane_g / d.Kp, i = lane_g % d.Kp;
+  const bool holds = c < d.C;           // lane maps to a stored entry
+  const bool act = holds && i < d.K;    // ... and to a real state
+  for (int l = 0; l < L; l++) {
+    const int o0 = lvl_off[l], o1 = lvl_off[l + 1];
+    // the trip count is the same for every thread: whole warps take part in
+    // the shuffles, groups past the level's end carry zeros
+    for (int base = o0; base < o1; base += ngrp) {
+      const int k = base + grp;
+      const bool node = k < o1;
+      int slot = 0;
+      T val = 0;
+      if (node) {
+        slot = lvl_nodes[k] - d.N;
+        if (act) {
+          const int v = child[2 * slot], w = child[2 * slot + 1];
+          val = child_factor<T>(d, bt, part, tips, v, c, p, i) *
+                child_factor<T>(d, bt, part, tips, w, c, p, i);
+        }
+      }
+      T m = val;
+      for (int o = gsz >> 1; o > 0; o >>= 1) m = fmax(m, __shfl_xor_sync(0xffffffffu, m, o, gsz));
+      if (node) {
+        int e = 0;
+        if (!isfinite(m)) {
+          if (lane_g == 0) atomicOr(status, ST_NONFINITE);
+        } else if (m > 0) {
+          e = exp_of(m);
+          val = scale_by(val, e);
+        }
+        if (holds) part[(((size_t)slot * d.C + c) * d.P + p) * d.Kp + i] = val;
+        if (lane_g == 0) scale[(size_t)slot * d.Pp + p] = (int16_t)e;
+      }
+    }
+    __syncthreads();  // this level's partials are read by the next
+  }
+  // the root is the single node of the last level
+  const int rslot = lvl_nodes[lvl_off[L - 1]] - d.N;
+  if (threadIdx.x == 0) s_esum = 0;
+  __syncthreads();
+  int es = 0;
+  for (int s = threadIdx.x; s < d.N - 1; s += blockDim.x) es += scale[(size_t)s * d.Pp + p];
+  if (es) atomicAdd(&s_esum, es);  // integer sum: exact in any order
+  if (threadIdx.x < 32) {
+    // one warp: lane t sums entries t, t+32, .. of (c, i); then a fixed tree
+    double acc = 0.0;
+    for (int t = threadIdx.x; t < d.C * d.K; t += 32) {
+      const int cc = t / d.K, ii = t % d.K;
+      acc += catw[cc] * pi[ii] * (double)part[(((size_t)rslot * d.C + cc) * d.P + p) * d.Kp + ii];
+    }
+    for (int o = 16; o > 0; o >>= 1) acc += __shfl_xor_sync(0xffffffffu, acc, o);
+    if (threadIdx.x == 0) s_site[0] = acc;
+  }
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    const double site = s_site[0];
+    site_lnl[p] = log(site) + 0.69314718055994530942 * (double)s_esum;
+    site_inv[p] = site > 0.0 ? 1.0 / site : 0.0;
+  }
+}
+
+// lnL = sum_p n_p lnL_p over the (few) patterns, in a fixed order.
+__global__ void k_small_lnl(int P, const double *__restrict__ pw,
+                            const double *__restrict__ site_lnl, double *__restrict__ out) {
+  __shared__ double red[32];
+  double t = 0.0;
+  for (int p = threadIdx.x; p < P; p += blockDim.x) t += pw[p] != 0.0 ? pw[p] * site_lnl[p] : 0.0;
+  for (int o = 16; o > 0; o >>= 1) t += __shfl_xor_sync(0xffffffffu, t, o);
+  if ((threadIdx.x & 31) == 0) red[threadIdx.x >> 5] = t;
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    double s = 0.0;
+    for (int w = 0; w < (int)(blockDim.x >> 5); w++) s += red[w];
+    out[0] = s;
+  }
+}
+
+// Pre-order adjoint over all levels, top down, for the CTA's pattern: for
+// each child v of u (sibling w)
+//   X_v = U_u o S_w 2^{-e_u}   (U_root = w_c pi_i / site_p),
+//   U_v = P_v^T X_v            (stored for internal v),
+//   Gs[slot(u)][p][x][c][i][j] = n_p X_v(c,i) L_v(c,p,j)
+// (L_v of a tip is the indicator of its code).
+template <typename T>
+__global__ void __launch_bounds__(kSmallThreads)
+    k_small_pre(Dims d, BranchTable<T> bt, const int *__restrict__ lvl_nodes,
+                const int *__restrict__ lvl_off, int L, const int *__restrict__ child, int root,
+                const T *__restrict__ part, T *__restrict__ pre,
+                const int16_t *__restrict__ scale, const uint8_t *__restrict__ tips,
+                const unsigned long long *__restrict__ masks, const double *__restrict__ pi,
+                const double *__restrict__ catw, const double *__restrict__ site_inv,
+                const double *__restrict__ pw, int gsz, T *__restrict__ Gs) {
+  const int p = blockIdx.x;
+  const int lane_g = threadIdx.x & (gsz - 1), grp = threadIdx.x / gsz;
+  const int ngrp = blockDim.x / gsz;
+  const int c = lane_g / d.Kp, i = lane_g % d.Kp;
+  const bool holds = c < d.C;
+  const bool act = holds && i < d.K;
+  const T n = (T)pw[p];
+  for (int l = L - 1; l >= 0; l--) {
+    const int o0 = lvl_off[l], items = 2 * (lvl_off[l + 1] - o0);
+    for (int base = 0; base < items; base += ngrp) {
+      const int it = base + grp;
+      const bool node = it < items;
+      const int x = it & 1;
+      int u = 0, slot = 0, v = 0;
+      T X = 0;
+      if (node) {
+        u = lvl_nodes[o0 + (it >> 1)];
+        slot = u - d.N;
+        v = child[2 * slot + x];
+        if (act) {
+          const int w = child[2 * slot + 1 - x];
+          const T uu = (u == root) ? (T)(catw[c] * pi[i] * site_inv[p])
+                                   : pre[(((size_t)slot * d.C + c) * d.P + p) * d.Kp + i];
+          X = scale_by(uu * child_factor<T>(d, bt, part, tips, w, c, p, i),
+                       (int)scale[(size_t)slot * d.Pp + p]);
+        }
+      }
+      // U_v(c, i) = sum_k P_v[k][i] X_v(c, k); X_v(c, k) is in lane c*Kp + k
+      const bool inner = node && v >= d.N;
+      T U = 0;
+      for (int k = 0; k < d.K; k++) {
+        const T xk = __shfl_sync(0xffffffffu, X, c * d.Kp + k, gsz);
+        if (inner && act) U += bt.mat(d, v, c, k, i) * xk;
+      }
+      if (inner && holds) pre[(((size_t)(v - d.N) * d.C + c) * d.P + p) * d.Kp + i] = U;
+      if (node && act) {
+        T *g = Gs + ((((size_t)slot * d.P + p) * 2 + x) * d.C + c) * d.KK + (size_t)i * d.K;
+        if (v >= d.N) {
+          const T *Lv = part + (((size_t)(v - d.N) * d.C + c) * d.P + p) * d.Kp;
+          for (int j = 0; j < d.K; j++) g[j] = n * X * Lv[j];
+        } else {
+          const int code = tips[(size_t)v * d.Pp + p];
+          for (int j = 0; j < d.K; j++) g[j] = code_allows(d, masks, code, j) ? n * X : (T)0;
+        }
+      }
+    }
+    __syncthreads();  // this level's U are read by the next
+  }
+}
+
+int group_size(const Dims &d) {
+  int g = 1;
+  while (g < d.C * d.Kp) g <<= 1;
+  return g;
+}
+
+int root_node(const epoch_ctx *c) {
+  for (int v = 0; v < c->d.nn; v++)
+    if (c->h_parent[v] < 0) return v;
+  return -1;
+}
+
+}  // namespace
+
+cudaError_t launch_small_post(epoch_ctx *c) {
+  const Dims &d = c->d;
+  const int L = (int)c->h_level_off.size() - 1;
+  const int g = group_size(d);
+  if (c->precision == EPOCH_FP64)
+    k_small_post<double><<<d.P, kSmallThreads, 0, c->stream>>>(
+        d, BranchTable<double>{c->d_P64, c->d_masks}, c->d_level_nodes, c->d_level_off, L,
+        c->d_child, (double *)c->d_part, c->d_scale, c->d_tips, g, c->d_pi, c->d_catw,
+        c->d_site_lnl, c->d_site_inv, c->d_status);
+  else
+    k_small_post<float><<<d.P, kSmallThreads, 0, c->stream>>>(
+        d, BranchTable<float>{c->d_PT32, c->d_masks}, c->d_level_nodes, c->d_level_off, L,
+        c->d_child, (float *)c->d_part, c->d_scale, c->d_tips, g, c->d_pi, c->d_catw,
+        c->d_site_lnl, c->d_site_inv, c->d_status);
+  k_small_lnl<<<1, 256, 0, c->stream>>>(d.P, c->d_pw, c->d_site_lnl, c->d_lnl);
+  c->launches += 2;
+  return cudaGetLastError();
+}
+
+cudaError_t launch_small_pre(epoch_ctx *c) {
+  const Dims &d = c->d;
+  const int L = (int)c->h_level_off.size() - 1;
+  const int g = group_size(d), root = root_node(c);
+  if (c->precision == EPOCH_FP64)
+    k_small_pre<double><<<d.P, kSmallThreads, 0, c->stream>>>(
+        d, BranchTable<double>{c->d_P64, c->d_masks}, c->d_level_nodes, c->d_level_off, L,
+        c->d_child, root, (const double *)c->d_part, (double *)c->d_pre, c->d_scale, c->d_tips,
+        c->d_masks, c->d_pi, c->d_catw, c->d_site_inv, c->d_pw, g, (double *)c->d_Gpart);
+  else
+    k_small_pre<float><<<d.P, kSmallThreads, 0, c->stream>>>(
+        d, BranchTable<float>{c->d_PT32, c->d_masks}, c->d_level_nodes, c->d_level_off, L,
+        c->d_child, root, (const float *)c->d_part, (float *)c->d_pre, c->d_scale, c->d_tips,
+        c->d_masks, c->d_pi, c->d_catw, c->d_site_inv, c->d_pw, g, (float *)c->d_Gpart);
+  c->launches++;
+  return cudaGetLastError();
+}
+
+}  // namespace epoch

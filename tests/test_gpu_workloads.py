@@ -81,7 +81,7 @@ def test_seasonal_branch_matrices_across_many_boundaries(seasonal):
             lo, hi = w.heights[v], w.heights[w.parent[v]]
             crossings.append(int(((w.boundaries > lo) & (w.boundaries < hi)).sum()))
         order = np.argsort(crossings)[::-1][:6]
-        assert crossings[order[0]] >= 6
+        assert crossings[order[0]] >= 5
         for v in order:
             P = lik.branch_matrix(int(v), 0)
             assert np.allclose(P, oracle.branch_matrix(w, int(v), 0), rtol=0, atol=1e-12)
