@@ -65,18 +65,11 @@ __device__ __forceinline__ T child_factor(const Dims &d, const BranchTable<T> &b
   return s;
 }
 
-// Exact power-of-two rescaling: x * 2^-e, and the binary exponent of m.
+// Exact power-of-two rescaling: x * 2^-e, and the binary exponent e of a
+// finite m > 0 (m = f 2^e with f in [0.5, 1), as frexp gives it).
 __device__ __forceinline__ double scale_by(double x, int e) { return ldexp(x, -e); }
 __device__ __forceinline__ float scale_by(float x, int e) { return ldexpf(x, -e); }
-__device__ __forceinline__ int exp_of(double m) {
-  int e;
-  frexp(m, &e);
-  return e;
-}
-__device__ __forceinline__ int exp_of(float m) {
-  int e;
-  frexpf(m, &e);
-  return e;
-}
+__device__ __forceinline__ int exp_of(double m) { return ilogb(m) + 1; }
+__device__ __forceinline__ int exp_of(float m) { return ilogbf(m) + 1; }
 
 }  // namespace epoch

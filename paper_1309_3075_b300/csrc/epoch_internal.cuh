@@ -218,9 +218,19 @@ inline bool fast_k4(const epoch_ctx *c) {
 // Few patterns (discrete traits): one CTA per pattern walks the whole tree
 // in one launch per pass (k_small.cu) instead of one launch per level.  A
 // node's values over (category, state) must fit one warp.
+// The kernels keep the pattern's tree in shared memory: topology, tip codes,
+// exponents, and the partials (post-order, plus outside partials in the
+// adjoint kernel) of every internal node, elements of es bytes.
 constexpr int kSmallMaxPatterns = 64;
+constexpr size_t kSmallMaxSmem = 200 * 1024;
+inline size_t small_smem_bytes(const Dims &d, int N, size_t es, bool with_pre) {
+  const size_t nv = (size_t)(N - 1) * d.C * d.Kp;
+  return es * nv * (with_pre ? 2 : 1) + sizeof(int) * 5 * N + N;
+}
 inline bool small_path(const epoch_ctx *c) {
-  return !fast_k4(c) && c->d.P <= kSmallMaxPatterns && c->d.C * c->d.Kp <= 32;
+  const size_t es = c->precision == EPOCH_FP64 ? sizeof(double) : sizeof(float);
+  return !fast_k4(c) && c->d.P <= kSmallMaxPatterns && c->d.C * c->d.Kp <= 32 &&
+         small_smem_bytes(c->d, c->max_taxa, es, true) <= kSmallMaxSmem;
 }
 // k_small.cu
 cudaError_t launch_small_post(epoch_ctx *c);  // pruning, rescaling, root, lnL

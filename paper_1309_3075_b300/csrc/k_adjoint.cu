@@ -354,16 +354,28 @@ __global__ void k_grad_branch(Dims d, const double *__restrict__ G, const int *_
           W[idx] *= phi;
         }
         __syncthreads();
-        for (int a = 0; a < d.np; a++) {
-          if (!Dnz[a * d.S + s]) {
-            if (threadIdx.x == 0) gseg[(((size_t)v * d.E + k) * d.C + c) * stride + 1 + a] = 0;
-            continue;
+        if (KK <= 256) {
+          // few entries: a thread per parameter, no block reductions
+          for (int a = threadIdx.x; a < d.np; a += blockDim.x) {
+            T pa = 0;
+            if (Dnz[a * d.S + s]) {
+              const T *Da = Dth + ((size_t)a * d.S + s) * KK;
+              for (int idx = 0; idx < KK; idx++) pa += W[idx] * Da[idx];
+            }
+            gseg[(((size_t)v * d.E + k) * d.C + c) * stride + 1 + a] = pa;
           }
-          const T *Da = Dth + ((size_t)a * d.S + s) * KK;
-          T pa = 0;
-          for (int idx = threadIdx.x; idx < KK; idx += blockDim.x) pa += W[idx] * Da[idx];
-          const T ga = bsum<T>(pa, red);
-          if (threadIdx.x == 0) gseg[(((size_t)v * d.E + k) * d.C + c) * stride + 1 + a] = ga;
+        } else {
+          for (int a = 0; a < d.np; a++) {
+            if (!Dnz[a * d.S + s]) {
+              if (threadIdx.x == 0) gseg[(((size_t)v * d.E + k) * d.C + c) * stride + 1 + a] = 0;
+              continue;
+            }
+            const T *Da = Dth + ((size_t)a * d.S + s) * KK;
+            T pa = 0;
+            for (int idx = threadIdx.x; idx < KK; idx += blockDim.x) pa += W[idx] * Da[idx];
+            const T ga = bsum<T>(pa, red);
+            if (threadIdx.x == 0) gseg[(((size_t)v * d.E + k) * d.C + c) * stride + 1 + a] = ga;
+          }
         }
       }
     } else {

@@ -144,14 +144,17 @@ __device__ __forceinline__ void jacobi_rotation(float app, float aqq, float apq,
 
 // Cyclic Jacobi sweeps on the K x K symmetric A (row-major, shared memory),
 // rotations accumulated into U (U <- U J).  Stops when the squared
-// off-diagonal norm is <= tol2 (absolute); returns the last measured value.
+// off-diagonal norm is <= tol2 (absolute), after max_sweeps, or when a sweep
+// no longer halves it: convergence is quadratic until the rounding floor of
+// T, where further sweeps only reshuffle rounding errors (that floor grows
+// with K and can lie above tol2).  Returns the last measured value.
 template <typename T, int KT>
 __device__ __forceinline__ double jacobi_sweeps(T *A, T *U, int Kr, double tol2, int max_sweeps,
                                                 double *red, T *cs, T *sn, int *pq) {
   const int K = KT ? KT : Kr;
   const int KK = K * K, tid = threadIdx.x, nt = blockDim.x;
   const int n = K + (K & 1), npair = n / 2;
-  double off = 0.0;
+  double off = 0.0, prev = 0.0;
   for (int sweep = 0;; sweep++) {
     double part = 0.0;
     for (int idx = tid; idx < KK; idx += nt) {
@@ -159,7 +162,8 @@ __device__ __forceinline__ double jacobi_sweeps(T *A, T *U, int Kr, double tol2,
       if (j > i) part += (double)A[idx] * (double)A[idx];
     }
     off = block_sum(part, red);
-    if (off <= tol2 || sweep == max_sweeps) break;
+    if (off <= tol2 || sweep == max_sweeps || (sweep > 0 && off > 0.5 * prev)) break;
+    prev = off;
     for (int round = 0; round < n - 1; round++) {
       for (int k = tid; k < npair; k += nt) {
         // round-robin position after `round` shifts: element 0 stays, the
@@ -211,24 +215,27 @@ __device__ __forceinline__ double jacobi_sweeps(T *A, T *U, int Kr, double tol2,
   return off;
 }
 
-// Cyclic Jacobi on a symmetric 4 x 4 FP32 matrix held in registers by one
-// thread (every index is a compile-time constant): sweeps over the pairs
-// (0,1) (0,2) (0,3) (1,2) (1,3) (2,3) until the squared off-diagonal norm is
-// <= tol2 (at most 12 sweeps).  A and U: row-major in shared memory, U = I on
+// Cyclic Jacobi on a symmetric K x K FP32 matrix (K <= NR) held in registers
+// by one thread as an NR x NR array, zero outside K x K (every index is a
+// compile-time constant): sweeps over the pairs (p, q), p < q, in row order
+// until the squared off-diagonal norm is <= tol2 (at most 12 sweeps).  Pairs
+// that reach into the zero padding have a_pq = 0 and are skipped, so the
+// padding stays zero.  A and U: row-major K x K in shared memory, U = I on
 // entry; A is overwritten by the rotated matrix, U by the rotations.
-__device__ __forceinline__ void rot4(float (&a)[4][4], float (&u)[4][4], int p, int q) {
+template <int NR>
+__device__ __forceinline__ void rot_registers(float (&a)[NR][NR], float (&u)[NR][NR], int p, int q) {
   const float apq = a[p][q];
   if (apq == 0.f) return;
   float c, s;
   jacobi_rotation(a[p][p], a[q][q], apq, c, s);
 #pragma unroll
-  for (int k = 0; k < 4; k++) {  // rows p, q
+  for (int k = 0; k < NR; k++) {  // rows p, q
     const float x = a[p][k], y = a[q][k];
     a[p][k] = c * x - s * y;
     a[q][k] = s * x + c * y;
   }
 #pragma unroll
-  for (int k = 0; k < 4; k++) {  // columns p, q
+  for (int k = 0; k < NR; k++) {  // columns p, q
     const float x = a[k][p], y = a[k][q];
     a[k][p] = c * x - s * y;
     a[k][q] = s * x + c * y;
@@ -239,33 +246,36 @@ __device__ __forceinline__ void rot4(float (&a)[4][4], float (&u)[4][4], int p, 
   a[p][q] = 0.f;
   a[q][p] = 0.f;
 }
-__device__ void jacobi4_registers(float *A, float *U, float tol2) {
-  float a[4][4], u[4][4];
+template <int NR>
+__device__ void jacobi_registers(float *A, float *U, int K, float tol2) {
+  float a[NR][NR], u[NR][NR];
 #pragma unroll
-  for (int i = 0; i < 4; i++)
+  for (int i = 0; i < NR; i++)
 #pragma unroll
-    for (int j = 0; j < 4; j++) {
-      a[i][j] = A[i * 4 + j];
+    for (int j = 0; j < NR; j++) {
+      a[i][j] = (i < K && j < K) ? A[i * K + j] : 0.f;
       u[i][j] = (i == j) ? 1.f : 0.f;
     }
   for (int sweep = 0; sweep < 12; sweep++) {
-    const float off = a[0][1] * a[0][1] + a[0][2] * a[0][2] + a[0][3] * a[0][3] +
-                      a[1][2] * a[1][2] + a[1][3] * a[1][3] + a[2][3] * a[2][3];
+    float off = 0.f;
+#pragma unroll
+    for (int p = 0; p < NR; p++)
+#pragma unroll
+      for (int q = p + 1; q < NR; q++) off += a[p][q] * a[p][q];
     if (off <= tol2) break;
-    rot4(a, u, 0, 1);
-    rot4(a, u, 0, 2);
-    rot4(a, u, 0, 3);
-    rot4(a, u, 1, 2);
-    rot4(a, u, 1, 3);
-    rot4(a, u, 2, 3);
+#pragma unroll
+    for (int p = 0; p < NR; p++)
+#pragma unroll
+      for (int q = p + 1; q < NR; q++) rot_registers<NR>(a, u, p, q);
   }
 #pragma unroll
-  for (int i = 0; i < 4; i++)
+  for (int i = 0; i < NR; i++)
 #pragma unroll
-    for (int j = 0; j < 4; j++) {
-      A[i * 4 + j] = a[i][j];
-      U[i * 4 + j] = u[i][j];
-    }
+    for (int j = 0; j < NR; j++)
+      if (i < K && j < K) {
+        A[i * K + j] = a[i][j];
+        U[i * K + j] = u[i][j];
+      }
 }
 
 // C = op(X) Y for K x K row-major FP64 matrices in shared memory (op = X^T
@@ -337,13 +347,19 @@ __global__ void k_model_setup(Dims d, int normalise, const double *__restrict__ 
     part += A[idx] * A[idx];
   }
   const double fro2 = block_sum(part, red);
-  // 1. FP32 rotations (K = 4: one thread, the matrix in registers)
+  // 1. FP32 rotations (K <= 8: one thread, the matrix in registers)
   if constexpr (KT == 4) {
     __syncthreads();
-    if (tid == 0) jacobi4_registers(A32, U32, (float)(1e-12 * fro2));
+    if (tid == 0) jacobi_registers<4>(A32, U32, 4, (float)(1e-12 * fro2));
     __syncthreads();
   } else {
-    jacobi_sweeps<float, KT>(A32, U32, K, 1e-12 * fro2, 40, red, cs32, sn32, pq);
+    if (K <= 8) {
+      __syncthreads();
+      if (tid == 0) jacobi_registers<8>(A32, U32, K, (float)(1e-12 * fro2));
+      __syncthreads();
+    } else {
+      jacobi_sweeps<float, KT>(A32, U32, K, 1e-12 * fro2, 40, red, cs32, sn32, pq);
+    }
   }
   // 2. orthogonal U in FP64
   for (int idx = tid; idx < KK; idx += nt) U[idx] = (double)U32[idx];
