@@ -89,38 +89,66 @@ __global__ void k_tc_prep(Dims d, const double *__restrict__ P64, const int *__r
   }
 }
 
-// Shared memory of one tile: A hi, A lo (32 KB each), B hi, B lo (16 KB each).
-constexpr size_t kTcSmem = sizeof(float) * (2 * kATile + 2 * kTile4) + 1024;
+// Shared memory: two stages, each one operand pair: A hi, A lo (32 KB each),
+// B hi, B lo (16 KB each).
+constexpr int kStageFloats = 2 * kATile + 2 * kTile4;
+constexpr size_t kTcSmem = sizeof(float) * 2 * kStageFloats + 1024;
 
-// A: the thread's own row (rows >= rows read as zero) -> hi / lo in core order.
-__device__ __forceinline__ void tc_stage_A(const float *A, int lda, int rows, float *sm) {
-  float *sAh = sm, *sAl = sAh + kATile;
-  const int r = threadIdx.x;
-  const float4 *src = reinterpret_cast<const float4 *>(A + (size_t)r * lda);
-#pragma unroll 4
+// An A tile in registers: thread (warp w, lane l) holds, for q < 16, row
+// 8q + (l & 7), columns 4 (4w + (l >> 3)) .. +3.  A warp's load covers 8 rows
+// x 64 contiguous bytes (whole sectors); a quarter-warp's store covers 8
+// consecutive rows of one core-matrix column, 128 contiguous bytes (no bank
+// conflicts).
+struct ATile {
+  float4 x[16];
+};
+__device__ __forceinline__ int a_col() {
+  return 4 * (4 * (threadIdx.x >> 5) + ((threadIdx.x & 31) >> 3));
+}
+// Rows >= rows read as zero.
+__device__ __forceinline__ void tc_load_A(const float *A, int lda, int rows, ATile &t) {
+  const int col = a_col(), r0 = threadIdx.x & 7;
+#pragma unroll
   for (int q = 0; q < 16; q++) {
-    const float4 x = r < rows ? src[q] : make_float4(0.f, 0.f, 0.f, 0.f);
+    const int r = 8 * q + r0;
+    t.x[q] = r < rows ? *reinterpret_cast<const float4 *>(A + (size_t)r * lda + col)
+                      : make_float4(0.f, 0.f, 0.f, 0.f);
+  }
+}
+// hi / lo split into the stage's A area, core order.
+__device__ __forceinline__ void tc_store_A(const ATile &t, float *st) {
+  float *sAh = st, *sAl = st + kATile;
+  const int col = a_col(), r0 = threadIdx.x & 7;
+#pragma unroll
+  for (int q = 0; q < 16; q++) {
+    const float4 x = t.x[q];
     const float4 h = make_float4(to_tf32(x.x), to_tf32(x.y), to_tf32(x.z), to_tf32(x.w));
     const float4 l = make_float4(to_tf32(x.x - h.x), to_tf32(x.y - h.y), to_tf32(x.z - h.z),
                                  to_tf32(x.w - h.w));
-    const int o = core_off(r, 4 * q);
+    const int o = core_off(8 * q + r0, col);
     *reinterpret_cast<float4 *>(sAh + o) = h;
     *reinterpret_cast<float4 *>(sAl + o) = l;
   }
 }
-// B: hi | lo (2 x 16 KB) copied as laid out by k_tc_prep.
-__device__ __forceinline__ void tc_stage_B(const float *Bq, float *sm) {
-  const float4 *src = reinterpret_cast<const float4 *>(Bq);
-  float4 *dst = reinterpret_cast<float4 *>(sm + 2 * kATile);
-  for (int i = threadIdx.x; i < 2 * kTile4 / 4; i += kTcThr) dst[i] = src[i];
+// B: hi | lo (2 x 16 KB, laid out by k_tc_prep) into the stage's B area by
+// cp.async, as one commit group.
+__device__ __forceinline__ void tc_async_B(const float *Bq, float *st) {
+  const uint32_t dst = su32(st + 2 * kATile);
+  const size_t src = __cvta_generic_to_global(Bq);
+#pragma unroll 4
+  for (int i = threadIdx.x; i < 2 * kTile4 / 4; i += kTcThr)
+    asm volatile("cp.async.cg.shared.global [%0], [%1], 16;" ::"r"(dst + 16 * i),
+                 "l"(src + 16 * (size_t)i)
+                 : "memory");
+  asm volatile("cp.async.commit_group;" ::: "memory");
 }
-// Issue (thread 0) D[col..col+63] = A B^T with the three split products, then
-// signal mbar when they have completed.  Staged operands must be fenced and
-// the CTA synchronised before the call.
-__device__ __forceinline__ void tc_mma(uint32_t dtmem, float *sm, uint64_t *mbar) {
+// Issue (thread 0) D[col..col+63] = A B^T from stage st with the three split
+// products, then signal mbar when they have completed.  Staged operands must
+// be fenced and the CTA synchronised before the call.
+__device__ __forceinline__ void tc_mma(uint32_t dtmem, const float *st, uint64_t *mbar) {
   if (threadIdx.x != 0) return;
   asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
-  const uint32_t ah = su32(sm), al = ah + kATile * 4, bh = ah + 2 * kATile * 4,
+  const uint32_t ah = su32(st), al = ah + kATile * 4, bh = ah + 2 * kATile * 4,
                  bl = bh + kTile4 * 4;
   for (int ks = 0; ks < 8; ks++) {  // 8 TF32 of K per instruction = 256 bytes
     const uint32_t o = ks * 256;
@@ -166,35 +194,48 @@ __device__ __forceinline__ void tc_ld16(uint32_t taddr, int col, float *out) {
   for (int j = 0; j < 16; j++) out[j] = __uint_as_float(v[j]);
 }
 
-// One 128-row tile: D[r][0..63] = sum_k A[r][k] B[n][k] for the rows r < rows
-// (A rows lda floats apart; rows >= rows read as zero and are not stored).
-// Returns false when the MMAs did not complete within the wait bound.
-__device__ bool tc_tile(const float *A, int lda, int rows, const float *Bq, float *D, int ldd,
-                        float *sm, uint32_t taddr, uint64_t *mbar, uint32_t &phase) {
-  tc_stage_A(A, lda, rows, sm);
-  tc_stage_B(Bq, sm);
-  tc_sync_staged();
-  tc_mma(taddr, sm, mbar);
-  if (!tc_wait(mbar, phase)) return false;
-  const int r = threadIdx.x;
-  float *drow = D + (size_t)r * ldd;
-#pragma unroll
-  for (int cb = 0; cb < 4; cb++) {
-    float v[16];
-    tc_ld16(taddr, cb * 16, v);
-    if (r < rows) {
-#pragma unroll
-      for (int q = 0; q < 4; q++)
-        *reinterpret_cast<float4 *>(drow + cb * 16 + 4 * q) =
-            make_float4(v[4 * q], v[4 * q + 1], v[4 * q + 2], v[4 * q + 3]);
+// Tile products D_j[128 x 64] = A_j B_j^T into TMEM columns col_j, j < n,
+// for one tile of 128 rows (A rows lda floats apart; rows >= `rows` read as
+// zero), through the two shared-memory stages: while the tensor cores run
+// item j, item j+1's A is loaded into registers and its B copied by
+// cp.async.  item(j, A, B, col) names the operands.  Every thread takes
+// part.  Returns false when an MMA did not complete within the wait bound;
+// nothing is then left in flight but that MMA.
+template <class Item>
+__device__ bool tc_pipeline(int n, int lda, int rows, Item item, float *sm, uint32_t taddr,
+                            uint64_t *mbar, uint32_t *ph) {
+  if (n <= 0) return true;
+  ATile ra;
+  const float *A, *B;
+  uint32_t col;
+  item(0, A, B, col);
+  tc_async_B(B, sm);
+  tc_load_A(A, lda, rows, ra);
+  for (int j = 0; j < n; j++) {
+    float *st = sm + (j & 1) * kStageFloats;
+    tc_store_A(ra, st);  // stage j&1 is free: MMA j-2 was waited for at j-1
+    const uint32_t colj = col;
+    if (j + 1 < n) {
+      item(j + 1, A, B, col);
+      tc_load_A(A, lda, rows, ra);  // in flight during this item's MMA
     }
+    if (j >= 1 && !tc_wait(&mbar[(j - 1) & 1], ph[(j - 1) & 1])) {
+      asm volatile("cp.async.wait_all;" ::: "memory");
+      return false;
+    }
+    if (j + 1 < n) {  // MMA j-1 has released stage (j+1)&1
+      tc_async_B(B, sm + ((j + 1) & 1) * kStageFloats);
+      asm volatile("cp.async.wait_group 1;" ::: "memory");  // B of item j has landed
+    } else {
+      asm volatile("cp.async.wait_group 0;" ::: "memory");
+    }
+    tc_sync_staged();
+    tc_mma(taddr + colj, st, &mbar[j & 1]);
   }
-  asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
-  __syncthreads();  // shared memory and TMEM free for the next tile
-  return true;
+  return tc_wait(&mbar[(n - 1) & 1], ph[(n - 1) & 1]);
 }
 
-// CTA prologue / epilogue: TMEM columns and the MMA-completion barrier.
+// CTA prologue / epilogue: TMEM columns and the two MMA-completion barriers.
 __device__ uint32_t tc_begin(uint32_t *s_tmem, uint64_t *mbar, uint32_t ncols) {
   if ((threadIdx.x >> 5) == 0) {
     asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(
@@ -202,7 +243,10 @@ __device__ uint32_t tc_begin(uint32_t *s_tmem, uint64_t *mbar, uint32_t ncols) {
                  "r"(ncols));
     asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;");
   }
-  if (threadIdx.x == 0) asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(su32(mbar)), "r"(1));
+  if (threadIdx.x == 0) {
+    asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(su32(&mbar[0])), "r"(1));
+    asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(su32(&mbar[1])), "r"(1));
+  }
   asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
   asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
   __syncthreads();
@@ -215,34 +259,82 @@ __device__ void tc_end(uint32_t taddr, uint32_t ncols) {
   if ((threadIdx.x >> 5) == 0)
     asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(taddr), "r"(ncols));
 }
+__device__ __forceinline__ float *tc_smem(float *tsm) {
+  return reinterpret_cast<float *>((reinterpret_cast<uintptr_t>(tsm) + 1023) & ~(uintptr_t)1023);
+}
+// TMEM allocation for `used` columns: a power of two >= 32.
+__host__ __device__ inline uint32_t tmem_cols(uint32_t used) {
+  uint32_t n = 32;
+  while (n < used) n <<= 1;
+  return n;
+}
 
-// Pre-order: U_v = P_v^T X_v for the non-tip children of one level's nodes.
-// grid = (tiles of 128 patterns, level nodes * 2 children, categories).
+// Pre-order: U_v = P_v^T X_v for the non-tip children of one level's nodes,
+// every category.  grid = (tiles of 128 patterns, level nodes * 2 children).
 __global__ void __launch_bounds__(kTcThr) k_tc_pre_u(Dims d, const int *__restrict__ lvl_nodes,
                                                     int lvl_off, const int *__restrict__ child,
                                                     const float *__restrict__ xbuf,
                                                     const float *__restrict__ tcB,
-                                                    float *__restrict__ pre, int *status) {
+                                                    float *__restrict__ pre, uint32_t ncols,
+                                                    int *status) {
   extern __shared__ __align__(1024) float tsm[];
   __shared__ uint32_t s_tmem;
-  __shared__ __align__(8) uint64_t mbar;
-  const int bi = blockIdx.y >> 1, x = blockIdx.y & 1, c = blockIdx.z;
+  __shared__ __align__(8) uint64_t mbar[2];
+  const int bi = blockIdx.y >> 1, x = blockIdx.y & 1;
   const int u = lvl_nodes[lvl_off + bi];
   const int v = child[2 * (u - d.N) + x];
   if (v < d.N) return;  // tips carry no outside partial (uniform over the CTA)
-  float *sm = reinterpret_cast<float *>((reinterpret_cast<uintptr_t>(tsm) + 1023) & ~(uintptr_t)1023);
-  const uint32_t taddr = tc_begin(&s_tmem, &mbar, 64);
-  uint32_t phase = 0;
+  float *sm = tc_smem(tsm);
+  const uint32_t taddr = tc_begin(&s_tmem, mbar, ncols);
+  uint32_t ph[2] = {0, 0};
   const int p0 = blockIdx.x * kRows;
   const int rows = min(kRows, d.P - p0);
-  const float *A = xbuf + ((((size_t)bi * 2 + x) * d.C + c) * d.P + p0) * d.Kp;
-  const float *B = tcB + ((size_t)v * d.C + c) * 4 * kTile4 + 2 * kTile4;  // pre hi | lo
-  float *D = pre + ((((size_t)(v - d.N) * d.C + c) * d.P) + p0) * d.Kp;
-  if (!tc_tile(A, d.Kp, rows, B, D, d.Kp, sm, taddr, &mbar, phase) && threadIdx.x == 0)
-    atomicOr(status, ST_TIMEOUT);
-  tc_end(taddr, 64);
+  auto item = [&](int c, const float *&A, const float *&B, uint32_t &col) {
+    A = xbuf + ((((size_t)bi * 2 + x) * d.C + c) * d.P + p0) * d.Kp;
+    B = tcB + ((size_t)v * d.C + c) * 4 * kTile4 + 2 * kTile4;  // pre hi | lo
+    col = c * 64;
+  };
+  if (!tc_pipeline(d.C, d.Kp, rows, item, sm, taddr, mbar, ph)) {
+    if (threadIdx.x == 0) atomicOr(status, ST_TIMEOUT);
+    tc_end(taddr, ncols);
+    return;
+  }
+  const int r = threadIdx.x;
+  for (int c = 0; c < d.C; c++) {
+    float *drow = pre + ((((size_t)(v - d.N) * d.C + c) * d.P) + p0 + r) * d.Kp;
+#pragma unroll
+    for (int cb = 0; cb < 4; cb++) {
+      float vv[16];
+      tc_ld16(taddr, c * 64 + cb * 16, vv);
+      if (r < rows) {
+#pragma unroll
+        for (int q = 0; q < 4; q++)
+          *reinterpret_cast<float4 *>(drow + cb * 16 + 4 * q) =
+              make_float4(vv[4 * q], vv[4 * q + 1], vv[4 * q + 2], vv[4 * q + 3]);
+      }
+    }
+  }
+  tc_end(taddr, ncols);
 }
 
+// S of both children of node u for every category into TMEM (column block
+// (c * 2 + sd) * 64); tips are skipped (their S is a table row).
+__device__ __forceinline__ bool tc_children_S(const Dims &d, const int (&kid)[2],
+                                              const float *part, const float *tcB, int p0,
+                                              int rows, float *sm, uint32_t taddr,
+                                              uint64_t *mbar, uint32_t *ph) {
+  const bool st0 = kid[0] >= d.N, st1 = kid[1] >= d.N;
+  const int per = (int)st0 + (int)st1;
+  auto item = [&](int j, const float *&A, const float *&B, uint32_t &col) {
+    const int c = j / per;
+    const int sd = per == 2 ? (j & 1) : (st0 ? 0 : 1);
+    const int v = kid[sd];
+    A = part + ((((size_t)(v - d.N) * d.C + c) * d.P) + p0) * d.Kp;
+    B = tcB + ((size_t)v * d.C + c) * 4 * kTile4;  // post hi | lo
+    col = (uint32_t)(c * 2 + sd) * 64;
+  };
+  return tc_pipeline(per * d.C, d.Kp, rows, item, sm, taddr, mbar, ph);
+}
 
 // Post-order level: for every node u of the level and category c, S of each
 // stored child by a tile product (tips: the table row of their code), then
@@ -258,26 +350,15 @@ __global__ void __launch_bounds__(kTcThr) k_tc_post(Dims d, const int *__restric
                                                    int *status) {
   extern __shared__ __align__(1024) float tsm[];
   __shared__ uint32_t s_tmem;
-  __shared__ __align__(8) uint64_t mbar;
-  float *sm = reinterpret_cast<float *>((reinterpret_cast<uintptr_t>(tsm) + 1023) & ~(uintptr_t)1023);
+  __shared__ __align__(8) uint64_t mbar[2];
+  float *sm = tc_smem(tsm);
   const int u = lvl_nodes[lvl_off + blockIdx.y];
   const int slot = u - d.N;
   const int kid[2] = {child[2 * slot], child[2 * slot + 1]};
-  const uint32_t taddr = tc_begin(&s_tmem, &mbar, ncols);
-  uint32_t phase = 0;
+  const uint32_t taddr = tc_begin(&s_tmem, mbar, ncols);
+  uint32_t ph[2] = {0, 0};
   const int p0 = blockIdx.x * kRows, rows = min(kRows, d.P - p0);
-  bool ok = true;
-  for (int c = 0; c < d.C && ok; c++)
-    for (int sd = 0; sd < 2 && ok; sd++) {
-      const int v = kid[sd];
-      if (v < d.N) continue;
-      tc_stage_A(part + ((((size_t)(v - d.N) * d.C + c) * d.P) + p0) * d.Kp, d.Kp, rows, sm);
-      tc_stage_B(tcB + ((size_t)v * d.C + c) * 4 * kTile4, sm);
-      tc_sync_staged();
-      tc_mma(taddr + (c * 2 + sd) * 64, sm, &mbar);
-      ok = tc_wait(&mbar, phase);
-    }
-  if (!ok) {
+  if (!tc_children_S(d, kid, part, tcB, p0, rows, sm, taddr, mbar, ph)) {
     if (threadIdx.x == 0) atomicOr(status, ST_TIMEOUT);
     tc_end(taddr, ncols);
     return;
@@ -345,40 +426,30 @@ __global__ void __launch_bounds__(kTcThr) k_tc_post(Dims d, const int *__restric
   tc_end(taddr, ncols);
 }
 
-// Pre-order level, one category: X of both children of u,
+// Pre-order level: X of both children of u for every category,
 //   X_0 = U_u o S_1 2^-e_u,  X_1 = U_u o S_0 2^-e_u,
 // with S of stored children by tile products, into the adjoint scratch.
-// grid = (tiles of 128 patterns, nodes, categories).
+// grid = (tiles of 128 patterns, nodes).
 __global__ void __launch_bounds__(kTcThr) k_tc_pre_x(
     Dims d, const int *__restrict__ lvl_nodes, int lvl_off, const int *__restrict__ child, int root,
     const float *__restrict__ PT, const uint8_t *__restrict__ tips, const float *__restrict__ tcB,
     const float *__restrict__ part, const float *__restrict__ pre, const int16_t *__restrict__ scale,
     const double *__restrict__ pi, const double *__restrict__ catw,
-    const double *__restrict__ site_inv, float *__restrict__ xbuf, int *status) {
+    const double *__restrict__ site_inv, float *__restrict__ xbuf, uint32_t ncols, int *status) {
   extern __shared__ __align__(1024) float tsm[];
   __shared__ uint32_t s_tmem;
-  __shared__ __align__(8) uint64_t mbar;
-  float *sm = reinterpret_cast<float *>((reinterpret_cast<uintptr_t>(tsm) + 1023) & ~(uintptr_t)1023);
-  const int bi = blockIdx.y, c = blockIdx.z;
+  __shared__ __align__(8) uint64_t mbar[2];
+  float *sm = tc_smem(tsm);
+  const int bi = blockIdx.y;
   const int u = lvl_nodes[lvl_off + bi];
   const int slot = u - d.N;
   const int kid[2] = {child[2 * slot], child[2 * slot + 1]};
-  const uint32_t taddr = tc_begin(&s_tmem, &mbar, 128);
-  uint32_t phase = 0;
+  const uint32_t taddr = tc_begin(&s_tmem, mbar, ncols);
+  uint32_t ph[2] = {0, 0};
   const int p0 = blockIdx.x * kRows, rows = min(kRows, d.P - p0);
-  bool ok = true;
-  for (int sd = 0; sd < 2 && ok; sd++) {
-    const int v = kid[sd];
-    if (v < d.N) continue;
-    tc_stage_A(part + ((((size_t)(v - d.N) * d.C + c) * d.P) + p0) * d.Kp, d.Kp, rows, sm);
-    tc_stage_B(tcB + ((size_t)v * d.C + c) * 4 * kTile4, sm);
-    tc_sync_staged();
-    tc_mma(taddr + sd * 64, sm, &mbar);
-    ok = tc_wait(&mbar, phase);
-  }
-  if (!ok) {
+  if (!tc_children_S(d, kid, part, tcB, p0, rows, sm, taddr, mbar, ph)) {
     if (threadIdx.x == 0) atomicOr(status, ST_TIMEOUT);
-    tc_end(taddr, 128);
+    tc_end(taddr, ncols);
     return;
   }
   const int r = threadIdx.x, p = p0 + r;
@@ -388,45 +459,47 @@ __global__ void __launch_bounds__(kTcThr) k_tc_pre_x(
   for (int sd = 0; sd < 2; sd++)
     if (kid[sd] < d.N) code[sd] = tips[(size_t)kid[sd] * d.Pp + pc];
   const Pow2 f = pow2_neg(scale[(size_t)slot * d.Pp + pc]);
-  const double rootw = (u == root) ? catw[c] * site_inv[pc] : 0.0;
-  const float *urow = pre + ((((size_t)slot * d.C + c) * d.P) + pc) * d.Kp;
-  float *x0 = xbuf + ((((size_t)bi * 2 + 0) * d.C + c) * d.P + pc) * d.Kp;
-  float *x1 = xbuf + ((((size_t)bi * 2 + 1) * d.C + c) * d.P + pc) * d.Kp;
-  for (int cb = 0; cb < 4; cb++) {
-    float s[2][16];
-    for (int sd = 0; sd < 2; sd++) {
-      if (kid[sd] >= d.N) {
-        tc_ld16(taddr, sd * 64 + cb * 16, s[sd]);
-      } else {
-        const float *row = PT + (((size_t)kid[sd] * d.C + c) * d.NR + code[sd]) * d.Kp + cb * 16;
-#pragma unroll
-        for (int j = 0; j < 16; j++) s[sd][j] = row[j];
-      }
-    }
-    if (live) {
-#pragma unroll
-      for (int q = 0; q < 4; q++) {
-        const int i = cb * 16 + 4 * q;
-        float4 uu;
-        if (u == root) {
-          uu = make_float4(i < d.K ? (float)(rootw * pi[i]) : 0.f,
-                           i + 1 < d.K ? (float)(rootw * pi[i + 1]) : 0.f,
-                           i + 2 < d.K ? (float)(rootw * pi[i + 2]) : 0.f,
-                           i + 3 < d.K ? (float)(rootw * pi[i + 3]) : 0.f);
+  for (int c = 0; c < d.C; c++) {
+    const double rootw = (u == root) ? catw[c] * site_inv[pc] : 0.0;
+    const float *urow = pre + ((((size_t)slot * d.C + c) * d.P) + pc) * d.Kp;
+    float *x0 = xbuf + ((((size_t)bi * 2 + 0) * d.C + c) * d.P + pc) * d.Kp;
+    float *x1 = xbuf + ((((size_t)bi * 2 + 1) * d.C + c) * d.P + pc) * d.Kp;
+    for (int cb = 0; cb < 4; cb++) {
+      float s[2][16];
+      for (int sd = 0; sd < 2; sd++) {
+        if (kid[sd] >= d.N) {
+          tc_ld16(taddr, (c * 2 + sd) * 64 + cb * 16, s[sd]);
         } else {
-          uu = *reinterpret_cast<const float4 *>(urow + i);  // zero beyond K
+          const float *row = PT + (((size_t)kid[sd] * d.C + c) * d.NR + code[sd]) * d.Kp + cb * 16;
+#pragma unroll
+          for (int j = 0; j < 16; j++) s[sd][j] = row[j];
         }
-        const float *a = s[1] + 4 * q, *b = s[0] + 4 * q;
-        *reinterpret_cast<float4 *>(x0 + i) =
-            make_float4(sc(uu.x * a[0], f), sc(uu.y * a[1], f), sc(uu.z * a[2], f),
-                        sc(uu.w * a[3], f));
-        *reinterpret_cast<float4 *>(x1 + i) =
-            make_float4(sc(uu.x * b[0], f), sc(uu.y * b[1], f), sc(uu.z * b[2], f),
-                        sc(uu.w * b[3], f));
+      }
+      if (live) {
+#pragma unroll
+        for (int q = 0; q < 4; q++) {
+          const int i = cb * 16 + 4 * q;
+          float4 uu;
+          if (u == root) {
+            uu = make_float4(i < d.K ? (float)(rootw * pi[i]) : 0.f,
+                             i + 1 < d.K ? (float)(rootw * pi[i + 1]) : 0.f,
+                             i + 2 < d.K ? (float)(rootw * pi[i + 2]) : 0.f,
+                             i + 3 < d.K ? (float)(rootw * pi[i + 3]) : 0.f);
+          } else {
+            uu = *reinterpret_cast<const float4 *>(urow + i);  // zero beyond K
+          }
+          const float *a = s[1] + 4 * q, *b = s[0] + 4 * q;
+          *reinterpret_cast<float4 *>(x0 + i) =
+              make_float4(sc(uu.x * a[0], f), sc(uu.y * a[1], f), sc(uu.z * a[2], f),
+                          sc(uu.w * a[3], f));
+          *reinterpret_cast<float4 *>(x1 + i) =
+              make_float4(sc(uu.x * b[0], f), sc(uu.y * b[1], f), sc(uu.z * b[2], f),
+                          sc(uu.w * b[3], f));
+        }
       }
     }
   }
-  tc_end(taddr, 128);
+  tc_end(taddr, ncols);
 }
 
 }  // namespace
@@ -438,12 +511,10 @@ bool tc_path(const epoch_ctx *c) {
 cudaError_t launch_tc_post(epoch_ctx *c, int level) {
   const Dims &d = c->d;
   const int w = c->h_level_off[level + 1] - c->h_level_off[level];
-  uint32_t ncols = 128;
-  while (ncols < (uint32_t)(2 * d.C * 64)) ncols <<= 1;
   cudaFuncSetAttribute(k_tc_post, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kTcSmem);
   k_tc_post<<<dim3(ceil_div(d.P, kRows), w), kTcThr, kTcSmem, c->stream>>>(
       d, c->d_level_nodes, c->h_level_off[level], c->d_child, c->d_PT32, c->d_tips, c->d_tcB,
-      (float *)c->d_part, c->d_scale, ncols, c->d_status);
+      (float *)c->d_part, c->d_scale, tmem_cols(2 * d.C * 64), c->d_status);
   c->launches++;
   return cudaGetLastError();
 }
@@ -452,10 +523,10 @@ cudaError_t launch_tc_pre_x(epoch_ctx *c, int level, int root) {
   const Dims &d = c->d;
   const int w = c->h_level_off[level + 1] - c->h_level_off[level];
   cudaFuncSetAttribute(k_tc_pre_x, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kTcSmem);
-  k_tc_pre_x<<<dim3(ceil_div(d.P, kRows), w, d.C), kTcThr, kTcSmem, c->stream>>>(
+  k_tc_pre_x<<<dim3(ceil_div(d.P, kRows), w), kTcThr, kTcSmem, c->stream>>>(
       d, c->d_level_nodes, c->h_level_off[level], c->d_child, root, c->d_PT32, c->d_tips,
       c->d_tcB, (const float *)c->d_part, (const float *)c->d_pre, c->d_scale, c->d_pi,
-      c->d_catw, c->d_site_inv, (float *)c->d_xbuf, c->d_status);
+      c->d_catw, c->d_site_inv, (float *)c->d_xbuf, tmem_cols(2 * d.C * 64), c->d_status);
   c->launches++;
   return cudaGetLastError();
 }
@@ -471,10 +542,11 @@ cudaError_t launch_tc_pre_u(epoch_ctx *c, int level) {
   const Dims &d = c->d;
   const int w = c->h_level_off[level + 1] - c->h_level_off[level];
   cudaFuncSetAttribute(k_tc_pre_u, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kTcSmem);
-  dim3 g(ceil_div(d.P, kRows), 2 * w, d.C);
+  dim3 g(ceil_div(d.P, kRows), 2 * w);
   k_tc_pre_u<<<g, kTcThr, kTcSmem, c->stream>>>(d, c->d_level_nodes, c->h_level_off[level],
                                                  c->d_child, (const float *)c->d_xbuf, c->d_tcB,
-                                                 (float *)c->d_pre, c->d_status);
+                                                 (float *)c->d_pre, tmem_cols(d.C * 64),
+                                                 c->d_status);
   c->launches++;
   return cudaGetLastError();
 }
