@@ -178,20 +178,83 @@ __device__ __forceinline__ bool tc_wait(uint64_t *mbar, uint32_t &phase) {
   asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
   return done != 0;
 }
-// 16 columns of the thread's TMEM lane (warp w reads lanes 32w..32w+31).
-__device__ __forceinline__ void tc_ld16(uint32_t taddr, int col, float *out) {
-  uint32_t v[16];
+// 64 columns of the thread's TMEM lane (warp w reads lanes 32w..32w+31),
+// one load and one wait.
+__device__ __forceinline__ void tc_ld64(uint32_t taddr, int col, float *out) {
+  uint32_t v[64];
   const uint32_t a = taddr + ((uint32_t)(32 * (threadIdx.x >> 5)) << 16) + col;
   asm volatile(
-      "tcgen05.ld.sync.aligned.32x32b.x16.b32 {%0,%1,%2,%3,%4,%5,%6,%7,%8,%9,%10,%11,%12,%13,%14,%"
-      "15}, [%16];"
+      "tcgen05.ld.sync.aligned.32x32b.x64.b32 {%0,%1,%2,%3,%4,%5,%6,%7,%8,%9,%10,%11,"
+      "%12,%13,%14,%15,%16,%17,%18,%19,%20,%21,%22,%23,%24,%25,%26,%27,%28,%29,%30,%31,"
+      "%32,%33,%34,%35,%36,%37,%38,%39,%40,%41,%42,%43,%44,%45,%46,%47,%48,%49,%50,%51,"
+      "%52,%53,%54,%55,%56,%57,%58,%59,%60,%61,%62,%63}, [%64];"
       : "=r"(v[0]), "=r"(v[1]), "=r"(v[2]), "=r"(v[3]), "=r"(v[4]), "=r"(v[5]), "=r"(v[6]),
         "=r"(v[7]), "=r"(v[8]), "=r"(v[9]), "=r"(v[10]), "=r"(v[11]), "=r"(v[12]), "=r"(v[13]),
-        "=r"(v[14]), "=r"(v[15])
+        "=r"(v[14]), "=r"(v[15]), "=r"(v[16]), "=r"(v[17]), "=r"(v[18]), "=r"(v[19]), "=r"(v[20]),
+        "=r"(v[21]), "=r"(v[22]), "=r"(v[23]), "=r"(v[24]), "=r"(v[25]), "=r"(v[26]), "=r"(v[27]),
+        "=r"(v[28]), "=r"(v[29]), "=r"(v[30]), "=r"(v[31]), "=r"(v[32]), "=r"(v[33]), "=r"(v[34]),
+        "=r"(v[35]), "=r"(v[36]), "=r"(v[37]), "=r"(v[38]), "=r"(v[39]), "=r"(v[40]), "=r"(v[41]),
+        "=r"(v[42]), "=r"(v[43]), "=r"(v[44]), "=r"(v[45]), "=r"(v[46]), "=r"(v[47]), "=r"(v[48]),
+        "=r"(v[49]), "=r"(v[50]), "=r"(v[51]), "=r"(v[52]), "=r"(v[53]), "=r"(v[54]), "=r"(v[55]),
+        "=r"(v[56]), "=r"(v[57]), "=r"(v[58]), "=r"(v[59]), "=r"(v[60]), "=r"(v[61]), "=r"(v[62]),
+        "=r"(v[63])
       : "r"(a));
   asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
 #pragma unroll
-  for (int j = 0; j < 16; j++) out[j] = __uint_as_float(v[j]);
+  for (int j = 0; j < 64; j++) out[j] = __uint_as_float(v[j]);
+}
+
+// Epilogue row buffers in the (then free) stage memory: 128 rows of 64
+// floats, padded to 68 so that the eight rows a quarter-warp writes at one
+// column fall in distinct banks.
+constexpr int kRowPad = 68;
+constexpr int kRowBuf = kRows * kRowPad;  // floats of one buffer
+// Thread r's row of 64 values into buffer row r (float4 stores).
+__device__ __forceinline__ void row_put(float *buf, const float (&v)[64]) {
+  float *dst = buf + threadIdx.x * kRowPad;
+#pragma unroll
+  for (int q = 0; q < 16; q++)
+    *reinterpret_cast<float4 *>(dst + 4 * q) =
+        make_float4(v[4 * q], v[4 * q + 1], v[4 * q + 2], v[4 * q + 3]);
+}
+// A buffer of `rows` rows to global rows (ld floats apart) with whole-warp
+// contiguous float4 stores; each row scaled by 2^-e[row] when e is given.
+__device__ __forceinline__ void rows_store(const float *buf, float *dst, int ld, int rows,
+                                           const int *e) {
+#pragma unroll 4
+  for (int q = 0; q < 16; q++) {
+    const int idx = threadIdx.x + kTcThr * q, row = idx >> 4, c4 = idx & 15;
+    if (row < rows) {
+      float4 v = *reinterpret_cast<const float4 *>(buf + row * kRowPad + 4 * c4);
+      if (e) {
+        const Pow2 f = pow2_neg(e[row]);
+        v = make_float4(sc(v.x, f), sc(v.y, f), sc(v.z, f), sc(v.w, f));
+      }
+      *reinterpret_cast<float4 *>(dst + (size_t)row * ld + 4 * c4) = v;
+    }
+  }
+}
+// Global rows (ld floats apart) into a buffer with contiguous loads; rows >=
+// `rows` become zero.
+__device__ __forceinline__ void rows_load(const float *src, int ld, int rows, float *buf) {
+#pragma unroll 4
+  for (int q = 0; q < 16; q++) {
+    const int idx = threadIdx.x + kTcThr * q, row = idx >> 4, c4 = idx & 15;
+    const float4 v = row < rows ? *reinterpret_cast<const float4 *>(src + (size_t)row * ld + 4 * c4)
+                                : make_float4(0.f, 0.f, 0.f, 0.f);
+    *reinterpret_cast<float4 *>(buf + row * kRowPad + 4 * c4) = v;
+  }
+}
+// 64 floats of a table row (a tip's S: the row of its code).
+__device__ __forceinline__ void row_get(const float *src, float (&v)[64]) {
+#pragma unroll
+  for (int q = 0; q < 16; q++) {
+    const float4 t = reinterpret_cast<const float4 *>(src)[q];
+    v[4 * q] = t.x;
+    v[4 * q + 1] = t.y;
+    v[4 * q + 2] = t.z;
+    v[4 * q + 3] = t.w;
+  }
 }
 
 // Tile products D_j[128 x 64] = A_j B_j^T into TMEM columns col_j, j < n,
@@ -299,21 +362,16 @@ __global__ void __launch_bounds__(kTcThr) k_tc_pre_u(Dims d, const int *__restri
     tc_end(taddr, ncols);
     return;
   }
-  const int r = threadIdx.x;
+  // U of every category: TMEM -> row buffers -> contiguous stores
   for (int c = 0; c < d.C; c++) {
-    float *drow = pre + ((((size_t)(v - d.N) * d.C + c) * d.P) + p0 + r) * d.Kp;
-#pragma unroll
-    for (int cb = 0; cb < 4; cb++) {
-      float vv[16];
-      tc_ld16(taddr, c * 64 + cb * 16, vv);
-      if (r < rows) {
-#pragma unroll
-        for (int q = 0; q < 4; q++)
-          *reinterpret_cast<float4 *>(drow + cb * 16 + 4 * q) =
-              make_float4(vv[4 * q], vv[4 * q + 1], vv[4 * q + 2], vv[4 * q + 3]);
-      }
-    }
+    float vv[64];
+    tc_ld64(taddr, c * 64, vv);
+    row_put(sm + c * kRowBuf, vv);
   }
+  __syncthreads();
+  for (int c = 0; c < d.C; c++)
+    rows_store(sm + c * kRowBuf, pre + ((((size_t)(v - d.N) * d.C + c) * d.P) + p0) * d.Kp,
+               d.Kp, rows, nullptr);
   tc_end(taddr, ncols);
 }
 
@@ -363,66 +421,44 @@ __global__ void __launch_bounds__(kTcThr) k_tc_post(Dims d, const int *__restric
     tc_end(taddr, ncols);
     return;
   }
+  __shared__ int s_e[kRows];
   const int r = threadIdx.x, p = p0 + r;
   const bool live = r < rows;
   int code[2] = {0, 0};
   for (int sd = 0; sd < 2; sd++)
     if (kid[sd] < d.N && live) code[sd] = tips[(size_t)kid[sd] * d.Pp + p];
-  // S values of child sd, category c, columns cb*16.. (TMEM or the tip row)
-  auto load_s = [&](int sd, int c, int cb, float *s) {
-    if (kid[sd] >= d.N) {
-      tc_ld16(taddr, (c * 2 + sd) * 64 + cb * 16, s);
-    } else {
-      const float4 *row = reinterpret_cast<const float4 *>(
-          PT + (((size_t)kid[sd] * d.C + c) * d.NR + code[sd]) * d.Kp + cb * 16);
-#pragma unroll
-      for (int q = 0; q < 4; q++) {
-        const float4 t = row[q];
-        s[4 * q] = t.x;
-        s[4 * q + 1] = t.y;
-        s[4 * q + 2] = t.z;
-        s[4 * q + 3] = t.w;
-      }
-    }
+  // S of child sd, category c: TMEM block, or the table row of the tip's code
+  auto load_s = [&](int sd, int c, float (&v)[64]) {
+    if (kid[sd] >= d.N)
+      tc_ld64(taddr, (c * 2 + sd) * 64, v);
+    else
+      row_get(PT + (((size_t)kid[sd] * d.C + c) * d.NR + code[sd]) * d.Kp, v);
   };
+  // unscaled L_u rows of every category into the row buffers; their maximum
   float m = 0.f;
-  for (int c = 0; c < d.C; c++)
-    for (int cb = 0; cb < 4; cb++) {
-      float s0[16], s1[16];
-      load_s(0, c, cb, s0);
-      load_s(1, c, cb, s1);
+  for (int c = 0; c < d.C; c++) {
+    float s0[64], s1[64];
+    load_s(0, c, s0);
+    load_s(1, c, s1);
 #pragma unroll
-      for (int j = 0; j < 16; j++)
-        if (cb * 16 + j < d.K) m = fmaxf(m, s0[j] * s1[j]);
+    for (int j = 0; j < 64; j++) {
+      s0[j] = j < d.K ? s0[j] * s1[j] : 0.f;
+      m = fmaxf(m, s0[j]);
     }
+    row_put(sm + c * kRowBuf, s0);
+  }
   int e = 0;
   if (!(m <= 3.0e38f)) {
     if (live) atomicOr(status, ST_NONFINITE);
   } else if (m > 0.f) {
     frexpf(m, &e);
   }
-  const Pow2 f = pow2_neg(e);
-  for (int c = 0; c < d.C; c++) {
-    float *dst = part + ((((size_t)slot * d.C + c) * d.P) + p) * d.Kp;
-    for (int cb = 0; cb < 4; cb++) {
-      float s0[16], s1[16];
-      load_s(0, c, cb, s0);
-      load_s(1, c, cb, s1);
-      if (live) {
-#pragma unroll
-        for (int q = 0; q < 4; q++) {
-          const int i = cb * 16 + 4 * q;
-          float4 o;
-          o.x = i + 0 < d.K ? sc(s0[4 * q + 0] * s1[4 * q + 0], f) : 0.f;
-          o.y = i + 1 < d.K ? sc(s0[4 * q + 1] * s1[4 * q + 1], f) : 0.f;
-          o.z = i + 2 < d.K ? sc(s0[4 * q + 2] * s1[4 * q + 2], f) : 0.f;
-          o.w = i + 3 < d.K ? sc(s0[4 * q + 3] * s1[4 * q + 3], f) : 0.f;
-          *reinterpret_cast<float4 *>(dst + i) = o;
-        }
-      }
-    }
-  }
+  s_e[r] = e;
   if (live) scale[(size_t)slot * d.Pp + p] = (int16_t)e;
+  __syncthreads();
+  for (int c = 0; c < d.C; c++)
+    rows_store(sm + c * kRowBuf, part + ((((size_t)slot * d.C + c) * d.P) + p0) * d.Kp, d.Kp,
+               rows, s_e);
   tc_end(taddr, ncols);
 }
 
@@ -459,45 +495,36 @@ __global__ void __launch_bounds__(kTcThr) k_tc_pre_x(
   for (int sd = 0; sd < 2; sd++)
     if (kid[sd] < d.N) code[sd] = tips[(size_t)kid[sd] * d.Pp + pc];
   const Pow2 f = pow2_neg(scale[(size_t)slot * d.Pp + pc]);
+  float *ubuf = sm, *xb0 = sm + kRowBuf, *xb1 = sm + 2 * kRowBuf;
   for (int c = 0; c < d.C; c++) {
+    if (u != root)  // U_u rows of this category, contiguous loads
+      rows_load(pre + ((((size_t)slot * d.C + c) * d.P) + p0) * d.Kp, d.Kp, rows, ubuf);
+    __syncthreads();
     const double rootw = (u == root) ? catw[c] * site_inv[pc] : 0.0;
-    const float *urow = pre + ((((size_t)slot * d.C + c) * d.P) + pc) * d.Kp;
-    float *x0 = xbuf + ((((size_t)bi * 2 + 0) * d.C + c) * d.P + pc) * d.Kp;
-    float *x1 = xbuf + ((((size_t)bi * 2 + 1) * d.C + c) * d.P + pc) * d.Kp;
-    for (int cb = 0; cb < 4; cb++) {
-      float s[2][16];
-      for (int sd = 0; sd < 2; sd++) {
-        if (kid[sd] >= d.N) {
-          tc_ld16(taddr, (c * 2 + sd) * 64 + cb * 16, s[sd]);
-        } else {
-          const float *row = PT + (((size_t)kid[sd] * d.C + c) * d.NR + code[sd]) * d.Kp + cb * 16;
-#pragma unroll
-          for (int j = 0; j < 16; j++) s[sd][j] = row[j];
-        }
-      }
-      if (live) {
-#pragma unroll
-        for (int q = 0; q < 4; q++) {
-          const int i = cb * 16 + 4 * q;
-          float4 uu;
-          if (u == root) {
-            uu = make_float4(i < d.K ? (float)(rootw * pi[i]) : 0.f,
-                             i + 1 < d.K ? (float)(rootw * pi[i + 1]) : 0.f,
-                             i + 2 < d.K ? (float)(rootw * pi[i + 2]) : 0.f,
-                             i + 3 < d.K ? (float)(rootw * pi[i + 3]) : 0.f);
-          } else {
-            uu = *reinterpret_cast<const float4 *>(urow + i);  // zero beyond K
-          }
-          const float *a = s[1] + 4 * q, *b = s[0] + 4 * q;
-          *reinterpret_cast<float4 *>(x0 + i) =
-              make_float4(sc(uu.x * a[0], f), sc(uu.y * a[1], f), sc(uu.z * a[2], f),
-                          sc(uu.w * a[3], f));
-          *reinterpret_cast<float4 *>(x1 + i) =
-              make_float4(sc(uu.x * b[0], f), sc(uu.y * b[1], f), sc(uu.z * b[2], f),
-                          sc(uu.w * b[3], f));
-        }
-      }
+    float s0[64], s1[64];
+    for (int sd = 0; sd < 2; sd++) {
+      float(&sv)[64] = sd ? s1 : s0;
+      if (kid[sd] >= d.N)
+        tc_ld64(taddr, (c * 2 + sd) * 64, sv);
+      else
+        row_get(PT + (((size_t)kid[sd] * d.C + c) * d.NR + code[sd]) * d.Kp, sv);
     }
+    const float *urow = ubuf + r * kRowPad;
+#pragma unroll
+    for (int j = 0; j < 64; j++) {
+      const float uu = (u == root) ? (j < d.K ? (float)(rootw * pi[j]) : 0.f) : urow[j];
+      const float a = s1[j], b = s0[j];
+      s0[j] = sc(uu * a, f);  // X_0 = U o S_1 2^-e
+      s1[j] = sc(uu * b, f);  // X_1 = U o S_0 2^-e
+    }
+    row_put(xb0, s0);
+    row_put(xb1, s1);
+    __syncthreads();
+    rows_store(xb0, xbuf + ((((size_t)bi * 2 + 0) * d.C + c) * d.P + p0) * d.Kp, d.Kp, rows,
+               nullptr);
+    rows_store(xb1, xbuf + ((((size_t)bi * 2 + 1) * d.C + c) * d.P + p0) * d.Kp, d.Kp, rows,
+               nullptr);
+    __syncthreads();  // buffers reused by the next category
   }
   tc_end(taddr, ncols);
 }
