@@ -93,6 +93,7 @@ __global__ void k_tc_prep(Dims d, const double *__restrict__ P64, const int *__r
 // B hi, B lo (16 KB each).
 constexpr int kStageFloats = 2 * kATile + 2 * kTile4;
 constexpr size_t kTcSmem = sizeof(float) * 2 * kStageFloats + 1024;
+constexpr size_t kTcSmem1 = sizeof(float) * kStageFloats + 1024;  // one stage (one product)
 
 // An A tile in registers: thread (warp w, lane l) holds, for q < 16, row
 // 8q + (l & 7), columns 4 (4w + (l >> 3)) .. +3.  A warp's load covers 8 rows
@@ -325,128 +326,137 @@ __device__ void tc_end(uint32_t taddr, uint32_t ncols) {
 __device__ __forceinline__ float *tc_smem(float *tsm) {
   return reinterpret_cast<float *>((reinterpret_cast<uintptr_t>(tsm) + 1023) & ~(uintptr_t)1023);
 }
-// TMEM allocation for `used` columns: a power of two >= 32.
-__host__ __device__ inline uint32_t tmem_cols(uint32_t used) {
-  uint32_t n = 32;
-  while (n < used) n <<= 1;
-  return n;
-}
-
-// Pre-order: U_v = P_v^T X_v for the non-tip children of one level's nodes,
-// every category.  grid = (tiles of 128 patterns, level nodes * 2 children).
+// Pre-order: U_v = P_v^T X_v for the non-tip children of one level's nodes.
+// grid = (tiles of 128 patterns, level nodes * 2 children, categories); one
+// tile product per CTA (one shared-memory stage).
 __global__ void __launch_bounds__(kTcThr) k_tc_pre_u(Dims d, const int *__restrict__ lvl_nodes,
                                                     int lvl_off, const int *__restrict__ child,
                                                     const float *__restrict__ xbuf,
                                                     const float *__restrict__ tcB,
-                                                    float *__restrict__ pre, uint32_t ncols,
-                                                    int *status) {
+                                                    float *__restrict__ pre, int *status) {
   extern __shared__ __align__(1024) float tsm[];
   __shared__ uint32_t s_tmem;
   __shared__ __align__(8) uint64_t mbar[2];
-  const int bi = blockIdx.y >> 1, x = blockIdx.y & 1;
+  const int bi = blockIdx.y >> 1, x = blockIdx.y & 1, c = blockIdx.z;
   const int u = lvl_nodes[lvl_off + bi];
   const int v = child[2 * (u - d.N) + x];
   if (v < d.N) return;  // tips carry no outside partial (uniform over the CTA)
   float *sm = tc_smem(tsm);
-  const uint32_t taddr = tc_begin(&s_tmem, mbar, ncols);
+  const uint32_t taddr = tc_begin(&s_tmem, mbar, 64);
   uint32_t ph[2] = {0, 0};
   const int p0 = blockIdx.x * kRows;
   const int rows = min(kRows, d.P - p0);
-  auto item = [&](int c, const float *&A, const float *&B, uint32_t &col) {
+  auto item = [&](int, const float *&A, const float *&B, uint32_t &col) {
     A = xbuf + ((((size_t)bi * 2 + x) * d.C + c) * d.P + p0) * d.Kp;
     B = tcB + ((size_t)v * d.C + c) * 4 * kTile4 + 2 * kTile4;  // pre hi | lo
-    col = c * 64;
+    col = 0;
   };
-  if (!tc_pipeline(d.C, d.Kp, rows, item, sm, taddr, mbar, ph)) {
+  if (!tc_pipeline(1, d.Kp, rows, item, sm, taddr, mbar, ph)) {
     if (threadIdx.x == 0) atomicOr(status, ST_TIMEOUT);
-    tc_end(taddr, ncols);
+    tc_end(taddr, 64);
     return;
   }
-  // U of every category: TMEM -> row buffers -> contiguous stores
-  for (int c = 0; c < d.C; c++) {
-    float vv[64];
-    tc_ld64(taddr, c * 64, vv);
-    row_put(sm + c * kRowBuf, vv);
-  }
+  float vv[64];
+  tc_ld64(taddr, 0, vv);
+  row_put(sm, vv);
   __syncthreads();
-  for (int c = 0; c < d.C; c++)
-    rows_store(sm + c * kRowBuf, pre + ((((size_t)(v - d.N) * d.C + c) * d.P) + p0) * d.Kp,
-               d.Kp, rows, nullptr);
-  tc_end(taddr, ncols);
+  rows_store(sm, pre + ((((size_t)(v - d.N) * d.C + c) * d.P) + p0) * d.Kp, d.Kp, rows, nullptr);
+  tc_end(taddr, 64);
 }
 
-// S of both children of node u for every category into TMEM (column block
-// (c * 2 + sd) * 64); tips are skipped (their S is a table row).
-__device__ __forceinline__ bool tc_children_S(const Dims &d, const int (&kid)[2],
+// S of both children of node u for category c into TMEM columns sd * 64;
+// tips are skipped (their S is a table row).
+__device__ __forceinline__ bool tc_children_S(const Dims &d, const int (&kid)[2], int c,
                                               const float *part, const float *tcB, int p0,
                                               int rows, float *sm, uint32_t taddr,
                                               uint64_t *mbar, uint32_t *ph) {
   const bool st0 = kid[0] >= d.N, st1 = kid[1] >= d.N;
-  const int per = (int)st0 + (int)st1;
+  const int n = (int)st0 + (int)st1;
   auto item = [&](int j, const float *&A, const float *&B, uint32_t &col) {
-    const int c = j / per;
-    const int sd = per == 2 ? (j & 1) : (st0 ? 0 : 1);
+    const int sd = n == 2 ? j : (st0 ? 0 : 1);
     const int v = kid[sd];
     A = part + ((((size_t)(v - d.N) * d.C + c) * d.P) + p0) * d.Kp;
     B = tcB + ((size_t)v * d.C + c) * 4 * kTile4;  // post hi | lo
-    col = (uint32_t)(c * 2 + sd) * 64;
+    col = (uint32_t)sd * 64;
   };
-  return tc_pipeline(per * d.C, d.Kp, rows, item, sm, taddr, mbar, ph);
+  return tc_pipeline(n, d.Kp, rows, item, sm, taddr, mbar, ph);
 }
 
-// Post-order level: for every node u of the level and category c, S of each
-// stored child by a tile product (tips: the table row of their code), then
+// S of child sd (TMEM block sd, or the table row of a tip's code).
+__device__ __forceinline__ void child_S(const Dims &d, const float *PT, int kid, int c, int code,
+                                        uint32_t taddr, int sd, float (&v)[64]) {
+  if (kid >= d.N)
+    tc_ld64(taddr, sd * 64, v);
+  else
+    row_get(PT + (((size_t)kid * d.C + c) * d.NR + code) * d.Kp, v);
+}
+
+// Cluster-wide barrier (every CTA of the cluster arrives, then waits).
+__device__ __forceinline__ void cluster_sync() {
+  asm volatile("barrier.cluster.arrive.release.aligned;\nbarrier.cluster.wait.acquire.aligned;" ::
+                   : "memory");
+}
+// The float at the same shared-memory location in CTA `rank` of the cluster.
+__device__ __forceinline__ float cluster_ld(const float *p, uint32_t rank) {
+  uint32_t remote;
+  asm volatile("mapa.shared::cluster.u32 %0, %1, %2;" : "=r"(remote) : "r"(su32(p)), "r"(rank));
+  float v;
+  asm volatile("ld.shared::cluster.f32 %0, [%1];" : "=f"(v) : "r"(remote) : "memory");
+  return v;
+}
+
+// Post-order level: for node u, category c = blockIdx.z: S of each stored
+// child by a tile product (tips: the table row of their code), then
 // L_u = S_0 o S_1 rescaled per pattern by 2^-e, e the binary exponent of the
-// max over (c, i) (frexp convention).  TMEM holds S for both children and all
-// categories: 2 C blocks of 64 columns.  grid = (tiles of 128 patterns, nodes).
+// max over (c, i) (frexp convention).  The C CTAs of a (tile, node) form a
+// cluster: each publishes its rows' maxima over i in shared memory and reads
+// the others' through distributed shared memory.  grid = (tiles of 128
+// patterns, nodes, categories), cluster (1, 1, C).
 __global__ void __launch_bounds__(kTcThr) k_tc_post(Dims d, const int *__restrict__ lvl_nodes,
                                                    int lvl_off, const int *__restrict__ child,
                                                    const float *__restrict__ PT,
                                                    const uint8_t *__restrict__ tips,
                                                    const float *__restrict__ tcB, float *part,
-                                                   int16_t *__restrict__ scale, uint32_t ncols,
-                                                   int *status) {
+                                                   int16_t *__restrict__ scale, int *status) {
   extern __shared__ __align__(1024) float tsm[];
   __shared__ uint32_t s_tmem;
   __shared__ __align__(8) uint64_t mbar[2];
+  __shared__ float s_m[kRows];
+  __shared__ int s_e[kRows];
   float *sm = tc_smem(tsm);
+  const int c = blockIdx.z;
   const int u = lvl_nodes[lvl_off + blockIdx.y];
   const int slot = u - d.N;
   const int kid[2] = {child[2 * slot], child[2 * slot + 1]};
-  const uint32_t taddr = tc_begin(&s_tmem, mbar, ncols);
+  const uint32_t taddr = tc_begin(&s_tmem, mbar, 128);
   uint32_t ph[2] = {0, 0};
   const int p0 = blockIdx.x * kRows, rows = min(kRows, d.P - p0);
-  if (!tc_children_S(d, kid, part, tcB, p0, rows, sm, taddr, mbar, ph)) {
-    if (threadIdx.x == 0) atomicOr(status, ST_TIMEOUT);
-    tc_end(taddr, ncols);
-    return;
-  }
-  __shared__ int s_e[kRows];
+  const bool ok = tc_children_S(d, kid, c, part, tcB, p0, rows, sm, taddr, mbar, ph);
+  if (!ok && threadIdx.x == 0) atomicOr(status, ST_TIMEOUT);
   const int r = threadIdx.x, p = p0 + r;
   const bool live = r < rows;
   int code[2] = {0, 0};
   for (int sd = 0; sd < 2; sd++)
     if (kid[sd] < d.N && live) code[sd] = tips[(size_t)kid[sd] * d.Pp + p];
-  // S of child sd, category c: TMEM block, or the table row of the tip's code
-  auto load_s = [&](int sd, int c, float (&v)[64]) {
-    if (kid[sd] >= d.N)
-      tc_ld64(taddr, (c * 2 + sd) * 64, v);
-    else
-      row_get(PT + (((size_t)kid[sd] * d.C + c) * d.NR + code[sd]) * d.Kp, v);
-  };
-  // unscaled L_u rows of every category into the row buffers; their maximum
+  // unscaled L_u row of this category into the row buffer; its maximum
   float m = 0.f;
-  for (int c = 0; c < d.C; c++) {
+  if (ok) {
     float s0[64], s1[64];
-    load_s(0, c, s0);
-    load_s(1, c, s1);
+    child_S(d, PT, kid[0], c, code[0], taddr, 0, s0);
+    child_S(d, PT, kid[1], c, code[1], taddr, 1, s1);
 #pragma unroll
     for (int j = 0; j < 64; j++) {
       s0[j] = j < d.K ? s0[j] * s1[j] : 0.f;
       m = fmaxf(m, s0[j]);
     }
-    row_put(sm + c * kRowBuf, s0);
+    row_put(sm, s0);
   }
+  s_m[r] = m;
+  // every CTA of the cluster takes both barriers, whatever happened above
+  cluster_sync();
+  for (int q = 0; q < d.C; q++)
+    if (q != c) m = fmaxf(m, cluster_ld(&s_m[r], (uint32_t)q));
+  cluster_sync();  // the peers' maxima have been read: their CTAs may finish
   int e = 0;
   if (!(m <= 3.0e38f)) {
     if (live) atomicOr(status, ST_NONFINITE);
@@ -454,38 +464,37 @@ __global__ void __launch_bounds__(kTcThr) k_tc_post(Dims d, const int *__restric
     frexpf(m, &e);
   }
   s_e[r] = e;
-  if (live) scale[(size_t)slot * d.Pp + p] = (int16_t)e;
+  if (live && c == 0) scale[(size_t)slot * d.Pp + p] = (int16_t)e;
   __syncthreads();
-  for (int c = 0; c < d.C; c++)
-    rows_store(sm + c * kRowBuf, part + ((((size_t)slot * d.C + c) * d.P) + p0) * d.Kp, d.Kp,
-               rows, s_e);
-  tc_end(taddr, ncols);
+  if (ok)
+    rows_store(sm, part + ((((size_t)slot * d.C + c) * d.P) + p0) * d.Kp, d.Kp, rows, s_e);
+  tc_end(taddr, 128);
 }
 
-// Pre-order level: X of both children of u for every category,
+// Pre-order level, one category: X of both children of u,
 //   X_0 = U_u o S_1 2^-e_u,  X_1 = U_u o S_0 2^-e_u,
 // with S of stored children by tile products, into the adjoint scratch.
-// grid = (tiles of 128 patterns, nodes).
+// grid = (tiles of 128 patterns, nodes, categories).
 __global__ void __launch_bounds__(kTcThr) k_tc_pre_x(
     Dims d, const int *__restrict__ lvl_nodes, int lvl_off, const int *__restrict__ child, int root,
     const float *__restrict__ PT, const uint8_t *__restrict__ tips, const float *__restrict__ tcB,
     const float *__restrict__ part, const float *__restrict__ pre, const int16_t *__restrict__ scale,
     const double *__restrict__ pi, const double *__restrict__ catw,
-    const double *__restrict__ site_inv, float *__restrict__ xbuf, uint32_t ncols, int *status) {
+    const double *__restrict__ site_inv, float *__restrict__ xbuf, int *status) {
   extern __shared__ __align__(1024) float tsm[];
   __shared__ uint32_t s_tmem;
   __shared__ __align__(8) uint64_t mbar[2];
   float *sm = tc_smem(tsm);
-  const int bi = blockIdx.y;
+  const int bi = blockIdx.y, c = blockIdx.z;
   const int u = lvl_nodes[lvl_off + bi];
   const int slot = u - d.N;
   const int kid[2] = {child[2 * slot], child[2 * slot + 1]};
-  const uint32_t taddr = tc_begin(&s_tmem, mbar, ncols);
+  const uint32_t taddr = tc_begin(&s_tmem, mbar, 128);
   uint32_t ph[2] = {0, 0};
   const int p0 = blockIdx.x * kRows, rows = min(kRows, d.P - p0);
-  if (!tc_children_S(d, kid, part, tcB, p0, rows, sm, taddr, mbar, ph)) {
+  if (!tc_children_S(d, kid, c, part, tcB, p0, rows, sm, taddr, mbar, ph)) {
     if (threadIdx.x == 0) atomicOr(status, ST_TIMEOUT);
-    tc_end(taddr, ncols);
+    tc_end(taddr, 128);
     return;
   }
   const int r = threadIdx.x, p = p0 + r;
@@ -496,37 +505,29 @@ __global__ void __launch_bounds__(kTcThr) k_tc_pre_x(
     if (kid[sd] < d.N) code[sd] = tips[(size_t)kid[sd] * d.Pp + pc];
   const Pow2 f = pow2_neg(scale[(size_t)slot * d.Pp + pc]);
   float *ubuf = sm, *xb0 = sm + kRowBuf, *xb1 = sm + 2 * kRowBuf;
-  for (int c = 0; c < d.C; c++) {
-    if (u != root)  // U_u rows of this category, contiguous loads
-      rows_load(pre + ((((size_t)slot * d.C + c) * d.P) + p0) * d.Kp, d.Kp, rows, ubuf);
-    __syncthreads();
-    const double rootw = (u == root) ? catw[c] * site_inv[pc] : 0.0;
-    float s0[64], s1[64];
-    for (int sd = 0; sd < 2; sd++) {
-      float(&sv)[64] = sd ? s1 : s0;
-      if (kid[sd] >= d.N)
-        tc_ld64(taddr, (c * 2 + sd) * 64, sv);
-      else
-        row_get(PT + (((size_t)kid[sd] * d.C + c) * d.NR + code[sd]) * d.Kp, sv);
-    }
-    const float *urow = ubuf + r * kRowPad;
+  if (u != root)  // U_u rows, contiguous loads
+    rows_load(pre + ((((size_t)slot * d.C + c) * d.P) + p0) * d.Kp, d.Kp, rows, ubuf);
+  __syncthreads();
+  const double rootw = (u == root) ? catw[c] * site_inv[pc] : 0.0;
+  float s0[64], s1[64];
+  child_S(d, PT, kid[0], c, code[0], taddr, 0, s0);
+  child_S(d, PT, kid[1], c, code[1], taddr, 1, s1);
+  const float *urow = ubuf + r * kRowPad;
 #pragma unroll
-    for (int j = 0; j < 64; j++) {
-      const float uu = (u == root) ? (j < d.K ? (float)(rootw * pi[j]) : 0.f) : urow[j];
-      const float a = s1[j], b = s0[j];
-      s0[j] = sc(uu * a, f);  // X_0 = U o S_1 2^-e
-      s1[j] = sc(uu * b, f);  // X_1 = U o S_0 2^-e
-    }
-    row_put(xb0, s0);
-    row_put(xb1, s1);
-    __syncthreads();
-    rows_store(xb0, xbuf + ((((size_t)bi * 2 + 0) * d.C + c) * d.P + p0) * d.Kp, d.Kp, rows,
-               nullptr);
-    rows_store(xb1, xbuf + ((((size_t)bi * 2 + 1) * d.C + c) * d.P + p0) * d.Kp, d.Kp, rows,
-               nullptr);
-    __syncthreads();  // buffers reused by the next category
+  for (int j = 0; j < 64; j++) {
+    const float uu = (u == root) ? (j < d.K ? (float)(rootw * pi[j]) : 0.f) : urow[j];
+    const float a = s1[j], b = s0[j];
+    s0[j] = sc(uu * a, f);  // X_0 = U o S_1 2^-e
+    s1[j] = sc(uu * b, f);  // X_1 = U o S_0 2^-e
   }
-  tc_end(taddr, ncols);
+  row_put(xb0, s0);
+  row_put(xb1, s1);
+  __syncthreads();
+  rows_store(xb0, xbuf + ((((size_t)bi * 2 + 0) * d.C + c) * d.P + p0) * d.Kp, d.Kp, rows,
+             nullptr);
+  rows_store(xb1, xbuf + ((((size_t)bi * 2 + 1) * d.C + c) * d.P + p0) * d.Kp, d.Kp, rows,
+             nullptr);
+  tc_end(taddr, 128);
 }
 
 }  // namespace
@@ -539,21 +540,35 @@ cudaError_t launch_tc_post(epoch_ctx *c, int level) {
   const Dims &d = c->d;
   const int w = c->h_level_off[level + 1] - c->h_level_off[level];
   cudaFuncSetAttribute(k_tc_post, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kTcSmem);
-  k_tc_post<<<dim3(ceil_div(d.P, kRows), w), kTcThr, kTcSmem, c->stream>>>(
-      d, c->d_level_nodes, c->h_level_off[level], c->d_child, c->d_PT32, c->d_tips, c->d_tcB,
-      (float *)c->d_part, c->d_scale, tmem_cols(2 * d.C * 64), c->d_status);
+  cudaLaunchConfig_t cfg = {};
+  cfg.gridDim = dim3(ceil_div(d.P, kRows), w, d.C);
+  cfg.blockDim = dim3(kTcThr);
+  cfg.dynamicSmemBytes = kTcSmem;
+  cfg.stream = c->stream;
+  cudaLaunchAttribute at[1];
+  at[0].id = cudaLaunchAttributeClusterDimension;  // the categories of a (tile, node)
+  at[0].val.clusterDim.x = 1;
+  at[0].val.clusterDim.y = 1;
+  at[0].val.clusterDim.z = d.C;
+  cfg.attrs = at;
+  cfg.numAttrs = 1;
+  cudaError_t e = cudaLaunchKernelEx(&cfg, k_tc_post, d, (const int *)c->d_level_nodes,
+                                     c->h_level_off[level], (const int *)c->d_child,
+                                     (const float *)c->d_PT32, (const uint8_t *)c->d_tips,
+                                     (const float *)c->d_tcB, (float *)c->d_part, c->d_scale,
+                                     c->d_status);
   c->launches++;
-  return cudaGetLastError();
+  return e != cudaSuccess ? e : cudaGetLastError();
 }
 
 cudaError_t launch_tc_pre_x(epoch_ctx *c, int level, int root) {
   const Dims &d = c->d;
   const int w = c->h_level_off[level + 1] - c->h_level_off[level];
   cudaFuncSetAttribute(k_tc_pre_x, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kTcSmem);
-  k_tc_pre_x<<<dim3(ceil_div(d.P, kRows), w), kTcThr, kTcSmem, c->stream>>>(
+  k_tc_pre_x<<<dim3(ceil_div(d.P, kRows), w, d.C), kTcThr, kTcSmem, c->stream>>>(
       d, c->d_level_nodes, c->h_level_off[level], c->d_child, root, c->d_PT32, c->d_tips,
       c->d_tcB, (const float *)c->d_part, (const float *)c->d_pre, c->d_scale, c->d_pi,
-      c->d_catw, c->d_site_inv, (float *)c->d_xbuf, tmem_cols(2 * d.C * 64), c->d_status);
+      c->d_catw, c->d_site_inv, (float *)c->d_xbuf, c->d_status);
   c->launches++;
   return cudaGetLastError();
 }
@@ -568,12 +583,11 @@ cudaError_t launch_tc_prep(epoch_ctx *c) {
 cudaError_t launch_tc_pre_u(epoch_ctx *c, int level) {
   const Dims &d = c->d;
   const int w = c->h_level_off[level + 1] - c->h_level_off[level];
-  cudaFuncSetAttribute(k_tc_pre_u, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kTcSmem);
-  dim3 g(ceil_div(d.P, kRows), 2 * w);
-  k_tc_pre_u<<<g, kTcThr, kTcSmem, c->stream>>>(d, c->d_level_nodes, c->h_level_off[level],
-                                                 c->d_child, (const float *)c->d_xbuf, c->d_tcB,
-                                                 (float *)c->d_pre, tmem_cols(d.C * 64),
-                                                 c->d_status);
+  cudaFuncSetAttribute(k_tc_pre_u, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kTcSmem1);
+  dim3 g(ceil_div(d.P, kRows), 2 * w, d.C);
+  k_tc_pre_u<<<g, kTcThr, kTcSmem1, c->stream>>>(d, c->d_level_nodes, c->h_level_off[level],
+                                                  c->d_child, (const float *)c->d_xbuf, c->d_tcB,
+                                                  (float *)c->d_pre, c->d_status);
   c->launches++;
   return cudaGetLastError();
 }
