@@ -260,12 +260,14 @@ __device__ __forceinline__ void row_get(const float *src, float (&v)[64]) {
 
 // Tile products D_j[128 x 64] = A_j B_j^T into TMEM columns col_j, j < n,
 // for one tile of 128 rows (A rows lda floats apart; rows >= `rows` read as
-// zero), through the two shared-memory stages: while the tensor cores run
-// item j, item j+1's A is loaded into registers and its B copied by
-// cp.async.  item(j, A, B, col) names the operands.  Every thread takes
-// part.  Returns false when an MMA did not complete within the wait bound;
-// nothing is then left in flight but that MMA.
-template <class Item>
+// zero).  item(j, A, B, col) names the operands.  Every thread takes part.
+// NST = 2 (two shared-memory stages): while the tensor cores run item j, item
+// j+1's A is loaded into registers and its B copied by cp.async.  NST = 1
+// (one stage, so that two CTAs fit on an SM): item j+1's A is loaded into
+// registers during item j's MMA, its B once that MMA has completed.
+// Returns false when an MMA did not complete within the wait bound; nothing
+// is then left in flight but that MMA.
+template <int NST, class Item>
 __device__ bool tc_pipeline(int n, int lda, int rows, Item item, float *sm, uint32_t taddr,
                             uint64_t *mbar, uint32_t *ph) {
   if (n <= 0) return true;
@@ -276,20 +278,31 @@ __device__ bool tc_pipeline(int n, int lda, int rows, Item item, float *sm, uint
   tc_async_B(B, sm);
   tc_load_A(A, lda, rows, ra);
   for (int j = 0; j < n; j++) {
-    float *st = sm + (j & 1) * kStageFloats;
-    tc_store_A(ra, st);  // stage j&1 is free: MMA j-2 was waited for at j-1
+    float *st = sm + (NST == 2 ? (j & 1) * kStageFloats : 0);
+    if (NST == 1 && j >= 1) {  // the single stage is free once MMA j-1 has completed
+      if (!tc_wait(&mbar[(j - 1) & 1], ph[(j - 1) & 1])) {
+        asm volatile("cp.async.wait_all;" ::: "memory");
+        return false;
+      }
+      tc_async_B(B, st);
+    }
+    tc_store_A(ra, st);  // two stages: stage j&1 is free, MMA j-2 was waited for at j-1
     const uint32_t colj = col;
     if (j + 1 < n) {
       item(j + 1, A, B, col);
       tc_load_A(A, lda, rows, ra);  // in flight during this item's MMA
     }
-    if (j >= 1 && !tc_wait(&mbar[(j - 1) & 1], ph[(j - 1) & 1])) {
-      asm volatile("cp.async.wait_all;" ::: "memory");
-      return false;
-    }
-    if (j + 1 < n) {  // MMA j-1 has released stage (j+1)&1
-      tc_async_B(B, sm + ((j + 1) & 1) * kStageFloats);
-      asm volatile("cp.async.wait_group 1;" ::: "memory");  // B of item j has landed
+    if (NST == 2) {
+      if (j >= 1 && !tc_wait(&mbar[(j - 1) & 1], ph[(j - 1) & 1])) {
+        asm volatile("cp.async.wait_all;" ::: "memory");
+        return false;
+      }
+      if (j + 1 < n) {  // MMA j-1 has released stage (j+1)&1
+        tc_async_B(B, sm + ((j + 1) & 1) * kStageFloats);
+        asm volatile("cp.async.wait_group 1;" ::: "memory");  // B of item j has landed
+      } else {
+        asm volatile("cp.async.wait_group 0;" ::: "memory");
+      }
     } else {
       asm volatile("cp.async.wait_group 0;" ::: "memory");
     }
@@ -351,7 +364,7 @@ __global__ void __launch_bounds__(kTcThr) k_tc_pre_u(Dims d, const int *__restri
     B = tcB + ((size_t)v * d.C + c) * 4 * kTile4 + 2 * kTile4;  // pre hi | lo
     col = 0;
   };
-  if (!tc_pipeline(1, d.Kp, rows, item, sm, taddr, mbar, ph)) {
+  if (!tc_pipeline<1>(1, d.Kp, rows, item, sm, taddr, mbar, ph)) {
     if (threadIdx.x == 0) atomicOr(status, ST_TIMEOUT);
     tc_end(taddr, 64);
     return;
@@ -379,7 +392,7 @@ __device__ __forceinline__ bool tc_children_S(const Dims &d, const int (&kid)[2]
     B = tcB + ((size_t)v * d.C + c) * 4 * kTile4;  // post hi | lo
     col = (uint32_t)sd * 64;
   };
-  return tc_pipeline(n, d.Kp, rows, item, sm, taddr, mbar, ph);
+  return tc_pipeline<1>(n, d.Kp, rows, item, sm, taddr, mbar, ph);
 }
 
 // S of child sd (TMEM block sd, or the table row of a tip's code).
@@ -504,7 +517,9 @@ __global__ void __launch_bounds__(kTcThr) k_tc_pre_x(
   for (int sd = 0; sd < 2; sd++)
     if (kid[sd] < d.N) code[sd] = tips[(size_t)kid[sd] * d.Pp + pc];
   const Pow2 f = pow2_neg(scale[(size_t)slot * d.Pp + pc]);
-  float *ubuf = sm, *xb0 = sm + kRowBuf, *xb1 = sm + 2 * kRowBuf;
+  // X_0 overwrites U_u in place: each thread reads its whole U row before it
+  // writes that row of X_0
+  float *ubuf = sm, *xb0 = sm, *xb1 = sm + kRowBuf;
   if (u != root)  // U_u rows, contiguous loads
     rows_load(pre + ((((size_t)slot * d.C + c) * d.P) + p0) * d.Kp, d.Kp, rows, ubuf);
   __syncthreads();
@@ -539,11 +554,11 @@ bool tc_path(const epoch_ctx *c) {
 cudaError_t launch_tc_post(epoch_ctx *c, int level) {
   const Dims &d = c->d;
   const int w = c->h_level_off[level + 1] - c->h_level_off[level];
-  cudaFuncSetAttribute(k_tc_post, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kTcSmem);
+  cudaFuncSetAttribute(k_tc_post, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kTcSmem1);
   cudaLaunchConfig_t cfg = {};
   cfg.gridDim = dim3(ceil_div(d.P, kRows), w, d.C);
   cfg.blockDim = dim3(kTcThr);
-  cfg.dynamicSmemBytes = kTcSmem;
+  cfg.dynamicSmemBytes = kTcSmem1;
   cfg.stream = c->stream;
   cudaLaunchAttribute at[1];
   at[0].id = cudaLaunchAttributeClusterDimension;  // the categories of a (tile, node)
@@ -564,8 +579,8 @@ cudaError_t launch_tc_post(epoch_ctx *c, int level) {
 cudaError_t launch_tc_pre_x(epoch_ctx *c, int level, int root) {
   const Dims &d = c->d;
   const int w = c->h_level_off[level + 1] - c->h_level_off[level];
-  cudaFuncSetAttribute(k_tc_pre_x, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kTcSmem);
-  k_tc_pre_x<<<dim3(ceil_div(d.P, kRows), w, d.C), kTcThr, kTcSmem, c->stream>>>(
+  cudaFuncSetAttribute(k_tc_pre_x, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kTcSmem1);
+  k_tc_pre_x<<<dim3(ceil_div(d.P, kRows), w, d.C), kTcThr, kTcSmem1, c->stream>>>(
       d, c->d_level_nodes, c->h_level_off[level], c->d_child, root, c->d_PT32, c->d_tips,
       c->d_tcB, (const float *)c->d_part, (const float *)c->d_pre, c->d_scale, c->d_pi,
       c->d_catw, c->d_site_inv, (float *)c->d_xbuf, c->d_status);
