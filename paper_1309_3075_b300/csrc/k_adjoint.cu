@@ -479,11 +479,14 @@ __global__ void k_grad_reduce(Dims d, const int *__restrict__ parent, const int 
 
 // G over one chunk of kTile patterns for (level node, child x, category c),
 // register-tiled: the KB x KB block of (i, j) (KB = K rounded up to 8, 16, 32
-// or 64) is split over a (KB/4) x (KB/4) thread grid, each thread owning a
-// 4 x 4 tile.  Below KB = 64 the 256 threads form 256 / (KB/4)^2 groups that
-// take interleaved patterns and are summed in a fixed order at the end.
-// Patterns go through shared memory 2048 / KB at a time (X rows, and n_p L_v
-// rows or the tip code's indicator).  Same output layout as k_G_part.
+// or 64) is split over a (KB/RT) x (KB/RT) thread grid, each thread owning an
+// RT x RT tile (RT = 4; 8 x 8 tiles at KB = 64 measured slower).  The 256
+// threads form
+// NG = 256 / (KB/RT)^2 groups that take interleaved patterns and are summed in
+// a fixed order at the end.  Patterns go through shared memory SUB = 2048 / KB
+// at a time (X rows, and n_p L_v rows or the tip code's indicator); the next
+// batch is loaded into registers while the current one is multiplied.  Same
+// output layout as k_G_part.
 template <int KB>
 __global__ void __launch_bounds__(256) k_G_tiled(Dims d, const int *__restrict__ lvl_nodes,
                                                  int lvl_off, const int *__restrict__ child,
@@ -493,7 +496,8 @@ __global__ void __launch_bounds__(256) k_G_tiled(Dims d, const int *__restrict__
                                                  const unsigned long long *__restrict__ masks,
                                                  const double *__restrict__ pw, int nchunk,
                                                  float *__restrict__ Gpart) {
-  constexpr int TW = KB / 4, NG = 256 / (TW * TW), SUB = 2048 / KB;
+  constexpr int RT = 4, TW = KB / RT, NG = 256 / (TW * TW), SUB = 2048 / KB;
+  constexpr int V4 = SUB * KB / 4 / 256;  // float4 of X (and of L) per thread per batch: 2
   __shared__ __align__(16) float Xs[SUB * KB];
   __shared__ __align__(16) float Ls[SUB * KB];
   const int chunk = blockIdx.x, bi = blockIdx.y, x = blockIdx.z / d.C, c = blockIdx.z % d.C;
@@ -505,64 +509,104 @@ __global__ void __launch_bounds__(256) k_G_tiled(Dims d, const int *__restrict__
   const float *L = v >= d.N ? part + ((size_t)(v - d.N) * d.C + c) * d.P * d.Kp : nullptr;
   const int grp = threadIdx.x / (TW * TW), t = threadIdx.x % (TW * TW);
   const int ti = t / TW, tj = t % TW;
-  float acc[4][4] = {};
-  for (int q0 = p0; q0 < p1; q0 += SUB) {
-    for (int e = threadIdx.x; e < SUB * KB; e += blockDim.x) {
-      const int pr = e / KB, k = e % KB, p = q0 + pr;
-      float xv = 0.f, lv = 0.f;
-      if (p < p1 && k < d.K) {
-        xv = X[(size_t)p * d.Kp + k];
+  float4 xr[V4], lr[V4];
+  // batch q0 into registers: float4 e = threadIdx.x + 256 m is pattern e / (KB/4),
+  // states 4 (e % (KB/4)) ..
+  auto fetch = [&](int q0) {
+#pragma unroll
+    for (int m = 0; m < V4; m++) {
+      const int e = threadIdx.x + 256 * m, pr = e / (KB / 4), k = 4 * (e % (KB / 4)), p = q0 + pr;
+      float4 xv = make_float4(0.f, 0.f, 0.f, 0.f), lv = xv;
+      if (p < p1 && k < d.Kp) {  // entries K..Kp-1 are stored zeros
+        xv = *reinterpret_cast<const float4 *>(X + (size_t)p * d.Kp + k);
         const float n = (float)pw[p];
-        if (L) lv = n * L[(size_t)p * d.Kp + k];
-        else lv = code_allows(d, masks, tips[(size_t)v * d.Pp + p], k) ? n : 0.f;
+        if (L) {
+          lv = *reinterpret_cast<const float4 *>(L + (size_t)p * d.Kp + k);
+          lv = make_float4(n * lv.x, n * lv.y, n * lv.z, n * lv.w);
+        } else {
+          const int code = tips[(size_t)v * d.Pp + p];
+          lv = make_float4(code_allows(d, masks, code, k) && k < d.K ? n : 0.f,
+                           code_allows(d, masks, code, k + 1) && k + 1 < d.K ? n : 0.f,
+                           code_allows(d, masks, code, k + 2) && k + 2 < d.K ? n : 0.f,
+                           code_allows(d, masks, code, k + 3) && k + 3 < d.K ? n : 0.f);
+        }
       }
-      Xs[e] = xv;
-      Ls[e] = lv;
+      xr[m] = xv;
+      lr[m] = lv;
+    }
+  };
+  float acc[RT][RT] = {};
+  fetch(p0);
+  for (int q0 = p0; q0 < p1; q0 += SUB) {
+#pragma unroll
+    for (int m = 0; m < V4; m++) {
+      const int e = threadIdx.x + 256 * m;
+      reinterpret_cast<float4 *>(Xs)[e] = xr[m];
+      reinterpret_cast<float4 *>(Ls)[e] = lr[m];
     }
     __syncthreads();
-#pragma unroll 4
+    if (q0 + SUB < p1) fetch(q0 + SUB);  // in flight during the products
+#pragma unroll 2
     for (int pr = grp; pr < SUB; pr += NG) {
-      const float4 a = *reinterpret_cast<const float4 *>(&Xs[pr * KB + 4 * ti]);
-      const float4 b = *reinterpret_cast<const float4 *>(&Ls[pr * KB + 4 * tj]);
-      const float av[4] = {a.x, a.y, a.z, a.w}, bv[4] = {b.x, b.y, b.z, b.w};
+      float av[RT], bv[RT];
 #pragma unroll
-      for (int r = 0; r < 4; r++)
+      for (int h = 0; h < RT / 4; h++) {
+        const float4 a = *reinterpret_cast<const float4 *>(&Xs[pr * KB + RT * ti + 4 * h]);
+        const float4 b = *reinterpret_cast<const float4 *>(&Ls[pr * KB + RT * tj + 4 * h]);
+        av[4 * h] = a.x, av[4 * h + 1] = a.y, av[4 * h + 2] = a.z, av[4 * h + 3] = a.w;
+        bv[4 * h] = b.x, bv[4 * h + 1] = b.y, bv[4 * h + 2] = b.z, bv[4 * h + 3] = b.w;
+      }
 #pragma unroll
-        for (int q = 0; q < 4; q++) acc[r][q] += av[r] * bv[q];
+      for (int r = 0; r < RT; r++)
+#pragma unroll
+        for (int q = 0; q < RT; q++) acc[r][q] += av[r] * bv[q];
     }
     __syncthreads();
   }
   float *out = Gpart + (((size_t)slot * nchunk + chunk) * 2 + x) * d.C * d.KK + (size_t)c * d.KK;
   if (NG == 1) {
 #pragma unroll
-    for (int r = 0; r < 4; r++)
+    for (int r = 0; r < RT; r++)
 #pragma unroll
-      for (int q = 0; q < 4; q++) {
-        const int i = 4 * ti + r, j = 4 * tj + q;
+      for (int q = 0; q < RT; q++) {
+        const int i = RT * ti + r, j = RT * tj + q;
         if (i < d.K && j < d.K) out[i * d.K + j] = acc[r][q];
       }
     return;
   }
-  // NG * KB * KB = 4096 floats: the two staging buffers together hold every
-  // group's tile (flat index e, split at SUB * KB between Xs and Ls)
-  float *red = Xs;
+  // group sums in a fixed order through the 4096 floats of Xs | Ls (flat
+  // index f, split at SUB * KB): all groups at once when NG * KB^2 fits,
+  // else one group after another
+  auto red_at = [&](int f) -> float & { return f < SUB * KB ? Xs[f] : Ls[f - SUB * KB]; };
+  if (NG * KB * KB <= 2 * SUB * KB) {
 #pragma unroll
-  for (int r = 0; r < 4; r++)
+    for (int r = 0; r < RT; r++)
 #pragma unroll
-    for (int q = 0; q < 4; q++) {
-      const int e = grp * KB * KB + (4 * ti + r) * KB + 4 * tj + q;
-      if (e < SUB * KB) red[e] = acc[r][q];
-      else Ls[e - SUB * KB] = acc[r][q];
+      for (int q = 0; q < RT; q++) red_at(grp * KB * KB + (RT * ti + r) * KB + RT * tj + q) = acc[r][q];
+    __syncthreads();
+    for (int e = threadIdx.x; e < KB * KB; e += blockDim.x) {
+      const int i = e / KB, j = e % KB;
+      float sum = 0.f;
+      for (int g = 0; g < NG; g++) sum += red_at(g * KB * KB + e);
+      if (i < d.K && j < d.K) out[i * d.K + j] = sum;
     }
-  __syncthreads();
-  for (int e = threadIdx.x; e < KB * KB; e += blockDim.x) {
-    const int i = e / KB, j = e % KB;
-    float sum = 0.f;
+  } else {
     for (int g = 0; g < NG; g++) {
-      const int f = g * KB * KB + e;
-      sum += f < SUB * KB ? red[f] : Ls[f - SUB * KB];
+      if (grp == g) {
+#pragma unroll
+        for (int r = 0; r < RT; r++)
+#pragma unroll
+          for (int q = 0; q < RT; q++) {
+            float &cell = red_at((RT * ti + r) * KB + RT * tj + q);
+            cell = g ? cell + acc[r][q] : acc[r][q];
+          }
+      }
+      __syncthreads();
     }
-    if (i < d.K && j < d.K) out[i * d.K + j] = sum;
+    for (int e = threadIdx.x; e < KB * KB; e += blockDim.x) {
+      const int i = e / KB, j = e % KB;
+      if (i < d.K && j < d.K) out[i * d.K + j] = red_at(e);
+    }
   }
 }
 
