@@ -195,6 +195,28 @@ epoch_status epoch_gradient(epoch_ctx *ctx, double *d_heights,
                             double *d_boundaries, double *d_params,
                             double *d_branch_rates);
 
+/* Expected numbers of transitions i -> j ("Markov jumps") given the data,
+ * summed over the weighted patterns (n_p) and the rate categories, for the
+ * inputs of the last gradient evaluation (epoch_gradient, or
+ * epoch_evaluate_async with with_gradient = 1; EPOCH_ERR_ORDER otherwise).
+ * Not in the paper: it uses the per-branch adjoints G = d lnL / d P of the
+ * gradient.  For a segment with E = exp(tau Q_s) (tau = r_v rho_c dt) the
+ * expected count given both end states is q_ij d log E_ab / d q_ij with
+ * q_ii held fixed (a path's density is a product of jump factors q_ij and
+ * holding factors); over the data this is
+ *   N_ij = q_ij < A^T G Z^T , dE/dq_ij >,
+ * A / Z the products of the segment exponentials above / below (Eq.
+ * convolution), dE/dq_ij by the Daleckii-Krein form of the eigensystem.
+ * q is the normalised Q_s, so counts do not depend on the normalisation.
+ * Outputs (host, caller-owned, either may be NULL), diagonal entries 0:
+ *   per_branch [2N-1][K][K]  summed over the branch's segments (root: 0);
+ *   per_epoch  [E][K][K]     summed over the segments lying in epoch e.
+ * FP64 on every precision (from the path's G).  Needs reversible = 1
+ * (EPOCH_ERR_UNSUPPORTED otherwise).  Synchronises.  Allocates a per-
+ * segment buffer [2N-1][E][C][K][K] doubles on first use
+ * (EPOCH_ERR_CAPACITY if that fails). */
+epoch_status epoch_expected_counts(epoch_ctx *ctx, double *per_branch, double *per_epoch);
+
 /* Test hook: P_{node,cat} [K][K] of the last epoch_compute_branch_matrices. */
 epoch_status epoch_get_branch_matrix(epoch_ctx *ctx, int node, int category,
                                      double *out);

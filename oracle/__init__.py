@@ -93,6 +93,8 @@ def _load():
         _lib.or_branch_adjoints.argtypes = [pp, dp, dp]
         _lib.or_gradient.restype = C.c_int
         _lib.or_gradient.argtypes = [pp, dp, dp, dp, dp, dp]
+        _lib.or_expected_counts.restype = C.c_int
+        _lib.or_expected_counts.argtypes = [pp, dp, dp]
     return _lib
 
 
@@ -241,6 +243,24 @@ def gradient(w, scaling=True):
         raise RuntimeError(f"oracle gradient failed ({rc})")
     return {"lnL": lnl.value, "heights": dh, "boundaries": db[: pk.E - 1],
             "params": dp[: pk.n_params], "branch_rates": dr}
+
+
+def expected_counts(w, scaling=True):
+    """Expected numbers of i -> j transitions given the data, summed over the
+    weighted patterns and the categories: per branch [2N-1][K][K] and per
+    epoch [E][K][K] (q_ij times the derivative of lnL with respect to q_ij
+    with q_ii held fixed, segment by segment; Minin and Suchard 2008)."""
+    lib = _load()
+    pk = _Packed(w, scaling)
+    nn = 2 * pk.N - 1
+    per_branch = np.zeros((nn, pk.K, pk.K))
+    per_epoch = np.zeros((pk.E, pk.K, pk.K))
+    P = C.POINTER(C.c_double)
+    rc = lib.or_expected_counts(C.byref(pk.pr), per_branch.ctypes.data_as(P),
+                                per_epoch.ctypes.data_as(P))
+    if rc != 0:
+        raise RuntimeError(f"oracle expected_counts failed ({rc})")
+    return per_branch, per_epoch
 
 
 def normalise(Q, pi):

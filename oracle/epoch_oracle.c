@@ -905,6 +905,101 @@ int or_gradient(const or_problem *pr, double *lnl, double *d_heights,
   return 0;
 }
 
+/* ------------------------------------------------------------------ */
+/* Expected numbers of i -> j transitions (Markov jumps) given the      */
+/* data, summed over the weighted patterns and the rate categories.     */
+/* A path's density is a product of jump factors (the off-diagonal     */
+/* rates of the moves it makes) and holding factors (the diagonal), so  */
+/* for a segment with exponential E = exp(tau Q_s), tau = r rho dt, the */
+/* expected count given both end states is q_ij d/dq_ij log E_ab with   */
+/* q_ii held fixed (Minin and Suchard 2008).  Over the data:           */
+/*   N_ij(segment) = q_ij <G, A_k L(tau Q_s, tau e_i e_j^T) Z_k>       */
+/* with G = d lnL / d P (branch_adjoints), A_k / Z_k the products of   */
+/* the segment exponentials above / below k and L the Frechet          */
+/* derivative of exp.  Since <H, L(X, Y)> = <L(X^T, H), Y> (cyclic      */
+/* trace of the integral form), all K^2 directions come from one       */
+/* derivative: N_ij = q_ij tau [L(tau Q_s^T, H)]_ij, H = A_k^T G Z_k^T. */
+/* Outputs: per branch [2N-1][K][K] (the root's block zero) and per    */
+/* epoch [E][K][K]; diagonal entries are zero.                         */
+/* ------------------------------------------------------------------ */
+int or_expected_counts(const or_problem *pr, double *per_branch, double *per_epoch) {
+  prep_t m;
+  if (prep_init(&m, pr) != 0) {
+    prep_free(&m);
+    return -1;
+  }
+  int K = pr->K, C = pr->n_categories, nn = m.nn, E = pr->n_epochs;
+  int KK = K * K;
+  double *P = all_branch_matrices(&m);
+  double *G = (double *)malloc(sizeof(double) * (size_t)nn * C * KK);
+  branch_adjoints(&m, P, G, NULL);
+  if (per_branch) memset(per_branch, 0, sizeof(double) * (size_t)nn * KK);
+  if (per_epoch) memset(per_epoch, 0, sizeof(double) * (size_t)E * KK);
+  double *Es = (double *)malloc(sizeof(double) * 64 * KK);
+  double *A = (double *)malloc(sizeof(double) * KK);
+  double *Z = (double *)malloc(sizeof(double) * KK);
+  double *T1 = (double *)malloc(sizeof(double) * KK);
+  double *D = (double *)malloc(sizeof(double) * KK);
+  double *X = (double *)malloc(sizeof(double) * KK);
+  double *Y = (double *)malloc(sizeof(double) * KK);
+  int ep[64], hi[64], lo[64];
+  double dt[64];
+  for (int v = 0; v < nn; v++) {
+    if (pr->parent[v] < 0) continue;
+    int n = branch_segments(&m, v, ep, dt, hi, lo);
+    double rb = branch_rate(pr, v);
+    for (int c = 0; c < C; c++) {
+      double rr = rb * pr->cat_rates[c];
+      const double *Gv = G + ((size_t)v * C + c) * KK;
+      for (int k = 0; k < n; k++)
+        segment_exp(&m, matrix_of_epoch(pr, ep[k]), rr * dt[k], Es + (size_t)k * KK);
+      for (int k = 0; k < n; k++) {
+        int s = matrix_of_epoch(pr, ep[k]);
+        const double *Qs = m.Q + (size_t)s * KK;
+        double tau = rr * dt[k];
+        mat_identity(K, A);
+        for (int q = 0; q < k; q++) mat_mul_right(K, A, Es + (size_t)q * KK, T1);
+        mat_identity(K, Z);
+        for (int q = k + 1; q < n; q++) mat_mul_right(K, Z, Es + (size_t)q * KK, T1);
+        /* H = A^T G Z^T */
+        for (int i = 0; i < K; i++)
+          for (int j = 0; j < K; j++) {
+            double acc = 0.0;
+            for (int a = 0; a < K; a++) acc += A[a * K + i] * Gv[a * K + j];
+            T1[i * K + j] = acc;
+          }
+        for (int i = 0; i < K; i++)
+          for (int j = 0; j < K; j++) {
+            double acc = 0.0;
+            for (int b = 0; b < K; b++) acc += T1[i * K + b] * Z[j * K + b];
+            Y[i * K + j] = acc;
+          }
+        for (int i = 0; i < K; i++)
+          for (int j = 0; j < K; j++) X[i * K + j] = tau * Qs[j * K + i]; /* (tau Q)^T */
+        expm_frechet(K, X, Y, D);
+        for (int i = 0; i < K; i++)
+          for (int j = 0; j < K; j++) {
+            if (i == j) continue;
+            double nij = Qs[i * K + j] * tau * D[i * K + j];
+            if (per_branch) per_branch[(size_t)v * KK + i * K + j] += nij;
+            if (per_epoch) per_epoch[(size_t)ep[k] * KK + i * K + j] += nij;
+          }
+      }
+    }
+  }
+  free(Es);
+  free(A);
+  free(Z);
+  free(T1);
+  free(D);
+  free(X);
+  free(Y);
+  free(G);
+  free(P);
+  prep_free(&m);
+  return 0;
+}
+
 /* exported eigen/exp helpers for the tests */
 int or_expm(int K, const double *Q, const double *pi, int reversible, double tau,
             double *P) {

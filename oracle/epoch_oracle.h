@@ -55,6 +55,7 @@ double or_brute_force(const or_problem *pr, double *site_lnl);
 int or_branch_adjoints(const or_problem *pr, double *G, double *lnl);
 int or_gradient(const or_problem *pr, double *lnl, double *d_heights,
                 double *d_boundaries, double *d_params, double *d_rates);
+int or_expected_counts(const or_problem *pr, double *per_branch, double *per_epoch);
 
 #ifdef __cplusplus
 }

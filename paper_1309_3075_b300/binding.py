@@ -55,6 +55,7 @@ _SIGS = {
     "epoch_site_log_likelihoods": [_vp, _dp],
     "epoch_gradient": [_vp, _dp, _dp, _dp, _dp],
     "epoch_get_branch_matrix": [_vp, C.c_int, C.c_int, _dp],
+    "epoch_expected_counts": [_vp, _dp, _dp],
     "epoch_evaluate_async": [_vp, C.c_int],
     "epoch_read_results": [_vp, _dp, _dp, _dp, _dp, _dp],
     "epoch_counters": [_vp, C.POINTER(C.c_longlong), C.POINTER(C.c_longlong)],
@@ -228,6 +229,17 @@ def epoch_gradient(ctx, n_nodes, n_epochs, n_params):
             "branch_rates": dr}
 
 
+def epoch_expected_counts(ctx, n_nodes, n_epochs, K):
+    """Expected transition counts of the last gradient evaluation:
+    (per_branch [n_nodes][K][K], per_epoch [n_epochs][K][K])."""
+    per_branch = np.zeros((n_nodes, K, K))
+    per_epoch = np.zeros((n_epochs, K, K))
+    _check(ctx, lib().epoch_expected_counts(ctx, per_branch.ctypes.data_as(_dp),
+                                            per_epoch.ctypes.data_as(_dp)),
+           "epoch_expected_counts")
+    return per_branch, per_epoch
+
+
 def epoch_get_branch_matrix(ctx, node, category, K):
     out = np.zeros((K, K))
     _check(ctx, lib().epoch_get_branch_matrix(ctx, int(node), int(category),
@@ -333,6 +345,11 @@ class EpochLikelihood:
 
     def branch_matrix(self, node, cat):
         return epoch_get_branch_matrix(self.ctx, node, cat, self.K)
+
+    def expected_counts(self):
+        """(per_branch, per_epoch) expected i -> j transition counts of the
+        last gradient evaluation."""
+        return epoch_expected_counts(self.ctx, 2 * self.N - 1, self.E, self.K)
 
     def evaluate(self, with_gradient=True):
         epoch_evaluate_async(self.ctx, with_gradient)

@@ -371,7 +371,7 @@ void epoch_destroy(epoch_ctx *c) {
                   c->d_site_inv,   c->d_lnl_part, c->d_lnl,     c->d_Gpart,      c->d_G,
                   c->d_gseg,       c->d_grad,    c->d_status,   c->d_ctl,        c->d_site_log,
                   c->d_level_off,  c->d_pairS,   c->d_pairL,    c->d_k4_walk,    c->d_k4_nt,
-                  c->d_tcB};
+                  c->d_tcB,        c->d_jumps,   c->d_jump_out};
   for (void *p : bufs) dfree(p);
   if (c->h_grad_pinned) cudaFreeHost(c->h_grad_pinned);
   if (c->h_lnl_pinned) cudaFreeHost(c->h_lnl_pinned);
@@ -562,7 +562,7 @@ epoch_status epoch_set_boundaries(epoch_ctx *c, const double *boundaries) {
   CK(cudaMemcpyAsync(c->d_boundaries, c->h_boundaries.data(), sizeof(double) * (E - 1),
                      cudaMemcpyHostToDevice, c->stream),
      "cudaMemcpyAsync(boundaries)");
-  c->have &= ~(HAVE_BRANCH | HAVE_PARTIALS);
+  c->have &= ~(HAVE_BRANCH | HAVE_PARTIALS | HAVE_GRADIENT);
   return EPOCH_OK;
 }
 
@@ -619,7 +619,7 @@ epoch_status epoch_set_rate_matrices(epoch_ctx *c, const double *Q, const double
   CK(cudaMemcpyAsync(c->d_pi, c->h_pi.data(), sizeof(double) * K, cudaMemcpyHostToDevice, c->stream),
      "cudaMemcpyAsync(pi)");
   c->have |= HAVE_RATES;
-  c->have &= ~(HAVE_BRANCH | HAVE_PARTIALS);
+  c->have &= ~(HAVE_BRANCH | HAVE_PARTIALS | HAVE_GRADIENT);
   return EPOCH_OK;
 }
 
@@ -656,7 +656,7 @@ epoch_status epoch_set_rate_derivatives(epoch_ctx *c, int n_params, const double
     CK(cudaMemcpyAsync(c->d_dQraw, c->h_dQ.data(), sizeof(double) * n_params * d.S * d.KK,
                        cudaMemcpyHostToDevice, c->stream),
        "cudaMemcpyAsync(dQ)");
-  c->have &= ~(HAVE_BRANCH | HAVE_PARTIALS);
+  c->have &= ~(HAVE_BRANCH | HAVE_PARTIALS | HAVE_GRADIENT);
   return EPOCH_OK;
 }
 
@@ -680,7 +680,7 @@ epoch_status epoch_set_categories(epoch_ctx *c, const double *rates, const doubl
                      c->stream),
      "cudaMemcpyAsync(weights)");
   c->have |= HAVE_CATS;
-  c->have &= ~(HAVE_BRANCH | HAVE_PARTIALS);
+  c->have &= ~(HAVE_BRANCH | HAVE_PARTIALS | HAVE_GRADIENT);
   return EPOCH_OK;
 }
 
@@ -712,7 +712,7 @@ epoch_status epoch_set_ambiguity_masks(epoch_ctx *c, int n_masks, const unsigned
   invalidate_graphs(c);
   // the kernel path can depend on the number of masks: the tree must be set
   // again (re-planned), then the tip data
-  c->have &= ~(HAVE_BRANCH | HAVE_PARTIALS | HAVE_TIPS | HAVE_TREE);
+  c->have &= ~(HAVE_BRANCH | HAVE_PARTIALS | HAVE_GRADIENT | HAVE_TIPS | HAVE_TREE);
   c->h_parent.clear();
   c->d.N = 0;
   return EPOCH_OK;
@@ -821,7 +821,7 @@ epoch_status epoch_set_tree(epoch_ctx *c, int n_taxa, const double *heights, con
     CK(cudaStreamSynchronize(c->stream), "cudaStreamSynchronize");
   }
   c->have |= HAVE_TREE;
-  c->have &= ~(HAVE_BRANCH | HAVE_PARTIALS);
+  c->have &= ~(HAVE_BRANCH | HAVE_PARTIALS | HAVE_GRADIENT);
   return EPOCH_OK;
 }
 
@@ -835,7 +835,7 @@ epoch_status epoch_set_heights(epoch_ctx *c, const double *heights) {
   CK(cudaMemcpyAsync(c->d_heights, c->h_heights.data(), sizeof(double) * c->d.nn, cudaMemcpyHostToDevice,
                      c->stream),
      "cudaMemcpyAsync(heights)");
-  c->have &= ~(HAVE_BRANCH | HAVE_PARTIALS);
+  c->have &= ~(HAVE_BRANCH | HAVE_PARTIALS | HAVE_GRADIENT);
   return EPOCH_OK;
 }
 
@@ -885,7 +885,7 @@ epoch_status epoch_set_tip_data(epoch_ctx *c, const int *tip_codes, const double
   CK(cudaEventRecord(c->tips_staging_ev[c->tips_staging_cur], c->stream), "cudaEventRecord");
   c->tips_staging_cur ^= 1;
   c->have |= HAVE_TIPS;
-  c->have &= ~HAVE_PARTIALS;
+  c->have &= ~(HAVE_PARTIALS | HAVE_GRADIENT);
   return EPOCH_OK;
 }
 
@@ -897,7 +897,7 @@ epoch_status epoch_compute_branch_matrices(epoch_ctx *c) {
   if (s != EPOCH_OK) return s;
   CK(join_sides(c), "join");
   c->have |= HAVE_BRANCH;
-  c->have &= ~HAVE_PARTIALS;
+  c->have &= ~(HAVE_PARTIALS | HAVE_GRADIENT);
   return EPOCH_OK;
 }
 
@@ -909,6 +909,7 @@ epoch_status epoch_update_partials(epoch_ctx *c) {
   if (s != EPOCH_OK) return s;
   CK(join_sides(c), "join");
   c->have |= HAVE_PARTIALS;
+  c->have &= ~HAVE_GRADIENT;
   return EPOCH_OK;
 }
 
@@ -945,6 +946,7 @@ epoch_status epoch_gradient(epoch_ctx *c, double *d_heights, double *d_boundarie
   s = enqueue_gradient(c);
   if (s != EPOCH_OK) return s;
   CK(join_sides(c), "join");
+  c->have |= HAVE_GRADIENT;
   return copy_grad_out(c, d_heights, d_boundaries, d_params, d_branch_rates);
 }
 
@@ -956,7 +958,7 @@ epoch_status epoch_set_heights_device(epoch_ctx *c, const double *d_heights) {
                      c->stream),
      "cudaMemcpyAsync(heights)");
   CK(launch_check_heights(c), "height check kernel");
-  c->have &= ~(HAVE_BRANCH | HAVE_PARTIALS);
+  c->have &= ~(HAVE_BRANCH | HAVE_PARTIALS | HAVE_GRADIENT);
   return EPOCH_OK;
 }
 
@@ -984,6 +986,37 @@ epoch_status epoch_get_branch_matrix(epoch_ctx *c, int node, int category, doubl
   CK(cudaMemcpyAsync(out, c->d_P64 + ((size_t)node * c->d.C + category) * c->d.KK,
                      sizeof(double) * c->d.KK, cudaMemcpyDeviceToHost, c->stream),
      "cudaMemcpyAsync(branch matrix)");
+  return read_status(c);
+}
+
+epoch_status epoch_expected_counts(epoch_ctx *c, double *per_branch, double *per_epoch) {
+  if (!c) return EPOCH_ERR_ARG;
+  epoch_status s = need(c, HAVE_GRADIENT, "expected_counts");
+  if (s != EPOCH_OK) return s;
+  if (!c->d.reversible)
+    return fail(c, EPOCH_ERR_UNSUPPORTED, "expected counts need reversible=1");
+  const Dims &d = c->d;
+  if (!c->d_jumps) {
+    const size_t nn_max = (size_t)(2 * c->max_taxa - 1);
+    if (dalloc(&c->d_jumps, nn_max * d.E * d.C * d.KK) != cudaSuccess ||
+        dalloc(&c->d_jump_out, (nn_max + d.E) * d.KK) != cudaSuccess) {
+      cudaGetLastError();
+      dfree(c->d_jumps);
+      dfree(c->d_jump_out);
+      c->d_jumps = c->d_jump_out = nullptr;
+      return fail(c, EPOCH_ERR_CAPACITY, "cannot allocate the expected-count buffers");
+    }
+  }
+  double *d_branch = c->d_jump_out, *d_epoch = c->d_jump_out + (size_t)d.nn * d.KK;
+  CK(launch_expected_counts(c, d_branch, d_epoch), "expected-count kernels");
+  if (per_branch)
+    CK(cudaMemcpyAsync(per_branch, d_branch, sizeof(double) * d.nn * d.KK, cudaMemcpyDeviceToHost,
+                       c->stream),
+       "cudaMemcpyAsync(counts per branch)");
+  if (per_epoch)
+    CK(cudaMemcpyAsync(per_epoch, d_epoch, sizeof(double) * d.E * d.KK, cudaMemcpyDeviceToHost,
+                       c->stream),
+       "cudaMemcpyAsync(counts per epoch)");
   return read_status(c);
 }
 
@@ -1022,6 +1055,10 @@ epoch_status epoch_evaluate_async(epoch_ctx *c, int with_gradient) {
   CK(cudaGraphLaunch(c->graph_exec[g], c->stream), "cudaGraphLaunch");
   c->launches += c->graph_kernels[g];
   c->have |= HAVE_BRANCH | HAVE_PARTIALS;
+  if (g)
+    c->have |= HAVE_GRADIENT;
+  else
+    c->have &= ~HAVE_GRADIENT;
   return EPOCH_OK;
 }
 

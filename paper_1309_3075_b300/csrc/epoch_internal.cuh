@@ -27,7 +27,8 @@ constexpr int kTile = 256;       // patterns per CTA in the streaming kernels
 // What has been set on the context (for EPOCH_ERR_ORDER).
 enum : unsigned {
   HAVE_RATES = 1u, HAVE_CATS = 2u, HAVE_TREE = 4u, HAVE_TIPS = 8u,
-  HAVE_BRANCH = 16u, HAVE_PARTIALS = 32u
+  HAVE_BRANCH = 16u, HAVE_PARTIALS = 32u,
+  HAVE_GRADIENT = 64u  // G of the current inputs (expected counts need it)
 };
 
 // Device views handed to kernels (plain pointers and sizes).
@@ -130,6 +131,8 @@ struct epoch_ctx {
   double *d_G = nullptr;              // [nn][C][K][K]
   void *d_gseg = nullptr;             // [nn][E][C][1+np]  (T)
   double *d_grad = nullptr;           // [nn (heights) + (E-1) + np + nn (rates)]
+  double *d_jumps = nullptr;          // [nn][E][C][K][K] expected counts per segment
+  double *d_jump_out = nullptr;       // [nn + E][K][K] per-branch | per-epoch sums
   int *d_status = nullptr;            // [1]
   int *d_ctl = nullptr;               // [8] block counters of last-block reductions
   double *d_site_log = nullptr;       // [P] log of the scaled root sum
@@ -191,6 +194,7 @@ cudaError_t launch_root(epoch_ctx *c);
 // k_adjoint.cu
 cudaError_t launch_adjoint(epoch_ctx *c);
 cudaError_t launch_chain_rule(epoch_ctx *c);
+cudaError_t launch_expected_counts(epoch_ctx *c, double *d_per_branch, double *d_per_epoch);
 // k_k4.cu (FP32, K = 4)
 int k4_tiles(int P);                            // pattern tiles of the K = 4 kernels
 cudaError_t launch_pair_tables_k4(epoch_ctx *c); // cherries' code-pair tables

@@ -404,6 +404,136 @@ __global__ void k_grad_branch(Dims d, const double *__restrict__ G, const int *_
   }
 }
 
+// Expected transition counts of every segment (FP64, reversible models), one
+// CTA per (branch v, category c).  For segment k (parent end first), with A /
+// Z the products of the segment exponentials above / below it,
+//   H = A^T G Z^T,  Hhat = V^T H V^-T,  M = V^-T (Hhat o Phi) V^T,
+//   N_ij = q_ij M_ij  (i != j; 0 on the diagonal),
+// i.e. q_ij <H, dE/dq_ij> with dE/dq_ij = V ((V^-1 e_i e_j^T V) o Phi) V^-1
+// (Daleckii-Krein, Phi as in the parameter terms of k_grad_branch).
+// out[v][k][c][K][K].
+__global__ void k_jump_counts(Dims d, const double *__restrict__ G, const int *__restrict__ nseg,
+                              const int *__restrict__ seg_mat, const double *__restrict__ seg_dt,
+                              const double *__restrict__ brate, const double *__restrict__ catr,
+                              const double *__restrict__ lam, const double *__restrict__ V,
+                              const double *__restrict__ Vinv, const double *__restrict__ Qn,
+                              double *__restrict__ out) {
+  extern __shared__ unsigned char smraw[];
+  double *sm = reinterpret_cast<double *>(smraw);
+  const int v = blockIdx.x, c = blockIdx.y;
+  const int ns = nseg[v];
+  if (ns == 0) return;
+  const int K = d.K, KK = d.KK;
+  double *A = sm, *Z = A + KK, *H = Z + KK, *E = H + KK, *W = E + KK, *Y = W + KK, *ev = Y + KK;
+  const double r = brate[v] * catr[c];
+  const double *Gm = G + ((size_t)v * d.C + c) * KK;
+  for (int idx = threadIdx.x; idx < KK; idx += blockDim.x) A[idx] = (idx / K == idx % K) ? 1.0 : 0.0;
+  __syncthreads();
+  for (int k = 0; k < ns; k++) {
+    const int s = seg_mat[v * d.E + k];
+    const double tau = r * seg_dt[v * d.E + k];
+    // Z = E_{k+1} ... E_{ns-1}
+    for (int idx = threadIdx.x; idx < KK; idx += blockDim.x) Z[idx] = (idx / K == idx % K) ? 1.0 : 0.0;
+    __syncthreads();
+    for (int q = k + 1; q < ns; q++) {
+      seg_exp<double>(d, seg_mat[v * d.E + q], r * seg_dt[v * d.E + q], lam, V, Vinv, Qn, E, W, Y,
+                      W, ev);
+      mm<double>(d, Z, E, W, false, false);
+      __syncthreads();
+      for (int idx = threadIdx.x; idx < KK; idx += blockDim.x) Z[idx] = W[idx];
+      __syncthreads();
+    }
+    mm<double>(d, A, Gm, W, true, false);  // W = A^T G
+    __syncthreads();
+    mm<double>(d, W, Z, H, false, true);   // H = A^T G Z^T
+    __syncthreads();
+    const double *Vs = V + (size_t)s * KK, *Vi = Vinv + (size_t)s * KK;
+    for (int idx = threadIdx.x; idx < KK; idx += blockDim.x) {  // Y = H V^-T
+      const int i = idx / K, j = idx % K;
+      double acc = 0.0;
+      for (int m = 0; m < K; m++) acc += H[i * K + m] * Vi[j * K + m];
+      Y[idx] = acc;
+    }
+    __syncthreads();
+    for (int idx = threadIdx.x; idx < KK; idx += blockDim.x) {  // W = V^T Y = Hhat
+      const int i = idx / K, j = idx % K;
+      double acc = 0.0;
+      for (int m = 0; m < K; m++) acc += Vs[m * K + i] * Y[m * K + j];
+      W[idx] = acc;
+    }
+    for (int i = threadIdx.x; i < K; i += blockDim.x) ev[i] = exp(tau * lam[(size_t)s * K + i]);
+    __syncthreads();
+    for (int idx = threadIdx.x; idx < KK; idx += blockDim.x) {  // W <- Hhat o Phi
+      const int i = idx / K, j = idx % K;
+      const double xx = tau * (lam[(size_t)s * K + i] - lam[(size_t)s * K + j]);
+      W[idx] *= (xx == 0.0) ? tau * ev[j] : ev[j] * tau * (expm1(xx) / xx);
+    }
+    __syncthreads();
+    for (int idx = threadIdx.x; idx < KK; idx += blockDim.x) {  // Y = W V^T
+      const int i = idx / K, j = idx % K;
+      double acc = 0.0;
+      for (int m = 0; m < K; m++) acc += W[i * K + m] * Vs[j * K + m];
+      Y[idx] = acc;
+    }
+    __syncthreads();
+    const double *Qs = Qn + (size_t)s * KK;
+    double *o = out + (((size_t)v * d.E + k) * d.C + c) * KK;
+    for (int idx = threadIdx.x; idx < KK; idx += blockDim.x) {  // M = V^-T Y; N = Q o M
+      const int i = idx / K, j = idx % K;
+      double acc = 0.0;
+      for (int m = 0; m < K; m++) acc += Vi[m * K + i] * Y[m * K + j];
+      o[idx] = (i != j) ? Qs[idx] * acc : 0.0;
+    }
+    __syncthreads();
+    if (k + 1 < ns) {  // A <- A E_k
+      seg_exp<double>(d, s, tau, lam, V, Vinv, Qn, E, W, Y, W, ev);
+      mm<double>(d, A, E, W, false, false);
+      __syncthreads();
+      for (int idx = threadIdx.x; idx < KK; idx += blockDim.x) A[idx] = W[idx];
+      __syncthreads();
+    }
+  }
+}
+
+// Sums of the segment counts in a fixed order: threads [0, nn*KK) per branch
+// (over segments and categories), then [nn*KK, (nn+E)*KK) per epoch (over
+// every segment lying in the epoch: above boundary j it is epoch j+1, the
+// bottom segment is in the epoch of its child's height).
+__global__ void k_jump_reduce(Dims d, const int *__restrict__ parent, const int *__restrict__ nseg,
+                              const int *__restrict__ seg_lo, const double *__restrict__ heights,
+                              const double *__restrict__ b, const double *__restrict__ jumps,
+                              double *__restrict__ per_branch, double *__restrict__ per_epoch) {
+  long long idx = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+  const long long nb = (long long)d.nn * d.KK;
+  auto seg_sum = [&](int v, int k, int ij) {
+    double acc = 0.0;
+    for (int c = 0; c < d.C; c++) acc += jumps[(((size_t)v * d.E + k) * d.C + c) * d.KK + ij];
+    return acc;
+  };
+  if (idx < nb) {
+    const int v = (int)(idx / d.KK), ij = (int)(idx % d.KK);
+    double acc = 0.0;
+    if (parent[v] >= 0)
+      for (int k = 0; k < nseg[v]; k++) acc += seg_sum(v, k, ij);
+    per_branch[idx] = acc;
+    return;
+  }
+  idx -= nb;
+  if (idx >= (long long)d.E * d.KK) return;
+  const int e = (int)(idx / d.KK), ij = (int)(idx % d.KK);
+  double acc = 0.0;
+  for (int v = 0; v < d.nn; v++) {
+    if (parent[v] < 0) continue;
+    int eb = 0;
+    for (int j = 0; j < d.E - 1; j++) eb += (b[j] <= heights[v]);
+    for (int k = 0; k < nseg[v]; k++) {
+      const int lo = seg_lo[v * d.E + k];
+      if ((lo < 0 ? -lo : eb) == e) acc += seg_sum(v, k, ij);
+    }
+  }
+  per_epoch[idx] = acc;
+}
+
 // Final reductions into FP64 outputs (fixed order, deterministic):
 //   blocks [0, nb_nodes): node heights and branch rates (thread per node);
 //   next E-1 blocks: boundary j;  next np blocks: parameter a.
@@ -665,6 +795,22 @@ void launch_pre_generic(epoch_ctx *c, BranchTable<T> bt, int root) {
 }
 
 }  // namespace
+
+cudaError_t launch_expected_counts(epoch_ctx *c, double *d_per_branch, double *d_per_epoch) {
+  const Dims &d = c->d;
+  const int threads = d.KK >= 1024 ? 256 : (d.KK >= 256 ? 128 : 32);
+  const size_t smem = sizeof(double) * (6 * d.KK + d.K);
+  cudaFuncSetAttribute(k_jump_counts, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+  k_jump_counts<<<dim3(d.nn, d.C), threads, smem, c->stream>>>(
+      d, c->d_G, c->d_nseg, c->d_seg_mat, c->d_seg_dt, c->d_brate, c->d_catr, c->d_lam, c->d_V,
+      c->d_Vinv, c->d_Q, c->d_jumps);
+  const long long n = (long long)(d.nn + d.E) * d.KK;
+  k_jump_reduce<<<ceil_div(n, 256), 256, 0, c->stream>>>(d, c->d_parent, c->d_nseg, c->d_seg_lo,
+                                                         c->d_heights, c->d_boundaries,
+                                                         c->d_jumps, d_per_branch, d_per_epoch);
+  c->launches += 2;
+  return cudaGetLastError();
+}
 
 cudaError_t launch_adjoint(epoch_ctx *c) {
   const Dims &d = c->d;

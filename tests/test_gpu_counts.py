@@ -1,0 +1,89 @@
+"""Expected transition counts (Markov jumps) through the C ABI against the
+FP64 oracle: per branch and per epoch, on the FP64 path and on the FP32
+paths (K = 4 level kernels, the few-pattern kernels at K = 7, the
+tensor-core kernels at K = 61), which differ only in how G is formed.
+
+Tolerances: 1e-9 (FP64 path) and 1e-4 (FP32 paths) relative to the largest
+count, the bounds of the gradient tests (the counts are contractions of the
+same G)."""
+import numpy as np
+import pytest
+
+import oracle
+import synth
+from paper_1309_3075_b300 import binding
+from paper_1309_3075_b300.binding import (EPOCH_FP32, EPOCH_FP32_TC, EPOCH_FP64, EpochError,
+                                          EpochLikelihood)
+
+pytestmark = pytest.mark.gpu
+
+TOL = {EPOCH_FP64: 1e-9, EPOCH_FP32: 1e-4, EPOCH_FP32_TC: 1e-4}
+
+
+@pytest.fixture(scope="module", autouse=True)
+def _built():
+    from paper_1309_3075_b300 import build
+
+    build.build()
+
+
+def check_counts(w, prec):
+    lik = EpochLikelihood(w, precision=prec)
+    try:
+        lik.evaluate(with_gradient=True)
+        pb, pe = lik.expected_counts()
+    finally:
+        lik.close()
+    rb, re = oracle.expected_counts(w)
+    scale = max(np.abs(rb).max(), 1e-300)
+    assert np.abs(pb - rb).max() <= TOL[prec] * scale, (w.name, np.abs(pb - rb).max(), scale)
+    assert np.abs(pe - re).max() <= TOL[prec] * max(np.abs(re).max(), 1e-300)
+    return pb, pe
+
+
+@pytest.mark.parametrize("prec", [EPOCH_FP64, EPOCH_FP32])
+def test_counts_nucleotide_dated_rates(prec):
+    w = synth.small_nucleotide(411, n_taxa=24, n_sites=150, n_cat=3, n_epochs=3, dated=True)
+    w = w.replace(branch_rates=np.random.default_rng(4).uniform(0.6, 1.4, 2 * w.n_taxa - 1))
+    check_counts(w, prec)
+
+
+@pytest.mark.parametrize("prec", [EPOCH_FP64, EPOCH_FP32])
+def test_counts_seasonal_trait(prec):
+    """One location trait, 13 alternating epochs: the per-epoch counts are
+    the paper's per-season summaries of location changes."""
+    w = synth.flu_seasonal(seed=1319, n_taxa=60)
+    pb, pe = check_counts(w, prec)
+    assert pe.shape == (13, 7, 7)
+
+
+def test_counts_codon_tensor_cores():
+    w = synth.small_codon(412, n_taxa=10, n_sites=60, n_cat=2, n_epochs=2)
+    check_counts(w, EPOCH_FP32_TC)
+
+
+def test_counts_need_a_gradient_and_a_reversible_model():
+    w = synth.tiny_tree_workload(413, K=4, n_taxa=6, n_sites=5, n_epochs=2)
+    lik = EpochLikelihood(w, precision=EPOCH_FP64)
+    try:
+        lik.log_likelihood()
+        with pytest.raises(EpochError) as e:
+            lik.expected_counts()
+        assert e.value.status == 2  # EPOCH_ERR_ORDER: no gradient of these inputs yet
+        lik.evaluate(with_gradient=True)
+        lik.expected_counts()
+        binding.epoch_set_heights(lik.ctx, w.heights)  # new inputs: stale G
+        with pytest.raises(EpochError) as e:
+            lik.expected_counts()
+        assert e.value.status == 2
+    finally:
+        lik.close()
+    wa = synth.tiny_tree_workload(414, K=5, n_taxa=6, n_sites=5, n_epochs=2, reversible=False)
+    lik = EpochLikelihood(wa, precision=EPOCH_FP64)
+    try:
+        lik.evaluate(with_gradient=True)
+        with pytest.raises(EpochError) as e:
+            lik.expected_counts()
+        assert e.value.status == 7  # EPOCH_ERR_UNSUPPORTED
+    finally:
+        lik.close()

@@ -476,3 +476,35 @@ def test_many_epochs_one_process_is_homogeneous(oracle_lib):
     w2 = synth.flu_seasonal(seed=21, n_taxa=40, n_processes=2, n_traits=5)
     g2 = oracle_lib.gradient(w2.replace(dQ=None))
     assert np.abs(g2["boundaries"]).max() > 1e-3
+
+
+def test_expected_counts_are_rate_derivatives(oracle_lib):
+    """Markov jump counts: with raw (unnormalised) matrices, the count of
+    i -> j jumps in epoch e equals q_ij d lnL / d (Q_e)_ij with the diagonal
+    held fixed (the jump factors of a path's density), checked by central
+    differences of lnL; the per-branch and per-epoch sums agree and no
+    count is negative."""
+    w = synth.tiny_tree_workload(61, K=4, n_taxa=6, n_sites=7, n_epochs=3, n_cat=2,
+                                 reversible=True, dated=True)
+    w = w.replace(branch_rates=np.random.default_rng(5).uniform(0.7, 1.3, 2 * w.n_taxa - 1))
+    per_branch, per_epoch = oracle_lib.expected_counts(w)
+    assert np.allclose(per_branch.sum(0), per_epoch.sum(0), rtol=1e-12)
+    assert per_branch.min() >= 0.0 and per_epoch.min() >= 0.0
+    assert np.all(np.diagonal(per_branch, axis1=1, axis2=2) == 0.0)
+    w0 = w.replace(normalise=0, reversible=0)
+    _, pe0 = oracle_lib.expected_counts(w0)
+    lnl = lambda ww: oracle_lib.log_likelihood(ww)[0]
+    h = 1e-6
+    for e in range(w.n_epochs):
+        for i, j in [(0, 1), (1, 0), (2, 3), (3, 1)]:
+            Qp, Qm = w0.Q.copy(), w0.Q.copy()
+            Qp[e, i, j] += h
+            Qm[e, i, j] -= h
+            fd = (lnl(w0.replace(Q=Qp)) - lnl(w0.replace(Q=Qm))) / (2 * h)
+            assert abs(w0.Q[e, i, j] * fd - pe0[e, i, j]) <= 1e-7 * max(1.0, pe0[e, i, j]), (e, i, j)
+    # the counts do not depend on how Q is scaled: the normalised model with
+    # the same effective rates gives the same counts
+    pb_n, _ = oracle_lib.expected_counts(w.replace(normalise=1))
+    Qn = np.stack([oracle_lib.normalise(w.Q[s], w.pi)[0] for s in range(w.n_matrices)])
+    pb_raw, _ = oracle_lib.expected_counts(w.replace(Q=Qn, normalise=0))
+    assert np.allclose(pb_n, pb_raw, rtol=1e-10, atol=1e-12)
