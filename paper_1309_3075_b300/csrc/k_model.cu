@@ -164,6 +164,7 @@ __device__ __forceinline__ double jacobi_sweeps(T *A, T *U, int Kr, double tol2,
     off = block_sum(part, red);
     if (off <= tol2 || sweep == max_sweeps || (sweep > 0 && off > 0.5 * prev)) break;
     prev = off;
+    const int nw = nt >> 5, w = tid >> 5, lane = tid & 31;
     for (int round = 0; round < n - 1; round++) {
       for (int k = tid; k < npair; k += nt) {
         // round-robin position after `round` shifts: element 0 stays, the
@@ -183,23 +184,30 @@ __device__ __forceinline__ double jacobi_sweeps(T *A, T *U, int Kr, double tol2,
         pq[2 * k + 1] = q;
       }
       __syncthreads();
-      for (int idx = tid; idx < npair * K; idx += nt) {  // rows: B = J^T A
-        const int k = idx / K, col = idx % K, p = pq[2 * k], q = pq[2 * k + 1];
-        if (q >= K || sn[k] == T(0)) continue;
-        const T ap = A[p * K + col], aq = A[q * K + col];
-        A[p * K + col] = cs[k] * ap - sn[k] * aq;
-        A[q * K + col] = sn[k] * ap + cs[k] * aq;
+      // a warp per pair (warp-uniform skip), lanes along the row or column
+      for (int k = w; k < npair; k += nw) {  // rows: B = J^T A
+        const int p = pq[2 * k], q = pq[2 * k + 1];
+        const T ck = cs[k], sk = sn[k];
+        if (q >= K || sk == T(0)) continue;
+        for (int col = lane; col < K; col += 32) {
+          const T ap = A[p * K + col], aq = A[q * K + col];
+          A[p * K + col] = ck * ap - sk * aq;
+          A[q * K + col] = sk * ap + ck * aq;
+        }
       }
       __syncthreads();
-      for (int idx = tid; idx < npair * K; idx += nt) {  // columns: A' = B J, U' = U J
-        const int k = idx / K, row = idx % K, p = pq[2 * k], q = pq[2 * k + 1];
-        if (q >= K || sn[k] == T(0)) continue;
-        const T ap = A[row * K + p], aq = A[row * K + q];
-        A[row * K + p] = cs[k] * ap - sn[k] * aq;
-        A[row * K + q] = sn[k] * ap + cs[k] * aq;
-        const T up = U[row * K + p], uq = U[row * K + q];
-        U[row * K + p] = cs[k] * up - sn[k] * uq;
-        U[row * K + q] = sn[k] * up + cs[k] * uq;
+      for (int k = w; k < npair; k += nw) {  // columns: A' = B J, U' = U J
+        const int p = pq[2 * k], q = pq[2 * k + 1];
+        const T ck = cs[k], sk = sn[k];
+        if (q >= K || sk == T(0)) continue;
+        for (int row = lane; row < K; row += 32) {
+          const T ap = A[row * K + p], aq = A[row * K + q];
+          A[row * K + p] = ck * ap - sk * aq;
+          A[row * K + q] = sk * ap + ck * aq;
+          const T up = U[row * K + p], uq = U[row * K + q];
+          U[row * K + p] = ck * up - sk * uq;
+          U[row * K + q] = sk * up + ck * uq;
+        }
       }
       __syncthreads();
       for (int k = tid; k < npair; k += nt) {  // the annihilated pair
@@ -293,8 +301,11 @@ __device__ __forceinline__ void mm_shared(const double *X, const double *Y, doub
   __syncthreads();
 }
 
-template <int KT>  // KT: K known at compile time (0 = take d.K)
-__global__ void k_model_setup(Dims d, int normalise, const double *__restrict__ Qraw,
+// KT: K known at compile time (0 = take d.K).  RJ: FP32 rotations in one
+// thread's registers for K <= RJ (4 or 8; one warp per matrix), or 0: shared-
+// memory sweeps by a 512-thread CTA.
+template <int KT, int RJ>
+__global__ void __launch_bounds__(RJ ? 32 : 512) k_model_setup(Dims d, int normalise, const double *__restrict__ Qraw,
                               const double *__restrict__ pi, double *__restrict__ Qn,
                               double *__restrict__ cnorm, double *__restrict__ lam,
                               double *__restrict__ V, double *__restrict__ Vinv,
@@ -347,19 +358,13 @@ __global__ void k_model_setup(Dims d, int normalise, const double *__restrict__ 
     part += A[idx] * A[idx];
   }
   const double fro2 = block_sum(part, red);
-  // 1. FP32 rotations (K <= 8: one thread, the matrix in registers)
-  if constexpr (KT == 4) {
+  // 1. FP32 rotations (K <= RJ: one thread, the matrix in registers)
+  if constexpr (RJ > 0) {
     __syncthreads();
-    if (tid == 0) jacobi_registers<4>(A32, U32, 4, (float)(1e-12 * fro2));
+    if (tid == 0) jacobi_registers<RJ>(A32, U32, K, (float)(1e-12 * fro2));
     __syncthreads();
   } else {
-    if (K <= 8) {
-      __syncthreads();
-      if (tid == 0) jacobi_registers<8>(A32, U32, K, (float)(1e-12 * fro2));
-      __syncthreads();
-    } else {
-      jacobi_sweeps<float, KT>(A32, U32, K, 1e-12 * fro2, 40, red, cs32, sn32, pq);
-    }
+    jacobi_sweeps<float, KT>(A32, U32, K, 1e-12 * fro2, 40, red, cs32, sn32, pq);
   }
   // 2. orthogonal U in FP64
   for (int idx = tid; idx < KK; idx += nt) U[idx] = (double)U32[idx];
@@ -606,9 +611,9 @@ cudaError_t launch_check_heights(epoch_ctx *c) {
 cudaError_t launch_model_setup(epoch_ctx *c) {
   const Dims &d = c->d;
   size_t smem = setup_smem(d);
-  // small K: one warp per matrix (its barriers are cheap); large K: 8 warps
-  const int threads = d.K <= 8 ? 32 : 256;
-  auto kern = d.K == 4 ? k_model_setup<4> : k_model_setup<0>;
+  // small K: one warp per matrix, rotations in registers; large K: 16 warps
+  const int threads = d.K <= 8 ? 32 : 512;
+  auto kern = d.K == 4 ? k_model_setup<4, 4> : (d.K <= 8 ? k_model_setup<0, 8> : k_model_setup<0, 0>);
   cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
   kern<<<d.S, threads, smem, c->stream>>>(d, c->normalise, c->d_Qraw, c->d_pi, c->d_Q, c->d_cnorm,
                                           c->d_lam, c->d_V, c->d_Vinv, c->d_status);
