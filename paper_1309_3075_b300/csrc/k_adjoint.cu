@@ -317,21 +317,17 @@ __global__ void k_grad_branch(Dims d, const double *__restrict__ G, const int *_
     seg_exp<T>(d, s, tau, lam, V, Vinv, Qn, E, W, Y, Bm, ev);
     T dk;
     if (d.reversible) {
-      // Hhat = V^T H V^-T  into W
+      // Hhat = V^T H V^-T  into W, with V^-1 and then V of this segment's
+      // matrix staged in Bm (free on the eigen path) for the shared-memory
+      // products
       const double *Vs = V + (size_t)s * KK, *Vi = Vinv + (size_t)s * KK;
-      for (int idx = threadIdx.x; idx < KK; idx += blockDim.x) {  // Y = H V^-T
-        const int i = idx / K, j = idx % K;
-        T acc = 0;
-        for (int m = 0; m < K; m++) acc += H[i * K + m] * (T)Vi[j * K + m];
-        Y[idx] = acc;
-      }
+      for (int idx = threadIdx.x; idx < KK; idx += blockDim.x) Bm[idx] = (T)Vi[idx];
       __syncthreads();
-      for (int idx = threadIdx.x; idx < KK; idx += blockDim.x) {  // W = V^T Y
-        const int i = idx / K, j = idx % K;
-        T acc = 0;
-        for (int m = 0; m < K; m++) acc += (T)Vs[m * K + i] * Y[m * K + j];
-        W[idx] = acc;
-      }
+      mm<T>(d, H, Bm, Y, false, true);  // Y = H V^-T
+      __syncthreads();
+      for (int idx = threadIdx.x; idx < KK; idx += blockDim.x) Bm[idx] = (T)Vs[idx];
+      __syncthreads();
+      mm<T>(d, Bm, Y, W, true, false);  // W = V^T Y
       for (int i = threadIdx.x; i < K; i += blockDim.x)
         ev[i] = (T)exp(tau * lam[(size_t)s * K + i]);
       __syncthreads();
