@@ -161,9 +161,14 @@ def partials_bytes(w):
     """Bytes the partials pass (pruning, rescaling, root log-sum) must move in
     this design: every stored partial written once and read once by its
     parent, one-byte tip codes, int16 exponents written and summed, the root's
-    per-pattern outputs.  Cherries (non-root nodes whose children are both
-    tips) are not stored; their parents read the two tip codes instead."""
+    per-pattern outputs.  At K = 4, cherries (non-root nodes whose children
+    are both tips) are not stored; their parents read the two tip codes
+    instead.  Other K store every internal node (rows of 4 * Kp bytes)."""
     N, P, C = w.n_taxa, w.n_patterns, w.n_categories
+    if w.K != 4:
+        kp = 64 if w.K > 32 else (w.K + 3) // 4 * 4
+        vec = 4 * kp * C * P
+        return (N - 1) * (2 * vec + 4 * P) + N * P + 40 * P
     nn = 2 * N - 1
     parent = np.asarray(w.parent)
     kids = [[] for _ in range(nn)]
