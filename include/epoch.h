@@ -217,6 +217,17 @@ epoch_status epoch_gradient(epoch_ctx *ctx, double *d_heights,
  * (EPOCH_ERR_CAPACITY if that fails). */
 epoch_status epoch_expected_counts(epoch_ctx *ctx, double *per_branch, double *per_epoch);
 
+/* Marginal posterior probability of the state of every internal node given
+ * each pattern, for the inputs of the last gradient evaluation
+ * (EPOCH_ERR_ORDER otherwise).  Not in the paper: with L_u the post-order
+ * partials (Eq. partial_likelihood) and U_u the outside partials of the
+ * adjoint pass, Pr(x_u = i | data_p) = sum_c U_u(c,p,i) L_u(c,p,i) / (its
+ * sum over i), the root's U being w_c pi_i.  Any model and precision.
+ *   out [N-1][P][K]  host, caller-owned, FP64; row u - N is internal node u.
+ * Synchronises.  Allocates an [N-1][P][K] FP64 device buffer on first use
+ * (EPOCH_ERR_CAPACITY if that fails). */
+epoch_status epoch_ancestral_states(epoch_ctx *ctx, double *out);
+
 /* Test hook: P_{node,cat} [K][K] of the last epoch_compute_branch_matrices. */
 epoch_status epoch_get_branch_matrix(epoch_ctx *ctx, int node, int category,
                                      double *out);

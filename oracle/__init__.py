@@ -95,6 +95,10 @@ def _load():
         _lib.or_gradient.argtypes = [pp, dp, dp, dp, dp, dp]
         _lib.or_expected_counts.restype = C.c_int
         _lib.or_expected_counts.argtypes = [pp, dp, dp]
+        _lib.or_ancestral.restype = C.c_int
+        _lib.or_ancestral.argtypes = [pp, dp]
+        _lib.or_ancestral_brute.restype = C.c_int
+        _lib.or_ancestral_brute.argtypes = [pp, dp]
     return _lib
 
 
@@ -261,6 +265,21 @@ def expected_counts(w, scaling=True):
     if rc != 0:
         raise RuntimeError(f"oracle expected_counts failed ({rc})")
     return per_branch, per_epoch
+
+
+def ancestral_states(w, brute=False):
+    """Marginal posterior of every internal node's state given each pattern,
+    [N-1][P][K] (internal nodes N..2N-2 in order): outside x inside
+    probabilities summed over categories and normalised; ``brute=True``
+    enumerates every joint assignment instead (small trees only)."""
+    lib = _load()
+    pk = _Packed(w, True)
+    out = np.zeros((pk.N - 1, pk.P, pk.K))
+    fn = lib.or_ancestral_brute if brute else lib.or_ancestral
+    rc = fn(C.byref(pk.pr), out.ctypes.data_as(C.POINTER(C.c_double)))
+    if rc != 0:
+        raise RuntimeError(f"oracle ancestral states failed ({rc})")
+    return out
 
 
 def normalise(Q, pi):

@@ -1000,6 +1000,144 @@ int or_expected_counts(const or_problem *pr, double *per_branch, double *per_epo
   return 0;
 }
 
+/* ------------------------------------------------------------------ */
+/* Marginal posterior of the state of every internal node u given one   */
+/* pattern: Pr(x_u = i | data_p) = sum_c w_c O_u(c,i) L_u(c,i) / site_p */
+/* with L the post-order partials (Eq. partial_likelihood) and O the    */
+/* outside probabilities: O_root(c,i) = pi_i; for a child v of u,       */
+/*   O_v(c,j) = sum_i O_u(c,i) (prod_{siblings w} S_w(c,i)) P_v,c[i][j] */
+/* (S_w = P_w L_w).  Every vector may carry its own positive factor:    */
+/* the posterior is normalised at the end, so L and O are rescaled by   */
+/* their maxima.  out[u - N][p][i].                                    */
+/* ------------------------------------------------------------------ */
+int or_ancestral(const or_problem *pr, double *out) {
+  prep_t m;
+  if (prep_init(&m, pr) != 0) {
+    prep_free(&m);
+    return -1;
+  }
+  int K = pr->K, C = pr->n_categories, nn = m.nn, N = pr->n_taxa, P = pr->n_patterns;
+  double *Pm = all_branch_matrices(&m);
+  double *L = (double *)malloc(sizeof(double) * nn * C * K);
+  double *O = (double *)malloc(sizeof(double) * nn * C * K);
+  double *ms = (double *)malloc(sizeof(double) * nn);
+  double *T = (double *)malloc(sizeof(double) * C * K);
+  for (int p = 0; p < P; p++) {
+    double ls;
+    pattern_forward(&m, Pm, p, L, ms, &ls);
+    /* outside pass, parents before children (reverse post-order) */
+    for (int c = 0; c < C; c++)
+      for (int i = 0; i < K; i++) O[((size_t)m.root * C + c) * K + i] = pr->cat_weights[c] * pr->pi[i];
+    for (int a = nn - 1; a >= 0; a--) {
+      int u = m.post[a];
+      if (u < N) continue;
+      int nc;
+      const int *ch = children_of(&m, u, &nc);
+      for (int k = 0; k < nc; k++) {
+        int v = ch[k];
+        for (int q = 0; q < C * K; q++) T[q] = O[(size_t)u * C * K + q];
+        for (int k2 = 0; k2 < nc; k2++) {
+          if (k2 == k) continue;
+          int w = ch[k2];
+          for (int c = 0; c < C; c++) {
+            const double *Pw = Pm + ((size_t)w * C + c) * K * K;
+            for (int i = 0; i < K; i++) {
+              double sw = 0.0;
+              for (int j = 0; j < K; j++) sw += Pw[i * K + j] * L[((size_t)w * C + c) * K + j];
+              T[c * K + i] *= sw;
+            }
+          }
+        }
+        double mx = 0.0;
+        for (int c = 0; c < C; c++) {
+          const double *Pv = Pm + ((size_t)v * C + c) * K * K;
+          for (int j = 0; j < K; j++) {
+            double o = 0.0;
+            for (int i = 0; i < K; i++) o += T[c * K + i] * Pv[i * K + j];
+            O[((size_t)v * C + c) * K + j] = o;
+            mx = fmax(mx, o);
+          }
+        }
+        if (mx > 0.0)
+          for (int q = 0; q < C * K; q++) O[(size_t)v * C * K + q] /= mx;
+      }
+    }
+    for (int u = N; u < nn; u++) {
+      double *o = out + ((size_t)(u - N) * P + p) * K;
+      double tot = 0.0;
+      for (int i = 0; i < K; i++) {
+        double x = 0.0;
+        for (int c = 0; c < C; c++) x += O[((size_t)u * C + c) * K + i] * L[((size_t)u * C + c) * K + i];
+        o[i] = x;
+        tot += x;
+      }
+      for (int i = 0; i < K; i++) o[i] = tot > 0.0 ? o[i] / tot : 0.0;
+    }
+  }
+  free(Pm);
+  free(L);
+  free(O);
+  free(ms);
+  free(T);
+  prep_free(&m);
+  return 0;
+}
+
+/* The same posteriors by enumeration of every joint assignment of the   */
+/* internal nodes' states (the brute-force joint of or_brute_force,      */
+/* accumulated per node and state).  Small trees only.                   */
+int or_ancestral_brute(const or_problem *pr, double *out) {
+  prep_t m;
+  if (prep_init(&m, pr) != 0) {
+    prep_free(&m);
+    return -1;
+  }
+  int K = pr->K, C = pr->n_categories, nn = m.nn, N = pr->n_taxa, Pn = pr->n_patterns;
+  double *P = all_branch_matrices(&m);
+  int *st = (int *)calloc(nn, sizeof(int));
+  for (int p = 0; p < Pn; p++) {
+    for (int u = N; u < nn; u++)
+      for (int i = 0; i < K; i++) out[((size_t)(u - N) * Pn + p) * K + i] = 0.0;
+    double site = 0.0;
+    for (int c = 0; c < C; c++) {
+      for (int u = 0; u < nn; u++) st[u] = 0;
+      for (;;) {
+        double term = pr->cat_weights[c] * pr->pi[st[m.root]];
+        for (int v = 0; v < nn; v++) {
+          int u = pr->parent[v];
+          if (u < 0) continue;
+          const double *Pv = P + ((size_t)v * C + c) * K * K;
+          if (v < N) {
+            int code = pr->tips[(size_t)v * Pn + p];
+            double f = 0.0;
+            for (int j = 0; j < K; j++)
+              if (tip_allows(pr, code, j)) f += Pv[st[u] * K + j];
+            term *= f;
+          } else {
+            term *= Pv[st[u] * K + st[v]];
+          }
+        }
+        site += term;
+        for (int u = N; u < nn; u++) out[((size_t)(u - N) * Pn + p) * K + st[u]] += term;
+        int u = N;
+        while (u < nn) {
+          st[u]++;
+          if (st[u] < K) break;
+          st[u] = 0;
+          u++;
+        }
+        if (u == nn) break;
+      }
+    }
+    for (int u = N; u < nn; u++)
+      for (int i = 0; i < K; i++) out[((size_t)(u - N) * Pn + p) * K + i] /= site;
+  }
+  free(st);
+  free(P);
+  prep_free(&m);
+  return 0;
+}
+
 /* exported eigen/exp helpers for the tests */
 int or_expm(int K, const double *Q, const double *pi, int reversible, double tau,
             double *P) {

@@ -56,6 +56,8 @@ int or_branch_adjoints(const or_problem *pr, double *G, double *lnl);
 int or_gradient(const or_problem *pr, double *lnl, double *d_heights,
                 double *d_boundaries, double *d_params, double *d_rates);
 int or_expected_counts(const or_problem *pr, double *per_branch, double *per_epoch);
+int or_ancestral(const or_problem *pr, double *out);
+int or_ancestral_brute(const or_problem *pr, double *out);
 
 #ifdef __cplusplus
 }

@@ -56,6 +56,7 @@ _SIGS = {
     "epoch_gradient": [_vp, _dp, _dp, _dp, _dp],
     "epoch_get_branch_matrix": [_vp, C.c_int, C.c_int, _dp],
     "epoch_expected_counts": [_vp, _dp, _dp],
+    "epoch_ancestral_states": [_vp, _dp],
     "epoch_evaluate_async": [_vp, C.c_int],
     "epoch_read_results": [_vp, _dp, _dp, _dp, _dp, _dp],
     "epoch_counters": [_vp, C.POINTER(C.c_longlong), C.POINTER(C.c_longlong)],
@@ -240,6 +241,14 @@ def epoch_expected_counts(ctx, n_nodes, n_epochs, K):
     return per_branch, per_epoch
 
 
+def epoch_ancestral_states(ctx, n_taxa, n_patterns, K):
+    """Posterior state probabilities of the internal nodes, [N-1][P][K]."""
+    out = np.zeros((n_taxa - 1, n_patterns, K))
+    _check(ctx, lib().epoch_ancestral_states(ctx, out.ctypes.data_as(_dp)),
+           "epoch_ancestral_states")
+    return out
+
+
 def epoch_get_branch_matrix(ctx, node, category, K):
     out = np.zeros((K, K))
     _check(ctx, lib().epoch_get_branch_matrix(ctx, int(node), int(category),
@@ -350,6 +359,11 @@ class EpochLikelihood:
         """(per_branch, per_epoch) expected i -> j transition counts of the
         last gradient evaluation."""
         return epoch_expected_counts(self.ctx, 2 * self.N - 1, self.E, self.K)
+
+    def ancestral_states(self):
+        """Posterior state probabilities of the internal nodes [N-1][P][K]
+        (the last gradient evaluation)."""
+        return epoch_ancestral_states(self.ctx, self.N, self.P, self.K)
 
     def evaluate(self, with_gradient=True):
         epoch_evaluate_async(self.ctx, with_gradient)

@@ -371,7 +371,7 @@ void epoch_destroy(epoch_ctx *c) {
                   c->d_site_inv,   c->d_lnl_part, c->d_lnl,     c->d_Gpart,      c->d_G,
                   c->d_gseg,       c->d_grad,    c->d_status,   c->d_ctl,        c->d_site_log,
                   c->d_level_off,  c->d_pairS,   c->d_pairL,    c->d_k4_walk,    c->d_k4_nt,
-                  c->d_tcB,        c->d_jumps,   c->d_jump_out};
+                  c->d_tcB,        c->d_jumps,   c->d_jump_out, c->d_anc};
   for (void *p : bufs) dfree(p);
   if (c->h_grad_pinned) cudaFreeHost(c->h_grad_pinned);
   if (c->h_lnl_pinned) cudaFreeHost(c->h_lnl_pinned);
@@ -1017,6 +1017,24 @@ epoch_status epoch_expected_counts(epoch_ctx *c, double *per_branch, double *per
     CK(cudaMemcpyAsync(per_epoch, d_epoch, sizeof(double) * d.E * d.KK, cudaMemcpyDeviceToHost,
                        c->stream),
        "cudaMemcpyAsync(counts per epoch)");
+  return read_status(c);
+}
+
+epoch_status epoch_ancestral_states(epoch_ctx *c, double *out) {
+  if (!c || !out) return EPOCH_ERR_ARG;
+  epoch_status s = need(c, HAVE_GRADIENT, "ancestral_states");
+  if (s != EPOCH_OK) return s;
+  const Dims &d = c->d;
+  if (!c->d_anc &&
+      dalloc(&c->d_anc, (size_t)(c->max_taxa - 1) * d.P * d.K) != cudaSuccess) {
+    cudaGetLastError();
+    c->d_anc = nullptr;
+    return fail(c, EPOCH_ERR_CAPACITY, "cannot allocate the ancestral-state buffer");
+  }
+  CK(launch_ancestral(c, c->d_anc), "ancestral-state kernel");
+  CK(cudaMemcpyAsync(out, c->d_anc, sizeof(double) * (d.N - 1) * d.P * d.K,
+                     cudaMemcpyDeviceToHost, c->stream),
+     "cudaMemcpyAsync(ancestral states)");
   return read_status(c);
 }
 

@@ -133,6 +133,7 @@ struct epoch_ctx {
   double *d_grad = nullptr;           // [nn (heights) + (E-1) + np + nn (rates)]
   double *d_jumps = nullptr;          // [nn][E][C][K][K] expected counts per segment
   double *d_jump_out = nullptr;       // [nn + E][K][K] per-branch | per-epoch sums
+  double *d_anc = nullptr;            // [N-1][P][K] ancestral-state posteriors
   int *d_status = nullptr;            // [1]
   int *d_ctl = nullptr;               // [8] block counters of last-block reductions
   double *d_site_log = nullptr;       // [P] log of the scaled root sum
@@ -195,6 +196,8 @@ cudaError_t launch_root(epoch_ctx *c);
 cudaError_t launch_adjoint(epoch_ctx *c);
 cudaError_t launch_chain_rule(epoch_ctx *c);
 cudaError_t launch_expected_counts(epoch_ctx *c, double *d_per_branch, double *d_per_epoch);
+// k_ancestral.cu
+cudaError_t launch_ancestral(epoch_ctx *c, double *d_out);  // [N-1][P][K]
 // k_k4.cu (FP32, K = 4)
 int k4_tiles(int P);                            // pattern tiles of the K = 4 kernels
 cudaError_t launch_pair_tables_k4(epoch_ctx *c); // cherries' code-pair tables

@@ -177,14 +177,14 @@ __global__ void k_small_lnl(int P, const double *__restrict__ pw,
 // Pre-order adjoint over all levels, top down, for the CTA's pattern: for
 // each child v of u (sibling w)
 //   X_v = U_u o S_w 2^{-e_u}   (U_root = w_c pi_i / site_p),
-//   U_v = P_v^T X_v            (kept in shared memory for internal v),
+//   U_v = P_v^T X_v            (internal v: kept in shared memory and stored),
 //   Gs[slot(u)][p][x][c][i][j] = n_p X_v(c,i) L_v(c,p,j)
 // (L_v of a tip is the indicator of its code).
 template <typename T>
 __global__ void __launch_bounds__(kSmallThreads)
     k_small_pre(Dims d, BranchTable<T> bt, const int *__restrict__ lvl_nodes,
                 const int *__restrict__ lvl_off, int L, const int *__restrict__ child, int root,
-                const T *__restrict__ part, const int16_t *__restrict__ scale,
+                const T *__restrict__ part, T *__restrict__ pre, const int16_t *__restrict__ scale,
                 const uint8_t *__restrict__ tips, const unsigned long long *__restrict__ masks,
                 const double *__restrict__ pi, const double *__restrict__ catw,
                 const double *__restrict__ site_inv, const double *__restrict__ pw, int gsz,
@@ -232,7 +232,10 @@ __global__ void __launch_bounds__(kSmallThreads)
         const T xk = __shfl_sync(0xffffffffu, X, c * d.Kp + k, gsz);
         if (inner && act) U += bt.mat(d, v, c, k, i) * xk;
       }
-      if (inner && holds) sm.pre[((size_t)(v - d.N) * d.C + c) * d.Kp + i] = U;
+      if (inner && holds) {  // read by the next level; kept for the ancestral states
+        sm.pre[((size_t)(v - d.N) * d.C + c) * d.Kp + i] = U;
+        pre[(((size_t)(v - d.N) * d.C + c) * d.P + p) * d.Kp + i] = U;
+      }
       if (node && act) {
         T *g = Gs + ((((size_t)slot * d.P + p) * 2 + x) * d.C + c) * d.KK + (size_t)i * d.K;
         if (v >= d.N) {
@@ -297,15 +300,15 @@ cudaError_t launch_small_pre(epoch_ctx *c) {
                          (int)smem);
     k_small_pre<double><<<d.P, kSmallThreads, smem, c->stream>>>(
         d, BranchTable<double>{c->d_P64, c->d_masks}, c->d_level_nodes, c->d_level_off, L,
-        c->d_child, root, (const double *)c->d_part, c->d_scale, c->d_tips, c->d_masks, c->d_pi,
-        c->d_catw, c->d_site_inv, c->d_pw, g, (double *)c->d_Gpart);
+        c->d_child, root, (const double *)c->d_part, (double *)c->d_pre, c->d_scale, c->d_tips,
+        c->d_masks, c->d_pi, c->d_catw, c->d_site_inv, c->d_pw, g, (double *)c->d_Gpart);
   } else {
     cudaFuncSetAttribute(k_small_pre<float>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                          (int)smem);
     k_small_pre<float><<<d.P, kSmallThreads, smem, c->stream>>>(
         d, BranchTable<float>{c->d_PT32, c->d_masks}, c->d_level_nodes, c->d_level_off, L,
-        c->d_child, root, (const float *)c->d_part, c->d_scale, c->d_tips, c->d_masks, c->d_pi,
-        c->d_catw, c->d_site_inv, c->d_pw, g, (float *)c->d_Gpart);
+        c->d_child, root, (const float *)c->d_part, (float *)c->d_pre, c->d_scale, c->d_tips,
+        c->d_masks, c->d_pi, c->d_catw, c->d_site_inv, c->d_pw, g, (float *)c->d_Gpart);
   }
   c->launches++;
   return cudaGetLastError();

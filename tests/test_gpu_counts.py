@@ -1,11 +1,13 @@
-"""Expected transition counts (Markov jumps) through the C ABI against the
-FP64 oracle: per branch and per epoch, on the FP64 path and on the FP32
-paths (K = 4 level kernels, the few-pattern kernels at K = 7, the
-tensor-core kernels at K = 61), which differ only in how G is formed.
+"""Outputs built on the adjoint pass, through the C ABI against the FP64
+oracle, on the FP64 path and on the FP32 paths (K = 4 level kernels, the
+few-pattern kernels at K = 7, generic kernels, the tensor-core kernels at
+K = 61):
 
-Tolerances: 1e-9 (FP64 path) and 1e-4 (FP32 paths) relative to the largest
-count, the bounds of the gradient tests (the counts are contractions of the
-same G)."""
+* expected transition counts (Markov jumps) per branch and per epoch;
+  tolerances 1e-9 (FP64) and 1e-4 (FP32) relative to the largest count, the
+  bounds of the gradient tests (the counts are contractions of the same G);
+* marginal posterior state probabilities of every internal node; absolute
+  tolerances 1e-10 (FP64) and 1e-5 (FP32) per probability."""
 import numpy as np
 import pytest
 
@@ -87,3 +89,32 @@ def test_counts_need_a_gradient_and_a_reversible_model():
         assert e.value.status == 7  # EPOCH_ERR_UNSUPPORTED
     finally:
         lik.close()
+
+
+ANC_TOL = {EPOCH_FP64: 1e-10, EPOCH_FP32: 1e-5, EPOCH_FP32_TC: 1e-5}
+
+
+@pytest.mark.parametrize("prec,make", [
+    (EPOCH_FP64, lambda: synth.small_nucleotide(421, n_taxa=20, n_sites=90, n_cat=2, n_epochs=3)),
+    (EPOCH_FP32, lambda: synth.small_nucleotide(421, n_taxa=20, n_sites=90, n_cat=2, n_epochs=3)),
+    (EPOCH_FP32, lambda: synth.flu_seasonal(seed=1320, n_taxa=50, n_traits=3)),
+    (EPOCH_FP32, lambda: synth.tiny_tree_workload(422, K=12, n_taxa=15, n_sites=300, n_epochs=3,
+                                                  n_cat=2, reversible=False, missing_frac=0.1)),
+    (EPOCH_FP32_TC, lambda: synth.small_codon(423, n_taxa=9, n_sites=80, n_cat=2, n_epochs=2)),
+])
+def test_ancestral_states_match_oracle(prec, make):
+    """Posterior state probabilities of every internal node and pattern on
+    the FP64 path, the K = 4 level kernels (cherries from their code-pair
+    tables), the few-pattern kernels, the generic FP32 kernels (asymmetric
+    model) and the tensor-core kernels; absolute error per probability."""
+    w = make()
+    lik = EpochLikelihood(w, precision=prec)
+    try:
+        lik.evaluate(with_gradient=True)
+        got = lik.ancestral_states()
+    finally:
+        lik.close()
+    ref = oracle.ancestral_states(w)
+    assert got.shape == ref.shape
+    assert np.abs(got - ref).max() <= ANC_TOL[prec], (w.name, np.abs(got - ref).max())
+    assert np.allclose(got.sum(-1), 1.0, atol=1e-12)

@@ -508,3 +508,18 @@ def test_expected_counts_are_rate_derivatives(oracle_lib):
     Qn = np.stack([oracle_lib.normalise(w.Q[s], w.pi)[0] for s in range(w.n_matrices)])
     pb_raw, _ = oracle_lib.expected_counts(w.replace(Q=Qn, normalise=0))
     assert np.allclose(pb_n, pb_raw, rtol=1e-10, atol=1e-12)
+
+
+@pytest.mark.parametrize("K,rev,cats", [(4, True, 2), (3, False, 1), (5, True, 3)])
+def test_ancestral_states_equal_enumeration(oracle_lib, K, rev, cats):
+    """Marginal posterior of every internal node's state: the two-pass
+    (outside x inside) computation against enumeration of every joint
+    assignment of the internal states (missing data, several categories,
+    an asymmetric model); rows sum to one."""
+    w = synth.tiny_tree_workload(71 + K, K=K, n_taxa=5, n_sites=6, n_epochs=2, n_cat=cats,
+                                 reversible=rev, dated=True, missing_frac=0.2)
+    a = oracle_lib.ancestral_states(w)
+    b = oracle_lib.ancestral_states(w, brute=True)
+    assert a.shape == (w.n_taxa - 1, w.n_patterns, K)
+    assert np.abs(a - b).max() <= 1e-13
+    assert np.allclose(a.sum(-1), 1.0, atol=1e-13)
