@@ -184,32 +184,54 @@ __device__ __forceinline__ double jacobi_sweeps(T *A, T *U, int Kr, double tol2,
         pq[2 * k + 1] = q;
       }
       __syncthreads();
-      // a warp per pair (warp-uniform skip), lanes along the row or column
-      for (int k = w; k < npair; k += nw) {  // rows: B = J^T A
-        const int p = pq[2 * k], q = pq[2 * k + 1];
-        const T ck = cs[k], sk = sn[k];
-        if (q >= K || sk == T(0)) continue;
-        for (int col = lane; col < K; col += 32) {
+      if (K < 16) {  // few columns: threads over (pair, column)
+        for (int idx = tid; idx < npair * K; idx += nt) {  // rows: B = J^T A
+          const int k = idx / K, col = idx % K, p = pq[2 * k], q = pq[2 * k + 1];
+          if (q >= K || sn[k] == T(0)) continue;
           const T ap = A[p * K + col], aq = A[q * K + col];
-          A[p * K + col] = ck * ap - sk * aq;
-          A[q * K + col] = sk * ap + ck * aq;
+          A[p * K + col] = cs[k] * ap - sn[k] * aq;
+          A[q * K + col] = sn[k] * ap + cs[k] * aq;
         }
-      }
-      __syncthreads();
-      for (int k = w; k < npair; k += nw) {  // columns: A' = B J, U' = U J
-        const int p = pq[2 * k], q = pq[2 * k + 1];
-        const T ck = cs[k], sk = sn[k];
-        if (q >= K || sk == T(0)) continue;
-        for (int row = lane; row < K; row += 32) {
+        __syncthreads();
+        for (int idx = tid; idx < npair * K; idx += nt) {  // columns: A' = B J, U' = U J
+          const int k = idx / K, row = idx % K, p = pq[2 * k], q = pq[2 * k + 1];
+          if (q >= K || sn[k] == T(0)) continue;
           const T ap = A[row * K + p], aq = A[row * K + q];
-          A[row * K + p] = ck * ap - sk * aq;
-          A[row * K + q] = sk * ap + ck * aq;
+          A[row * K + p] = cs[k] * ap - sn[k] * aq;
+          A[row * K + q] = sn[k] * ap + cs[k] * aq;
           const T up = U[row * K + p], uq = U[row * K + q];
-          U[row * K + p] = ck * up - sk * uq;
-          U[row * K + q] = sk * up + ck * uq;
+          U[row * K + p] = cs[k] * up - sn[k] * uq;
+          U[row * K + q] = sn[k] * up + cs[k] * uq;
         }
+        __syncthreads();
+      } else {
+        // a warp per pair (warp-uniform skip), lanes along the row or column
+        for (int k = w; k < npair; k += nw) {  // rows: B = J^T A
+          const int p = pq[2 * k], q = pq[2 * k + 1];
+          const T ck = cs[k], sk = sn[k];
+          if (q >= K || sk == T(0)) continue;
+          for (int col = lane; col < K; col += 32) {
+            const T ap = A[p * K + col], aq = A[q * K + col];
+            A[p * K + col] = ck * ap - sk * aq;
+            A[q * K + col] = sk * ap + ck * aq;
+          }
+        }
+        __syncthreads();
+        for (int k = w; k < npair; k += nw) {  // columns: A' = B J, U' = U J
+          const int p = pq[2 * k], q = pq[2 * k + 1];
+          const T ck = cs[k], sk = sn[k];
+          if (q >= K || sk == T(0)) continue;
+          for (int row = lane; row < K; row += 32) {
+            const T ap = A[row * K + p], aq = A[row * K + q];
+            A[row * K + p] = ck * ap - sk * aq;
+            A[row * K + q] = sk * ap + ck * aq;
+            const T up = U[row * K + p], uq = U[row * K + q];
+            U[row * K + p] = ck * up - sk * uq;
+            U[row * K + q] = sk * up + ck * uq;
+          }
+        }
+        __syncthreads();
       }
-      __syncthreads();
       for (int k = tid; k < npair; k += nt) {  // the annihilated pair
         const int p = pq[2 * k], q = pq[2 * k + 1];
         if (q < K && sn[k] != T(0)) {
@@ -226,9 +248,9 @@ __device__ __forceinline__ double jacobi_sweeps(T *A, T *U, int Kr, double tol2,
 // Cyclic Jacobi on a symmetric K x K FP32 matrix (K <= NR) held in registers
 // by one thread as an NR x NR array, zero outside K x K (every index is a
 // compile-time constant): sweeps over the pairs (p, q), p < q, in row order
-// until the squared off-diagonal norm is <= tol2 (at most 12 sweeps).  Pairs
-// that reach into the zero padding have a_pq = 0 and are skipped, so the
-// padding stays zero.  A and U: row-major K x K in shared memory, U = I on
+// until the squared off-diagonal norm is <= tol2 or no longer halves (at most
+// 12 sweeps).  Pairs that reach into the zero padding have a_pq = 0 and are
+// skipped, so the padding stays zero.  A and U: row-major K x K in shared memory, U = I on
 // entry; A is overwritten by the rotated matrix, U by the rotations.
 template <int NR>
 __device__ __forceinline__ void rot_registers(float (&a)[NR][NR], float (&u)[NR][NR], int p, int q) {
@@ -264,13 +286,16 @@ __device__ void jacobi_registers(float *A, float *U, int K, float tol2) {
       a[i][j] = (i < K && j < K) ? A[i * K + j] : 0.f;
       u[i][j] = (i == j) ? 1.f : 0.f;
     }
+  float prev = 0.f;
   for (int sweep = 0; sweep < 12; sweep++) {
     float off = 0.f;
 #pragma unroll
     for (int p = 0; p < NR; p++)
 #pragma unroll
       for (int q = p + 1; q < NR; q++) off += a[p][q] * a[p][q];
-    if (off <= tol2) break;
+    // converged, or at the FP32 rounding floor (a sweep no longer halves it)
+    if (off <= tol2 || (sweep > 0 && off > 0.5f * prev)) break;
+    prev = off;
 #pragma unroll
     for (int p = 0; p < NR; p++)
 #pragma unroll
