@@ -1,20 +1,22 @@
-// k_tc.cu -- tensor-core contractions of the large-K path (codon K = 61,
-// traits; K <= 64): tcgen05.mma with the accumulator in tensor memory.
+// k_tc.cu -- tensor-core contractions of the larger state spaces (codon
+// K = 61, amino acids K = 20, traits; 16 < K <= 64): tcgen05.mma with the
+// accumulator in tensor memory.
 //
-// A partial vector of one (category, pattern) is a 64-float row (K padded
-// with zeros), so a branch applied to 128 patterns is one tile product
-//     D[128 x 64] = A[128 x 64] * B^T,   B[n][k] = P[n][k] (S = P L)
+// A partial vector of one (category, pattern) is a row of KW floats (K
+// padded with zeros; KW = 64 for 32 < K <= 64, 32 for 16 < K <= 32), so a
+// branch applied to 128 patterns is one tile product
+//     D[128 x KW] = A[128 x KW] * B^T,   B[n][k] = P[n][k] (S = P L)
 //                                        or  B[n][k] = P[k][n] (U = P^T X),
-// run as tcgen05.mma kind::tf32 (M = 128, N = 64, K = 8 per instruction).
+// run as tcgen05.mma kind::tf32 (M = 128, N = KW, K = 8 per instruction).
 // FP32 accuracy comes from the three-term split x = hi + lo (hi = x rounded
 // to TF32, lo = the rest rounded to TF32): A B ~ Ahi Bhi + Ahi Blo + Alo Bhi;
 // the dropped Alo Blo is below 2^-22 of the product.
 //
 // Operands sit in shared memory in the no-swizzle K-major canonical layout:
 // 8-row x 16-byte core matrices, element (r, k) at byte
-//     (r / 8) * 2048 + (k / 4) * 128 + (r % 8) * 16 + (k % 4) * 4,
+//     (r / 8) * 32 KW + (k / 4) * 128 + (r % 8) * 16 + (k % 4) * 4,
 // i.e. leading-dimension (K) byte offset 128 between core matrices and
-// stride-dimension byte offset 2048 between 8-row groups.  The B operands of
+// stride-dimension byte offset 32 KW between 8-row groups.  The B operands of
 // every (branch, category) are laid out once per evaluation (k_tc_prep).
 #include <stdint.h>
 
@@ -25,11 +27,21 @@ namespace {
 
 constexpr int kRows = 128;            // tile rows (patterns)
 constexpr int kTcThr = 128;           // one thread per row; warp w owns TMEM lanes 32w..
-constexpr int kTile4 = 64 * 64;       // floats of one 64 x 64 operand
-constexpr int kATile = kRows * 64;    // floats of one 128 x 64 operand
 
+// Sizes for the tile width KW, in floats.
+template <int KW>
+struct Tw {
+  static constexpr int B = KW * KW;            // one KW x KW operand
+  static constexpr int A = kRows * KW;         // one 128 x KW operand
+  static constexpr int stage = 2 * A + 2 * B;  // A hi, A lo, B hi, B lo
+  static constexpr int c4 = KW / 4;            // float4 per row
+  static constexpr int pad = KW + 4;           // row-buffer stride (bank spread)
+  static constexpr int buf = kRows * pad;      // one row buffer
+};
+
+template <int KW>
 __device__ __forceinline__ int core_off(int r, int k) {  // in floats
-  return (r >> 3) * 512 + (k >> 2) * 32 + (r & 7) * 4 + (k & 3);
+  return (r >> 3) * (8 * KW) + (k >> 2) * 32 + (r & 7) * 4 + (k & 3);
 }
 __device__ __forceinline__ float to_tf32(float x) {
   uint32_t r;
@@ -49,113 +61,132 @@ __device__ __forceinline__ float sc(float x, Pow2 f) { return (x * f.a) * f.b; }
 __device__ __forceinline__ uint32_t su32(const void *p) {
   return (uint32_t)__cvta_generic_to_shared(p);
 }
+template <int KW>
 __device__ __forceinline__ uint64_t smem_desc(uint32_t addr) {
   uint64_t d = (uint64_t)((addr >> 4) & 0x3FFF);
-  d |= (uint64_t)(128 >> 4) << 16;   // leading (K) byte offset
-  d |= (uint64_t)(2048 >> 4) << 32;  // stride (8-row group) byte offset
-  d |= (uint64_t)1 << 46;            // descriptor version; no swizzle, base offset 0
+  d |= (uint64_t)(128 >> 4) << 16;      // leading (K) byte offset
+  d |= (uint64_t)(32 * KW >> 4) << 32;  // stride (8-row group) byte offset
+  d |= (uint64_t)1 << 46;               // descriptor version; no swizzle, base offset 0
   return d;
 }
-// kind::tf32, D = F32, A = B = TF32, both K-major, N = 64, M = 128
-constexpr uint32_t kIdesc = (1u << 4) | (2u << 7) | (2u << 10) | ((64u >> 3) << 17) |
-                            ((128u >> 4) << 24);
+// kind::tf32, D = F32, A = B = TF32, both K-major, N = KW, M = 128
+template <int KW>
+__host__ __device__ constexpr uint32_t idesc() {
+  return (1u << 4) | (2u << 7) | (2u << 10) | (((uint32_t)KW >> 3) << 17) | ((128u >> 4) << 24);
+}
 
+template <int KW>
 __device__ __forceinline__ void mma_tf32(uint32_t dtmem, uint64_t a, uint64_t b, uint32_t acc) {
   asm volatile(
       "{\n.reg .pred p;\nsetp.ne.b32 p, %4, 0;\n"
       "tcgen05.mma.cta_group::1.kind::tf32 [%0], %1, %2, %3, p;\n}\n" ::"r"(dtmem),
-      "l"(a), "l"(b), "r"(kIdesc), "r"(acc));
+      "l"(a), "l"(b), "r"(idesc<KW>()), "r"(acc));
 }
 
 // B operands: for every (v, c): [post hi | post lo | pre hi | pre lo], each
-// 64 x 64 in core order; post = P_v (rows = parent state), pre = P_v^T.
+// KW x KW in core order; post = P_v (rows = parent state), pre = P_v^T.
+template <int KW>
 __global__ void k_tc_prep(Dims d, const double *__restrict__ P64, const int *__restrict__ parent,
                           float *__restrict__ tcB) {
+  constexpr int B = Tw<KW>::B;
   const int v = blockIdx.x / d.C, c = blockIdx.x % d.C;
   if (parent[v] < 0) return;
   const double *P = P64 + ((size_t)v * d.C + c) * d.KK;
-  float *out = tcB + ((size_t)v * d.C + c) * 4 * kTile4;
-  for (int idx = threadIdx.x; idx < kTile4; idx += blockDim.x) {
-    const int r = idx >> 6, k = idx & 63;
+  float *out = tcB + ((size_t)v * d.C + c) * 4 * B;
+  for (int idx = threadIdx.x; idx < B; idx += blockDim.x) {
+    const int r = idx / KW, k = idx % KW;
     const bool in = r < d.K && k < d.K;
     const float vp = in ? (float)P[r * d.K + k] : 0.f;   // post: B[r][k] = P[r][k]
     const float vq = in ? (float)P[k * d.K + r] : 0.f;   // pre:  B[r][k] = P[k][r]
     const float hp = to_tf32(vp), hq = to_tf32(vq);
-    const int o = core_off(r, k);
+    const int o = core_off<KW>(r, k);
     out[o] = hp;
-    out[kTile4 + o] = to_tf32(vp - hp);
-    out[2 * kTile4 + o] = hq;
-    out[3 * kTile4 + o] = to_tf32(vq - hq);
+    out[B + o] = to_tf32(vp - hp);
+    out[2 * B + o] = hq;
+    out[3 * B + o] = to_tf32(vq - hq);
   }
 }
 
-// Shared memory: two stages, each one operand pair: A hi, A lo (32 KB each),
-// B hi, B lo (16 KB each).
-constexpr int kStageFloats = 2 * kATile + 2 * kTile4;
-constexpr size_t kTcSmem = sizeof(float) * 2 * kStageFloats + 1024;
-constexpr size_t kTcSmem1 = sizeof(float) * kStageFloats + 1024;  // one stage (one product)
+// Shared memory of a stage: one operand pair (A hi, A lo, B hi, B lo); two
+// stages for the pipelined variant.
+template <int KW>
+__host__ __device__ constexpr size_t tc_smem(int nst) {
+  return sizeof(float) * nst * Tw<KW>::stage + 1024;
+}
 
-// An A tile in registers: thread (warp w, lane l) holds, for q < 16, row
-// 8q + (l & 7), columns 4 (4w + (l >> 3)) .. +3.  A warp's load covers 8 rows
-// x 64 contiguous bytes (whole sectors); a quarter-warp's store covers 8
-// consecutive rows of one core-matrix column, 128 contiguous bytes (no bank
-// conflicts).
+// An A tile in registers.  A warp's load instruction covers 8 rows x 4
+// consecutive float4 (64 contiguous bytes of each row: whole sectors); a
+// quarter-warp's store covers 8 consecutive rows of one core-matrix column,
+// 128 contiguous bytes (no bank conflicts).  With nG = KW / 16 column groups
+// of 4 float4, warp w takes group w % nG and every (4 / nG)-th block of 8
+// rows from w / nG: thread (w, l) holds, for q < KW / 4, row
+// 8 (q (4 / nG) + w / nG) + (l & 7), float4 4 (w % nG) + (l >> 3).
+template <int KW>
 struct ATile {
-  float4 x[16];
+  float4 x[KW / 4];
 };
-__device__ __forceinline__ int a_col() {
-  return 4 * (4 * (threadIdx.x >> 5) + ((threadIdx.x & 31) >> 3));
+template <int KW>
+__device__ __forceinline__ void a_pos(int q, int &r, int &col) {
+  constexpr int nG = KW / 16, RB = 4 / nG;
+  const int w = threadIdx.x >> 5, l = threadIdx.x & 31;
+  r = 8 * (q * RB + w / nG) + (l & 7);
+  col = 4 * (4 * (w % nG) + (l >> 3));
 }
 // Rows >= rows read as zero.
-__device__ __forceinline__ void tc_load_A(const float *A, int lda, int rows, ATile &t) {
-  const int col = a_col(), r0 = threadIdx.x & 7;
+template <int KW>
+__device__ __forceinline__ void tc_load_A(const float *A, int lda, int rows, ATile<KW> &t) {
 #pragma unroll
-  for (int q = 0; q < 16; q++) {
-    const int r = 8 * q + r0;
+  for (int q = 0; q < KW / 4; q++) {
+    int r, col;
+    a_pos<KW>(q, r, col);
     t.x[q] = r < rows ? *reinterpret_cast<const float4 *>(A + (size_t)r * lda + col)
                       : make_float4(0.f, 0.f, 0.f, 0.f);
   }
 }
 // hi / lo split into the stage's A area, core order.
-__device__ __forceinline__ void tc_store_A(const ATile &t, float *st) {
-  float *sAh = st, *sAl = st + kATile;
-  const int col = a_col(), r0 = threadIdx.x & 7;
+template <int KW>
+__device__ __forceinline__ void tc_store_A(const ATile<KW> &t, float *st) {
+  float *sAh = st, *sAl = st + Tw<KW>::A;
 #pragma unroll
-  for (int q = 0; q < 16; q++) {
+  for (int q = 0; q < KW / 4; q++) {
+    int r, col;
+    a_pos<KW>(q, r, col);
     const float4 x = t.x[q];
     const float4 h = make_float4(to_tf32(x.x), to_tf32(x.y), to_tf32(x.z), to_tf32(x.w));
     const float4 l = make_float4(to_tf32(x.x - h.x), to_tf32(x.y - h.y), to_tf32(x.z - h.z),
                                  to_tf32(x.w - h.w));
-    const int o = core_off(8 * q + r0, col);
+    const int o = core_off<KW>(r, col);
     *reinterpret_cast<float4 *>(sAh + o) = h;
     *reinterpret_cast<float4 *>(sAl + o) = l;
   }
 }
-// B: hi | lo (2 x 16 KB, laid out by k_tc_prep) into the stage's B area by
-// cp.async, as one commit group.
+// B: hi | lo (laid out by k_tc_prep) into the stage's B area by cp.async, as
+// one commit group.
+template <int KW>
 __device__ __forceinline__ void tc_async_B(const float *Bq, float *st) {
-  const uint32_t dst = su32(st + 2 * kATile);
+  const uint32_t dst = su32(st + 2 * Tw<KW>::A);
   const size_t src = __cvta_generic_to_global(Bq);
 #pragma unroll 4
-  for (int i = threadIdx.x; i < 2 * kTile4 / 4; i += kTcThr)
+  for (int i = threadIdx.x; i < 2 * Tw<KW>::B / 4; i += kTcThr)
     asm volatile("cp.async.cg.shared.global [%0], [%1], 16;" ::"r"(dst + 16 * i),
                  "l"(src + 16 * (size_t)i)
                  : "memory");
   asm volatile("cp.async.commit_group;" ::: "memory");
 }
-// Issue (thread 0) D[col..col+63] = A B^T from stage st with the three split
-// products, then signal mbar when they have completed.  Staged operands must
-// be fenced and the CTA synchronised before the call.
+// Issue (thread 0) D[col..col+KW-1] = A B^T from stage st with the three
+// split products, then signal mbar when they have completed.  Staged operands
+// must be fenced and the CTA synchronised before the call.
+template <int KW>
 __device__ __forceinline__ void tc_mma(uint32_t dtmem, const float *st, uint64_t *mbar) {
   if (threadIdx.x != 0) return;
   asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
-  const uint32_t ah = su32(st), al = ah + kATile * 4, bh = ah + 2 * kATile * 4,
-                 bl = bh + kTile4 * 4;
-  for (int ks = 0; ks < 8; ks++) {  // 8 TF32 of K per instruction = 256 bytes
+  const uint32_t ah = su32(st), al = ah + Tw<KW>::A * 4, bh = ah + 2 * Tw<KW>::A * 4,
+                 bl = bh + Tw<KW>::B * 4;
+  for (int ks = 0; ks < KW / 8; ks++) {  // 8 TF32 of K per instruction = 256 bytes
     const uint32_t o = ks * 256;
-    mma_tf32(dtmem, smem_desc(ah + o), smem_desc(bh + o), ks > 0);
-    mma_tf32(dtmem, smem_desc(ah + o), smem_desc(bl + o), 1);
-    mma_tf32(dtmem, smem_desc(al + o), smem_desc(bh + o), 1);
+    mma_tf32<KW>(dtmem, smem_desc<KW>(ah + o), smem_desc<KW>(bh + o), ks > 0);
+    mma_tf32<KW>(dtmem, smem_desc<KW>(ah + o), smem_desc<KW>(bl + o), 1);
+    mma_tf32<KW>(dtmem, smem_desc<KW>(al + o), smem_desc<KW>(bh + o), 1);
   }
   asm volatile(
       "tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(
@@ -205,28 +236,55 @@ __device__ __forceinline__ void tc_ld64(uint32_t taddr, int col, float *out) {
   for (int j = 0; j < 64; j++) out[j] = __uint_as_float(v[j]);
 }
 
-// Epilogue row buffers in the (then free) stage memory: 128 rows of 64
-// floats, padded to 68 so that the eight rows a quarter-warp writes at one
-// column fall in distinct banks.
-constexpr int kRowPad = 68;
-constexpr int kRowBuf = kRows * kRowPad;  // floats of one buffer
-// Thread r's row of 64 values into buffer row r (float4 stores).
-__device__ __forceinline__ void row_put(float *buf, const float (&v)[64]) {
-  float *dst = buf + threadIdx.x * kRowPad;
+// 32 columns of the thread's TMEM lane, one load and one wait.
+__device__ __forceinline__ void tc_ld32(uint32_t taddr, int col, float *out) {
+  uint32_t v[32];
+  const uint32_t a = taddr + ((uint32_t)(32 * (threadIdx.x >> 5)) << 16) + col;
+  asm volatile(
+      "tcgen05.ld.sync.aligned.32x32b.x32.b32 {%0,%1,%2,%3,%4,%5,%6,%7,%8,%9,%10,%11,%12,"
+      "%13,%14,%15,%16,%17,%18,%19,%20,%21,%22,%23,%24,%25,%26,%27,%28,%29,%30,%31}, [%32];"
+      : "=r"(v[0]), "=r"(v[1]), "=r"(v[2]), "=r"(v[3]), "=r"(v[4]), "=r"(v[5]), "=r"(v[6]),
+        "=r"(v[7]), "=r"(v[8]), "=r"(v[9]), "=r"(v[10]), "=r"(v[11]), "=r"(v[12]), "=r"(v[13]),
+        "=r"(v[14]), "=r"(v[15]), "=r"(v[16]), "=r"(v[17]), "=r"(v[18]), "=r"(v[19]), "=r"(v[20]),
+        "=r"(v[21]), "=r"(v[22]), "=r"(v[23]), "=r"(v[24]), "=r"(v[25]), "=r"(v[26]), "=r"(v[27]),
+        "=r"(v[28]), "=r"(v[29]), "=r"(v[30]), "=r"(v[31])
+      : "r"(a));
+  asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
 #pragma unroll
-  for (int q = 0; q < 16; q++)
+  for (int j = 0; j < 32; j++) out[j] = __uint_as_float(v[j]);
+}
+// KW columns of the thread's TMEM lane.
+template <int KW>
+__device__ __forceinline__ void tc_ld(uint32_t taddr, int col, float *out) {
+  if constexpr (KW == 64)
+    tc_ld64(taddr, col, out);
+  else
+    tc_ld32(taddr, col, out);
+}
+
+// Epilogue row buffers in the (then free) stage memory: 128 rows of KW
+// floats, padded to KW + 4 so that the eight rows a quarter-warp writes at
+// one column fall in distinct banks.
+// Thread r's row of KW values into buffer row r (float4 stores).
+template <int KW>
+__device__ __forceinline__ void row_put(float *buf, const float (&v)[KW]) {
+  float *dst = buf + threadIdx.x * Tw<KW>::pad;
+#pragma unroll
+  for (int q = 0; q < KW / 4; q++)
     *reinterpret_cast<float4 *>(dst + 4 * q) =
         make_float4(v[4 * q], v[4 * q + 1], v[4 * q + 2], v[4 * q + 3]);
 }
 // A buffer of `rows` rows to global rows (ld floats apart) with whole-warp
 // contiguous float4 stores; each row scaled by 2^-e[row] when e is given.
+template <int KW>
 __device__ __forceinline__ void rows_store(const float *buf, float *dst, int ld, int rows,
                                            const int *e) {
+  constexpr int C4 = Tw<KW>::c4;
 #pragma unroll 4
-  for (int q = 0; q < 16; q++) {
-    const int idx = threadIdx.x + kTcThr * q, row = idx >> 4, c4 = idx & 15;
+  for (int q = 0; q < C4; q++) {
+    const int idx = threadIdx.x + kTcThr * q, row = idx / C4, c4 = idx % C4;
     if (row < rows) {
-      float4 v = *reinterpret_cast<const float4 *>(buf + row * kRowPad + 4 * c4);
+      float4 v = *reinterpret_cast<const float4 *>(buf + row * Tw<KW>::pad + 4 * c4);
       if (e) {
         const Pow2 f = pow2_neg(e[row]);
         v = make_float4(sc(v.x, f), sc(v.y, f), sc(v.z, f), sc(v.w, f));
@@ -237,19 +295,22 @@ __device__ __forceinline__ void rows_store(const float *buf, float *dst, int ld,
 }
 // Global rows (ld floats apart) into a buffer with contiguous loads; rows >=
 // `rows` become zero.
+template <int KW>
 __device__ __forceinline__ void rows_load(const float *src, int ld, int rows, float *buf) {
+  constexpr int C4 = Tw<KW>::c4;
 #pragma unroll 4
-  for (int q = 0; q < 16; q++) {
-    const int idx = threadIdx.x + kTcThr * q, row = idx >> 4, c4 = idx & 15;
+  for (int q = 0; q < C4; q++) {
+    const int idx = threadIdx.x + kTcThr * q, row = idx / C4, c4 = idx % C4;
     const float4 v = row < rows ? *reinterpret_cast<const float4 *>(src + (size_t)row * ld + 4 * c4)
                                 : make_float4(0.f, 0.f, 0.f, 0.f);
-    *reinterpret_cast<float4 *>(buf + row * kRowPad + 4 * c4) = v;
+    *reinterpret_cast<float4 *>(buf + row * Tw<KW>::pad + 4 * c4) = v;
   }
 }
-// 64 floats of a table row (a tip's S: the row of its code).
-__device__ __forceinline__ void row_get(const float *src, float (&v)[64]) {
+// KW floats of a table row (a tip's S: the row of its code).
+template <int KW>
+__device__ __forceinline__ void row_get(const float *src, float (&v)[KW]) {
 #pragma unroll
-  for (int q = 0; q < 16; q++) {
+  for (int q = 0; q < KW / 4; q++) {
     const float4 t = reinterpret_cast<const float4 *>(src)[q];
     v[4 * q] = t.x;
     v[4 * q + 1] = t.y;
@@ -258,7 +319,7 @@ __device__ __forceinline__ void row_get(const float *src, float (&v)[64]) {
   }
 }
 
-// Tile products D_j[128 x 64] = A_j B_j^T into TMEM columns col_j, j < n,
+// Tile products D_j[128 x KW] = A_j B_j^T into TMEM columns col_j, j < n,
 // for one tile of 128 rows (A rows lda floats apart; rows >= `rows` read as
 // zero).  item(j, A, B, col) names the operands.  Every thread takes part.
 // NST = 2 (two shared-memory stages): while the tensor cores run item j, item
@@ -267,16 +328,17 @@ __device__ __forceinline__ void row_get(const float *src, float (&v)[64]) {
 // registers during item j's MMA, its B once that MMA has completed.
 // Returns false when an MMA did not complete within the wait bound; nothing
 // is then left in flight but that MMA.
-template <int NST, class Item>
+template <int NST, int KW, class Item>
 __device__ bool tc_pipeline(int n, int lda, int rows, Item item, float *sm, uint32_t taddr,
                             uint64_t *mbar, uint32_t *ph) {
+  constexpr int kStageFloats = Tw<KW>::stage;
   if (n <= 0) return true;
-  ATile ra;
+  ATile<KW> ra;
   const float *A, *B;
   uint32_t col;
   item(0, A, B, col);
-  tc_async_B(B, sm);
-  tc_load_A(A, lda, rows, ra);
+  tc_async_B<KW>(B, sm);
+  tc_load_A<KW>(A, lda, rows, ra);
   for (int j = 0; j < n; j++) {
     float *st = sm + (NST == 2 ? (j & 1) * kStageFloats : 0);
     if (NST == 1 && j >= 1) {  // the single stage is free once MMA j-1 has completed
@@ -284,13 +346,13 @@ __device__ bool tc_pipeline(int n, int lda, int rows, Item item, float *sm, uint
         asm volatile("cp.async.wait_all;" ::: "memory");
         return false;
       }
-      tc_async_B(B, st);
+      tc_async_B<KW>(B, st);
     }
-    tc_store_A(ra, st);  // two stages: stage j&1 is free, MMA j-2 was waited for at j-1
+    tc_store_A<KW>(ra, st);  // two stages: stage j&1 is free, MMA j-2 was waited for at j-1
     const uint32_t colj = col;
     if (j + 1 < n) {
       item(j + 1, A, B, col);
-      tc_load_A(A, lda, rows, ra);  // in flight during this item's MMA
+      tc_load_A<KW>(A, lda, rows, ra);  // in flight during this item's MMA
     }
     if (NST == 2) {
       if (j >= 1 && !tc_wait(&mbar[(j - 1) & 1], ph[(j - 1) & 1])) {
@@ -298,7 +360,7 @@ __device__ bool tc_pipeline(int n, int lda, int rows, Item item, float *sm, uint
         return false;
       }
       if (j + 1 < n) {  // MMA j-1 has released stage (j+1)&1
-        tc_async_B(B, sm + ((j + 1) & 1) * kStageFloats);
+        tc_async_B<KW>(B, sm + ((j + 1) & 1) * kStageFloats);
         asm volatile("cp.async.wait_group 1;" ::: "memory");  // B of item j has landed
       } else {
         asm volatile("cp.async.wait_group 0;" ::: "memory");
@@ -307,7 +369,7 @@ __device__ bool tc_pipeline(int n, int lda, int rows, Item item, float *sm, uint
       asm volatile("cp.async.wait_group 0;" ::: "memory");
     }
     tc_sync_staged();
-    tc_mma(taddr + colj, st, &mbar[j & 1]);
+    tc_mma<KW>(taddr + colj, st, &mbar[j & 1]);
   }
   return tc_wait(&mbar[(n - 1) & 1], ph[(n - 1) & 1]);
 }
@@ -342,6 +404,7 @@ __device__ __forceinline__ float *tc_smem(float *tsm) {
 // Pre-order: U_v = P_v^T X_v for the non-tip children of one level's nodes.
 // grid = (tiles of 128 patterns, level nodes * 2 children, categories); one
 // tile product per CTA (one shared-memory stage).
+template <int KW>
 __global__ void __launch_bounds__(kTcThr) k_tc_pre_u(Dims d, const int *__restrict__ lvl_nodes,
                                                     int lvl_off, const int *__restrict__ child,
                                                     const float *__restrict__ xbuf,
@@ -355,30 +418,33 @@ __global__ void __launch_bounds__(kTcThr) k_tc_pre_u(Dims d, const int *__restri
   const int v = child[2 * (u - d.N) + x];
   if (v < d.N) return;  // tips carry no outside partial (uniform over the CTA)
   float *sm = tc_smem(tsm);
-  const uint32_t taddr = tc_begin(&s_tmem, mbar, 64);
+  const uint32_t ncols = KW < 32 ? 32 : KW;  // a TMEM allocation is >= 32 columns
+  const uint32_t taddr = tc_begin(&s_tmem, mbar, ncols);
   uint32_t ph[2] = {0, 0};
   const int p0 = blockIdx.x * kRows;
   const int rows = min(kRows, d.P - p0);
   auto item = [&](int, const float *&A, const float *&B, uint32_t &col) {
     A = xbuf + ((((size_t)bi * 2 + x) * d.C + c) * d.P + p0) * d.Kp;
-    B = tcB + ((size_t)v * d.C + c) * 4 * kTile4 + 2 * kTile4;  // pre hi | lo
+    B = tcB + ((size_t)v * d.C + c) * 4 * Tw<KW>::B + 2 * Tw<KW>::B;  // pre hi | lo
     col = 0;
   };
-  if (!tc_pipeline<1>(1, d.Kp, rows, item, sm, taddr, mbar, ph)) {
+  if (!tc_pipeline<1, KW>(1, d.Kp, rows, item, sm, taddr, mbar, ph)) {
     if (threadIdx.x == 0) atomicOr(status, ST_TIMEOUT);
-    tc_end(taddr, 64);
+    tc_end(taddr, ncols);
     return;
   }
-  float vv[64];
-  tc_ld64(taddr, 0, vv);
-  row_put(sm, vv);
+  float vv[KW];
+  tc_ld<KW>(taddr, 0, vv);
+  row_put<KW>(sm, vv);
   __syncthreads();
-  rows_store(sm, pre + ((((size_t)(v - d.N) * d.C + c) * d.P) + p0) * d.Kp, d.Kp, rows, nullptr);
-  tc_end(taddr, 64);
+  rows_store<KW>(sm, pre + ((((size_t)(v - d.N) * d.C + c) * d.P) + p0) * d.Kp, d.Kp, rows,
+                 nullptr);
+  tc_end(taddr, ncols);
 }
 
-// S of both children of node u for category c into TMEM columns sd * 64;
+// S of both children of node u for category c into TMEM columns sd * KW;
 // tips are skipped (their S is a table row).
+template <int KW>
 __device__ __forceinline__ bool tc_children_S(const Dims &d, const int (&kid)[2], int c,
                                               const float *part, const float *tcB, int p0,
                                               int rows, float *sm, uint32_t taddr,
@@ -389,19 +455,20 @@ __device__ __forceinline__ bool tc_children_S(const Dims &d, const int (&kid)[2]
     const int sd = n == 2 ? j : (st0 ? 0 : 1);
     const int v = kid[sd];
     A = part + ((((size_t)(v - d.N) * d.C + c) * d.P) + p0) * d.Kp;
-    B = tcB + ((size_t)v * d.C + c) * 4 * kTile4;  // post hi | lo
-    col = (uint32_t)sd * 64;
+    B = tcB + ((size_t)v * d.C + c) * 4 * Tw<KW>::B;  // post hi | lo
+    col = (uint32_t)(sd * KW);
   };
-  return tc_pipeline<1>(n, d.Kp, rows, item, sm, taddr, mbar, ph);
+  return tc_pipeline<1, KW>(n, d.Kp, rows, item, sm, taddr, mbar, ph);
 }
 
 // S of child sd (TMEM block sd, or the table row of a tip's code).
+template <int KW>
 __device__ __forceinline__ void child_S(const Dims &d, const float *PT, int kid, int c, int code,
-                                        uint32_t taddr, int sd, float (&v)[64]) {
+                                        uint32_t taddr, int sd, float (&v)[KW]) {
   if (kid >= d.N)
-    tc_ld64(taddr, sd * 64, v);
+    tc_ld<KW>(taddr, sd * KW, v);
   else
-    row_get(PT + (((size_t)kid * d.C + c) * d.NR + code) * d.Kp, v);
+    row_get<KW>(PT + (((size_t)kid * d.C + c) * d.NR + code) * d.Kp, v);
 }
 
 // Cluster-wide barrier (every CTA of the cluster arrives, then waits).
@@ -425,6 +492,7 @@ __device__ __forceinline__ float cluster_ld(const float *p, uint32_t rank) {
 // cluster: each publishes its rows' maxima over i in shared memory and reads
 // the others' through distributed shared memory.  grid = (tiles of 128
 // patterns, nodes, categories), cluster (1, 1, C).
+template <int KW>
 __global__ void __launch_bounds__(kTcThr) k_tc_post(Dims d, const int *__restrict__ lvl_nodes,
                                                    int lvl_off, const int *__restrict__ child,
                                                    const float *__restrict__ PT,
@@ -441,10 +509,10 @@ __global__ void __launch_bounds__(kTcThr) k_tc_post(Dims d, const int *__restric
   const int u = lvl_nodes[lvl_off + blockIdx.y];
   const int slot = u - d.N;
   const int kid[2] = {child[2 * slot], child[2 * slot + 1]};
-  const uint32_t taddr = tc_begin(&s_tmem, mbar, 128);
+  const uint32_t taddr = tc_begin(&s_tmem, mbar, 2 * KW);
   uint32_t ph[2] = {0, 0};
   const int p0 = blockIdx.x * kRows, rows = min(kRows, d.P - p0);
-  const bool ok = tc_children_S(d, kid, c, part, tcB, p0, rows, sm, taddr, mbar, ph);
+  const bool ok = tc_children_S<KW>(d, kid, c, part, tcB, p0, rows, sm, taddr, mbar, ph);
   if (!ok && threadIdx.x == 0) atomicOr(status, ST_TIMEOUT);
   const int r = threadIdx.x, p = p0 + r;
   const bool live = r < rows;
@@ -454,15 +522,15 @@ __global__ void __launch_bounds__(kTcThr) k_tc_post(Dims d, const int *__restric
   // unscaled L_u row of this category into the row buffer; its maximum
   float m = 0.f;
   if (ok) {
-    float s0[64], s1[64];
-    child_S(d, PT, kid[0], c, code[0], taddr, 0, s0);
-    child_S(d, PT, kid[1], c, code[1], taddr, 1, s1);
+    float s0[KW], s1[KW];
+    child_S<KW>(d, PT, kid[0], c, code[0], taddr, 0, s0);
+    child_S<KW>(d, PT, kid[1], c, code[1], taddr, 1, s1);
 #pragma unroll
-    for (int j = 0; j < 64; j++) {
+    for (int j = 0; j < KW; j++) {
       s0[j] = j < d.K ? s0[j] * s1[j] : 0.f;
       m = fmaxf(m, s0[j]);
     }
-    row_put(sm, s0);
+    row_put<KW>(sm, s0);
   }
   s_m[r] = m;
   // every CTA of the cluster takes both barriers, whatever happened above
@@ -480,14 +548,15 @@ __global__ void __launch_bounds__(kTcThr) k_tc_post(Dims d, const int *__restric
   if (live && c == 0) scale[(size_t)slot * d.Pp + p] = (int16_t)e;
   __syncthreads();
   if (ok)
-    rows_store(sm, part + ((((size_t)slot * d.C + c) * d.P) + p0) * d.Kp, d.Kp, rows, s_e);
-  tc_end(taddr, 128);
+    rows_store<KW>(sm, part + ((((size_t)slot * d.C + c) * d.P) + p0) * d.Kp, d.Kp, rows, s_e);
+  tc_end(taddr, 2 * KW);
 }
 
 // Pre-order level, one category: X of both children of u,
 //   X_0 = U_u o S_1 2^-e_u,  X_1 = U_u o S_0 2^-e_u,
 // with S of stored children by tile products, into the adjoint scratch.
 // grid = (tiles of 128 patterns, nodes, categories).
+template <int KW>
 __global__ void __launch_bounds__(kTcThr) k_tc_pre_x(
     Dims d, const int *__restrict__ lvl_nodes, int lvl_off, const int *__restrict__ child, int root,
     const float *__restrict__ PT, const uint8_t *__restrict__ tips, const float *__restrict__ tcB,
@@ -502,12 +571,12 @@ __global__ void __launch_bounds__(kTcThr) k_tc_pre_x(
   const int u = lvl_nodes[lvl_off + bi];
   const int slot = u - d.N;
   const int kid[2] = {child[2 * slot], child[2 * slot + 1]};
-  const uint32_t taddr = tc_begin(&s_tmem, mbar, 128);
+  const uint32_t taddr = tc_begin(&s_tmem, mbar, 2 * KW);
   uint32_t ph[2] = {0, 0};
   const int p0 = blockIdx.x * kRows, rows = min(kRows, d.P - p0);
-  if (!tc_children_S(d, kid, c, part, tcB, p0, rows, sm, taddr, mbar, ph)) {
+  if (!tc_children_S<KW>(d, kid, c, part, tcB, p0, rows, sm, taddr, mbar, ph)) {
     if (threadIdx.x == 0) atomicOr(status, ST_TIMEOUT);
-    tc_end(taddr, 128);
+    tc_end(taddr, 2 * KW);
     return;
   }
   const int r = threadIdx.x, p = p0 + r;
@@ -519,46 +588,52 @@ __global__ void __launch_bounds__(kTcThr) k_tc_pre_x(
   const Pow2 f = pow2_neg(scale[(size_t)slot * d.Pp + pc]);
   // X_0 overwrites U_u in place: each thread reads its whole U row before it
   // writes that row of X_0
-  float *ubuf = sm, *xb0 = sm, *xb1 = sm + kRowBuf;
+  float *ubuf = sm, *xb0 = sm, *xb1 = sm + Tw<KW>::buf;
   if (u != root)  // U_u rows, contiguous loads
-    rows_load(pre + ((((size_t)slot * d.C + c) * d.P) + p0) * d.Kp, d.Kp, rows, ubuf);
+    rows_load<KW>(pre + ((((size_t)slot * d.C + c) * d.P) + p0) * d.Kp, d.Kp, rows, ubuf);
   __syncthreads();
   const double rootw = (u == root) ? catw[c] * site_inv[pc] : 0.0;
-  float s0[64], s1[64];
-  child_S(d, PT, kid[0], c, code[0], taddr, 0, s0);
-  child_S(d, PT, kid[1], c, code[1], taddr, 1, s1);
-  const float *urow = ubuf + r * kRowPad;
+  float s0[KW], s1[KW];
+  child_S<KW>(d, PT, kid[0], c, code[0], taddr, 0, s0);
+  child_S<KW>(d, PT, kid[1], c, code[1], taddr, 1, s1);
+  const float *urow = ubuf + r * Tw<KW>::pad;
 #pragma unroll
-  for (int j = 0; j < 64; j++) {
+  for (int j = 0; j < KW; j++) {
     const float uu = (u == root) ? (j < d.K ? (float)(rootw * pi[j]) : 0.f) : urow[j];
     const float a = s1[j], b = s0[j];
     s0[j] = sc(uu * a, f);  // X_0 = U o S_1 2^-e
     s1[j] = sc(uu * b, f);  // X_1 = U o S_0 2^-e
   }
-  row_put(xb0, s0);
-  row_put(xb1, s1);
+  row_put<KW>(xb0, s0);
+  row_put<KW>(xb1, s1);
   __syncthreads();
-  rows_store(xb0, xbuf + ((((size_t)bi * 2 + 0) * d.C + c) * d.P + p0) * d.Kp, d.Kp, rows,
-             nullptr);
-  rows_store(xb1, xbuf + ((((size_t)bi * 2 + 1) * d.C + c) * d.P + p0) * d.Kp, d.Kp, rows,
-             nullptr);
-  tc_end(taddr, 128);
+  rows_store<KW>(xb0, xbuf + ((((size_t)bi * 2 + 0) * d.C + c) * d.P + p0) * d.Kp, d.Kp, rows,
+                 nullptr);
+  rows_store<KW>(xb1, xbuf + ((((size_t)bi * 2 + 1) * d.C + c) * d.P + p0) * d.Kp, d.Kp, rows,
+                 nullptr);
+  tc_end(taddr, 2 * KW);
 }
 
 }  // namespace
 
+// Tile width 64 (32 < K <= 64) or 32 (16 < K <= 32): the padded row length.
 bool tc_path(const epoch_ctx *c) {
-  return c->precision == EPOCH_FP32_TC && !fast_k4(c) && c->d.Kp == 64 && c->d.C <= 4;
+  return c->precision == EPOCH_FP32_TC && !fast_k4(c) && (c->d.Kp == 64 || c->d.Kp == 32) &&
+         c->d.C <= 4;
 }
 
-cudaError_t launch_tc_post(epoch_ctx *c, int level) {
+namespace {
+
+template <int KW>
+cudaError_t tc_post(epoch_ctx *c, int level) {
   const Dims &d = c->d;
   const int w = c->h_level_off[level + 1] - c->h_level_off[level];
-  cudaFuncSetAttribute(k_tc_post, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kTcSmem1);
+  const size_t smem = tc_smem<KW>(1);
+  cudaFuncSetAttribute(k_tc_post<KW>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
   cudaLaunchConfig_t cfg = {};
   cfg.gridDim = dim3(ceil_div(d.P, kRows), w, d.C);
   cfg.blockDim = dim3(kTcThr);
-  cfg.dynamicSmemBytes = kTcSmem1;
+  cfg.dynamicSmemBytes = smem;
   cfg.stream = c->stream;
   cudaLaunchAttribute at[1];
   at[0].id = cudaLaunchAttributeClusterDimension;  // the categories of a (tile, node)
@@ -567,48 +642,73 @@ cudaError_t launch_tc_post(epoch_ctx *c, int level) {
   at[0].val.clusterDim.z = d.C;
   cfg.attrs = at;
   cfg.numAttrs = 1;
-  cudaError_t e = cudaLaunchKernelEx(&cfg, k_tc_post, d, (const int *)c->d_level_nodes,
-                                     c->h_level_off[level], (const int *)c->d_child,
-                                     (const float *)c->d_PT32, (const uint8_t *)c->d_tips,
-                                     (const float *)c->d_tcB, (float *)c->d_part, c->d_scale,
-                                     c->d_status);
+  return cudaLaunchKernelEx(&cfg, k_tc_post<KW>, d, (const int *)c->d_level_nodes,
+                            c->h_level_off[level], (const int *)c->d_child,
+                            (const float *)c->d_PT32, (const uint8_t *)c->d_tips,
+                            (const float *)c->d_tcB, (float *)c->d_part, c->d_scale, c->d_status);
+}
+
+template <int KW>
+void tc_pre_x(epoch_ctx *c, int level, int root) {
+  const Dims &d = c->d;
+  const int w = c->h_level_off[level + 1] - c->h_level_off[level];
+  const size_t smem = tc_smem<KW>(1);
+  cudaFuncSetAttribute(k_tc_pre_x<KW>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+  k_tc_pre_x<KW><<<dim3(ceil_div(d.P, kRows), w, d.C), kTcThr, smem, c->stream>>>(
+      d, c->d_level_nodes, c->h_level_off[level], c->d_child, root, c->d_PT32, c->d_tips,
+      c->d_tcB, (const float *)c->d_part, (const float *)c->d_pre, c->d_scale, c->d_pi,
+      c->d_catw, c->d_site_inv, (float *)c->d_xbuf, c->d_status);
+}
+
+template <int KW>
+void tc_pre_u(epoch_ctx *c, int level) {
+  const Dims &d = c->d;
+  const int w = c->h_level_off[level + 1] - c->h_level_off[level];
+  const size_t smem = tc_smem<KW>(1);
+  cudaFuncSetAttribute(k_tc_pre_u<KW>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+  k_tc_pre_u<KW><<<dim3(ceil_div(d.P, kRows), 2 * w, d.C), kTcThr, smem, c->stream>>>(
+      d, c->d_level_nodes, c->h_level_off[level], c->d_child, (const float *)c->d_xbuf, c->d_tcB,
+      (float *)c->d_pre, c->d_status);
+}
+
+}  // namespace
+
+cudaError_t launch_tc_post(epoch_ctx *c, int level) {
+  cudaError_t e = c->d.Kp == 64 ? tc_post<64>(c, level) : tc_post<32>(c, level);
   c->launches++;
   return e != cudaSuccess ? e : cudaGetLastError();
 }
 
 cudaError_t launch_tc_pre_x(epoch_ctx *c, int level, int root) {
-  const Dims &d = c->d;
-  const int w = c->h_level_off[level + 1] - c->h_level_off[level];
-  cudaFuncSetAttribute(k_tc_pre_x, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kTcSmem1);
-  k_tc_pre_x<<<dim3(ceil_div(d.P, kRows), w, d.C), kTcThr, kTcSmem1, c->stream>>>(
-      d, c->d_level_nodes, c->h_level_off[level], c->d_child, root, c->d_PT32, c->d_tips,
-      c->d_tcB, (const float *)c->d_part, (const float *)c->d_pre, c->d_scale, c->d_pi,
-      c->d_catw, c->d_site_inv, (float *)c->d_xbuf, c->d_status);
+  if (c->d.Kp == 64)
+    tc_pre_x<64>(c, level, root);
+  else
+    tc_pre_x<32>(c, level, root);
   c->launches++;
   return cudaGetLastError();
 }
 
 cudaError_t launch_tc_prep(epoch_ctx *c) {
   const Dims &d = c->d;
-  k_tc_prep<<<d.nn * d.C, 256, 0, c->stream>>>(d, c->d_P64, c->d_parent, c->d_tcB);
+  if (d.Kp == 64)
+    k_tc_prep<64><<<d.nn * d.C, 256, 0, c->stream>>>(d, c->d_P64, c->d_parent, c->d_tcB);
+  else
+    k_tc_prep<32><<<d.nn * d.C, 256, 0, c->stream>>>(d, c->d_P64, c->d_parent, c->d_tcB);
   c->launches++;
   return cudaGetLastError();
 }
 
 cudaError_t launch_tc_pre_u(epoch_ctx *c, int level) {
-  const Dims &d = c->d;
-  const int w = c->h_level_off[level + 1] - c->h_level_off[level];
-  cudaFuncSetAttribute(k_tc_pre_u, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kTcSmem1);
-  dim3 g(ceil_div(d.P, kRows), 2 * w, d.C);
-  k_tc_pre_u<<<g, kTcThr, kTcSmem1, c->stream>>>(d, c->d_level_nodes, c->h_level_off[level],
-                                                  c->d_child, (const float *)c->d_xbuf, c->d_tcB,
-                                                  (float *)c->d_pre, c->d_status);
+  if (c->d.Kp == 64)
+    tc_pre_u<64>(c, level);
+  else
+    tc_pre_u<32>(c, level);
   c->launches++;
   return cudaGetLastError();
 }
 
 size_t tc_operand_floats(const epoch_ctx *c) {
-  return (size_t)(2 * c->max_taxa - 1) * c->d.C * 4 * kTile4;
+  return (size_t)(2 * c->max_taxa - 1) * c->d.C * 4 * c->d.Kp * c->d.Kp;
 }
 
 }  // namespace epoch

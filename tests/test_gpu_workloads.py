@@ -7,7 +7,8 @@ FP64 oracle at full size:
   symmetric model with the gradient in all 42 exchangeabilities, the
   asymmetric model with the height, boundary and branch-rate gradients, and
   64 replicate traits;
-* amino-acid-shaped data: K = 20, 3 epochs, 200 taxa, 2,000 sites.
+* amino-acid-shaped data: K = 20, 3 epochs, 200 taxa, 2,000 sites (also on
+  the 32-wide tensor-core tiles).
 
 Tolerances as in the other parity tests: lnL 1e-10 (FP64) and 1e-5 (FP32)
 relative; gradients 1e-9 and 1e-4 max-norm relative; branch matrices 1e-12.
@@ -17,12 +18,12 @@ import pytest
 
 import oracle
 import synth
-from paper_1309_3075_b300.binding import EPOCH_FP32, EPOCH_FP64, EpochLikelihood
+from paper_1309_3075_b300.binding import EPOCH_FP32, EPOCH_FP32_TC, EPOCH_FP64, EpochLikelihood
 
 pytestmark = pytest.mark.gpu
 
-LNL_TOL = {EPOCH_FP64: 1e-10, EPOCH_FP32: 1e-5}
-GRAD_TOL = {EPOCH_FP64: 1e-9, EPOCH_FP32: 1e-4}
+LNL_TOL = {EPOCH_FP64: 1e-10, EPOCH_FP32: 1e-5, EPOCH_FP32_TC: 1e-5}
+GRAD_TOL = {EPOCH_FP64: 1e-9, EPOCH_FP32: 1e-4, EPOCH_FP32_TC: 1e-4}
 
 
 @pytest.fixture(scope="module", autouse=True)
@@ -101,6 +102,6 @@ def test_seasonal_replicate_traits_three_processes(prec):
     check(w, prec)
 
 
-@pytest.mark.parametrize("prec", [EPOCH_FP64, EPOCH_FP32])
+@pytest.mark.parametrize("prec", [EPOCH_FP64, EPOCH_FP32, EPOCH_FP32_TC])
 def test_amino_acid_20_states(prec):
     check(synth.amino_acid(), prec)
