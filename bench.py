@@ -236,10 +236,10 @@ def run_ours(args, w, cfg, rank, world):
     dev = rank % max(torch.cuda.device_count(), 1)
     torch.cuda.set_device(dev)
     stream = torch.cuda.Stream()
-    # above 16 states the contractions run on the tensor cores (TF32 x 3 split,
-    # tiles 32 or 64 states wide): faster than the SIMT kernels at every
-    # measured K from 17 to 64
-    prec = EPOCH_FP32_TC if w.K > 16 else EPOCH_FP32
+    # above 8 states the contractions run on the tensor cores (TF32 x 3 split,
+    # tiles 16, 32 or 64 states wide): faster than the SIMT kernels at every
+    # measured K from 9 to 64
+    prec = EPOCH_FP32_TC if w.K > 8 else EPOCH_FP32
     lik = EpochLikelihood(w, precision=prec, cuda_stream=stream.cuda_stream)
     nn = 2 * w.n_taxa - 1
 

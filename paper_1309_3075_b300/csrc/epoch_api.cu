@@ -420,9 +420,10 @@ epoch_status epoch_create(epoch_ctx **out, int states, int n_epochs, const doubl
   Dims &d = c->d;
   d.K = states;
   d.Kp = (states + 3) / 4 * 4;
-  // the tensor-core tiles are 64 or 32 states wide: pad to the tile width
+  // the tensor-core tiles are 64, 32 or 16 states wide: pad to the tile width
   if (precision == EPOCH_FP32_TC && states > 32) d.Kp = 64;
   if (precision == EPOCH_FP32_TC && states > 16 && states <= 32) d.Kp = 32;
+  if (precision == EPOCH_FP32_TC && states > 8 && states <= 16) d.Kp = 16;
   d.KK = states * states;
   d.n_masks = 0;
   d.NR = states + 1;

@@ -1,10 +1,10 @@
 // k_tc.cu -- tensor-core contractions of the larger state spaces (codon
-// K = 61, amino acids K = 20, traits; 16 < K <= 64): tcgen05.mma with the
+// K = 61, amino acids K = 20, traits; 8 < K <= 64): tcgen05.mma with the
 // accumulator in tensor memory.
 //
 // A partial vector of one (category, pattern) is a row of KW floats (K
-// padded with zeros; KW = 64 for 32 < K <= 64, 32 for 16 < K <= 32), so a
-// branch applied to 128 patterns is one tile product
+// padded with zeros; KW = 64 for 32 < K <= 64, 32 for 16 < K <= 32, 16 for
+// 8 < K <= 16), so a branch applied to 128 patterns is one tile product
 //     D[128 x KW] = A[128 x KW] * B^T,   B[n][k] = P[n][k] (S = P L)
 //                                        or  B[n][k] = P[k][n] (U = P^T X),
 // run as tcgen05.mma kind::tf32 (M = 128, N = KW, K = 8 per instruction).
@@ -107,11 +107,14 @@ __global__ void k_tc_prep(Dims d, const double *__restrict__ P64, const int *__r
   }
 }
 
-// Shared memory of a stage: one operand pair (A hi, A lo, B hi, B lo); two
-// stages for the pipelined variant.
+// Shared memory: nst stages of one operand pair each (A hi, A lo, B hi, B lo),
+// and at least the two epilogue row buffers that reuse them, plus room to
+// align the start to 1024 bytes.
 template <int KW>
 __host__ __device__ constexpr size_t tc_smem(int nst) {
-  return sizeof(float) * nst * Tw<KW>::stage + 1024;
+  return sizeof(float) * (nst * Tw<KW>::stage > 2 * Tw<KW>::buf ? nst * Tw<KW>::stage
+                                                                  : 2 * Tw<KW>::buf) +
+         1024;
 }
 
 // An A tile in registers.  A warp's load instruction covers 8 rows x 4
@@ -253,13 +256,30 @@ __device__ __forceinline__ void tc_ld32(uint32_t taddr, int col, float *out) {
 #pragma unroll
   for (int j = 0; j < 32; j++) out[j] = __uint_as_float(v[j]);
 }
+// 16 columns of the thread's TMEM lane, one load and one wait.
+__device__ __forceinline__ void tc_ld16(uint32_t taddr, int col, float *out) {
+  uint32_t v[16];
+  const uint32_t a = taddr + ((uint32_t)(32 * (threadIdx.x >> 5)) << 16) + col;
+  asm volatile(
+      "tcgen05.ld.sync.aligned.32x32b.x16.b32 {%0,%1,%2,%3,%4,%5,%6,%7,%8,%9,%10,%11,%12,"
+      "%13,%14,%15}, [%16];"
+      : "=r"(v[0]), "=r"(v[1]), "=r"(v[2]), "=r"(v[3]), "=r"(v[4]), "=r"(v[5]), "=r"(v[6]),
+        "=r"(v[7]), "=r"(v[8]), "=r"(v[9]), "=r"(v[10]), "=r"(v[11]), "=r"(v[12]), "=r"(v[13]),
+        "=r"(v[14]), "=r"(v[15])
+      : "r"(a));
+  asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
+#pragma unroll
+  for (int j = 0; j < 16; j++) out[j] = __uint_as_float(v[j]);
+}
 // KW columns of the thread's TMEM lane.
 template <int KW>
 __device__ __forceinline__ void tc_ld(uint32_t taddr, int col, float *out) {
   if constexpr (KW == 64)
     tc_ld64(taddr, col, out);
-  else
+  else if constexpr (KW == 32)
     tc_ld32(taddr, col, out);
+  else
+    tc_ld16(taddr, col, out);
 }
 
 // Epilogue row buffers in the (then free) stage memory: 128 rows of KW
@@ -616,9 +636,11 @@ __global__ void __launch_bounds__(kTcThr) k_tc_pre_x(
 
 }  // namespace
 
-// Tile width 64 (32 < K <= 64) or 32 (16 < K <= 32): the padded row length.
+// Tile width 64 (32 < K <= 64), 32 (16 < K <= 32) or 16 (8 < K <= 16): the
+// padded row length.
 bool tc_path(const epoch_ctx *c) {
-  return c->precision == EPOCH_FP32_TC && !fast_k4(c) && (c->d.Kp == 64 || c->d.Kp == 32) &&
+  const int kp = c->d.Kp;
+  return c->precision == EPOCH_FP32_TC && !fast_k4(c) && (kp == 64 || kp == 32 || kp == 16) &&
          c->d.C <= 4;
 }
 
@@ -674,7 +696,9 @@ void tc_pre_u(epoch_ctx *c, int level) {
 }  // namespace
 
 cudaError_t launch_tc_post(epoch_ctx *c, int level) {
-  cudaError_t e = c->d.Kp == 64 ? tc_post<64>(c, level) : tc_post<32>(c, level);
+  const int kp = c->d.Kp;
+  cudaError_t e = kp == 64 ? tc_post<64>(c, level)
+                           : (kp == 32 ? tc_post<32>(c, level) : tc_post<16>(c, level));
   c->launches++;
   return e != cudaSuccess ? e : cudaGetLastError();
 }
@@ -682,8 +706,10 @@ cudaError_t launch_tc_post(epoch_ctx *c, int level) {
 cudaError_t launch_tc_pre_x(epoch_ctx *c, int level, int root) {
   if (c->d.Kp == 64)
     tc_pre_x<64>(c, level, root);
-  else
+  else if (c->d.Kp == 32)
     tc_pre_x<32>(c, level, root);
+  else
+    tc_pre_x<16>(c, level, root);
   c->launches++;
   return cudaGetLastError();
 }
@@ -692,8 +718,10 @@ cudaError_t launch_tc_prep(epoch_ctx *c) {
   const Dims &d = c->d;
   if (d.Kp == 64)
     k_tc_prep<64><<<d.nn * d.C, 256, 0, c->stream>>>(d, c->d_P64, c->d_parent, c->d_tcB);
-  else
+  else if (d.Kp == 32)
     k_tc_prep<32><<<d.nn * d.C, 256, 0, c->stream>>>(d, c->d_P64, c->d_parent, c->d_tcB);
+  else
+    k_tc_prep<16><<<d.nn * d.C, 256, 0, c->stream>>>(d, c->d_P64, c->d_parent, c->d_tcB);
   c->launches++;
   return cudaGetLastError();
 }
@@ -701,8 +729,10 @@ cudaError_t launch_tc_prep(epoch_ctx *c) {
 cudaError_t launch_tc_pre_u(epoch_ctx *c, int level) {
   if (c->d.Kp == 64)
     tc_pre_u<64>(c, level);
-  else
+  else if (c->d.Kp == 32)
     tc_pre_u<32>(c, level);
+  else
+    tc_pre_u<16>(c, level);
   c->launches++;
   return cudaGetLastError();
 }

@@ -131,11 +131,12 @@ def test_other_state_counts(prec, K):
 
 
 @pytest.mark.parametrize("prec", [EPOCH_FP32_TC])
-@pytest.mark.parametrize("K,P", [(50, 300), (64, 129), (20, 257), (32, 130), (17, 140)])
+@pytest.mark.parametrize("K,P", [(50, 300), (64, 129), (20, 257), (32, 130), (17, 140),
+                                 (9, 200), (16, 131)])
 def test_tensor_core_large_state_spaces(prec, K, P):
     """Tensor-core tiles: 64 wide for K = 50 asymmetric traits and K = 64 (no
-    padding), 32 wide for K = 17, 20 and 32; pattern counts that leave a
-    ragged last tile of 128."""
+    padding), 32 wide for K = 17, 20 and 32, 16 wide for K = 9 and 16; pattern
+    counts that leave a ragged last tile of 128."""
     w = synth.tiny_tree_workload(320 + K, K=K, n_taxa=12, n_sites=P, n_epochs=3, n_cat=2,
                                  reversible=(K != 50), missing_frac=0.05)
     check_lnl(w, prec)
