@@ -512,13 +512,19 @@ __global__ void k_branch_matrices(Dims d, const int *__restrict__ nseg,
       const double *Vs = V + (size_t)s * KK, *Vi = Vinv + (size_t)s * KK;
       for (int i = tid; i < K; i += nt) ev[i] = exp(tau * lam[(size_t)s * K + i]);
       __syncthreads();
+      // V diag(ev) and V^-1 staged in shared memory (Y and B are free here)
+      for (int idx = tid; idx < KK; idx += nt) {
+        Y[idx] = Vs[idx] * ev[idx % K];
+        B[idx] = Vi[idx];
+      }
+      __syncthreads();
       // W = V diag(ev) V^-1; transition probabilities are >= 0, so the
       // rounding-level negatives of the eigen form are cut at 0 (keeps
       // every partial likelihood >= 0)
       for (int idx = tid; idx < KK; idx += nt) {
         int i = idx / K, j = idx % K;
         double acc = 0.0;
-        for (int m = 0; m < K; m++) acc += Vs[i * K + m] * ev[m] * Vi[m * K + j];
+        for (int m = 0; m < K; m++) acc += Y[i * K + m] * B[m * K + j];
         W[idx] = fmax(acc, 0.0);
       }
       __syncthreads();
