@@ -190,6 +190,28 @@ def partials_bytes(w):
     return total
 
 
+def adjoint_bytes(w):
+    """Bytes the gradient pass must move in this design: the outside partial
+    U of every internal non-root node written once (by its parent's level)
+    and read once (by its own), every stored partial read once more, tip
+    codes, exponents and pattern weights once per internal node; the G tile
+    sums and the chain rule are small.  At K = 4 the cherries' partials are
+    not stored (recomputed from their tips' codes)."""
+    N, P, C = w.n_taxa, w.n_patterns, w.n_categories
+    nn = 2 * N - 1
+    kp = 4 if w.K <= 4 else (64 if w.K > 32 else (w.K + 3) // 4 * 4)
+    vec = 4 * kp * C * P
+    parent = np.asarray(w.parent)
+    kids = [[] for _ in range(nn)]
+    for v in range(nn):
+        if parent[v] >= 0:
+            kids[parent[v]].append(v)
+    root = int(np.where(parent < 0)[0][0])
+    cherry = [u >= N and u != root and all(k < N for k in kids[u]) for u in range(nn)]
+    stored = sum(1 for u in range(N, nn) if not (w.K == 4 and cherry[u]))
+    return (N - 2) * 2 * vec + stored * vec + N * P + (N - 1) * 6 * P
+
+
 def survey_bytes(w):
     """The same pass counted with every internal node stored (no cherry
     tables): the reference figure for this pass."""
@@ -279,6 +301,22 @@ def run_ours(args, w, cfg, rank, world):
     torch.cuda.synchronize()
     part_ms = e0.elapsed_time(e1) / reps
     pbytes = partials_bytes(w)
+
+    # ---- the gradient pass alone (pre-order adjoint, G, chain rule) --------
+    # epoch_gradient after the partials of the same inputs; its enqueued
+    # kernels sit between the events (it reads the gradient back at the end)
+    gr = max(5, min(args.steps, 50))
+    grad_ms = 0.0
+    for _ in range(gr + 2):
+        binding.epoch_update_partials(lik.ctx)
+        g0, g1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        g0.record(stream)
+        binding.epoch_gradient(lik.ctx, nn, w.n_epochs, lik.n_params)
+        g1.record(stream)
+        torch.cuda.synchronize()
+        if _ >= 2:
+            grad_ms += g0.elapsed_time(g1) / gr
+    abytes = adjoint_bytes(w)
     achieved = pbytes / (part_ms * 1e-3) / 1e9
     peak, peak_kind = hbm_peak()
 
@@ -379,6 +417,12 @@ def run_ours(args, w, cfg, rank, world):
                      "kernel": "partials pass (post-order pruning + rescaling + root)",
                      "effective_gbs_all_nodes_stored": survey_bytes(w) / (part_ms * 1e-3) / 1e9,
                      "ms_per_launch": part_ms, "algorithmic_bytes": int(pbytes)},
+        "roofline_gradient_pass": {
+            "bound": "hbm", "achieved": abytes / (grad_ms * 1e-3) / 1e9, "peak": peak,
+            "unit": "GB/s", "frac": abytes / (grad_ms * 1e-3) / 1e9 / peak,
+            "peak_source": peak_kind, "ms_per_launch": grad_ms, "algorithmic_bytes": int(abytes),
+            "kernel": "gradient pass (pre-order adjoint + G + chain rule; includes the "
+                      "read-back of the gradient)"},
         "fp64_gpu": {"value": 1e3 / fp64_ms, "unit": UNIT, "ms_per_step": fp64_ms,
                      "lnL_rel_err_fp32_vs_fp64": rel_err, "grad_rel_err_fp32_vs_fp64": grad_err,
                      "speedup": fp64_ms / ms_step},
