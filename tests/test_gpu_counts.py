@@ -118,3 +118,37 @@ def test_ancestral_states_match_oracle(prec, make):
     assert got.shape == ref.shape
     assert np.abs(got - ref).max() <= ANC_TOL[prec], (w.name, np.abs(got - ref).max())
     assert np.allclose(got.sum(-1), 1.0, atol=1e-12)
+
+
+@pytest.mark.parametrize("prec", [EPOCH_FP64, EPOCH_FP32])
+def test_two_taxa_and_single_epoch_edges(prec):
+    """Two taxa (the root is the only internal node, on the K = 4 path the
+    root's own level) and a single epoch: ancestral states of the root and
+    counts on both branches against the oracle."""
+    w = synth.tiny_tree_workload(431, K=4, n_taxa=2, n_sites=9, n_epochs=1, n_cat=2, dated=True)
+    lik = EpochLikelihood(w, precision=prec)
+    try:
+        lik.evaluate(with_gradient=True)
+        anc = lik.ancestral_states()
+        pb, pe = lik.expected_counts()
+    finally:
+        lik.close()
+    assert anc.shape == (1, w.n_patterns, 4) and pe.shape == (1, 4, 4)
+    assert np.abs(anc - oracle.ancestral_states(w)).max() <= ANC_TOL[prec]
+    rb, re = oracle.expected_counts(w)
+    assert np.abs(pb - rb).max() <= TOL[prec] * max(np.abs(rb).max(), 1e-300)
+    assert np.abs(pe - re).max() <= TOL[prec] * max(np.abs(re).max(), 1e-300)
+
+
+def test_tensor_core_request_with_many_categories_uses_simt():
+    """EPOCH_FP32_TC with more categories than the tensor-core kernels take
+    (C = 6 > 4) runs the SIMT kernels; results match the oracle."""
+    w = synth.tiny_tree_workload(432, K=20, n_taxa=10, n_sites=150, n_epochs=2, n_cat=6)
+    lik = EpochLikelihood(w, precision=EPOCH_FP32_TC)
+    try:
+        lnl, g = lik.evaluate(with_gradient=True)
+    finally:
+        lik.close()
+    ref = oracle.gradient(w)
+    assert abs(lnl - ref["lnL"]) <= 1e-5 * abs(ref["lnL"])
+    assert np.abs(g["heights"] - ref["heights"]).max() <= 1e-4 * max(np.abs(ref["heights"]).max(), 1.0)
