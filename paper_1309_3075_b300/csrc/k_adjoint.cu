@@ -191,6 +191,16 @@ __device__ T bsum(T x, T *red) {
 
 __device__ __forceinline__ double t_expm1(double x) { return expm1(x); }
 __device__ __forceinline__ float t_expm1(float x) { return expm1f(x); }
+// e^{tau lambda} in the precision of the path (FP32: single-precision exp
+// of the rounded exponent; each dependent FP64 instruction costs tens of
+// cycles on this part, and these exponentials sit on the chain rule's
+// critical path)
+template <typename T>
+__device__ __forceinline__ T t_exp(double x);
+template <>
+__device__ __forceinline__ double t_exp<double>(double x) { return exp(x); }
+template <>
+__device__ __forceinline__ float t_exp<float>(double x) { return expf((float)x); }
 
 // Segment exponential E = exp(tau Q_s) into Eo (eigen path or
 // uniformisation); scratch W, Y, B.
@@ -199,7 +209,7 @@ __device__ void seg_exp(const Dims &d, int s, double tau, const double *lam, con
                         const double *Vinv, const double *Qn, T *Eo, T *W, T *Y, T *Bm, T *ev) {
   const int K = d.K, KK = d.KK;
   if (d.reversible) {
-    for (int i = threadIdx.x; i < K; i += blockDim.x) ev[i] = (T)exp(tau * lam[(size_t)s * K + i]);
+    for (int i = threadIdx.x; i < K; i += blockDim.x) ev[i] = t_exp<T>(tau * lam[(size_t)s * K + i]);
     __syncthreads();
     const double *Vs = V + (size_t)s * KK, *Vi = Vinv + (size_t)s * KK;
     if (sizeof(T) == sizeof(float) && blockDim.x == 256 && K > 16) {
@@ -329,7 +339,7 @@ __global__ void k_grad_branch(Dims d, const double *__restrict__ G, const int *_
       __syncthreads();
       mm<T>(d, Bm, Y, W, true, false);  // W = V^T Y
       for (int i = threadIdx.x; i < K; i += blockDim.x)
-        ev[i] = (T)exp(tau * lam[(size_t)s * K + i]);
+        ev[i] = t_exp<T>(tau * lam[(size_t)s * K + i]);
       __syncthreads();
       T part = 0;
       for (int i = threadIdx.x; i < K; i += blockDim.x)
