@@ -212,8 +212,9 @@ __device__ void seg_exp(const Dims &d, int s, double tau, const double *lam, con
     for (int i = threadIdx.x; i < K; i += blockDim.x) ev[i] = t_exp<T>(tau * lam[(size_t)s * K + i]);
     __syncthreads();
     const double *Vs = V + (size_t)s * KK, *Vi = Vinv + (size_t)s * KK;
-    if (sizeof(T) == sizeof(float) && blockDim.x == 256 && K > 16) {
-      // E = (V diag(ev)) V^-1 through shared memory and the tiled product
+    if (sizeof(T) == sizeof(float)) {
+      // E = (V diag(ev)) V^-1 through shared memory (the tiled product for
+      // large K; one batch of global loads for small K)
       for (int idx = threadIdx.x; idx < KK; idx += blockDim.x) {
         W[idx] = (T)Vs[idx] * ev[idx % K];
         Y[idx] = (T)Vi[idx];
