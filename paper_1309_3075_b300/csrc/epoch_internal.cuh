@@ -230,9 +230,11 @@ inline bool fast_k4(const epoch_ctx *c) {
 // adjoint kernel) of every internal node, elements of es bytes.
 constexpr int kSmallMaxPatterns = 64;
 constexpr size_t kSmallMaxSmem = 200 * 1024;
-inline size_t small_smem_bytes(const Dims &d, int N, size_t es, bool with_pre) {
+inline size_t small_smem_bytes(const Dims &d, int N, size_t es, bool with_pre,
+                               bool tables = false) {
   const size_t nv = (size_t)(N - 1) * d.C * d.Kp;
-  return es * nv * (with_pre ? 2 : 1) + sizeof(int) * 5 * N + N;
+  const size_t nt = tables ? (size_t)(N - 1) * d.C * d.KK + (size_t)N * d.C * d.K : 0;
+  return es * (nv * (with_pre ? 2 : 1) + nt) + sizeof(int) * 5 * N + N;
 }
 inline bool small_path(const epoch_ctx *c) {
   const size_t es = c->precision == EPOCH_FP64 ? sizeof(double) : sizeof(float);

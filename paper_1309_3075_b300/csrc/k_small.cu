@@ -25,10 +25,12 @@ constexpr int kSmallThreads = 1024;
 
 // Shared-memory image of one pattern's tree: topology (level order), tip
 // codes, exponents and the partials of every internal node, so that a level
-// waits on global memory only for its branch-matrix rows (layout sized by
-// small_smem_bytes).
+// waits on global memory only for its branch-matrix rows; and, when they fit
+// too, those rows as well (layout sized by small_smem_bytes).
 template <typename T>
 struct SmallSmem {
+  T *mat;       // [N-1][C][K][K] P of the branch above each internal node (tables)
+  T *tiprow;    // [N][C][K] the P row set a tip's code selects (tables)
   T *part;      // [N-1][C*Kp] post-order partials of this pattern
   T *pre;       // [N-1][C*Kp] outside partials (pre-order kernel only)
   int *nodes;   // [N-1] internal nodes, level-ascending
@@ -36,9 +38,13 @@ struct SmallSmem {
   int *escale;  // [N-1] exponents of this pattern
   int *off;     // [L+1] level offsets into nodes (L <= N-1)
   uint8_t *code;  // [N] tip codes of this pattern
-  __device__ SmallSmem(unsigned char *raw, const Dims &d, bool with_pre) {
+  bool tabs;
+  __device__ SmallSmem(unsigned char *raw, const Dims &d, bool with_pre, bool tables)
+      : tabs(tables) {
     const size_t nv = (size_t)(d.N - 1) * d.C * d.Kp;
-    part = reinterpret_cast<T *>(raw);
+    mat = reinterpret_cast<T *>(raw);
+    tiprow = mat + (tables ? (size_t)(d.N - 1) * d.C * d.KK : 0);
+    part = tiprow + (tables ? (size_t)d.N * d.C * d.K : 0);
     pre = part + nv;
     nodes = reinterpret_cast<int *>(pre + (with_pre ? nv : 0));
     child = nodes + (d.N - 1);
@@ -63,15 +69,39 @@ __device__ void stage_topology(const Dims &d, SmallSmem<T> &sm, const int *__res
   for (int v = threadIdx.x; v < d.N; v += blockDim.x) sm.code[v] = tips[(size_t)v * d.Pp + p];
 }
 
+// The branch matrices every level will read, in one batch of loads (after
+// stage_topology and a barrier: the tip rows depend on the codes).
+template <typename T>
+__device__ void stage_tables(const Dims &d, SmallSmem<T> &sm, const BranchTable<T> &bt) {
+  if (!sm.tabs) return;
+  const int CKK = d.C * d.KK, CK = d.C * d.K;
+  for (int e = threadIdx.x; e < (d.N - 1) * CKK; e += blockDim.x) {
+    const int slot = e / CKK, r = e % CKK, c = r / d.KK, ij = r % d.KK;
+    sm.mat[e] = bt.mat(d, slot + d.N, c, ij / d.K, ij % d.K);
+  }
+  for (int e = threadIdx.x; e < d.N * CK; e += blockDim.x) {
+    const int x = e / CK, r = e % CK;
+    sm.tiprow[e] = bt.tip(d, x, r / d.K, r % d.K, sm.code[x]);
+  }
+}
+// P_x[i][j] for an internal node x (from the tables when they are staged)
+template <typename T>
+__device__ __forceinline__ T mat_sm(const Dims &d, const BranchTable<T> &bt,
+                                    const SmallSmem<T> &sm, int x, int c, int i, int j) {
+  if (sm.tabs) return sm.mat[(((size_t)(x - d.N) * d.C + c) * d.K + i) * d.K + j];
+  return bt.mat(d, x, c, i, j);
+}
+
 // S_x(c, i) = sum_j P_x[i][j] L_x(c, j) with L_x from shared memory (tip:
 // the table row of its code).
 template <typename T>
 __device__ __forceinline__ T child_factor_sm(const Dims &d, const BranchTable<T> &bt,
                                              const SmallSmem<T> &sm, int x, int c, int i) {
-  if (x < d.N) return bt.tip(d, x, c, i, sm.code[x]);
+  if (x < d.N)
+    return sm.tabs ? sm.tiprow[((size_t)x * d.C + c) * d.K + i] : bt.tip(d, x, c, i, sm.code[x]);
   const T *L = sm.part + ((size_t)(x - d.N) * d.C + c) * d.Kp;
   T s = 0;
-  for (int j = 0; j < d.K; j++) s += bt.mat(d, x, c, i, j) * L[j];
+  for (int j = 0; j < d.K; j++) s += mat_sm(d, bt, sm, x, c, i, j) * L[j];
   return s;
 }
 
@@ -85,14 +115,16 @@ __global__ void __launch_bounds__(kSmallThreads)
                  T *__restrict__ part, int16_t *__restrict__ scale,
                  const uint8_t *__restrict__ tips, int gsz, const double *__restrict__ pi,
                  const double *__restrict__ catw, double *__restrict__ site_lnl,
-                 double *__restrict__ site_inv, int *__restrict__ status) {
+                 double *__restrict__ site_inv, int *__restrict__ status, int tables) {
   extern __shared__ __align__(16) unsigned char smraw[];
   __shared__ int s_esum;
   __shared__ double s_site;
   const int p = blockIdx.x;
-  SmallSmem<T> sm(smraw, d, false);
+  SmallSmem<T> sm(smraw, d, false, tables != 0);
   stage_topology<T>(d, sm, lvl_nodes, lvl_off, L, child, tips, p);
   if (threadIdx.x == 0) s_esum = 0;
+  __syncthreads();
+  stage_tables<T>(d, sm, bt);
   __syncthreads();
   const int lane_g = threadIdx.x & (gsz - 1), grp = threadIdx.x / gsz;
   const int ngrp = blockDim.x / gsz;
@@ -188,11 +220,13 @@ __global__ void __launch_bounds__(kSmallThreads)
                 const uint8_t *__restrict__ tips, const unsigned long long *__restrict__ masks,
                 const double *__restrict__ pi, const double *__restrict__ catw,
                 const double *__restrict__ site_inv, const double *__restrict__ pw, int gsz,
-                T *__restrict__ Gs) {
+                T *__restrict__ Gs, int tables) {
   extern __shared__ __align__(16) unsigned char smraw[];
   const int p = blockIdx.x;
-  SmallSmem<T> sm(smraw, d, true);
+  SmallSmem<T> sm(smraw, d, true, tables != 0);
   stage_topology<T>(d, sm, lvl_nodes, lvl_off, L, child, tips, p);
+  __syncthreads();
+  stage_tables<T>(d, sm, bt);
   const int CKp = d.C * d.Kp;
   for (int e = threadIdx.x; e < (d.N - 1) * CKp; e += blockDim.x) {
     const int slot = e / CKp, r = e % CKp;  // r = c * Kp + i
@@ -230,7 +264,7 @@ __global__ void __launch_bounds__(kSmallThreads)
       T U = 0;
       for (int k = 0; k < d.K; k++) {
         const T xk = __shfl_sync(0xffffffffu, X, c * d.Kp + k, gsz);
-        if (inner && act) U += bt.mat(d, v, c, k, i) * xk;
+        if (inner && act) U += mat_sm(d, bt, sm, v, c, k, i) * xk;
       }
       if (inner && holds) {  // read by the next level; kept for the ancestral states
         sm.pre[((size_t)(v - d.N) * d.C + c) * d.Kp + i] = U;
@@ -269,21 +303,24 @@ cudaError_t launch_small_post(epoch_ctx *c) {
   const Dims &d = c->d;
   const int L = (int)c->h_level_off.size() - 1;
   const int g = group_size(d);
-  const size_t smem = small_smem_bytes(d, d.N, sizeof(float) * (c->precision == EPOCH_FP64 ? 2 : 1), false);
+  const size_t es = c->precision == EPOCH_FP64 ? sizeof(double) : sizeof(float);
+  // stage the branch matrices too when the pre-order kernel's image fits
+  const int tabs = small_smem_bytes(d, d.N, es, true, true) <= kSmallMaxSmem ? 1 : 0;
+  const size_t smem = small_smem_bytes(d, d.N, es, false, tabs != 0);
   if (c->precision == EPOCH_FP64) {
     cudaFuncSetAttribute(k_small_post<double>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                          (int)smem);
     k_small_post<double><<<d.P, kSmallThreads, smem, c->stream>>>(
         d, BranchTable<double>{c->d_P64, c->d_masks}, c->d_level_nodes, c->d_level_off, L,
         c->d_child, (double *)c->d_part, c->d_scale, c->d_tips, g, c->d_pi, c->d_catw,
-        c->d_site_lnl, c->d_site_inv, c->d_status);
+        c->d_site_lnl, c->d_site_inv, c->d_status, tabs);
   } else {
     cudaFuncSetAttribute(k_small_post<float>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                          (int)smem);
     k_small_post<float><<<d.P, kSmallThreads, smem, c->stream>>>(
         d, BranchTable<float>{c->d_PT32, c->d_masks}, c->d_level_nodes, c->d_level_off, L,
         c->d_child, (float *)c->d_part, c->d_scale, c->d_tips, g, c->d_pi, c->d_catw,
-        c->d_site_lnl, c->d_site_inv, c->d_status);
+        c->d_site_lnl, c->d_site_inv, c->d_status, tabs);
   }
   k_small_lnl<<<1, 256, 0, c->stream>>>(d.P, c->d_pw, c->d_site_lnl, c->d_lnl);
   c->launches += 2;
@@ -294,21 +331,23 @@ cudaError_t launch_small_pre(epoch_ctx *c) {
   const Dims &d = c->d;
   const int L = (int)c->h_level_off.size() - 1;
   const int g = group_size(d), root = root_node(c);
-  const size_t smem = small_smem_bytes(d, d.N, sizeof(float) * (c->precision == EPOCH_FP64 ? 2 : 1), true);
+  const size_t es = c->precision == EPOCH_FP64 ? sizeof(double) : sizeof(float);
+  const int tabs = small_smem_bytes(d, d.N, es, true, true) <= kSmallMaxSmem ? 1 : 0;
+  const size_t smem = small_smem_bytes(d, d.N, es, true, tabs != 0);
   if (c->precision == EPOCH_FP64) {
     cudaFuncSetAttribute(k_small_pre<double>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                          (int)smem);
     k_small_pre<double><<<d.P, kSmallThreads, smem, c->stream>>>(
         d, BranchTable<double>{c->d_P64, c->d_masks}, c->d_level_nodes, c->d_level_off, L,
         c->d_child, root, (const double *)c->d_part, (double *)c->d_pre, c->d_scale, c->d_tips,
-        c->d_masks, c->d_pi, c->d_catw, c->d_site_inv, c->d_pw, g, (double *)c->d_Gpart);
+        c->d_masks, c->d_pi, c->d_catw, c->d_site_inv, c->d_pw, g, (double *)c->d_Gpart, tabs);
   } else {
     cudaFuncSetAttribute(k_small_pre<float>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                          (int)smem);
     k_small_pre<float><<<d.P, kSmallThreads, smem, c->stream>>>(
         d, BranchTable<float>{c->d_PT32, c->d_masks}, c->d_level_nodes, c->d_level_off, L,
         c->d_child, root, (const float *)c->d_part, (float *)c->d_pre, c->d_scale, c->d_tips,
-        c->d_masks, c->d_pi, c->d_catw, c->d_site_inv, c->d_pw, g, (float *)c->d_Gpart);
+        c->d_masks, c->d_pi, c->d_catw, c->d_site_inv, c->d_pw, g, (float *)c->d_Gpart, tabs);
   }
   c->launches++;
   return cudaGetLastError();
