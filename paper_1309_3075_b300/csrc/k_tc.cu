@@ -107,13 +107,12 @@ __global__ void k_tc_prep(Dims d, const double *__restrict__ P64, const int *__r
   }
 }
 
-// Shared memory: nst stages of one operand pair each (A hi, A lo, B hi, B lo),
-// and at least the two epilogue row buffers that reuse them, plus room to
-// align the start to 1024 bytes.
+// Shared memory: one stage (A hi, A lo, B hi, B lo), and at least the two
+// epilogue row buffers that reuse it, plus room to align the start to 1024
+// bytes.
 template <int KW>
-__host__ __device__ constexpr size_t tc_smem(int nst) {
-  return sizeof(float) * (nst * Tw<KW>::stage > 2 * Tw<KW>::buf ? nst * Tw<KW>::stage
-                                                                  : 2 * Tw<KW>::buf) +
+__host__ __device__ constexpr size_t tc_smem() {
+  return sizeof(float) * (Tw<KW>::stage > 2 * Tw<KW>::buf ? Tw<KW>::stage : 2 * Tw<KW>::buf) +
          1024;
 }
 
@@ -341,53 +340,38 @@ __device__ __forceinline__ void row_get(const float *src, float (&v)[KW]) {
 
 // Tile products D_j[128 x KW] = A_j B_j^T into TMEM columns col_j, j < n,
 // for one tile of 128 rows (A rows lda floats apart; rows >= `rows` read as
-// zero).  item(j, A, B, col) names the operands.  Every thread takes part.
-// NST = 2 (two shared-memory stages): while the tensor cores run item j, item
-// j+1's A is loaded into registers and its B copied by cp.async.  NST = 1
-// (one stage, so that two CTAs fit on an SM): item j+1's A is loaded into
-// registers during item j's MMA, its B once that MMA has completed.
-// Returns false when an MMA did not complete within the wait bound; nothing
-// is then left in flight but that MMA.
-template <int NST, int KW, class Item>
-__device__ bool tc_pipeline(int n, int lda, int rows, Item item, float *sm, uint32_t taddr,
+// zero), through one shared-memory stage so that two CTAs fit on an SM:
+// item j+1's A is loaded into registers during item j's MMA, its B (by
+// cp.async) once that MMA has completed.  item(j, A, B, col) names the
+// operands.  Every thread takes part.  (Two stages with one CTA per SM were
+// measured slower on the wide levels.)  Returns false when an MMA did not
+// complete within the wait bound; nothing is then left in flight but that
+// MMA.
+template <int KW, class Item>
+__device__ bool tc_pipeline(int n, int lda, int rows, Item item, float *st, uint32_t taddr,
                             uint64_t *mbar, uint32_t *ph) {
-  constexpr int kStageFloats = Tw<KW>::stage;
   if (n <= 0) return true;
   ATile<KW> ra;
   const float *A, *B;
   uint32_t col;
   item(0, A, B, col);
-  tc_async_B<KW>(B, sm);
+  tc_async_B<KW>(B, st);
   tc_load_A<KW>(A, lda, rows, ra);
   for (int j = 0; j < n; j++) {
-    float *st = sm + (NST == 2 ? (j & 1) * kStageFloats : 0);
-    if (NST == 1 && j >= 1) {  // the single stage is free once MMA j-1 has completed
+    if (j >= 1) {  // the stage is free once MMA j-1 has completed
       if (!tc_wait(&mbar[(j - 1) & 1], ph[(j - 1) & 1])) {
         asm volatile("cp.async.wait_all;" ::: "memory");
         return false;
       }
       tc_async_B<KW>(B, st);
     }
-    tc_store_A<KW>(ra, st);  // two stages: stage j&1 is free, MMA j-2 was waited for at j-1
+    tc_store_A<KW>(ra, st);
     const uint32_t colj = col;
     if (j + 1 < n) {
       item(j + 1, A, B, col);
       tc_load_A<KW>(A, lda, rows, ra);  // in flight during this item's MMA
     }
-    if (NST == 2) {
-      if (j >= 1 && !tc_wait(&mbar[(j - 1) & 1], ph[(j - 1) & 1])) {
-        asm volatile("cp.async.wait_all;" ::: "memory");
-        return false;
-      }
-      if (j + 1 < n) {  // MMA j-1 has released stage (j+1)&1
-        tc_async_B<KW>(B, sm + ((j + 1) & 1) * kStageFloats);
-        asm volatile("cp.async.wait_group 1;" ::: "memory");  // B of item j has landed
-      } else {
-        asm volatile("cp.async.wait_group 0;" ::: "memory");
-      }
-    } else {
-      asm volatile("cp.async.wait_group 0;" ::: "memory");
-    }
+    asm volatile("cp.async.wait_group 0;" ::: "memory");
     tc_sync_staged();
     tc_mma<KW>(taddr + colj, st, &mbar[j & 1]);
   }
@@ -448,7 +432,7 @@ __global__ void __launch_bounds__(kTcThr) k_tc_pre_u(Dims d, const int *__restri
     B = tcB + ((size_t)v * d.C + c) * 4 * Tw<KW>::B + 2 * Tw<KW>::B;  // pre hi | lo
     col = 0;
   };
-  if (!tc_pipeline<1, KW>(1, d.Kp, rows, item, sm, taddr, mbar, ph)) {
+  if (!tc_pipeline<KW>(1, d.Kp, rows, item, sm, taddr, mbar, ph)) {
     if (threadIdx.x == 0) atomicOr(status, ST_TIMEOUT);
     tc_end(taddr, ncols);
     return;
@@ -478,7 +462,7 @@ __device__ __forceinline__ bool tc_children_S(const Dims &d, const int (&kid)[2]
     B = tcB + ((size_t)v * d.C + c) * 4 * Tw<KW>::B;  // post hi | lo
     col = (uint32_t)(sd * KW);
   };
-  return tc_pipeline<1, KW>(n, d.Kp, rows, item, sm, taddr, mbar, ph);
+  return tc_pipeline<KW>(n, d.Kp, rows, item, sm, taddr, mbar, ph);
 }
 
 // S of child sd (TMEM block sd, or the table row of a tip's code).
@@ -650,7 +634,7 @@ template <int KW>
 cudaError_t tc_post(epoch_ctx *c, int level) {
   const Dims &d = c->d;
   const int w = c->h_level_off[level + 1] - c->h_level_off[level];
-  const size_t smem = tc_smem<KW>(1);
+  const size_t smem = tc_smem<KW>();
   cudaFuncSetAttribute(k_tc_post<KW>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
   cudaLaunchConfig_t cfg = {};
   cfg.gridDim = dim3(ceil_div(d.P, kRows), w, d.C);
@@ -674,7 +658,7 @@ template <int KW>
 void tc_pre_x(epoch_ctx *c, int level, int root) {
   const Dims &d = c->d;
   const int w = c->h_level_off[level + 1] - c->h_level_off[level];
-  const size_t smem = tc_smem<KW>(1);
+  const size_t smem = tc_smem<KW>();
   cudaFuncSetAttribute(k_tc_pre_x<KW>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
   k_tc_pre_x<KW><<<dim3(ceil_div(d.P, kRows), w, d.C), kTcThr, smem, c->stream>>>(
       d, c->d_level_nodes, c->h_level_off[level], c->d_child, root, c->d_PT32, c->d_tips,
@@ -686,7 +670,7 @@ template <int KW>
 void tc_pre_u(epoch_ctx *c, int level) {
   const Dims &d = c->d;
   const int w = c->h_level_off[level + 1] - c->h_level_off[level];
-  const size_t smem = tc_smem<KW>(1);
+  const size_t smem = tc_smem<KW>();
   cudaFuncSetAttribute(k_tc_pre_u<KW>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
   k_tc_pre_u<KW><<<dim3(ceil_div(d.P, kRows), 2 * w, d.C), kTcThr, smem, c->stream>>>(
       d, c->d_level_nodes, c->h_level_off[level], c->d_child, (const float *)c->d_xbuf, c->d_tcB,
