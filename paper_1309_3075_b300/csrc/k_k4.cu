@@ -498,7 +498,7 @@ __global__ void __launch_bounds__(kThr, 2) k4_pre(K4Args g, int off, int Cp, int
 // global operands of step i + kWalkDepth while it computes step i (a register
 // ring; the step loop is unrolled by kWalkDepth so the ring is indexed
 // statically), so the walk waits on memory only at its start.
-constexpr int kWalkDepth = 4;
+constexpr int kWalkDepth = 8;
 
 struct WalkOp {
   float4 l0, l1;  // stored child: its partial; tip / cherry: table index in .x
