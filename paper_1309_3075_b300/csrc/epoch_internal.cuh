@@ -149,7 +149,9 @@ struct epoch_ctx {
   int k4_top_begin = 0;               // level-order index of the first walk node
   int k4_walk_post = 0, k4_walk_pre = 0;    // steps of each walk
   int k4_slots_post = 0, k4_slots_pre = 0;  // value slots per walk thread
-  std::vector<int4> h_k4_walk;        // post-order steps, then pre-order steps (4 int4 each)
+  std::vector<int4> h_k4_walk;        // post-order steps, then pre-order steps (4 int4 each),
+                                      // then the level kernels' node descriptors (3 int4 each)
+  int k4_desc_off = 0;                // int4 offset of the node descriptors in h_k4_walk
   std::vector<int> h_k4_launch;       // adjoint launches: (first node, nodes, tiles per CTA)
   std::vector<int> h_k4_nt;           // [nn] G tiles of each branch
   int4 *d_k4_walk = nullptr;

@@ -98,8 +98,6 @@ struct K4Args {
   const float4 *PT;        // [nn][C][NR] rows of Kp = 4 floats
   const float4 *pairS;     // [nn][C][NR*NR] S of a cherry for each code pair
   const float4 *pairL;     // [nn][C][NR*NR] L of a cherry for each code pair
-  const int *nodes;        // internal nodes, level-ascending
-  const int *child;        // [N-1][2]
   float4 *part;            // [N-1][C][P]
   float4 *pre;             // [N-1][C][P]
   int16_t *scale;          // [N-1][Pp]
@@ -112,6 +110,7 @@ struct K4Args {
   float *Gpart;            // [nn][gstride][C][16]
   int gstride;             // fine tiles of 256 patterns
   int top_begin;           // level-order index from which the adjoint stores no U
+  const int4 *desc;        // [N-1][3] per internal node, level order (k4_schedule)
   int *status;
 };
 
@@ -119,20 +118,8 @@ struct K4Args {
 struct Kid {
   int node, kind, a, b;
 };
-__device__ __forceinline__ Kid classify(const K4Args &g, int x) {
-  Kid k{x, kTip, -1, -1};
-  if (x >= g.d.N) {
-    const int a = g.child[2 * (x - g.d.N)], b = g.child[2 * (x - g.d.N) + 1];
-    if (a < g.d.N && b < g.d.N && x != g.root) {
-      k.kind = kCherry;
-      k.a = a;
-      k.b = b;
-    } else {
-      k.kind = kStored;
-    }
-  }
-  return k;
-}
+// From its descriptor {kind, node, tip a, tip b} (k4_schedule).
+__device__ __forceinline__ Kid kid_of(int4 q) { return Kid{q.y, q.x, q.z, q.w}; }
 
 // ---- pair tables of the cherries --------------------------------------------
 // One CTA per internal node (non-cherries return); threads over (c, pair).
@@ -259,14 +246,9 @@ template <int CMAX>
 __global__ void __launch_bounds__(kThr) k4_post(K4Args g, int off, int early) {
   extern __shared__ float4 tabs[];
   if (!early) pdl_wait();
-  const int u = g.nodes[off + blockIdx.y];
-  const int slot = u - g.d.N;
-  Kid k0 = classify(g, g.child[2 * slot]), k1 = classify(g, g.child[2 * slot + 1]);
-  if (k0.kind > k1.kind) {
-    const Kid t = k0;
-    k0 = k1;
-    k1 = t;
-  }
+  const int4 *D = g.desc + 3 * (off + blockIdx.y);
+  const int u = D[0].x;
+  const Kid k0 = kid_of(D[1]), k1 = kid_of(D[2]);
   float4 *t0 = tabs, *t1 = tabs + table_size(g, k0, false);
   load_table(g, k0, false, t0);
   load_table(g, k1, false, t1);
@@ -435,15 +417,11 @@ __global__ void __launch_bounds__(kThr, 2) k4_pre(K4Args g, int off, int Cp, int
   const Dims &d = g.d;
   const int C = d.C;
   const int idx = off + blockIdx.y;
-  const int u = g.nodes[idx];
+  const int4 *D = g.desc + 3 * idx;
+  const int u = D[0].x;
   const int slot = u - d.N;
   const bool is_root = (u == g.root), store = idx < g.top_begin;
-  Kid k0 = classify(g, g.child[2 * slot]), k1 = classify(g, g.child[2 * slot + 1]);
-  if (k0.kind > k1.kind) {
-    const Kid t = k0;
-    k0 = k1;
-    k1 = t;
-  }
+  const Kid k0 = kid_of(D[1]), k1 = kid_of(D[2]);
   float4 *t0 = tabs, *t1 = tabs + table_size(g, k0, true);
   float4 *Ltip = t1 + table_size(g, k1, true);
   float4 *stage = tabs + 2 * C * (2 * d.NR * d.NR + 4) + d.NR;  // after the largest table set
@@ -552,6 +530,25 @@ __device__ float4 *walk_stage(const K4Args &g, const int4 *__restrict__ W, int n
   return rows + (size_t)nsteps * 8 * C;
 }
 
+// The root's per-pattern outputs from its scaled partial v (one category per
+// lane, CP lanes per pattern): site = sum_c w_c <pi, v_c>, its log and its
+// inverse, in FP32 (relative error ~1e-7, far below the FP32 path's bound;
+// the per-pattern exponent sum is added in FP64 by k4_site_lnl).  Out of
+// line: the walk's step loop is unrolled, and the root is its last step.
+template <int CP>
+__device__ __noinline__ void walk_root_site(const K4Args &g, float4 v, bool act, int c, int p) {
+  float site = 0.f;
+  if (act)
+    site = (float)g.catw[c] * (v.x * (float)g.pi[0] + v.y * (float)g.pi[1] +
+                               v.z * (float)g.pi[2] + v.w * (float)g.pi[3]);
+#pragma unroll
+  for (int o = 1; o < CP; o <<= 1) site += __shfl_xor_sync(0xffffffffu, site, o);
+  if (c == 0 && p < g.d.P) {
+    g.site_log[p] = (double)logf(site);
+    g.site_inv[p] = site > 0.f ? (double)(1.0f / site) : 0.0;
+  }
+}
+
 template <int CP>
 __global__ void __launch_bounds__(kWalkThr) k4_walk_post(K4Args g, const int4 *__restrict__ W,
                                                          int nsteps) {
@@ -597,15 +594,7 @@ __global__ void __launch_bounds__(kWalkThr) k4_walk_post(K4Args g, const int4 *_
         if (act) g.part[((size_t)slot * C + c) * d.P + p] = v;
         if (c == 0 && p < d.P) g.scale[(size_t)slot * d.Pp + p] = (int16_t)e;
         if (h.z) {
-          double site = act ? g.catw[c] * ((double)v.x * g.pi[0] + (double)v.y * g.pi[1] +
-                                           (double)v.z * g.pi[2] + (double)v.w * g.pi[3])
-                            : 0.0;
-#pragma unroll
-          for (int o = 1; o < CP; o <<= 1) site += __shfl_xor_sync(0xffffffffu, site, o);
-          if (c == 0 && p < d.P) {
-            g.site_log[p] = log(site);
-            g.site_inv[p] = site > 0.0 ? 1.0 / site : 0.0;
-          }
+          walk_root_site<CP>(g, v, act, c, p);
         } else if (h.y >= 0) {
           vals[h.y * kWalkThr + threadIdx.x] = v;
         }
@@ -692,36 +681,52 @@ __global__ void k4_G_reduce(Dims d, int gstride, const int *__restrict__ parent,
 }
 
 // lnL_p = log(scaled root sum) + ln2 * sum_u e_u(p); block sums of n_p lnL_p
-// reduced in a fixed order by the last block to finish.  Block = 32 patterns
-// x 8 warps; warp w adds the exponents of nodes w, w + 8, ...
-constexpr int kLnlWarps = 8;
+// reduced in a fixed order by the last block to finish.  Block = 64 patterns
+// (lane l: patterns 2l, 2l + 1, both exponents in one 4-byte load; rows are
+// Pp int16 apart, Pp a multiple of 16) x 32 warps; warp w adds the exponents
+// of nodes w, w + 32, ..., eight loads in flight.
+constexpr int kLnlWarps = 32;
+constexpr int kLnlPat = 64;
 __global__ void __launch_bounds__(32 * kLnlWarps) k4_site_lnl(Dims d, const int16_t *__restrict__ scale,
                                                               const double *__restrict__ site_log,
                                                               const double *__restrict__ pw,
                                                               double *__restrict__ site_lnl,
                                                               double *__restrict__ part, int *ctl,
                                                               double *__restrict__ lnl) {
-  __shared__ int es[kLnlWarps][33];
+  __shared__ int2 es[kLnlWarps][33];
   __shared__ double redd[kLnlWarps];
   __shared__ int s_last;
   const int pl = threadIdx.x & 31, gi = threadIdx.x >> 5;
-  const int p = blockIdx.x * 32 + pl;
-  int acc = 0;
-  if (p < d.P)
-#pragma unroll 4
-    for (int s = gi; s < d.N - 1; s += kLnlWarps) acc += scale[(size_t)s * d.Pp + p];
-  es[gi][pl] = acc;
+  const int p0 = blockIdx.x * kLnlPat + 2 * pl;
+  int lo = 0, hi = 0;
+  if (p0 < d.P) {
+    const int *col = reinterpret_cast<const int *>(scale + p0);
+    const size_t row = (size_t)d.Pp / 2;
+#pragma unroll 8
+    for (int s = gi; s < d.N - 1; s += kLnlWarps) {
+      const int v = __ldcg(col + (size_t)s * row);
+      lo += (int)(int16_t)(v & 0xffff);  // pattern p0 (little-endian low half)
+      hi += v >> 16;                     // pattern p0 + 1, sign-extended
+    }
+  }
+  es[gi][pl] = make_int2(lo, hi);
   __syncthreads();
   double contrib = 0.0;
-  if (gi == 0 && p < d.P) {
-    int tot = 0;
-    for (int k = 0; k < kLnlWarps; k++) tot += es[k][pl];
-    const double lp = site_log[p] + 0.69314718055994530942 * (double)tot;
-    site_lnl[p] = lp;
-    const double nw = pw[p];
-    contrib = (nw != 0.0) ? nw * lp : 0.0;
-  }
   if (gi == 0) {
+    int tl = 0, th = 0;
+    for (int k = 0; k < kLnlWarps; k++) {
+      tl += es[k][pl].x;
+      th += es[k][pl].y;
+    }
+    for (int h = 0; h < 2; h++) {
+      const int p = p0 + h;
+      if (p < d.P) {
+        const double lp = site_log[p] + 0.69314718055994530942 * (double)(h ? th : tl);
+        site_lnl[p] = lp;
+        const double nw = pw[p];
+        contrib += (nw != 0.0) ? nw * lp : 0.0;
+      }
+    }
     for (int o = 16; o > 0; o >>= 1) contrib += __shfl_xor_sync(0xffffffffu, contrib, o);
     if (pl == 0) {
       part[blockIdx.x] = contrib;
@@ -750,8 +755,6 @@ K4Args make_args(epoch_ctx *c) {
   a.PT = reinterpret_cast<const float4 *>(c->d_PT32);
   a.pairS = reinterpret_cast<const float4 *>(c->d_pairS);
   a.pairL = reinterpret_cast<const float4 *>(c->d_pairL);
-  a.nodes = c->d_level_nodes;
-  a.child = c->d_child;
   a.part = reinterpret_cast<float4 *>(c->d_part);
   a.pre = reinterpret_cast<float4 *>(c->d_pre);
   a.scale = c->d_scale;
@@ -766,6 +769,7 @@ K4Args make_args(epoch_ctx *c) {
   a.Gpart = (float *)c->d_Gpart;
   a.gstride = k4_tiles(c->d.P);
   a.top_begin = c->k4_top_begin;
+  a.desc = c->d_k4_walk + c->k4_desc_off;
   a.status = c->d_status;
   return a;
 }
@@ -839,7 +843,7 @@ cudaError_t post(epoch_ctx *c) {
   // adjoint pass (joined before the results are read)
   return fork_side(c, 1, [&] {
     cudaMemsetAsync(c->d_ctl, 0, sizeof(int), c->stream);
-    k4_site_lnl<<<ceil_div(c->d.P, 32), 32 * kLnlWarps, 0, c->stream>>>(
+    k4_site_lnl<<<ceil_div(c->d.P, kLnlPat), 32 * kLnlWarps, 0, c->stream>>>(
         c->d, c->d_scale, c->d_site_log, c->d_pw, c->d_site_lnl, c->d_lnl_part, c->d_ctl,
         c->d_lnl);
     c->launches++;
@@ -983,6 +987,18 @@ void k4_schedule(epoch_ctx *c) {
   c->k4_slots_pre = slots_pre;
   c->h_k4_walk = post_steps;
   c->h_k4_walk.insert(c->h_k4_walk.end(), pre_steps.begin(), pre_steps.end());
+  // level kernels: per internal node in level order {u, 0, 0, 0} and its two
+  // children's descriptors, the one of smaller kind first, so that a CTA
+  // learns its node and both children with one round of loads
+  c->k4_desc_off = (int)c->h_k4_walk.size();
+  for (int i = 0; i < off[L]; i++) {
+    const int u = nodes[i];
+    int4 q0 = kid_desc(child[2 * (u - N)]), q1 = kid_desc(child[2 * (u - N) + 1]);
+    if (q0.x > q1.x) std::swap(q0, q1);
+    c->h_k4_walk.push_back(int4{u, 0, 0, 0});
+    c->h_k4_walk.push_back(q0);
+    c->h_k4_walk.push_back(q1);
+  }
   // adjoint launches
   const int T0 = k4_tiles(d.P);
   const long long want = 4LL * 148;  // CTAs: >= 2 per SM at 2 resident per SM
