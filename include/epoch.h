@@ -173,7 +173,9 @@ epoch_status epoch_compute_branch_matrices(epoch_ctx *ctx);
 
 /* Async.  Post-order pruning over all patterns and categories with
  * per-pattern power-of-two rescaling after every internal node, then the
- * root sum and the weighted FP64 log-sum. */
+ * root sum and the weighted FP64 log-sum.  Replayed from a CUDA graph that
+ * the context captures on the first call and again after the topology or a
+ * size changes. */
 epoch_status epoch_update_partials(epoch_ctx *ctx);
 
 /* Synchronises; returns lnL of the last epoch_update_partials. */
@@ -184,7 +186,9 @@ epoch_status epoch_site_log_likelihoods(epoch_ctx *ctx, double *out);
 
 /* Gradient of lnL by a pre-order adjoint pass over the stored post-order
  * partials, per-branch dlnL/dP, then the chain rule through the segment
- * products.  Synchronises.  Each output may be NULL (not wanted):
+ * products, replayed from a CUDA graph captured on the first call (and again
+ * after the topology or a size changes).  Synchronises.  Each output may be
+ * NULL (not wanted):
  *   d_heights      [2N-1]  d lnL / d height of every node
  *   d_boundaries   [E-1]   d lnL / d b_k
  *   d_params       [n_params] d lnL / d theta_a (needs reversible = 1)

@@ -103,7 +103,7 @@ epoch_status ensure_param_buffers(epoch_ctx *c) {
 }
 
 void invalidate_graphs(epoch_ctx *c) {
-  for (int g = 0; g < 2; g++) {
+  for (int g = 0; g < epoch_ctx::kGraphSlots; g++) {
     if (c->graph_exec[g]) cudaGraphExecDestroy(c->graph_exec[g]);
     c->graph_exec[g] = nullptr;
     c->graph_topo[g] = -1;
@@ -165,6 +165,43 @@ epoch_status need(epoch_ctx *c, unsigned bits, const char *what) {
     return fail(c, EPOCH_ERR_ORDER, std::string(what) + ": required inputs not set yet");
   return EPOCH_OK;
 }
+
+// Replays the captured graph of slot g (0: branch matrices + partials,
+// 1: the same + gradient, 2: partials only, 3: gradient only), capturing it
+// first when there is none for the current topology.  enqueue() puts the slot's work on the
+// stream; every side branch rejoins before the capture ends.
+template <class F>
+epoch_status replay(epoch_ctx *c, int g, F enqueue) {
+  if (!c->graph_exec[g] || c->graph_topo[g] != c->topo_version) {
+    if (c->graph_exec[g]) cudaGraphExecDestroy(c->graph_exec[g]);
+    c->graph_exec[g] = nullptr;
+    cudaGraph_t graph;
+    const long long before = c->launches;
+    CK(cudaStreamBeginCapture(c->stream, cudaStreamCaptureModeRelaxed), "cudaStreamBeginCapture");
+    c->capturing = true;
+    epoch_status es = enqueue();
+    cudaError_t je = join_sides(c);
+    if (es == EPOCH_OK && je != cudaSuccess) es = cuda_fail(c, je, "join");
+    cudaError_t ee = cudaStreamEndCapture(c->stream, &graph);
+    c->capturing = false;
+    if (es != EPOCH_OK) {
+      if (ee == cudaSuccess) cudaGraphDestroy(graph);
+      return es;
+    }
+    CK(ee, "cudaStreamEndCapture");
+    cudaError_t ie = cudaGraphInstantiate(&c->graph_exec[g], graph, 0);
+    cudaGraphDestroy(graph);
+    CK(ie, "cudaGraphInstantiate");
+    c->graph_kernels[g] = c->launches - before;
+    c->launches = before;
+    c->graph_topo[g] = c->topo_version;
+    c->captures++;
+  }
+  CK(cudaGraphLaunch(c->graph_exec[g], c->stream), "cudaGraphLaunch");
+  c->launches += c->graph_kernels[g];
+  return EPOCH_OK;
+}
+
 
 epoch_status copy_grad_out(epoch_ctx *c, double *d_heights, double *d_boundaries,
                            double *d_params, double *d_branch_rates) {
@@ -306,6 +343,10 @@ epoch_status plan_k4(epoch_ctx *c) {
     CK(cudaMalloc(&c->d_k4_walk, sizeof(int4) * c->k4_walk_cap), "cudaMalloc(walk steps)");
   }
   if (!c->d_k4_nt) CK(dalloc(&c->d_k4_nt, nn_max), "cudaMalloc(G tile counts)");
+  if (!c->d_k4_esum) CK(dalloc(&c->d_k4_esum, d.P), "cudaMalloc(exponent sums)");
+  // the partials pass leaves both zero for the next one
+  CK(cudaMemsetAsync(c->d_k4_esum, 0, sizeof(int) * d.P, c->stream), "cudaMemset(exponent sums)");
+  CK(cudaMemsetAsync(c->d_ctl, 0, sizeof(int), c->stream), "cudaMemset(counter)");
   if (!c->h_k4_walk.empty())
     CK(cudaMemcpyAsync(c->d_k4_walk, c->h_k4_walk.data(), sizeof(int4) * c->h_k4_walk.size(),
                        cudaMemcpyHostToDevice, c->stream),
@@ -371,7 +412,7 @@ void epoch_destroy(epoch_ctx *c) {
                   c->d_site_inv,   c->d_lnl_part, c->d_lnl,     c->d_Gpart,      c->d_G,
                   c->d_gseg,       c->d_grad,    c->d_status,   c->d_ctl,        c->d_site_log,
                   c->d_level_off,  c->d_pairS,   c->d_pairL,    c->d_k4_walk,    c->d_k4_nt,
-                  c->d_tcB,        c->d_jumps,   c->d_jump_out, c->d_anc};
+                  c->d_k4_esum,    c->d_tcB,     c->d_jumps,    c->d_jump_out,   c->d_anc};
   for (void *p : bufs) dfree(p);
   if (c->h_grad_pinned) cudaFreeHost(c->h_grad_pinned);
   if (c->h_lnl_pinned) cudaFreeHost(c->h_lnl_pinned);
@@ -502,7 +543,7 @@ epoch_status epoch_create(epoch_ctx **out, int states, int n_epochs, const doubl
   A(dalloc(&c->d_pwf, d.Pp));
   A(dalloc(&c->d_site_lnl, P));
   A(dalloc(&c->d_site_inv, P));
-  A(dalloc(&c->d_lnl_part, ceil_div(n_patterns, 32)));
+  A(dalloc(&c->d_lnl_part, ceil_div(n_patterns, 16)));  // one per block of >= 16 patterns
   A(dalloc(&c->d_lnl, 1));
   if (precision == EPOCH_FP64 || states != 4 || n_categories > 8) {  // K = 4 FP32: per tree
     // G terms per pattern on the few-pattern path, else per tile of kTile
@@ -907,9 +948,8 @@ epoch_status epoch_update_partials(epoch_ctx *c) {
   if (!c) return EPOCH_ERR_ARG;
   epoch_status s = need(c, HAVE_BRANCH | HAVE_TIPS, "update_partials");
   if (s != EPOCH_OK) return s;
-  s = enqueue_partials(c);
+  s = replay(c, 2, [&] { return enqueue_partials(c); });
   if (s != EPOCH_OK) return s;
-  CK(join_sides(c), "join");
   c->have |= HAVE_PARTIALS;
   c->have &= ~HAVE_GRADIENT;
   return EPOCH_OK;
@@ -945,9 +985,8 @@ epoch_status epoch_gradient(epoch_ctx *c, double *d_heights, double *d_boundarie
   if (s != EPOCH_OK) return s;
   if (d_params && c->d.np > 0 && !c->d.reversible)
     return fail(c, EPOCH_ERR_UNSUPPORTED, "parameter gradients need reversible=1");
-  s = enqueue_gradient(c);
+  s = replay(c, 3, [&] { return enqueue_gradient(c); });
   if (s != EPOCH_OK) return s;
-  CK(join_sides(c), "join");
   c->have |= HAVE_GRADIENT;
   return copy_grad_out(c, d_heights, d_boundaries, d_params, d_branch_rates);
 }
@@ -1045,35 +1084,13 @@ epoch_status epoch_evaluate_async(epoch_ctx *c, int with_gradient) {
   epoch_status s = need(c, HAVE_RATES | HAVE_CATS | HAVE_TREE | HAVE_TIPS, "evaluate_async");
   if (s != EPOCH_OK) return s;
   const int g = with_gradient ? 1 : 0;
-  if (!c->graph_exec[g] || c->graph_topo[g] != c->topo_version) {
-    if (c->graph_exec[g]) cudaGraphExecDestroy(c->graph_exec[g]);
-    c->graph_exec[g] = nullptr;
-    cudaGraph_t graph;
-    const long long before = c->launches;
-    CK(cudaStreamBeginCapture(c->stream, cudaStreamCaptureModeRelaxed), "cudaStreamBeginCapture");
-    c->capturing = true;
+  s = replay(c, g, [&] {
     epoch_status es = enqueue_branch(c);
     if (es == EPOCH_OK) es = enqueue_partials(c);
     if (es == EPOCH_OK && g) es = enqueue_gradient(c);
-    cudaError_t je = join_sides(c);  // every side branch rejoins before the capture ends
-    if (es == EPOCH_OK && je != cudaSuccess) es = cuda_fail(c, je, "join");
-    cudaError_t ee = cudaStreamEndCapture(c->stream, &graph);
-    c->capturing = false;
-    if (es != EPOCH_OK) {
-      if (ee == cudaSuccess) cudaGraphDestroy(graph);
-      return es;
-    }
-    CK(ee, "cudaStreamEndCapture");
-    cudaError_t ie = cudaGraphInstantiate(&c->graph_exec[g], graph, 0);
-    cudaGraphDestroy(graph);
-    CK(ie, "cudaGraphInstantiate");
-    c->graph_kernels[g] = c->launches - before;
-    c->launches = before;
-    c->graph_topo[g] = c->topo_version;
-    c->captures++;
-  }
-  CK(cudaGraphLaunch(c->graph_exec[g], c->stream), "cudaGraphLaunch");
-  c->launches += c->graph_kernels[g];
+    return es;
+  });
+  if (s != EPOCH_OK) return s;
   c->have |= HAVE_BRANCH | HAVE_PARTIALS;
   if (g)
     c->have |= HAVE_GRADIENT;

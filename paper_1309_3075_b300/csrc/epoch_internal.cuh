@@ -157,6 +157,7 @@ struct epoch_ctx {
   int4 *d_k4_walk = nullptr;
   size_t k4_walk_cap = 0;             // int4 capacity of d_k4_walk
   int *d_k4_nt = nullptr;             // [nn]
+  int *d_k4_esum = nullptr;           // [P] per-pattern exponent sum of the level kernels
   float *d_tcB = nullptr;             // [nn][C][4][64*64] tensor-core operands (k_tc.cu)
   float *d_pairS = nullptr;           // [nn][C][NR*NR][4] S of each cherry per code pair
   float *d_pairL = nullptr;           // [nn][C][NR*NR][4] L of each cherry per code pair
@@ -174,9 +175,12 @@ struct epoch_ctx {
   cudaEvent_t tips_staging_ev[2] = {nullptr, nullptr};  // copy out of each half done
 
   // graph replay
-  cudaGraphExec_t graph_exec[2] = {nullptr, nullptr};
-  int graph_topo[2] = {-1, -1};
-  long long graph_kernels[2] = {0, 0};
+  // slots: lnL, lnL + gradient (epoch_evaluate_async), partials only
+  // (epoch_update_partials), gradient only (epoch_gradient)
+  static constexpr int kGraphSlots = 4;
+  cudaGraphExec_t graph_exec[kGraphSlots] = {nullptr, nullptr, nullptr, nullptr};
+  int graph_topo[kGraphSlots] = {-1, -1, -1, -1};
+  long long graph_kernels[kGraphSlots] = {0, 0, 0, 0};
   long long launches = 0;
   long long captures = 0;
   bool capturing = false;

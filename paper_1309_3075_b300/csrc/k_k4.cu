@@ -111,6 +111,12 @@ struct K4Args {
   int gstride;             // fine tiles of 256 patterns
   int top_begin;           // level-order index from which the adjoint stores no U
   const int4 *desc;        // [N-1][3] per internal node, level order (k4_schedule)
+  const double *pw;        // [P] pattern weights
+  double *site_lnl;        // [P] per-pattern lnL
+  double *lnl_part;        // per walk CTA: its sum of n_p lnL_p
+  double *lnl;             // [1]
+  int *esum;               // [P] sum of the level kernels' exponents (zero between passes)
+  int *ctl;                // walk CTAs finished (zero between passes)
   int *status;
 };
 
@@ -235,6 +241,7 @@ __device__ __forceinline__ void post_node(const K4Args &g, int u, const Kid &k0,
                              (double)v.z * g.pi[2] + (double)v.w * g.pi[3]);
     }
   g.scale[(size_t)slot * d.Pp + p] = (int16_t)e;
+  atomicAdd(g.esum + p, e);  // exact; the walk adds its own nodes' and clears it
   if (is_root) {
     g.site_log[p] = log(site);
     g.site_inv[p] = site > 0.0 ? 1.0 / site : 0.0;
@@ -470,12 +477,15 @@ __global__ void __launch_bounds__(kThr, 2) k4_pre(K4Args g, int off, int Cp, int
 //   w[3] = {child 0 slot, child 1 slot, 0, 0}  (post: where a stored child's
 //          value is; pre: where the child's U goes; -1 = not in the walk)
 // Shared memory of a walk CTA: the descriptors [steps][4] int4, the first
-// four table rows of every non-tip child [steps][2][C][4] float4, then the
-// value slots [slots][kWalkThr] float4.
+// four table rows of every non-tip child [steps][2][C][4] float4, the table
+// index of every tip or cherry child for the CTA's patterns [steps][2][NPC]
+// int (tip: its code; cherry: code_a NR + code_b), then the value slots
+// [slots][kWalkThr] float4.  NPC = kWalkThr / CP patterns per CTA.
 // Thread = (pattern pl, category c), lane = pl * CP + c.  A thread loads the
 // global operands of step i + kWalkDepth while it computes step i (a register
 // ring; the step loop is unrolled by kWalkDepth so the ring is indexed
-// statically), so the walk waits on memory only at its start.
+// statically), so the walk waits on memory only at its start.  The operand of
+// a tip or cherry child is its S row itself, found through the staged index.
 constexpr int kWalkDepth = 8;
 
 struct WalkOp {
@@ -483,69 +493,116 @@ struct WalkOp {
   int e;          // pre-order: scale exponent of u
 };
 
-__device__ __forceinline__ float4 walk_load(const K4Args &g, int4 k, bool in_slot, int c, int p) {
+__device__ __forceinline__ float4 walk_load(const K4Args &g, int4 k, bool in_slot, int c, int p,
+                                            int idx) {
   const Dims &d = g.d;
-  if (k.x == kTip) return make_float4(__int_as_float(g.tips[(size_t)k.y * d.Pp + p]), 0.f, 0.f, 0.f);
-  if (k.x == kCherry)
-    return make_float4(
-        __int_as_float(g.tips[(size_t)k.z * d.Pp + p] * d.NR + g.tips[(size_t)k.w * d.Pp + p]), 0.f,
-        0.f, 0.f);
+  if (k.x == kTip) return __ldg(g.PT + ((size_t)k.y * d.C + c) * d.NR + idx);
+  if (k.x == kCherry) return __ldg(g.pairS + ((size_t)k.y * d.C + c) * d.NR * d.NR + idx);
   if (in_slot) return make_float4(0.f, 0.f, 0.f, 0.f);
   return g.part[((size_t)(k.y - d.N) * d.C + c) * d.P + p];
 }
 
-template <bool POST>
-__device__ __forceinline__ void walk_fetch(const K4Args &g, const int4 *sd, int s, int nsteps, int c,
-                                           int p, WalkOp &f) {
+template <bool POST, int NPC>
+__device__ __forceinline__ void walk_fetch(const K4Args &g, const int4 *sd, const int *codes, int s,
+                                           int nsteps, int c, int p, int pl, WalkOp &f) {
   if (s >= nsteps) return;
   const int4 h = sd[4 * s], q0 = sd[4 * s + 1], q1 = sd[4 * s + 2], sl = sd[4 * s + 3];
-  f.l0 = walk_load(g, q0, POST && sl.x >= 0, c, p);
-  f.l1 = walk_load(g, q1, POST && sl.y >= 0, c, p);
+  f.l0 = walk_load(g, q0, POST && sl.x >= 0, c, p, codes[(2 * s) * NPC + pl]);
+  f.l1 = walk_load(g, q1, POST && sl.y >= 0, c, p, codes[(2 * s + 1) * NPC + pl]);
   if (!POST) f.e = g.scale[(size_t)(h.x - g.d.N) * g.d.Pp + p];
 }
 
-// S = P_x L_x of child q for category c; rows = its staged first four rows
-__device__ __forceinline__ float4 walk_S(const K4Args &g, int4 q, float4 op, const float4 *rows,
-                                         const float4 *slotv, int c) {
-  const Dims &d = g.d;
-  if (q.x == kTip) return __ldg(g.PT + ((size_t)q.y * d.C + c) * d.NR + __float_as_int(op.x));
-  if (q.x == kCherry)
-    return __ldg(g.pairS + ((size_t)q.y * d.C + c) * d.NR * d.NR + __float_as_int(op.x));
+// S = P_x L_x of child q for category c: a tip's or cherry's prefetched row,
+// else the product with its staged first four rows
+__device__ __forceinline__ float4 walk_S(int4 q, float4 op, const float4 *rows,
+                                         const float4 *slotv) {
+  if (q.x != kStored) return op;
   return matvec_t(rows, slotv ? *slotv : op);
 }
 
-// Stages the descriptors and the table rows; returns the value slots.
+// Stages the descriptors, the table rows and the tip / cherry indices of the
+// CTA's patterns (inputs and tables that no kernel of this pass writes: safe
+// before pdl_wait); returns the value slots.
+template <int NPC>
 __device__ float4 *walk_stage(const K4Args &g, const int4 *__restrict__ W, int nsteps, float4 *sm) {
   const Dims &d = g.d;
   const int C = d.C;
   int4 *sd = reinterpret_cast<int4 *>(sm);
   float4 *rows = sm + 4 * nsteps;
+  int *codes = reinterpret_cast<int *>(rows + (size_t)nsteps * 8 * C);
   for (int i = threadIdx.x; i < 4 * nsteps; i += blockDim.x) sd[i] = W[i];
   for (int i = threadIdx.x; i < nsteps * 8 * C; i += blockDim.x) {
     const int s = i / (8 * C), r = i % (8 * C), side = r / (4 * C), cr = r % (4 * C);
     const int4 q = W[4 * s + 1 + side];
     if (q.x != kTip) rows[i] = g.PT[((size_t)q.y * C + cr / 4) * d.NR + (cr & 3)];
   }
+  for (int i = threadIdx.x; i < nsteps * 2 * NPC; i += blockDim.x) {
+    const int sside = i / NPC, pl = i % NPC;
+    const int p = blockIdx.x * NPC + pl;
+    const int4 q = W[4 * (sside >> 1) + 1 + (sside & 1)];
+    int idx = 0;
+    if (p < d.P) {
+      if (q.x == kTip) idx = g.tips[(size_t)q.y * d.Pp + p];
+      else if (q.x == kCherry) idx = g.tips[(size_t)q.z * d.Pp + p] * d.NR + g.tips[(size_t)q.w * d.Pp + p];
+    }
+    codes[i] = idx;
+  }
   __syncthreads();
-  return rows + (size_t)nsteps * 8 * C;
+  return reinterpret_cast<float4 *>(codes + (size_t)nsteps * 2 * NPC);
 }
 
 // The root's per-pattern outputs from its scaled partial v (one category per
-// lane, CP lanes per pattern): site = sum_c w_c <pi, v_c>, its log and its
-// inverse, in FP32 (relative error ~1e-7, far below the FP32 path's bound;
-// the per-pattern exponent sum is added in FP64 by k4_site_lnl).  Out of
-// line: the walk's step loop is unrolled, and the root is its last step.
+// lane, CP lanes per pattern): site = sum_c w_c <pi, v_c>, its inverse and
+// its log, in FP32 (relative error ~1e-7, far below the FP32 path's bound);
+// returns log(site) (every lane).  Out of line: the walk's step loop is
+// unrolled, and the root is its last step.
 template <int CP>
-__device__ __noinline__ void walk_root_site(const K4Args &g, float4 v, bool act, int c, int p) {
+__device__ __noinline__ float walk_root_site(const K4Args &g, float4 v, bool act, int c, int p) {
   float site = 0.f;
   if (act)
     site = (float)g.catw[c] * (v.x * (float)g.pi[0] + v.y * (float)g.pi[1] +
                                v.z * (float)g.pi[2] + v.w * (float)g.pi[3]);
 #pragma unroll
   for (int o = 1; o < CP; o <<= 1) site += __shfl_xor_sync(0xffffffffu, site, o);
+  const float ls = logf(site);
   if (c == 0 && p < g.d.P) {
-    g.site_log[p] = (double)logf(site);
+    g.site_log[p] = (double)ls;
     g.site_inv[p] = site > 0.f ? (double)(1.0f / site) : 0.0;
+  }
+  return ls;
+}
+
+// lnL = sum_p n_p lnL_p over the walk's CTAs: each CTA's sum in a fixed
+// order into lnl_part, then the last CTA to finish adds those in order and
+// zeroes the counter for the next pass.
+__device__ void walk_lnl_reduce(const K4Args &g, double contrib) {
+  __shared__ double s_red[kWalkThr / 32];
+  __shared__ int s_last;
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+  for (int o = 16; o > 0; o >>= 1) contrib += __shfl_xor_sync(0xffffffffu, contrib, o);
+  if (lane == 0) s_red[warp] = contrib;
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    double t = 0.0;
+    for (int k = 0; k < kWalkThr / 32; k++) t += s_red[k];
+    g.lnl_part[blockIdx.x] = t;
+    __threadfence();
+    s_last = (atomicAdd(g.ctl, 1) == (int)gridDim.x - 1);
+  }
+  __syncthreads();
+  if (!s_last) return;
+  __threadfence();
+  double t = 0.0;
+  for (int i = threadIdx.x; i < (int)gridDim.x; i += blockDim.x) t += __ldcg(g.lnl_part + i);
+  for (int o = 16; o > 0; o >>= 1) t += __shfl_xor_sync(0xffffffffu, t, o);
+  __syncthreads();  // s_red is reused
+  if (lane == 0) s_red[warp] = t;
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    double sum = 0.0;
+    for (int k = 0; k < kWalkThr / 32; k++) sum += s_red[k];
+    g.lnl[0] = sum;
+    *g.ctl = 0;
   }
 }
 
@@ -555,30 +612,41 @@ __global__ void __launch_bounds__(kWalkThr) k4_walk_post(K4Args g, const int4 *_
   extern __shared__ float4 sm[];
   const Dims &d = g.d;
   const int C = d.C;
-  float4 *vals = walk_stage(g, W, nsteps, sm);
+  constexpr int NPC = kWalkThr / CP;
+  float4 *vals = walk_stage<NPC>(g, W, nsteps, sm);
   pdl_wait();
   pdl_trigger();
   const int4 *sd = reinterpret_cast<const int4 *>(sm);
   const float4 *rows = sm + 4 * nsteps;
+  const int *codes = reinterpret_cast<const int *>(rows + (size_t)nsteps * 8 * C);
   const int c = threadIdx.x % CP, pl = threadIdx.x / CP;
-  const int p = blockIdx.x * (kWalkThr / CP) + pl;
+  const int p = blockIdx.x * NPC + pl;
   const bool act = c < C && p < d.P;
   const int cc = c < C ? c : 0, pc = p < d.P ? p : 0;
+  // lnL_p = log(site) + ln2 sum_u e_u(p): lane 0 of a pattern adds the walk's
+  // own exponents to the level kernels' sum
+  int esum = 0, ebelow = 0;
+  double nw = 0.0;
+  if (c == 0 && p < d.P) {  // read early: the level kernels have finished
+    ebelow = __ldcg(g.esum + p);
+    nw = g.pw[p];
+  }
+  float lsite = 0.f;
   WalkOp ring[kWalkDepth];
 #pragma unroll
-  for (int k = 0; k < kWalkDepth; k++) walk_fetch<true>(g, sd, k, nsteps, cc, pc, ring[k]);
+  for (int k = 0; k < kWalkDepth; k++) walk_fetch<true, NPC>(g, sd, codes, k, nsteps, cc, pc, pl, ring[k]);
   for (int i0 = 0; i0 < nsteps; i0 += kWalkDepth) {
 #pragma unroll
     for (int k = 0; k < kWalkDepth; k++) {
       const int i = i0 + k;
       if (i < nsteps) {
         const WalkOp f = ring[k];
-        walk_fetch<true>(g, sd, i + kWalkDepth, nsteps, cc, pc, ring[k]);
+        walk_fetch<true, NPC>(g, sd, codes, i + kWalkDepth, nsteps, cc, pc, pl, ring[k]);
         const int4 h = sd[4 * i], q0 = sd[4 * i + 1], q1 = sd[4 * i + 2], sl = sd[4 * i + 3];
         const float4 *r0 = rows + (size_t)i * 8 * C + 4 * cc;
         const float4 *r1 = r0 + 4 * C;
-        const float4 s0 = walk_S(g, q0, f.l0, r0, sl.x >= 0 ? vals + sl.x * kWalkThr + threadIdx.x : nullptr, cc);
-        const float4 s1 = walk_S(g, q1, f.l1, r1, sl.y >= 0 ? vals + sl.y * kWalkThr + threadIdx.x : nullptr, cc);
+        const float4 s0 = walk_S(q0, f.l0, r0, sl.x >= 0 ? vals + sl.x * kWalkThr + threadIdx.x : nullptr);
+        const float4 s1 = walk_S(q1, f.l1, r1, sl.y >= 0 ? vals + sl.y * kWalkThr + threadIdx.x : nullptr);
         const float4 acc = act ? mul4(s0, s1) : make_float4(0.f, 0.f, 0.f, 0.f);
         float mx = max4(acc);
 #pragma unroll
@@ -593,14 +661,24 @@ __global__ void __launch_bounds__(kWalkThr) k4_walk_post(K4Args g, const int4 *_
         const int slot = h.x - d.N;
         if (act) g.part[((size_t)slot * C + c) * d.P + p] = v;
         if (c == 0 && p < d.P) g.scale[(size_t)slot * d.Pp + p] = (int16_t)e;
+        if (c == 0) esum += e;
         if (h.z) {
-          walk_root_site<CP>(g, v, act, c, p);
+          lsite = walk_root_site<CP>(g, v, act, c, p);
         } else if (h.y >= 0) {
           vals[h.y * kWalkThr + threadIdx.x] = v;
         }
       }
     }
   }
+  double contrib = 0.0;
+  if (c == 0 && p < d.P) {
+    esum += ebelow;
+    g.esum[p] = 0;  // ready for the next pass
+    const double lp = (double)lsite + 0.69314718055994530942 * (double)esum;
+    g.site_lnl[p] = lp;
+    contrib = (nw != 0.0) ? nw * lp : 0.0;
+  }
+  walk_lnl_reduce(g, contrib);
 }
 
 template <int CP>
@@ -609,34 +687,36 @@ __global__ void __launch_bounds__(kWalkThr) k4_walk_pre(K4Args g, const int4 *__
   extern __shared__ float4 sm[];
   const Dims &d = g.d;
   const int C = d.C;
-  float4 *vals = walk_stage(g, W, nsteps, sm);
+  constexpr int NPC = kWalkThr / CP;
+  float4 *vals = walk_stage<NPC>(g, W, nsteps, sm);
   pdl_wait();
   pdl_trigger();
   const int4 *sd = reinterpret_cast<const int4 *>(sm);
   const float4 *rows = sm + 4 * nsteps;
+  const int *codes = reinterpret_cast<const int *>(rows + (size_t)nsteps * 8 * C);
   const int c = threadIdx.x % CP, pl = threadIdx.x / CP;
-  const int p = blockIdx.x * (kWalkThr / CP) + pl;
+  const int p = blockIdx.x * NPC + pl;
   const bool act = c < C && p < d.P;
   const int cc = c < C ? c : 0, pc = p < d.P ? p : 0;
   const double wcd = g.catw[cc];
   const float4 pi4 = make_float4((float)g.pi[0], (float)g.pi[1], (float)g.pi[2], (float)g.pi[3]);
   WalkOp ring[kWalkDepth];
 #pragma unroll
-  for (int k = 0; k < kWalkDepth; k++) walk_fetch<false>(g, sd, k, nsteps, cc, pc, ring[k]);
+  for (int k = 0; k < kWalkDepth; k++) walk_fetch<false, NPC>(g, sd, codes, k, nsteps, cc, pc, pl, ring[k]);
   for (int i0 = 0; i0 < nsteps; i0 += kWalkDepth) {
 #pragma unroll
     for (int k = 0; k < kWalkDepth; k++) {
       const int i = i0 + k;
       if (i < nsteps) {
         const WalkOp f = ring[k];
-        walk_fetch<false>(g, sd, i + kWalkDepth, nsteps, cc, pc, ring[k]);
+        walk_fetch<false, NPC>(g, sd, codes, i + kWalkDepth, nsteps, cc, pc, pl, ring[k]);
         const int4 h = sd[4 * i], q0 = sd[4 * i + 1], q1 = sd[4 * i + 2], sl = sd[4 * i + 3];
         const float4 *r0 = rows + (size_t)i * 8 * C + 4 * cc;
         const float4 *r1 = r0 + 4 * C;
         const float4 uu = h.z ? scl4(pi4, (float)(wcd * g.site_inv[pc]))
                               : vals[h.y * kWalkThr + threadIdx.x];
-        const float4 s0 = walk_S(g, q0, f.l0, r0, nullptr, cc);
-        const float4 s1 = walk_S(g, q1, f.l1, r1, nullptr, cc);
+        const float4 s0 = walk_S(q0, f.l0, r0, nullptr);
+        const float4 s1 = walk_S(q1, f.l1, r1, nullptr);
         if (q0.x != kTip) {
           const float4 U = matvec(r0, pow2_scale(mul4(uu, s1), f.e));
           if (act) g.pre[((size_t)(q0.y - d.N) * C + c) * d.P + p] = U;
@@ -680,75 +760,6 @@ __global__ void k4_G_reduce(Dims d, int gstride, const int *__restrict__ parent,
   if (live && part == 0) G[idx] = acc;
 }
 
-// lnL_p = log(scaled root sum) + ln2 * sum_u e_u(p); block sums of n_p lnL_p
-// reduced in a fixed order by the last block to finish.  Block = 64 patterns
-// (lane l: patterns 2l, 2l + 1, both exponents in one 4-byte load; rows are
-// Pp int16 apart, Pp a multiple of 16) x 32 warps; warp w adds the exponents
-// of nodes w, w + 32, ..., eight loads in flight.
-constexpr int kLnlWarps = 32;
-constexpr int kLnlPat = 64;
-__global__ void __launch_bounds__(32 * kLnlWarps) k4_site_lnl(Dims d, const int16_t *__restrict__ scale,
-                                                              const double *__restrict__ site_log,
-                                                              const double *__restrict__ pw,
-                                                              double *__restrict__ site_lnl,
-                                                              double *__restrict__ part, int *ctl,
-                                                              double *__restrict__ lnl) {
-  __shared__ int2 es[kLnlWarps][33];
-  __shared__ double redd[kLnlWarps];
-  __shared__ int s_last;
-  const int pl = threadIdx.x & 31, gi = threadIdx.x >> 5;
-  const int p0 = blockIdx.x * kLnlPat + 2 * pl;
-  int lo = 0, hi = 0;
-  if (p0 < d.P) {
-    const int *col = reinterpret_cast<const int *>(scale + p0);
-    const size_t row = (size_t)d.Pp / 2;
-#pragma unroll 8
-    for (int s = gi; s < d.N - 1; s += kLnlWarps) {
-      const int v = __ldcg(col + (size_t)s * row);
-      lo += (int)(int16_t)(v & 0xffff);  // pattern p0 (little-endian low half)
-      hi += v >> 16;                     // pattern p0 + 1, sign-extended
-    }
-  }
-  es[gi][pl] = make_int2(lo, hi);
-  __syncthreads();
-  double contrib = 0.0;
-  if (gi == 0) {
-    int tl = 0, th = 0;
-    for (int k = 0; k < kLnlWarps; k++) {
-      tl += es[k][pl].x;
-      th += es[k][pl].y;
-    }
-    for (int h = 0; h < 2; h++) {
-      const int p = p0 + h;
-      if (p < d.P) {
-        const double lp = site_log[p] + 0.69314718055994530942 * (double)(h ? th : tl);
-        site_lnl[p] = lp;
-        const double nw = pw[p];
-        contrib += (nw != 0.0) ? nw * lp : 0.0;
-      }
-    }
-    for (int o = 16; o > 0; o >>= 1) contrib += __shfl_xor_sync(0xffffffffu, contrib, o);
-    if (pl == 0) {
-      part[blockIdx.x] = contrib;
-      __threadfence();
-      s_last = (atomicAdd(ctl, 1) == (int)gridDim.x - 1);
-    }
-  }
-  __syncthreads();
-  if (!s_last) return;
-  __threadfence();
-  double t = 0.0;
-  for (int i = threadIdx.x; i < (int)gridDim.x; i += blockDim.x) t += __ldcg(part + i);
-  for (int o = 16; o > 0; o >>= 1) t += __shfl_xor_sync(0xffffffffu, t, o);
-  if (pl == 0) redd[gi] = t;
-  __syncthreads();
-  if (threadIdx.x == 0) {
-    double s = 0.0;
-    for (int k = 0; k < kLnlWarps; k++) s += redd[k];
-    lnl[0] = s;
-  }
-}
-
 K4Args make_args(epoch_ctx *c) {
   K4Args a{};
   a.d = c->d;
@@ -770,6 +781,12 @@ K4Args make_args(epoch_ctx *c) {
   a.gstride = k4_tiles(c->d.P);
   a.top_begin = c->k4_top_begin;
   a.desc = c->d_k4_walk + c->k4_desc_off;
+  a.pw = c->d_pw;
+  a.site_lnl = c->d_site_lnl;
+  a.lnl_part = c->d_lnl_part;
+  a.lnl = c->d_lnl;
+  a.esum = c->d_k4_esum;
+  a.ctl = c->d_ctl;
   a.status = c->d_status;
   return a;
 }
@@ -781,15 +798,18 @@ size_t table_smem(const Dims &d) {
 }
 size_t pre_smem(const Dims &d) { return table_smem(d) + sizeof(float4) * kStageF4; }
 
-size_t walk_smem(int C, int nsteps, int slots) {
-  return sizeof(float4) * ((size_t)nsteps * (4 + 8 * C) + (size_t)kWalkThr * slots);
-}
-
 int pow2_at_least(int x) {
   int p = 1;
   while (p < x) p <<= 1;
   return p;
 }
+
+size_t walk_smem(int C, int nsteps, int slots) {
+  const int npc = kWalkThr / pow2_at_least(C);  // patterns per walk CTA
+  return sizeof(float4) * ((size_t)nsteps * (4 + 8 * C) + (size_t)kWalkThr * slots) +
+         sizeof(int) * (size_t)nsteps * 2 * npc;
+}
+
 
 template <int CP>
 cudaError_t walk(epoch_ctx *c, bool post) {
@@ -837,18 +857,8 @@ cudaError_t post(epoch_ctx *c) {
     if (e != cudaSuccess) return e;
     c->launches++;
   }
-  cudaError_t err = walk_dispatch(c, true);
-  if (err != cudaSuccess) return err;
-  // the log-sum feeds no later kernel of the evaluation: it runs beside the
-  // adjoint pass (joined before the results are read)
-  return fork_side(c, 1, [&] {
-    cudaMemsetAsync(c->d_ctl, 0, sizeof(int), c->stream);
-    k4_site_lnl<<<ceil_div(c->d.P, kLnlPat), 32 * kLnlWarps, 0, c->stream>>>(
-        c->d, c->d_scale, c->d_site_log, c->d_pw, c->d_site_lnl, c->d_lnl_part, c->d_ctl,
-        c->d_lnl);
-    c->launches++;
-    return cudaGetLastError();
-  });
+  // the walk ends with the root: site sums, per-pattern lnL and the log-sum
+  return walk_dispatch(c, true);
 }
 
 cudaError_t pre(epoch_ctx *c) {

@@ -236,13 +236,16 @@ def test_graph_replay_matches_direct_calls():
                 assert np.array_equal(g2["params"], g["params"])
             lnl3, _ = lik.evaluate(with_gradient=False)
             assert lnl3 == lnl
+            # one graph each: partials only (log_likelihood), gradient only,
+            # lnL + gradient, lnL
             launches, captures = lik.counters()
-            assert launches > 0 and captures == 2
-            # new heights, same topology: the captured graph is reused
+            assert launches > 0 and captures == 4
+            # new heights, same topology: the captured graphs are reused
             h = w.heights * 1.1
             binding.epoch_set_heights(lik.ctx, h)
             lnl4, _ = lik.evaluate(with_gradient=True)
-            assert lik.counters()[1] == 2
+            assert lik.log_likelihood() == lnl4
+            assert lik.counters()[1] == 4
             assert rel(lnl4, oracle.log_likelihood(w.replace(heights=h, boundaries=w.boundaries))[0]) \
                 <= LNL_TOL[prec]
         finally:
