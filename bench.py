@@ -136,12 +136,12 @@ class ClockSampler:
 # K = 4 FP32 layout: 16 B per (category, pattern) vector, 1 B tip codes,
 # 2 B scale exponents) plus the root log-sum
 # ---------------------------------------------------------------------------
-# DRAM bytes of one partials pass (the k4_post levels, k4_walk_post and
-# k4_site_lnl of one evaluation) on the GTR 500-taxon workload, from one ncu
+# DRAM bytes of one partials pass (the k4_post levels and k4_walk_post of one
+# evaluation) on the GTR 500-taxon workload, from one ncu
 # capture with warm L2 (profiles/k4_passes_gtr500.md).  Reported only while
 # the kernel source is the one that was measured.
 PARTIALS_TRAFFIC = {"source": "paper_1309_3075_b300/csrc/k_k4.cu",
-                    "sha1": "63f66efdf112b759e93f4317adab68fe8bea996c", "bytes": 184556544}
+                    "sha1": "21b5f885278c580bf3fd5e0a75400129fb5c4413", "bytes": 187612160}
 
 
 def measured_traffic(workload):
