@@ -252,6 +252,42 @@ def test_graph_replay_matches_direct_calls():
             lik.close()
 
 
+@pytest.mark.parametrize("n_cat,n_taxa,n_sites", [(1, 40, 333), (2, 3, 17), (3, 25, 130),
+                                                    (5, 2, 9), (8, 60, 257)])
+def test_repeated_and_interleaved_passes_k4(n_cat, n_taxa, n_sites):
+    """The FP32 K = 4 pass keeps per-pattern exponent totals and a CTA
+    counter on the device and leaves both zeroed for the next pass.  Repeated
+    and interleaved calls (partials only, lnL + gradient, lnL only, new
+    heights) must agree exactly with each other and with the oracle, for
+    walks of 1, 2, 4 and 8 category lanes per pattern (C = 1, 2, 3, 5, 8),
+    pattern counts that are not multiples of a walk CTA's patterns, and two-
+    and three-taxon trees."""
+    w = synth.small_nucleotide(230 + n_cat, n_taxa=n_taxa, n_sites=n_sites, n_cat=n_cat, n_epochs=3)
+    lik = EpochLikelihood(w, precision=EPOCH_FP32)
+    try:
+        first = lik.log_likelihood()
+        site = lik.site_log_likelihoods()
+        for _ in range(3):
+            assert lik.log_likelihood() == first
+        lnl_g, g = lik.evaluate(with_gradient=True)
+        lnl_n, _ = lik.evaluate(with_gradient=False)
+        assert lnl_g == first and lnl_n == first
+        assert np.array_equal(lik.site_log_likelihoods(), site)
+        assert lik.log_likelihood() == first
+        h = w.heights * 1.05
+        binding.epoch_set_heights(lik.ctx, h)
+        second = lik.log_likelihood()
+        lnl2, _ = lik.evaluate(with_gradient=True)
+        assert lnl2 == second
+    finally:
+        lik.close()
+    rlnl, rsite = oracle.log_likelihood(w)
+    assert rel(first, rlnl) <= LNL_TOL[EPOCH_FP32]
+    assert np.allclose(site, rsite, rtol=1e-4, atol=1e-4 * np.abs(rsite).max())
+    w2 = w.replace(heights=h, boundaries=w.boundaries)
+    assert rel(second, oracle.log_likelihood(w2)[0]) <= LNL_TOL[EPOCH_FP32]
+
+
 def test_errors_are_status_codes():
     w = synth.small_nucleotide(211, n_taxa=10, n_sites=20, n_cat=2, n_epochs=2)
     ctx = binding.epoch_create(4, 2, w.boundaries, None, 2, 10, 20, 2, EPOCH_FP32)
