@@ -157,6 +157,9 @@ __device__ __forceinline__ int table_size(const K4Args &g, const Kid &k, bool pr
   if (k.kind == kCherry) return pre ? C * (2 * NR * NR + 4) : C * NR * NR;
   return C * 4;
 }
+// float4 of the largest post-order table set (two cherry children), 16-byte
+// aligned start of the post-order stage
+__host__ __device__ __forceinline__ int post_tables_f4(const Dims &d) { return 2 * d.C * d.NR * d.NR; }
 __device__ void load_table(const K4Args &g, const Kid &k, bool pre, float4 *dst) {
   const int C = g.d.C, NR = g.d.NR, NR2 = NR * NR;
   if (k.kind == kTip) {
@@ -175,112 +178,7 @@ __device__ void load_table(const K4Args &g, const Kid &k, bool pre, float4 *dst)
   }
 }
 
-// ---- post-order level kernel ---------------------------------------------------
-// Thread = pattern (all categories).  Loads first, then the tables barrier.
-template <int CMAX, int K0, int K1>
-__device__ __forceinline__ void post_node(const K4Args &g, int u, const Kid &k0, const Kid &k1,
-                                          const float4 *t0, const float4 *t1) {
-  const Dims &d = g.d;
-  const int C = d.C, NR = d.NR, NR2 = NR * NR;
-  const int slot = u - d.N;
-  const int p = blockIdx.x * kTP + threadIdx.x;
-  float4 l0[CMAX], l1[CMAX];
-  int i0 = 0, i1 = 0;
-  if (p < d.P) {
-    if constexpr (K0 == kStored) {
-      const float4 *src = g.part + (size_t)(k0.node - d.N) * C * d.P + p;
-#pragma unroll
-      for (int c = 0; c < CMAX; c++)
-        if (c < C) l0[c] = __ldcs(src + (size_t)c * d.P);
-    } else if constexpr (K0 == kCherry) {
-      i0 = g.tips[(size_t)k0.a * d.Pp + p] * NR + g.tips[(size_t)k0.b * d.Pp + p];
-    } else {
-      i0 = g.tips[(size_t)k0.node * d.Pp + p];
-    }
-    if constexpr (K1 == kStored) {
-      const float4 *src = g.part + (size_t)(k1.node - d.N) * C * d.P + p;
-#pragma unroll
-      for (int c = 0; c < CMAX; c++)
-        if (c < C) l1[c] = __ldcs(src + (size_t)c * d.P);
-    } else if constexpr (K1 == kCherry) {
-      i1 = g.tips[(size_t)k1.a * d.Pp + p] * NR + g.tips[(size_t)k1.b * d.Pp + p];
-    } else {
-      i1 = g.tips[(size_t)k1.node * d.Pp + p];
-    }
-  }
-  __syncthreads();
-  if (p >= d.P) return;
-  float4 acc[CMAX];
-  float m = 0.f;
-#pragma unroll
-  for (int c = 0; c < CMAX; c++)
-    if (c < C) {
-      float4 s0, s1;
-      if constexpr (K0 == kStored) s0 = matvec_t(t0 + 4 * c, l0[c]);
-      else if constexpr (K0 == kCherry) s0 = t0[c * NR2 + i0];
-      else s0 = t0[c * NR + i0];
-      if constexpr (K1 == kStored) s1 = matvec_t(t1 + 4 * c, l1[c]);
-      else if constexpr (K1 == kCherry) s1 = t1[c * NR2 + i1];
-      else s1 = t1[c * NR + i1];
-      acc[c] = mul4(s0, s1);
-      m = fmaxf(m, max4(acc[c]));
-    }
-  int e = 0;
-  if (!(m <= 3.0e38f)) atomicOr(g.status, ST_NONFINITE);  // NaN or Inf
-  else e = binary_exponent(m);
-  double site = 0.0;
-  const bool is_root = (u == g.root);
-  float4 *dst = g.part + (size_t)slot * C * d.P + p;
-#pragma unroll
-  for (int c = 0; c < CMAX; c++)
-    if (c < C) {
-      const float4 v = pow2_scale(acc[c], e);
-      dst[(size_t)c * d.P] = v;
-      if (is_root)
-        site += g.catw[c] * ((double)v.x * g.pi[0] + (double)v.y * g.pi[1] +
-                             (double)v.z * g.pi[2] + (double)v.w * g.pi[3]);
-    }
-  g.scale[(size_t)slot * d.Pp + p] = (int16_t)e;
-  atomicAdd(g.esum + p, e);  // exact; the walk adds its own nodes' and clears it
-  if (is_root) {
-    g.site_log[p] = log(site);
-    g.site_inv[p] = site > 0.0 ? 1.0 / site : 0.0;
-  }
-}
-
-// early = 1: the predecessor wrote none of the tables (see pdl_wait)
-template <int CMAX>
-__global__ void __launch_bounds__(kThr) k4_post(K4Args g, int off, int early) {
-  extern __shared__ float4 tabs[];
-  if (!early) pdl_wait();
-  const int4 *D = g.desc + 3 * (off + blockIdx.y);
-  const int u = D[0].x;
-  const Kid k0 = kid_of(D[1]), k1 = kid_of(D[2]);
-  float4 *t0 = tabs, *t1 = tabs + table_size(g, k0, false);
-  load_table(g, k0, false, t0);
-  load_table(g, k1, false, t1);
-  if (early) pdl_wait();
-  pdl_trigger();
-  switch (k0.kind * 3 + k1.kind) {
-    case 0: post_node<CMAX, kTip, kTip>(g, u, k0, k1, t0, t1); break;
-    case 1: post_node<CMAX, kTip, kCherry>(g, u, k0, k1, t0, t1); break;
-    case 2: post_node<CMAX, kTip, kStored>(g, u, k0, k1, t0, t1); break;
-    case 4: post_node<CMAX, kCherry, kCherry>(g, u, k0, k1, t0, t1); break;
-    case 5: post_node<CMAX, kCherry, kStored>(g, u, k0, k1, t0, t1); break;
-    default: post_node<CMAX, kStored, kStored>(g, u, k0, k1, t0, t1); break;
-  }
-}
-
-// ---- pre-order level kernel ------------------------------------------------------
-// Thread = (category c, lane): c = tid / GS, GS = kThr / Cp; the CTA covers m
-// fine tiles and the thread owns patterns lane + GS k of them (Cp m in all),
-// kPreB at a time.  The float4 operands of the next kPreB patterns (U of the
-// node, partials of stored children) are copied into the thread's own
-// shared-memory stage with cp.async while it computes the current ones
-// (double buffer; a thread reads only what it copied, so no barrier).
-constexpr int kPreB = 2;
-constexpr int kStageF4 = 2 * kPreB * 3 * kThr;  // float4 of the stage
-
+// ---- cp.async into a thread's own shared-memory stage -----------------------------
 __device__ __forceinline__ void cp_async16(void *smem, const void *gmem, bool full) {
   const unsigned s = (unsigned)__cvta_generic_to_shared(smem);
   const int n = full ? 16 : 0;  // 0: fill the 16 bytes with zeros, read nothing
@@ -293,6 +191,132 @@ __device__ __forceinline__ void cp_async_commit() {
 __device__ __forceinline__ void cp_async_wait_prev() {
   asm volatile("cp.async.wait_group 1;\n" ::: "memory");
 }
+
+// ---- post-order level kernel ---------------------------------------------------
+// Thread = pattern (all categories).  A CTA covers m fine tiles of one node:
+// its tables are staged once, and the stored children's vectors of the next
+// tile are copied into the thread's own shared-memory stage by cp.async while
+// it computes the current one (double buffer; a thread reads only what it
+// copied, so no barrier).  The host picks m per level so that the grid fits
+// the resident CTAs in as few rounds as possible.
+// Stage: [buffer 2][child 2][CMAX][kThr] float4.
+struct PostSmall {
+  int i0, i1;
+};
+
+template <int CMAX, int K0, int K1>
+__device__ __forceinline__ void post_tiles(const K4Args &g, int u, const Kid &k0, const Kid &k1,
+                                           const float4 *t0, const float4 *t1, float4 *stage,
+                                           int m) {
+  const Dims &d = g.d;
+  const int C = d.C, NR = d.NR, NR2 = NR * NR;
+  const int slot = u - d.N;
+  const float4 *l0p = K0 == kStored ? g.part + (size_t)(k0.node - d.N) * C * d.P : nullptr;
+  const float4 *l1p = K1 == kStored ? g.part + (size_t)(k1.node - d.N) * C * d.P : nullptr;
+  const uint8_t *c0a = g.tips + (size_t)(K0 == kCherry ? k0.a : k0.node) * d.Pp;
+  const uint8_t *c0b = g.tips + (size_t)(K0 == kCherry ? k0.b : 0) * d.Pp;
+  const uint8_t *c1a = g.tips + (size_t)(K1 == kCherry ? k1.a : k1.node) * d.Pp;
+  const uint8_t *c1b = g.tips + (size_t)(K1 == kCherry ? k1.b : 0) * d.Pp;
+  auto sp = [&](int buf, int side, int c) {
+    return stage + ((buf * 2 + side) * CMAX + c) * kThr + threadIdx.x;
+  };
+  auto pat = [&](int j) { return (blockIdx.x * m + j) * kTP + (int)threadIdx.x; };
+  auto issue = [&](int j, int buf, PostSmall &nx) {
+    const int p = pat(j);
+    const bool act = j < m && p < d.P;
+    const int pc = act ? p : 0;
+#pragma unroll
+    for (int c = 0; c < CMAX; c++)
+      if (c < C) {
+        if constexpr (K0 == kStored) cp_async16(sp(buf, 0, c), l0p + (size_t)c * d.P + pc, act);
+        if constexpr (K1 == kStored) cp_async16(sp(buf, 1, c), l1p + (size_t)c * d.P + pc, act);
+      }
+    if constexpr (K0 == kCherry) nx.i0 = act ? c0a[pc] * NR + c0b[pc] : 0;
+    else if constexpr (K0 == kTip) nx.i0 = act ? c0a[pc] : 0;
+    if constexpr (K1 == kCherry) nx.i1 = act ? c1a[pc] * NR + c1b[pc] : 0;
+    else if constexpr (K1 == kTip) nx.i1 = act ? c1a[pc] : 0;
+    cp_async_commit();
+  };
+  auto compute = [&](int j, int buf, const PostSmall &cur) {
+    const int p = pat(j);
+    if (j >= m || p >= d.P) return;
+    float4 acc[CMAX];
+    float mx = 0.f;
+#pragma unroll
+    for (int c = 0; c < CMAX; c++)
+      if (c < C) {
+        float4 s0, s1;
+        if constexpr (K0 == kStored) s0 = matvec_t(t0 + 4 * c, *sp(buf, 0, c));
+        else if constexpr (K0 == kCherry) s0 = t0[c * NR2 + cur.i0];
+        else s0 = t0[c * NR + cur.i0];
+        if constexpr (K1 == kStored) s1 = matvec_t(t1 + 4 * c, *sp(buf, 1, c));
+        else if constexpr (K1 == kCherry) s1 = t1[c * NR2 + cur.i1];
+        else s1 = t1[c * NR + cur.i1];
+        acc[c] = mul4(s0, s1);
+        mx = fmaxf(mx, max4(acc[c]));
+      }
+    int e = 0;
+    if (!(mx <= 3.0e38f)) atomicOr(g.status, ST_NONFINITE);  // NaN or Inf
+    else e = binary_exponent(mx);
+    float4 *dst = g.part + (size_t)slot * C * d.P + p;
+#pragma unroll
+    for (int c = 0; c < CMAX; c++)
+      if (c < C) dst[(size_t)c * d.P] = pow2_scale(acc[c], e);
+    g.scale[(size_t)slot * d.Pp + p] = (int16_t)e;
+    atomicAdd(g.esum + p, e);  // exact; the walk adds its own nodes' and clears it
+  };
+  PostSmall sa{0, 0}, sb{0, 0};
+  issue(0, 0, sa);
+  for (int j = 0; j < m; j += 2) {
+    if (j + 1 < m) issue(j + 1, 1, sb);
+    else cp_async_commit();  // empty group keeps the count
+    cp_async_wait_prev();    // buffer 0's copies have landed
+    compute(j, 0, sa);
+    if (j + 1 >= m) break;
+    if (j + 2 < m) issue(j + 2, 0, sa);
+    else cp_async_commit();
+    cp_async_wait_prev();    // buffer 1's copies have landed
+    compute(j + 1, 1, sb);
+  }
+  asm volatile("cp.async.wait_all;\n" ::: "memory");
+}
+
+// early = 1: the predecessor wrote none of the tables (see pdl_wait).  The
+// root is never a level kernel's node: the post-order walk always ends with
+// the root's level.
+template <int CMAX>
+__global__ void __launch_bounds__(kThr) k4_post(K4Args g, int off, int early, int m) {
+  extern __shared__ float4 tabs[];
+  if (!early) pdl_wait();
+  const int4 *D = g.desc + 3 * (off + blockIdx.y);
+  const int u = D[0].x;
+  const Kid k0 = kid_of(D[1]), k1 = kid_of(D[2]);
+  float4 *t0 = tabs, *t1 = tabs + table_size(g, k0, false);
+  float4 *stage = tabs + post_tables_f4(g.d);
+  load_table(g, k0, false, t0);
+  load_table(g, k1, false, t1);
+  if (early) pdl_wait();
+  pdl_trigger();
+  __syncthreads();
+  switch (k0.kind * 3 + k1.kind) {
+    case 0: post_tiles<CMAX, kTip, kTip>(g, u, k0, k1, t0, t1, stage, m); break;
+    case 1: post_tiles<CMAX, kTip, kCherry>(g, u, k0, k1, t0, t1, stage, m); break;
+    case 2: post_tiles<CMAX, kTip, kStored>(g, u, k0, k1, t0, t1, stage, m); break;
+    case 4: post_tiles<CMAX, kCherry, kCherry>(g, u, k0, k1, t0, t1, stage, m); break;
+    case 5: post_tiles<CMAX, kCherry, kStored>(g, u, k0, k1, t0, t1, stage, m); break;
+    default: post_tiles<CMAX, kStored, kStored>(g, u, k0, k1, t0, t1, stage, m); break;
+  }
+}
+
+// ---- pre-order level kernel ------------------------------------------------------
+// Thread = (category c, lane): c = tid / GS, GS = kThr / Cp; the CTA covers m
+// fine tiles and the thread owns patterns lane + GS k of them (Cp m in all),
+// kPreB at a time.  The float4 operands of the next kPreB patterns (U of the
+// node, partials of stored children) are copied into the thread's own
+// shared-memory stage with cp.async while it computes the current ones
+// (double buffer; a thread reads only what it copied, so no barrier).
+constexpr int kPreB = 2;
+constexpr int kStageF4 = 2 * kPreB * 3 * kThr;  // float4 of the stage
 
 struct PreSmall {
   int e, i0, i1;
@@ -842,18 +866,44 @@ cudaError_t walk_dispatch(epoch_ctx *c, bool post) {
   }
 }
 
+// Tiles per CTA for a post-order level of w nodes and T0 fine tiles: the
+// fewest rounds of resident CTAs (slots), a CTA's fixed cost (its descriptor
+// and tables) counted as three tiles' worth.
+int pick_post_m(int w, int T0, int slots) {
+  int best = 1;
+  long long best_cost = -1;
+  for (int m = 1; m <= T0; m++) {
+    const long long ctas = (long long)w * ((T0 + m - 1) / m);
+    const long long cost = (ctas + slots - 1) / slots * (3 + m);
+    if (best_cost < 0 || cost < best_cost) {
+      best_cost = cost;
+      best = m;
+    }
+  }
+  return best;
+}
+
 template <int CMAX>
 cudaError_t post(epoch_ctx *c) {
   K4Args a = make_args(c);
-  const size_t smem = table_smem(c->d);
-  cudaFuncSetAttribute(k4_post<CMAX>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+  const size_t smem = sizeof(float4) * ((size_t)post_tables_f4(c->d) + 2 * 2 * CMAX * kThr);
+  cudaError_t err = cudaFuncSetAttribute(k4_post<CMAX>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+  if (err != cudaSuccess) return err;
+  int dev = 0, nsm = 0, per_sm = 0;
+  err = cudaGetDevice(&dev);
+  if (err == cudaSuccess) err = cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev);
+  if (err == cudaSuccess)
+    err = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k4_post<CMAX>, kThr, smem);
+  if (err != cudaSuccess) return err;
+  const int slots = std::max(1, nsm * per_sm), T0 = k4_tiles(c->d.P);
   const int last = std::max(c->k4_top, c->k4_first_level);
   for (int l = c->k4_first_level; l < last; l++) {
     const int w = c->h_level_off[l + 1] - c->h_level_off[l];
+    const int m = pick_post_m(w, T0, slots);
     // the first level's predecessor wrote the cherry tables it loads
     const int early = l > c->k4_first_level ? 1 : 0;
-    cudaError_t e = launch_pdl(k4_post<CMAX>, dim3(k4_tiles(c->d.P), w), dim3(kThr), smem,
-                               c->stream, a, c->h_level_off[l], early);
+    cudaError_t e = launch_pdl(k4_post<CMAX>, dim3(ceil_div(T0, m), w), dim3(kThr), smem,
+                               c->stream, a, c->h_level_off[l], early, m);
     if (e != cudaSuccess) return e;
     c->launches++;
   }
