@@ -266,7 +266,8 @@ __device__ __forceinline__ void post_tiles(const K4Args &g, int u, const Kid &k0
     atomicAdd(g.esum + p, e);  // exact; the walk adds its own nodes' and clears it
   };
   PostSmall sa{0, 0}, sb{0, 0};
-  issue(0, 0, sa);
+  issue(0, 0, sa);  // the first tile's operands need no tables: before the barrier
+  __syncthreads();  // the node's tables are staged
   for (int j = 0; j < m; j += 2) {
     if (j + 1 < m) issue(j + 1, 1, sb);
     else cp_async_commit();  // empty group keeps the count
@@ -297,8 +298,7 @@ __global__ void __launch_bounds__(kThr) k4_post(K4Args g, int off, int early, in
   load_table(g, k1, false, t1);
   if (early) pdl_wait();
   pdl_trigger();
-  __syncthreads();
-  switch (k0.kind * 3 + k1.kind) {
+  switch (k0.kind * 3 + k1.kind) {  // uniform over the CTA (post_tiles has a barrier)
     case 0: post_tiles<CMAX, kTip, kTip>(g, u, k0, k1, t0, t1, stage, m); break;
     case 1: post_tiles<CMAX, kTip, kCherry>(g, u, k0, k1, t0, t1, stage, m); break;
     case 2: post_tiles<CMAX, kTip, kStored>(g, u, k0, k1, t0, t1, stage, m); break;
@@ -332,7 +332,10 @@ __device__ __forceinline__ void pre_node(const K4Args &g, int slot, bool is_root
   const int C = d.C, NR = d.NR, NR2 = NR * NR;
   const int GS = kThr / Cp;
   const int c = threadIdx.x / GS, lp = threadIdx.x % GS;
-  if (c >= C) return;  // idle lanes when C is not a power of two
+  if (c >= C) {  // idle lanes when C is not a power of two (they take the barrier below)
+    __syncthreads();
+    return;
+  }
   const double wcd = g.catw[c];
   const float4 pi4 = make_float4((float)g.pi[0], (float)g.pi[1], (float)g.pi[2], (float)g.pi[3]);
   // this category's table views
@@ -426,7 +429,8 @@ __device__ __forceinline__ void pre_node(const K4Args &g, int slot, bool is_root
     }
   };
   PreSmall sa[kPreB], sb[kPreB];
-  issue(0, 0, sa);
+  issue(0, 0, sa);  // the first operands need no tables: before the barrier
+  __syncthreads();  // the node's tables are staged
   for (int j0 = 0; j0 < npat; j0 += 2 * kPreB) {
     if (j0 + kPreB < npat) issue(j0 + kPreB, 1, sb);
     else cp_async_commit();  // empty group keeps the count
@@ -461,11 +465,10 @@ __global__ void __launch_bounds__(kThr, 2) k4_pre(K4Args g, int off, int Cp, int
   for (int i = threadIdx.x; i < d.NR; i += blockDim.x) Ltip[i] = onehot(i, g.masks);
   pdl_wait();  // the level above (or the walk) has stored this level's U
   pdl_trigger();
-  __syncthreads();
   float acc[32];
 #pragma unroll
   for (int q = 0; q < 32; q++) acc[q] = 0.f;
-  switch (k0.kind * 3 + k1.kind) {
+  switch (k0.kind * 3 + k1.kind) {  // uniform over the CTA (pre_node has a barrier)
     case 0: pre_node<kTip, kTip>(g, slot, is_root, store, k0, k1, t0, t1, Ltip, stage, Cp, m, acc); break;
     case 1: pre_node<kTip, kCherry>(g, slot, is_root, store, k0, k1, t0, t1, Ltip, stage, Cp, m, acc); break;
     case 2: pre_node<kTip, kStored>(g, slot, is_root, store, k0, k1, t0, t1, Ltip, stage, Cp, m, acc); break;
