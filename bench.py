@@ -141,7 +141,7 @@ class ClockSampler:
 # capture with warm L2 (profiles/k4_passes_gtr500.md).  Reported only while
 # the kernel source is the one that was measured.
 PARTIALS_TRAFFIC = {"source": "paper_1309_3075_b300/csrc/k_k4.cu",
-                    "sha1": "75c89776b71392a20ff0f4e151b5f7c8137ad3af", "bytes": 215048960}
+                    "sha1": "10fa6711ae065e7750a1dcf38ba5179cdd8a56b4", "bytes": 214757120}
 
 
 def measured_traffic(workload):
