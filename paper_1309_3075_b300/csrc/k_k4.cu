@@ -1062,14 +1062,22 @@ void k4_schedule(epoch_ctx *c) {
     c->h_k4_walk.push_back(q0);
     c->h_k4_walk.push_back(q1);
   }
-  // adjoint launches
+  // adjoint launches: tiles per CTA for the fewest rounds of resident CTAs
   const int T0 = k4_tiles(d.P);
-  const long long want = 4LL * 148;  // CTAs: >= 2 per SM at 2 resident per SM
-  auto pick_m = [&](int w) {
-    for (int m = 4; m > 1; m >>= 1)
-      if ((long long)w * ((T0 + m - 1) / m) >= want) return m;
-    return 1;
-  };
+  int slots = 2 * 148;
+  {
+    int dev = 0, nsm = 0, per_sm = 0;
+    const size_t smem = pre_smem(d);
+    if (cudaGetDevice(&dev) == cudaSuccess &&
+        cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev) == cudaSuccess &&
+        cudaFuncSetAttribute(k4_pre, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem) ==
+            cudaSuccess &&
+        cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k4_pre, kThr, smem) == cudaSuccess &&
+        nsm * per_sm > 0)
+      slots = nsm * per_sm;
+    cudaGetLastError();
+  }
+  auto pick_m = [&](int w) { return pick_post_m(w, T0, slots); };
   c->h_k4_launch.clear();
   c->h_k4_nt.assign(nn, 0);
   auto add_launch = [&](int first, int count) {
