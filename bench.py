@@ -137,9 +137,9 @@ class ClockSampler:
 # 2 B scale exponents) plus the root log-sum
 # ---------------------------------------------------------------------------
 # DRAM bytes of one partials pass (the k4_post levels and k4_walk_post of one
-# evaluation) on the GTR 500-taxon workload, from one ncu
-# capture with warm L2 (profiles/k4_passes_gtr500.md).  Reported only while
-# the kernel source is the one that was measured.
+# evaluation) on the GTR 500-taxon workload, from one ncu capture of those
+# launches with warm L2 (dram__bytes_read.sum + dram__bytes_write.sum).
+# Reported only while the kernel source is the one that was measured.
 PARTIALS_TRAFFIC = {"source": "paper_1309_3075_b300/csrc/k_k4.cu",
                     "sha1": "a983f79822a0cca755b9c88c626c75824b98a782", "bytes": 216046848}
 

@@ -71,7 +71,7 @@ typedef enum {
   EPOCH_ERR_NUMERIC = 4,  /* NaN/negative rates, rows not summing to 0, ...   */
   EPOCH_ERR_CUDA = 5,     /* a CUDA runtime call failed                       */
   EPOCH_ERR_TIMEOUT = 6,  /* a bounded device-side wait ran out               */
-  EPOCH_ERR_UNSUPPORTED = 7 /* valid request this build does not provide      */
+  EPOCH_ERR_UNSUPPORTED = 7 /* valid request the library does not support     */
 } epoch_status;
 
 typedef enum {
