@@ -17,7 +17,10 @@ case, brute-force enumeration, or finite differences.
                  closed forms with different (pi, mu) per epoch.
   pruning a5-a7  brute force over all internal states (K = 3, 4, 61);
                  two-taxon JC69 closed form; all-missing tip == tip removed;
-                 duplicated site == weight 2; scaling on == off; permutation.
+                 duplicated site == weight 2; scaling on == off; permutation;
+                 ambiguity masks: linearity in the tip indicator vector (a mask
+                 tip's site likelihood is the sum over its states), full mask ==
+                 missing, one-state mask == that state.
   gradient       central finite differences (h = 1e-6, FP64) for heights,
                  boundaries, branch rates and model parameters; d/db = 0
                  exactly when Q_k = Q_{k+1}; time-rescaling identity
@@ -350,6 +353,106 @@ def test_missing_tip_equals_removed_tip(oracle_lib):
     wr = drop_tip(w, t)
     assert np.isclose(oracle_lib.log_likelihood(wm)[0], oracle_lib.log_likelihood(wr)[0],
                       rtol=1e-13)
+
+
+def _with_tip_codes(w, changes):
+    """Copy of w with tips[t, p] = code for every (t, p, code) in changes."""
+    tips = w.tips.copy()
+    for t, p, code in changes:
+        tips[t, p] = code
+    return w.replace(tips=tips)
+
+
+@pytest.mark.parametrize("K,rev,cats", [(3, True, 1), (4, True, 2), (6, False, 2)])
+def test_ambiguity_masks_are_sums_over_their_states(oracle_lib, K, rev, cats):
+    """Pruning is linear in each tip's indicator vector (Eq. partial_likelihood:
+    a tip's partial is 1 on every state it allows).  So a tip coded by the mask
+    {i, j, ...} gives site likelihood L(tip = i) + L(tip = j) + ..., each term
+    computed with the tip observed in one state.  Two mask tips in one pattern
+    give the double sum.  Every pattern uses a different mask, so an off-by-one
+    mask index or a reversed bit order changes the result."""
+    rng = np.random.default_rng(7 + K)
+    w = synth.tiny_tree_workload(60 + K, K=K, n_taxa=6, n_sites=8, n_epochs=3,
+                                 n_cat=cats, reversible=rev)
+    P = w.n_patterns
+    full = (1 << K) - 1
+    masks = []
+    for _ in range(2 * P):
+        while True:
+            m = int(rng.integers(1, full))
+            if bin(m).count("1") >= 2:
+                break
+        masks.append(m)
+    masks = np.array(masks, np.uint64)
+    t1, t2 = 1, 4
+    w = w.replace(masks=masks)
+    # one mask tip per pattern: tip t1 uses mask p
+    wm = _with_tip_codes(w, [(t1, p, K + 1 + p) for p in range(P)])
+    _, site_m = oracle_lib.log_likelihood(wm)
+    per_state = np.array([oracle_lib.log_likelihood(
+        _with_tip_codes(w, [(t1, p, s) for p in range(P)]))[1] for s in range(K)])
+    for p in range(P):
+        states = [s for s in range(K) if (int(masks[p]) >> s) & 1]
+        ref = np.logaddexp.reduce(per_state[states, p])
+        assert np.isclose(site_m[p], ref, rtol=1e-12, atol=1e-13), (p, site_m[p], ref)
+    # two mask tips in the same pattern: t1 uses mask p, t2 uses mask P + p
+    wm2 = _with_tip_codes(w, [(t, p, K + 1 + p + (P if t == t2 else 0))
+                              for p in range(P) for t in (t1, t2)])
+    _, site_m2 = oracle_lib.log_likelihood(wm2)
+    pair = np.empty((K, K, P))
+    for a in range(K):
+        for b in range(K):
+            pair[a, b] = oracle_lib.log_likelihood(
+                _with_tip_codes(w, [(t, p, a if t == t1 else b)
+                                    for p in range(P) for t in (t1, t2)]))[1]
+    for p in range(P):
+        sa = [s for s in range(K) if (int(masks[p]) >> s) & 1]
+        sb = [s for s in range(K) if (int(masks[P + p]) >> s) & 1]
+        ref = np.logaddexp.reduce([pair[a, b, p] for a in sa for b in sb])
+        assert np.isclose(site_m2[p], ref, rtol=1e-12, atol=1e-13), (p, site_m2[p], ref)
+
+
+def test_full_and_single_state_masks(oracle_lib):
+    """A mask with every state set is the missing code K; a mask with one
+    state set is that state's code (the tip's indicator vector is the same)."""
+    K = 4
+    w = synth.tiny_tree_workload(71, K=K, n_taxa=7, n_sites=6, n_epochs=2, n_cat=2)
+    masks = np.array([(1 << K) - 1] + [1 << s for s in range(K)], np.uint64)
+    w = w.replace(masks=masks)
+    P = w.n_patterns
+    for t in (0, 3, 6):
+        full = _with_tip_codes(w, [(t, p, K + 1) for p in range(P)])
+        miss = _with_tip_codes(w, [(t, p, K) for p in range(P)])
+        assert np.allclose(oracle_lib.log_likelihood(full)[1],
+                           oracle_lib.log_likelihood(miss)[1], rtol=1e-14)
+        for s in range(K):
+            one = _with_tip_codes(w, [(t, p, K + 2 + s) for p in range(P)])
+            obs = _with_tip_codes(w, [(t, p, s) for p in range(P)])
+            assert np.allclose(oracle_lib.log_likelihood(one)[1],
+                               oracle_lib.log_likelihood(obs)[1], rtol=1e-14)
+
+
+def test_mask_gradient_matches_central_differences(oracle_lib):
+    """The adjoint reads tip indicator vectors too: with mask tips the height
+    gradient still equals central differences of lnL (h = 1e-6, FP64)."""
+    K = 4
+    w = synth.tiny_tree_workload(73, K=K, n_taxa=6, n_sites=6, n_epochs=3, n_cat=2)
+    masks = np.array([0b0101, 0b1010, 0b0111], np.uint64)
+    P = w.n_patterns
+    w = _with_tip_codes(w.replace(masks=masks),
+                        [(p % w.n_taxa, p, K + 1 + p % 3) for p in range(P)])
+    g = oracle_lib.gradient(w)
+    N = w.n_taxa
+    for u in range(N, 2 * N - 1):
+        if w.parent[u] < 0:
+            continue
+
+        def f(x, u=u):
+            h = w.heights.copy()
+            h[u] = x
+            return oracle_lib.log_likelihood(w.replace(heights=h))[0]
+
+        _check(g["heights"][u], _fd(f, w.heights[u]), ("height", u))
 
 
 def test_weights_duplication_permutation_scaling(oracle_lib):
