@@ -199,18 +199,51 @@ __device__ __forceinline__ void tc_sync_staged() {
   asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
   __syncthreads();
 }
-// Bounded wait for the MMAs signalled on mbar; flips the phase.
-__device__ __forceinline__ bool tc_wait(uint64_t *mbar, uint32_t &phase) {
-  uint32_t done = 0;
-  for (int it = 0; it < (1 << 24) && !done; it++)
+// Waits on an MMA-completion barrier are bounded in time, not in polls: a
+// kernel slowed by a profiler's replay must not reach the limit.
+constexpr uint64_t kWaitNs = 2000000000ull;  // 2 s per wait
+__device__ __forceinline__ uint64_t gtimer() {
+  uint64_t t;
+  asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(t));
+  return t;
+}
+// Thread 0 polls mbar for the given phase until it completes or kWaitNs has
+// passed on %globaltimer.
+__device__ __forceinline__ bool mbar_poll(uint64_t *mbar, uint32_t phase) {
+  const uint64_t t0 = gtimer();
+  while (true) {
+    uint32_t done;
     asm volatile(
         "{\n.reg .pred p;\nmbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n"
         "selp.u32 %0, 1, 0, p;\n}\n"
         : "=r"(done)
-        : "r"(su32(mbar)), "r"(phase));
-  phase ^= 1u;
+        : "r"(su32(mbar)), "r"(phase)
+        : "memory");
+    if (done) return true;
+    if (gtimer() - t0 > kWaitNs) return false;
+  }
+}
+// Wait for the MMAs signalled on mbar.  One thread polls and publishes the
+// outcome in *s_ok, so that every thread of the CTA takes the same branch
+// (the tcgen05 loads and the barriers after it are CTA- or warp-collective).
+// On success the phase flips.  On failure it does not: the MMA is still in
+// flight, and the caller must call tc_drain on the same phase before the CTA
+// releases its tensor memory or exits.  Callers separate two calls by a
+// __syncthreads, so *s_ok is never rewritten while a thread still reads it.
+__device__ __forceinline__ bool tc_wait(uint64_t *mbar, uint32_t &phase, int *s_ok) {
+  if (threadIdx.x == 0) *s_ok = mbar_poll(mbar, phase) ? 1 : 0;
+  __syncthreads();
+  const bool ok = *s_ok != 0;
+  if (ok) phase ^= 1u;
   asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
-  return done != 0;
+  return ok;
+}
+// After a timed-out wait: wait once more, again bounded, for the MMA that is
+// still in flight, so that its shared-memory operands, its barrier and its
+// tensor-memory columns stay valid while it runs.  CTA-collective.
+__device__ __forceinline__ void tc_drain(uint64_t *mbar, uint32_t phase) {
+  if (threadIdx.x == 0) (void)mbar_poll(mbar, phase);
+  __syncthreads();
 }
 // 64 columns of the thread's TMEM lane (warp w reads lanes 32w..32w+31),
 // one load and one wait.
@@ -344,12 +377,14 @@ __device__ __forceinline__ void row_get(const float *src, float (&v)[KW]) {
 // item j+1's A is loaded into registers during item j's MMA, its B (by
 // cp.async) once that MMA has completed.  item(j, A, B, col) names the
 // operands.  Every thread takes part.  (Two stages with one CTA per SM were
-// measured slower on the wide levels.)  Returns false when an MMA did not
-// complete within the wait bound; nothing is then left in flight but that
-// MMA.
+// measured slower on the wide levels.)  At most one MMA is in flight at any
+// time.  Returns false when an MMA did not complete within the wait bound;
+// that MMA has then been drained (a second bounded wait) and no cp.async is
+// pending, so the caller may release tensor memory.  The result is the same
+// in every thread of the CTA.
 template <int KW, class Item>
 __device__ bool tc_pipeline(int n, int lda, int rows, Item item, float *st, uint32_t taddr,
-                            uint64_t *mbar, uint32_t *ph) {
+                            uint64_t *mbar, uint32_t *ph, int *s_ok) {
   if (n <= 0) return true;
   ATile<KW> ra;
   const float *A, *B;
@@ -359,8 +394,9 @@ __device__ bool tc_pipeline(int n, int lda, int rows, Item item, float *st, uint
   tc_load_A<KW>(A, lda, rows, ra);
   for (int j = 0; j < n; j++) {
     if (j >= 1) {  // the stage is free once MMA j-1 has completed
-      if (!tc_wait(&mbar[(j - 1) & 1], ph[(j - 1) & 1])) {
-        asm volatile("cp.async.wait_all;" ::: "memory");
+      const int b = (j - 1) & 1;
+      if (!tc_wait(&mbar[b], ph[b], s_ok)) {
+        tc_drain(&mbar[b], ph[b]);
         return false;
       }
       tc_async_B<KW>(B, st);
@@ -375,7 +411,12 @@ __device__ bool tc_pipeline(int n, int lda, int rows, Item item, float *st, uint
     tc_sync_staged();
     tc_mma<KW>(taddr + colj, st, &mbar[j & 1]);
   }
-  return tc_wait(&mbar[(n - 1) & 1], ph[(n - 1) & 1]);
+  const int b = (n - 1) & 1;
+  if (!tc_wait(&mbar[b], ph[b], s_ok)) {
+    tc_drain(&mbar[b], ph[b]);
+    return false;
+  }
+  return true;
 }
 
 // CTA prologue / epilogue: TMEM columns and the two MMA-completion barriers.
@@ -417,6 +458,7 @@ __global__ void __launch_bounds__(kTcThr) k_tc_pre_u(Dims d, const int *__restri
   extern __shared__ __align__(1024) float tsm[];
   __shared__ uint32_t s_tmem;
   __shared__ __align__(8) uint64_t mbar[2];
+  __shared__ int s_ok;
   const int bi = blockIdx.y >> 1, x = blockIdx.y & 1, c = blockIdx.z;
   const int u = lvl_nodes[lvl_off + bi];
   const int v = child[2 * (u - d.N) + x];
@@ -432,7 +474,7 @@ __global__ void __launch_bounds__(kTcThr) k_tc_pre_u(Dims d, const int *__restri
     B = tcB + ((size_t)v * d.C + c) * 4 * Tw<KW>::B + 2 * Tw<KW>::B;  // pre hi | lo
     col = 0;
   };
-  if (!tc_pipeline<KW>(1, d.Kp, rows, item, sm, taddr, mbar, ph)) {
+  if (!tc_pipeline<KW>(1, d.Kp, rows, item, sm, taddr, mbar, ph, &s_ok)) {
     if (threadIdx.x == 0) atomicOr(status, ST_TIMEOUT);
     tc_end(taddr, ncols);
     return;
@@ -452,7 +494,7 @@ template <int KW>
 __device__ __forceinline__ bool tc_children_S(const Dims &d, const int (&kid)[2], int c,
                                               const float *part, const float *tcB, int p0,
                                               int rows, float *sm, uint32_t taddr,
-                                              uint64_t *mbar, uint32_t *ph) {
+                                              uint64_t *mbar, uint32_t *ph, int *s_ok) {
   const bool st0 = kid[0] >= d.N, st1 = kid[1] >= d.N;
   const int n = (int)st0 + (int)st1;
   auto item = [&](int j, const float *&A, const float *&B, uint32_t &col) {
@@ -462,7 +504,7 @@ __device__ __forceinline__ bool tc_children_S(const Dims &d, const int (&kid)[2]
     B = tcB + ((size_t)v * d.C + c) * 4 * Tw<KW>::B;  // post hi | lo
     col = (uint32_t)(sd * KW);
   };
-  return tc_pipeline<KW>(n, d.Kp, rows, item, sm, taddr, mbar, ph);
+  return tc_pipeline<KW>(n, d.Kp, rows, item, sm, taddr, mbar, ph, s_ok);
 }
 
 // S of child sd (TMEM block sd, or the table row of a tip's code).
@@ -506,6 +548,7 @@ __global__ void __launch_bounds__(kTcThr) k_tc_post(Dims d, const int *__restric
   extern __shared__ __align__(1024) float tsm[];
   __shared__ uint32_t s_tmem;
   __shared__ __align__(8) uint64_t mbar[2];
+  __shared__ int s_ok;
   __shared__ float s_m[kRows];
   __shared__ int s_e[kRows];
   float *sm = tc_smem(tsm);
@@ -516,7 +559,7 @@ __global__ void __launch_bounds__(kTcThr) k_tc_post(Dims d, const int *__restric
   const uint32_t taddr = tc_begin(&s_tmem, mbar, 2 * KW);
   uint32_t ph[2] = {0, 0};
   const int p0 = blockIdx.x * kRows, rows = min(kRows, d.P - p0);
-  const bool ok = tc_children_S<KW>(d, kid, c, part, tcB, p0, rows, sm, taddr, mbar, ph);
+  const bool ok = tc_children_S<KW>(d, kid, c, part, tcB, p0, rows, sm, taddr, mbar, ph, &s_ok);
   if (!ok && threadIdx.x == 0) atomicOr(status, ST_TIMEOUT);
   const int r = threadIdx.x, p = p0 + r;
   const bool live = r < rows;
@@ -570,6 +613,7 @@ __global__ void __launch_bounds__(kTcThr) k_tc_pre_x(
   extern __shared__ __align__(1024) float tsm[];
   __shared__ uint32_t s_tmem;
   __shared__ __align__(8) uint64_t mbar[2];
+  __shared__ int s_ok;
   float *sm = tc_smem(tsm);
   const int bi = blockIdx.y, c = blockIdx.z;
   const int u = lvl_nodes[lvl_off + bi];
@@ -578,7 +622,7 @@ __global__ void __launch_bounds__(kTcThr) k_tc_pre_x(
   const uint32_t taddr = tc_begin(&s_tmem, mbar, 2 * KW);
   uint32_t ph[2] = {0, 0};
   const int p0 = blockIdx.x * kRows, rows = min(kRows, d.P - p0);
-  if (!tc_children_S<KW>(d, kid, c, part, tcB, p0, rows, sm, taddr, mbar, ph)) {
+  if (!tc_children_S<KW>(d, kid, c, part, tcB, p0, rows, sm, taddr, mbar, ph, &s_ok)) {
     if (threadIdx.x == 0) atomicOr(status, ST_TIMEOUT);
     tc_end(taddr, 2 * KW);
     return;
