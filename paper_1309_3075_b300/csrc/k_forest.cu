@@ -12,8 +12,10 @@
 // (nonnegative, rows summing to one),
 //     exp(dt Q) x = sum_m Poisson(m; mu dt) R^m x,
 // truncated once a bound on the Poisson tail is below kTail (R^m never
-// increases max(x), so that is also the error relative to max(x)).  Every term is
-// nonnegative, so FP32 loses nothing to cancellation.  Segments are applied
+// increases max(x), so that is also the error relative to max(x)).  A segment
+// with mu dt > 30 is applied as equal pieces of mu dt <= 30, so that the first
+// Poisson weight exp(-mu dt) never underflows.  Every term is nonnegative, so
+// FP32 loses nothing to cancellation.  Segments are applied
 // from the child end upwards (the left factor of Eq. convolution is the
 // parent end).
 //
@@ -41,7 +43,9 @@ namespace {
 
 constexpr int kMaxPat = 4;          // patterns per tree (one float4 per state)
 constexpr float kTail = 1e-9f;      // Poisson mass left out
-constexpr int kMaxTerms = 4096;     // bound on uniformisation terms
+constexpr int kMaxTerms = 4096;     // bound on uniformisation terms of one series
+constexpr float kPiece = 30.f;      // longest mu dt of one series
+constexpr int kMaxPieces = 1 << 16; // bound on the series of one segment
 constexpr size_t kSmemCap = 200 * 1024;
 constexpr int kMeta = 12;
 enum { T_N, T_E, T_P, T_NODE, T_BND, T_Q, T_CODE, T_W, T_LVL, T_NLVL, T_L, T_ROOT };
@@ -97,11 +101,11 @@ struct ForestArgs {
   int *status;
 };
 
-// x <- exp(dt Q_e) x for the lane's two states; buf = this warp's K float4
-__device__ __forceinline__ void apply_segment(const ForestArgs &g, const float *RT, float mu, float dt, int K,
-                              float4 &x0, float4 &x1, float4 *buf, int lane) {
-  const float mt = mu * dt;
-  if (!(mt > 0.f)) return;  // zero length: identity
+// One uniformisation series, x <- exp(dt Q_e) x with mu dt = mt in (0, kPiece]:
+// the first Poisson weight exp(-mt) >= exp(-kPiece) stays far above the FP32
+// underflow threshold.  buf = this warp's K float4.
+__device__ __forceinline__ void apply_piece(const ForestArgs &g, const float *RT, float mt, int K,
+                                            float4 &x0, float4 &x1, float4 *buf, int lane) {
   const bool has0 = lane < K, has1 = lane + 32 < K;
   float wgt = expf(-mt);
   float4 a0 = scl4(x0, wgt), a1 = scl4(x1, wgt);
@@ -137,6 +141,26 @@ __device__ __forceinline__ void apply_segment(const ForestArgs &g, const float *
   }
   x0 = a0;
   x1 = a1;
+}
+
+// x <- exp(dt Q_e) x for the lane's two states.  A segment with mu dt above
+// kPiece is applied as n = ceil(mu dt / kPiece) equal pieces (exp(dt Q) =
+// exp(dt Q / n)^n), so that no series starts from an underflowed weight.  A
+// segment longer than kMaxPieces pieces (or a non-finite one) sets FS_TERMS.
+__device__ __forceinline__ void apply_segment(const ForestArgs &g, const float *RT, float mu, float dt, int K,
+                              float4 &x0, float4 &x1, float4 *buf, int lane) {
+  const float mt = mu * dt;
+  if (!(mt > 0.f)) return;  // zero length: identity
+  int n = 1;
+  if (mt > kPiece) {
+    if (!(mt <= kPiece * (float)kMaxPieces)) {
+      if (lane == 0) atomicOr(g.status, FS_TERMS);
+      return;
+    }
+    n = (int)ceilf(mt / kPiece);
+  }
+  const float mp = mt / (float)n;
+  for (int i = 0; i < n; i++) apply_piece(g, RT, mp, K, x0, x1, buf, lane);
 }
 
 __global__ void __launch_bounds__(256, 2) k_forest(ForestArgs g) {

@@ -54,6 +54,58 @@ def test_forest_small_K_dated_tips_missing_data(cuda):
         assert abs(got[t] - ref) <= TOL * abs(ref), (t, got[t], ref)
 
 
+def _longest_mu_segment(w):
+    """Largest mu * dt over the segments of w (mu = max_i |q_ii| of the
+    normalised matrix of the segment's epoch): the length of the longest
+    uniformisation series the batched kernel would run without splitting."""
+    E = w.n_epochs
+    mus = []
+    for e in range(E):
+        q = w.Q[w.epoch_to_matrix[e]]
+        c = -(w.pi * np.diag(q)).sum() if w.normalise else 1.0
+        mus.append(np.max(-np.diag(q)) / c)
+    b = np.r_[w.boundaries, np.inf]
+    best = 0.0
+    for v, u in enumerate(w.parent):
+        if u < 0:
+            continue
+        lo, hi = w.heights[v], w.heights[u]
+        e = int(np.searchsorted(w.boundaries, lo, side="right"))
+        while lo < hi:
+            top = min(b[e], hi)
+            best = max(best, mus[e] * (top - lo))
+            lo, e = top, e + 1
+    return best
+
+
+@pytest.mark.parametrize("target", [50.0, 120.0, 400.0])
+def test_forest_long_segments(cuda, target):
+    """Branches far longer than the uniformisation rate's time scale: each
+    tree is stretched so that its longest segment has mu dt = target.  Above
+    mu dt ~ 88 the first Poisson weight exp(-mu dt) underflows in FP32, so the
+    kernel must split such segments (exp(t Q) = exp(t Q / n)^n, Eq. convolution
+    applied to equal pieces)."""
+    from paper_1309_3075_b300.binding import EpochBatch
+    for K, shapes in ((6, [(12, 1), (2, 1), (30, 4)]), (50, [(20, 2), (40, 3)])):
+        trees = []  # one state count per batch
+        for i, (n, e) in enumerate(shapes):
+            w = synth.tiny_tree_workload(500 + 10 * i + K, K=K, n_taxa=n, n_sites=3, n_epochs=e,
+                                         n_cat=1, reversible=False, dated=True, missing_frac=0.1)
+            f = target / _longest_mu_segment(w)
+            w = w.replace(heights=w.heights * f, boundaries=w.boundaries * f)
+            assert np.isclose(_longest_mu_segment(w), target)
+            trees.append(w)
+        b = EpochBatch(trees)
+        try:
+            got = b.evaluate()
+        finally:
+            b.close()
+        for t, w in enumerate(trees):
+            ref = oracle.log_likelihood(w)[0]
+            assert np.isfinite(got[t]), (K, t, got[t])
+            assert abs(got[t] - ref) <= TOL * abs(ref), (K, t, got[t], ref)
+
+
 def test_forest_of_one_equals_single_tree_path(cuda):
     from paper_1309_3075_b300.binding import EPOCH_FP32, EpochBatch, EpochLikelihood
     w = synth.tiny_tree_workload(77, K=12, n_taxa=60, n_sites=4, n_epochs=5, n_cat=1,

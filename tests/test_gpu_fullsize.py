@@ -11,6 +11,7 @@ import oracle
 import synth
 from paper_1309_3075_b300 import binding
 from paper_1309_3075_b300.binding import EPOCH_FP32, EPOCH_FP32_TC, EPOCH_FP64, EpochLikelihood
+from tolerances import grad_close
 
 pytestmark = pytest.mark.gpu
 
@@ -46,11 +47,9 @@ def test_gtr_full_size_lnl_and_gradient(gtr_full, prec, tol):
         lik.close()
     ref = oracle.gradient(w)
     assert abs(lnl - ref["lnL"]) <= tol * abs(ref["lnL"])
-    gtol = 1e-9 if prec == EPOCH_FP64 else 1e-4
-    assert maxrel(g["heights"], ref["heights"]) <= gtol
-    assert maxrel(g["boundaries"], ref["boundaries"]) <= gtol
-    assert maxrel(g["params"], ref["params"]) <= gtol
-    assert maxrel(g["branch_rates"], ref["branch_rates"]) <= gtol
+    for key in ("heights", "boundaries", "params", "branch_rates"):
+        ok, worst = grad_close(g[key], ref[key], prec)
+        assert ok, (key, worst)
 
 
 @pytest.mark.parametrize("prec,tol", [(EPOCH_FP64, 1e-10), (EPOCH_FP32, 1e-5),
@@ -70,7 +69,41 @@ def test_gy94_full_size_sampled_sites(gy94_full, prec, tol):
     sub = w.replace(tips=np.ascontiguousarray(w.tips[:, idx]),
                     pattern_weights=w.pattern_weights[idx])
     _, rsite = oracle.log_likelihood(sub)
-    assert np.abs(site[idx] - rsite).max() <= tol * np.abs(rsite).max() * 10
+    # each sampled pattern on its own, at ten times the lnL bound
+    assert np.all(np.abs(site[idx] - rsite) <= 10 * tol * np.abs(rsite)), \
+        np.max(np.abs(site[idx] - rsite) / np.abs(rsite))
+
+
+@pytest.fixture(scope="module")
+def gy94_slice(gy94_full):
+    """The codon gradient workload at its own shape (128 taxa, 4 epochs,
+    C = 4, the shared kappa and the four omega_k) on 32 of its patterns, with
+    the oracle's analytic gradient (its cost is per branch, about a minute)."""
+    w = gy94_full.slice_patterns(0, 32)
+    return w, oracle.gradient(w), oracle.log_likelihood(w)[1]
+
+
+@pytest.mark.parametrize("prec", [EPOCH_FP64, EPOCH_FP32, EPOCH_FP32_TC])
+def test_gy94_gradient_against_oracle_at_config_shape(gy94_slice, prec):
+    """d lnL / d (node heights, boundaries, kappa, omega_k) of the codon
+    epoch model (Eq. convolution differentiated), GPU against the FP64 oracle
+    element by element, and lnL per pattern, on every precision path."""
+    w, ref, rsite = gy94_slice
+    lik = EpochLikelihood(w, precision=prec)
+    try:
+        lnl, g = lik.evaluate(with_gradient=True)
+        site = lik.site_log_likelihoods()
+    finally:
+        lik.close()
+    ltol = 1e-10 if prec == EPOCH_FP64 else 1e-5
+    assert abs(lnl - ref["lnL"]) <= ltol * abs(ref["lnL"]), (lnl, ref["lnL"])
+    assert np.all(np.abs(site - rsite) <= 10 * ltol * np.abs(rsite))
+    internal = np.arange(w.n_taxa, 2 * w.n_taxa - 1)
+    internal = internal[w.parent[internal] >= 0]
+    for key, idx in (("heights", internal), ("boundaries", slice(None)), ("params", slice(None))):
+        got, want = np.asarray(g[key])[idx], np.asarray(ref[key])[idx]
+        ok, worst = grad_close(got, want, prec)
+        assert ok, (key, worst, got, want)
 
 
 def test_gy94_full_size_gradient_vs_finite_differences(gy94_full):
@@ -129,8 +162,10 @@ def test_gy94_full_size_gradient_vs_finite_differences(gy94_full):
             fd4 = (-f[0] + 8 * f[1] - 8 * f[2] + f[3]) / (12 * H)
             assert abs(g["params"][a] - fd4) <= 1e-4 * max(1.0, abs(fd4)), (w.param_names[a], g["params"][a], fd4)
         for k in ("heights", "boundaries", "params"):
-            assert maxrel(g32[k], g[k]) <= 1e-4, k
-            assert maxrel(gtc[k], g[k]) <= 1e-4, ("tensor cores", k)
+            ok, worst = grad_close(g32[k], g[k], EPOCH_FP32)
+            assert ok, (k, worst)
+            ok, worst = grad_close(gtc[k], g[k], EPOCH_FP32_TC)
+            assert ok, ("tensor cores", k, worst)
         assert abs(lnl - lik32.evaluate(with_gradient=False)[0]) <= 1e-5 * abs(lnl)
         assert abs(lnl - lnltc) <= 1e-5 * abs(lnl)
     finally:
@@ -140,8 +175,10 @@ def test_gy94_full_size_gradient_vs_finite_differences(gy94_full):
 
 
 def test_forest_full_size_sampled_trees():
-    """The 256-tree batch in the launch the bench times; the oracle checks four
-    of the smaller trees (its dense uniformisation is slow at K = 50)."""
+    """The 256-tree batch in the launch the bench times.  The oracle (dense
+    uniformisation, a few seconds per 1,000-taxon tree at K = 50) checks the
+    three smallest trees, the 13th smallest, the two largest and the largest
+    tree with 8 epochs."""
     torch = pytest.importorskip("torch")
     if not torch.cuda.is_available():
         pytest.skip("needs a GPU")
@@ -155,7 +192,9 @@ def test_forest_full_size_sampled_trees():
     assert np.all(np.isfinite(got))
     sizes = np.array([t.n_taxa for t in bw.trees])
     order = np.argsort(sizes, kind="stable")
-    pick = [int(order[i]) for i in (0, 1, 2, 12)]
+    pick = [int(order[i]) for i in (0, 1, 2, 12, -1, -2)]
+    eight = [t for t in range(len(bw.trees)) if bw.trees[t].n_epochs == 8]
+    pick.append(max(eight, key=lambda t: bw.trees[t].n_taxa))
     for t in pick:
         ref = oracle.log_likelihood(bw.trees[t])[0]
         assert abs(got[t] - ref) <= 1e-5 * abs(ref), (t, got[t], ref)
