@@ -3,9 +3,10 @@ same seeded inputs.
 
 Tolerances: lnL relative error <= 1e-10 on the FP64 path and <= 1e-5 on
 the FP32 paths.  Branch matrices on every path are FP64 and must match to
-1e-12.  Gradients: FP64 path within 1e-9 of the oracle's (max-norm
-relative); FP32 paths within 1e-4 (max-norm relative), the bound also used
-for the finite-difference check of the gradient.
+1e-12.  Gradients: FP64 path within 1e-9 of the oracle's, FP32 paths
+within 1e-4, each component relative to its own size (floors in
+tests/tolerances.py); 1e-4 is also the bound of the finite-difference check
+of the gradient.
 """
 import numpy as np
 import pytest
@@ -15,12 +16,9 @@ import synth
 from paper_1309_3075_b300 import binding
 from paper_1309_3075_b300.binding import (EPOCH_FP32, EPOCH_FP32_TC, EPOCH_FP64, EpochError,
                                           EpochLikelihood)
+from tolerances import GRAD_TOL, LNL_TOL, grad_close
 
 pytestmark = pytest.mark.gpu
-
-LNL_TOL = {EPOCH_FP64: 1e-10, EPOCH_FP32: 1e-5, EPOCH_FP32_TC: 1e-5}
-GRAD_TOL = {EPOCH_FP64: 1e-9, EPOCH_FP32: 1e-4, EPOCH_FP32_TC: 1e-4}
-
 
 @pytest.fixture(scope="module", autouse=True)
 def _built():
@@ -31,14 +29,6 @@ def _built():
 
 def rel(a, b):
     return abs(a - b) / max(abs(b), 1e-300)
-
-
-def vec_close(g, ref, tol):
-    # relative to the largest component, with an absolute floor of tol for
-    # derivatives that vanish exactly (e.g. a scale parameter removed by
-    # the normalisation of Q)
-    scale = max(np.abs(ref).max() if ref.size else 0.0, 1.0)
-    return np.abs(np.asarray(g) - np.asarray(ref)).max() <= tol * scale
 
 
 def check_lnl(w, prec, site_sample=None):
@@ -63,19 +53,21 @@ def check_grad(w, prec):
     finally:
         lik.close()
     ref = oracle.gradient(w)
-    tol = GRAD_TOL[prec]
     nn = 2 * w.n_taxa - 1
-    assert vec_close(g["heights"], ref["heights"], tol), ("heights", np.abs(g["heights"] - ref["heights"]).max())
+    ok, worst = grad_close(g["heights"], ref["heights"], prec)
+    assert ok, ("heights", worst)
     if w.n_epochs > 1:
         # a boundary derivative is a difference of per-segment terms of the
         # size of the height derivatives; it can cancel to ~0 (identical
-        # processes on both sides), so its error is measured on that scale
+        # processes on both sides), so its floor is on that scale
         scale = max(np.abs(ref["boundaries"]).max(), np.abs(ref["heights"]).max())
-        assert np.abs(g["boundaries"] - ref["boundaries"]).max() <= tol * scale, \
-            (g["boundaries"], ref["boundaries"])
-    assert vec_close(g["branch_rates"][: nn], ref["branch_rates"], tol)
+        ok, worst = grad_close(g["boundaries"], ref["boundaries"], prec, scale)
+        assert ok, ("boundaries", worst, g["boundaries"], ref["boundaries"])
+    ok, worst = grad_close(g["branch_rates"][:nn], ref["branch_rates"], prec)
+    assert ok, ("branch rates", worst)
     if w.n_params and w.reversible:
-        assert vec_close(g["params"], ref["params"], tol), (g["params"], ref["params"])
+        ok, worst = grad_close(g["params"], ref["params"], prec)
+        assert ok, ("params", worst, g["params"], ref["params"])
     return g, ref
 
 
