@@ -330,6 +330,29 @@ epoch_status epoch_batch_read(epoch_batch *b, double *lnL);
 epoch_status epoch_batch_launch_shape(const epoch_batch *b, int *warps_per_cta,
                                       int *ctas_per_sm);
 
+/* lnL and its gradient for every tree in one persistent launch: after a
+ * tree's post-order pass, the same CTA runs its pre-order adjoint (outside
+ * vectors moved down each branch segment by segment with the transposed
+ * uniformised exponential) and differentiates each segment's length,
+ * d log L / d dt = ub . Q_e z (Eq. convolution differentiated; Relaxing
+ * time-homogeneity).  Height derivatives collect the terms of the segments a
+ * node ends; boundary derivatives the terms of the segments on both sides of
+ * each crossed boundary.  Sums run in a fixed order (no atomics), so replays
+ * are bitwise reproducible.  Async; the first call tunes the launch shape of
+ * this variant and captures it in a graph, and allocates the gradient's
+ * device buffers (about (sum 2N_t - 1) (E_max + 3) doubles and a scratch of
+ * forward vectors per resident warp).  Errors as epoch_batch_evaluate_async. */
+epoch_status epoch_batch_evaluate_gradient_async(epoch_batch *b);
+
+/* Synchronises; lnL [n_trees], d lnL_t / d height [sum_t (2 N_t - 1)] (tree
+ * order, local node order within a tree; tips included) and d lnL_t / d
+ * boundary [sum_t (E_t - 1)] (NULL allowed when every tree has one epoch) of
+ * the last evaluation.  EPOCH_ERR_ORDER unless that evaluation was
+ * epoch_batch_evaluate_gradient_async with the current inputs;
+ * EPOCH_ERR_NUMERIC as epoch_batch_read. */
+epoch_status epoch_batch_read_gradient(epoch_batch *b, double *lnL, double *d_heights,
+                                       double *d_boundaries);
+
 /* ---- allocation-free root log-sum (no counterpart in the paper) ---------- */
 
 /* The weighted log-sum that ends the root step, for callers that must not

@@ -73,6 +73,8 @@ _SIGS = {
     "epoch_batch_evaluate_async": [_vp],
     "epoch_batch_read": [_vp, _dp],
     "epoch_batch_launch_shape": [_vp, _ip, _ip],
+    "epoch_batch_evaluate_gradient_async": [_vp],
+    "epoch_batch_read_gradient": [_vp, _dp, _dp, _dp],
 }
 _RESTYPE = {"epoch_destroy": None, "epoch_last_error": C.c_char_p,
             "epoch_status_string": C.c_char_p, "epoch_batch_destroy": None,
@@ -449,6 +451,20 @@ def epoch_batch_read(b, n_trees):
     return out
 
 
+def epoch_batch_evaluate_gradient_async(b):
+    _bcheck(b, lib().epoch_batch_evaluate_gradient_async(b), "epoch_batch_evaluate_gradient_async")
+
+
+def epoch_batch_read_gradient(b, n_trees, n_nodes, n_boundaries):
+    lnl = np.empty(n_trees)
+    dh = np.empty(n_nodes)
+    db = np.empty(max(n_boundaries, 1))
+    _bcheck(b, lib().epoch_batch_read_gradient(b, lnl.ctypes.data_as(_dp), dh.ctypes.data_as(_dp),
+                                               db.ctypes.data_as(_dp) if n_boundaries else None),
+            "epoch_batch_read_gradient")
+    return lnl, dh, db[:n_boundaries]
+
+
 def epoch_batch_launch_shape(b):
     w, c = C.c_int(0), C.c_int(0)
     _bcheck(b, lib().epoch_batch_launch_shape(b, C.byref(w), C.byref(c)),
@@ -465,6 +481,8 @@ class EpochBatch:
         trees = list(trees)
         self.T = len(trees)
         self.K = int(trees[0].K)
+        self._nodes = [2 * np.asarray(t.tips).shape[0] - 1 for t in trees]
+        self._bnds = [len(np.asarray(t.boundaries).reshape(-1)) for t in trees]
         self.b = epoch_batch_create(
             self.K, [np.asarray(t.tips).shape[0] for t in trees],
             [len(np.asarray(t.boundaries).reshape(-1)) + 1 for t in trees],
@@ -487,6 +505,17 @@ class EpochBatch:
     def evaluate(self):
         epoch_batch_evaluate_async(self.b)
         return epoch_batch_read(self.b, self.T)
+
+    def evaluate_gradient(self):
+        """lnL per tree and, per tree, d lnL / d heights [2N_t - 1] and
+        d lnL / d boundaries [E_t - 1] (lists of arrays)."""
+        epoch_batch_evaluate_gradient_async(self.b)
+        lnl, dh, db = epoch_batch_read_gradient(self.b, self.T, int(sum(self._nodes)),
+                                                int(sum(self._bnds)))
+        ho = np.cumsum([0] + self._nodes)
+        bo = np.cumsum([0] + self._bnds)
+        return (lnl, [dh[ho[t]:ho[t + 1]] for t in range(self.T)],
+                [db[bo[t]:bo[t + 1]] for t in range(self.T)])
 
     def launch_shape(self):
         return epoch_batch_launch_shape(self.b)

@@ -99,11 +99,22 @@ struct ForestArgs {
   double *lnl;           // [T]
   int *ctl;              // [2] queue head, CTAs done
   int *status;
+  // gradient launch only
+  int4 *ex;              // [sum N_t - 1] rescaling exponents of every internal node
+  double *dseg;          // [sum 2N_t - 1][Emax] d lnL / d (segment length), by epoch
+  float4 *chain;         // per warp [2][Emax][K]: forward vectors at segment tops
+  double *dh;            // [sum 2N_t - 1] d lnL / d node height
+  double *db;            // [sum E_t - 1] d lnL / d boundary
+  double *dbot;          // [sum 2N_t - 1] the bottom-segment term of each branch
+  int2 *span;            // [sum 2N_t - 1] epochs of each branch's bottom and top segments
 };
 
-// One uniformisation series, x <- exp(dt Q_e) x with mu dt = mt in (0, kPiece]:
-// the first Poisson weight exp(-mt) >= exp(-kPiece) stays far above the FP32
-// underflow threshold.  buf = this warp's K float4.
+// One uniformisation series, x <- exp(dt Q_e) x with mu dt = mt in (0, kPiece]
+// (TR: x <- exp(dt Q_e)^T x, the adjoint, with R^T for R): the first Poisson
+// weight exp(-mt) >= exp(-kPiece) stays far above the FP32 underflow
+// threshold.  buf = this warp's K float4.  RT holds R transposed, RT[j K + i]
+// = R_ij.
+template <bool TR>
 __device__ __forceinline__ void apply_piece(const ForestArgs &g, const float *RT, float mt, int K,
                                             float4 &x0, float4 &x1, float4 *buf, int lane) {
   const bool has0 = lane < K, has1 = lane + 32 < K;
@@ -120,8 +131,8 @@ __device__ __forceinline__ void apply_piece(const ForestArgs &g, const float *RT
       if (lane == 0) atomicOr(g.status, FS_TERMS);
       break;
     }
-    // t <- R t (warp matvec through shared memory; buf holds K entries, so
-    // lanes >= K neither write nor read a row)
+    // t <- R t (or R^T t): warp matvec through shared memory; buf holds K
+    // entries, so lanes >= K neither write nor read a row
     __syncwarp();
     if (has0) buf[lane] = t0;
     if (has1) buf[lane + 32] = t1;
@@ -129,8 +140,8 @@ __device__ __forceinline__ void apply_piece(const ForestArgs &g, const float *RT
     float4 n0 = f4(0.f), n1 = f4(0.f);
     for (int j = 0; j < K; j++) {
       const float4 tj = buf[j];
-      if (has0) fma4(n0, RT[j * K + lane], tj);
-      if (has1) fma4(n1, RT[j * K + lane + 32], tj);
+      if (has0) fma4(n0, TR ? RT[lane * K + j] : RT[j * K + lane], tj);
+      if (has1) fma4(n1, TR ? RT[(lane + 32) * K + j] : RT[j * K + lane + 32], tj);
     }
     t0 = n0;
     t1 = n1;
@@ -143,10 +154,12 @@ __device__ __forceinline__ void apply_piece(const ForestArgs &g, const float *RT
   x1 = a1;
 }
 
-// x <- exp(dt Q_e) x for the lane's two states.  A segment with mu dt above
-// kPiece is applied as n = ceil(mu dt / kPiece) equal pieces (exp(dt Q) =
-// exp(dt Q / n)^n), so that no series starts from an underflowed weight.  A
-// segment longer than kMaxPieces pieces (or a non-finite one) sets FS_TERMS.
+// x <- exp(dt Q_e) x (TR: its transpose) for the lane's two states.  A
+// segment with mu dt above kPiece is applied as n = ceil(mu dt / kPiece)
+// equal pieces (exp(dt Q) = exp(dt Q / n)^n), so that no series starts from an
+// underflowed weight.  A segment longer than kMaxPieces pieces (or a
+// non-finite one) sets FS_TERMS.
+template <bool TR = false>
 __device__ __forceinline__ void apply_segment(const ForestArgs &g, const float *RT, float mu, float dt, int K,
                               float4 &x0, float4 &x1, float4 *buf, int lane) {
   const float mt = mu * dt;
@@ -160,9 +173,64 @@ __device__ __forceinline__ void apply_segment(const ForestArgs &g, const float *
     n = (int)ceilf(mt / kPiece);
   }
   const float mp = mt / (float)n;
-  for (int i = 0; i < n; i++) apply_piece(g, RT, mp, K, x0, x1, buf, lane);
+  for (int i = 0; i < n; i++) apply_piece<TR>(g, RT, mp, K, x0, x1, buf, lane);
 }
 
+__device__ __forceinline__ float4 warp_sum4(float4 v) {
+  for (int o = 16; o > 0; o >>= 1) {
+    v.x += __shfl_xor_sync(0xffffffffu, v.x, o);
+    v.y += __shfl_xor_sync(0xffffffffu, v.y, o);
+    v.z += __shfl_xor_sync(0xffffffffu, v.z, o);
+    v.w += __shfl_xor_sync(0xffffffffu, v.w, o);
+  }
+  return v;
+}
+
+// The indicator vector of a tip's code for the lane's two states (code K =
+// missing: all ones), four patterns packed.
+__device__ __forceinline__ void tip_vector(const uint8_t *cv, int P, int K, int lane, float4 &x0,
+                                           float4 &x1) {
+  float c4[4];
+#pragma unroll
+  for (int p = 0; p < kMaxPat; p++) c4[p] = p < P ? (float)cv[p] : -1.f;
+  auto ind = [&](int i) {
+    float4 r;
+    r.x = (c4[0] == (float)i || c4[0] == (float)K) ? 1.f : 0.f;
+    r.y = (c4[1] == (float)i || c4[1] == (float)K) ? 1.f : 0.f;
+    r.z = (c4[2] == (float)i || c4[2] == (float)K) ? 1.f : 0.f;
+    r.w = (c4[3] == (float)i || c4[3] == (float)K) ? 1.f : 0.f;
+    return r;
+  };
+  x0 = lane < K ? ind(lane) : f4(0.f);
+  x1 = lane + 32 < K ? ind(lane + 32) : f4(0.f);
+}
+
+// Epochs of the bottom and top segments of the branch [hv, hu]: a segment
+// belongs to the epoch of its lower end; a zero-length branch has one
+// zero-length segment in the epoch of hv.
+__device__ __forceinline__ void branch_epochs(const double *b, int E, double hv, double hu,
+                                              int &ebot, int &etop) {
+  ebot = 0;
+  while (ebot < E - 1 && b[ebot] <= hv) ebot++;
+  etop = 0;
+  while (etop < E - 1 && b[etop] < hu) etop++;
+  etop = max(etop, ebot);
+}
+
+// One CTA per tree at a time.  GRAD = false: post-order pruning and the root
+// log-sum.  GRAD = true: then the pre-order adjoint of the same tree in the
+// same CTA, and d lnL / d (node heights, boundaries).
+//
+// Adjoint (per pattern; tilde = stored, rescaled values): L~_u = S~_v o S~_w
+// 2^-e_u with S~_x = P_x L~_x; U~_root = pi / s~ (s~ = pi . L~_root), and for
+// a child v of u, X~_v = U~_u o S~_w 2^-e_u = d log site / d S~_v, U~_v =
+// P_v^T X~_v.  For the segments of branch v, z_k at the top of segment k
+// (z_0 = S~_v) and zb_k the adjoint there (zb_0 = X~_v), the derivative of
+// log site by the segment's length is zb_k . Q_e z_k = mu_e zb_k . (R_e z_k -
+// z_k) (Eq. convolution differentiated; exp(t Q) commutes with Q), and zb
+// moves down a segment by exp(dt Q_e)^T.  U~ overwrites L~ in place: a
+// node's L~ is last read when its parent forms its branch.
+template <bool GRAD>
 __global__ void __launch_bounds__(256, 2) k_forest(ForestArgs g) {
   extern __shared__ float smem[];
   __shared__ int s_tree;
@@ -174,6 +242,8 @@ __global__ void __launch_bounds__(256, 2) k_forest(ForestArgs g) {
   float *RT = smem;                                          // [Emax][K][K] transposed R
   float4 *wbuf = reinterpret_cast<float4 *>(RT + (size_t)g.Emax * KK);  // [nwarps][K]
   float4 *buf = wbuf + (size_t)warp * K;
+  // this warp's forward vectors at the segment tops of both children
+  float4 *chain = GRAD ? g.chain + ((size_t)blockIdx.x * nwarps + warp) * 2 * g.Emax * K : nullptr;
   while (true) {
     if (threadIdx.x == 0) s_tree = atomicAdd(&g.ctl[0], 1);
     __syncthreads();
@@ -224,20 +294,7 @@ __global__ void __launch_bounds__(256, 2) k_forest(ForestArgs g) {
           const int v = child[2 * (u - N) + side];
           float4 x0, x1;
           if (v < N) {  // tip: indicator of the observed state (K = missing)
-            const uint8_t *cv = codes + (size_t)v * P;
-            float c4[4];
-#pragma unroll
-            for (int p = 0; p < kMaxPat; p++) c4[p] = p < P ? (float)cv[p] : -1.f;
-            auto ind = [&](int i) {
-              float4 r;
-              r.x = (c4[0] == (float)i || c4[0] == (float)K) ? 1.f : 0.f;
-              r.y = (c4[1] == (float)i || c4[1] == (float)K) ? 1.f : 0.f;
-              r.z = (c4[2] == (float)i || c4[2] == (float)K) ? 1.f : 0.f;
-              r.w = (c4[3] == (float)i || c4[3] == (float)K) ? 1.f : 0.f;
-              return r;
-            };
-            x0 = lane < K ? ind(lane) : f4(0.f);
-            x1 = lane + 32 < K ? ind(lane + 32) : f4(0.f);
+            tip_vector(codes + (size_t)v * P, P, K, lane, x0, x1);
           } else {
             const float4 *src = Lt + (size_t)(v - N) * K;
             x0 = lane < K ? src[lane] : f4(0.f);
@@ -270,25 +327,25 @@ __global__ void __launch_bounds__(256, 2) k_forest(ForestArgs g) {
           atomicOr(g.status, FS_NONFINITE);
         const int ex = binary_exponent(mx), ey = binary_exponent(my), ez = binary_exponent(mz),
                   ew = binary_exponent(mw);
-        const float4 sc = make_float4(pow2(-max(ex, -126)), pow2(-max(ey, -126)),
-                                      pow2(-max(ez, -126)), pow2(-max(ew, -126)));
+        const int es[4] = {max(ex, -126), max(ey, -126), max(ez, -126), max(ew, -126)};
+        const float4 sc = make_float4(pow2(-es[0]), pow2(-es[1]), pow2(-es[2]), pow2(-es[3]));
         l0 = mul4(l0, sc);
         l1 = mul4(l1, sc);
         float4 *dst = Lt + (size_t)(u - N) * K;
         if (lane < K) dst[lane] = l0;
         if (lane + 32 < K) dst[lane + 32] = l1;
         if (lane == 0) {
-          const int es[4] = {max(ex, -126), max(ey, -126), max(ez, -126), max(ew, -126)};
 #pragma unroll
           for (int p = 0; p < kMaxPat; p++)
             if (p < P) atomicAdd(&s_exp[p], es[p]);
+          if (GRAD) g.ex[mt[T_L] + (u - N)] = make_int4(es[0], es[1], es[2], es[3]);
         }
       }
       __syncthreads();
     }
     // root: lnL = sum_p w_p (log sum_i pi_i L_root(i,p) + ln2 * sum_u e_u(p))
     if (warp == 0) {
-      const float4 *Lr = Lt + (size_t)(root - N) * K;
+      float4 *Lr = Lt + (size_t)(root - N) * K;
       const double *pi = g.pi + (size_t)t * K;
       double sp[4] = {0.0, 0.0, 0.0, 0.0};
       for (int i = lane; i < K; i += 32) {
@@ -309,8 +366,147 @@ __global__ void __launch_bounds__(256, 2) k_forest(ForestArgs g) {
         }
         g.lnl[t] = acc;
       }
+      if (GRAD) {
+        // U~_root = pi / s~ per pattern (0 for an impossible or absent
+        // pattern: it adds nothing to the gradient), over L~_root
+        float inv[4];
+#pragma unroll
+        for (int p = 0; p < kMaxPat; p++) inv[p] = (p < P && sp[p] > 0.0) ? (float)(1.0 / sp[p]) : 0.f;
+        for (int i = lane; i < K; i += 32) {
+          const float pf = (float)pi[i];
+          Lr[i] = make_float4(pf * inv[0], pf * inv[1], pf * inv[2], pf * inv[3]);
+        }
+      }
     }
     __syncthreads();
+    if (GRAD) {
+      const double *w = g.w + mt[T_W];
+      double *dseg = g.dseg + (size_t)mt[T_NODE] * g.Emax;
+      // pre-order, top level first: a warp per node forms both children's
+      // branches
+      for (int l = nl - 1; l >= 0; l--) {
+        for (int k = loff[l] + warp; k < loff[l + 1]; k += nwarps) {
+          const int u = lvl[k];
+          float4 *Uu = Lt + (size_t)(u - N) * K;
+          const float4 uu0 = lane < K ? Uu[lane] : f4(0.f);
+          const float4 uu1 = lane + 32 < K ? Uu[lane + 32] : f4(0.f);
+          const int4 eu = g.ex[mt[T_L] + (u - N)];
+          const float4 su = make_float4(pow2(-eu.x), pow2(-eu.y), pow2(-eu.z), pow2(-eu.w));
+          float4 top0[2], top1[2];
+          int eb[2], et[2];
+          // forward: each child's vectors at its segment tops, by epoch
+#pragma unroll
+          for (int side = 0; side < 2; side++) {
+            const int v = child[2 * (u - N) + side];
+            float4 x0, x1;
+            if (v < N) {
+              tip_vector(codes + (size_t)v * P, P, K, lane, x0, x1);
+            } else {
+              const float4 *src = Lt + (size_t)(v - N) * K;
+              x0 = lane < K ? src[lane] : f4(0.f);
+              x1 = lane + 32 < K ? src[lane + 32] : f4(0.f);
+            }
+            const double hv = hgt[v], hu = hgt[u];
+            branch_epochs(s_b, E, hv, hu, eb[side], et[side]);
+            float4 *ch = chain + (size_t)side * g.Emax * K;
+            if (hv >= hu) {  // zero length: one segment, P = I
+              if (lane < K) ch[eb[side] * K + lane] = x0;
+              if (lane + 32 < K) ch[eb[side] * K + lane + 32] = x1;
+            }
+            double lo = hv;
+            int e = eb[side];
+            while (lo < hu) {
+              const double top = (e < E - 1 && s_b[e] < hu) ? s_b[e] : hu;
+              apply_segment(g, RT + (size_t)e * KK, s_mu[e], (float)(top - lo), K, x0, x1, buf, lane);
+              if (lane < K) ch[e * K + lane] = x0;
+              if (lane + 32 < K) ch[e * K + lane + 32] = x1;
+              lo = top;
+              e++;
+            }
+            top0[side] = x0;  // S~ of this child
+            top1[side] = x1;
+          }
+          // adjoint: each child's branch from its top down
+          double dtop = 0.0;  // lane 0: the top-segment terms of both branches
+#pragma unroll
+          for (int side = 0; side < 2; side++) {
+            const int v = child[2 * (u - N) + side];
+            const int o = 1 - side;
+            float4 zb0 = mul4(mul4(uu0, top0[o]), su);  // X~_v
+            float4 zb1 = mul4(mul4(uu1, top1[o]), su);
+            const float4 *ch = chain + (size_t)side * g.Emax * K;
+            double *drow = dseg + (size_t)v * g.Emax;
+            const double hv = hgt[v], hu = hgt[u];
+            for (int e = et[side]; e >= eb[side]; e--) {
+              // mu_e zb . (R_e z - z), z the forward vector at the segment top
+              const float4 z0 = lane < K ? ch[e * K + lane] : f4(0.f);
+              const float4 z1 = lane + 32 < K ? ch[e * K + lane + 32] : f4(0.f);
+              const float *R = RT + (size_t)e * KK;
+              __syncwarp();
+              if (lane < K) buf[lane] = z0;
+              if (lane + 32 < K) buf[lane + 32] = z1;
+              __syncwarp();
+              float4 r0 = f4(0.f), r1 = f4(0.f);
+              for (int j = 0; j < K; j++) {
+                const float4 zj = buf[j];
+                if (lane < K) fma4(r0, R[j * K + lane], zj);
+                if (lane + 32 < K) fma4(r1, R[j * K + lane + 32], zj);
+              }
+              float4 d = mul4(zb0, make_float4(r0.x - z0.x, r0.y - z0.y, r0.z - z0.z, r0.w - z0.w));
+              const float4 d1 = mul4(zb1, make_float4(r1.x - z1.x, r1.y - z1.y, r1.z - z1.z, r1.w - z1.w));
+              d = make_float4(d.x + d1.x, d.y + d1.y, d.z + d1.z, d.w + d1.w);
+              d = warp_sum4(d);
+              if (lane == 0) {
+                const double ds = (P > 0 ? w[0] * (double)d.x : 0.0) + (P > 1 ? w[1] * (double)d.y : 0.0) +
+                                  (P > 2 ? w[2] * (double)d.z : 0.0) + (P > 3 ? w[3] * (double)d.w : 0.0);
+                drow[e] = (double)s_mu[e] * ds;
+              }
+              // zb down this segment
+              const double lo = (e > eb[side]) ? s_b[e - 1] : hv;
+              const double top = (e < et[side]) ? s_b[e] : hu;
+              if (top > lo)
+                apply_segment<true>(g, R, s_mu[e], (float)(top - lo), K, zb0, zb1, buf, lane);
+            }
+            if (lane == 0) {
+              for (int e = 0; e < g.Emax; e++)
+                if (e < eb[side] || e > et[side] || e >= E) drow[e] = 0.0;
+              dtop += drow[et[side]];
+              g.dbot[mt[T_NODE] + v] = drow[eb[side]];
+              g.span[mt[T_NODE] + v] = make_int2(eb[side], et[side]);
+            }
+            if (v >= N) {  // U~_v over L~_v
+              float4 *dst = Lt + (size_t)(v - N) * K;
+              if (lane < K) dst[lane] = zb0;
+              if (lane + 32 < K) dst[lane + 32] = zb1;
+            }
+          }
+          if (lane == 0) g.dh[mt[T_NODE] + u] = dtop;
+        }
+        __syncthreads();
+      }
+      // d lnL / d h_x: the top-segment terms of x's child branches (written by
+      // x's warp) minus the bottom-segment term of x's own branch (written by
+      // its parent's); d lnL / d b_j: over the branches that cross b_j, the
+      // term of the segment below minus the one above.  Fixed order, no
+      // atomics.
+      const int nn = 2 * N - 1;
+      double *dh = g.dh + mt[T_NODE];
+      const double *dbot = g.dbot + mt[T_NODE];
+      const int2 *span = g.span + mt[T_NODE];
+      for (int x = threadIdx.x; x < nn; x += blockDim.x)
+        dh[x] = (x >= N ? dh[x] : 0.0) - (x != root ? dbot[x] : 0.0);
+      for (int j = warp; j < E - 1; j += nwarps) {
+        double acc = 0.0;
+        for (int x = lane; x < nn; x += 32) {
+          if (x == root) continue;
+          const int2 sp = span[x];
+          if (sp.x <= j && j < sp.y) acc += dseg[(size_t)x * g.Emax + j] - dseg[(size_t)x * g.Emax + j + 1];
+        }
+        for (int o = 16; o > 0; o >>= 1) acc += __shfl_xor_sync(0xffffffffu, acc, o);
+        if (lane == 0) g.db[mt[T_BND] + j] = acc;
+      }
+      __syncthreads();
+    }
   }
   // the last CTA to finish resets the queue for the next launch
   if (threadIdx.x == 0) {
@@ -352,6 +548,14 @@ struct epoch_batch {
   // launch shape (autotuned on first evaluation) and graph
   int warps = 0, ctas_per_sm = 0, n_sm = 0;
   cudaGraphExec_t graph = nullptr;
+  // the gradient launch: its buffers (allocated on first use), shape, graph
+  int4 *d_ex = nullptr;
+  double *d_dseg = nullptr, *d_dh = nullptr, *d_db = nullptr, *d_dbot = nullptr;
+  int2 *d_span = nullptr;
+  float4 *d_chain = nullptr;
+  int gwarps = 0, gctas_per_sm = 0;
+  cudaGraphExec_t ggraph = nullptr;
+  bool grad_valid = false;  // the last evaluation was a gradient evaluation
 };
 
 namespace {
@@ -392,43 +596,55 @@ ForestArgs forest_args(epoch_batch *b) {
   a.lnl = b->d_lnl;
   a.ctl = b->d_ctl;
   a.status = b->d_status;
+  a.ex = b->d_ex;
+  a.dseg = b->d_dseg;
+  a.chain = b->d_chain;
+  a.dh = b->d_dh;
+  a.db = b->d_db;
+  a.dbot = b->d_dbot;
+  a.span = b->d_span;
   return a;
 }
 
+constexpr int kMaxCtasPerSm = 3;
+constexpr int kMaxWarps = 8;
+
+template <bool GRAD>
 cudaError_t forest_launch(epoch_batch *b, int warps, int ctas_per_sm) {
   const size_t smem = forest_smem(b, warps);
-  cudaError_t e = cudaFuncSetAttribute(k_forest, cudaFuncAttributeMaxDynamicSharedMemorySize,
+  cudaError_t e = cudaFuncSetAttribute(k_forest<GRAD>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                        (int)smem);
   if (e != cudaSuccess) return e;
   const int grid = std::max(1, std::min(b->T, b->n_sm * ctas_per_sm));
-  k_forest<<<grid, 32 * warps, smem, b->stream>>>(forest_args(b));
+  k_forest<GRAD><<<grid, 32 * warps, smem, b->stream>>>(forest_args(b));
   return cudaGetLastError();
 }
 
 // Autotuner: time every launch shape that fits (warps per CTA x CTAs per SM)
 // on the current inputs and keep the fastest.
-epoch_status forest_tune(epoch_batch *b) {
-  const int cand_w[] = {4, 8};
-  const int cand_c[] = {1, 2, 3};
+template <bool GRAD>
+epoch_status forest_tune(epoch_batch *b, int &best_w, int &best_c) {
+  const int cand_w[] = {4, kMaxWarps};
+  const int cand_c[] = {1, 2, kMaxCtasPerSm};
   cudaEvent_t e0, e1;
   BCK(cudaEventCreate(&e0), "cudaEventCreate");
   BCK(cudaEventCreate(&e1), "cudaEventCreate");
   float best = 1e30f;
-  int bw = 8, bc = 1;
+  int bw = kMaxWarps, bc = 1;
   for (int w : cand_w)
     for (int cps : cand_c) {
       const size_t smem = forest_smem(b, w);
       if (smem * cps > kSmemCap) continue;
       int nb = 0;
-      if (cudaFuncSetAttribute(k_forest, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem) !=
-              cudaSuccess ||
-          cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, k_forest, 32 * w, smem) !=
+      if (cudaFuncSetAttribute(k_forest<GRAD>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                               (int)smem) != cudaSuccess ||
+          cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, k_forest<GRAD>, 32 * w, smem) !=
               cudaSuccess ||
           nb < cps)
         continue;
-      BCK(forest_launch(b, w, cps), "forest launch");  // warm-up
+      BCK(forest_launch<GRAD>(b, w, cps), "forest launch");  // warm-up
       BCK(cudaEventRecord(e0, b->stream), "cudaEventRecord");
-      for (int r = 0; r < 2; r++) BCK(forest_launch(b, w, cps), "forest launch");
+      for (int r = 0; r < 2; r++) BCK(forest_launch<GRAD>(b, w, cps), "forest launch");
       BCK(cudaEventRecord(e1, b->stream), "cudaEventRecord");
       BCK(cudaEventSynchronize(e1), "cudaEventSynchronize");
       float ms = 0.f;
@@ -441,8 +657,8 @@ epoch_status forest_tune(epoch_batch *b) {
     }
   cudaEventDestroy(e0);
   cudaEventDestroy(e1);
-  b->warps = bw;
-  b->ctas_per_sm = bc;
+  best_w = bw;
+  best_c = bc;
   return EPOCH_OK;
 }
 
@@ -455,6 +671,28 @@ cudaError_t balloc(T **p, size_t n) {
 void invalidate(epoch_batch *b) {
   if (b->graph) cudaGraphExecDestroy(b->graph);
   b->graph = nullptr;
+  if (b->ggraph) cudaGraphExecDestroy(b->ggraph);
+  b->ggraph = nullptr;
+}
+
+// Capture the launch of the given shape in a graph (once) and replay it.
+template <bool GRAD>
+epoch_status forest_replay(epoch_batch *b, cudaGraphExec_t &graph, int warps, int ctas) {
+  if (!graph) {
+    cudaGraph_t g = nullptr;
+    BCK(cudaStreamBeginCapture(b->stream, cudaStreamCaptureModeRelaxed), "cudaStreamBeginCapture");
+    cudaError_t e = forest_launch<GRAD>(b, warps, ctas);
+    cudaError_t e2 = cudaStreamEndCapture(b->stream, &g);
+    if (e != cudaSuccess || e2 != cudaSuccess) {
+      if (g) cudaGraphDestroy(g);
+      return bfail(b, EPOCH_ERR_CUDA, "capturing the forest launch failed");
+    }
+    e = cudaGraphInstantiate(&graph, g, 0);
+    cudaGraphDestroy(g);
+    if (e != cudaSuccess) return bfail(b, EPOCH_ERR_CUDA, cudaGetErrorString(e));
+  }
+  BCK(cudaGraphLaunch(graph, b->stream), "cudaGraphLaunch");
+  return EPOCH_OK;
 }
 
 }  // namespace
@@ -562,7 +800,8 @@ void epoch_batch_destroy(epoch_batch *b) {
   invalidate(b);
   void *bufs[] = {b->d_meta, b->d_order, b->d_heights, b->d_child, b->d_lvl_nodes, b->d_lvl_off,
                   b->d_bnd,  b->d_Q,     b->d_pi,      b->d_codes, b->d_w,         b->d_L,
-                  b->d_lnl,  b->d_ctl,   b->d_status};
+                  b->d_lnl,  b->d_ctl,   b->d_status,  b->d_ex,    b->d_dseg,      b->d_chain,
+                  b->d_dh,   b->d_db,    b->d_dbot,    b->d_span};
   for (void *p : bufs)
     if (p) cudaFree(p);
   if (b->h_status) cudaFreeHost(b->h_status);
@@ -575,6 +814,7 @@ const char *epoch_batch_last_error(const epoch_batch *b) { return b ? b->err.c_s
 epoch_status epoch_batch_set_models(epoch_batch *b, const double *boundaries, const double *Q,
                                     const double *pi, int normalise) {
   if (!b) return EPOCH_ERR_ARG;
+  b->grad_valid = false;
   if (!Q || !pi || (b->total_bnd > 0 && !boundaries))
     return bfail(b, EPOCH_ERR_ARG, "NULL model array");
   const int K = b->K;
@@ -625,6 +865,7 @@ epoch_status epoch_batch_set_models(epoch_batch *b, const double *boundaries, co
 
 epoch_status epoch_batch_set_trees(epoch_batch *b, const double *heights, const int *parent) {
   if (!b) return EPOCH_ERR_ARG;
+  b->grad_valid = false;
   if (!heights || !parent) return bfail(b, EPOCH_ERR_ARG, "NULL tree array");
   std::vector<int> child((size_t)2 * b->total_internal), lvl_nodes(b->total_internal), lvl_off;
   std::vector<double> cost(b->T);
@@ -721,6 +962,7 @@ epoch_status epoch_batch_set_trees(epoch_batch *b, const double *heights, const 
 
 epoch_status epoch_batch_set_tip_data(epoch_batch *b, const int *codes, const double *weights) {
   if (!b) return EPOCH_ERR_ARG;
+  b->grad_valid = false;
   if (!codes || !weights) return bfail(b, EPOCH_ERR_ARG, "NULL tip array");
   std::vector<uint8_t> c8(b->total_codes);
   unsigned bad = 0;
@@ -748,24 +990,34 @@ epoch_status epoch_batch_evaluate_async(epoch_batch *b) {
   if ((b->have & 7u) != 7u)
     return bfail(b, EPOCH_ERR_ORDER, "set models, trees and tip data before evaluating");
   if (!b->warps) {
-    epoch_status s = forest_tune(b);
+    epoch_status s = forest_tune<false>(b, b->warps, b->ctas_per_sm);
     if (s != EPOCH_OK) return s;
   }
-  if (!b->graph) {
-    cudaGraph_t g = nullptr;
-    BCK(cudaStreamBeginCapture(b->stream, cudaStreamCaptureModeRelaxed), "cudaStreamBeginCapture");
-    cudaError_t e = forest_launch(b, b->warps, b->ctas_per_sm);
-    cudaError_t e2 = cudaStreamEndCapture(b->stream, &g);
-    if (e != cudaSuccess || e2 != cudaSuccess) {
-      if (g) cudaGraphDestroy(g);
-      return bfail(b, EPOCH_ERR_CUDA, "capturing the forest launch failed");
-    }
-    e = cudaGraphInstantiate(&b->graph, g, 0);
-    cudaGraphDestroy(g);
-    if (e != cudaSuccess) return bfail(b, EPOCH_ERR_CUDA, cudaGetErrorString(e));
+  b->grad_valid = false;
+  return forest_replay<false>(b, b->graph, b->warps, b->ctas_per_sm);
+}
+
+epoch_status epoch_batch_evaluate_gradient_async(epoch_batch *b) {
+  if (!b) return EPOCH_ERR_ARG;
+  if ((b->have & 7u) != 7u)
+    return bfail(b, EPOCH_ERR_ORDER, "set models, trees and tip data before evaluating");
+  if (!b->d_dh) {  // the gradient's buffers, on first use
+    const size_t chain = (size_t)b->n_sm * kMaxCtasPerSm * kMaxWarps * 2 * b->Emax * b->K;
+    BCK(balloc(&b->d_ex, b->total_internal), "cudaMalloc(exponents)");
+    BCK(balloc(&b->d_dseg, (size_t)b->total_nodes * b->Emax), "cudaMalloc(segment terms)");
+    BCK(balloc(&b->d_chain, chain), "cudaMalloc(forward vectors)");
+    BCK(balloc(&b->d_dh, b->total_nodes), "cudaMalloc(height gradient)");
+    BCK(balloc(&b->d_db, b->total_bnd), "cudaMalloc(boundary gradient)");
+    BCK(balloc(&b->d_dbot, b->total_nodes), "cudaMalloc(bottom terms)");
+    BCK(balloc(&b->d_span, b->total_nodes), "cudaMalloc(segment spans)");
   }
-  BCK(cudaGraphLaunch(b->graph, b->stream), "cudaGraphLaunch");
-  return EPOCH_OK;
+  if (!b->gwarps) {
+    epoch_status s = forest_tune<true>(b, b->gwarps, b->gctas_per_sm);
+    if (s != EPOCH_OK) return s;
+  }
+  epoch_status s = forest_replay<true>(b, b->ggraph, b->gwarps, b->gctas_per_sm);
+  b->grad_valid = s == EPOCH_OK;
+  return s;
 }
 
 epoch_status epoch_batch_read(epoch_batch *b, double *lnL) {
@@ -782,6 +1034,21 @@ epoch_status epoch_batch_read(epoch_batch *b, double *lnL) {
                                                        : "non-finite partial likelihood");
   }
   return EPOCH_OK;
+}
+
+epoch_status epoch_batch_read_gradient(epoch_batch *b, double *lnL, double *d_heights,
+                                       double *d_boundaries) {
+  if (!b || !lnL || !d_heights || (b->total_bnd > 0 && !d_boundaries)) return EPOCH_ERR_ARG;
+  if (!b->grad_valid)
+    return bfail(b, EPOCH_ERR_ORDER, "the last evaluation was not a gradient evaluation");
+  BCK(cudaMemcpyAsync(d_heights, b->d_dh, sizeof(double) * b->total_nodes, cudaMemcpyDeviceToHost,
+                      b->stream),
+      "cudaMemcpyAsync(height gradient)");
+  if (b->total_bnd > 0)
+    BCK(cudaMemcpyAsync(d_boundaries, b->d_db, sizeof(double) * b->total_bnd,
+                        cudaMemcpyDeviceToHost, b->stream),
+        "cudaMemcpyAsync(boundary gradient)");
+  return epoch_batch_read(b, lnL);
 }
 
 epoch_status epoch_batch_launch_shape(const epoch_batch *b, int *warps_per_cta, int *ctas_per_sm) {

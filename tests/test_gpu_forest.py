@@ -1,12 +1,14 @@
 """Batched trees (epoch_batch_*): one persistent launch over many uneven
 trees with their own epochs and asymmetric rate matrices, through the C ABI,
-against the FP64 oracle tree by tree (FP32 tolerance: 1e-5 relative lnL)
-and against the single-tree entry points."""
+against the FP64 oracle tree by tree (FP32 tolerance: 1e-5 relative lnL;
+gradients per component as in tests/tolerances.py) and against the
+single-tree entry points."""
 import numpy as np
 import pytest
 
 import oracle
 import synth
+from tolerances import grad_close
 
 pytestmark = pytest.mark.gpu
 
@@ -139,3 +141,67 @@ def test_forest_status_codes(cuda):
         assert e.value.status == 1
     finally:
         binding.epoch_batch_destroy(b)
+
+
+def _gradient_trees(K):
+    """Uneven trees with dated tips, missing data, 1-6 epochs, a two-taxon
+    tree and one stretched so that its longest segment has mu dt = 120."""
+    shapes = [(9, 3), (2, 1), (17, 4), (33, 2), (24, 6), (12, 1)]
+    trees = [synth.tiny_tree_workload(700 + 7 * i + K, K=K, n_taxa=n, n_sites=3, n_epochs=e,
+                                      n_cat=1, reversible=False, dated=True, missing_frac=0.1)
+             for i, (n, e) in enumerate(shapes)]
+    w = trees[-1]
+    f = 120.0 / _longest_mu_segment(w)
+    trees[-1] = w.replace(heights=w.heights * f, boundaries=w.boundaries * f)
+    return trees
+
+
+@pytest.mark.parametrize("K", [6, 50])
+def test_forest_gradient_matches_oracle_tree_by_tree(cuda, K):
+    """d lnL_t / d (node heights, boundaries) of every tree from the batched
+    pre-order adjoint (Eq. convolution differentiated segment by segment),
+    against the oracle's analytic gradient; replays are bitwise equal, and the
+    lnL of the gradient launch equals that of the likelihood launch."""
+    from paper_1309_3075_b300.binding import EPOCH_FP32, EpochBatch
+    trees = _gradient_trees(K)
+    b = EpochBatch(trees)
+    try:
+        lnl, dh, db = b.evaluate_gradient()
+        lnl2, dh2, db2 = b.evaluate_gradient()
+        plain = b.evaluate()
+    finally:
+        b.close()
+    for t, w in enumerate(trees):
+        ref = oracle.gradient(w)
+        assert abs(lnl[t] - ref["lnL"]) <= TOL * abs(ref["lnL"]), (t, lnl[t], ref["lnL"])
+        assert abs(lnl[t] - plain[t]) <= 1e-12 * abs(plain[t])
+        ok, worst = grad_close(dh[t], ref["heights"], EPOCH_FP32)
+        assert ok, ("heights", t, worst, dh[t], ref["heights"])
+        if w.n_epochs > 1:
+            scale = max(np.abs(ref["boundaries"]).max(), np.abs(ref["heights"]).max())
+            ok, worst = grad_close(db[t], ref["boundaries"], EPOCH_FP32, scale)
+            assert ok, ("boundaries", t, worst, db[t], ref["boundaries"])
+        else:
+            assert db[t].size == 0
+        assert np.array_equal(dh[t], dh2[t]) and np.array_equal(db[t], db2[t])
+
+
+def test_forest_gradient_needs_a_gradient_evaluation(cuda):
+    from paper_1309_3075_b300 import binding
+    from paper_1309_3075_b300.binding import EpochBatch, EpochError
+    trees = _gradient_trees(6)[:2]
+    b = EpochBatch(trees)
+    try:
+        b.evaluate()
+        with pytest.raises(EpochError) as e:
+            binding.epoch_batch_read_gradient(b.b, 2, sum(2 * w.n_taxa - 1 for w in trees),
+                                              sum(w.n_epochs - 1 for w in trees))
+        assert e.value.status == 2
+        b.evaluate_gradient()
+        b.load(trees)  # new inputs: the gradient must be evaluated again
+        with pytest.raises(EpochError) as e:
+            binding.epoch_batch_read_gradient(b.b, 2, sum(2 * w.n_taxa - 1 for w in trees),
+                                              sum(w.n_epochs - 1 for w in trees))
+        assert e.value.status == 2
+    finally:
+        b.close()

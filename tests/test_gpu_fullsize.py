@@ -198,3 +198,35 @@ def test_forest_full_size_sampled_trees():
     for t in pick:
         ref = oracle.log_likelihood(bw.trees[t])[0]
         assert abs(got[t] - ref) <= 1e-5 * abs(ref), (t, got[t], ref)
+
+
+def test_forest_gradient_full_size_sampled_trees():
+    """The batched lnL + gradient launch over all 256 trees; the oracle's
+    gradient (a few seconds per 400-taxon tree at K = 50) checks the three
+    smallest trees and the smallest tree with 8 epochs."""
+    torch = pytest.importorskip("torch")
+    if not torch.cuda.is_available():
+        pytest.skip("needs a GPU")
+    from paper_1309_3075_b300.binding import EpochBatch
+    bw = synth.asym50_forest()
+    b = EpochBatch(bw.trees)
+    try:
+        lnl, dh, db = b.evaluate_gradient()
+    finally:
+        b.close()
+    assert np.all(np.isfinite(lnl))
+    sizes = np.array([t.n_taxa for t in bw.trees])
+    order = np.argsort(sizes, kind="stable")
+    pick = [int(order[i]) for i in (0, 1, 2)]
+    eight = [t for t in range(len(bw.trees)) if bw.trees[t].n_epochs == 8]
+    pick.append(min(eight, key=lambda t: bw.trees[t].n_taxa))
+    for t in pick:
+        w = bw.trees[t]
+        ref = oracle.gradient(w)
+        assert abs(lnl[t] - ref["lnL"]) <= 1e-5 * abs(ref["lnL"]), (t, lnl[t], ref["lnL"])
+        ok, worst = grad_close(dh[t], ref["heights"], EPOCH_FP32)
+        assert ok, ("heights", t, worst)
+        if w.n_epochs > 1:
+            scale = max(np.abs(ref["boundaries"]).max(), np.abs(ref["heights"]).max())
+            ok, worst = grad_close(db[t], ref["boundaries"], EPOCH_FP32, scale)
+            assert ok, ("boundaries", t, worst)
