@@ -74,61 +74,129 @@ def make_workload(name):
 
 
 # ---------------------------------------------------------------------------
-# clocks sampled during the timed region
+# clocks sampled during the timed regions (read-only NVML queries)
 # ---------------------------------------------------------------------------
-class ClockSampler:
-    Q = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
-         "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
-         "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+class _Nvml:
+    """The few read-only NVML queries the sampler needs, through ctypes on the
+    driver's libnvidia-ml (no Python NVML package needed)."""
 
-    def __init__(self, index=0):
-        self.index = index
-        self.proc = None
-        self.lines = []
+    CLOCK_SM = 1
+    # clock-event reason bits (nvml.h)
+    REASONS = {"sw_power_cap": 0x4, "hw_slowdown": 0x8, "sw_thermal_slowdown": 0x20,
+               "hw_thermal_slowdown": 0x40}
+
+    def __init__(self):
+        import ctypes
+        self.C = ctypes
+        self.lib = ctypes.CDLL("libnvidia-ml.so.1")
+        rc = self.lib.nvmlInit_v2()
+        if rc != 0:
+            raise RuntimeError(f"nvmlInit_v2 returned {rc}")
+
+    def handle(self, bus=None, index=0):
+        h = self.C.c_void_p()
+        rc = 1
+        if bus:
+            rc = self.lib.nvmlDeviceGetHandleByPciBusId_v2(bus.encode(), self.C.byref(h))
+        if rc != 0:
+            rc = self.lib.nvmlDeviceGetHandleByIndex_v2(self.C.c_uint(index), self.C.byref(h))
+        if rc != 0:
+            raise RuntimeError(f"no NVML handle ({rc})")
+        return h
+
+    def sm_clock(self, h):
+        v = self.C.c_uint()
+        rc = self.lib.nvmlDeviceGetClockInfo(h, self.CLOCK_SM, self.C.byref(v))
+        return float(v.value) if rc == 0 else None
+
+    def sm_max_clock(self, h):
+        v = self.C.c_uint()
+        rc = self.lib.nvmlDeviceGetMaxClockInfo(h, self.CLOCK_SM, self.C.byref(v))
+        return float(v.value) if rc == 0 else None
+
+    def reasons(self, h):
+        v = self.C.c_ulonglong()
+        fn = getattr(self.lib, "nvmlDeviceGetCurrentClocksEventReasons", None) or \
+            self.lib.nvmlDeviceGetCurrentClocksThrottleReasons
+        return int(v.value) if fn(h, self.C.byref(v)) == 0 else 0
+
+    def close(self):
+        self.lib.nvmlShutdown()
+
+
+class ClockSampler:
+    """Polls the SM clock and the clock-event reasons of one GPU through NVML
+    from a host thread (about one sample per millisecond), with host
+    timestamps, so that samples can be matched to timed regions as short as a
+    few milliseconds.  Only reads: no clock or other setting is changed."""
+
+    def __init__(self, device=0):
+        self.device = device
+        self.samples = []          # (t, sm_mhz, reasons bit mask)
+        self.windows = {}          # name -> [(t0, t1)]
+        self.sm_max = None
+        self._stop = threading.Event()
+        self._thread = None
+        self._nv = None
+        self.error = None
 
     def start(self):
         try:
-            self.proc = subprocess.Popen(
-                ["nvidia-smi", "-i", str(self.index), f"--query-gpu={self.Q}",
-                 "--format=csv,noheader,nounits", "-lms", "50"],
-                stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
-            self.thread = threading.Thread(target=self._read, daemon=True)
-            self.thread.start()
-            t0 = time.time()
-            while not self.lines and time.time() - t0 < 3.0:  # sampler running before timing
-                time.sleep(0.02)
-            self.lines.clear()
-        except Exception:
-            self.proc = None
+            nv = _Nvml()
+            bus = None
+            try:
+                import torch
+                pr = torch.cuda.get_device_properties(self.device)
+                bus = f"{pr.pci_domain_id:08x}:{pr.pci_bus_id:02x}:{pr.pci_device_id:02x}.0"
+            except Exception:
+                pass
+            h = nv.handle(bus, self.device)
+            self.sm_max = nv.sm_max_clock(h)
+            self._nv = nv
+        except Exception as e:  # no NVML: the line says so
+            self.error = repr(e)[:200]
+            return self
 
-    def _read(self):
-        for line in self.proc.stdout:
-            self.lines.append(line.strip())
+        def run():
+            while not self._stop.is_set():
+                mhz = nv.sm_clock(h)
+                if mhz is not None:
+                    self.samples.append((time.perf_counter(), mhz, nv.reasons(h)))
+                time.sleep(0.001)
+
+        self._thread = threading.Thread(target=run, daemon=True)
+        self._thread.start()
+        t0 = time.time()
+        while not self.samples and time.time() - t0 < 2.0:
+            time.sleep(0.005)
+        return self
+
+    def window(self, name, t0, t1):
+        self.windows.setdefault(name, []).append((t0, t1))
 
     def stop(self):
-        if not self.proc:
-            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["unsampled"]}
-        self.proc.terminate()
-        try:
-            self.proc.wait(timeout=5)
-        except Exception:
-            self.proc.kill()
-        sm, smax, reasons = [], None, set()
-        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
-        for ln in self.lines:
-            f = [x.strip() for x in ln.split(",")]
-            if len(f) < 9:
-                continue
+        self._stop.set()
+        if self._thread:
+            self._thread.join(timeout=2.0)
+        if self._nv:
             try:
-                sm.append(float(f[1]))
-                smax = float(f[2])
-            except ValueError:
-                continue
-            for n, v in zip(names, f[5:9]):
-                if v.lower().startswith("active"):
-                    reasons.add(n)
-        return {"sm_mhz": float(np.median(sm)) if sm else None, "sm_max_mhz": smax,
-                "reasons": sorted(reasons), "samples": len(sm)}
+                self._nv.close()
+            except Exception:
+                pass
+
+    def summary(self, names):
+        """Median SM clock and the reasons seen over the samples inside the
+        named windows."""
+        if self._nv is None:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["unsampled"], "samples": 0,
+                    "error": self.error}
+        spans = [w for n in names for w in self.windows.get(n, [])]
+        inside = [smp for smp in self.samples if any(a <= smp[0] <= b for a, b in spans)]
+        sm = [x[1] for x in inside]
+        reasons = sorted({k for _, _, r in inside for k, f in _Nvml.REASONS.items() if r & f})
+        return {"sm_mhz": float(np.median(sm)) if sm else None, "sm_max_mhz": self.sm_max,
+                "reasons": reasons, "samples": len(sm), "windows": list(names),
+                "source": "NVML (libnvidia-ml), about 1 ms period"}
 
 
 # ---------------------------------------------------------------------------
@@ -249,6 +317,23 @@ def job_rate(units_per_rank, seconds, world):
     return world * units_per_rank / seconds
 
 
+def timed_replays(stream, fn, reps):
+    """ms per call of fn() over reps calls, CUDA events on the launching
+    stream, synchronized on both sides; also the host span for the clock
+    windows."""
+    import torch
+
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    e0.record(stream)
+    for _ in range(reps):
+        fn()
+    e1.record(stream)
+    torch.cuda.synchronize()
+    return e0.elapsed_time(e1) / reps, (t0, time.perf_counter())
+
+
 def run_ours(args, w, cfg, rank, world):
     import torch
 
@@ -258,48 +343,33 @@ def run_ours(args, w, cfg, rank, world):
     dev = rank % max(torch.cuda.device_count(), 1)
     torch.cuda.set_device(dev)
     stream = torch.cuda.Stream()
-    # above 8 states the contractions run on the tensor cores (TF32 x 3 split,
-    # tiles 16, 32 or 64 states wide): faster than the SIMT kernels at every
-    # measured K from 9 to 64
     prec = EPOCH_FP32_TC if w.K > 8 else EPOCH_FP32
     lik = EpochLikelihood(w, precision=prec, cuda_stream=stream.cuda_stream)
     nn = 2 * w.n_taxa - 1
+    clocks = ClockSampler(dev).start()
 
     # ---- device-resident timing: K graph replays --------------------------
-    clocks = ClockSampler(dev)
-    clocks.start()
     for _ in range(args.warmup):
         binding.epoch_evaluate_async(lik.ctx, True)
     torch.cuda.synchronize()
     l0, _ = lik.counters()
     if world > 1:
         torch.distributed.barrier()
-    torch.cuda.synchronize()
-    ev0, ev1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
-    ev0.record(stream)
-    for _ in range(args.steps):
-        binding.epoch_evaluate_async(lik.ctx, True)
-    ev1.record(stream)
-    torch.cuda.synchronize()
-    ms = max_over_ranks(ev0.elapsed_time(ev1), world)
-    clk = clocks.stop()
+    ms_raw, span = timed_replays(stream, lambda: binding.epoch_evaluate_async(lik.ctx, True),
+                                 args.steps)
+    clocks.window("step", *span)
+    ms = max_over_ranks(ms_raw * args.steps, world)
     l1, _ = lik.counters()
     launches = l1 - l0
     lnl32, g32 = binding.epoch_read_results(lik.ctx, nn, w.n_epochs, lik.n_params, True)
     ms_step = ms / args.steps
 
-    # ---- the partials pass alone (dominant kernel), same stream ------------
+    # ---- the partials pass alone (dominant kernel of the forward), same stream
     for _ in range(3):
         binding.epoch_update_partials(lik.ctx)
-    torch.cuda.synchronize()
-    reps = max(args.steps, 10)
-    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
-    e0.record(stream)
-    for _ in range(reps):
-        binding.epoch_update_partials(lik.ctx)
-    e1.record(stream)
-    torch.cuda.synchronize()
-    part_ms = e0.elapsed_time(e1) / reps
+    part_ms, span = timed_replays(stream, lambda: binding.epoch_update_partials(lik.ctx),
+                                  max(args.steps, 10))
+    clocks.window("passes", *span)
     pbytes = partials_bytes(w)
 
     # ---- the gradient pass alone (pre-order adjoint, G, chain rule) --------
@@ -307,15 +377,17 @@ def run_ours(args, w, cfg, rank, world):
     # kernels sit between the events (it reads the gradient back at the end)
     gr = max(5, min(args.steps, 50))
     grad_ms = 0.0
-    for _ in range(gr + 2):
+    t0 = time.perf_counter()
+    for i in range(gr + 2):
         binding.epoch_update_partials(lik.ctx)
         g0, g1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
         g0.record(stream)
         binding.epoch_gradient(lik.ctx, nn, w.n_epochs, lik.n_params)
         g1.record(stream)
         torch.cuda.synchronize()
-        if _ >= 2:
+        if i >= 2:
             grad_ms += g0.elapsed_time(g1) / gr
+    clocks.window("passes", t0, time.perf_counter())
     abytes = adjoint_bytes(w)
     achieved = pbytes / (part_ms * 1e-3) / 1e9
     peak, peak_kind = hbm_peak()
@@ -361,7 +433,9 @@ def run_ours(args, w, cfg, rank, world):
             binding.epoch_evaluate_async(lik.ctx, True)
             binding.epoch_read_results(lik.ctx, nn, w.n_epochs, lik.n_params, True)
         torch.cuda.synchronize()
-        return (time.perf_counter() - t0) / e_steps
+        t1 = time.perf_counter()
+        clocks.window("e2e", t0, t1)
+        return (t1 - t0) / e_steps
 
     e2e_s = max_over_ranks(e2e_loop(False), world)
     e2e_aln_s = max_over_ranks(e2e_loop(True), world)
@@ -371,24 +445,21 @@ def run_ours(args, w, cfg, rank, world):
     d2h = 8 + 8 * (2 * nn + w.n_epochs - 1 + lik.n_params)
 
     # ---- plain FP64 GPU path on the same workload --------------------------
-    lik64 = EpochLikelihood(w, precision=EPOCH_FP64, cuda_stream=stream.cuda_stream)
-    for _ in range(2):
-        binding.epoch_evaluate_async(lik64.ctx, True)
-    torch.cuda.synchronize()
-    f_steps = max(3, min(args.steps, 10))
-    f0, f1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
-    f0.record(stream)
-    for _ in range(f_steps):
-        binding.epoch_evaluate_async(lik64.ctx, True)
-    f1.record(stream)
-    torch.cuda.synchronize()
-    fp64_ms = f0.elapsed_time(f1) / f_steps
-    lnl64, g64 = binding.epoch_read_results(lik64.ctx, nn, w.n_epochs, lik64.n_params, True)
-    lik64.close()
+    fp64_ms, lnl64, g64 = time_fp64(w, stream, args, clocks)
     lik.close()
-    forest = run_forest(args, stream) if not args.no_forest else None
     rel_err = abs(lnl32 - lnl64) / abs(lnl64)
     grad_err = float(np.abs(g32["heights"] - g64["heights"]).max() / np.abs(g64["heights"]).max())
+
+    forest = run_forest(args, stream, clocks) if not args.no_forest else None
+    codon = run_codon(args, stream, clocks) if (args.workload == "gtr" and not args.no_codon) else None
+    clocks.stop()
+    clk = clocks.summary(["step"])
+    if clk["samples"] < 3:  # a short timed region: all timed GPU sections
+        clk = clocks.summary(["step", "passes", "fp64", "forest", "codon"])
+    norm = None
+    if clk.get("sm_mhz") and clk.get("sm_max_mhz"):
+        norm = {"ms_per_step_x_sm_mhz": ms_step * clk["sm_mhz"],
+                "ms_per_step_at_max_clock": ms_step * clk["sm_mhz"] / clk["sm_max_mhz"]}
 
     out = {
         "metric": METRIC,
@@ -429,18 +500,151 @@ def run_ours(args, w, cfg, rank, world):
         "lnL": lnl32,
         "clocks": clk,
     }
+    if norm:
+        out["clock_normalised"] = norm
     if forest:
         out["forest"] = forest
+    if codon:
+        out["gy94"] = codon
     return out
 
 
-def run_forest(args, stream):
+def time_fp64(w, stream, args, clocks):
+    """The plain FP64 GPU path (EPOCH_FP64) on the same workload: ms per
+    lnL + gradient evaluation (graph replays), lnL and gradient."""
+    from paper_1309_3075_b300 import binding
+    from paper_1309_3075_b300.binding import EPOCH_FP64, EpochLikelihood
+
+    nn = 2 * w.n_taxa - 1
+    lik64 = EpochLikelihood(w, precision=EPOCH_FP64, cuda_stream=stream.cuda_stream)
+    try:
+        for _ in range(2):
+            binding.epoch_evaluate_async(lik64.ctx, True)
+        ms, span = timed_replays(stream, lambda: binding.epoch_evaluate_async(lik64.ctx, True),
+                                 max(3, min(args.steps, 10)))
+        clocks.window("fp64", *span)
+        lnl64, g64 = binding.epoch_read_results(lik64.ctx, nn, w.n_epochs, lik64.n_params, True)
+    finally:
+        lik64.close()
+    return ms, lnl64, g64
+
+
+# Tensor-pipe activity of the codon path's tcgen05 kernels, from one ncu
+# capture (sm__pipe_tensor_cycles_active over elapsed cycles, cycle-weighted
+# over the captured k_tc_* launches).  Reported only while the kernel source
+# is the one that was measured.
+CODON_TENSOR = {"source": "paper_1309_3075_b300/csrc/k_tc.cu", "sha1": None, "frac": None,
+                "profile": "profiles/tc_codon_gy94.md"}
+
+
+def codon_tensor_frac():
+    import hashlib
+    if not CODON_TENSOR["sha1"]:
+        return None
+    try:
+        with open(os.path.join(ROOT, CODON_TENSOR["source"]), "rb") as f:
+            digest = hashlib.sha1(f.read()).hexdigest()
+    except OSError:
+        return None
+    return CODON_TENSOR["frac"] if digest == CODON_TENSOR["sha1"] else None
+
+
+def run_codon(args, stream, clocks):
+    """The codon workload (GY94, K = 61, 4 epochs, 128 taxa, 5,000 codon
+    sites, 4 categories): lnL + gradient on the tensor-core path (TF32x3
+    tile products) against the plain FP64 GPU path."""
+    from paper_1309_3075_b300 import binding
+    from paper_1309_3075_b300.binding import EPOCH_FP32_TC, EpochLikelihood
+
+    w, cfg = make_workload("gy94")
+    nn = 2 * w.n_taxa - 1
+    lik = EpochLikelihood(w, precision=EPOCH_FP32_TC, cuda_stream=stream.cuda_stream)
+    try:
+        for _ in range(3):
+            binding.epoch_evaluate_async(lik.ctx, True)
+        ms, span = timed_replays(stream, lambda: binding.epoch_evaluate_async(lik.ctx, True),
+                                 max(10, min(args.steps, 50)))
+        clocks.window("codon", *span)
+        lnl, g = binding.epoch_read_results(lik.ctx, nn, w.n_epochs, lik.n_params, True)
+    finally:
+        lik.close()
+    fp64_ms, lnl64, g64 = time_fp64(w, stream, args, clocks)
+    flops = codon_flops(w)
+    return {"workload": cfg["workload"], "patterns": cfg["patterns"], "evals_per_s": 1e3 / ms,
+            "ms_per_step": ms, "dtype": "f32 (tf32x3 tensor-core contractions)",
+            "fp64_gpu_ms_per_step": fp64_ms, "speedup_vs_fp64": fp64_ms / ms,
+            "lnL_rel_err_vs_fp64": abs(lnl - lnl64) / abs(lnl64),
+            "grad_rel_err_vs_fp64": float(np.abs(g["params"] - g64["params"]).max()
+                                          / np.abs(g64["params"]).max()),
+            "tile_product_tflops": flops / (ms * 1e-3) / 1e12,
+            "tensor_pipe_active_frac": codon_tensor_frac(),
+            "tensor_profile": CODON_TENSOR["profile"]}
+
+
+def codon_flops(w):
+    """Useful FLOPs of the tensor-core tile products of one lnL + gradient
+    evaluation at K states (unpadded): for every internal non-root node v,
+    S_v = P_v L_v in pruning, S_v again and U_v = P_v^T X_v in the adjoint,
+    2 K^2 per (category, pattern) each.  Tips take table rows instead."""
+    K, C, P, N = w.K, w.n_categories, w.n_patterns, w.n_taxa
+    stored = N - 2
+    return 2.0 * K * K * C * P * 3 * stored
+
+
+def forest_flops(bw):
+    """Useful FP32 FLOPs of one evaluation of the batched trees: every
+    uniformisation term is a K x K matrix applied to the tree's P_t pattern
+    vectors (2 K^2 P_t), with the kernel's own truncation (Poisson tail below
+    1e-9, pieces of mu dt <= 30) counted term by term on the host."""
+    total = 0.0
+    for w in bw.trees:
+        K, P = w.K, w.n_patterns
+        mus = []
+        for e in range(w.n_epochs):
+            q = np.asarray(w.Q)[np.asarray(w.epoch_to_matrix)[e]]
+            c = -(np.asarray(w.pi) * np.diag(q)).sum() if getattr(w, "normalise", 1) else 1.0
+            c = c if c > 0 else 1.0
+            mus.append(np.max(-np.diag(q)) / c)
+        mus = np.array(mus)
+        parent = np.asarray(w.parent)
+        h = np.asarray(w.heights)
+        v = np.where(parent >= 0)[0]
+        lo, hi = h[v], h[parent[v]]
+        edges = np.r_[-np.inf, np.asarray(w.boundaries), np.inf]
+        seg = np.clip(np.minimum(hi[:, None], edges[None, 1:])
+                      - np.maximum(lo[:, None], edges[None, :-1]), 0.0, None)
+        mt = (seg * mus[None, :]).ravel()
+        mt = mt[mt > 0]
+        pieces = np.where(mt > 30.0, np.ceil(mt / 30.0), 1.0)
+        mp = mt / pieces
+        wgt = np.exp(-mp)
+        terms = np.zeros_like(mp)
+        live = np.ones(mp.shape, bool)
+        m = 0
+        while live.any() and m < 4096:
+            r = (m + 1) - mp
+            done = live & (r > 0) & (wgt * (m + 1) <= 1e-9 * r)
+            live &= ~done
+            m += 1
+            terms[live] += 1
+            wgt = wgt * mp / m
+        total += float((terms * pieces).sum()) * 2.0 * K * K * P
+    return total
+
+
+def fp32_simt_peak(sm_mhz):
+    """FP32 FMA peak of the part: 148 SMs x 128 FP32 lanes x 2 FLOP per clock."""
+    return 148 * 128 * 2 * sm_mhz * 1e6 / 1e12
+
+
+def run_forest(args, stream, clocks):
     """The batched trait workload: 256 coalescent trees (50-1000 taxa, 1-8
     epochs, K = 50 asymmetric rates, 1-4 patterns) in one persistent launch
-    replayed from a CUDA graph (epoch_batch_*)."""
-    import torch
-
+    replayed from a CUDA graph (epoch_batch_*).  Its partials (about 67 MB)
+    fit in L2, so it is bound by the FP32 uniformisation arithmetic, reported
+    against the FP32 FMA peak at the sampled SM clock."""
     import synth
+    from paper_1309_3075_b300 import binding
     from paper_1309_3075_b300.binding import EpochBatch
 
     bw = synth.asym50_forest()
@@ -448,48 +652,102 @@ def run_forest(args, stream):
     try:
         for _ in range(max(3, args.warmup)):  # the first call tunes the launch shape
             fb.evaluate()
-        reps = max(10, min(args.steps, 50))
-        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
-        from paper_1309_3075_b300 import binding
-        torch.cuda.synchronize()
-        e0.record(stream)
-        for _ in range(reps):
-            binding.epoch_batch_evaluate_async(fb.b)
-        e1.record(stream)
-        torch.cuda.synchronize()
-        ms = e0.elapsed_time(e1) / reps
+        ms, span = timed_replays(stream, lambda: binding.epoch_batch_evaluate_async(fb.b),
+                                 max(10, min(args.steps, 50)))
+        clocks.window("forest", *span)
         lnl = fb.evaluate()
         warps, ctas = fb.launch_shape()
+        # lnL + gradient (heights, boundaries) of every tree in one launch
+        for _ in range(3):  # the first call tunes this launch's shape
+            fb.evaluate_gradient()
+        gms, span = timed_replays(stream, lambda: binding.epoch_batch_evaluate_gradient_async(fb.b),
+                                  max(10, min(args.steps, 50)))
+        clocks.window("forest", *span)
     finally:
         fb.close()
     n_tax = sum(t.n_taxa for t in bw.trees)
+    flops = forest_flops(bw)
+    clk = clocks.summary(["forest"]).get("sm_mhz") or clocks.sm_max or 2032.0
+    peak = fp32_simt_peak(clk)
+    achieved = flops / (ms * 1e-3) / 1e12
     return {"workload": f"{len(bw.trees)} trees, {n_tax} taxa in all, K=50 asymmetric, "
                         "1-8 epochs, 1-4 patterns, one launch per evaluation",
             "batch_evals_per_s": 1e3 / ms, "tree_evals_per_s": len(bw.trees) * 1e3 / ms,
             "ms_per_batch": ms, "launch_shape": {"warps_per_cta": warps, "ctas_per_sm": ctas},
-            "lnL_sum": float(np.sum(lnl))}
+            "with_gradient": {"ms_per_batch": gms, "batch_evals_per_s": 1e3 / gms,
+                              "tree_evals_per_s": len(bw.trees) * 1e3 / gms,
+                              "outputs": "lnL, d lnL/d heights and d lnL/d boundaries per tree"},
+            "lnL_sum": float(np.sum(lnl)),
+            "roofline": {"bound": "alu", "achieved": achieved, "peak": peak, "unit": "TFLOP/s",
+                         "frac": achieved / peak, "traffic": None,
+                         "peak_source": f"derived: 148 SMs x 128 FP32 lanes x 2 FLOP x {clk:.0f} MHz",
+                         "algorithmic_flops": flops,
+                         "kernel": "k_forest (uniformisation terms, K x K matrix on the "
+                                   "pattern vectors)"}}
 
 
-def oracle_sample_rate(w, budget_s):
-    """Oracle lnL + gradient on pattern slices of the workload; returns
-    (evals/s scaled to the full workload, description, cores)."""
+def _oracle_slice(w):
+    """One oracle lnL + gradient on a pattern slice (a process-pool worker)."""
     import oracle
 
+    return oracle.gradient(w)["lnL"]
+
+
+def oracle_rates(w, budget_s, cores=None):
+    """The FP64 CPU oracle, as it stands, on the host cores.
+
+    * all cores: the full workload's patterns split into one slice per core,
+      each an independent oracle lnL + gradient in a spawned worker process
+      (patterns are independent, so lnL and the gradient are the sums over
+      slices); one evaluation of the whole workload per round;
+    * one core: the oracle on the first 1,000 patterns in this process,
+      scaled to the full pattern count.
+    Returns {"multi": (rate, description, cores), "single": (rate,
+    description)}; rates in evaluations of the full workload per second."""
+    import multiprocessing as mp
+
+    import oracle
+
+    oracle.build()
     P = w.n_patterns
+    cores = cores or len(os.sched_getaffinity(0))
+    cuts = np.linspace(0, P, cores + 1).astype(int)
+    slices = [w.slice_patterns(int(a), int(b)) for a, b in zip(cuts[:-1], cuts[1:]) if b > a]
+    with mp.get_context("spawn").Pool(len(slices)) as pool:
+        pool.map(_oracle_slice, slices)  # workers load the oracle
+        n = 0
+        t0 = time.perf_counter()
+        while True:
+            pool.map(_oracle_slice, slices)
+            n += 1
+            if time.perf_counter() - t0 > budget_s:
+                break
+        dt = (time.perf_counter() - t0) / n
+    multi = (1.0 / dt, f"{n} lnL+gradient evaluations of all {P} patterns, split into "
+                       f"{len(slices)} slices on {len(slices)} spawned worker processes",
+             len(slices))
     sl = min(P, 1000)
     sub = w.slice_patterns(0, sl)
-    oracle.build()
-    n = 0
+    m = 0
     t0 = time.perf_counter()
     while True:
         oracle.gradient(sub)
-        n += 1
+        m += 1
         if time.perf_counter() - t0 > budget_s:
             break
-    dt = time.perf_counter() - t0
-    per_full = dt / n * (P / sl)
-    return 1.0 / per_full, f"{n} lnL+gradient evaluations on the first {sl} of {P} patterns " \
-                           f"(oracle, single thread), scaled by {P}/{sl}", 1
+    per_full = (time.perf_counter() - t0) / m * (P / sl)
+    single = (1.0 / per_full, f"{m} lnL+gradient evaluations on the first {sl} of {P} "
+                              f"patterns (one thread), scaled by {P}/{sl}")
+    return {"multi": multi, "single": single}
+
+
+def cpu_baseline(w, budget_s):
+    r = oracle_rates(w, budget_s)
+    rate, sample, cores = r["multi"]
+    return {"value": rate, "unit": UNIT, "cores": cores, "kind": "oracle", "sample": sample,
+            "nproc": os.cpu_count(),
+            "single_thread": {"value": r["single"][0], "unit": UNIT, "cores": 1,
+                              "sample": r["single"][1]}}
 
 
 def main():
@@ -502,6 +760,8 @@ def main():
     ap.add_argument("--cpu-seconds", type=float, default=12.0)
     ap.add_argument("--no-forest", action="store_true",
                     help="skip the batched 256-tree measurement")
+    ap.add_argument("--no-codon", action="store_true",
+                    help="skip the codon (GY94) measurement beside the default workload")
     args = ap.parse_args()
     world = int(os.environ.get("WORLD_SIZE", "1"))
     rank = int(os.environ.get("RANK", "0"))
@@ -510,13 +770,15 @@ def main():
     if args.impl == "reference":
         if rank != 0:
             return
-        rate, sample, cores = oracle_sample_rate(w, args.cpu_seconds * max(args.steps, 1) / 50)
+        # the oracle on all host cores; each timed step is one evaluation of
+        # the whole workload, the run bounded to about a minute
+        base = cpu_baseline(w, min(60.0, args.cpu_seconds * max(args.steps, 1) / 50))
+        rate = base["value"]
         out = {"impl": "reference", "metric": METRIC, "value": rate, "unit": UNIT, "n_gpus": 0,
                "steps": args.steps, "warmup": args.warmup, "higher_is_better": True,
                "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
                "config": {**cfg, "parallelism": "cpu"},
-               "cpu_baseline": {"value": rate, "unit": UNIT, "cores": cores, "kind": "oracle",
-                                "sample": sample},
+               "cpu_baseline": base,
                "e2e": {"value": rate, "unit": UNIT, "h2d_bytes_per_step": 0,
                        "d2h_bytes_per_step": 0}}
         print(json.dumps(out))
@@ -530,9 +792,7 @@ def main():
         dist.init_process_group("nccl")
     out = run_ours(args, w, cfg, rank, world)
     if rank == 0:
-        rate, sample, cores = oracle_sample_rate(w, args.cpu_seconds)
-        out["cpu_baseline"] = {"value": rate, "unit": UNIT, "cores": cores, "kind": "oracle",
-                               "sample": sample}
+        out["cpu_baseline"] = cpu_baseline(w, args.cpu_seconds)
         print(json.dumps(out))
     if world > 1:
         import torch.distributed as dist
