@@ -338,13 +338,17 @@ def run_ours(args, w, cfg, rank, world):
     import torch
 
     from paper_1309_3075_b300 import binding
-    from paper_1309_3075_b300.binding import EPOCH_FP32, EPOCH_FP32_TC, EPOCH_FP64, EpochLikelihood
+    from paper_1309_3075_b300.binding import (EPOCH_FP32, EPOCH_FP32_AUTO, EPOCH_FP32_TC,
+                                              EpochLikelihood)
 
     dev = rank % max(torch.cuda.device_count(), 1)
     torch.cuda.set_device(dev)
     stream = torch.cuda.Stream()
-    prec = EPOCH_FP32_TC if w.K > 8 else EPOCH_FP32
-    lik = EpochLikelihood(w, precision=prec, cuda_stream=stream.cuda_stream)
+    # K = 4 has its own FP32 path; other K take whichever FP32 path (SIMT or
+    # tensor-core tile products) the library's probe measures faster
+    lik = EpochLikelihood(w, precision=EPOCH_FP32 if w.K == 4 else EPOCH_FP32_AUTO,
+                          cuda_stream=stream.cuda_stream)
+    prec, probe_simt, probe_tc = binding.epoch_path_info(lik.ctx)
     nn = 2 * w.n_taxa - 1
     clocks = ClockSampler(dev).start()
 
@@ -498,6 +502,8 @@ def run_ours(args, w, cfg, rank, world):
                      "lnL_rel_err_fp32_vs_fp64": rel_err, "grad_rel_err_fp32_vs_fp64": grad_err,
                      "speedup": fp64_ms / ms_step},
         "lnL": lnl32,
+        "path": {"precision_in_use": {1: "EPOCH_FP32", 2: "EPOCH_FP32_TC"}.get(prec, str(prec)),
+                 "probe_ms_simt": probe_simt, "probe_ms_tc": probe_tc},
         "clocks": clk,
     }
     if norm:
@@ -554,11 +560,12 @@ def run_codon(args, stream, clocks):
     sites, 4 categories): lnL + gradient on the tensor-core path (TF32x3
     tile products) against the plain FP64 GPU path."""
     from paper_1309_3075_b300 import binding
-    from paper_1309_3075_b300.binding import EPOCH_FP32_TC, EpochLikelihood
+    from paper_1309_3075_b300.binding import EPOCH_FP32_AUTO, EPOCH_FP32_TC, EpochLikelihood
 
     w, cfg = make_workload("gy94")
     nn = 2 * w.n_taxa - 1
-    lik = EpochLikelihood(w, precision=EPOCH_FP32_TC, cuda_stream=stream.cuda_stream)
+    lik = EpochLikelihood(w, precision=EPOCH_FP32_AUTO, cuda_stream=stream.cuda_stream)
+    prec, probe_simt, probe_tc = binding.epoch_path_info(lik.ctx)
     try:
         for _ in range(3):
             binding.epoch_evaluate_async(lik.ctx, True)
@@ -571,7 +578,10 @@ def run_codon(args, stream, clocks):
     fp64_ms, lnl64, g64 = time_fp64(w, stream, args, clocks)
     flops = codon_flops(w)
     return {"workload": cfg["workload"], "patterns": cfg["patterns"], "evals_per_s": 1e3 / ms,
-            "ms_per_step": ms, "dtype": "f32 (tf32x3 tensor-core contractions)",
+            "ms_per_step": ms,
+            "dtype": "f32 (tf32x3 tensor-core contractions)" if prec == EPOCH_FP32_TC else "f32",
+            "path": {"precision_in_use": "EPOCH_FP32_TC" if prec == EPOCH_FP32_TC else "EPOCH_FP32",
+                     "probe_ms_simt": probe_simt, "probe_ms_tc": probe_tc},
             "fp64_gpu_ms_per_step": fp64_ms, "speedup_vs_fp64": fp64_ms / ms,
             "lnL_rel_err_vs_fp64": abs(lnl - lnl64) / abs(lnl64),
             "grad_rel_err_vs_fp64": float(np.abs(g["params"] - g64["params"]).max()

@@ -76,9 +76,22 @@ typedef enum {
 
 typedef enum {
   EPOCH_FP64 = 0,     /* plain FP64 path: one thread per (pattern, category, state) */
-  EPOCH_FP32 = 1,     /* FP32 partials with per-pattern power-of-two rescaling */
-  EPOCH_FP32_TC = 2   /* FP32 partials; dense contractions (K >= 16) on tensor
-                         cores with 3-term BF16 splitting, FP32 accumulate   */
+  EPOCH_FP32 = 1,     /* FP32 partials with per-pattern power-of-two rescaling,
+                         contractions on the FP32 SIMT pipes */
+  EPOCH_FP32_TC = 2,  /* FP32 partials; for 8 < K <= 64 and at most 4
+                         categories the partials contractions (S = P L in
+                         pruning, S and U = P^T X in the adjoint) run on the
+                         tensor cores (tcgen05, tiles 16, 32 or 64 states
+                         wide) as three TF32 products of the split
+                         x = hi + lo (hi hi + hi lo + lo hi), FP32
+                         accumulate; other shapes as EPOCH_FP32 */
+  EPOCH_FP32_AUTO = 3 /* EPOCH_FP32 or EPOCH_FP32_TC, whichever evaluates lnL +
+                         gradient faster for this shape on this device: the
+                         first context of a (K, categories, pattern-count
+                         bucket) times both on a synthetic problem of that
+                         shape and the choice is kept for the process
+                         (epoch_path_info reports it).  K <= 8 or more than
+                         4 categories: EPOCH_FP32 without a probe */
 } epoch_precision;
 
 /* ---- context ----------------------------------------------------------- */
@@ -102,6 +115,15 @@ epoch_status epoch_create(epoch_ctx **out, int states, int n_epochs,
                           int n_categories, int precision, void *cuda_stream);
 
 void epoch_destroy(epoch_ctx *ctx);
+
+/* The path a context runs (an epoch_precision value; EPOCH_FP32_AUTO is
+ * resolved at creation) and, for EPOCH_FP32_AUTO, the probe's lnL + gradient
+ * times in ms on the SIMT and the tensor-core path (-1 when no probe ran or a
+ * path could not run).  Any pointer may be NULL.  Not in the paper: a
+ * report of the library's own choice between two implementations of the
+ * same computation. */
+epoch_status epoch_path_info(const epoch_ctx *ctx, int *precision_in_use, double *probe_ms_simt,
+                             double *probe_ms_tc);
 
 /* Human-readable text of the last failure on this context ("" if none). */
 const char *epoch_last_error(const epoch_ctx *ctx);

@@ -389,6 +389,15 @@ const char *epoch_status_string(epoch_status s) {
 
 const char *epoch_last_error(const epoch_ctx *c) { return c ? c->err.c_str() : "null context"; }
 
+epoch_status epoch_path_info(const epoch_ctx *c, int *precision_in_use, double *probe_ms_simt,
+                             double *probe_ms_tc) {
+  if (!c) return EPOCH_ERR_ARG;
+  if (precision_in_use) *precision_in_use = c->precision;
+  if (probe_ms_simt) *probe_ms_simt = c->probe_ms_simt;
+  if (probe_ms_tc) *probe_ms_tc = c->probe_ms_tc;
+  return EPOCH_OK;
+}
+
 epoch_status epoch_counters(const epoch_ctx *c, long long *kernel_launches,
                             long long *graph_captures) {
   if (!c) return EPOCH_ERR_ARG;
@@ -441,7 +450,7 @@ epoch_status epoch_create(epoch_ctx **out, int states, int n_epochs, const doubl
   if (max_taxa < 2 || max_taxa > 65535) return EPOCH_ERR_ARG;
   if (n_patterns < 1) return EPOCH_ERR_ARG;
   if (n_categories < 1 || n_categories > EPOCH_MAX_CATEGORIES) return EPOCH_ERR_ARG;
-  if (precision < EPOCH_FP64 || precision > EPOCH_FP32_TC) return EPOCH_ERR_ARG;
+  if (precision < EPOCH_FP64 || precision > EPOCH_FP32_AUTO) return EPOCH_ERR_ARG;
   if (n_epochs > 1) {
     if (!boundaries) return EPOCH_ERR_ARG;
     for (int j = 0; j < n_epochs - 1; j++) {
@@ -456,8 +465,19 @@ epoch_status epoch_create(epoch_ctx **out, int states, int n_epochs, const doubl
   }
   if (!epoch_to_matrix && n_matrices != n_epochs) return EPOCH_ERR_ARG;
 
+  // EPOCH_FP32_AUTO: the faster FP32 path for this shape, timed once per
+  // process (autotune.cu)
+  double probe_simt = -1.0, probe_tc = -1.0;
+  const int requested = precision;
+  if (precision == EPOCH_FP32_AUTO)
+    precision = resolve_auto(states, n_epochs, n_categories, n_patterns, max_taxa,
+                             (cudaStream_t)cuda_stream, &probe_simt, &probe_tc);
+
   epoch_ctx *c = new (std::nothrow) epoch_ctx();
   if (!c) return EPOCH_ERR_CAPACITY;
+  c->requested_precision = requested;
+  c->probe_ms_simt = probe_simt;
+  c->probe_ms_tc = probe_tc;
   Dims &d = c->d;
   d.K = states;
   d.Kp = (states + 3) / 4 * 4;

@@ -57,7 +57,9 @@ struct epoch_state;  // forward
 struct epoch_ctx {
   epoch::Dims d{};
   int max_taxa = 0;
-  int precision = 0;
+  int precision = 0;            // the path in use (EPOCH_FP32_AUTO resolved)
+  int requested_precision = 0;  // as passed to epoch_create
+  double probe_ms_simt = -1.0, probe_ms_tc = -1.0;  // EPOCH_FP32_AUTO's timings
   cudaStream_t stream = nullptr;
   bool own_stream = false;
   // side branches: work no later kernel of the pass needs runs off the main
@@ -206,6 +208,8 @@ cudaError_t launch_expected_counts(epoch_ctx *c, double *d_per_branch, double *d
 cudaError_t launch_ancestral(epoch_ctx *c, double *d_out);  // [N-1][P][K]
 // k_k4.cu (FP32, K = 4)
 int k4_tiles(int P);                            // pattern tiles of the K = 4 kernels
+int resolve_auto(int K, int E, int C, int P, int max_taxa, cudaStream_t stream, double *ms_simt,
+                 double *ms_tc);               // EPOCH_FP32_AUTO (autotune.cu)
 cudaError_t launch_pair_tables_k4(epoch_ctx *c); // cherries' code-pair tables
 cudaError_t launch_partials_k4(epoch_ctx *c);   // pruning, rescaling, root log-sum
 cudaError_t launch_preorder_k4(epoch_ctx *c);   // adjoint pass and G

@@ -14,8 +14,8 @@ import pytest
 import oracle
 import synth
 from paper_1309_3075_b300 import binding
-from paper_1309_3075_b300.binding import (EPOCH_FP32, EPOCH_FP32_TC, EPOCH_FP64, EpochError,
-                                          EpochLikelihood)
+from paper_1309_3075_b300.binding import (EPOCH_FP32, EPOCH_FP32_AUTO, EPOCH_FP32_TC, EPOCH_FP64,
+                                          EpochError, EpochLikelihood)
 from tolerances import GRAD_TOL, LNL_TOL, grad_close
 
 pytestmark = pytest.mark.gpu
@@ -334,3 +334,33 @@ def test_impossible_pattern_gives_minus_infinity():
             assert (site[impossible] == -np.inf).all() and np.isfinite(site[~impossible]).all()
         finally:
             lik.close()
+
+
+@pytest.mark.parametrize("K,P", [(4, 300), (7, 200), (12, 150), (20, 257), (61, 130)])
+def test_auto_path_is_the_faster_and_matches_the_oracle(K, P):
+    """EPOCH_FP32_AUTO: the library times its SIMT and tensor-core FP32 paths
+    on a synthetic problem of the same shape and keeps the faster (K <= 8:
+    the SIMT path, no probe); a second context of the shape reuses the
+    choice; the chosen path meets the FP32 tolerances against the oracle."""
+    if K == 61:
+        w = synth.small_codon(61, n_taxa=10, n_sites=P, n_cat=2, n_epochs=2).slice_patterns(0, P)
+    else:
+        w = synth.tiny_tree_workload(330 + K, K=K, n_taxa=14, n_sites=P, n_epochs=3, n_cat=2,
+                                     missing_frac=0.05)
+    lik = EpochLikelihood(w, precision=EPOCH_FP32_AUTO)
+    try:
+        prec, ms_simt, ms_tc = binding.epoch_path_info(lik.ctx)
+    finally:
+        lik.close()
+    if K <= 8:
+        assert prec == EPOCH_FP32 and ms_simt < 0 and ms_tc < 0
+    else:
+        assert ms_simt > 0 and ms_tc > 0, (ms_simt, ms_tc)
+        assert prec == (EPOCH_FP32_TC if ms_tc < ms_simt else EPOCH_FP32), (prec, ms_simt, ms_tc)
+    lik2 = EpochLikelihood(w, precision=EPOCH_FP32_AUTO)
+    try:
+        assert binding.epoch_path_info(lik2.ctx) == (prec, ms_simt, ms_tc)
+    finally:
+        lik2.close()
+    check_lnl(w, EPOCH_FP32_AUTO)
+    check_grad(w, EPOCH_FP32_AUTO)
