@@ -34,6 +34,9 @@ import numpy as np
 ROOT = os.path.dirname(os.path.abspath(__file__))
 sys.path.insert(0, ROOT)
 
+PATH_NAMES = {1: "EPOCH_FP32", 2: "EPOCH_FP32_TC", 4: "EPOCH_FP32_TC_BF16"}
+DTYPES = {1: "f32", 2: "f32 (tf32x3 tensor-core contractions)",
+          4: "f32 (bf16x3 tensor-core contractions)"}
 METRIC = "lnL+gradient evals/sec & partials GB/s (%HBM roofline) vs plain FP64 GPU path at <=1e-5 rel"
 UNIT = "evals/s"
 
@@ -348,7 +351,7 @@ def run_ours(args, w, cfg, rank, world):
     # tensor-core tile products) the library's probe measures faster
     lik = EpochLikelihood(w, precision=EPOCH_FP32 if w.K == 4 else EPOCH_FP32_AUTO,
                           cuda_stream=stream.cuda_stream)
-    prec, probe_simt, probe_tc = binding.epoch_path_info(lik.ctx)
+    prec, probe_simt, probe_tc, probe_bf = binding.epoch_path_info(lik.ctx)
     nn = 2 * w.n_taxa - 1
     clocks = ClockSampler(dev).start()
 
@@ -476,7 +479,7 @@ def run_ours(args, w, cfg, rank, world):
         "higher_is_better": True,
         "scaling": "weak",
         "vs_baseline": None,
-        "dtype": "f32" if prec == EPOCH_FP32 else "f32 (tf32x3 tensor-core contractions)",
+        "dtype": DTYPES.get(prec, "f32"),
         "data": "synthetic (seeded coalescent tree, simulated alignment)",
         "config": {**cfg, "parallelism": f"replicas{world}", "l2": l2_note(w)},
         "e2e": {"value": job_rate(1.0, e2e_s, world), "unit": UNIT, "h2d_bytes_per_step": int(h2d),
@@ -502,8 +505,9 @@ def run_ours(args, w, cfg, rank, world):
                      "lnL_rel_err_fp32_vs_fp64": rel_err, "grad_rel_err_fp32_vs_fp64": grad_err,
                      "speedup": fp64_ms / ms_step},
         "lnL": lnl32,
-        "path": {"precision_in_use": {1: "EPOCH_FP32", 2: "EPOCH_FP32_TC"}.get(prec, str(prec)),
-                 "probe_ms_simt": probe_simt, "probe_ms_tc": probe_tc},
+        "path": {"precision_in_use": PATH_NAMES.get(prec, str(prec)),
+                 "probe_ms_simt": probe_simt, "probe_ms_tc_tf32x3": probe_tc,
+                 "probe_ms_tc_bf16x3": probe_bf},
         "clocks": clk,
     }
     if norm:
@@ -565,7 +569,7 @@ def run_codon(args, stream, clocks):
     w, cfg = make_workload("gy94")
     nn = 2 * w.n_taxa - 1
     lik = EpochLikelihood(w, precision=EPOCH_FP32_AUTO, cuda_stream=stream.cuda_stream)
-    prec, probe_simt, probe_tc = binding.epoch_path_info(lik.ctx)
+    prec, probe_simt, probe_tc, probe_bf = binding.epoch_path_info(lik.ctx)
     try:
         for _ in range(3):
             binding.epoch_evaluate_async(lik.ctx, True)
@@ -579,9 +583,10 @@ def run_codon(args, stream, clocks):
     flops = codon_flops(w)
     return {"workload": cfg["workload"], "patterns": cfg["patterns"], "evals_per_s": 1e3 / ms,
             "ms_per_step": ms,
-            "dtype": "f32 (tf32x3 tensor-core contractions)" if prec == EPOCH_FP32_TC else "f32",
-            "path": {"precision_in_use": "EPOCH_FP32_TC" if prec == EPOCH_FP32_TC else "EPOCH_FP32",
-                     "probe_ms_simt": probe_simt, "probe_ms_tc": probe_tc},
+            "dtype": DTYPES.get(prec, "f32"),
+            "path": {"precision_in_use": PATH_NAMES.get(prec, str(prec)),
+                     "probe_ms_simt": probe_simt, "probe_ms_tc_tf32x3": probe_tc,
+                     "probe_ms_tc_bf16x3": probe_bf},
             "fp64_gpu_ms_per_step": fp64_ms, "speedup_vs_fp64": fp64_ms / ms,
             "lnL_rel_err_vs_fp64": abs(lnl - lnl64) / abs(lnl64),
             "grad_rel_err_vs_fp64": float(np.abs(g["params"] - g64["params"]).max()

@@ -85,13 +85,18 @@ typedef enum {
                          wide) as three TF32 products of the split
                          x = hi + lo (hi hi + hi lo + lo hi), FP32
                          accumulate; other shapes as EPOCH_FP32 */
-  EPOCH_FP32_AUTO = 3 /* EPOCH_FP32 or EPOCH_FP32_TC, whichever evaluates lnL +
-                         gradient faster for this shape on this device: the
-                         first context of a (K, categories, pattern-count
-                         bucket) times both on a synthetic problem of that
-                         shape and the choice is kept for the process
+  EPOCH_FP32_AUTO = 3, /* EPOCH_FP32, EPOCH_FP32_TC or EPOCH_FP32_TC_BF16,
+                         whichever evaluates lnL + gradient fastest for this
+                         shape on this device: the first context of a (K,
+                         categories, pattern-count bucket) times each on a
+                         synthetic problem of that shape and the choice is
+                         kept for the process
                          (epoch_path_info reports it).  K <= 8 or more than
                          4 categories: EPOCH_FP32 without a probe */
+  EPOCH_FP32_TC_BF16 = 4 /* as EPOCH_FP32_TC, with the tile products as BF16 x 3:
+                         x = x1 + x2 + x3 (each part the rest rounded to
+                         BF16), A B ~ A1 B1 + A1 B2 + A2 B1 + A1 B3 + A2 B2 +
+                         A3 B1 on tcgen05 kind::f16, FP32 accumulate */
 } epoch_precision;
 
 /* ---- context ----------------------------------------------------------- */
@@ -118,12 +123,12 @@ void epoch_destroy(epoch_ctx *ctx);
 
 /* The path a context runs (an epoch_precision value; EPOCH_FP32_AUTO is
  * resolved at creation) and, for EPOCH_FP32_AUTO, the probe's lnL + gradient
- * times in ms on the SIMT and the tensor-core path (-1 when no probe ran or a
- * path could not run).  Any pointer may be NULL.  Not in the paper: a
- * report of the library's own choice between two implementations of the
- * same computation. */
+ * times in ms on the SIMT, the TF32 x 3 and the BF16 x 3 tensor-core paths
+ * (-1 when no probe ran or a path could not run).  Any pointer may be NULL.
+ * Not in the paper: a report of the library's own choice between
+ * implementations of the same computation. */
 epoch_status epoch_path_info(const epoch_ctx *ctx, int *precision_in_use, double *probe_ms_simt,
-                             double *probe_ms_tc);
+                             double *probe_ms_tc, double *probe_ms_tc_bf16);
 
 /* Human-readable text of the last failure on this context ("" if none). */
 const char *epoch_last_error(const epoch_ctx *ctx);

@@ -16,7 +16,7 @@ import numpy as np
 _HERE = os.path.dirname(os.path.abspath(__file__))
 LIB_PATH = os.path.join(_HERE, "libepoch.so")
 
-EPOCH_FP64, EPOCH_FP32, EPOCH_FP32_TC, EPOCH_FP32_AUTO = 0, 1, 2, 3
+EPOCH_FP64, EPOCH_FP32, EPOCH_FP32_TC, EPOCH_FP32_AUTO, EPOCH_FP32_TC_BF16 = 0, 1, 2, 3, 4
 STATUS = {0: "EPOCH_OK", 1: "EPOCH_ERR_ARG", 2: "EPOCH_ERR_ORDER", 3: "EPOCH_ERR_CAPACITY",
           4: "EPOCH_ERR_NUMERIC", 5: "EPOCH_ERR_CUDA", 6: "EPOCH_ERR_TIMEOUT",
           7: "EPOCH_ERR_UNSUPPORTED"}
@@ -39,7 +39,7 @@ _SIGS = {
                      C.c_int, C.c_int, _vp],
     "epoch_destroy": [_vp],
     "epoch_last_error": [_vp],
-    "epoch_path_info": [_vp, _ip, _dp, _dp],
+    "epoch_path_info": [_vp, _ip, _dp, _dp, _dp],
     "epoch_status_string": [C.c_int],
     "epoch_set_boundaries": [_vp, _dp],
     "epoch_set_rate_matrices": [_vp, _dp, _dp, C.c_int, C.c_int],
@@ -295,10 +295,11 @@ def epoch_read_results_device(ctx, lnl_ptr=0, grad_ptr=0):
 
 
 def epoch_path_info(ctx):
-    """(precision in use, probe ms SIMT, probe ms tensor cores)."""
-    p, a, b = C.c_int(0), C.c_double(0.0), C.c_double(0.0)
-    _check(ctx, lib().epoch_path_info(ctx, C.byref(p), C.byref(a), C.byref(b)), "epoch_path_info")
-    return p.value, a.value, b.value
+    """(precision in use, probe ms SIMT, probe ms TF32 x 3, probe ms BF16 x 3)."""
+    p, a, b, e = C.c_int(0), C.c_double(0.0), C.c_double(0.0), C.c_double(0.0)
+    _check(ctx, lib().epoch_path_info(ctx, C.byref(p), C.byref(a), C.byref(b), C.byref(e)),
+           "epoch_path_info")
+    return p.value, a.value, b.value, e.value
 
 
 def epoch_counters(ctx):

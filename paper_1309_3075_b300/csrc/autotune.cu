@@ -9,9 +9,9 @@
 // first context created with EPOCH_FP32_AUTO for a (K, C, pattern-count
 // bucket) builds a synthetic problem of that shape (a random binary tree of
 // up to 64 taxa, a random reversible Q per epoch with uniform pi and one
-// parameter derivative, random tip codes), evaluates lnL + gradient on both
-// paths through this library's own entry points (graph replays timed with
-// CUDA events after warm-up) and caches the faster path for the process.
+// parameter derivative, random tip codes), evaluates lnL + gradient on each
+// path through this library's own entry points (graph replays timed with
+// CUDA events after warm-up) and caches the fastest for the process.
 #include <math.h>
 #include <stdint.h>
 
@@ -28,7 +28,7 @@ namespace {
 
 struct Probe {
   int precision;
-  double ms_simt, ms_tc;
+  double ms_simt, ms_tc, ms_bf;
 };
 std::mutex g_mu;
 std::map<std::tuple<int, int, int, int>, Probe> g_cache;  // (device, K, C, pattern bucket)
@@ -86,13 +86,13 @@ double time_path(int prec, int K, int C, int P, int N, int E, const std::vector<
 
 }  // namespace
 
-// The path EPOCH_FP32_AUTO resolves to for this shape (EPOCH_FP32 or
-// EPOCH_FP32_TC), with the probe's times; probes once per (device, K, C,
-// pattern bucket).  Shapes the tensor-core path does not take resolve to
-// EPOCH_FP32 without a probe.
+// The path EPOCH_FP32_AUTO resolves to for this shape (EPOCH_FP32,
+// EPOCH_FP32_TC or EPOCH_FP32_TC_BF16), with the probe's times; probes once
+// per (device, K, C, pattern bucket).  Shapes the tensor-core paths do not
+// take resolve to EPOCH_FP32 without a probe.
 int resolve_auto(int K, int E, int C, int P, int max_taxa, cudaStream_t stream, double *ms_simt,
-                 double *ms_tc) {
-  *ms_simt = *ms_tc = -1.0;
+                 double *ms_tc, double *ms_bf) {
+  *ms_simt = *ms_tc = *ms_bf = -1.0;
   if (K <= 8 || K > 64 || C > 4) return EPOCH_FP32;
   int dev = 0;
   if (cudaGetDevice(&dev) != cudaSuccess) return EPOCH_FP32;
@@ -105,6 +105,7 @@ int resolve_auto(int K, int E, int C, int P, int max_taxa, cudaStream_t stream, 
     if (it != g_cache.end()) {
       *ms_simt = it->second.ms_simt;
       *ms_tc = it->second.ms_tc;
+      *ms_bf = it->second.ms_bf;
       return it->second.precision;
     }
   }
@@ -153,15 +154,22 @@ int resolve_auto(int K, int E, int C, int P, int max_taxa, cudaStream_t stream, 
   std::vector<double> w(Pp, 1.0);
   const double ms_s = time_path(EPOCH_FP32, K, C, Pp, N, E, b, Q, dQ, pi, heights, parent, codes, w, stream);
   const double ms_t = time_path(EPOCH_FP32_TC, K, C, Pp, N, E, b, Q, dQ, pi, heights, parent, codes, w, stream);
+  const double ms_b = time_path(EPOCH_FP32_TC_BF16, K, C, Pp, N, E, b, Q, dQ, pi, heights, parent, codes, w, stream);
   cudaGetLastError();
-  Probe pr{EPOCH_FP32, ms_s, ms_t};
-  if (ms_t > 0.0 && (ms_s < 0.0 || ms_t < ms_s)) pr.precision = EPOCH_FP32_TC;
+  Probe pr{EPOCH_FP32, ms_s, ms_t, ms_b};
+  double best = ms_s > 0.0 ? ms_s : 1e300;
+  if (ms_t > 0.0 && ms_t < best) {
+    best = ms_t;
+    pr.precision = EPOCH_FP32_TC;
+  }
+  if (ms_b > 0.0 && ms_b < best) pr.precision = EPOCH_FP32_TC_BF16;
   {
     std::lock_guard<std::mutex> lk(g_mu);
     g_cache[key] = pr;
   }
   *ms_simt = ms_s;
   *ms_tc = ms_t;
+  *ms_bf = ms_b;
   return pr.precision;
 }
 

@@ -390,11 +390,12 @@ const char *epoch_status_string(epoch_status s) {
 const char *epoch_last_error(const epoch_ctx *c) { return c ? c->err.c_str() : "null context"; }
 
 epoch_status epoch_path_info(const epoch_ctx *c, int *precision_in_use, double *probe_ms_simt,
-                             double *probe_ms_tc) {
+                             double *probe_ms_tc, double *probe_ms_tc_bf16) {
   if (!c) return EPOCH_ERR_ARG;
   if (precision_in_use) *precision_in_use = c->precision;
   if (probe_ms_simt) *probe_ms_simt = c->probe_ms_simt;
   if (probe_ms_tc) *probe_ms_tc = c->probe_ms_tc;
+  if (probe_ms_tc_bf16) *probe_ms_tc_bf16 = c->probe_ms_bf;
   return EPOCH_OK;
 }
 
@@ -450,7 +451,7 @@ epoch_status epoch_create(epoch_ctx **out, int states, int n_epochs, const doubl
   if (max_taxa < 2 || max_taxa > 65535) return EPOCH_ERR_ARG;
   if (n_patterns < 1) return EPOCH_ERR_ARG;
   if (n_categories < 1 || n_categories > EPOCH_MAX_CATEGORIES) return EPOCH_ERR_ARG;
-  if (precision < EPOCH_FP64 || precision > EPOCH_FP32_AUTO) return EPOCH_ERR_ARG;
+  if (precision < EPOCH_FP64 || precision > EPOCH_FP32_TC_BF16) return EPOCH_ERR_ARG;
   if (n_epochs > 1) {
     if (!boundaries) return EPOCH_ERR_ARG;
     for (int j = 0; j < n_epochs - 1; j++) {
@@ -467,24 +468,25 @@ epoch_status epoch_create(epoch_ctx **out, int states, int n_epochs, const doubl
 
   // EPOCH_FP32_AUTO: the faster FP32 path for this shape, timed once per
   // process (autotune.cu)
-  double probe_simt = -1.0, probe_tc = -1.0;
+  double probe_simt = -1.0, probe_tc = -1.0, probe_bf = -1.0;
   const int requested = precision;
   if (precision == EPOCH_FP32_AUTO)
     precision = resolve_auto(states, n_epochs, n_categories, n_patterns, max_taxa,
-                             (cudaStream_t)cuda_stream, &probe_simt, &probe_tc);
+                             (cudaStream_t)cuda_stream, &probe_simt, &probe_tc, &probe_bf);
 
   epoch_ctx *c = new (std::nothrow) epoch_ctx();
   if (!c) return EPOCH_ERR_CAPACITY;
   c->requested_precision = requested;
   c->probe_ms_simt = probe_simt;
   c->probe_ms_tc = probe_tc;
+  c->probe_ms_bf = probe_bf;
   Dims &d = c->d;
   d.K = states;
   d.Kp = (states + 3) / 4 * 4;
   // the tensor-core tiles are 64, 32 or 16 states wide: pad to the tile width
-  if (precision == EPOCH_FP32_TC && states > 32) d.Kp = 64;
-  if (precision == EPOCH_FP32_TC && states > 16 && states <= 32) d.Kp = 32;
-  if (precision == EPOCH_FP32_TC && states > 8 && states <= 16) d.Kp = 16;
+  if (is_tc_precision(precision) && states > 32) d.Kp = 64;
+  if (is_tc_precision(precision) && states > 16 && states <= 32) d.Kp = 32;
+  if (is_tc_precision(precision) && states > 8 && states <= 16) d.Kp = 16;
   d.KK = states * states;
   d.n_masks = 0;
   d.NR = states + 1;

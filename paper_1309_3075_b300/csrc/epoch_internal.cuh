@@ -59,7 +59,7 @@ struct epoch_ctx {
   int max_taxa = 0;
   int precision = 0;            // the path in use (EPOCH_FP32_AUTO resolved)
   int requested_precision = 0;  // as passed to epoch_create
-  double probe_ms_simt = -1.0, probe_ms_tc = -1.0;  // EPOCH_FP32_AUTO's timings
+  double probe_ms_simt = -1.0, probe_ms_tc = -1.0, probe_ms_bf = -1.0;  // EPOCH_FP32_AUTO's timings
   cudaStream_t stream = nullptr;
   bool own_stream = false;
   // side branches: work no later kernel of the pass needs runs off the main
@@ -209,7 +209,7 @@ cudaError_t launch_ancestral(epoch_ctx *c, double *d_out);  // [N-1][P][K]
 // k_k4.cu (FP32, K = 4)
 int k4_tiles(int P);                            // pattern tiles of the K = 4 kernels
 int resolve_auto(int K, int E, int C, int P, int max_taxa, cudaStream_t stream, double *ms_simt,
-                 double *ms_tc);               // EPOCH_FP32_AUTO (autotune.cu)
+                 double *ms_tc, double *ms_bf);  // EPOCH_FP32_AUTO (autotune.cu)
 cudaError_t launch_pair_tables_k4(epoch_ctx *c); // cherries' code-pair tables
 cudaError_t launch_partials_k4(epoch_ctx *c);   // pruning, rescaling, root log-sum
 cudaError_t launch_preorder_k4(epoch_ctx *c);   // adjoint pass and G
@@ -221,6 +221,8 @@ size_t k4_chain_smem(const Dims &d);            // its shared memory (model tabl
 
 // k_tc.cu (FP32_TC, 4 < K <= 64): tcgen05 tile products
 bool tc_path(const epoch_ctx *c);
+// the tensor-core precisions (TF32 x 3 or BF16 x 3 tile products)
+inline bool is_tc_precision(int p) { return p == EPOCH_FP32_TC || p == EPOCH_FP32_TC_BF16; }
 cudaError_t launch_tc_prep(epoch_ctx *c);          // P and P^T as TF32 hi/lo operands
 cudaError_t launch_tc_pre_u(epoch_ctx *c, int level);  // U = P^T X of one level
 cudaError_t launch_tc_post(epoch_ctx *c, int level);   // pruning + rescaling of one level

@@ -7,18 +7,29 @@
 // 8 < K <= 16), so a branch applied to 128 patterns is one tile product
 //     D[128 x KW] = A[128 x KW] * B^T,   B[n][k] = P[n][k] (S = P L)
 //                                        or  B[n][k] = P[k][n] (U = P^T X),
-// run as tcgen05.mma kind::tf32 (M = 128, N = KW, K = 8 per instruction).
-// FP32 accuracy comes from the three-term split x = hi + lo (hi = x rounded
-// to TF32, lo = the rest rounded to TF32): A B ~ Ahi Bhi + Ahi Blo + Alo Bhi;
-// the dropped Alo Blo is below 2^-22 of the product.
+// run on the tensor cores in one of two operand formats, both accumulated
+// in FP32 in tensor memory (M = 128, N = KW):
+//  * TF32 x 3 (EPOCH_FP32_TC): tcgen05.mma kind::tf32, K = 8 per
+//    instruction.  x = hi + lo (hi = x rounded to TF32, lo = the rest
+//    rounded to TF32): A B ~ Ahi Bhi + Ahi Blo + Alo Bhi; the dropped Alo Blo
+//    is below 2^-22 of the product.
+//  * BF16 x 3 (EPOCH_FP32_TC_BF16): kind::f16 with BF16 A and B, K = 16 per
+//    instruction.  x = x1 + x2 + x3, each the rest so far rounded to BF16 (8
+//    significant bits each, 24 in all): A B ~ A1 B1 + A1 B2 + A2 B1 + A1 B3
+//    + A2 B2 + A3 B1; the dropped terms are below 2^-23 of the product.
 //
 // Operands sit in shared memory in the no-swizzle K-major canonical layout:
-// 8-row x 16-byte core matrices, element (r, k) at byte
-//     (r / 8) * 32 KW + (k / 4) * 128 + (r % 8) * 16 + (k % 4) * 4,
+// 8-row x 16-byte core matrices (4 TF32 or 8 BF16 along K), element (r, k)
+// at byte
+//     TF32: (r / 8) * 32 KW + (k / 4) * 128 + (r % 8) * 16 + (k % 4) * 4,
+//     BF16: (r / 8) * 16 KW + (k / 8) * 128 + (r % 8) * 16 + (k % 8) * 2,
 // i.e. leading-dimension (K) byte offset 128 between core matrices and
-// stride-dimension byte offset 32 KW between 8-row groups.  The B operands of
-// every (branch, category) are laid out once per evaluation (k_tc_prep).
+// stride-dimension byte offset 32 KW (TF32) or 16 KW (BF16) between 8-row
+// groups.  The B operands of every (branch, category) are laid out once per
+// evaluation (k_tc_prep).
 #include <stdint.h>
+
+#include <type_traits>
 
 #include "epoch_internal.cuh"
 
@@ -28,25 +39,48 @@ namespace {
 constexpr int kRows = 128;            // tile rows (patterns)
 constexpr int kTcThr = 128;           // one thread per row; warp w owns TMEM lanes 32w..
 
-// Sizes for the tile width KW, in floats.
-template <int KW>
+// Sizes for the tile width KW and operand format (BF: BF16 x 3, else TF32 x
+// 3), in bytes unless named in floats.
+template <int KW, bool BF>
 struct Tw {
-  static constexpr int B = KW * KW;            // one KW x KW operand
-  static constexpr int A = kRows * KW;         // one 128 x KW operand
-  static constexpr int stage = 2 * A + 2 * B;  // A hi, A lo, B hi, B lo
-  static constexpr int c4 = KW / 4;            // float4 per row
-  static constexpr int pad = KW + 4;           // row-buffer stride (bank spread)
-  static constexpr int buf = kRows * pad;      // one row buffer
+  static constexpr int ES = BF ? 2 : 4;           // bytes per operand element
+  static constexpr int NP = BF ? 3 : 2;           // planes of the split
+  static constexpr int A = kRows * KW * ES;       // one 128 x KW operand plane
+  static constexpr int B = KW * KW * ES;          // one KW x KW operand plane
+  static constexpr int stage = NP * A + NP * B;   // A planes, then B planes
+  static constexpr int c4 = KW / 4;               // float4 per FP32 row
+  static constexpr int pad = KW + 4;              // row-buffer stride in floats (bank spread)
+  static constexpr int buf = kRows * pad;         // one FP32 row buffer, in floats
+  static constexpr int kstep = BF ? 16 : 8;       // K per instruction
+  static constexpr int sbo = BF ? 16 * KW : 32 * KW;  // 8-row group stride
+  // B operands of one (branch, category) in tcB: [post planes | pre planes]
+  static constexpr int vc_floats = 4 * KW * KW;   // per (v, c) stride, either format
 };
 
-template <int KW>
-__device__ __forceinline__ int core_off(int r, int k) {  // in floats
-  return (r >> 3) * (8 * KW) + (k >> 2) * 32 + (r & 7) * 4 + (k & 3);
+template <int KW, bool BF>
+__device__ __forceinline__ int core_off(int r, int k) {  // in bytes
+  return BF ? (r >> 3) * (16 * KW) + (k >> 3) * 128 + (r & 7) * 16 + (k & 7) * 2
+            : (r >> 3) * (32 * KW) + (k >> 2) * 128 + (r & 7) * 16 + (k & 3) * 4;
 }
 __device__ __forceinline__ float to_tf32(float x) {
   uint32_t r;
   asm("cvt.rna.tf32.f32 %0, %1;" : "=r"(r) : "f"(x));
   return __uint_as_float(r);
+}
+// x rounded to BF16 (nearest even): the bits, and the value as FP32
+__device__ __forceinline__ uint16_t to_bf16(float x, float &back) {
+  uint16_t h;
+  asm("cvt.rn.bf16.f32 %0, %1;" : "=h"(h) : "f"(x));
+  back = __uint_as_float((uint32_t)h << 16);
+  return h;
+}
+// The three BF16 parts of x (x1 + x2 + x3 ~ x to 2^-24).
+__device__ __forceinline__ void split3(float x, uint16_t &a, uint16_t &b, uint16_t &c) {
+  float v;
+  a = to_bf16(x, v);
+  const float r1 = x - v;
+  b = to_bf16(r1, v);
+  c = to_bf16(r1 - v, v);
 }
 // x * 2^-e for the binary exponent e of a value in (0, 2] (e in [-148, 1]),
 // exactly: one multiply by 2^-e when -e <= 126, else 2^126 then 2^(-e-126).
@@ -61,59 +95,80 @@ __device__ __forceinline__ float sc(float x, Pow2 f) { return (x * f.a) * f.b; }
 __device__ __forceinline__ uint32_t su32(const void *p) {
   return (uint32_t)__cvta_generic_to_shared(p);
 }
-template <int KW>
+template <int KW, bool BF>
 __device__ __forceinline__ uint64_t smem_desc(uint32_t addr) {
   uint64_t d = (uint64_t)((addr >> 4) & 0x3FFF);
-  d |= (uint64_t)(128 >> 4) << 16;      // leading (K) byte offset
-  d |= (uint64_t)(32 * KW >> 4) << 32;  // stride (8-row group) byte offset
-  d |= (uint64_t)1 << 46;               // descriptor version; no swizzle, base offset 0
+  d |= (uint64_t)(128 >> 4) << 16;              // leading (K) byte offset
+  d |= (uint64_t)(Tw<KW, BF>::sbo >> 4) << 32;  // stride (8-row group) byte offset
+  d |= (uint64_t)1 << 46;                       // descriptor version; no swizzle, base offset 0
   return d;
 }
-// kind::tf32, D = F32, A = B = TF32, both K-major, N = KW, M = 128
-template <int KW>
+// D = F32, A = B = TF32 (kind::tf32) or BF16 (kind::f16), both K-major,
+// N = KW, M = 128
+template <int KW, bool BF>
 __host__ __device__ constexpr uint32_t idesc() {
-  return (1u << 4) | (2u << 7) | (2u << 10) | (((uint32_t)KW >> 3) << 17) | ((128u >> 4) << 24);
+  return (1u << 4) | ((BF ? 1u : 2u) << 7) | ((BF ? 1u : 2u) << 10) |
+         (((uint32_t)KW >> 3) << 17) | ((128u >> 4) << 24);
 }
 
-template <int KW>
-__device__ __forceinline__ void mma_tf32(uint32_t dtmem, uint64_t a, uint64_t b, uint32_t acc) {
-  asm volatile(
-      "{\n.reg .pred p;\nsetp.ne.b32 p, %4, 0;\n"
-      "tcgen05.mma.cta_group::1.kind::tf32 [%0], %1, %2, %3, p;\n}\n" ::"r"(dtmem),
-      "l"(a), "l"(b), "r"(idesc<KW>()), "r"(acc));
+template <int KW, bool BF>
+__device__ __forceinline__ void mma_issue(uint32_t dtmem, uint64_t a, uint64_t b, uint32_t acc) {
+  if constexpr (BF)
+    asm volatile(
+        "{\n.reg .pred p;\nsetp.ne.b32 p, %4, 0;\n"
+        "tcgen05.mma.cta_group::1.kind::f16 [%0], %1, %2, %3, p;\n}\n" ::"r"(dtmem),
+        "l"(a), "l"(b), "r"(idesc<KW, BF>()), "r"(acc));
+  else
+    asm volatile(
+        "{\n.reg .pred p;\nsetp.ne.b32 p, %4, 0;\n"
+        "tcgen05.mma.cta_group::1.kind::tf32 [%0], %1, %2, %3, p;\n}\n" ::"r"(dtmem),
+        "l"(a), "l"(b), "r"(idesc<KW, BF>()), "r"(acc));
 }
 
-// B operands: for every (v, c): [post hi | post lo | pre hi | pre lo], each
-// KW x KW in core order; post = P_v (rows = parent state), pre = P_v^T.
-template <int KW>
+// B operands: for every (v, c): [post planes | pre planes], each KW x KW in
+// core order; post = P_v (rows = parent state), pre = P_v^T.  TF32: planes
+// hi, lo; BF16: the three parts.
+template <int KW, bool BF>
 __global__ void k_tc_prep(Dims d, const double *__restrict__ P64, const int *__restrict__ parent,
                           float *__restrict__ tcB) {
-  constexpr int B = Tw<KW>::B;
+  using W = Tw<KW, BF>;
   const int v = blockIdx.x / d.C, c = blockIdx.x % d.C;
   if (parent[v] < 0) return;
   const double *P = P64 + ((size_t)v * d.C + c) * d.KK;
-  float *out = tcB + ((size_t)v * d.C + c) * 4 * B;
-  for (int idx = threadIdx.x; idx < B; idx += blockDim.x) {
+  unsigned char *out = reinterpret_cast<unsigned char *>(tcB + ((size_t)v * d.C + c) * W::vc_floats);
+  for (int idx = threadIdx.x; idx < KW * KW; idx += blockDim.x) {
     const int r = idx / KW, k = idx % KW;
     const bool in = r < d.K && k < d.K;
     const float vp = in ? (float)P[r * d.K + k] : 0.f;   // post: B[r][k] = P[r][k]
     const float vq = in ? (float)P[k * d.K + r] : 0.f;   // pre:  B[r][k] = P[k][r]
-    const float hp = to_tf32(vp), hq = to_tf32(vq);
-    const int o = core_off<KW>(r, k);
-    out[o] = hp;
-    out[B + o] = to_tf32(vp - hp);
-    out[2 * B + o] = hq;
-    out[3 * B + o] = to_tf32(vq - hq);
+    const int o = core_off<KW, BF>(r, k);
+    if constexpr (BF) {
+      uint16_t a, b, cc;
+      split3(vp, a, b, cc);
+      *reinterpret_cast<uint16_t *>(out + o) = a;
+      *reinterpret_cast<uint16_t *>(out + W::B + o) = b;
+      *reinterpret_cast<uint16_t *>(out + 2 * W::B + o) = cc;
+      split3(vq, a, b, cc);
+      *reinterpret_cast<uint16_t *>(out + 3 * W::B + o) = a;
+      *reinterpret_cast<uint16_t *>(out + 4 * W::B + o) = b;
+      *reinterpret_cast<uint16_t *>(out + 5 * W::B + o) = cc;
+    } else {
+      const float hp = to_tf32(vp), hq = to_tf32(vq);
+      *reinterpret_cast<float *>(out + o) = hp;
+      *reinterpret_cast<float *>(out + W::B + o) = to_tf32(vp - hp);
+      *reinterpret_cast<float *>(out + 2 * W::B + o) = hq;
+      *reinterpret_cast<float *>(out + 3 * W::B + o) = to_tf32(vq - hq);
+    }
   }
 }
 
-// Shared memory: one stage (A hi, A lo, B hi, B lo), and at least the two
+// Shared memory: one stage (A planes, B planes), and at least the two FP32
 // epilogue row buffers that reuse it, plus room to align the start to 1024
 // bytes.
-template <int KW>
+template <int KW, bool BF>
 __host__ __device__ constexpr size_t tc_smem() {
-  return sizeof(float) * (Tw<KW>::stage > 2 * Tw<KW>::buf ? Tw<KW>::stage : 2 * Tw<KW>::buf) +
-         1024;
+  using W = Tw<KW, BF>;
+  return (size_t)(W::stage > 8 * W::buf ? W::stage : 8 * W::buf) + 1024;
 }
 
 // An A tile in registers.  A warp's load instruction covers 8 rows x 4
@@ -145,50 +200,77 @@ __device__ __forceinline__ void tc_load_A(const float *A, int lda, int rows, ATi
                       : make_float4(0.f, 0.f, 0.f, 0.f);
   }
 }
-// hi / lo split into the stage's A area, core order.
-template <int KW>
-__device__ __forceinline__ void tc_store_A(const ATile<KW> &t, float *st) {
-  float *sAh = st, *sAl = st + Tw<KW>::A;
+// The split of an A tile into the stage's A planes, core order (TF32: hi,
+// lo; BF16: the three parts).  st: the stage's first byte.
+template <int KW, bool BF>
+__device__ __forceinline__ void tc_store_A(const ATile<KW> &t, unsigned char *st) {
+  using W = Tw<KW, BF>;
 #pragma unroll
   for (int q = 0; q < KW / 4; q++) {
     int r, col;
     a_pos<KW>(q, r, col);
     const float4 x = t.x[q];
-    const float4 h = make_float4(to_tf32(x.x), to_tf32(x.y), to_tf32(x.z), to_tf32(x.w));
-    const float4 l = make_float4(to_tf32(x.x - h.x), to_tf32(x.y - h.y), to_tf32(x.z - h.z),
-                                 to_tf32(x.w - h.w));
-    const int o = core_off<KW>(r, col);
-    *reinterpret_cast<float4 *>(sAh + o) = h;
-    *reinterpret_cast<float4 *>(sAl + o) = l;
+    const int o = core_off<KW, BF>(r, col);
+    if constexpr (BF) {
+      uint16_t a[4], b[4], c[4];
+      split3(x.x, a[0], b[0], c[0]);
+      split3(x.y, a[1], b[1], c[1]);
+      split3(x.z, a[2], b[2], c[2]);
+      split3(x.w, a[3], b[3], c[3]);
+      auto pack = [](const uint16_t (&h)[4]) {
+        return make_uint2((uint32_t)h[0] | ((uint32_t)h[1] << 16),
+                          (uint32_t)h[2] | ((uint32_t)h[3] << 16));
+      };
+      *reinterpret_cast<uint2 *>(st + o) = pack(a);
+      *reinterpret_cast<uint2 *>(st + W::A + o) = pack(b);
+      *reinterpret_cast<uint2 *>(st + 2 * W::A + o) = pack(c);
+    } else {
+      const float4 h = make_float4(to_tf32(x.x), to_tf32(x.y), to_tf32(x.z), to_tf32(x.w));
+      const float4 l = make_float4(to_tf32(x.x - h.x), to_tf32(x.y - h.y), to_tf32(x.z - h.z),
+                                   to_tf32(x.w - h.w));
+      *reinterpret_cast<float4 *>(st + o) = h;
+      *reinterpret_cast<float4 *>(st + W::A + o) = l;
+    }
   }
 }
-// B: hi | lo (laid out by k_tc_prep) into the stage's B area by cp.async, as
-// one commit group.
-template <int KW>
-__device__ __forceinline__ void tc_async_B(const float *Bq, float *st) {
-  const uint32_t dst = su32(st + 2 * Tw<KW>::A);
+// The B planes (laid out by k_tc_prep) into the stage's B area by cp.async,
+// as one commit group.
+template <int KW, bool BF>
+__device__ __forceinline__ void tc_async_B(const float *Bq, unsigned char *st) {
+  using W = Tw<KW, BF>;
+  const uint32_t dst = su32(st + W::NP * W::A);
   const size_t src = __cvta_generic_to_global(Bq);
 #pragma unroll 4
-  for (int i = threadIdx.x; i < 2 * Tw<KW>::B / 4; i += kTcThr)
+  for (int i = threadIdx.x; i < W::NP * W::B / 16; i += kTcThr)
     asm volatile("cp.async.cg.shared.global [%0], [%1], 16;" ::"r"(dst + 16 * i),
                  "l"(src + 16 * (size_t)i)
                  : "memory");
   asm volatile("cp.async.commit_group;" ::: "memory");
 }
-// Issue (thread 0) D[col..col+KW-1] = A B^T from stage st with the three
-// split products, then signal mbar when they have completed.  Staged operands
-// must be fenced and the CTA synchronised before the call.
-template <int KW>
-__device__ __forceinline__ void tc_mma(uint32_t dtmem, const float *st, uint64_t *mbar) {
+// Issue (thread 0) D[col..col+KW-1] = A B^T from stage st with the split
+// products (TF32: 3, BF16: 6 per K step), then signal mbar when they have
+// completed.  Staged operands must be fenced and the CTA synchronised before
+// the call.
+template <int KW, bool BF>
+__device__ __forceinline__ void tc_mma(uint32_t dtmem, const unsigned char *st, uint64_t *mbar) {
+  using W = Tw<KW, BF>;
   if (threadIdx.x != 0) return;
   asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
-  const uint32_t ah = su32(st), al = ah + Tw<KW>::A * 4, bh = ah + 2 * Tw<KW>::A * 4,
-                 bl = bh + Tw<KW>::B * 4;
-  for (int ks = 0; ks < KW / 8; ks++) {  // 8 TF32 of K per instruction = 256 bytes
+  const uint32_t a0 = su32(st), b0 = a0 + W::NP * W::A;
+  for (int ks = 0; ks < KW / W::kstep; ks++) {  // one K step = 2 core matrices = 256 bytes
     const uint32_t o = ks * 256;
-    mma_tf32<KW>(dtmem, smem_desc<KW>(ah + o), smem_desc<KW>(bh + o), ks > 0);
-    mma_tf32<KW>(dtmem, smem_desc<KW>(ah + o), smem_desc<KW>(bl + o), 1);
-    mma_tf32<KW>(dtmem, smem_desc<KW>(al + o), smem_desc<KW>(bh + o), 1);
+    auto mm = [&](int i, int j, uint32_t acc) {
+      mma_issue<KW, BF>(dtmem, smem_desc<KW, BF>(a0 + i * W::A + o),
+                        smem_desc<KW, BF>(b0 + j * W::B + o), acc);
+    };
+    mm(0, 0, ks > 0);
+    mm(0, 1, 1);
+    mm(1, 0, 1);
+    if constexpr (BF) {
+      mm(0, 2, 1);
+      mm(1, 1, 1);
+      mm(2, 0, 1);
+    }
   }
   asm volatile(
       "tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(
@@ -320,7 +402,7 @@ __device__ __forceinline__ void tc_ld(uint32_t taddr, int col, float *out) {
 // Thread r's row of KW values into buffer row r (float4 stores).
 template <int KW>
 __device__ __forceinline__ void row_put(float *buf, const float (&v)[KW]) {
-  float *dst = buf + threadIdx.x * Tw<KW>::pad;
+  float *dst = buf + threadIdx.x * Tw<KW, false>::pad;
 #pragma unroll
   for (int q = 0; q < KW / 4; q++)
     *reinterpret_cast<float4 *>(dst + 4 * q) =
@@ -331,12 +413,12 @@ __device__ __forceinline__ void row_put(float *buf, const float (&v)[KW]) {
 template <int KW>
 __device__ __forceinline__ void rows_store(const float *buf, float *dst, int ld, int rows,
                                            const int *e) {
-  constexpr int C4 = Tw<KW>::c4;
+  constexpr int C4 = Tw<KW, false>::c4;
 #pragma unroll 4
   for (int q = 0; q < C4; q++) {
     const int idx = threadIdx.x + kTcThr * q, row = idx / C4, c4 = idx % C4;
     if (row < rows) {
-      float4 v = *reinterpret_cast<const float4 *>(buf + row * Tw<KW>::pad + 4 * c4);
+      float4 v = *reinterpret_cast<const float4 *>(buf + row * Tw<KW, false>::pad + 4 * c4);
       if (e) {
         const Pow2 f = pow2_neg(e[row]);
         v = make_float4(sc(v.x, f), sc(v.y, f), sc(v.z, f), sc(v.w, f));
@@ -349,13 +431,13 @@ __device__ __forceinline__ void rows_store(const float *buf, float *dst, int ld,
 // `rows` become zero.
 template <int KW>
 __device__ __forceinline__ void rows_load(const float *src, int ld, int rows, float *buf) {
-  constexpr int C4 = Tw<KW>::c4;
+  constexpr int C4 = Tw<KW, false>::c4;
 #pragma unroll 4
   for (int q = 0; q < C4; q++) {
     const int idx = threadIdx.x + kTcThr * q, row = idx / C4, c4 = idx % C4;
     const float4 v = row < rows ? *reinterpret_cast<const float4 *>(src + (size_t)row * ld + 4 * c4)
                                 : make_float4(0.f, 0.f, 0.f, 0.f);
-    *reinterpret_cast<float4 *>(buf + row * Tw<KW>::pad + 4 * c4) = v;
+    *reinterpret_cast<float4 *>(buf + row * Tw<KW, false>::pad + 4 * c4) = v;
   }
 }
 // KW floats of a table row (a tip's S: the row of its code).
@@ -382,15 +464,15 @@ __device__ __forceinline__ void row_get(const float *src, float (&v)[KW]) {
 // that MMA has then been drained (a second bounded wait) and no cp.async is
 // pending, so the caller may release tensor memory.  The result is the same
 // in every thread of the CTA.
-template <int KW, class Item>
-__device__ bool tc_pipeline(int n, int lda, int rows, Item item, float *st, uint32_t taddr,
+template <int KW, bool BF, class Item>
+__device__ bool tc_pipeline(int n, int lda, int rows, Item item, unsigned char *st, uint32_t taddr,
                             uint64_t *mbar, uint32_t *ph, int *s_ok) {
   if (n <= 0) return true;
   ATile<KW> ra;
   const float *A, *B;
   uint32_t col;
   item(0, A, B, col);
-  tc_async_B<KW>(B, st);
+  tc_async_B<KW, BF>(B, st);
   tc_load_A<KW>(A, lda, rows, ra);
   for (int j = 0; j < n; j++) {
     if (j >= 1) {  // the stage is free once MMA j-1 has completed
@@ -399,9 +481,9 @@ __device__ bool tc_pipeline(int n, int lda, int rows, Item item, float *st, uint
         tc_drain(&mbar[b], ph[b]);
         return false;
       }
-      tc_async_B<KW>(B, st);
+      tc_async_B<KW, BF>(B, st);
     }
-    tc_store_A<KW>(ra, st);
+    tc_store_A<KW, BF>(ra, st);
     const uint32_t colj = col;
     if (j + 1 < n) {
       item(j + 1, A, B, col);
@@ -409,7 +491,7 @@ __device__ bool tc_pipeline(int n, int lda, int rows, Item item, float *st, uint
     }
     asm volatile("cp.async.wait_group 0;" ::: "memory");
     tc_sync_staged();
-    tc_mma<KW>(taddr + colj, st, &mbar[j & 1]);
+    tc_mma<KW, BF>(taddr + colj, st, &mbar[j & 1]);
   }
   const int b = (n - 1) & 1;
   if (!tc_wait(&mbar[b], ph[b], s_ok)) {
@@ -449,7 +531,7 @@ __device__ __forceinline__ float *tc_smem(float *tsm) {
 // Pre-order: U_v = P_v^T X_v for the non-tip children of one level's nodes.
 // grid = (tiles of 128 patterns, level nodes * 2 children, categories); one
 // tile product per CTA (one shared-memory stage).
-template <int KW>
+template <int KW, bool BF>
 __global__ void __launch_bounds__(kTcThr) k_tc_pre_u(Dims d, const int *__restrict__ lvl_nodes,
                                                     int lvl_off, const int *__restrict__ child,
                                                     const float *__restrict__ xbuf,
@@ -471,10 +553,12 @@ __global__ void __launch_bounds__(kTcThr) k_tc_pre_u(Dims d, const int *__restri
   const int rows = min(kRows, d.P - p0);
   auto item = [&](int, const float *&A, const float *&B, uint32_t &col) {
     A = xbuf + ((((size_t)bi * 2 + x) * d.C + c) * d.P + p0) * d.Kp;
-    B = tcB + ((size_t)v * d.C + c) * 4 * Tw<KW>::B + 2 * Tw<KW>::B;  // pre hi | lo
+    B = tcB + ((size_t)v * d.C + c) * Tw<KW, BF>::vc_floats +
+        Tw<KW, BF>::NP * Tw<KW, BF>::B / 4;  // the pre planes
     col = 0;
   };
-  if (!tc_pipeline<KW>(1, d.Kp, rows, item, sm, taddr, mbar, ph, &s_ok)) {
+  if (!tc_pipeline<KW, BF>(1, d.Kp, rows, item, reinterpret_cast<unsigned char *>(sm), taddr,
+                           mbar, ph, &s_ok)) {
     if (threadIdx.x == 0) atomicOr(status, ST_TIMEOUT);
     tc_end(taddr, ncols);
     return;
@@ -490,7 +574,7 @@ __global__ void __launch_bounds__(kTcThr) k_tc_pre_u(Dims d, const int *__restri
 
 // S of both children of node u for category c into TMEM columns sd * KW;
 // tips are skipped (their S is a table row).
-template <int KW>
+template <int KW, bool BF>
 __device__ __forceinline__ bool tc_children_S(const Dims &d, const int (&kid)[2], int c,
                                               const float *part, const float *tcB, int p0,
                                               int rows, float *sm, uint32_t taddr,
@@ -501,10 +585,11 @@ __device__ __forceinline__ bool tc_children_S(const Dims &d, const int (&kid)[2]
     const int sd = n == 2 ? j : (st0 ? 0 : 1);
     const int v = kid[sd];
     A = part + ((((size_t)(v - d.N) * d.C + c) * d.P) + p0) * d.Kp;
-    B = tcB + ((size_t)v * d.C + c) * 4 * Tw<KW>::B;  // post hi | lo
+    B = tcB + ((size_t)v * d.C + c) * Tw<KW, BF>::vc_floats;  // the post planes
     col = (uint32_t)(sd * KW);
   };
-  return tc_pipeline<KW>(n, d.Kp, rows, item, sm, taddr, mbar, ph, s_ok);
+  return tc_pipeline<KW, BF>(n, d.Kp, rows, item, reinterpret_cast<unsigned char *>(sm), taddr,
+                             mbar, ph, s_ok);
 }
 
 // S of child sd (TMEM block sd, or the table row of a tip's code).
@@ -538,7 +623,7 @@ __device__ __forceinline__ float cluster_ld(const float *p, uint32_t rank) {
 // cluster: each publishes its rows' maxima over i in shared memory and reads
 // the others' through distributed shared memory.  grid = (tiles of 128
 // patterns, nodes, categories), cluster (1, 1, C).
-template <int KW>
+template <int KW, bool BF>
 __global__ void __launch_bounds__(kTcThr) k_tc_post(Dims d, const int *__restrict__ lvl_nodes,
                                                    int lvl_off, const int *__restrict__ child,
                                                    const float *__restrict__ PT,
@@ -559,7 +644,7 @@ __global__ void __launch_bounds__(kTcThr) k_tc_post(Dims d, const int *__restric
   const uint32_t taddr = tc_begin(&s_tmem, mbar, 2 * KW);
   uint32_t ph[2] = {0, 0};
   const int p0 = blockIdx.x * kRows, rows = min(kRows, d.P - p0);
-  const bool ok = tc_children_S<KW>(d, kid, c, part, tcB, p0, rows, sm, taddr, mbar, ph, &s_ok);
+  const bool ok = tc_children_S<KW, BF>(d, kid, c, part, tcB, p0, rows, sm, taddr, mbar, ph, &s_ok);
   if (!ok && threadIdx.x == 0) atomicOr(status, ST_TIMEOUT);
   const int r = threadIdx.x, p = p0 + r;
   const bool live = r < rows;
@@ -603,7 +688,7 @@ __global__ void __launch_bounds__(kTcThr) k_tc_post(Dims d, const int *__restric
 //   X_0 = U_u o S_1 2^-e_u,  X_1 = U_u o S_0 2^-e_u,
 // with S of stored children by tile products, into the adjoint scratch.
 // grid = (tiles of 128 patterns, nodes, categories).
-template <int KW>
+template <int KW, bool BF>
 __global__ void __launch_bounds__(kTcThr) k_tc_pre_x(
     Dims d, const int *__restrict__ lvl_nodes, int lvl_off, const int *__restrict__ child, int root,
     const float *__restrict__ PT, const uint8_t *__restrict__ tips, const float *__restrict__ tcB,
@@ -622,7 +707,7 @@ __global__ void __launch_bounds__(kTcThr) k_tc_pre_x(
   const uint32_t taddr = tc_begin(&s_tmem, mbar, 2 * KW);
   uint32_t ph[2] = {0, 0};
   const int p0 = blockIdx.x * kRows, rows = min(kRows, d.P - p0);
-  if (!tc_children_S<KW>(d, kid, c, part, tcB, p0, rows, sm, taddr, mbar, ph, &s_ok)) {
+  if (!tc_children_S<KW, BF>(d, kid, c, part, tcB, p0, rows, sm, taddr, mbar, ph, &s_ok)) {
     if (threadIdx.x == 0) atomicOr(status, ST_TIMEOUT);
     tc_end(taddr, 2 * KW);
     return;
@@ -636,7 +721,7 @@ __global__ void __launch_bounds__(kTcThr) k_tc_pre_x(
   const Pow2 f = pow2_neg(scale[(size_t)slot * d.Pp + pc]);
   // X_0 overwrites U_u in place: each thread reads its whole U row before it
   // writes that row of X_0
-  float *ubuf = sm, *xb0 = sm, *xb1 = sm + Tw<KW>::buf;
+  float *ubuf = sm, *xb0 = sm, *xb1 = sm + Tw<KW, false>::buf;
   if (u != root)  // U_u rows, contiguous loads
     rows_load<KW>(pre + ((((size_t)slot * d.C + c) * d.P) + p0) * d.Kp, d.Kp, rows, ubuf);
   __syncthreads();
@@ -644,7 +729,7 @@ __global__ void __launch_bounds__(kTcThr) k_tc_pre_x(
   float s0[KW], s1[KW];
   child_S<KW>(d, PT, kid[0], c, code[0], taddr, 0, s0);
   child_S<KW>(d, PT, kid[1], c, code[1], taddr, 1, s1);
-  const float *urow = ubuf + r * Tw<KW>::pad;
+  const float *urow = ubuf + r * Tw<KW, false>::pad;
 #pragma unroll
   for (int j = 0; j < KW; j++) {
     const float uu = (u == root) ? (j < d.K ? (float)(rootw * pi[j]) : 0.f) : urow[j];
@@ -668,18 +753,18 @@ __global__ void __launch_bounds__(kTcThr) k_tc_pre_x(
 // padded row length.
 bool tc_path(const epoch_ctx *c) {
   const int kp = c->d.Kp;
-  return c->precision == EPOCH_FP32_TC && !fast_k4(c) && (kp == 64 || kp == 32 || kp == 16) &&
+  return is_tc_precision(c->precision) && !fast_k4(c) && (kp == 64 || kp == 32 || kp == 16) &&
          c->d.C <= 4;
 }
 
 namespace {
 
-template <int KW>
+template <int KW, bool BF>
 cudaError_t tc_post(epoch_ctx *c, int level) {
   const Dims &d = c->d;
   const int w = c->h_level_off[level + 1] - c->h_level_off[level];
-  const size_t smem = tc_smem<KW>();
-  cudaFuncSetAttribute(k_tc_post<KW>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+  const size_t smem = tc_smem<KW, BF>();
+  cudaFuncSetAttribute(k_tc_post<KW, BF>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
   cudaLaunchConfig_t cfg = {};
   cfg.gridDim = dim3(ceil_div(d.P, kRows), w, d.C);
   cfg.blockDim = dim3(kTcThr);
@@ -692,75 +777,81 @@ cudaError_t tc_post(epoch_ctx *c, int level) {
   at[0].val.clusterDim.z = d.C;
   cfg.attrs = at;
   cfg.numAttrs = 1;
-  return cudaLaunchKernelEx(&cfg, k_tc_post<KW>, d, (const int *)c->d_level_nodes,
+  return cudaLaunchKernelEx(&cfg, k_tc_post<KW, BF>, d, (const int *)c->d_level_nodes,
                             c->h_level_off[level], (const int *)c->d_child,
                             (const float *)c->d_PT32, (const uint8_t *)c->d_tips,
                             (const float *)c->d_tcB, (float *)c->d_part, c->d_scale, c->d_status);
 }
 
-template <int KW>
+template <int KW, bool BF>
 void tc_pre_x(epoch_ctx *c, int level, int root) {
   const Dims &d = c->d;
   const int w = c->h_level_off[level + 1] - c->h_level_off[level];
-  const size_t smem = tc_smem<KW>();
-  cudaFuncSetAttribute(k_tc_pre_x<KW>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
-  k_tc_pre_x<KW><<<dim3(ceil_div(d.P, kRows), w, d.C), kTcThr, smem, c->stream>>>(
+  const size_t smem = tc_smem<KW, BF>();
+  cudaFuncSetAttribute(k_tc_pre_x<KW, BF>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+  k_tc_pre_x<KW, BF><<<dim3(ceil_div(d.P, kRows), w, d.C), kTcThr, smem, c->stream>>>(
       d, c->d_level_nodes, c->h_level_off[level], c->d_child, root, c->d_PT32, c->d_tips,
       c->d_tcB, (const float *)c->d_part, (const float *)c->d_pre, c->d_scale, c->d_pi,
       c->d_catw, c->d_site_inv, (float *)c->d_xbuf, c->d_status);
 }
 
-template <int KW>
+template <int KW, bool BF>
 void tc_pre_u(epoch_ctx *c, int level) {
   const Dims &d = c->d;
   const int w = c->h_level_off[level + 1] - c->h_level_off[level];
-  const size_t smem = tc_smem<KW>();
-  cudaFuncSetAttribute(k_tc_pre_u<KW>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
-  k_tc_pre_u<KW><<<dim3(ceil_div(d.P, kRows), 2 * w, d.C), kTcThr, smem, c->stream>>>(
+  const size_t smem = tc_smem<KW, BF>();
+  cudaFuncSetAttribute(k_tc_pre_u<KW, BF>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+  k_tc_pre_u<KW, BF><<<dim3(ceil_div(d.P, kRows), 2 * w, d.C), kTcThr, smem, c->stream>>>(
       d, c->d_level_nodes, c->h_level_off[level], c->d_child, (const float *)c->d_xbuf, c->d_tcB,
       (float *)c->d_pre, c->d_status);
+}
+
+// Dispatch on the tile width (Kp) and the operand format (precision).
+template <class F>
+auto by_shape(const epoch_ctx *c, F f) {
+  const bool bf = c->precision == EPOCH_FP32_TC_BF16;
+  const int kp = c->d.Kp;
+  if (kp == 64) return bf ? f(std::integral_constant<int, 64>(), std::true_type())
+                          : f(std::integral_constant<int, 64>(), std::false_type());
+  if (kp == 32) return bf ? f(std::integral_constant<int, 32>(), std::true_type())
+                          : f(std::integral_constant<int, 32>(), std::false_type());
+  return bf ? f(std::integral_constant<int, 16>(), std::true_type())
+            : f(std::integral_constant<int, 16>(), std::false_type());
 }
 
 }  // namespace
 
 cudaError_t launch_tc_post(epoch_ctx *c, int level) {
-  const int kp = c->d.Kp;
-  cudaError_t e = kp == 64 ? tc_post<64>(c, level)
-                           : (kp == 32 ? tc_post<32>(c, level) : tc_post<16>(c, level));
+  cudaError_t e = by_shape(c, [&](auto kw, auto bf) { return tc_post<kw.value, bf.value>(c, level); });
   c->launches++;
   return e != cudaSuccess ? e : cudaGetLastError();
 }
 
 cudaError_t launch_tc_pre_x(epoch_ctx *c, int level, int root) {
-  if (c->d.Kp == 64)
-    tc_pre_x<64>(c, level, root);
-  else if (c->d.Kp == 32)
-    tc_pre_x<32>(c, level, root);
-  else
-    tc_pre_x<16>(c, level, root);
+  by_shape(c, [&](auto kw, auto bf) {
+    tc_pre_x<kw.value, bf.value>(c, level, root);
+    return 0;
+  });
   c->launches++;
   return cudaGetLastError();
 }
 
 cudaError_t launch_tc_prep(epoch_ctx *c) {
   const Dims &d = c->d;
-  if (d.Kp == 64)
-    k_tc_prep<64><<<d.nn * d.C, 256, 0, c->stream>>>(d, c->d_P64, c->d_parent, c->d_tcB);
-  else if (d.Kp == 32)
-    k_tc_prep<32><<<d.nn * d.C, 256, 0, c->stream>>>(d, c->d_P64, c->d_parent, c->d_tcB);
-  else
-    k_tc_prep<16><<<d.nn * d.C, 256, 0, c->stream>>>(d, c->d_P64, c->d_parent, c->d_tcB);
+  by_shape(c, [&](auto kw, auto bf) {
+    k_tc_prep<kw.value, bf.value><<<d.nn * d.C, 256, 0, c->stream>>>(d, c->d_P64, c->d_parent,
+                                                                      c->d_tcB);
+    return 0;
+  });
   c->launches++;
   return cudaGetLastError();
 }
 
 cudaError_t launch_tc_pre_u(epoch_ctx *c, int level) {
-  if (c->d.Kp == 64)
-    tc_pre_u<64>(c, level);
-  else if (c->d.Kp == 32)
-    tc_pre_u<32>(c, level);
-  else
-    tc_pre_u<16>(c, level);
+  by_shape(c, [&](auto kw, auto bf) {
+    tc_pre_u<kw.value, bf.value>(c, level);
+    return 0;
+  });
   c->launches++;
   return cudaGetLastError();
 }

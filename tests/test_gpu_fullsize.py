@@ -10,7 +10,8 @@ import pytest
 import oracle
 import synth
 from paper_1309_3075_b300 import binding
-from paper_1309_3075_b300.binding import EPOCH_FP32, EPOCH_FP32_TC, EPOCH_FP64, EpochLikelihood
+from paper_1309_3075_b300.binding import (EPOCH_FP32, EPOCH_FP32_TC, EPOCH_FP32_TC_BF16, EPOCH_FP64,
+                                          EpochLikelihood)
 from tolerances import grad_close
 
 pytestmark = pytest.mark.gpu
@@ -53,7 +54,7 @@ def test_gtr_full_size_lnl_and_gradient(gtr_full, prec, tol):
 
 
 @pytest.mark.parametrize("prec,tol", [(EPOCH_FP64, 1e-10), (EPOCH_FP32, 1e-5),
-                                      (EPOCH_FP32_TC, 1e-5)])
+                                      (EPOCH_FP32_TC, 1e-5), (EPOCH_FP32_TC_BF16, 1e-5)])
 def test_gy94_full_size_sampled_sites(gy94_full, prec, tol):
     w = gy94_full
     lik = EpochLikelihood(w, precision=prec)
@@ -83,7 +84,7 @@ def gy94_slice(gy94_full):
     return w, oracle.gradient(w), oracle.log_likelihood(w)[1]
 
 
-@pytest.mark.parametrize("prec", [EPOCH_FP64, EPOCH_FP32, EPOCH_FP32_TC])
+@pytest.mark.parametrize("prec", [EPOCH_FP64, EPOCH_FP32, EPOCH_FP32_TC, EPOCH_FP32_TC_BF16])
 def test_gy94_gradient_against_oracle_at_config_shape(gy94_slice, prec):
     """d lnL / d (node heights, boundaries, kappa, omega_k) of the codon
     epoch model (Eq. convolution differentiated), GPU against the FP64 oracle

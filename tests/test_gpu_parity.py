@@ -14,8 +14,9 @@ import pytest
 import oracle
 import synth
 from paper_1309_3075_b300 import binding
-from paper_1309_3075_b300.binding import (EPOCH_FP32, EPOCH_FP32_AUTO, EPOCH_FP32_TC, EPOCH_FP64,
-                                          EpochError, EpochLikelihood)
+from paper_1309_3075_b300.binding import (EPOCH_FP32, EPOCH_FP32_AUTO, EPOCH_FP32_TC,
+                                          EPOCH_FP32_TC_BF16, EPOCH_FP64, EpochError,
+                                          EpochLikelihood)
 from tolerances import GRAD_TOL, LNL_TOL, grad_close
 
 pytestmark = pytest.mark.gpu
@@ -122,7 +123,7 @@ def test_other_state_counts(prec, K):
     check_grad(w, prec)
 
 
-@pytest.mark.parametrize("prec", [EPOCH_FP32_TC])
+@pytest.mark.parametrize("prec", [EPOCH_FP32_TC, EPOCH_FP32_TC_BF16])
 @pytest.mark.parametrize("K,P", [(50, 300), (64, 129), (20, 257), (32, 130), (17, 140),
                                  (9, 200), (16, 131)])
 def test_tensor_core_large_state_spaces(prec, K, P):
@@ -349,17 +350,18 @@ def test_auto_path_is_the_faster_and_matches_the_oracle(K, P):
                                      missing_frac=0.05)
     lik = EpochLikelihood(w, precision=EPOCH_FP32_AUTO)
     try:
-        prec, ms_simt, ms_tc = binding.epoch_path_info(lik.ctx)
+        info = binding.epoch_path_info(lik.ctx)
     finally:
         lik.close()
+    prec, times = info[0], dict(zip((EPOCH_FP32, EPOCH_FP32_TC, EPOCH_FP32_TC_BF16), info[1:]))
     if K <= 8:
-        assert prec == EPOCH_FP32 and ms_simt < 0 and ms_tc < 0
+        assert prec == EPOCH_FP32 and all(t < 0 for t in times.values())
     else:
-        assert ms_simt > 0 and ms_tc > 0, (ms_simt, ms_tc)
-        assert prec == (EPOCH_FP32_TC if ms_tc < ms_simt else EPOCH_FP32), (prec, ms_simt, ms_tc)
+        assert all(t > 0 for t in times.values()), times
+        assert prec == min(times, key=times.get), (prec, times)
     lik2 = EpochLikelihood(w, precision=EPOCH_FP32_AUTO)
     try:
-        assert binding.epoch_path_info(lik2.ctx) == (prec, ms_simt, ms_tc)
+        assert binding.epoch_path_info(lik2.ctx) == info
     finally:
         lik2.close()
     check_lnl(w, EPOCH_FP32_AUTO)

@@ -10,15 +10,19 @@ against the floor.
 """
 import numpy as np
 
-from paper_1309_3075_b300.binding import EPOCH_FP32, EPOCH_FP32_AUTO, EPOCH_FP32_TC, EPOCH_FP64
+from paper_1309_3075_b300.binding import (EPOCH_FP32, EPOCH_FP32_AUTO, EPOCH_FP32_TC,
+                                          EPOCH_FP32_TC_BF16, EPOCH_FP64)
 
-LNL_TOL = {EPOCH_FP64: 1e-10, EPOCH_FP32: 1e-5, EPOCH_FP32_TC: 1e-5, EPOCH_FP32_AUTO: 1e-5}
-GRAD_TOL = {EPOCH_FP64: 1e-9, EPOCH_FP32: 1e-4, EPOCH_FP32_TC: 1e-4, EPOCH_FP32_AUTO: 1e-4}
+LNL_TOL = {EPOCH_FP64: 1e-10, EPOCH_FP32: 1e-5, EPOCH_FP32_TC: 1e-5, EPOCH_FP32_AUTO: 1e-5,
+           EPOCH_FP32_TC_BF16: 1e-5}
+GRAD_TOL = {EPOCH_FP64: 1e-9, EPOCH_FP32: 1e-4, EPOCH_FP32_TC: 1e-4, EPOCH_FP32_AUTO: 1e-4,
+            EPOCH_FP32_TC_BF16: 1e-4}
 # Measured worst per-component errors (GPU against the oracle on the parity
 # workloads, components at least this fraction of the largest): FP32 and
 # TF32x3 2.4e-6 .. 4.0e-5 at 0.3, up to 7.7e-5 at 0.1 and 5.9e-4 at 0.01;
 # FP64 2.4e-10 at 0.1, 7.1e-10 at 0.01 and 2.6e-9 at 0.001.
-GRAD_FLOOR = {EPOCH_FP64: 1e-1, EPOCH_FP32: 3e-1, EPOCH_FP32_TC: 3e-1, EPOCH_FP32_AUTO: 3e-1}
+GRAD_FLOOR = {EPOCH_FP64: 1e-1, EPOCH_FP32: 3e-1, EPOCH_FP32_TC: 3e-1, EPOCH_FP32_AUTO: 3e-1,
+              EPOCH_FP32_TC_BF16: 3e-1}
 # absolute floor, for derivatives that vanish exactly (a parameter whose
 # effect the normalisation of Q removes)
 GRAD_ABS = 1e-6
