@@ -342,15 +342,17 @@ def run_ours(args, w, cfg, rank, world):
 
     from paper_1309_3075_b300 import binding
     from paper_1309_3075_b300.binding import (EPOCH_FP32, EPOCH_FP32_AUTO, EPOCH_FP32_TC,
-                                              EpochLikelihood)
+                                              EPOCH_FP32_TC_BF16, EpochLikelihood)
 
     dev = rank % max(torch.cuda.device_count(), 1)
     torch.cuda.set_device(dev)
     stream = torch.cuda.Stream()
     # K = 4 has its own FP32 path; other K take whichever FP32 path (SIMT or
-    # tensor-core tile products) the library's probe measures faster
-    lik = EpochLikelihood(w, precision=EPOCH_FP32 if w.K == 4 else EPOCH_FP32_AUTO,
-                          cuda_stream=stream.cuda_stream)
+    # tensor-core tile products) the library's probe measures faster, unless
+    # --precision names one
+    chosen = {"simt": EPOCH_FP32, "tf32x3": EPOCH_FP32_TC, "bf16x3": EPOCH_FP32_TC_BF16}
+    want = chosen.get(args.precision, EPOCH_FP32 if w.K == 4 else EPOCH_FP32_AUTO)
+    lik = EpochLikelihood(w, precision=want, cuda_stream=stream.cuda_stream)
     prec, probe_simt, probe_tc, probe_bf = binding.epoch_path_info(lik.ctx)
     nn = 2 * w.n_taxa - 1
     clocks = ClockSampler(dev).start()
@@ -564,7 +566,8 @@ def run_codon(args, stream, clocks):
     sites, 4 categories): lnL + gradient on the tensor-core path (TF32x3
     tile products) against the plain FP64 GPU path."""
     from paper_1309_3075_b300 import binding
-    from paper_1309_3075_b300.binding import EPOCH_FP32_AUTO, EPOCH_FP32_TC, EpochLikelihood
+    from paper_1309_3075_b300.binding import (EPOCH_FP32, EPOCH_FP32_AUTO, EPOCH_FP32_TC,
+                                              EPOCH_FP32_TC_BF16, EpochLikelihood)
 
     w, cfg = make_workload("gy94")
     nn = 2 * w.n_taxa - 1
@@ -581,6 +584,26 @@ def run_codon(args, stream, clocks):
         lik.close()
     fp64_ms, lnl64, g64 = time_fp64(w, stream, args, clocks)
     flops = codon_flops(w)
+    # every FP32 arm on the same workload: SIMT contractions, TF32 x 3 and
+    # BF16 x 3 tile products (lnL + gradient, graph replays)
+    arms = {}
+    for name, p in (("EPOCH_FP32", EPOCH_FP32), ("EPOCH_FP32_TC", EPOCH_FP32_TC),
+                    ("EPOCH_FP32_TC_BF16", EPOCH_FP32_TC_BF16)):
+        la = EpochLikelihood(w, precision=p, cuda_stream=stream.cuda_stream)
+        try:
+            for _ in range(2):
+                binding.epoch_evaluate_async(la.ctx, True)
+            ams, span = timed_replays(stream, lambda: binding.epoch_evaluate_async(la.ctx, True),
+                                      max(3, min(args.steps, 10)))
+            clocks.window("codon", *span)
+            lnl_a, g_a = binding.epoch_read_results(la.ctx, nn, w.n_epochs, la.n_params, True)
+        finally:
+            la.close()
+        arms[name] = {"ms_per_step": ams, "tile_product_tflops": flops / (ams * 1e-3) / 1e12
+                      if p != EPOCH_FP32 else None,
+                      "lnL_rel_err_vs_fp64": abs(lnl_a - lnl64) / abs(lnl64),
+                      "grad_rel_err_vs_fp64": float(np.abs(g_a["params"] - g64["params"]).max()
+                                                    / np.abs(g64["params"]).max())}
     return {"workload": cfg["workload"], "patterns": cfg["patterns"], "evals_per_s": 1e3 / ms,
             "ms_per_step": ms,
             "dtype": DTYPES.get(prec, "f32"),
@@ -592,6 +615,7 @@ def run_codon(args, stream, clocks):
             "grad_rel_err_vs_fp64": float(np.abs(g["params"] - g64["params"]).max()
                                           / np.abs(g64["params"]).max()),
             "tile_product_tflops": flops / (ms * 1e-3) / 1e12,
+            "arms": arms,
             "tensor_pipe_active_frac": codon_tensor_frac(),
             "tensor_profile": CODON_TENSOR["profile"]}
 
@@ -777,6 +801,8 @@ def main():
                     help="skip the batched 256-tree measurement")
     ap.add_argument("--no-codon", action="store_true",
                     help="skip the codon (GY94) measurement beside the default workload")
+    ap.add_argument("--precision", default="auto", choices=["auto", "simt", "tf32x3", "bf16x3"],
+                    help="FP32 arm of the timed workload (auto: the library's probe)")
     args = ap.parse_args()
     world = int(os.environ.get("WORLD_SIZE", "1"))
     rank = int(os.environ.get("RANK", "0"))

@@ -422,7 +422,8 @@ void epoch_destroy(epoch_ctx *c) {
                   c->d_site_inv,   c->d_lnl_part, c->d_lnl,     c->d_Gpart,      c->d_G,
                   c->d_gseg,       c->d_grad,    c->d_status,   c->d_ctl,        c->d_site_log,
                   c->d_level_off,  c->d_pairS,   c->d_pairL,    c->d_k4_walk,    c->d_k4_nt,
-                  c->d_k4_esum,    c->d_tcB,     c->d_jumps,    c->d_jump_out,   c->d_anc};
+                  c->d_k4_esum,    c->d_tcB,     c->d_jumps,    c->d_jump_out,   c->d_anc,
+                  c->d_eig};
   for (void *p : bufs) dfree(p);
   if (c->h_grad_pinned) cudaFreeHost(c->h_grad_pinned);
   if (c->h_lnl_pinned) cudaFreeHost(c->h_lnl_pinned);
@@ -544,6 +545,7 @@ epoch_status epoch_create(epoch_ctx **out, int states, int n_epochs, const doubl
   A(dalloc(&c->d_lam, (size_t)d.S * d.K));
   A(dalloc(&c->d_V, (size_t)d.S * KK));
   A(dalloc(&c->d_Vinv, (size_t)d.S * KK));
+  if (d.K > 8) A(dalloc(&c->d_eig, eig_scratch_doubles(d.K, d.S)));  // eigenvector refinement
   A(dalloc(&c->d_catr, C));
   A(dalloc(&c->d_catw, C));
   A(dalloc(&c->d_heights, nn_max));

@@ -97,6 +97,7 @@ struct epoch_ctx {
   double *d_lam = nullptr;            // [S][K]
   double *d_V = nullptr;              // [S][K][K]
   double *d_Vinv = nullptr;           // [S][K][K]
+  double *d_eig = nullptr;            // K > 8: eigenvector refinement scratch (k_model.cu)
   double *d_dQraw = nullptr;          // [np][S][K][K]
   double *d_Dth = nullptr;            // [np][S][K][K]  V^-1 dQ_eff V (FP64)
   float *d_Dth32 = nullptr;           // same in FP32
@@ -194,6 +195,7 @@ namespace epoch {
 // k_model.cu
 cudaError_t launch_segments(epoch_ctx *c);
 cudaError_t launch_model_setup(epoch_ctx *c);
+size_t eig_scratch_doubles(int K, int S);  // eigenvector refinement scratch (K > 8)
 cudaError_t launch_param_transform(epoch_ctx *c);
 cudaError_t launch_branch_matrices(epoch_ctx *c);
 cudaError_t launch_check_heights(epoch_ctx *c);  // device-side check of d_heights

@@ -7,6 +7,8 @@
 // Eq. convolution) and Appendix A (eigen-decomposition reuse).
 #include <math.h>
 
+#include <utility>
+
 #include "epoch_internal.cuh"
 
 namespace epoch {
@@ -326,15 +328,187 @@ __device__ __forceinline__ void mm_shared(const double *X, const double *Y, doub
   __syncthreads();
 }
 
+// ---------------------------------------------------------------------------
+// FP64 refinement of the eigenvectors for large K (Ogita and Aishima 2018,
+// "Iterative refinement for symmetric eigenvalue decomposition"), restated:
+// with X the current eigenvector estimate of the symmetric S,
+//     R = I - X^T X,  T = X^T S X,  lambda_i = t_ii / (1 - r_ii),
+//     delta = 2 (||T - diag(lambda)|| + ||S|| ||R||)   (Frobenius bounds),
+//     E_ij = (t_ij + lambda_j r_ij) / (lambda_j - lambda_i)  if
+//            |lambda_i - lambda_j| > delta, else r_ij / 2  (E_ii = r_ii / 2),
+//     X <- X + X E,
+// which solves X^T X = I and X^T S X diagonal to first order, so the error
+// squares each step.  Its products are spread over many CTAs, where the
+// Jacobi sweeps they replace ran on one SM per matrix at the part's FP64
+// rate.  A pair closer than delta (an eigenvalue cluster) is only
+// orthogonalised; k_eig_finish then rotates such pairs exactly.
+// ---------------------------------------------------------------------------
+struct EigLayout {  // offsets in doubles within one matrix's block
+  int A, X0, X1, T1, T2, T3, E, lam, rs, fro2, cluster, stride;
+  __host__ __device__ explicit EigLayout(int K) {
+    const int KK = K * K;
+    A = 0;
+    X0 = KK;
+    X1 = 2 * KK;
+    T1 = 3 * KK;
+    T2 = 4 * KK;
+    T3 = 5 * KK;
+    E = 6 * KK;
+    lam = 7 * KK;
+    rs = lam + K;
+    fro2 = rs + K;
+    cluster = fro2 + 1;  // 1 when the last step left a pair closer than delta
+    stride = fro2 + 2;
+  }
+};
+
+// C = op(A) B (+ D) for the K x K matrices of every block; several products
+// per launch (blockIdx.z = matrix * n + product).  A 16 x 16 tile of C per
+// CTA, its rows of op(A) and columns of B staged in shared memory.  Offsets:
+// -1 = no D.  No output may alias an input of the same launch.  comp = 1:
+// each dot product is accumulated as an unevaluated sum s + c of FP64 values
+// with the exact rounding errors of every product (fma) and every addition
+// (Knuth's two-sum) collected in c (Ogita, Rump and Oishi 2005, "Dot2"):
+// as accurate as a dot product in twice the working precision, rounded once.
+struct EigProd {
+  int a, b, c, add, ta, comp;  // comp: compensated dot products
+};
+struct EigProds {
+  EigProd p[2];
+  int n;
+};
+__global__ void __launch_bounds__(256) k_eig_gemm(int K, double *__restrict__ base, int stride,
+                                                  EigProds pr) {
+  __shared__ double As[16][65];
+  __shared__ double Bs[64][17];
+  const int s = blockIdx.z / pr.n;
+  const EigProd q = pr.p[blockIdx.z % pr.n];
+  double *M = base + (size_t)s * stride;
+  const int i0 = blockIdx.y * 16, j0 = blockIdx.x * 16, tid = threadIdx.x;
+  for (int idx = tid; idx < 16 * K; idx += 256) {
+    const int r = idx / K, k = idx % K, i = i0 + r;
+    As[r][k] = i < K ? (q.ta ? M[q.a + k * K + i] : M[q.a + i * K + k]) : 0.0;
+  }
+  for (int idx = tid; idx < 16 * K; idx += 256) {
+    const int k = idx / 16, cc = idx % 16, j = j0 + cc;
+    Bs[k][cc] = j < K ? M[q.b + k * K + j] : 0.0;
+  }
+  __syncthreads();
+  const int r = tid / 16, cc = tid % 16, i = i0 + r, j = j0 + cc;
+  if (i < K && j < K) {
+    double acc = q.add >= 0 ? M[q.add + i * K + j] : 0.0;
+    if (q.comp) {
+      double c = 0.0;
+      for (int k = 0; k < K; k++) {
+        const double a = As[r][k], b = Bs[k][cc];
+        const double p = a * b, e = fma(a, b, -p);  // a b = p + e exactly
+        const double t = acc + p, z = t - acc;        // acc + p = t + (err) exactly
+        c += ((acc - (t - z)) + (p - z)) + e;
+        acc = t;
+      }
+      acc += c;
+    } else {
+      for (int k = 0; k < K; k++) acc = fma(As[r][k], Bs[k][cc], acc);
+    }
+    M[q.c + i * K + j] = acc;
+  }
+}
+
+// One refinement step's E and lambda from T1 = X^T X and T3 = X^T S X (one
+// CTA per matrix).
+__global__ void __launch_bounds__(256) k_eig_update(int K, double *__restrict__ base, int stride) {
+  __shared__ double red[32];
+  const EigLayout L(K);
+  double *M = base + (size_t)blockIdx.x * stride;
+  const double *T1 = M + L.T1, *T3 = M + L.T3;
+  double *lam = M + L.lam, *E = M + L.E;
+  const int KK = K * K, tid = threadIdx.x, nt = blockDim.x;
+  for (int i = tid; i < K; i += nt) lam[i] = T3[i * K + i] / T1[i * K + i];  // 1 - r_ii = t1_ii
+  __syncthreads();
+  double po = 0.0, pr = 0.0;
+  for (int idx = tid; idx < KK; idx += nt) {
+    const int i = idx / K, j = idx % K;
+    const double t = T3[idx] - (i == j ? lam[i] : 0.0);
+    const double r = (i == j ? 1.0 : 0.0) - T1[idx];
+    po += t * t;
+    pr += r * r;
+  }
+  const double off = block_sum(po, red);
+  const double rr = block_sum(pr, red);
+  const double delta = 2.0 * (sqrt(off) + sqrt(M[L.fro2]) * sqrt(rr));
+  int close = 0;
+  for (int idx = tid; idx < KK; idx += nt) {
+    const int i = idx / K, j = idx % K;
+    const double r = (i == j ? 1.0 : 0.0) - T1[idx];
+    double e = 0.5 * r;
+    if (i != j) {
+      if (fabs(lam[i] - lam[j]) > delta)
+        e = (T3[idx] + lam[j] * r) / (lam[j] - lam[i]);
+      else
+        close = 1;
+    }
+    E[idx] = e;
+  }
+  close = __syncthreads_or(close);
+  if (tid == 0) M[L.cluster] = close ? 1.0 : 0.0;
+}
+
+// After the refinement: lambda from the last step (its Rayleigh quotients,
+// formed with compensated products from an X already accurate to ~1e-14,
+// are accurate to rounding) and the updated X give lambda, V = Pi^{-1/2} X
+// and V^{-1} = X^T Pi^{1/2}.  When the last step left a pair closer than
+// delta (an eigenvalue cluster, only orthogonalised), T = X^T S X is formed
+// here and exact FP64 Jacobi sweeps rotate the pair out.  One 512-thread CTA
+// per matrix.
+__global__ void __launch_bounds__(512) k_eig_finish(int K, const double *__restrict__ base, int stride,
+                                                    int xoff, double *__restrict__ lam,
+                                                    double *__restrict__ V,
+                                                    double *__restrict__ Vinv, int *status) {
+  extern __shared__ double sm[];
+  const int KK = K * K, tid = threadIdx.x, nt = blockDim.x, s = blockIdx.x;
+  const EigLayout L(K);
+  const double *M = base + (size_t)s * stride;
+  double *A = sm, *U = A + KK, *T = U + KK, *red = T + KK, *cs = red + 32, *sn = cs + 32;
+  int *pq = (int *)(sn + 32);
+  for (int idx = tid; idx < KK; idx += nt) U[idx] = M[xoff + idx];
+  if (M[L.cluster] != 0.0) {
+    for (int idx = tid; idx < KK; idx += nt) T[idx] = M[L.A + idx];
+    __syncthreads();
+    mm_shared<0>(T, U, A, K, false);  // A = S X
+    mm_shared<0>(U, A, T, K, true);   // T = X^T S X
+    for (int idx = tid; idx < KK; idx += nt) {
+      const int i = idx / K, j = idx % K;
+      A[idx] = 0.5 * (T[idx] + T[j * K + i]);
+    }
+    __syncthreads();
+    const double fro2 = M[L.fro2];
+    const double off = jacobi_sweeps<double, 0>(A, U, K, 1e-32 * fro2, 30, red, cs, sn, pq);
+    if (off > 1e-24 * fro2 && tid == 0) atomicOr(status, ST_EIG_NOCONV);
+    for (int i = tid; i < K; i += nt) lam[(size_t)s * K + i] = A[i * K + i];
+  } else {
+    for (int i = tid; i < K; i += nt) lam[(size_t)s * K + i] = M[L.lam + i];
+  }
+  __syncthreads();
+  const double *rs = M + L.rs;
+  for (int idx = tid; idx < KK; idx += nt) {
+    const int i = idx / K, j = idx % K;
+    V[(size_t)s * KK + idx] = U[idx] / rs[i];
+    Vinv[(size_t)s * KK + idx] = U[j * K + i] * rs[j];
+  }
+}
+
 // KT: K known at compile time (0 = take d.K).  RJ: FP32 rotations in one
 // thread's registers for K <= RJ (4 or 8; one warp per matrix), or 0: shared-
 // memory sweeps by a 512-thread CTA.
+// refine != NULL (large K): stop after the FP32 rotations and hand S, the
+// rotations U (in FP64), sqrt(pi) and ||S||_F^2 to the refinement kernels
+// below, in the matrix's block of `refine` (layout: EigLayout).
 template <int KT, int RJ>
 __global__ void __launch_bounds__(RJ ? 32 : 512) k_model_setup(Dims d, int normalise, const double *__restrict__ Qraw,
                               const double *__restrict__ pi, double *__restrict__ Qn,
                               double *__restrict__ cnorm, double *__restrict__ lam,
                               double *__restrict__ V, double *__restrict__ Vinv,
-                              int *__restrict__ status) {
+                              int *__restrict__ status, double *__restrict__ refine) {
   extern __shared__ double sm[];
   const int K = KT ? KT : d.K, KK = K * K;
   const int s = blockIdx.x;
@@ -390,6 +564,17 @@ __global__ void __launch_bounds__(RJ ? 32 : 512) k_model_setup(Dims d, int norma
     __syncthreads();
   } else {
     jacobi_sweeps<float, KT>(A32, U32, K, 1e-12 * fro2, 40, red, cs32, sn32, pq);
+  }
+  if (refine) {  // the FP64 stage runs as the refinement kernels
+    const EigLayout L(K);
+    double *blk = refine + (size_t)s * L.stride;
+    for (int idx = tid; idx < KK; idx += nt) {
+      blk[L.A + idx] = A[idx];
+      blk[L.X0 + idx] = (double)U32[idx];
+    }
+    for (int i = tid; i < K; i += nt) blk[L.rs + i] = rs[i];
+    if (tid == 0) blk[L.fro2] = fro2;
+    return;
   }
   // 2. orthogonal U in FP64
   for (int idx = tid; idx < KK; idx += nt) U[idx] = (double)U32[idx];
@@ -639,15 +824,47 @@ cudaError_t launch_check_heights(epoch_ctx *c) {
   return cudaGetLastError();
 }
 
+// Large K (reversible): the FP32 rotations in k_model_setup, then
+// kEigSteps refinement steps of four launches (X^T X and S X; X^T (S X); E;
+// X + X E), the last with compensated products, and k_eig_finish.
+constexpr int kEigSteps = 5;
+bool eig_refined(const Dims &d) { return d.K > 8 && d.reversible; }
+size_t eig_scratch_doubles(int K, int S) { return (size_t)S * EigLayout(K).stride; }
+
 cudaError_t launch_model_setup(epoch_ctx *c) {
   const Dims &d = c->d;
   size_t smem = setup_smem(d);
   // small K: one warp per matrix, rotations in registers; large K: 16 warps
   const int threads = d.K <= 8 ? 32 : 512;
   auto kern = d.K == 4 ? k_model_setup<4, 4> : (d.K <= 8 ? k_model_setup<0, 8> : k_model_setup<0, 0>);
+  const bool refine = eig_refined(d) && c->d_eig;
   cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
   kern<<<d.S, threads, smem, c->stream>>>(d, c->normalise, c->d_Qraw, c->d_pi, c->d_Q, c->d_cnorm,
-                                          c->d_lam, c->d_V, c->d_Vinv, c->d_status);
+                                          c->d_lam, c->d_V, c->d_Vinv, c->d_status,
+                                          refine ? c->d_eig : nullptr);
+  c->launches++;
+  if (!refine) return cudaGetLastError();
+  const int K = d.K;
+  const EigLayout L(K);
+  const int tiles = (K + 15) / 16;
+  auto gemm = [&](EigProds pr) {
+    k_eig_gemm<<<dim3(tiles, tiles, d.S * pr.n), 256, 0, c->stream>>>(K, c->d_eig, L.stride, pr);
+    c->launches++;
+  };
+  int x = L.X0, xn = L.X1;
+  for (int it = 0; it < kEigSteps; it++) {
+    const int comp = it == kEigSteps - 1;  // the last step at the FP64 rounding floor
+    gemm(EigProds{{{x, x, L.T1, -1, 1, comp}, {L.A, x, L.T2, -1, 0, comp}}, 2});  // X^T X, S X
+    gemm(EigProds{{{x, L.T2, L.T3, -1, 1, comp}, {}}, 1});                        // X^T S X
+    k_eig_update<<<d.S, 256, 0, c->stream>>>(K, c->d_eig, L.stride);
+    c->launches++;
+    gemm(EigProds{{{x, L.E, xn, x, 0, 0}, {}}, 1});  // X + X E
+    std::swap(x, xn);
+  }
+  const size_t fsmem = sizeof(double) * (3 * (size_t)K * K + 96) + sizeof(int) * 64;
+  cudaFuncSetAttribute(k_eig_finish, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)fsmem);
+  k_eig_finish<<<d.S, 512, fsmem, c->stream>>>(K, c->d_eig, L.stride, x, c->d_lam, c->d_V,
+                                               c->d_Vinv, c->d_status);
   c->launches++;
   return cudaGetLastError();
 }
