@@ -298,6 +298,21 @@ epoch_status epoch_read_results(epoch_ctx *ctx, double *lnL, double *d_heights,
 epoch_status epoch_set_heights_device(epoch_ctx *ctx, const double *d_heights);
 epoch_status epoch_read_results_device(epoch_ctx *ctx, double *d_lnL, double *d_grad);
 
+/* One step of an inference loop in one call: the per-step inputs that are
+ * not NULL replace the current ones exactly as the setters would (Q and pi
+ * together, with the context's normalise and reversible flags; dQ with the
+ * context's parameter count; category rates and weights together; node
+ * heights of the current topology), then lnL (and, with_gradient, the
+ * gradient) is evaluated and read back as epoch_read_results.  Synchronises.
+ * The same checks and error codes as the separate calls; on an error the
+ * inputs set before it stay set. */
+epoch_status epoch_evaluate_step(epoch_ctx *ctx, const double *Q, const double *pi,
+                                 const double *dQ, const double *boundaries,
+                                 const double *cat_rates, const double *cat_weights,
+                                 const double *heights, int with_gradient, double *lnL,
+                                 double *d_heights, double *d_boundaries, double *d_params,
+                                 double *d_branch_rates);
+
 /* Counters: kernels launched by this context since creation (graph
  * replays count their kernels), and graph captures made. */
 epoch_status epoch_counters(const epoch_ctx *ctx, long long *kernel_launches,

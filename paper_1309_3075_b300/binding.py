@@ -40,6 +40,8 @@ _SIGS = {
     "epoch_destroy": [_vp],
     "epoch_last_error": [_vp],
     "epoch_path_info": [_vp, _ip, _dp, _dp, _dp],
+    "epoch_evaluate_step": [_vp, _dp, _dp, _dp, _dp, _dp, _dp, _dp, C.c_int, _dp, _dp, _dp, _dp,
+                            _dp],
     "epoch_status_string": [C.c_int],
     "epoch_set_boundaries": [_vp, _dp],
     "epoch_set_rate_matrices": [_vp, _dp, _dp, C.c_int, C.c_int],
@@ -292,6 +294,32 @@ def epoch_read_results_device(ctx, lnl_ptr=0, grad_ptr=0):
     _check(ctx, lib().epoch_read_results_device(ctx, _vp(int(lnl_ptr)) if lnl_ptr else None,
                                                 _vp(int(grad_ptr)) if grad_ptr else None),
            "epoch_read_results_device")
+
+
+def _opt(a):
+    """A float64 C pointer for an array already float64 and contiguous (the
+    caller's buffer, no copy), or NULL for None."""
+    if a is None:
+        return None
+    if a.dtype != np.float64 or not a.flags.c_contiguous:
+        raise ValueError("step inputs must be contiguous float64 arrays")
+    return a.ctypes.data_as(_dp)
+
+
+def epoch_evaluate_step(ctx, Q=None, pi=None, dQ=None, boundaries=None, cat_rates=None,
+                        cat_weights=None, heights=None, with_gradient=True, out=None):
+    """One inference step in one call (see include/epoch.h).  Inputs and the
+    outputs in ``out`` (a dict of preallocated float64 arrays with keys
+    heights, boundaries, params, branch_rates) are passed without copies.
+    Returns lnL."""
+    lnl = C.c_double(0.0)
+    o = out or {}
+    _check(ctx, lib().epoch_evaluate_step(
+        ctx, _opt(Q), _opt(pi), _opt(dQ), _opt(boundaries), _opt(cat_rates), _opt(cat_weights),
+        _opt(heights), 1 if with_gradient else 0, C.byref(lnl), _opt(o.get("heights")),
+        _opt(o.get("boundaries")), _opt(o.get("params")), _opt(o.get("branch_rates"))),
+        "epoch_evaluate_step")
+    return lnl.value
 
 
 def epoch_path_info(ctx):

@@ -1123,6 +1123,41 @@ epoch_status epoch_evaluate_async(epoch_ctx *c, int with_gradient) {
   return EPOCH_OK;
 }
 
+epoch_status epoch_evaluate_step(epoch_ctx *c, const double *Q, const double *pi, const double *dQ,
+                                 const double *boundaries, const double *cat_rates,
+                                 const double *cat_weights, const double *heights,
+                                 int with_gradient, double *lnL, double *d_heights,
+                                 double *d_boundaries, double *d_params, double *d_branch_rates) {
+  if (!c) return EPOCH_ERR_ARG;
+  epoch_status s = EPOCH_OK;
+  if (Q || pi) {
+    if (!Q || !pi) return fail(c, EPOCH_ERR_ARG, "Q and pi go together");
+    s = epoch_set_rate_matrices(c, Q, pi, c->normalise, c->d.reversible);
+    if (s != EPOCH_OK) return s;
+  }
+  if (dQ && c->d.np > 0) {
+    s = epoch_set_rate_derivatives(c, c->d.np, dQ);
+    if (s != EPOCH_OK) return s;
+  }
+  if (boundaries) {
+    s = epoch_set_boundaries(c, boundaries);
+    if (s != EPOCH_OK) return s;
+  }
+  if (cat_rates || cat_weights) {
+    if (!cat_rates || !cat_weights) return fail(c, EPOCH_ERR_ARG, "category rates and weights go together");
+    s = epoch_set_categories(c, cat_rates, cat_weights);
+    if (s != EPOCH_OK) return s;
+  }
+  if (heights) {
+    s = epoch_set_heights(c, heights);
+    if (s != EPOCH_OK) return s;
+  }
+  s = epoch_evaluate_async(c, with_gradient);
+  if (s != EPOCH_OK) return s;
+  if (!with_gradient) return epoch_read_results(c, lnL, nullptr, nullptr, nullptr, nullptr);
+  return epoch_read_results(c, lnL, d_heights, d_boundaries, d_params, d_branch_rates);
+}
+
 epoch_status epoch_read_results(epoch_ctx *c, double *lnL, double *d_heights,
                                 double *d_boundaries, double *d_params, double *d_branch_rates) {
   if (!c) return EPOCH_ERR_ARG;

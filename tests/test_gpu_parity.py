@@ -366,3 +366,44 @@ def test_auto_path_is_the_faster_and_matches_the_oracle(K, P):
         lik2.close()
     check_lnl(w, EPOCH_FP32_AUTO)
     check_grad(w, EPOCH_FP32_AUTO)
+
+
+def test_one_call_step_equals_separate_calls():
+    """epoch_evaluate_step sets the per-step inputs exactly as the setters and
+    returns the results of epoch_evaluate_async + epoch_read_results; its
+    errors are the setters' (a parent below its child: EPOCH_ERR_ARG)."""
+    w = synth.small_nucleotide(808, n_taxa=20, n_sites=300, n_cat=4, n_epochs=3, dated=True)
+    w2 = synth.small_nucleotide(809, n_taxa=20, n_sites=300, n_cat=4, n_epochs=3, dated=True)
+    nn = 2 * w.n_taxa - 1
+    for prec in (EPOCH_FP64, EPOCH_FP32):
+        a = EpochLikelihood(w, precision=prec)
+        b = EpochLikelihood(w, precision=prec)
+        try:
+            # new model and heights (w2's values on w's topology)
+            h = np.array(w.heights) * 1.1
+            Q, pi = np.ascontiguousarray(w2.Q, dtype=float), np.ascontiguousarray(w2.pi, dtype=float)
+            dQ = np.ascontiguousarray(w.dQ, dtype=float)
+            bd = np.ascontiguousarray(w.boundaries * 1.1)
+            cr = np.ascontiguousarray(w.cat_rates, dtype=float)
+            cw = np.ascontiguousarray(w.cat_weights, dtype=float)
+            out = {"heights": np.zeros(nn), "boundaries": np.zeros(w.n_epochs - 1),
+                   "params": np.zeros(a.n_params), "branch_rates": np.zeros(nn)}
+            lnl = binding.epoch_evaluate_step(a.ctx, Q, pi, dQ, bd, cr, cw, h, True, out)
+            binding.epoch_set_rate_matrices(b.ctx, Q, pi)
+            binding.epoch_set_rate_derivatives(b.ctx, dQ)
+            binding.epoch_set_boundaries(b.ctx, bd)
+            binding.epoch_set_categories(b.ctx, cr, cw)
+            binding.epoch_set_heights(b.ctx, h)
+            binding.epoch_evaluate_async(b.ctx, True)
+            lnl_b, g_b = binding.epoch_read_results(b.ctx, nn, w.n_epochs, b.n_params, True)
+            assert lnl == lnl_b
+            for k in ("heights", "boundaries", "params", "branch_rates"):
+                assert np.array_equal(out[k], np.asarray(g_b[k])[: out[k].size]), k
+            bad = h.copy()
+            bad[int(np.where(np.asarray(w.parent) < 0)[0][0])] = -1.0
+            with pytest.raises(EpochError) as e:
+                binding.epoch_evaluate_step(a.ctx, heights=bad)
+            assert e.value.status == 1
+        finally:
+            a.close()
+            b.close()
