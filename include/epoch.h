@@ -304,8 +304,12 @@ epoch_status epoch_read_results_device(epoch_ctx *ctx, double *d_lnL, double *d_
  * context's parameter count; category rates and weights together; node
  * heights of the current topology), then lnL (and, with_gradient, the
  * gradient) is evaluated and read back as epoch_read_results.  Synchronises.
- * The same checks and error codes as the separate calls; on an error the
- * inputs set before it stay set. */
+ * The same checks and error codes as the separate calls.  Every given input
+ * is checked before any is taken, so on an error nothing has changed.
+ * Host arrays (pinned or not) are free again when the call returns: they are
+ * copied into the context's pinned staging area, which one small kernel on
+ * the context's stream reads into device memory (the results come back the
+ * same way), so a step makes no copy-engine transfer. */
 epoch_status epoch_evaluate_step(epoch_ctx *ctx, const double *Q, const double *pi,
                                  const double *dQ, const double *boundaries,
                                  const double *cat_rates, const double *cat_weights,

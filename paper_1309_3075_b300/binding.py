@@ -40,8 +40,10 @@ _SIGS = {
     "epoch_destroy": [_vp],
     "epoch_last_error": [_vp],
     "epoch_path_info": [_vp, _ip, _dp, _dp, _dp],
-    "epoch_evaluate_step": [_vp, _dp, _dp, _dp, _dp, _dp, _dp, _dp, C.c_int, _dp, _dp, _dp, _dp,
-                            _dp],
+    # addresses as plain integers: the step is called every iteration, and
+    # an int marshals several times faster than a typed pointer
+    "epoch_evaluate_step": [_vp, _vp, _vp, _vp, _vp, _vp, _vp, _vp, C.c_int, _dp, _vp, _vp, _vp,
+                            _vp],
     "epoch_status_string": [C.c_int],
     "epoch_set_boundaries": [_vp, _dp],
     "epoch_set_rate_matrices": [_vp, _dp, _dp, C.c_int, C.c_int],
@@ -296,14 +298,20 @@ def epoch_read_results_device(ctx, lnl_ptr=0, grad_ptr=0):
            "epoch_read_results_device")
 
 
+_F64 = np.dtype(np.float64)
+
+
 def _opt(a):
-    """A float64 C pointer for an array already float64 and contiguous (the
-    caller's buffer, no copy), or NULL for None."""
+    """The address of an array already float64 and contiguous (the caller's
+    buffer, no copy), or NULL for None."""
     if a is None:
         return None
-    if a.dtype != np.float64 or not a.flags.c_contiguous:
+    if a.dtype != _F64 or not a.flags.c_contiguous:
         raise ValueError("step inputs must be contiguous float64 arrays")
-    return a.ctypes.data_as(_dp)
+    return a.ctypes.data
+
+
+_STEP_OUT = ("heights", "boundaries", "params", "branch_rates")
 
 
 def epoch_evaluate_step(ctx, Q=None, pi=None, dQ=None, boundaries=None, cat_rates=None,
@@ -316,10 +324,34 @@ def epoch_evaluate_step(ctx, Q=None, pi=None, dQ=None, boundaries=None, cat_rate
     o = out or {}
     _check(ctx, lib().epoch_evaluate_step(
         ctx, _opt(Q), _opt(pi), _opt(dQ), _opt(boundaries), _opt(cat_rates), _opt(cat_weights),
-        _opt(heights), 1 if with_gradient else 0, C.byref(lnl), _opt(o.get("heights")),
-        _opt(o.get("boundaries")), _opt(o.get("params")), _opt(o.get("branch_rates"))),
+        _opt(heights), 1 if with_gradient else 0, C.byref(lnl),
+        *[_opt(o.get(k)) for k in _STEP_OUT]),
         "epoch_evaluate_step")
     return lnl.value
+
+
+def epoch_step_function(ctx, Q=None, pi=None, dQ=None, boundaries=None, cat_rates=None,
+                        cat_weights=None, heights=None, with_gradient=True, out=None):
+    """epoch_evaluate_step bound to fixed buffers: the arrays' addresses are
+    taken once, and the returned function (no arguments, returns lnL) makes
+    the call with them.  The caller updates the input arrays in place
+    between calls and reads the gradient from ``out``; the arrays must stay
+    alive (and not be resized) while the function is in use."""
+    o = out or {}
+    arrays = [Q, pi, dQ, boundaries, cat_rates, cat_weights, heights] + [o.get(k) for k in _STEP_OUT]
+    addr = [_opt(a) for a in arrays]
+    lnl = C.c_double(0.0)
+    args = (ctx, *addr[:7], 1 if with_gradient else 0, C.byref(lnl), *addr[7:])
+    fn = lib().epoch_evaluate_step
+
+    def step():
+        st = fn(*args)
+        if st != 0:
+            _check(ctx, st, "epoch_evaluate_step")
+        return lnl.value
+
+    step.buffers = arrays  # keeps the arrays referenced
+    return step
 
 
 def epoch_path_info(ctx):

@@ -86,19 +86,39 @@ epoch_status ensure_param_buffers(epoch_ctx *c) {
   const Dims &d = c->d;
   const int nn_max = 2 * c->max_taxa - 1;
   dfree(c->d_gseg);
-  dfree(c->d_grad);
-  cudaFreeHost(c->h_grad_pinned);
   c->d_gseg = nullptr;
-  c->d_grad = nullptr;
-  c->h_grad_pinned = nullptr;
   size_t ng = (size_t)nn_max * d.E * d.C * (1 + d.np);
   if (c->precision == EPOCH_FP64)
     CK(dalloc((double **)&c->d_gseg, ng), "cudaMalloc(gseg)");
   else
     CK(dalloc((float **)&c->d_gseg, ng), "cudaMalloc(gseg)");
-  size_t nout = (size_t)2 * nn_max + (d.E - 1) + d.np;
-  CK(dalloc(&c->d_grad, nout), "cudaMalloc(grad)");
-  CK(cudaMallocHost((void **)&c->h_grad_pinned, nout * sizeof(double)), "cudaMallocHost");
+  // [lnL | status word | gradient]; the lnL and a pending status word carry
+  // over when the block grows
+  const size_t nout = 2 + (size_t)2 * nn_max + (d.E - 1) + d.np;
+  double *out = nullptr, *h = nullptr;
+  CK(dalloc(&out, nout), "cudaMalloc(results)");
+  if (cudaMallocHost((void **)&h, nout * sizeof(double)) != cudaSuccess) {
+    dfree(out);
+    return fail(c, EPOCH_ERR_CUDA, "cudaMallocHost(results)");
+  }
+  if (c->d_out) {
+    CK(cudaMemcpyAsync(out, c->d_out, 2 * sizeof(double), cudaMemcpyDeviceToDevice, c->stream),
+       "cudaMemcpyAsync(results)");
+    CK(cudaStreamSynchronize(c->stream), "cudaStreamSynchronize");
+    dfree(c->d_out);
+    cudaFreeHost(c->h_out);
+  } else {
+    CK(cudaMemsetAsync(out, 0, 2 * sizeof(double), c->stream), "cudaMemset(results)");
+  }
+  CK(cudaHostGetDevicePointer((void **)&c->h_out_dev, h, 0), "cudaHostGetDevicePointer(results)");
+  c->d_out = out;
+  c->h_out = h;
+  c->d_lnl = out;
+  c->d_status = reinterpret_cast<int *>(out + 1);
+  c->d_grad = out + 2;
+  c->h_lnl_pinned = h;
+  c->h_status_pinned = reinterpret_cast<int *>(h + 1);
+  c->h_grad_pinned = h + 2;
   return EPOCH_OK;
 }
 
@@ -110,10 +130,12 @@ void invalidate_graphs(epoch_ctx *c) {
   }
 }
 
-epoch_status read_status(epoch_ctx *c) {
-  CK(cudaMemcpyAsync(c->h_status_pinned, c->d_status, sizeof(int), cudaMemcpyDeviceToHost,
-                     c->stream),
-     "cudaMemcpyAsync(status)");
+// Copies the first n doubles of the result block (lnL, the status word, then
+// the gradient) to its pinned mirror, waits, and turns the status word into
+// the call's status.
+static epoch_status read_results_head(epoch_ctx *c, size_t n) {
+  CK(launch_stage(c->d_out, c->h_out_dev, n, nullptr, nullptr, 0, c->stream), "k_stage(results)");
+  c->launches++;
   CK(cudaStreamSynchronize(c->stream), "cudaStreamSynchronize");
   int st = *c->h_status_pinned;
   if (st == 0) return EPOCH_OK;
@@ -129,6 +151,8 @@ epoch_status read_status(epoch_ctx *c) {
   if (st & ST_SEGMENTS) return fail(c, EPOCH_ERR_NUMERIC, "segment overflow");
   return fail(c, EPOCH_ERR_NUMERIC, "device status word set");
 }
+
+epoch_status read_status(epoch_ctx *c) { return read_results_head(c, 2); }
 
 // ---- the enqueued sequences ---------------------------------------------
 
@@ -207,11 +231,8 @@ epoch_status copy_grad_out(epoch_ctx *c, double *d_heights, double *d_boundaries
                            double *d_params, double *d_branch_rates) {
   const Dims &d = c->d;
   const size_t nout = (size_t)2 * d.nn + (d.E - 1) + d.np;
-  // the device layout is [heights nn | boundaries E-1 | params np | rates nn]
-  CK(cudaMemcpyAsync(c->h_grad_pinned, c->d_grad, nout * sizeof(double),
-                     cudaMemcpyDeviceToHost, c->stream),
-     "cudaMemcpyAsync(grad)");
-  epoch_status s = read_status(c);
+  // the gradient's layout is [heights nn | boundaries E-1 | params np | rates nn]
+  epoch_status s = read_results_head(c, 2 + nout);
   if (s != EPOCH_OK) return s;
   const double *g = c->h_grad_pinned;
   if (d_heights) memcpy(d_heights, g, sizeof(double) * d.nn);
@@ -411,23 +432,24 @@ void epoch_destroy(epoch_ctx *c) {
   if (!c) return;
   if (c->stream) cudaStreamSynchronize(c->stream);
   invalidate_graphs(c);
-  void *bufs[] = {c->d_boundaries, c->d_phi,     c->d_Qraw,     c->d_pi,         c->d_Q,
+  void *bufs[] = {c->d_in,         c->d_phi,     c->d_Q,
                   c->d_cnorm,      c->d_lam,     c->d_V,        c->d_Vinv,       c->d_dQraw,
-                  c->d_Dth,        c->d_Dth32,   c->d_Dnz,      c->d_catr,       c->d_catw,
-                  c->d_masks,      c->d_heights, c->d_parent,   c->d_brate,      c->d_child,
+                  c->d_Dth,        c->d_Dth32,   c->d_Dnz,
+                  c->d_masks,      c->d_parent,   c->d_brate,      c->d_child,
                   c->d_level_nodes, c->d_nseg,   c->d_seg_mat,  c->d_seg_dt,     c->d_seg_hi,
                   c->d_seg_lo,     c->d_P64,     c->d_PT32,     c->d_part,       c->d_pre,
                   c->d_xbuf,       c->d_scale,   c->d_tips,     c->d_pw,         c->d_pwf,
                   c->d_site_lnl,
-                  c->d_site_inv,   c->d_lnl_part, c->d_lnl,     c->d_Gpart,      c->d_G,
-                  c->d_gseg,       c->d_grad,    c->d_status,   c->d_ctl,        c->d_site_log,
+                  c->d_site_inv,   c->d_lnl_part, c->d_out,     c->d_Gpart,      c->d_G,
+                  c->d_gseg,       c->d_ctl,        c->d_site_log,
                   c->d_level_off,  c->d_pairS,   c->d_pairL,    c->d_k4_walk,    c->d_k4_nt,
                   c->d_k4_esum,    c->d_tcB,     c->d_jumps,    c->d_jump_out,   c->d_anc,
                   c->d_eig};
   for (void *p : bufs) dfree(p);
-  if (c->h_grad_pinned) cudaFreeHost(c->h_grad_pinned);
-  if (c->h_lnl_pinned) cudaFreeHost(c->h_lnl_pinned);
-  if (c->h_status_pinned) cudaFreeHost(c->h_status_pinned);
+  if (c->h_out) cudaFreeHost(c->h_out);
+  if (c->h_in) cudaFreeHost(c->h_in);
+  if (c->h_dq) cudaFreeHost(c->h_dq);
+  if (c->in_ev) cudaEventDestroy(c->in_ev);
   if (c->h_tips_staging) cudaFreeHost(c->h_tips_staging);
   for (cudaEvent_t e : c->tips_staging_ev)
     if (e) cudaEventDestroy(e);
@@ -502,8 +524,6 @@ epoch_status epoch_create(epoch_ctx **out, int states, int n_epochs, const doubl
   d.reversible = 1;
   c->max_taxa = max_taxa;
   c->precision = precision;
-  c->h_boundaries.assign(boundaries ? boundaries : nullptr,
-                         boundaries ? boundaries + (n_epochs - 1) : nullptr);
   c->h_phi = phi;
 
   epoch_status st = check_device(c);
@@ -536,19 +556,36 @@ epoch_status epoch_create(epoch_ctx **out, int states, int n_epochs, const doubl
   const int nchunk = ceil_div(n_patterns, kTile);
   bool ok = true;
   auto A = [&](cudaError_t e) { ok = ok && (e == cudaSuccess); };
-  A(dalloc(&c->d_boundaries, std::max(1, n_epochs - 1)));
   A(dalloc(&c->d_phi, n_epochs));
-  A(dalloc(&c->d_Qraw, (size_t)d.S * KK));
-  A(dalloc(&c->d_pi, d.K));
+  {  // the per-step inputs: one device block, one pinned mirror
+    size_t *o = c->in_off;
+    o[IN_Q] = 0;                                       // Q [S][K][K]
+    o[IN_PI] = o[IN_Q] + (size_t)d.S * KK;             // pi [K]
+    o[IN_BOUND] = o[IN_PI] + d.K;                      // boundaries [E-1]
+    o[IN_CATR] = o[IN_BOUND] + std::max(1, n_epochs - 1);  // category rates [C]
+    o[IN_CATW] = o[IN_CATR] + C;                       // category weights [C]
+    o[IN_HEIGHTS] = o[IN_CATW] + C;                    // heights [nn_max]
+    o[IN_END] = o[IN_HEIGHTS] + nn_max;
+    A(dalloc(&c->d_in, o[IN_END]));
+    A(cudaMallocHost((void **)&c->h_in, sizeof(double) * o[IN_END]));
+    A(cudaEventCreateWithFlags(&c->in_ev, cudaEventDisableTiming));
+    if (ok) A(cudaHostGetDevicePointer((void **)&c->h_in_dev, c->h_in, 0));
+    if (ok) {
+      memset(c->h_in, 0, sizeof(double) * o[IN_END]);
+      c->d_Qraw = c->d_in + o[IN_Q];
+      c->d_pi = c->d_in + o[IN_PI];
+      c->d_boundaries = c->d_in + o[IN_BOUND];
+      c->d_catr = c->d_in + o[IN_CATR];
+      c->d_catw = c->d_in + o[IN_CATW];
+      c->d_heights = c->d_in + o[IN_HEIGHTS];
+    }
+  }
   A(dalloc(&c->d_Q, (size_t)d.S * KK));
   A(dalloc(&c->d_cnorm, d.S));
   A(dalloc(&c->d_lam, (size_t)d.S * d.K));
   A(dalloc(&c->d_V, (size_t)d.S * KK));
   A(dalloc(&c->d_Vinv, (size_t)d.S * KK));
   if (d.K > 8) A(dalloc(&c->d_eig, eig_scratch_doubles(d.K, d.S)));  // eigenvector refinement
-  A(dalloc(&c->d_catr, C));
-  A(dalloc(&c->d_catw, C));
-  A(dalloc(&c->d_heights, nn_max));
   A(dalloc(&c->d_parent, nn_max));
   A(dalloc(&c->d_brate, nn_max));
   A(dalloc(&c->d_child, 2 * ni_max));
@@ -568,7 +605,6 @@ epoch_status epoch_create(epoch_ctx **out, int states, int n_epochs, const doubl
   A(dalloc(&c->d_site_lnl, P));
   A(dalloc(&c->d_site_inv, P));
   A(dalloc(&c->d_lnl_part, ceil_div(n_patterns, 16)));  // one per block of >= 16 patterns
-  A(dalloc(&c->d_lnl, 1));
   if (precision == EPOCH_FP64 || states != 4 || n_categories > 8) {  // K = 4 FP32: per tree
     // G terms per pattern on the few-pattern path, else per tile of kTile
     const size_t nG = small_path(c) ? P : (size_t)nchunk;
@@ -576,12 +612,9 @@ epoch_status epoch_create(epoch_ctx **out, int states, int n_epochs, const doubl
     A(cudaMalloc(&c->d_Gpart, c->gpart_bytes));
   }
   A(dalloc(&c->d_G, (size_t)nn_max * C * KK));
-  A(dalloc(&c->d_status, 1));
   A(dalloc(&c->d_ctl, 8));
   A(dalloc(&c->d_level_off, max_taxa + 1));
   A(dalloc(&c->d_site_log, P));
-  A(cudaMallocHost((void **)&c->h_lnl_pinned, sizeof(double)));
-  A(cudaMallocHost((void **)&c->h_status_pinned, sizeof(int)));
   c->tips_staging_half = ((size_t)max_taxa * d.Pp + sizeof(float) * d.Pp + 255) & ~(size_t)255;
   A(cudaMallocHost((void **)&c->h_tips_staging, 2 * c->tips_staging_half));
   A(cudaEventCreateWithFlags(&c->tips_staging_ev[0], cudaEventDisableTiming));
@@ -595,11 +628,11 @@ epoch_status epoch_create(epoch_ctx **out, int states, int n_epochs, const doubl
   // zero the partials once: padding lanes (state >= K) must stay zero
   A(cudaMemsetAsync(c->d_part, 0, (size_t)ni_max * C * P * d.Kp * es, c->stream));
   A(cudaMemsetAsync(c->d_pre, 0, (size_t)ni_max * C * P * d.Kp * es, c->stream));
-  A(cudaMemsetAsync(c->d_status, 0, sizeof(int), c->stream));
   A(cudaMemsetAsync(c->d_P64, 0, (size_t)nn_max * C * KK * sizeof(double), c->stream));
   if (n_epochs > 1)
-    A(cudaMemcpyAsync(c->d_boundaries, boundaries, sizeof(double) * (n_epochs - 1),
-                      cudaMemcpyHostToDevice, c->stream));
+    memcpy(c->h_in + c->in_off[IN_BOUND], boundaries, sizeof(double) * (n_epochs - 1));
+  A(launch_stage(c->h_in_dev, c->d_in, c->in_off[IN_END], nullptr, nullptr, 0, c->stream));
+  A(cudaEventRecord(c->in_ev, c->stream));
   A(cudaMemcpyAsync(c->d_phi, phi.data(), sizeof(int) * n_epochs, cudaMemcpyHostToDevice,
                     c->stream));
   if (!ok || ensure_pt32(c) != EPOCH_OK || ensure_param_buffers(c) != EPOCH_OK) {
@@ -615,27 +648,53 @@ epoch_status epoch_create(epoch_ctx **out, int states, int n_epochs, const doubl
   return EPOCH_OK;
 }
 
-epoch_status epoch_set_boundaries(epoch_ctx *c, const double *boundaries) {
-  if (!c) return EPOCH_ERR_ARG;
-  const int E = c->d.E;
-  if (E == 1) return EPOCH_OK;
+// The input mirror (h_in) is written only once the last copy out of it has
+// been made.
+static epoch_status mirror_wait(epoch_ctx *c) {
+  CK(cudaEventSynchronize(c->in_ev), "cudaEventSynchronize(inputs)");
+  return EPOCH_OK;
+}
+
+// Copies doubles [lo, hi) of the input mirror to the device block and, when
+// n_dq > 0, the first n_dq doubles of the dQ mirror to d_dQraw (one k_stage
+// launch on the context's stream).
+static epoch_status upload_inputs(epoch_ctx *c, size_t lo, size_t hi, size_t n_dq = 0) {
+  if (hi < lo) hi = lo;
+  if (hi == lo && n_dq == 0) return EPOCH_OK;
+  CK(launch_stage(c->h_in_dev + lo, c->d_in + lo, hi - lo, c->h_dq_dev, c->d_dQraw, n_dq,
+                  c->stream),
+     "k_stage(inputs)");
+  c->launches++;
+  CK(cudaEventRecord(c->in_ev, c->stream), "cudaEventRecord(inputs)");
+  return EPOCH_OK;
+}
+
+static epoch_status check_boundaries(epoch_ctx *c, const double *boundaries) {
   if (!boundaries) return fail(c, EPOCH_ERR_ARG, "boundaries is NULL");
-  for (int j = 0; j < E - 1; j++) {
+  for (int j = 0; j < c->d.E - 1; j++) {
     if (!fin(boundaries[j])) return fail(c, EPOCH_ERR_ARG, "non-finite boundary");
     if (j > 0 && !(boundaries[j] > boundaries[j - 1]))
       return fail(c, EPOCH_ERR_ARG, "boundaries must be strictly increasing");
   }
-  c->h_boundaries.assign(boundaries, boundaries + (E - 1));
-  CK(cudaMemcpyAsync(c->d_boundaries, c->h_boundaries.data(), sizeof(double) * (E - 1),
-                     cudaMemcpyHostToDevice, c->stream),
-     "cudaMemcpyAsync(boundaries)");
+  return EPOCH_OK;
+}
+
+epoch_status epoch_set_boundaries(epoch_ctx *c, const double *boundaries) {
+  if (!c) return EPOCH_ERR_ARG;
+  const int E = c->d.E;
+  if (E == 1) return EPOCH_OK;
+  epoch_status s = check_boundaries(c, boundaries);
+  if (s != EPOCH_OK) return s;
+  if ((s = mirror_wait(c)) != EPOCH_OK) return s;
+  const size_t o = c->in_off[IN_BOUND];
+  memcpy(c->h_in + o, boundaries, sizeof(double) * (E - 1));
+  if ((s = upload_inputs(c, o, o + E - 1)) != EPOCH_OK) return s;
   c->have &= ~(HAVE_BRANCH | HAVE_PARTIALS | HAVE_GRADIENT);
   return EPOCH_OK;
 }
 
-epoch_status epoch_set_rate_matrices(epoch_ctx *c, const double *Q, const double *pi,
-                                     int normalise, int reversible) {
-  if (!c) return EPOCH_ERR_ARG;
+static epoch_status check_rates(epoch_ctx *c, const double *Q, const double *pi, int normalise,
+                                int reversible) {
   if (!Q || !pi) return fail(c, EPOCH_ERR_ARG, "Q or pi is NULL");
   const Dims &d = c->d;
   const int K = d.K;
@@ -675,19 +734,41 @@ epoch_status epoch_set_rate_matrices(epoch_ctx *c, const double *Q, const double
         }
     }
   }
+  return EPOCH_OK;
+}
+
+// Q and pi into the input mirror (after mirror_wait); returns the end of
+// the written range, which starts at in_off[IN_Q].
+static size_t stage_rates(epoch_ctx *c, const double *Q, const double *pi) {
+  const Dims &d = c->d;
+  memcpy(c->h_in + c->in_off[IN_Q], Q, sizeof(double) * d.S * d.KK);
+  memcpy(c->h_in + c->in_off[IN_PI], pi, sizeof(double) * d.K);
+  c->have |= HAVE_RATES;
+  return c->in_off[IN_PI] + d.K;
+}
+
+epoch_status epoch_set_rate_matrices(epoch_ctx *c, const double *Q, const double *pi,
+                                     int normalise, int reversible) {
+  if (!c) return EPOCH_ERR_ARG;
+  epoch_status s = check_rates(c, Q, pi, normalise, reversible);
+  if (s != EPOCH_OK) return s;
+  if ((s = mirror_wait(c)) != EPOCH_OK) return s;
   c->normalise = normalise ? 1 : 0;
   if (c->d.reversible != (reversible ? 1 : 0)) invalidate_graphs(c);
   c->d.reversible = reversible ? 1 : 0;
-  c->h_Qraw.assign(Q, Q + (size_t)d.S * d.KK);
-  c->h_pi.assign(pi, pi + K);
-  CK(cudaMemcpyAsync(c->d_Qraw, c->h_Qraw.data(), sizeof(double) * d.S * d.KK, cudaMemcpyHostToDevice,
-                     c->stream),
-     "cudaMemcpyAsync(Q)");
-  CK(cudaMemcpyAsync(c->d_pi, c->h_pi.data(), sizeof(double) * K, cudaMemcpyHostToDevice, c->stream),
-     "cudaMemcpyAsync(pi)");
-  c->have |= HAVE_RATES;
+  const size_t hi = stage_rates(c, Q, pi);
+  if ((s = upload_inputs(c, c->in_off[IN_Q], hi)) != EPOCH_OK) return s;
   c->have &= ~(HAVE_BRANCH | HAVE_PARTIALS | HAVE_GRADIENT);
   return EPOCH_OK;
+}
+
+// dQ through its pinned mirror (which shares the input mirror's event).
+static epoch_status upload_dq(epoch_ctx *c, const double *dQ) {
+  const size_t n = (size_t)c->d.np * c->d.S * c->d.KK;
+  epoch_status s = mirror_wait(c);
+  if (s != EPOCH_OK) return s;
+  memcpy(c->h_dq, dQ, sizeof(double) * n);
+  return upload_inputs(c, 0, 0, n);
 }
 
 epoch_status epoch_set_rate_derivatives(epoch_ctx *c, int n_params, const double *dQ) {
@@ -707,8 +788,16 @@ epoch_status epoch_set_rate_derivatives(epoch_ctx *c, int n_params, const double
     c->d_Dth32 = nullptr;
     c->d_Dnz = nullptr;
     c->d.np = n_params;
+    if (c->h_dq) {
+      CK(cudaEventSynchronize(c->in_ev), "cudaEventSynchronize(inputs)");
+      cudaFreeHost(c->h_dq);
+      c->h_dq = nullptr;
+      c->h_dq_dev = nullptr;
+    }
     if (n_params > 0) {
       const size_t n = (size_t)n_params * d.S * d.KK;
+      CK(cudaMallocHost((void **)&c->h_dq, sizeof(double) * n), "cudaMallocHost(dQ)");
+      CK(cudaHostGetDevicePointer((void **)&c->h_dq_dev, c->h_dq, 0), "cudaHostGetDevicePointer(dQ)");
       CK(dalloc(&c->d_dQraw, n), "cudaMalloc(dQ)");
       CK(dalloc(&c->d_Dth, n), "cudaMalloc(D)");
       CK(dalloc(&c->d_Dth32, n), "cudaMalloc(D32)");
@@ -718,17 +807,15 @@ epoch_status epoch_set_rate_derivatives(epoch_ctx *c, int n_params, const double
     if (s != EPOCH_OK) return s;
     invalidate_graphs(c);
   }
-  if (n_params > 0) c->h_dQ.assign(dQ, dQ + (size_t)n_params * d.S * d.KK);
-  if (n_params > 0)
-    CK(cudaMemcpyAsync(c->d_dQraw, c->h_dQ.data(), sizeof(double) * n_params * d.S * d.KK,
-                       cudaMemcpyHostToDevice, c->stream),
-       "cudaMemcpyAsync(dQ)");
+  if (n_params > 0) {
+    epoch_status s = upload_dq(c, dQ);
+    if (s != EPOCH_OK) return s;
+  }
   c->have &= ~(HAVE_BRANCH | HAVE_PARTIALS | HAVE_GRADIENT);
   return EPOCH_OK;
 }
 
-epoch_status epoch_set_categories(epoch_ctx *c, const double *rates, const double *weights) {
-  if (!c) return EPOCH_ERR_ARG;
+static epoch_status check_categories(epoch_ctx *c, const double *rates, const double *weights) {
   if (!rates || !weights) return fail(c, EPOCH_ERR_ARG, "rates or weights is NULL");
   double ws = 0.0;
   for (int k = 0; k < c->d.C; k++) {
@@ -738,15 +825,25 @@ epoch_status epoch_set_categories(epoch_ctx *c, const double *rates, const doubl
     ws += weights[k];
   }
   if (!(ws > 0.0)) return fail(c, EPOCH_ERR_ARG, "category weights sum to zero");
-  c->h_catr.assign(rates, rates + c->d.C);
-  c->h_catw.assign(weights, weights + c->d.C);
-  CK(cudaMemcpyAsync(c->d_catr, c->h_catr.data(), sizeof(double) * c->d.C, cudaMemcpyHostToDevice,
-                     c->stream),
-     "cudaMemcpyAsync(rates)");
-  CK(cudaMemcpyAsync(c->d_catw, c->h_catw.data(), sizeof(double) * c->d.C, cudaMemcpyHostToDevice,
-                     c->stream),
-     "cudaMemcpyAsync(weights)");
+  return EPOCH_OK;
+}
+
+// Category rates and weights into the input mirror (after mirror_wait);
+// returns the end of the written range, which starts at in_off[IN_CATR].
+static size_t stage_categories(epoch_ctx *c, const double *rates, const double *weights) {
+  memcpy(c->h_in + c->in_off[IN_CATR], rates, sizeof(double) * c->d.C);
+  memcpy(c->h_in + c->in_off[IN_CATW], weights, sizeof(double) * c->d.C);
   c->have |= HAVE_CATS;
+  return c->in_off[IN_CATW] + c->d.C;
+}
+
+epoch_status epoch_set_categories(epoch_ctx *c, const double *rates, const double *weights) {
+  if (!c) return EPOCH_ERR_ARG;
+  epoch_status s = check_categories(c, rates, weights);
+  if (s != EPOCH_OK) return s;
+  if ((s = mirror_wait(c)) != EPOCH_OK) return s;
+  const size_t hi = stage_categories(c, rates, weights);
+  if ((s = upload_inputs(c, c->in_off[IN_CATR], hi)) != EPOCH_OK) return s;
   c->have &= ~(HAVE_BRANCH | HAVE_PARTIALS | HAVE_GRADIENT);
   return EPOCH_OK;
 }
@@ -871,10 +968,10 @@ epoch_status epoch_set_tree(epoch_ctx *c, int n_taxa, const double *heights, con
     CK(cudaStreamSynchronize(c->stream), "cudaStreamSynchronize");  // host vectors reused
     c->have &= ~HAVE_TIPS;
   }
-  c->h_heights.assign(heights, heights + nn);
-  CK(cudaMemcpyAsync(c->d_heights, c->h_heights.data(), sizeof(double) * nn, cudaMemcpyHostToDevice,
-                     c->stream),
-     "cudaMemcpyAsync(heights)");
+  if ((s = mirror_wait(c)) != EPOCH_OK) return s;
+  memcpy(c->h_in + c->in_off[IN_HEIGHTS], heights, sizeof(double) * nn);
+  s = upload_inputs(c, c->in_off[IN_HEIGHTS], c->in_off[IN_HEIGHTS] + nn);
+  if (s != EPOCH_OK) return s;
   if (branch_rates) {
     c->h_brate.assign(branch_rates, branch_rates + nn);
     CK(cudaMemcpyAsync(c->d_brate, c->h_brate.data(), sizeof(double) * nn, cudaMemcpyHostToDevice,
@@ -898,10 +995,10 @@ epoch_status epoch_set_heights(epoch_ctx *c, const double *heights) {
   if (!heights) return fail(c, EPOCH_ERR_ARG, "heights is NULL");
   epoch_status s = validate_heights(c, c->d.N, heights, c->h_parent.data());
   if (s != EPOCH_OK) return s;
-  c->h_heights.assign(heights, heights + c->d.nn);
-  CK(cudaMemcpyAsync(c->d_heights, c->h_heights.data(), sizeof(double) * c->d.nn, cudaMemcpyHostToDevice,
-                     c->stream),
-     "cudaMemcpyAsync(heights)");
+  if ((s = mirror_wait(c)) != EPOCH_OK) return s;
+  memcpy(c->h_in + c->in_off[IN_HEIGHTS], heights, sizeof(double) * c->d.nn);
+  s = upload_inputs(c, c->in_off[IN_HEIGHTS], c->in_off[IN_HEIGHTS] + c->d.nn);
+  if (s != EPOCH_OK) return s;
   c->have &= ~(HAVE_BRANCH | HAVE_PARTIALS | HAVE_GRADIENT);
   return EPOCH_OK;
 }
@@ -983,10 +1080,7 @@ epoch_status epoch_log_likelihood(epoch_ctx *c, double *out_lnL) {
   if (!c || !out_lnL) return EPOCH_ERR_ARG;
   epoch_status s = need(c, HAVE_PARTIALS, "log_likelihood");
   if (s != EPOCH_OK) return s;
-  CK(cudaMemcpyAsync(c->h_lnl_pinned, c->d_lnl, sizeof(double), cudaMemcpyDeviceToHost,
-                     c->stream),
-     "cudaMemcpyAsync(lnL)");
-  s = read_status(c);
+  s = read_status(c);  // the lnL comes back with the status word
   if (s != EPOCH_OK) return s;
   *out_lnL = *c->h_lnl_pinned;
   return EPOCH_OK;
@@ -1129,29 +1223,47 @@ epoch_status epoch_evaluate_step(epoch_ctx *c, const double *Q, const double *pi
                                  int with_gradient, double *lnL, double *d_heights,
                                  double *d_boundaries, double *d_params, double *d_branch_rates) {
   if (!c) return EPOCH_ERR_ARG;
+  const Dims &d = c->d;
+  // every given input is checked before any is taken
   epoch_status s = EPOCH_OK;
-  if (Q || pi) {
-    if (!Q || !pi) return fail(c, EPOCH_ERR_ARG, "Q and pi go together");
-    s = epoch_set_rate_matrices(c, Q, pi, c->normalise, c->d.reversible);
-    if (s != EPOCH_OK) return s;
-  }
-  if (dQ && c->d.np > 0) {
-    s = epoch_set_rate_derivatives(c, c->d.np, dQ);
-    if (s != EPOCH_OK) return s;
-  }
-  if (boundaries) {
-    s = epoch_set_boundaries(c, boundaries);
-    if (s != EPOCH_OK) return s;
-  }
-  if (cat_rates || cat_weights) {
-    if (!cat_rates || !cat_weights) return fail(c, EPOCH_ERR_ARG, "category rates and weights go together");
-    s = epoch_set_categories(c, cat_rates, cat_weights);
-    if (s != EPOCH_OK) return s;
-  }
+  if ((Q != nullptr) != (pi != nullptr)) return fail(c, EPOCH_ERR_ARG, "Q and pi go together");
+  if ((cat_rates != nullptr) != (cat_weights != nullptr))
+    return fail(c, EPOCH_ERR_ARG, "category rates and weights go together");
+  if (Q && (s = check_rates(c, Q, pi, c->normalise, d.reversible)) != EPOCH_OK) return s;
+  if (dQ && d.np > 0)
+    for (size_t i = 0; i < (size_t)d.np * d.S * d.KK; i++)
+      if (!fin(dQ[i])) return fail(c, EPOCH_ERR_NUMERIC, "non-finite dQ");
+  if (boundaries && d.E > 1 && (s = check_boundaries(c, boundaries)) != EPOCH_OK) return s;
+  if (cat_rates && (s = check_categories(c, cat_rates, cat_weights)) != EPOCH_OK) return s;
   if (heights) {
-    s = epoch_set_heights(c, heights);
-    if (s != EPOCH_OK) return s;
+    if (!(c->have & HAVE_TREE)) return fail(c, EPOCH_ERR_ORDER, "heights before set_tree");
+    if ((s = validate_heights(c, d.N, heights, c->h_parent.data())) != EPOCH_OK) return s;
   }
+  // all of them into the mirror, then one copy over the span they cover:
+  // the regions in between hold what the device block holds
+  if ((s = mirror_wait(c)) != EPOCH_OK) return s;
+  size_t lo = c->in_off[IN_END], hi = 0;
+  auto span = [&](size_t a, size_t b) {
+    lo = std::min(lo, a);
+    hi = std::max(hi, b);
+  };
+  if (Q) span(c->in_off[IN_Q], stage_rates(c, Q, pi));
+  if (boundaries && d.E > 1) {
+    memcpy(c->h_in + c->in_off[IN_BOUND], boundaries, sizeof(double) * (d.E - 1));
+    span(c->in_off[IN_BOUND], c->in_off[IN_BOUND] + d.E - 1);
+  }
+  if (cat_rates) span(c->in_off[IN_CATR], stage_categories(c, cat_rates, cat_weights));
+  if (heights) {
+    memcpy(c->h_in + c->in_off[IN_HEIGHTS], heights, sizeof(double) * d.nn);
+    span(c->in_off[IN_HEIGHTS], c->in_off[IN_HEIGHTS] + d.nn);
+  }
+  size_t n_dq = 0;
+  if (dQ && d.np > 0) {
+    n_dq = (size_t)d.np * d.S * d.KK;
+    memcpy(c->h_dq, dQ, sizeof(double) * n_dq);
+  }
+  if ((s = upload_inputs(c, lo, hi, n_dq)) != EPOCH_OK) return s;
+  c->have &= ~(HAVE_BRANCH | HAVE_PARTIALS | HAVE_GRADIENT);
   s = epoch_evaluate_async(c, with_gradient);
   if (s != EPOCH_OK) return s;
   if (!with_gradient) return epoch_read_results(c, lnL, nullptr, nullptr, nullptr, nullptr);
@@ -1163,10 +1275,7 @@ epoch_status epoch_read_results(epoch_ctx *c, double *lnL, double *d_heights,
   if (!c) return EPOCH_ERR_ARG;
   epoch_status s = need(c, HAVE_PARTIALS, "read_results");
   if (s != EPOCH_OK) return s;
-  if (lnL)
-    CK(cudaMemcpyAsync(c->h_lnl_pinned, c->d_lnl, sizeof(double), cudaMemcpyDeviceToHost,
-                       c->stream),
-       "cudaMemcpyAsync(lnL)");
+  // the lnL comes back with the status word (and the gradient) in one copy
   if (d_heights || d_boundaries || d_params || d_branch_rates) {
     s = copy_grad_out(c, d_heights, d_boundaries, d_params, d_branch_rates);
   } else {

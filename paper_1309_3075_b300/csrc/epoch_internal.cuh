@@ -31,6 +31,9 @@ enum : unsigned {
   HAVE_GRADIENT = 64u  // G of the current inputs (expected counts need it)
 };
 
+// Regions of the per-step input block (epoch_ctx::d_in).
+enum : int { IN_Q = 0, IN_PI, IN_BOUND, IN_CATR, IN_CATW, IN_HEIGHTS, IN_END };
+
 // Device views handed to kernels (plain pointers and sizes).
 struct Dims {
   int K;      // states
@@ -73,25 +76,37 @@ struct epoch_ctx {
   int normalise = 1;
 
   // host copies of inputs
-  std::vector<double> h_boundaries;   // [E-1]
   std::vector<int> h_phi;             // [E]
   std::vector<int> h_parent;          // [nn]
-  std::vector<double> h_heights;      // [nn]
   std::vector<int> h_child;           // [NI][2]
   std::vector<int> h_level_nodes;     // internal nodes, level-ascending
   std::vector<int> h_level_off;       // [L+1]
   std::vector<unsigned long long> h_masks;
   // host copies of the other inputs: device copies are made from these
-  // (pageable, owned by the context), so a caller's array -- pinned or not --
-  // is free again when the call returns
-  std::vector<double> h_Qraw, h_pi, h_dQ, h_catr, h_catw, h_brate, h_pw;
+  // (owned by the context), so a caller's array -- pinned or not -- is free
+  // again when the call returns
+  std::vector<double> h_brate, h_pw;
   int topo_version = 0;
 
   // ---- device buffers (owned) ----
-  double *d_boundaries = nullptr;     // [E-1] (at least 1)
+  // The per-step inputs (Q, pi, boundaries, category rates and weights,
+  // heights) are regions of one device block d_in with a pinned host mirror
+  // h_in: a setter writes its region of the mirror and copies it up, and
+  // epoch_evaluate_step copies all the regions it was given with one copy.
+  // in_ev marks the last copy out of the mirror, which is written only after
+  // it; the mirror equals the device block in every region except the
+  // heights after epoch_set_heights_device (the last region, so a copy
+  // spanning it is one that was given heights).
+  double *d_in = nullptr, *h_in = nullptr;
+  size_t in_off[7] = {0, 0, 0, 0, 0, 0, 0};  // region starts (IN_Q ... IN_HEIGHTS), end
+  cudaEvent_t in_ev = nullptr;
+  double *h_dq = nullptr;             // pinned mirror of dQ [np][S][K][K]
+  // device addresses of the pinned mirrors (k_stage.cu reads and writes them)
+  double *h_in_dev = nullptr, *h_dq_dev = nullptr, *h_out_dev = nullptr;
+  double *d_boundaries = nullptr;     // [E-1] (at least 1), in d_in
   int *d_phi = nullptr;               // [E]
-  double *d_Qraw = nullptr;           // [S][K][K]
-  double *d_pi = nullptr;             // [K]
+  double *d_Qraw = nullptr;           // [S][K][K], in d_in
+  double *d_pi = nullptr;             // [K], in d_in
   double *d_Q = nullptr;              // [S][K][K] normalised
   double *d_cnorm = nullptr;          // [S]
   double *d_lam = nullptr;            // [S][K]
@@ -129,15 +144,18 @@ struct epoch_ctx {
   double *d_site_lnl = nullptr;       // [P]
   double *d_site_inv = nullptr;       // [P]  1 / scaled site value
   double *d_lnl_part = nullptr;       // [ceil(P/kTile)]
-  double *d_lnl = nullptr;            // [1]
+  // lnL, the status word and the gradient are one block d_out (pinned
+  // mirror h_out), read back with one copy: [lnL | status | gradient]
+  double *d_out = nullptr, *h_out = nullptr;
+  double *d_lnl = nullptr;            // [1], d_out[0]
   void *d_Gpart = nullptr;            // [NI*nblk*2][C][K][K] (T)
   double *d_G = nullptr;              // [nn][C][K][K]
   void *d_gseg = nullptr;             // [nn][E][C][1+np]  (T)
-  double *d_grad = nullptr;           // [nn (heights) + (E-1) + np + nn (rates)]
+  double *d_grad = nullptr;           // [nn (heights) + (E-1) + np + nn (rates)], d_out + 2
   double *d_jumps = nullptr;          // [nn][E][C][K][K] expected counts per segment
   double *d_jump_out = nullptr;       // [nn + E][K][K] per-branch | per-epoch sums
   double *d_anc = nullptr;            // [N-1][P][K] ancestral-state posteriors
-  int *d_status = nullptr;            // [1]
+  int *d_status = nullptr;            // [1], in d_out[1]
   int *d_ctl = nullptr;               // [8] block counters of last-block reductions
   double *d_site_log = nullptr;       // [P] log of the scaled root sum
   int *d_level_off = nullptr;         // [L+1] level offsets into d_level_nodes
@@ -168,7 +186,7 @@ struct epoch_ctx {
   size_t part_elem = 0;               // sizeof(T) of partials
   int max_level_width = 0;
 
-  // pinned host staging
+  // pinned host staging (views of h_out)
   double *h_grad_pinned = nullptr;
   double *h_lnl_pinned = nullptr;
   int *h_status_pinned = nullptr;
@@ -193,6 +211,10 @@ namespace epoch {
 
 // ---- kernel launch wrappers (each returns cudaGetLastError()) ----
 // k_model.cu
+// k_stage.cu: n0 doubles src0 -> dst0 and n1 doubles src1 -> dst1 (n1 may
+// be 0) by a kernel on the stream; pinned host memory by its device address
+cudaError_t launch_stage(const double *src0, double *dst0, size_t n0, const double *src1,
+                         double *dst1, size_t n1, cudaStream_t stream);
 cudaError_t launch_segments(epoch_ctx *c);
 cudaError_t launch_model_setup(epoch_ctx *c);
 size_t eig_scratch_doubles(int K, int S);  // eigenvector refinement scratch (K > 8)

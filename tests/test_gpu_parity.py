@@ -402,8 +402,33 @@ def test_one_call_step_equals_separate_calls():
             bad = h.copy()
             bad[int(np.where(np.asarray(w.parent) < 0)[0][0])] = -1.0
             with pytest.raises(EpochError) as e:
-                binding.epoch_evaluate_step(a.ctx, heights=bad)
+                binding.epoch_evaluate_step(a.ctx, Q, pi, heights=bad)
             assert e.value.status == 1
+            # a refused step changed nothing
+            assert binding.epoch_evaluate_step(a.ctx, out=out) == lnl
+
+            # bound to fixed buffers, updated in place: only the heights are
+            # given, the other inputs stay as the last step left them
+            hbuf = h.copy()
+            step = binding.epoch_step_function(a.ctx, heights=hbuf, out=out)
+            hbuf *= 1.05
+            lnl2 = step()
+            binding.epoch_set_heights(b.ctx, h * 1.05)
+            binding.epoch_evaluate_async(b.ctx, True)
+            lnl2_b, g2_b = binding.epoch_read_results(b.ctx, nn, w.n_epochs, b.n_params, True)
+            assert lnl2 == lnl2_b and lnl2 != lnl
+            for k in ("heights", "boundaries", "params", "branch_rates"):
+                assert np.array_equal(out[k], np.asarray(g2_b[k])[: out[k].size]), k
+
+            # heights set from device memory survive a step that is given
+            # other inputs (the host copy of the heights is stale then)
+            import torch
+            dh = torch.tensor(h * 0.95, dtype=torch.float64, device="cuda")
+            binding.epoch_set_heights_device(a.ctx, dh.data_ptr())
+            lnl3 = binding.epoch_evaluate_step(a.ctx, Q, pi, dQ, bd, cr, cw, None, False)
+            binding.epoch_set_heights(b.ctx, h * 0.95)
+            binding.epoch_evaluate_async(b.ctx, False)
+            assert lnl3 == binding.epoch_read_results(b.ctx, nn, w.n_epochs, b.n_params, False)[0]
         finally:
             a.close()
             b.close()
