@@ -594,8 +594,12 @@ def time_fp64(w, stream, args, clocks):
 # capture (sm__pipe_tensor_cycles_active over elapsed cycles, cycle-weighted
 # over the captured k_tc_* launches).  Reported only while the kernel source
 # is the one that was measured.
-CODON_TENSOR = {"source": "paper_1309_3075_b300/csrc/k_tc.cu", "sha1": None, "frac": None,
-                "profile": "profiles/tc_codon_gy94.md"}
+# time-weighted sm__pipe_tensor_cycles_active of the BF16 x 3 tile-product
+# launches of one codon evaluation (ncu hardware counters), valid while the
+# tensor-core source is the one it was measured on
+CODON_TENSOR = {"source": "paper_1309_3075_b300/csrc/k_tc.cu",
+                "sha1": "64aeb387c566d565e01d2f1d4ab0ce96eccf18d2", "frac": 0.063,
+                "arm": "EPOCH_FP32_TC_BF16", "profile": "profiles/tc_codon_gy94.md"}
 
 
 def codon_tensor_frac():
@@ -666,6 +670,7 @@ def run_codon(args, stream, clocks):
             "tile_product_tflops": flops / (ms * 1e-3) / 1e12,
             "arms": arms,
             "tensor_pipe_active_frac": codon_tensor_frac(),
+            "tensor_pipe_arm": CODON_TENSOR["arm"],
             "tensor_profile": CODON_TENSOR["profile"]}
 
 
