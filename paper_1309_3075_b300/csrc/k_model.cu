@@ -676,6 +676,7 @@ __global__ void k_branch_matrices(Dims d, const int *__restrict__ nseg,
                                   const double *__restrict__ V,
                                   const double *__restrict__ Vinv,
                                   const double *__restrict__ Qn,
+                                  const double *__restrict__ pi,
                                   const unsigned long long *__restrict__ masks,
                                   double *__restrict__ P64, float *__restrict__ PT32) {
   extern __shared__ double sm[];
@@ -684,9 +685,15 @@ __global__ void k_branch_matrices(Dims d, const int *__restrict__ nseg,
   const int ns = nseg[v];
   if (ns == 0) return;  // root
   double *M = sm, *W = sm + KK, *Y = sm + 2 * KK, *B = sm + 3 * KK, *ev = sm + 4 * KK;
+  double *rs = ev + K, *irs = rs + K;  // sqrt(pi_i) and its inverse
   const int tid = threadIdx.x, nt = blockDim.x;
   const double r = brate[v] * catr[c];
   for (int idx = tid; idx < KK; idx += nt) M[idx] = (idx / K == idx % K) ? 1.0 : 0.0;
+  if (d.reversible)
+    for (int i = tid; i < K; i += nt) {
+      rs[i] = sqrt(pi[i]);
+      irs[i] = 1.0 / rs[i];
+    }
   __syncthreads();
   bool M_is_identity = true;
   for (int k = 0; k < ns; k++) {
@@ -694,23 +701,37 @@ __global__ void k_branch_matrices(Dims d, const int *__restrict__ nseg,
     const double tau = r * seg_dt[v * d.E + k];
     if (tau == 0.0) continue;  // exp(0) = I exactly (zero-length branch)
     if (d.reversible) {
-      const double *Vs = V + (size_t)s * KK, *Vi = Vinv + (size_t)s * KK;
+      // With D = diag(sqrt(pi)) the eigenvectors V = D^-1 U, V^-1 = U^T D
+      // (U orthonormal, the symmetrised matrix's), so
+      //   W = V diag(ev) V^-1 = D^-1 (U diag(ev) U^T) D
+      // and the middle factor is symmetric: only its upper triangle is
+      // formed (half the FP64 multiply-adds of the plain product).
+      const double *Vs = V + (size_t)s * KK;
       for (int i = tid; i < K; i += nt) ev[i] = exp(tau * lam[(size_t)s * K + i]);
       __syncthreads();
-      // V diag(ev) and V^-1 staged in shared memory (Y and B are free here)
+      // U diag(ev) and U staged in shared memory (Y and B are free here)
       for (int idx = tid; idx < KK; idx += nt) {
-        Y[idx] = Vs[idx] * ev[idx % K];
-        B[idx] = Vi[idx];
+        const double u = Vs[idx] * rs[idx / K];
+        Y[idx] = u * ev[idx % K];
+        B[idx] = u;
       }
       __syncthreads();
-      // W = V diag(ev) V^-1; transition probabilities are >= 0, so the
-      // rounding-level negatives of the eigen form are cut at 0 (keeps
-      // every partial likelihood >= 0)
-      for (int idx = tid; idx < KK; idx += nt) {
-        int i = idx / K, j = idx % K;
+      // entry t of the upper triangle, row-major: row i holds K - i entries
+      // starting at i K - i (i - 1) / 2.  Transition probabilities are >= 0,
+      // so the rounding-level negatives of the eigen form are cut at 0
+      // (keeps every partial likelihood >= 0).
+      const int ntri = K * (K + 1) / 2;
+      for (int t = tid; t < ntri; t += nt) {
+        const float b2 = 2.f * K + 1.f;
+        int i = (int)((b2 - sqrtf(b2 * b2 - 8.f * (float)t)) * 0.5f);
+        i = i < 0 ? 0 : (i > K - 1 ? K - 1 : i);
+        while (i > 0 && i * K - i * (i - 1) / 2 > t) i--;
+        while (i + 1 < K && (i + 1) * K - (i + 1) * i / 2 <= t) i++;
+        const int j = i + (t - (i * K - i * (i - 1) / 2));
         double acc = 0.0;
-        for (int m = 0; m < K; m++) acc += Y[i * K + m] * B[m * K + j];
-        W[idx] = fmax(acc, 0.0);
+        for (int m = 0; m < K; m++) acc += Y[i * K + m] * B[j * K + m];
+        W[i * K + j] = fmax(acc * rs[j] * irs[i], 0.0);
+        if (j != i) W[j * K + i] = fmax(acc * rs[i] * irs[j], 0.0);
       }
       __syncthreads();
       if (k == 0 || M_is_identity) {
@@ -885,14 +906,15 @@ cudaError_t launch_param_transform(epoch_ctx *c) {
 
 cudaError_t launch_branch_matrices(epoch_ctx *c) {
   const Dims &d = c->d;
-  size_t smem = sizeof(double) * (4 * d.KK + d.K);
+  size_t smem = sizeof(double) * (4 * d.KK + 3 * d.K);
   cudaFuncSetAttribute(k_branch_matrices, cudaFuncAttributeMaxDynamicSharedMemorySize,
                        (int)smem);
   int threads = d.KK >= 1024 ? 256 : (d.KK >= 256 ? 128 : 32);
   dim3 grid(d.nn, d.C);
   k_branch_matrices<<<grid, threads, smem, c->stream>>>(
       d, c->d_nseg, c->d_seg_mat, c->d_seg_dt, c->d_brate, c->d_catr, c->d_lam, c->d_V,
-      c->d_Vinv, c->d_Q, c->d_masks, c->d_P64, c->precision == EPOCH_FP64 ? nullptr : c->d_PT32);
+      c->d_Vinv, c->d_Q, c->d_pi, c->d_masks, c->d_P64,
+      c->precision == EPOCH_FP64 ? nullptr : c->d_PT32);
   c->launches++;
   return cudaGetLastError();
 }
