@@ -811,6 +811,162 @@ __global__ void k_branch_matrices(Dims d, const int *__restrict__ nseg,
   }
 }
 
+
+// ---------------------------------------------------------------------------
+// The same matrices for the FP32 paths of reversible models, in double-float
+// arithmetic: a value is the unevaluated sum hi + lo of two floats (Dekker,
+// 1971), products are formed exactly with an FMA and sums by Knuth's
+// two-sum, which carries about 48 significant bits on the FP32 pipes.  FP32
+// alone would not do: the eigen form adds terms up to 1 / sqrt(pi_i pi_j)
+// whose sum can be far smaller; and every FP64 instruction, conversions
+// included, runs at a small fraction of the FP32 rate on this part, so the
+// FP64 inputs are split into float pairs once per matrix (k_df_prep) and the
+// per-branch kernel does no FP64 arithmetic but the K exponentials of each
+// segment and the P64 output.  The result (about 1e-13 of the terms' size)
+// is written as P64 and as the FP32 table PT32, like k_branch_matrices.
+// ---------------------------------------------------------------------------
+__device__ __forceinline__ float2 df_split(double x) {
+  const float h = (float)x;
+  return make_float2(h, (float)(x - (double)h));
+}
+// (sh, sl) += a b; the intrinsics keep the compiler from fusing the
+// error-free steps
+__device__ __forceinline__ void df_mac(float2 a, float2 b, float &sh, float &sl) {
+  const float ph = __fmul_rn(a.x, b.x);
+  float pe = __fmaf_rn(a.x, b.x, -ph);  // a.x b.x - ph exactly
+  pe = __fmaf_rn(a.x, b.y, pe);
+  pe = __fmaf_rn(a.y, b.x, pe);
+  const float s = __fadd_rn(sh, ph);
+  const float z = __fsub_rn(s, sh);
+  const float e = __fadd_rn(__fsub_rn(sh, __fsub_rn(s, z)), __fsub_rn(ph, z));
+  sh = s;
+  sl = __fadd_rn(sl, __fadd_rn(e, pe));
+}
+// (h, l) renormalised so that |l| <= ulp(h) / 2
+__device__ __forceinline__ float2 df_norm(float h, float l) {
+  const float s = __fadd_rn(h, l);
+  return make_float2(s, __fsub_rn(l, __fsub_rn(s, h)));
+}
+__device__ __forceinline__ float2 df_mul(float2 a, float2 b) {
+  const float ph = __fmul_rn(a.x, b.x);
+  float pe = __fmaf_rn(a.x, b.x, -ph);
+  pe = __fmaf_rn(a.x, b.y, pe);
+  pe = __fmaf_rn(a.y, b.x, pe);
+  return df_norm(ph, pe);
+}
+
+// Per matrix s: U = D V (D = diag(sqrt(pi)), U orthonormal) and the
+// diagonals of D and D^-1, as float pairs: out[s] = [U (K K) | D (K) | D^-1 (K)].
+__global__ void k_df_prep(Dims d, const double *__restrict__ V, const double *__restrict__ pi,
+                          float2 *__restrict__ out) {
+  const int K = d.K, KK = d.KK, s = blockIdx.x;
+  float2 *o = out + (size_t)s * (KK + 2 * K);
+  for (int idx = threadIdx.x; idx < KK; idx += blockDim.x)
+    o[idx] = df_split(V[(size_t)s * KK + idx] * sqrt(pi[idx / K]));
+  for (int i = threadIdx.x; i < K; i += blockDim.x) {
+    const double r = sqrt(pi[i]);
+    o[KK + i] = df_split(r);
+    o[KK + K + i] = df_split(1.0 / r);
+  }
+}
+
+__global__ void k_branch_matrices_df(Dims d, const int *__restrict__ nseg,
+                                     const int *__restrict__ seg_mat,
+                                     const double *__restrict__ seg_dt,
+                                     const double *__restrict__ brate,
+                                     const double *__restrict__ catr,
+                                     const double *__restrict__ lam,
+                                     const float2 *__restrict__ dfU,
+                                     const unsigned long long *__restrict__ masks,
+                                     double *__restrict__ P64, float *__restrict__ PT32) {
+  extern __shared__ float2 smf[];
+  const int K = d.K, KK = d.KK;
+  const int v = blockIdx.x, c = blockIdx.y;
+  const int ns = nseg[v];
+  if (ns == 0) return;  // root
+  float2 *M = smf, *W = M + KK, *Y = W + KK, *B = Y + KK, *ev = B + KK, *rs = ev + K,
+         *irs = rs + K;
+  const int tid = threadIdx.x, nt = blockDim.x;
+  const double r = brate[v] * catr[c];
+  for (int idx = tid; idx < KK; idx += nt)
+    M[idx] = make_float2((idx / K == idx % K) ? 1.f : 0.f, 0.f);
+  bool M_is_identity = true;
+  for (int k = 0; k < ns; k++) {
+    const int s = seg_mat[v * d.E + k];
+    const double tau = r * seg_dt[v * d.E + k];
+    if (tau == 0.0) continue;  // exp(0) = I exactly (zero-length branch)
+    const float2 *U = dfU + (size_t)s * (KK + 2 * K);
+    for (int i = tid; i < K; i += nt) {
+      ev[i] = df_split(exp(tau * lam[(size_t)s * K + i]));
+      rs[i] = U[KK + i];
+      irs[i] = U[KK + K + i];
+    }
+    __syncthreads();
+    for (int idx = tid; idx < KK; idx += nt) {  // B = U, Y = U diag(ev)
+      const float2 u = U[idx];
+      B[idx] = u;
+      Y[idx] = df_mul(u, ev[idx % K]);
+    }
+    __syncthreads();
+    // W = D^-1 (U diag(ev) U^T) D from the upper triangle of the symmetric
+    // middle factor (entry t: row i holds K - i entries from i K - i (i-1)/2);
+    // negatives at rounding level are cut at 0
+    const int ntri = K * (K + 1) / 2;
+    for (int t = tid; t < ntri; t += nt) {
+      const float b2 = 2.f * K + 1.f;
+      int i = (int)((b2 - sqrtf(b2 * b2 - 8.f * (float)t)) * 0.5f);
+      i = i < 0 ? 0 : (i > K - 1 ? K - 1 : i);
+      while (i > 0 && i * K - i * (i - 1) / 2 > t) i--;
+      while (i + 1 < K && (i + 1) * K - (i + 1) * i / 2 <= t) i++;
+      const int j = i + (t - (i * K - i * (i - 1) / 2));
+      float sh = 0.f, sl = 0.f;
+      for (int m = 0; m < K; m++) df_mac(Y[i * K + m], B[j * K + m], sh, sl);
+      const float2 a = df_norm(sh, sl);
+      const float2 z = make_float2(0.f, 0.f);
+      const float2 wij = df_mul(df_mul(a, rs[j]), irs[i]);
+      W[i * K + j] = wij.x > 0.f ? wij : z;
+      if (j != i) {
+        const float2 wji = df_mul(df_mul(a, rs[i]), irs[j]);
+        W[j * K + i] = wji.x > 0.f ? wji : z;
+      }
+    }
+    __syncthreads();
+    if (M_is_identity) {
+      for (int idx = tid; idx < KK; idx += nt) M[idx] = W[idx];
+    } else {  // M <- M W through Y (free again)
+      for (int idx = tid; idx < KK; idx += nt) {
+        const int i = idx / K, j = idx % K;
+        float sh = 0.f, sl = 0.f;
+        for (int m = 0; m < K; m++) df_mac(M[i * K + m], W[m * K + j], sh, sl);
+        Y[idx] = df_norm(sh, sl);
+      }
+      __syncthreads();
+      for (int idx = tid; idx < KK; idx += nt) M[idx] = Y[idx];
+    }
+    M_is_identity = false;
+    __syncthreads();
+  }
+  double *out = P64 + ((size_t)v * d.C + c) * KK;
+  for (int idx = tid; idx < KK; idx += nt) out[idx] = (double)M[idx].x + (double)M[idx].y;
+  float *pt = PT32 + ((size_t)v * d.C + c) * d.NR * d.Kp;
+  for (int idx = tid; idx < d.NR * d.Kp; idx += nt) {
+    const int row = idx / d.Kp, i = idx % d.Kp;
+    float val = 0.f;
+    if (i < K) {
+      if (row < K) {
+        val = __fadd_rn(M[i * K + row].x, M[i * K + row].y);
+      } else {  // row sums over a mask: in FP32, as the FP32 path adds them
+        const unsigned long long mk = (row == K) ? ~0ull : masks[row - K - 1];
+        float sh = 0.f, sl = 0.f;
+        for (int j = 0; j < K; j++)
+          if ((mk >> j) & 1ull) df_mac(M[i * K + j], make_float2(1.f, 0.f), sh, sl);
+        val = __fadd_rn(sh, sl);
+      }
+    }
+    pt[idx] = val;
+  }
+}
+
 }  // namespace
 
 cudaError_t launch_segments(epoch_ctx *c) {
@@ -906,6 +1062,18 @@ cudaError_t launch_param_transform(epoch_ctx *c) {
 
 cudaError_t launch_branch_matrices(epoch_ctx *c) {
   const Dims &d = c->d;
+  if (c->precision != EPOCH_FP64 && d.reversible) {
+    k_df_prep<<<d.S, 256, 0, c->stream>>>(d, c->d_V, c->d_pi, c->d_dfU);
+    const size_t smem = sizeof(float2) * (4 * (size_t)d.KK + 3 * d.K);
+    cudaFuncSetAttribute(k_branch_matrices_df, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                         (int)smem);
+    const int threads = d.KK >= 1024 ? 512 : (d.KK >= 256 ? 128 : 32);
+    k_branch_matrices_df<<<dim3(d.nn, d.C), threads, smem, c->stream>>>(
+        d, c->d_nseg, c->d_seg_mat, c->d_seg_dt, c->d_brate, c->d_catr, c->d_lam, c->d_dfU,
+        c->d_masks, c->d_P64, c->d_PT32);
+    c->launches += 2;
+    return cudaGetLastError();
+  }
   size_t smem = sizeof(double) * (4 * d.KK + 3 * d.K);
   cudaFuncSetAttribute(k_branch_matrices, cudaFuncAttributeMaxDynamicSharedMemorySize,
                        (int)smem);

@@ -107,6 +107,26 @@ def test_branch_matrices_match_oracle(prec):
         lik.close()
 
 
+@pytest.mark.parametrize("prec", [EPOCH_FP32, EPOCH_FP32_TC])
+def test_branch_matrices_double_float(prec):
+    """For K > 4 the FP32 paths form the branch matrices of reversible models
+    in double-float arithmetic (float pairs, about 48 significant bits): every
+    entry against the oracle's FP64 product (Eq. convolution) to 1e-11, for a
+    61-state codon model over 3 epochs and a 20-state model."""
+    cases = (synth.small_codon(204, n_taxa=10, n_sites=60, n_cat=2, n_epochs=3),
+             synth.tiny_tree_workload(320, K=20, n_taxa=9, n_sites=50, n_epochs=3, n_cat=2))
+    for w in cases:
+        lik = EpochLikelihood(w, precision=prec)
+        try:
+            lik.log_likelihood()
+            for v in range(2 * w.n_taxa - 2):
+                for c in range(w.n_categories):
+                    err = np.abs(lik.branch_matrix(v, c) - oracle.branch_matrix(w, v, c)).max()
+                    assert err <= 1e-11, (w.K, v, c, err)
+        finally:
+            lik.close()
+
+
 @pytest.mark.parametrize("prec", [EPOCH_FP64, EPOCH_FP32, EPOCH_FP32_TC])
 def test_codon_small(prec):
     w = synth.small_codon(203, n_taxa=10, n_sites=120, n_cat=2, n_epochs=3)
