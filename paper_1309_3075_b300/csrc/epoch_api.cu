@@ -444,7 +444,7 @@ void epoch_destroy(epoch_ctx *c) {
                   c->d_gseg,       c->d_ctl,        c->d_site_log,
                   c->d_level_off,  c->d_pairS,   c->d_pairL,    c->d_k4_walk,    c->d_k4_nt,
                   c->d_k4_esum,    c->d_tcB,     c->d_jumps,    c->d_jump_out,   c->d_anc,
-                  c->d_eig,        c->d_dfU};
+                  c->d_eig,        c->d_dfU,     c->d_eig32};
   for (void *p : bufs) dfree(p);
   if (c->h_out) cudaFreeHost(c->h_out);
   if (c->h_in) cudaFreeHost(c->h_in);
@@ -585,6 +585,7 @@ epoch_status epoch_create(epoch_ctx **out, int states, int n_epochs, const doubl
   A(dalloc(&c->d_lam, (size_t)d.S * d.K));
   A(dalloc(&c->d_V, (size_t)d.S * KK));
   A(cudaMalloc(&c->d_dfU, sizeof(float2) * (size_t)d.S * (KK + 2 * d.K)));
+  A(cudaMalloc(&c->d_eig32, sizeof(float) * (size_t)d.S * (2 * KK + d.K)));
   A(dalloc(&c->d_Vinv, (size_t)d.S * KK));
   if (d.K > 8) A(dalloc(&c->d_eig, eig_scratch_doubles(d.K, d.S)));  // eigenvector refinement
   A(dalloc(&c->d_parent, nn_max));

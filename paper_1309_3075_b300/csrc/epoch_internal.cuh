@@ -114,6 +114,7 @@ struct epoch_ctx {
   double *d_Vinv = nullptr;           // [S][K][K]
   double *d_eig = nullptr;            // K > 8: eigenvector refinement scratch (k_model.cu)
   float2 *d_dfU = nullptr;            // [S][K K + 2 K] float pairs of U, sqrt(pi), 1/sqrt(pi)
+  float *d_eig32 = nullptr;           // V [S][K][K], V^-1 [S][K][K], lambda [S][K] in FP32
   double *d_dQraw = nullptr;          // [np][S][K][K]
   double *d_Dth = nullptr;            // [np][S][K][K]  V^-1 dQ_eff V (FP64)
   float *d_Dth32 = nullptr;           // same in FP32

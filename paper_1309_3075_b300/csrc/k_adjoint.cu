@@ -195,29 +195,27 @@ __device__ __forceinline__ float t_expm1(float x) { return expm1f(x); }
 // of the rounded exponent; each dependent FP64 instruction costs tens of
 // cycles on this part, and these exponentials sit on the chain rule's
 // critical path)
-template <typename T>
-__device__ __forceinline__ T t_exp(double x);
-template <>
-__device__ __forceinline__ double t_exp<double>(double x) { return exp(x); }
-template <>
-__device__ __forceinline__ float t_exp<float>(double x) { return expf((float)x); }
+__device__ __forceinline__ double t_exp(double x) { return exp(x); }
+__device__ __forceinline__ float t_exp(float x) { return expf(x); }
 
 // Segment exponential E = exp(tau Q_s) into Eo (eigen path or
 // uniformisation); scratch W, Y, B.
+// The eigensystem (lam, V, V^-1) in the path's precision T: the FP64 one, or
+// its FP32 copy (k_df_prep), so that the FP32 kernels convert nothing.
 template <typename T>
-__device__ void seg_exp(const Dims &d, int s, double tau, const double *lam, const double *V,
-                        const double *Vinv, const double *Qn, T *Eo, T *W, T *Y, T *Bm, T *ev) {
+__device__ void seg_exp(const Dims &d, int s, double tau, const T *lam, const T *V,
+                        const T *Vinv, const double *Qn, T *Eo, T *W, T *Y, T *Bm, T *ev) {
   const int K = d.K, KK = d.KK;
   if (d.reversible) {
-    for (int i = threadIdx.x; i < K; i += blockDim.x) ev[i] = t_exp<T>(tau * lam[(size_t)s * K + i]);
+    for (int i = threadIdx.x; i < K; i += blockDim.x) ev[i] = t_exp((T)tau * lam[(size_t)s * K + i]);
     __syncthreads();
-    const double *Vs = V + (size_t)s * KK, *Vi = Vinv + (size_t)s * KK;
+    const T *Vs = V + (size_t)s * KK, *Vi = Vinv + (size_t)s * KK;
     if (sizeof(T) == sizeof(float)) {
       // E = (V diag(ev)) V^-1 through shared memory (the tiled product for
       // large K; one batch of global loads for small K)
       for (int idx = threadIdx.x; idx < KK; idx += blockDim.x) {
-        W[idx] = (T)Vs[idx] * ev[idx % K];
-        Y[idx] = (T)Vi[idx];
+        W[idx] = Vs[idx] * ev[idx % K];
+        Y[idx] = Vi[idx];
       }
       __syncthreads();
       mm<T>(d, W, Y, Eo, false, false);
@@ -227,7 +225,7 @@ __device__ void seg_exp(const Dims &d, int s, double tau, const double *lam, con
     for (int idx = threadIdx.x; idx < KK; idx += blockDim.x) {
       const int i = idx / K, j = idx % K;
       T acc = 0;
-      for (int m = 0; m < K; m++) acc += (T)Vs[i * K + m] * ev[m] * (T)Vi[m * K + j];
+      for (int m = 0; m < K; m++) acc += Vs[i * K + m] * ev[m] * Vi[m * K + j];
       Eo[idx] = acc;
     }
     __syncthreads();
@@ -273,8 +271,8 @@ template <typename T>
 __global__ void k_grad_branch(Dims d, const double *__restrict__ G, const int *__restrict__ nseg,
                               const int *__restrict__ seg_mat, const double *__restrict__ seg_dt,
                               const double *__restrict__ brate, const double *__restrict__ catr,
-                              const double *__restrict__ lam, const double *__restrict__ V,
-                              const double *__restrict__ Vinv, const double *__restrict__ Qn,
+                              const T *__restrict__ lam, const T *__restrict__ V,
+                              const T *__restrict__ Vinv, const double *__restrict__ Qn,
                               const T *__restrict__ Dth, const int *__restrict__ Dnz,
                               T *__restrict__ gseg) {
   extern __shared__ unsigned char smraw[];
@@ -324,33 +322,34 @@ __global__ void k_grad_branch(Dims d, const double *__restrict__ G, const int *_
       mm<T>(d, W, Z, H, false, true);
     }
     __syncthreads();
-    // this segment's exponential
-    seg_exp<T>(d, s, tau, lam, V, Vinv, Qn, E, W, Y, Bm, ev);
+    // this segment's exponential: the eigen form needs it only to carry A
+    // to the next segment
+    if (!d.reversible || k + 1 < ns) seg_exp<T>(d, s, tau, lam, V, Vinv, Qn, E, W, Y, Bm, ev);
     T dk;
     if (d.reversible) {
       // Hhat = V^T H V^-T  into W, with V^-1 and then V of this segment's
       // matrix staged in Bm (free on the eigen path) for the shared-memory
       // products
-      const double *Vs = V + (size_t)s * KK, *Vi = Vinv + (size_t)s * KK;
-      for (int idx = threadIdx.x; idx < KK; idx += blockDim.x) Bm[idx] = (T)Vi[idx];
+      const T *Vs = V + (size_t)s * KK, *Vi = Vinv + (size_t)s * KK;
+      for (int idx = threadIdx.x; idx < KK; idx += blockDim.x) Bm[idx] = Vi[idx];
       __syncthreads();
       mm<T>(d, H, Bm, Y, false, true);  // Y = H V^-T
       __syncthreads();
-      for (int idx = threadIdx.x; idx < KK; idx += blockDim.x) Bm[idx] = (T)Vs[idx];
+      for (int idx = threadIdx.x; idx < KK; idx += blockDim.x) Bm[idx] = Vs[idx];
       __syncthreads();
       mm<T>(d, Bm, Y, W, true, false);  // W = V^T Y
       for (int i = threadIdx.x; i < K; i += blockDim.x)
-        ev[i] = t_exp<T>(tau * lam[(size_t)s * K + i]);
+        ev[i] = t_exp((T)tau * lam[(size_t)s * K + i]);
       __syncthreads();
       T part = 0;
       for (int i = threadIdx.x; i < K; i += blockDim.x)
-        part += W[i * K + i] * (T)lam[(size_t)s * K + i] * ev[i];
+        part += W[i * K + i] * lam[(size_t)s * K + i] * ev[i];
       dk = bsum<T>(part, red);
       // model parameters: <Hhat o Phi, D_a,s>
       if (d.np > 0) {
         for (int idx = threadIdx.x; idx < KK; idx += blockDim.x) {  // W <- Hhat o Phi
           const int i = idx / K, j = idx % K;
-          const T li = (T)lam[(size_t)s * K + i], lj = (T)lam[(size_t)s * K + j];
+          const T li = lam[(size_t)s * K + i], lj = lam[(size_t)s * K + j];
           const T tt = (T)tau;
           const T xx = tt * (li - lj);
           T phi;
@@ -881,9 +880,12 @@ cudaError_t launch_chain_rule(epoch_ctx *c) {
       size_t smem = sizeof(float) * (8 * d.KK + d.K + 32);
       cudaFuncSetAttribute(k_grad_branch<float>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                            (int)smem);
+      // the eigensystem in FP32 (k_df_prep; unused by non-reversible models)
+      const size_t SKK = (size_t)d.S * d.KK;
+      const float *e32 = c->d_eig32;
       k_grad_branch<float><<<grid, threads, smem, c->stream>>>(
-          d, c->d_G, c->d_nseg, c->d_seg_mat, c->d_seg_dt, c->d_brate, c->d_catr, c->d_lam,
-          c->d_V, c->d_Vinv, c->d_Q, c->d_Dth32, c->d_Dnz, (float *)c->d_gseg);
+          d, c->d_G, c->d_nseg, c->d_seg_mat, c->d_seg_dt, c->d_brate, c->d_catr,
+          e32 + 2 * SKK, e32, e32 + SKK, c->d_Q, c->d_Dth32, c->d_Dnz, (float *)c->d_gseg);
     }
     launch_pdl(k_grad_reduce<float>, dim3(nblocks), dim3(256), 0, c->stream, d,
                (const int *)c->d_parent, (const int *)c->d_child, (const int *)c->d_nseg,

@@ -856,17 +856,27 @@ __device__ __forceinline__ float2 df_mul(float2 a, float2 b) {
 }
 
 // Per matrix s: U = D V (D = diag(sqrt(pi)), U orthonormal) and the
-// diagonals of D and D^-1, as float pairs: out[s] = [U (K K) | D (K) | D^-1 (K)].
-__global__ void k_df_prep(Dims d, const double *__restrict__ V, const double *__restrict__ pi,
-                          float2 *__restrict__ out) {
+// diagonals of D and D^-1, as float pairs: out[s] = [U (K K) | D (K) | D^-1 (K)];
+// and the eigensystem rounded to FP32 for the FP32 chain rule, laid out
+// like the FP64 one: e32 = [V (S K K) | V^-1 (S K K) | lambda (S K)].
+__global__ void k_df_prep(Dims d, const double *__restrict__ lam, const double *__restrict__ V,
+                          const double *__restrict__ Vinv, const double *__restrict__ pi,
+                          float2 *__restrict__ out, float *__restrict__ e32) {
   const int K = d.K, KK = d.KK, s = blockIdx.x;
   float2 *o = out + (size_t)s * (KK + 2 * K);
-  for (int idx = threadIdx.x; idx < KK; idx += blockDim.x)
-    o[idx] = df_split(V[(size_t)s * KK + idx] * sqrt(pi[idx / K]));
+  float *fV = e32 + (size_t)s * KK, *fVi = e32 + (size_t)(d.S + s) * KK,
+        *fl = e32 + (size_t)2 * d.S * KK + (size_t)s * K;
+  for (int idx = threadIdx.x; idx < KK; idx += blockDim.x) {
+    const double vv = V[(size_t)s * KK + idx];
+    o[idx] = df_split(vv * sqrt(pi[idx / K]));
+    fV[idx] = (float)vv;
+    fVi[idx] = (float)Vinv[(size_t)s * KK + idx];
+  }
   for (int i = threadIdx.x; i < K; i += blockDim.x) {
     const double r = sqrt(pi[i]);
     o[KK + i] = df_split(r);
     o[KK + K + i] = df_split(1.0 / r);
+    fl[i] = (float)lam[(size_t)s * K + i];
   }
 }
 
@@ -1008,6 +1018,17 @@ constexpr int kEigSteps = 5;
 bool eig_refined(const Dims &d) { return d.K > 8 && d.reversible; }
 size_t eig_scratch_doubles(int K, int S) { return (size_t)S * EigLayout(K).stride; }
 
+// FP32 paths, reversible models: the float forms of the eigensystem that
+// the branch matrices and the chain rule read (k_df_prep).
+static cudaError_t launch_df_prep(epoch_ctx *c) {
+  const Dims &d = c->d;
+  if (c->precision == EPOCH_FP64 || !d.reversible) return cudaGetLastError();
+  k_df_prep<<<d.S, 256, 0, c->stream>>>(d, c->d_lam, c->d_V, c->d_Vinv, c->d_pi, c->d_dfU,
+                                        c->d_eig32);
+  c->launches++;
+  return cudaGetLastError();
+}
+
 cudaError_t launch_model_setup(epoch_ctx *c) {
   const Dims &d = c->d;
   size_t smem = setup_smem(d);
@@ -1020,7 +1041,7 @@ cudaError_t launch_model_setup(epoch_ctx *c) {
                                           c->d_lam, c->d_V, c->d_Vinv, c->d_status,
                                           refine ? c->d_eig : nullptr);
   c->launches++;
-  if (!refine) return cudaGetLastError();
+  if (!refine) return launch_df_prep(c);
   const int K = d.K;
   const EigLayout L(K);
   const int tiles = (K + 15) / 16;
@@ -1043,7 +1064,7 @@ cudaError_t launch_model_setup(epoch_ctx *c) {
   k_eig_finish<<<d.S, 512, fsmem, c->stream>>>(K, c->d_eig, L.stride, x, c->d_lam, c->d_V,
                                                c->d_Vinv, c->d_status);
   c->launches++;
-  return cudaGetLastError();
+  return launch_df_prep(c);
 }
 
 cudaError_t launch_param_transform(epoch_ctx *c) {
@@ -1063,7 +1084,6 @@ cudaError_t launch_param_transform(epoch_ctx *c) {
 cudaError_t launch_branch_matrices(epoch_ctx *c) {
   const Dims &d = c->d;
   if (c->precision != EPOCH_FP64 && d.reversible) {
-    k_df_prep<<<d.S, 256, 0, c->stream>>>(d, c->d_V, c->d_pi, c->d_dfU);
     const size_t smem = sizeof(float2) * (4 * (size_t)d.KK + 3 * d.K);
     cudaFuncSetAttribute(k_branch_matrices_df, cudaFuncAttributeMaxDynamicSharedMemorySize,
                          (int)smem);
@@ -1071,7 +1091,7 @@ cudaError_t launch_branch_matrices(epoch_ctx *c) {
     k_branch_matrices_df<<<dim3(d.nn, d.C), threads, smem, c->stream>>>(
         d, c->d_nseg, c->d_seg_mat, c->d_seg_dt, c->d_brate, c->d_catr, c->d_lam, c->d_dfU,
         c->d_masks, c->d_P64, c->d_PT32);
-    c->launches += 2;
+    c->launches++;
     return cudaGetLastError();
   }
   size_t smem = sizeof(double) * (4 * d.KK + 3 * d.K);
