@@ -302,20 +302,29 @@ __global__ void k_grad_branch(Dims d, const double *__restrict__ G, const int *_
   for (int k = 0; k < ns; k++) {
     const int s = seg_mat[v * d.E + k];
     const double tau = r * seg_dt[v * d.E + k];
-    // Z = E_{k+1} ... E_{n-1}  (recomputed; branches rarely have many segments)
-    for (int idx = threadIdx.x; idx < KK; idx += blockDim.x) Z[idx] = (idx / K == idx % K) ? 1 : 0;
-    __syncthreads();
+    // Z = E_{k+1} ... E_{n-1}  (recomputed; branches rarely have many
+    // segments).  A (k = 0) and Z (k = ns - 1) are the identity at the ends:
+    // products with them are copies.
+    const bool A_id = (k == 0), Z_id = (k + 1 == ns);
     for (int q = k + 1; q < ns; q++) {
       seg_exp<T>(d, seg_mat[v * d.E + q], r * seg_dt[v * d.E + q], lam, V, Vinv, Qn, E, W, Y, Bm,
                  ev);
-      mm<T>(d, Z, E, W, false, false);
-      __syncthreads();
-      for (int idx = threadIdx.x; idx < KK; idx += blockDim.x) Z[idx] = W[idx];
+      if (q == k + 1) {
+        for (int idx = threadIdx.x; idx < KK; idx += blockDim.x) Z[idx] = E[idx];
+      } else {
+        mm<T>(d, Z, E, W, false, false);
+        __syncthreads();
+        for (int idx = threadIdx.x; idx < KK; idx += blockDim.x) Z[idx] = W[idx];
+      }
       __syncthreads();
     }
     // H = A^T G Z^T
-    if (ns == 1) {
+    if (A_id && Z_id) {
       for (int idx = threadIdx.x; idx < KK; idx += blockDim.x) H[idx] = Gm[idx];
+    } else if (A_id) {
+      mm<T>(d, Gm, Z, H, false, true);
+    } else if (Z_id) {
+      mm<T>(d, A, Gm, H, true, false);
     } else {
       mm<T>(d, A, Gm, W, true, false);
       __syncthreads();
@@ -402,9 +411,13 @@ __global__ void k_grad_branch(Dims d, const double *__restrict__ G, const int *_
     // A <- A E_k
     __syncthreads();
     if (k + 1 < ns) {
-      mm<T>(d, A, E, W, false, false);
-      __syncthreads();
-      for (int idx = threadIdx.x; idx < KK; idx += blockDim.x) A[idx] = W[idx];
+      if (A_id) {
+        for (int idx = threadIdx.x; idx < KK; idx += blockDim.x) A[idx] = E[idx];
+      } else {
+        mm<T>(d, A, E, W, false, false);
+        __syncthreads();
+        for (int idx = threadIdx.x; idx < KK; idx += blockDim.x) A[idx] = W[idx];
+      }
       __syncthreads();
     }
   }
