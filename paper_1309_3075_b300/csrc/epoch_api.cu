@@ -8,7 +8,6 @@
 #include <cstdio>
 #include <new>
 #include <string>
-#include <thread>
 #include <vector>
 
 #include "epoch_internal.cuh"
@@ -1019,35 +1018,18 @@ epoch_status epoch_set_tip_data(epoch_ctx *c, const int *tip_codes, const double
   // does not wait for the work queued on the stream.
   uint8_t *stage = c->h_tips_staging + c->tips_staging_cur * c->tips_staging_half;
   CK(cudaEventSynchronize(c->tips_staging_ev[c->tips_staging_cur]), "cudaEventSynchronize");
-  // rows [x0, x1): branch-free so that the loop vectorises; a large alignment
-  // is split over host threads (the packing is bound by host memory
-  // bandwidth: 4 bytes read and 1 written per code)
-  auto pack = [&](int x0, int x1, unsigned *bad) {
+  std::vector<unsigned> bad(1, 0u);
+  for (int x = 0; x < d.N; x++) {  // branch-free so that the loop vectorises
+    uint8_t *row = stage + (size_t)x * d.Pp;
+    const int *src = tip_codes + (size_t)x * d.P;
     unsigned b = 0;
-    for (int x = x0; x < x1; x++) {
-      uint8_t *row = stage + (size_t)x * d.Pp;
-      const int *src = tip_codes + (size_t)x * d.P;
-      for (int p = 0; p < d.P; p++) {
-        const unsigned code = (unsigned)src[p];
-        b |= (unsigned)(code > (unsigned)maxcode);
-        row[p] = (uint8_t)code;
-      }
-      for (int p = d.P; p < d.Pp; p++) row[p] = 0;
+    for (int p = 0; p < d.P; p++) {
+      const unsigned code = (unsigned)src[p];
+      b |= (unsigned)(code > (unsigned)maxcode);
+      row[p] = (uint8_t)code;
     }
-    *bad = b;
-  };
-  const size_t ncodes = (size_t)d.N * d.P;
-  const unsigned hw = std::max(1u, std::thread::hardware_concurrency());
-  const int nth = ncodes < ((size_t)1 << 20) ? 1 : (int)std::min<unsigned>({hw, 8u, (unsigned)d.N});
-  std::vector<unsigned> bad(nth, 0u);
-  if (nth == 1) {
-    pack(0, d.N, &bad[0]);
-  } else {
-    std::vector<std::thread> pool;
-    for (int t = 0; t < nth; t++)
-      pool.emplace_back(pack, (int)((long long)d.N * t / nth), (int)((long long)d.N * (t + 1) / nth),
-                        &bad[t]);
-    for (auto &th : pool) th.join();
+    for (int p = d.P; p < d.Pp; p++) row[p] = 0;
+    bad[0] |= b;
   }
   for (unsigned b : bad)
     if (b) return fail(c, EPOCH_ERR_ARG, "tip code out of range");
