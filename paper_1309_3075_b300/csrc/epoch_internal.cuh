@@ -285,6 +285,31 @@ cudaError_t launch_small_pre(epoch_ctx *c);   // adjoint pass; G terms per patte
 
 inline int ceil_div(long long a, long long b) { return (int)((a + b - 1) / b); }
 
+// A sum of floats carried as a float and its running rounding error (each
+// addition by Knuth's two-sum, exact): about as accurate as adding in FP64,
+// on the FP32 pipes (FP64 instructions run at a small fraction of their
+// rate on this part).  value() is the sum in FP64.
+struct CSum {
+  float s = 0.f, e = 0.f;
+  __device__ __forceinline__ void add(float x) {
+    const float t = __fadd_rn(s, x);
+    const float z = __fsub_rn(t, s);
+    e = __fadd_rn(e, __fadd_rn(__fsub_rn(s, __fsub_rn(t, z)), __fsub_rn(x, z)));
+    s = t;
+  }
+  __device__ __forceinline__ void merge(const CSum &o) {
+    add(o.s);
+    e = __fadd_rn(e, o.e);
+  }
+  __device__ __forceinline__ CSum shfl_xor(int lane_mask) const {
+    CSum o;
+    o.s = __shfl_xor_sync(0xffffffffu, s, lane_mask);
+    o.e = __shfl_xor_sync(0xffffffffu, e, lane_mask);
+    return o;
+  }
+  __device__ __forceinline__ double value() const { return (double)s + (double)e; }
+};
+
 // Programmatic dependent launch: a level kernel is launched while its
 // predecessor finishes; it reads only data of launches before the predecessor
 // (tables, topology) until pdl_wait() returns, which is when the predecessor

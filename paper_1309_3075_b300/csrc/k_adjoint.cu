@@ -110,8 +110,8 @@ __global__ void k_G_part(Dims d, const int *__restrict__ lvl_nodes, int lvl_off,
   }
 }
 
-// G[v][c][i][j] = sum over pattern blocks of Gpart (FP64 accumulate, fixed
-// order).  One thread per (child node v, c, i, j).
+// G[v][c][i][j] = sum over pattern blocks of Gpart in a fixed order (FP64 on
+// the FP64 path; compensated FP32, as accurate, on the FP32 paths).  One thread per (child node v, c, i, j).
 template <typename T>
 __global__ void k_G_reduce(Dims d, const int *__restrict__ parent, const int *__restrict__ child,
                            const T *__restrict__ Gpart, int nchunk, double *__restrict__ G) {
@@ -127,10 +127,17 @@ __global__ void k_G_reduce(Dims d, const int *__restrict__ parent, const int *__
   }
   const int slot = u - d.N;
   const int x = (child[2 * slot] == v) ? 0 : 1;
-  double acc = 0.0;
-  for (int k = 0; k < nchunk; k++)
-    acc += (double)Gpart[((((size_t)slot * nchunk + k) * 2 + x) * d.C + c) * d.KK + ij];
-  G[idx] = acc;
+  if constexpr (sizeof(T) == sizeof(float)) {  // compensated FP32 (CSum)
+    CSum acc;
+    for (int k = 0; k < nchunk; k++)
+      acc.add(Gpart[((((size_t)slot * nchunk + k) * 2 + x) * d.C + c) * d.KK + ij]);
+    G[idx] = acc.value();
+  } else {
+    double acc = 0.0;
+    for (int k = 0; k < nchunk; k++)
+      acc += (double)Gpart[((((size_t)slot * nchunk + k) * 2 + x) * d.C + c) * d.KK + ij];
+    G[idx] = acc;
+  }
 }
 
 // ---- chain rule per (branch, category) --------------------------------------

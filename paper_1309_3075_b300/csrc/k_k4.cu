@@ -759,8 +759,9 @@ __global__ void __launch_bounds__(kWalkThr) k4_walk_pre(K4Args g, const int4 *__
   }
 }
 
-// G[v][c][ij] = sum over the tiles of branch v, FP64, fixed order: the four
-// threads of a quad take every fourth tile and combine by shuffles.
+// G[v][c][ij] = sum over the tiles of branch v, compensated FP32 (CSum),
+// fixed order: the four threads of a quad take every fourth tile and combine
+// by shuffles.
 __global__ void k4_G_reduce(Dims d, int gstride, const int *__restrict__ parent,
                             const int *__restrict__ nt, const float *__restrict__ Gpart,
                             double *__restrict__ G) {
@@ -770,7 +771,7 @@ __global__ void k4_G_reduce(Dims d, int gstride, const int *__restrict__ parent,
   const long long idx = t4 >> 2;
   const int part = (int)(t4 & 3);
   const bool live = idx < (long long)d.nn * d.C * 16;
-  double acc = 0.0;
+  CSum acc;  // compensated FP32: FP64-class accuracy without FP64 instructions
   if (live) {
     const int ij = (int)(idx & 15);
     const int c = (int)((idx >> 4) % d.C);
@@ -779,12 +780,12 @@ __global__ void k4_G_reduce(Dims d, int gstride, const int *__restrict__ parent,
       const int n = nt[v];
       const float *src = Gpart + ((size_t)v * gstride * d.C + c) * 16 + ij;
 #pragma unroll 4
-      for (int t = part; t < n; t += 4) acc += (double)src[(size_t)t * d.C * 16];
+      for (int t = part; t < n; t += 4) acc.add(src[(size_t)t * d.C * 16]);
     }
   }
-  acc += __shfl_xor_sync(0xffffffffu, acc, 1);
-  acc += __shfl_xor_sync(0xffffffffu, acc, 2);
-  if (live && part == 0) G[idx] = acc;
+  acc.merge(acc.shfl_xor(1));
+  acc.merge(acc.shfl_xor(2));
+  if (live && part == 0) G[idx] = acc.value();
 }
 
 K4Args make_args(epoch_ctx *c) {
