@@ -1023,6 +1023,9 @@ size_t eig_scratch_doubles(int K, int S) { return (size_t)S * EigLayout(K).strid
 static cudaError_t launch_df_prep(epoch_ctx *c) {
   const Dims &d = c->d;
   if (c->precision == EPOCH_FP64 || !d.reversible) return cudaGetLastError();
+  // the K = 4 kernels read neither form (unless its chain rule falls back to
+  // the generic kernel)
+  if (fast_k4(c) && k4_chain_smem(d) <= 160 * 1024) return cudaGetLastError();
   k_df_prep<<<d.S, 256, 0, c->stream>>>(d, c->d_lam, c->d_V, c->d_Vinv, c->d_pi, c->d_dfU,
                                         c->d_eig32);
   c->launches++;
