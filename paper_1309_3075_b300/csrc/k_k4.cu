@@ -41,7 +41,11 @@ namespace {
 constexpr int kThr = 256;       // threads per CTA of the level kernels
 constexpr int kTP = 256;        // patterns of one fine tile
 constexpr int kWalkThr = 128;   // threads per CTA of the walks
-constexpr int kWalkWidth = 4;   // widest level the walks take
+// widest level the walks take (lnL + gradient of the 500-taxon GTR workload by
+// the widest walked level: 1 node 0.433 ms, 2: 0.432, 3: 0.432, 4: 0.448,
+// 8: 0.467, 16: 0.502 -- a level kernel over a few nodes already fills more of
+// the GPU than the walk's one thread per (pattern, category))
+constexpr int kWalkWidth = 2;
 constexpr int kWalkSlots = 32;  // value slots per walk thread (16 B each)
 constexpr size_t kWalkSmem = 160 * 1024;  // shared memory of a walk CTA at most
 enum : int { kTip = 0, kCherry = 1, kStored = 2 };
