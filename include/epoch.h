@@ -305,7 +305,9 @@ epoch_status epoch_read_results_device(epoch_ctx *ctx, double *d_lnL, double *d_
  * heights of the current topology), then lnL (and, with_gradient, the
  * gradient) is evaluated and read back as epoch_read_results.  Synchronises.
  * The same checks and error codes as the separate calls.  Every given input
- * is checked before any is taken, so on an error nothing has changed.
+ * is checked before any is taken, so an invalid input changes nothing; an
+ * error of the evaluation itself (a missing set-up call, a device status)
+ * comes after the inputs were taken, as with the separate calls.
  * Host arrays (pinned or not) are free again when the call returns: they are
  * copied into the context's pinned staging area, which one small kernel on
  * the context's stream reads into device memory (the results come back the
