@@ -343,6 +343,9 @@ __device__ __forceinline__ void mm_shared(const double *X, const double *Y, doub
 // rate.  A pair closer than delta (an eigenvalue cluster) is only
 // orthogonalised; k_eig_finish then rotates such pairs exactly.
 // ---------------------------------------------------------------------------
+// The refinement's update runs as row blocks of kEigRows rows, one CTA each
+// (at most kEigRowBlocks for K <= EPOCH_MAX_STATES).
+constexpr int kEigRows = 4, kEigRowBlocks = (EPOCH_MAX_STATES + kEigRows - 1) / kEigRows;
 struct EigLayout {  // offsets in doubles within one matrix's block
   int A, X0, X1, T1, T2, T3, E, lam, rs, fro2, cluster, stride;
   __host__ __device__ explicit EigLayout(int K) {
@@ -357,8 +360,9 @@ struct EigLayout {  // offsets in doubles within one matrix's block
     lam = 7 * KK;
     rs = lam + K;
     fro2 = rs + K;
-    cluster = fro2 + 1;  // 1 when the last step left a pair closer than delta
-    stride = fro2 + 2;
+    cluster = fro2 + 1;  // per row block of the update: 1 when the last step
+                         // left a pair closer than delta
+    stride = cluster + kEigRowBlocks;
   }
 };
 
@@ -414,16 +418,23 @@ __global__ void __launch_bounds__(256) k_eig_gemm(int K, double *__restrict__ ba
   }
 }
 
-// One refinement step's E and lambda from T1 = X^T X and T3 = X^T S X (one
-// CTA per matrix).
+// One refinement step's E and lambda from T1 = X^T X and T3 = X^T S X; grid
+// (row blocks, matrices): every CTA forms lambda and the two norms of delta
+// (the same values, in the same order) and then the E entries of its rows,
+// whose FP64 divisions dominated when one CTA did all rows.
 __global__ void __launch_bounds__(256) k_eig_update(int K, double *__restrict__ base, int stride) {
   __shared__ double red[32];
   const EigLayout L(K);
-  double *M = base + (size_t)blockIdx.x * stride;
+  double *M = base + (size_t)blockIdx.y * stride;
+  const int r0 = blockIdx.x * kEigRows, r1 = min(K, r0 + kEigRows);
   const double *T1 = M + L.T1, *T3 = M + L.T3;
-  double *lam = M + L.lam, *E = M + L.E;
+  double *E = M + L.E;
+  __shared__ double lam[EPOCH_MAX_STATES];  // every CTA forms them; row block 0 stores them
   const int KK = K * K, tid = threadIdx.x, nt = blockDim.x;
-  for (int i = tid; i < K; i += nt) lam[i] = T3[i * K + i] / T1[i * K + i];  // 1 - r_ii = t1_ii
+  for (int i = tid; i < K; i += nt) {
+    lam[i] = T3[i * K + i] / T1[i * K + i];  // 1 - r_ii = t1_ii
+    if (blockIdx.x == 0) M[L.lam + i] = lam[i];
+  }
   __syncthreads();
   double po = 0.0, pr = 0.0;
   for (int idx = tid; idx < KK; idx += nt) {
@@ -437,7 +448,7 @@ __global__ void __launch_bounds__(256) k_eig_update(int K, double *__restrict__ 
   const double rr = block_sum(pr, red);
   const double delta = 2.0 * (sqrt(off) + sqrt(M[L.fro2]) * sqrt(rr));
   int close = 0;
-  for (int idx = tid; idx < KK; idx += nt) {
+  for (int idx = r0 * K + tid; idx < r1 * K; idx += nt) {
     const int i = idx / K, j = idx % K;
     const double r = (i == j ? 1.0 : 0.0) - T1[idx];
     double e = 0.5 * r;
@@ -450,7 +461,7 @@ __global__ void __launch_bounds__(256) k_eig_update(int K, double *__restrict__ 
     E[idx] = e;
   }
   close = __syncthreads_or(close);
-  if (tid == 0) M[L.cluster] = close ? 1.0 : 0.0;
+  if (tid == 0) M[L.cluster + blockIdx.x] = close ? 1.0 : 0.0;
 }
 
 // After the refinement: lambda from the last step (its Rayleigh quotients,
@@ -471,7 +482,9 @@ __global__ void __launch_bounds__(512) k_eig_finish(int K, const double *__restr
   double *A = sm, *U = A + KK, *T = U + KK, *red = T + KK, *cs = red + 32, *sn = cs + 32;
   int *pq = (int *)(sn + 32);
   for (int idx = tid; idx < KK; idx += nt) U[idx] = M[xoff + idx];
-  if (M[L.cluster] != 0.0) {
+  bool cluster = false;
+  for (int b = 0; b < (K + kEigRows - 1) / kEigRows; b++) cluster |= M[L.cluster + b] != 0.0;
+  if (cluster) {
     for (int idx = tid; idx < KK; idx += nt) T[idx] = M[L.A + idx];
     __syncthreads();
     mm_shared<0>(T, U, A, K, false);  // A = S X
@@ -1057,7 +1070,8 @@ cudaError_t launch_model_setup(epoch_ctx *c) {
     const int comp = it == kEigSteps - 1;  // the last step at the FP64 rounding floor
     gemm(EigProds{{{x, x, L.T1, -1, 1, comp}, {L.A, x, L.T2, -1, 0, comp}}, 2});  // X^T X, S X
     gemm(EigProds{{{x, L.T2, L.T3, -1, 1, comp}, {}}, 1});                        // X^T S X
-    k_eig_update<<<d.S, 256, 0, c->stream>>>(K, c->d_eig, L.stride);
+    k_eig_update<<<dim3((K + kEigRows - 1) / kEigRows, d.S), 256, 0, c->stream>>>(K, c->d_eig,
+                                                                                 L.stride);
     c->launches++;
     gemm(EigProds{{{x, L.E, xn, x, 0, 0}, {}}, 1});  // X + X E
     std::swap(x, xn);
