@@ -112,3 +112,22 @@ def test_build_flags_target_sm_103a():
     from paper_1309_3075_b300 import build
 
     assert "arch=compute_103a,code=sm_103a" in " ".join(build.ARCH)
+
+
+def test_step_call_marshals_without_copies_and_checks_its_arrays(L):
+    """epoch_evaluate_step / epoch_step_function take contiguous float64 arrays
+    by address (no copy): anything else is refused in the binding, and a NULL
+    context is refused by the library before any device work."""
+    ok = np.zeros(16)
+    with pytest.raises(ValueError):
+        binding.epoch_evaluate_step(None, Q=np.zeros(16, dtype=np.float32), pi=ok)
+    with pytest.raises(ValueError):
+        binding.epoch_step_function(None, heights=np.zeros((4, 4))[:, 1])
+    with pytest.raises(binding.EpochError) as e:
+        binding.epoch_evaluate_step(None, heights=ok)
+    assert e.value.status == 1  # EPOCH_ERR_ARG
+    buf = np.zeros(7)
+    step = binding.epoch_step_function(None, heights=buf)
+    assert step.buffers[6] is buf  # the caller's array itself, kept referenced
+    with pytest.raises(binding.EpochError):
+        step()
