@@ -288,22 +288,17 @@ __global__ void k_grad_branch(Dims d, const double *__restrict__ G, const int *_
   const int ns = nseg[v];
   if (ns == 0) return;
   const int K = d.K, KK = d.KK;
-  // seven K x K work matrices (an FP64 K = 64 set must fit in 227 KB); G is
-  // read from global memory on the FP64 path and staged as an eighth
-  // matrix on the FP32 path
+  // seven K x K work matrices (an FP64 K = 64 set must fit in 227 KB; on the
+  // FP32 path they leave room for two CTAs per SM at K = 61); G comes from
+  // global memory into a free work matrix where a product needs it
   T *A = sm, *Z = A + KK, *H = Z + KK, *E = H + KK, *W = E + KK, *Y = W + KK, *Bm = Y + KK,
     *ev = Bm + KK, *red = ev + K;
   const double r = brate[v] * catr[c];
   const int stride = 1 + d.np;
-  const T *Gm;
-  if constexpr (sizeof(T) == sizeof(double)) {
-    Gm = reinterpret_cast<const T *>(G + ((size_t)v * d.C + c) * KK);
-  } else {
-    T *g = red + 32;
-    for (int idx = threadIdx.x; idx < KK; idx += blockDim.x)
-      g[idx] = (T)G[((size_t)v * d.C + c) * KK + idx];
-    Gm = g;
-  }
+  const double *Gd = G + ((size_t)v * d.C + c) * KK;
+  auto g_into = [&](T *dst) {
+    for (int idx = threadIdx.x; idx < KK; idx += blockDim.x) dst[idx] = (T)Gd[idx];
+  };
   for (int idx = threadIdx.x; idx < KK; idx += blockDim.x) A[idx] = (idx / K == idx % K) ? 1 : 0;
   __syncthreads();
   for (int k = 0; k < ns; k++) {
@@ -325,15 +320,21 @@ __global__ void k_grad_branch(Dims d, const double *__restrict__ G, const int *_
       }
       __syncthreads();
     }
-    // H = A^T G Z^T
+    // H = A^T G Z^T (W and Y are free here)
     if (A_id && Z_id) {
-      for (int idx = threadIdx.x; idx < KK; idx += blockDim.x) H[idx] = Gm[idx];
+      g_into(H);
     } else if (A_id) {
-      mm<T>(d, Gm, Z, H, false, true);
+      g_into(W);
+      __syncthreads();
+      mm<T>(d, W, Z, H, false, true);
     } else if (Z_id) {
-      mm<T>(d, A, Gm, H, true, false);
+      g_into(W);
+      __syncthreads();
+      mm<T>(d, A, W, H, true, false);
     } else {
-      mm<T>(d, A, Gm, W, true, false);
+      g_into(Y);
+      __syncthreads();
+      mm<T>(d, A, Y, W, true, false);
       __syncthreads();
       mm<T>(d, W, Z, H, false, true);
     }
@@ -897,7 +898,7 @@ cudaError_t launch_chain_rule(epoch_ctx *c) {
       if (e != cudaSuccess) return e;
       c->launches--;  // counted below with the reduction
     } else {
-      size_t smem = sizeof(float) * (8 * d.KK + d.K + 32);
+      size_t smem = sizeof(float) * (7 * d.KK + d.K + 32);
       cudaFuncSetAttribute(k_grad_branch<float>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                            (int)smem);
       // the eigensystem in FP32 (k_df_prep; unused by non-reversible models)
